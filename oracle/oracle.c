@@ -1,0 +1,647 @@
+/*
+ * oracle.c -- CPU oracle for the OMPDart validity data-flow (TEST
+ * INFRASTRUCTURE ONLY; see oracle.h).  Plain, single-threaded C11: FIFO
+ * worklists over explicit bit planes, no blocking, no reordering beyond the
+ * phase order the method fixes.
+ *
+ * Phase order (each phase needs only earlier ones):
+ *   1. local rule per block (Sec. IV-D: a write in one space makes the other
+ *      stale; a read needs a valid copy; Sec. IV-B: R / W / RW / unknown=RW)
+ *   2. backward anticipation AntH, AntD and Live = AntH | AntD (Sec. II-B
+ *      liveness; Sec. IV-D region-exit liveness)
+ *   3. plain host validity Hp, forward must (Sec. IV-D)
+ *   4. loop masks: needed by a node of the loop and never made stale in
+ *      the body (Sec. IV-D loop rule; Algorithm 1's outward walk)
+ *   5. device validity D, forward must, with the masks as hoisted `to' on
+ *      loop-entry edges
+ *   6. host validity H, forward must, hoisted `from' on loop-entry edges and
+ *      a live join where neither space is valid resolved toward the host
+ *   7. emission of the Table II transfers from the final states.
+ */
+#include "oracle.h"
+
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- access word decoding (the documented input format) --------------- */
+#define A_KIND_R 1
+#define A_KIND_W 2
+#define A_KIND_RW 3
+#define SPACE_HOST 0
+#define SPACE_DEV 1
+
+static int a_var(uint32_t a) { return (int)(a & 0xFFFFFFu); }
+static int a_kind(uint32_t a) { return (int)((a >> 24) & 3u); }
+static int a_space(uint32_t a) { return (int)((a >> 26) & 1u); }
+static int a_is_call(uint32_t a) { return (int)(a >> 31); }
+static int a_call_row(uint32_t a) { return (int)(a & 0x7FFFFFFFu); }
+
+/* ---- bit rows ---------------------------------------------------------- */
+static int get_bit(const uint64_t *row, int v) { return (int)((row[v >> 6] >> (v & 63)) & 1u); }
+static void set_bit(uint64_t *row, int v, int x) {
+  uint64_t m = (uint64_t)1 << (v & 63);
+  if (x) row[v >> 6] |= m; else row[v >> 6] &= ~m;
+}
+
+typedef struct {
+  int N, E, A, W, V, entry;
+  const int32_t *so, *s, *ao;
+  const uint32_t *acc;
+  int32_t *po, *ps, *pe;   /* predecessor CSR: source block, edge id */
+  uint8_t *reach;
+  uint64_t *top;           /* [W] all variables set */
+} graph;
+
+static void *xcalloc(size_t n, size_t sz) { return calloc(n ? n : 1, sz); }
+
+/* ---- validation --------------------------------------------------------- */
+static int validate(const oracle_cfg *c) {
+  if (!c || c->n_blocks < 1 || c->n_vars < 1 || c->n_vars > (1 << 24)) return ORACLE_E_INVALID;
+  if (c->entry < 0 || c->entry >= c->n_blocks) return ORACLE_E_INVALID;
+  if (!c->succ_off || !c->acc_off) return ORACLE_E_INVALID;
+  if (c->succ_off[0] != 0 || c->acc_off[0] != 0) return ORACLE_E_INVALID;
+  for (int b = 0; b < c->n_blocks; ++b)
+    if (c->succ_off[b + 1] < c->succ_off[b] || c->acc_off[b + 1] < c->acc_off[b]) return ORACLE_E_INVALID;
+  int E = c->succ_off[c->n_blocks], A = c->acc_off[c->n_blocks];
+  if ((E && !c->succ) || (A && !c->acc)) return ORACLE_E_INVALID;
+  for (int e = 0; e < E; ++e) {
+    if (c->succ[e] < 0 || c->succ[e] >= c->n_blocks) return ORACLE_E_INVALID;
+    if (c->succ[e] == c->entry) return ORACLE_E_INVALID; /* entry has no predecessors */
+  }
+  for (int i = 0; i < A; ++i) {
+    uint32_t a = c->acc[i];
+    if (a_is_call(a)) {
+      if (!c->call_planes || a_call_row(a) >= c->n_calls) return ORACLE_E_INVALID;
+    } else {
+      if ((a >> 27) & 0xFu) return ORACLE_E_INVALID;
+      if (a_var(a) >= c->n_vars || a_kind(a) == 0) return ORACLE_E_INVALID;
+    }
+  }
+  return ORACLE_OK;
+}
+
+/* ---- predecessors and reachability -------------------------------------- */
+static int build_graph(const oracle_cfg *c, graph *g) {
+  memset(g, 0, sizeof *g);
+  g->N = c->n_blocks; g->V = c->n_vars; g->W = (c->n_vars + 63) / 64; g->entry = c->entry;
+  g->so = c->succ_off; g->s = c->succ; g->ao = c->acc_off; g->acc = c->acc;
+  g->E = c->succ_off[g->N]; g->A = c->acc_off[g->N];
+  g->po = xcalloc((size_t)g->N + 1, sizeof(int32_t));
+  g->ps = xcalloc((size_t)g->E, sizeof(int32_t));
+  g->pe = xcalloc((size_t)g->E, sizeof(int32_t));
+  g->reach = xcalloc((size_t)g->N, 1);
+  g->top = xcalloc((size_t)g->W, sizeof(uint64_t));
+  if (!g->po || !g->ps || !g->pe || !g->reach || !g->top) return ORACLE_E_NOMEM;
+  for (int e = 0; e < g->E; ++e) g->po[g->s[e] + 1]++;
+  for (int b = 0; b < g->N; ++b) g->po[b + 1] += g->po[b];
+  int32_t *fill = xcalloc((size_t)g->N, sizeof(int32_t));
+  if (!fill) return ORACLE_E_NOMEM;
+  for (int b = 0; b < g->N; ++b)
+    for (int e = g->so[b]; e < g->so[b + 1]; ++e) {
+      int t = g->s[e], k = g->po[t] + fill[t]++;
+      g->ps[k] = b; g->pe[k] = e;
+    }
+  free(fill);
+  for (int v = 0; v < g->V; ++v) set_bit(g->top, v, 1);
+  /* breadth-first reachability from the entry */
+  int32_t *q = xcalloc((size_t)g->N, sizeof(int32_t));
+  if (!q) return ORACLE_E_NOMEM;
+  int qh = 0, qt = 0;
+  q[qt++] = g->entry; g->reach[g->entry] = 1;
+  while (qh < qt) {
+    int b = q[qh++];
+    for (int e = g->so[b]; e < g->so[b + 1]; ++e)
+      if (!g->reach[g->s[e]]) { g->reach[g->s[e]] = 1; q[qt++] = g->s[e]; }
+  }
+  free(q);
+  return ORACLE_OK;
+}
+
+static void free_graph(graph *g) {
+  free(g->po); free(g->ps); free(g->pe); free(g->reach); free(g->top);
+}
+
+/* ---- step 1: local rule -------------------------------------------------
+ * Per block and variable, scanning the accesses in order (RW = read then
+ * write; a call row contributes its reads, then its net effect):
+ *   events touching space S: an S-read, an S-write, a write in the other
+ *   space.  GenS = last such event is an S-access; KillS = it is a write in
+ *   the other space.  UES = the first event among {S-read, any write} is an
+ *   S-read.  Def = some (must-)write.
+ * Implemented as a tiny state machine per variable: last[S] in {0 none,
+ * 1 S-access, 2 other-space write}; ue[S] in {0 undecided, 1 read first,
+ * 2 write first}. */
+typedef struct { uint8_t last[2], ue[2], def; } lstate;
+
+static void ev_read(lstate *st, int S) {
+  st->last[S] = 1;
+  if (st->ue[S] == 0) st->ue[S] = 1;
+}
+static void ev_write(lstate *st, int S) {
+  st->last[S] = 1;
+  st->last[1 - S] = 2;
+  if (st->ue[0] == 0) st->ue[0] = 2;
+  if (st->ue[1] == 0) st->ue[1] = 2;
+  st->def = 1;
+}
+
+/* planes of call row r, plane k (0 ReqH,1 ReqD,2 GenH,3 KillH,4 GenD,5 KillD,6 MustDef) */
+static const uint64_t *call_plane(const oracle_cfg *c, int W, int r, int k) {
+  return c->call_planes + ((size_t)r * 7 + (size_t)k) * (size_t)W;
+}
+
+static void local_rule(const oracle_cfg *c, const graph *g, uint64_t *GH, uint64_t *KH, uint64_t *GD,
+                       uint64_t *KD, uint64_t *UH, uint64_t *UD, uint64_t *DF) {
+  int W = g->W;
+  lstate *st = xcalloc((size_t)g->V, sizeof(lstate));
+  uint8_t *touched = xcalloc((size_t)g->V, 1);
+  int32_t *list = xcalloc((size_t)g->V, sizeof(int32_t));
+  for (int b = 0; b < g->N; ++b) {
+    int nt = 0;
+    for (int i = g->ao[b]; i < g->ao[b + 1]; ++i) {
+      uint32_t a = g->acc[i];
+      if (a_is_call(a)) {
+        int r = a_call_row(a);
+        for (int v = 0; v < g->V; ++v) {
+          int rq_h = get_bit(call_plane(c, W, r, 0), v), rq_d = get_bit(call_plane(c, W, r, 1), v);
+          int gh = get_bit(call_plane(c, W, r, 2), v), kh = get_bit(call_plane(c, W, r, 3), v);
+          int gd = get_bit(call_plane(c, W, r, 4), v), kd = get_bit(call_plane(c, W, r, 5), v);
+          int md = get_bit(call_plane(c, W, r, 6), v);
+          if (!(rq_h | rq_d | gh | kh | gd | kd | md)) continue;
+          if (!touched[v]) { touched[v] = 1; list[nt++] = v; memset(&st[v], 0, sizeof(lstate)); }
+          lstate *s = &st[v];
+          if (rq_h) ev_read(s, SPACE_HOST);
+          if (rq_d) ev_read(s, SPACE_DEV);
+          /* net effect on each space after the callee body */
+          if (gh) s->last[SPACE_HOST] = 1; else if (kh) s->last[SPACE_HOST] = 2;
+          if (gd) s->last[SPACE_DEV] = 1; else if (kd) s->last[SPACE_DEV] = 2;
+          if (md) {
+            s->def = 1;
+            if (s->ue[0] == 0) s->ue[0] = 2;
+            if (s->ue[1] == 0) s->ue[1] = 2;
+          }
+        }
+        continue;
+      }
+      int v = a_var(a), k = a_kind(a), S = a_space(a);
+      if (!touched[v]) { touched[v] = 1; list[nt++] = v; memset(&st[v], 0, sizeof(lstate)); }
+      if (k & A_KIND_R) ev_read(&st[v], S);
+      if (k & A_KIND_W) ev_write(&st[v], S);
+    }
+    size_t o = (size_t)b * W;
+    for (int j = 0; j < nt; ++j) {
+      int v = list[j];
+      lstate *s = &st[v];
+      if (GH) set_bit(GH + o, v, s->last[SPACE_HOST] == 1);
+      if (KH) set_bit(KH + o, v, s->last[SPACE_HOST] == 2);
+      if (GD) set_bit(GD + o, v, s->last[SPACE_DEV] == 1);
+      if (KD) set_bit(KD + o, v, s->last[SPACE_DEV] == 2);
+      if (UH) set_bit(UH + o, v, s->ue[SPACE_HOST] == 1);
+      if (UD) set_bit(UD + o, v, s->ue[SPACE_DEV] == 1);
+      if (DF) set_bit(DF + o, v, s->def);
+      touched[v] = 0;
+    }
+  }
+  free(st); free(touched); free(list);
+}
+
+/* ---- FIFO worklist ------------------------------------------------------ */
+typedef struct { int32_t *q; uint8_t *in; int n, head, count; } wlist;
+static int wl_init(wlist *w, int n) {
+  w->q = xcalloc((size_t)n, sizeof(int32_t)); w->in = xcalloc((size_t)n, 1);
+  w->n = n; w->head = 0; w->count = 0;
+  return (w->q && w->in) ? ORACLE_OK : ORACLE_E_NOMEM;
+}
+static void wl_push(wlist *w, int b) {
+  if (w->in[b]) return;
+  w->in[b] = 1; w->q[(w->head + w->count) % w->n] = b; w->count++;
+}
+static int wl_pop(wlist *w) {
+  int b = w->q[w->head]; w->head = (w->head + 1) % w->n; w->count--; w->in[b] = 0;
+  return b;
+}
+static void wl_free(wlist *w) { free(w->q); free(w->in); }
+
+/* ---- step 2: backward anticipation (least fixed point) ------------------
+ * AntS_out[b] = OR over successors s of AntS_in[s]; a block with no
+ * successor sees the region exit, where AntH = exit_host_live, AntD = 0.
+ * AntS_in[b] = UES[b] | (AntS_out[b] & ~Def[b]).  Over reachable blocks. */
+static int anticipation(const graph *g, const uint64_t *UES, const uint64_t *DF, const uint64_t *exit_live,
+                        uint64_t *ant_in) {
+  int W = g->W;
+  wlist wl;
+  if (wl_init(&wl, g->N)) return ORACLE_E_NOMEM;
+  uint64_t *out = xcalloc((size_t)W, sizeof(uint64_t));
+  memset(ant_in, 0, (size_t)g->N * W * sizeof(uint64_t));
+  for (int b = g->N - 1; b >= 0; --b) if (g->reach[b]) wl_push(&wl, b);
+  while (wl.count) {
+    int b = wl_pop(&wl);
+    if (g->so[b] == g->so[b + 1]) {
+      for (int w = 0; w < W; ++w) out[w] = exit_live ? exit_live[w] : 0;
+    } else {
+      memset(out, 0, (size_t)W * sizeof(uint64_t));
+      for (int e = g->so[b]; e < g->so[b + 1]; ++e)
+        for (int w = 0; w < W; ++w) out[w] |= ant_in[(size_t)g->s[e] * W + w];
+    }
+    int changed = 0;
+    for (int w = 0; w < W; ++w) {
+      size_t o = (size_t)b * W + w;
+      uint64_t nv = UES[o] | (out[w] & ~DF[o]);
+      if (nv != ant_in[o]) { ant_in[o] = nv; changed = 1; }
+    }
+    if (changed)
+      for (int k = g->po[b]; k < g->po[b + 1]; ++k)
+        if (g->reach[g->ps[k]]) wl_push(&wl, g->ps[k]);
+  }
+  free(out); wl_free(&wl);
+  return ORACLE_OK;
+}
+
+/* ---- steps 3, 5, 6: forward must problems (greatest fixed point) --------
+ * x_in[entry] = init; x_in[b] = AND over reachable predecessors p of
+ *   (x_out[p] | edge_gen(p->b)); then x_in[b] |= node_gen[b] (H only);
+ * x_out[b] = Gen[b] | (x_in[b] & ~Kill[b]).  Unreachable blocks stay at
+ * the top element and never enter a meet. */
+typedef struct {
+  const uint64_t *gen, *kill, *init;       /* init [W]                      */
+  const uint8_t *is_entry_edge;            /* [E] loop-entry edge flags      */
+  const uint64_t *edge_mask;               /* [N*W] mask row of the header   */
+  const uint64_t *edge_src;                /* [N*W] source-valid test of p   */
+  const uint64_t *node_gen;                /* [N*W] or NULL                  */
+  uint64_t *x_in, *x_out, *x_meet;         /* x_meet may be NULL             */
+} fwd_problem;
+
+static int forward_must(const graph *g, fwd_problem *P) {
+  int W = g->W;
+  wlist wl;
+  if (wl_init(&wl, g->N)) return ORACLE_E_NOMEM;
+  uint64_t *m = xcalloc((size_t)W, sizeof(uint64_t));
+  for (int b = 0; b < g->N; ++b)
+    for (int w = 0; w < W; ++w) {
+      P->x_in[(size_t)b * W + w] = g->top[w];
+      P->x_out[(size_t)b * W + w] = g->top[w];
+      if (P->x_meet) P->x_meet[(size_t)b * W + w] = g->top[w];
+    }
+  for (int b = 0; b < g->N; ++b) if (g->reach[b]) wl_push(&wl, b);
+  while (wl.count) {
+    int b = wl_pop(&wl);
+    if (b == g->entry) {
+      for (int w = 0; w < W; ++w) m[w] = P->init ? P->init[w] : g->top[w];
+    } else {
+      for (int w = 0; w < W; ++w) m[w] = g->top[w];
+      for (int k = g->po[b]; k < g->po[b + 1]; ++k) {
+        int p = g->ps[k];
+        if (!g->reach[p]) continue;
+        int e = g->pe[k];
+        for (int w = 0; w < W; ++w) {
+          uint64_t ev = P->x_out[(size_t)p * W + w];
+          if (P->is_entry_edge && P->is_entry_edge[e])
+            ev |= P->edge_mask[(size_t)b * W + w] & P->edge_src[(size_t)p * W + w];
+          m[w] &= ev;
+        }
+      }
+    }
+    int changed = 0;
+    for (int w = 0; w < W; ++w) {
+      size_t o = (size_t)b * W + w;
+      if (P->x_meet) P->x_meet[o] = m[w];
+      uint64_t in = m[w] | (P->node_gen ? P->node_gen[o] : 0);
+      P->x_in[o] = in;
+      uint64_t nv = P->gen[o] | (in & ~P->kill[o]);
+      if (nv != P->x_out[o]) { P->x_out[o] = nv; changed = 1; }
+    }
+    if (changed)
+      for (int e = g->so[b]; e < g->so[b + 1]; ++e) wl_push(&wl, g->s[e]);
+  }
+  free(m); wl_free(&wl);
+  return ORACLE_OK;
+}
+
+/* ---- dominators (Cooper, Harvey and Kennedy's iterative algorithm) ------- */
+static int dominators(const graph *g, int32_t *idom, int32_t *rpo_num) {
+  int N = g->N;
+  int32_t *order = xcalloc((size_t)N, sizeof(int32_t));
+  int32_t *stk = xcalloc((size_t)N, sizeof(int32_t));
+  int32_t *it = xcalloc((size_t)N, sizeof(int32_t));
+  uint8_t *seen = xcalloc((size_t)N, 1);
+  if (!order || !stk || !it || !seen) return ORACLE_E_NOMEM;
+  /* iterative depth-first search, post-order numbering */
+  int sp = 0, npost = 0;
+  stk[sp++] = g->entry; seen[g->entry] = 1; it[g->entry] = g->so[g->entry];
+  while (sp) {
+    int b = stk[sp - 1];
+    if (it[b] < g->so[b + 1]) {
+      int t = g->s[it[b]++];
+      if (!seen[t]) { seen[t] = 1; it[t] = g->so[t]; stk[sp++] = t; }
+    } else {
+      order[npost++] = b; --sp;
+    }
+  }
+  for (int b = 0; b < N; ++b) rpo_num[b] = -1;
+  for (int i = 0; i < npost; ++i) rpo_num[order[i]] = npost - 1 - i;
+  int32_t *rpo = stk;  /* reuse */
+  for (int i = 0; i < npost; ++i) rpo[npost - 1 - i] = order[i];
+  for (int b = 0; b < N; ++b) idom[b] = -1;
+  idom[g->entry] = g->entry;
+  int changed = 1;
+  while (changed) {
+    changed = 0;
+    for (int i = 1; i < npost; ++i) {
+      int b = rpo[i], nd = -1;
+      for (int k = g->po[b]; k < g->po[b + 1]; ++k) {
+        int p = g->ps[k];
+        if (!g->reach[p] || idom[p] < 0) continue;
+        if (nd < 0) { nd = p; continue; }
+        int f1 = p, f2 = nd;  /* intersect along the dominator tree */
+        while (f1 != f2) {
+          while (rpo_num[f1] > rpo_num[f2]) f1 = idom[f1];
+          while (rpo_num[f2] > rpo_num[f1]) f2 = idom[f2];
+        }
+        nd = f1;
+      }
+      if (nd >= 0 && idom[b] != nd) { idom[b] = nd; changed = 1; }
+    }
+  }
+  free(order); free(stk); free(it); free(seen);
+  return ORACLE_OK;
+}
+
+/* Dominator-tree interval numbering: a dom b  iff  pre[a] <= pre[b] and
+   post[b] <= post[a]. */
+static int dom_intervals(const graph *g, const int32_t *idom, int32_t *pre, int32_t *post) {
+  int N = g->N;
+  int32_t *co = xcalloc((size_t)N + 1, sizeof(int32_t));
+  int32_t *ch = xcalloc((size_t)N, sizeof(int32_t));
+  int32_t *fill = xcalloc((size_t)N, sizeof(int32_t));
+  int32_t *stk = xcalloc((size_t)N, sizeof(int32_t));
+  int32_t *it = xcalloc((size_t)N, sizeof(int32_t));
+  if (!co || !ch || !fill || !stk || !it) return ORACLE_E_NOMEM;
+  for (int b = 0; b < N; ++b)
+    if (g->reach[b] && b != g->entry) co[idom[b] + 1]++;
+  for (int b = 0; b < N; ++b) co[b + 1] += co[b];
+  for (int b = 0; b < N; ++b)
+    if (g->reach[b] && b != g->entry) ch[co[idom[b]] + fill[idom[b]]++] = b;
+  int sp = 0, clock = 0;
+  stk[sp++] = g->entry; it[g->entry] = co[g->entry]; pre[g->entry] = clock++;
+  while (sp) {
+    int b = stk[sp - 1];
+    if (it[b] < co[b + 1]) {
+      int c = ch[it[b]++];
+      pre[c] = clock++; it[c] = co[c]; stk[sp++] = c;
+    } else {
+      post[b] = clock++; --sp;
+    }
+  }
+  free(co); free(ch); free(fill); free(stk); free(it);
+  return ORACLE_OK;
+}
+
+/* ---- natural loops and loop masks -----------------------------------------
+ * Back edge t->h: both reachable and h dominates t.  body(h) = {h} plus
+ * every reachable block that reaches a latch of h without passing through
+ * h.  Entry edges of h: p->h with p outside body(h).
+ * For every header and space S:
+ *   LantS[h] = variables that some node of the loop reads in S before any
+ *              write, on a path from h that stays inside body(h) within one
+ *              iteration (least fixed point of the anticipation equations
+ *              restricted to body(h), edges back into h and edges leaving
+ *              the body dropped) -- "a node that is part of a loop needs
+ *              the data";
+ *   KOS[h]   = OR over body(h) of KillS -- the loop makes S stale somewhere;
+ *   MaskS[h] = LantS[h] & ~KOS[h] -- the need can be met before the loop. */
+static int natural_loops(const graph *g, const uint64_t *KH, const uint64_t *KD, const uint64_t *UH,
+                         const uint64_t *UD, const uint64_t *DF, uint8_t *is_header, uint8_t *is_entry_edge,
+                         uint64_t *MH, uint64_t *MD) {
+  int N = g->N, W = g->W, rc;
+  int32_t *idom = xcalloc((size_t)N, sizeof(int32_t));
+  int32_t *rpo_num = xcalloc((size_t)N, sizeof(int32_t));
+  int32_t *pre = xcalloc((size_t)N, sizeof(int32_t));
+  int32_t *post = xcalloc((size_t)N, sizeof(int32_t));
+  int32_t *stamp = xcalloc((size_t)N, sizeof(int32_t));
+  int32_t *stk = xcalloc((size_t)N, sizeof(int32_t));
+  int32_t *body = xcalloc((size_t)N, sizeof(int32_t));
+  uint64_t *LH = xcalloc((size_t)N * W, sizeof(uint64_t)), *LD = xcalloc((size_t)N * W, sizeof(uint64_t));
+  uint64_t *koh = xcalloc((size_t)W, sizeof(uint64_t)), *kod = xcalloc((size_t)W, sizeof(uint64_t));
+  uint64_t *oh = xcalloc((size_t)W, sizeof(uint64_t)), *od = xcalloc((size_t)W, sizeof(uint64_t));
+  wlist wl;
+  if (!idom || !rpo_num || !pre || !post || !stamp || !stk || !body || !LH || !LD || !koh || !kod || !oh ||
+      !od || wl_init(&wl, N))
+    return ORACLE_E_NOMEM;
+  if ((rc = dominators(g, idom, rpo_num))) return rc;
+  if ((rc = dom_intervals(g, idom, pre, post))) return rc;
+  for (int b = 0; b < N; ++b) stamp[b] = -1;
+  memset(is_header, 0, (size_t)N);
+  memset(is_entry_edge, 0, (size_t)g->E);
+  for (int h = 0; h < N; ++h) {
+    if (!g->reach[h]) continue;
+    int sp = 0, nb = 0;
+    for (int k = g->po[h]; k < g->po[h + 1]; ++k) {
+      int t = g->ps[k];
+      if (!g->reach[t]) continue;
+      int dom = pre[h] <= pre[t] && post[t] <= post[h];
+      if (!dom) continue;
+      is_header[h] = 1;
+      if (t != h && stamp[t] != h) { stamp[t] = h; stk[sp++] = t; }
+    }
+    if (!is_header[h]) continue;
+    stamp[h] = h;
+    body[nb++] = h;
+    /* collect the body by a backward walk from the latches */
+    while (sp) {
+      int b = stk[--sp];
+      body[nb++] = b;
+      for (int k = g->po[b]; k < g->po[b + 1]; ++k) {
+        int p = g->ps[k];
+        if (g->reach[p] && stamp[p] != h) { stamp[p] = h; stk[sp++] = p; }
+      }
+    }
+    for (int k = g->po[h]; k < g->po[h + 1]; ++k)
+      if (stamp[g->ps[k]] != h) is_entry_edge[g->pe[k]] = 1;
+    /* kills anywhere in the body */
+    memset(koh, 0, (size_t)W * sizeof(uint64_t));
+    memset(kod, 0, (size_t)W * sizeof(uint64_t));
+    for (int i = 0; i < nb; ++i)
+      for (int w = 0; w < W; ++w) {
+        koh[w] |= KH[(size_t)body[i] * W + w];
+        kod[w] |= KD[(size_t)body[i] * W + w];
+      }
+    /* anticipation restricted to the body, one iteration from h */
+    for (int i = 0; i < nb; ++i) {
+      memset(LH + (size_t)body[i] * W, 0, (size_t)W * sizeof(uint64_t));
+      memset(LD + (size_t)body[i] * W, 0, (size_t)W * sizeof(uint64_t));
+      wl_push(&wl, body[i]);
+    }
+    while (wl.count) {
+      int b = wl_pop(&wl);
+      memset(oh, 0, (size_t)W * sizeof(uint64_t));
+      memset(od, 0, (size_t)W * sizeof(uint64_t));
+      for (int e = g->so[b]; e < g->so[b + 1]; ++e) {
+        int s = g->s[e];
+        if (s == h || stamp[s] != h) continue;
+        for (int w = 0; w < W; ++w) {
+          oh[w] |= LH[(size_t)s * W + w];
+          od[w] |= LD[(size_t)s * W + w];
+        }
+      }
+      int changed = 0;
+      for (int w = 0; w < W; ++w) {
+        size_t o = (size_t)b * W + w;
+        uint64_t nh = UH[o] | (oh[w] & ~DF[o]), nd = UD[o] | (od[w] & ~DF[o]);
+        if (nh != LH[o] || nd != LD[o]) { LH[o] = nh; LD[o] = nd; changed = 1; }
+      }
+      if (changed && b != h)
+        for (int k = g->po[b]; k < g->po[b + 1]; ++k)
+          if (stamp[g->ps[k]] == h) wl_push(&wl, g->ps[k]);
+    }
+    for (int w = 0; w < W; ++w) {
+      size_t o = (size_t)h * W + w;
+      MH[o] = LH[o] & ~koh[w];
+      MD[o] = LD[o] & ~kod[w];
+    }
+  }
+  free(idom); free(rpo_num); free(pre); free(post); free(stamp); free(stk); free(body);
+  free(LH); free(LD); free(koh); free(kod); free(oh); free(od); wl_free(&wl);
+  return ORACLE_OK;
+}
+
+/* ---- step 7: access flags --------------------------------------------------
+ * Replay each reachable block from (H_in, D_in): an S-read that finds S
+ * stale gets a transfer right before it (`to' for a device read, `from'
+ * for a host read), after which S is valid; an S-write makes S valid and
+ * the other space stale.  This covers both the transfers at the top of the
+ * block (upward-exposed reads) and those after a write in the other space
+ * inside the block. */
+static void access_flags(const oracle_cfg *c, const graph *g, const uint64_t *h_in, const uint64_t *d_in,
+                         uint8_t *flag) {
+  int W = g->W;
+  uint64_t *h = xcalloc((size_t)W, sizeof(uint64_t)), *d = xcalloc((size_t)W, sizeof(uint64_t));
+  memset(flag, 0, (size_t)g->A);
+  for (int b = 0; b < g->N; ++b) {
+    if (!g->reach[b]) continue;
+    memcpy(h, h_in + (size_t)b * W, (size_t)W * sizeof(uint64_t));
+    memcpy(d, d_in + (size_t)b * W, (size_t)W * sizeof(uint64_t));
+    for (int i = g->ao[b]; i < g->ao[b + 1]; ++i) {
+      uint32_t a = g->acc[i];
+      if (a_is_call(a)) {
+        /* a call row needs per-variable transfers: reported through the
+           call-site planes, not this byte; replay its effect only */
+        int r = a_call_row(a);
+        for (int w = 0; w < W; ++w) {
+          uint64_t rqh = call_plane(c, W, r, 0)[w], rqd = call_plane(c, W, r, 1)[w];
+          h[w] |= rqh; d[w] |= rqd;
+          h[w] = call_plane(c, W, r, 2)[w] | (h[w] & ~call_plane(c, W, r, 3)[w]);
+          d[w] = call_plane(c, W, r, 4)[w] | (d[w] & ~call_plane(c, W, r, 5)[w]);
+        }
+        continue;
+      }
+      int v = a_var(a), k = a_kind(a), S = a_space(a);
+      uint64_t *own = S == SPACE_DEV ? d : h, *oth = S == SPACE_DEV ? h : d;
+      if (k & A_KIND_R) {
+        if (!get_bit(own, v)) { flag[i] = S == SPACE_DEV ? 1 : 2; set_bit(own, v, 1); }
+      }
+      if (k & A_KIND_W) { set_bit(own, v, 1); set_bit(oth, v, 0); }
+    }
+  }
+  free(h); free(d);
+}
+
+int oracle_solve(const oracle_cfg *c, oracle_out *out) {
+  int rc = validate(c);
+  if (rc) return rc;
+  graph g;
+  if ((rc = build_graph(c, &g))) { free_graph(&g); return rc; }
+  int N = g.N, W = g.W, E = g.E;
+  size_t NW = (size_t)N * W;
+  uint64_t *pl[26];
+  for (int i = 0; i < 26; ++i) {
+    pl[i] = xcalloc(NW, sizeof(uint64_t));
+    if (!pl[i]) { for (int j = 0; j < i; ++j) free(pl[j]); free_graph(&g); return ORACLE_E_NOMEM; }
+  }
+  uint64_t *GH = pl[0], *KH = pl[1], *GD = pl[2], *KD = pl[3], *UH = pl[4], *UD = pl[5], *DF = pl[6];
+  uint64_t *AH = pl[7], *AD = pl[8], *LV = pl[9], *HPI = pl[10], *HPO = pl[11];
+  uint64_t *MH = pl[14], *MD = pl[15];
+  uint64_t *DI = pl[16], *DO = pl[17], *HM = pl[18], *HI = pl[19], *HO = pl[20], *FX = pl[21];
+  uint8_t *hdr = xcalloc((size_t)N, 1), *ent = xcalloc((size_t)E, 1);
+  uint64_t *TE = xcalloc((size_t)E * W, sizeof(uint64_t)), *FE = xcalloc((size_t)E * W, sizeof(uint64_t));
+  uint8_t *fl = xcalloc((size_t)g.A, 1);
+  uint64_t *init_h = xcalloc((size_t)W, sizeof(uint64_t)), *init_d = xcalloc((size_t)W, sizeof(uint64_t));
+  uint64_t *xlive = xcalloc((size_t)W, sizeof(uint64_t));
+  if (!hdr || !ent || !TE || !FE || !fl || !init_h || !init_d || !xlive) { rc = ORACLE_E_NOMEM; goto done; }
+  for (int w = 0; w < W; ++w) {
+    init_h[w] = (c->entry_host_valid ? c->entry_host_valid[w] : ~(uint64_t)0) & g.top[w];
+    init_d[w] = (c->entry_dev_valid ? c->entry_dev_valid[w] : 0) & g.top[w];
+    xlive[w] = (c->exit_host_live ? c->exit_host_live[w] : ~(uint64_t)0) & g.top[w];
+  }
+
+  /* 1. local rule */
+  local_rule(c, &g, GH, KH, GD, KD, UH, UD, DF);
+  /* 2. anticipation and liveness */
+  if ((rc = anticipation(&g, UH, DF, xlive, AH))) goto done;
+  if ((rc = anticipation(&g, UD, DF, NULL, AD))) goto done;
+  for (size_t i = 0; i < NW; ++i) LV[i] = AH[i] | AD[i];
+  /* 3. plain host validity */
+  {
+    fwd_problem P = {GH, KH, init_h, NULL, NULL, NULL, NULL, HPI, HPO, NULL};
+    if ((rc = forward_must(&g, &P))) goto done;
+  }
+  /* 4. loops and masks */
+  if ((rc = natural_loops(&g, KH, KD, UH, UD, DF, hdr, ent, MH, MD))) goto done;
+  /* 5. device validity: hoisted `to' on loop-entry edges where the host
+        copy is valid (plain host validity as the source test) */
+  {
+    fwd_problem P = {GD, KD, init_d, ent, MD, HPO, NULL, DI, DO, NULL};
+    if ((rc = forward_must(&g, &P))) goto done;
+  }
+  /* 6. host validity: hoisted `from' on loop-entry edges where the device
+        copy is valid; live and valid in neither space -> host */
+  {
+    uint64_t *C = pl[22];
+    for (size_t i = 0; i < NW; ++i) C[i] = LV[i] & ~DI[i];
+    fwd_problem P = {GH, KH, init_h, ent, MH, DO, C, HI, HO, HM};
+    if ((rc = forward_must(&g, &P))) goto done;
+  }
+  /* 7. emission */
+  for (int b = 0; b < N; ++b) {
+    if (!g.reach[b]) continue;
+    for (int k = g.po[b]; k < g.po[b + 1]; ++k) {
+      int p = g.ps[k], e = g.pe[k];
+      if (!g.reach[p]) continue;
+      for (int w = 0; w < W; ++w) {
+        size_t ob = (size_t)b * W + w, op = (size_t)p * W + w, oe = (size_t)e * W + w;
+        uint64_t hedge = HO[op];
+        if (ent[e]) {
+          TE[oe] = MD[ob] & ~DO[op] & HPO[op];
+          FE[oe] = MH[ob] & ~HO[op] & DO[op];
+          hedge |= MH[ob] & DO[op];
+        }
+        FE[oe] |= (LV[ob] & ~DI[ob] & ~HM[ob]) & ~hedge;
+      }
+    }
+    if (g.so[b] == g.so[b + 1])
+      for (int w = 0; w < W; ++w) FX[(size_t)b * W + w] = xlive[w] & ~HO[(size_t)b * W + w];
+  }
+  access_flags(c, &g, HI, DI, fl);
+
+  /* copy out */
+#define CP(dst, src, n) do { if (dst) memcpy((dst), (src), (n) * sizeof(*(src))); } while (0)
+  CP(out->reachable, g.reach, (size_t)N);
+  CP(out->is_header, hdr, (size_t)N);
+  CP(out->is_loop_entry, ent, (size_t)E);
+  CP(out->gen_h, GH, NW); CP(out->kill_h, KH, NW); CP(out->gen_d, GD, NW); CP(out->kill_d, KD, NW);
+  CP(out->ue_h, UH, NW); CP(out->ue_d, UD, NW); CP(out->def, DF, NW);
+  CP(out->ant_h_in, AH, NW); CP(out->ant_d_in, AD, NW); CP(out->live_in, LV, NW);
+  CP(out->hp_in, HPI, NW); CP(out->hp_out, HPO, NW);
+  CP(out->mask_h, MH, NW); CP(out->mask_d, MD, NW);
+  CP(out->d_in, DI, NW); CP(out->d_out, DO, NW); CP(out->hm, HM, NW);
+  CP(out->h_in, HI, NW); CP(out->h_out, HO, NW);
+  CP(out->to_edge, TE, (size_t)E * W); CP(out->from_edge, FE, (size_t)E * W);
+  CP(out->from_exit, FX, NW);
+  CP(out->acc_flag, fl, (size_t)g.A);
+#undef CP
+  rc = ORACLE_OK;
+done:
+  for (int i = 0; i < 26; ++i) free(pl[i]);
+  free(hdr); free(ent); free(TE); free(FE); free(fl); free(init_h); free(init_d); free(xlive);
+  free_graph(&g);
+  return rc;
+}
