@@ -1,0 +1,163 @@
+/*
+ * ompdart.h -- C ABI of libompdart.so: host/device validity data-flow of
+ * OpenMP offload programs on one NVIDIA B300 (sm_103a).
+ *
+ * The analysis is the one of Marzen et al., "Static Generation of Efficient
+ * OpenMP Offload Data Mappings" (SC24):
+ *   - Sec. IV-D: data is valid in a memory space if it was last written
+ *     there; a write in one space makes the other stale; a read that may see
+ *     stale data is a true (read-after-write) dependency and needs one of
+ *     the Table II constructs; WAR/WAW need nothing.
+ *   - Sec. IV-D (loops) and Algorithm 1: a need inside a loop is met before
+ *     the loop when the data stays valid to the end of the loop body,
+ *     otherwise inside the loop.
+ *   - Sec. IV-D (last paragraph) and Sec. II-B: at the region exit, data the
+ *     host may read afterwards must be valid on the host (`from').
+ *   - Sec. IV-C: call sites carry the callee's side effects on globals and
+ *     pointer parameters (see ompdart_summarize_callee).
+ *
+ * INPUT FORMAT (the same for every entry point)
+ *   A CFG is n_blocks basic blocks, block `entry' has no predecessors.
+ *   succ_off[n_blocks+1], succ[n_edges]: CSR successor lists; the edge id
+ *       of succ[k] is k.  Duplicate edges are allowed (each is its own edge).
+ *   acc_off[n_blocks+1], acc[n_acc]: the ordered accesses of each block
+ *       (Sec. IV-B classification), packed as uint32:
+ *         bits  0-23  variable id (< n_vars)
+ *         bits 24-25  kind: 1 read, 2 write, 3 read-then-write (also used
+ *                     for "unknown", which the paper treats pessimistically)
+ *         bit  26     space: 0 host, 1 target (inside an offload kernel)
+ *         bits 27-30  zero
+ *         bit  31     call pseudo-access: bits 0-30 index the call table
+ *   Variable sets are bit planes of W = ceil(n_vars/64) uint64 words:
+ *   variable v is bit (v % 64) of word (v / 64); bits >= n_vars are zero.
+ *
+ * OUTPUT (ompdart_result)
+ *   h_in, d_in [n_blocks*W]: at the entry of each block, the variables
+ *       whose latest value is on the host / on the device (after the edge
+ *       transfers into the block).  Blocks unreachable from the entry are
+ *       all-ones.  h_out, d_out likewise at block exit (opts.keep_states).
+ *   acc_flag [n_acc]: 0 nothing, 1 `update to' (host->device) right before
+ *       this access, 2 `update from' (device->host) right before it.
+ *   edge_xfers [n_edge_xfers]: {edge, word, to_bits, from_bits} records for
+ *       transfers on CFG edges (hoisted before a loop, Sec. IV-D, or at a
+ *       join where the incoming paths disagree); order unspecified; only
+ *       words with a nonzero transfer appear.
+ *   exit_blocks [n_exits], from_exit [n_exits*W]: `from' at the end of each
+ *       reachable block without successors (region exit liveness).
+ *
+ * ERRORS
+ *   Every call returns OMPDART_OK (0) or a negative code; the text of the
+ *   last error of the calling thread is ompdart_last_error().  Invalid
+ *   inputs never reach the GPU.  Device loops are bounded (max_sweeps); a
+ *   bound that runs out makes the call return OMPDART_E_NOCONVERGE and
+ *   never traps.
+ *
+ * OWNERSHIP
+ *   Inputs are caller-owned and only read.  Plans and results are
+ *   library-owned and freed with ompdart_plan_destroy / ompdart_result_free.
+ */
+#ifndef OMPDART_H
+#define OMPDART_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OMPDART_OK 0
+#define OMPDART_E_INVALID (-1)    /* malformed CFG, ids out of range, entry with predecessors */
+#define OMPDART_E_NOMEM (-2)      /* host or device allocation failed                         */
+#define OMPDART_E_BUDGET (-3)     /* the request does not fit the device memory budget        */
+#define OMPDART_E_NOCONVERGE (-4) /* a device loop hit max_sweeps before its fixed point      */
+#define OMPDART_E_CUDA (-5)       /* a CUDA runtime call failed (no device, launch failure)   */
+#define OMPDART_E_TIMEOUT (-6)    /* a bounded device wait gave up                            */
+
+#define OMPDART_MEM_HOST 0
+#define OMPDART_MEM_DEVICE 1
+
+/* One CFG (see INPUT FORMAT).  All pointers are host pointers. */
+typedef struct {
+  int32_t n_blocks, n_vars, entry;
+  const int32_t *succ_off, *succ;
+  const int32_t *acc_off;
+  const uint32_t *acc;
+  const uint64_t *entry_host_valid; /* [W]; NULL = every variable valid on the host */
+  const uint64_t *entry_dev_valid;  /* [W]; NULL = nothing valid on the device      */
+  const uint64_t *exit_host_live;   /* [W]; NULL = every variable live after exit   */
+  /* call table for call pseudo-accesses: row r = 7 planes of W words, in
+     order ReqH, ReqD, GenH, KillH, GenD, KillD, MustDef (the layout
+     ompdart_summarize_callee writes after mapping to caller variables).
+     NULL when no access has bit 31 set. */
+  const uint64_t *call_planes;
+  int32_t n_calls;
+} ompdart_cfg;
+
+typedef struct {
+  int32_t max_sweeps;   /* bound on device fixed-point sweeps; 0 = 1<<20           */
+  int32_t keep_states;  /* nonzero: also produce h_out / d_out                     */
+  int32_t path;         /* 0 auto, 1 general sweep solver, 2 chunked scan solver   */
+  int32_t chunk_target; /* blocks per chunk for the scan solver; 0 = automatic     */
+  int32_t device;       /* CUDA device ordinal                                     */
+} ompdart_opts;
+
+typedef struct {
+  int32_t edge, word;
+  uint64_t to_bits, from_bits;
+} ompdart_edge_xfer;
+
+typedef struct {
+  int32_t n_blocks, n_vars, n_words, n_edges, n_acc, n_exits;
+  int32_t mem;                 /* OMPDART_MEM_HOST or OMPDART_MEM_DEVICE       */
+  uint64_t *h_in, *d_in;       /* [n_blocks*n_words]                           */
+  uint64_t *h_out, *d_out;     /* [n_blocks*n_words] or NULL                   */
+  uint8_t *acc_flag;           /* [n_acc]                                      */
+  int32_t n_edge_xfers;
+  ompdart_edge_xfer *edge_xfers;
+  int32_t *exit_blocks;        /* [n_exits]                                    */
+  uint64_t *from_exit;         /* [n_exits*n_words]                            */
+  int32_t path;                /* solver that ran: 1 sweep, 2 chunked scan      */
+  int32_t sweeps;              /* device sweeps executed (diagnostic)           */
+} ompdart_result;
+
+typedef struct ompdart_plan ompdart_plan;
+
+/* Ingest one CFG on the host (validation, predecessor lists, loop-ordered
+   reverse post-order, dominators, natural loops, chunking) and upload it.
+   Sec. IV-B (CFG, loops), Sec. IV-D (forward traversal). */
+int ompdart_plan_create(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdart_plan **plan);
+
+/* Enqueue the whole analysis of a plan on `stream' (cudaStream_t, NULL =
+   the plan's own stream).  Inputs and outputs stay on the device; returns
+   after enqueueing.  Sec. IV-D and Algorithm 1. */
+int ompdart_plan_run(ompdart_plan *plan, void *stream);
+
+/* Wait for the plan's last run and report its device status
+   (OMPDART_E_NOCONVERGE if a bounded loop ran out). */
+int ompdart_plan_sync(ompdart_plan *plan);
+
+/* Device-resident results of the last run (pointers owned by the plan,
+   valid until the next run or destroy; mem = OMPDART_MEM_DEVICE). */
+int ompdart_plan_view(ompdart_plan *plan, ompdart_result *view);
+
+/* Copy the results of the plan's last run to host memory; *out is
+   library-owned (ompdart_result_free), mem = OMPDART_MEM_HOST. */
+int ompdart_plan_fetch(ompdart_plan *plan, ompdart_result **out);
+
+/* Number of kernel launches one ompdart_plan_run enqueues. */
+int ompdart_plan_launches(const ompdart_plan *plan);
+
+void ompdart_plan_destroy(ompdart_plan *plan);
+
+/* One call: plan, run, copy every output to host memory.  *out is
+   library-owned (ompdart_result_free). */
+int ompdart_analyze(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdart_result **out);
+
+void ompdart_result_free(ompdart_result *res);
+
+/* Text of the calling thread's last error ("" if none). */
+const char *ompdart_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

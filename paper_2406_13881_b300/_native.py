@@ -1,0 +1,210 @@
+"""ctypes binding of libompdart.so (argument marshalling only).
+
+Every step of the analysis runs in the library's CUDA kernels; this module
+only converts numpy inputs to the C structs of ``include/ompdart.h`` and the
+results back to numpy.  There is no fallback: if the shared library is
+missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libompdart.so")
+_lock = threading.Lock()
+_lib = None
+
+OK = 0
+E_INVALID, E_NOMEM, E_BUDGET, E_NOCONVERGE, E_CUDA, E_TIMEOUT = -1, -2, -3, -4, -5, -6
+ERROR_NAMES = {-1: "E_INVALID", -2: "E_NOMEM", -3: "E_BUDGET", -4: "E_NOCONVERGE", -5: "E_CUDA",
+               -6: "E_TIMEOUT"}
+
+
+class OmpdartError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERROR_NAMES.get(code, "error"), code, msg))
+        self.code = code
+
+
+class Cfg(C.Structure):
+    _fields_ = [("n_blocks", C.c_int32), ("n_vars", C.c_int32), ("entry", C.c_int32),
+                ("succ_off", C.c_void_p), ("succ", C.c_void_p), ("acc_off", C.c_void_p),
+                ("acc", C.c_void_p), ("entry_host_valid", C.c_void_p),
+                ("entry_dev_valid", C.c_void_p), ("exit_host_live", C.c_void_p),
+                ("call_planes", C.c_void_p), ("n_calls", C.c_int32)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("max_sweeps", C.c_int32), ("keep_states", C.c_int32), ("path", C.c_int32),
+                ("chunk_target", C.c_int32), ("device", C.c_int32)]
+
+
+class EdgeXfer(C.Structure):
+    _fields_ = [("edge", C.c_int32), ("word", C.c_int32), ("to_bits", C.c_uint64),
+                ("from_bits", C.c_uint64)]
+
+
+XFER_DTYPE = np.dtype([("edge", np.int32), ("word", np.int32), ("to_bits", np.uint64),
+                       ("from_bits", np.uint64)])
+
+
+class Result(C.Structure):
+    _fields_ = [("n_blocks", C.c_int32), ("n_vars", C.c_int32), ("n_words", C.c_int32),
+                ("n_edges", C.c_int32), ("n_acc", C.c_int32), ("n_exits", C.c_int32),
+                ("mem", C.c_int32), ("h_in", C.c_void_p), ("d_in", C.c_void_p),
+                ("h_out", C.c_void_p), ("d_out", C.c_void_p), ("acc_flag", C.c_void_p),
+                ("n_edge_xfers", C.c_int32), ("edge_xfers", C.c_void_p),
+                ("exit_blocks", C.c_void_p), ("from_exit", C.c_void_p), ("path", C.c_int32),
+                ("sweeps", C.c_int32)]
+
+
+EXPORTS = {
+    "ompdart_plan_create": (C.c_int, [C.POINTER(Cfg), C.POINTER(Opts), C.POINTER(C.c_void_p)]),
+    "ompdart_plan_run": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ompdart_plan_sync": (C.c_int, [C.c_void_p]),
+    "ompdart_plan_view": (C.c_int, [C.c_void_p, C.POINTER(Result)]),
+    "ompdart_plan_fetch": (C.c_int, [C.c_void_p, C.POINTER(C.POINTER(Result))]),
+    "ompdart_plan_launches": (C.c_int, [C.c_void_p]),
+    "ompdart_plan_destroy": (None, [C.c_void_p]),
+    "ompdart_analyze": (C.c_int, [C.POINTER(Cfg), C.POINTER(Opts), C.POINTER(C.POINTER(Result))]),
+    "ompdart_result_free": (None, [C.POINTER(Result)]),
+    "ompdart_last_error": (C.c_char_p, []),
+}
+
+
+def load():
+    """Load libompdart.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise OSError("libompdart.so not built: run `python -m paper_2406_13881_b300.build`")
+            lib = C.CDLL(LIB_PATH)
+            for name, (res, args) in EXPORTS.items():
+                f = getattr(lib, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def _check(rc):
+    if rc != OK:
+        raise OmpdartError(rc, load().ompdart_last_error().decode())
+
+
+class _Inputs:
+    """Keeps the contiguous numpy copies alive while the C struct points at them."""
+
+    def __init__(self, cfg):
+        g = cfg if isinstance(cfg, dict) else cfg.__dict__
+        self.n, self.nv = int(g["n_blocks"]), int(g["n_vars"])
+        self.W = (self.nv + 63) // 64
+        self.so = np.ascontiguousarray(g["succ_off"], dtype=np.int32)
+        self.s = np.ascontiguousarray(g["succ"], dtype=np.int32)
+        self.ao = np.ascontiguousarray(g["acc_off"], dtype=np.int32)
+        self.acc = np.ascontiguousarray(g["acc"], dtype=np.uint32)
+
+        def opt(k):
+            v = g.get(k)
+            return None if v is None else np.ascontiguousarray(v, dtype=np.uint64)
+
+        self.ehv, self.edv, self.xhl = opt("entry_host_valid"), opt("entry_dev_valid"), opt("exit_host_live")
+        self.calls = opt("call_planes")
+        p = lambda a: None if a is None else a.ctypes.data  # noqa: E731
+        self.c = Cfg(self.n, self.nv, int(g.get("entry", 0)), p(self.so), p(self.s), p(self.ao),
+                     p(self.acc), p(self.ehv), p(self.edv), p(self.xhl), p(self.calls),
+                     0 if self.calls is None else int(self.calls.size // (7 * self.W)))
+
+
+def _opts(max_sweeps=0, keep_states=False, path=0, chunk_target=0, device=0):
+    return Opts(int(max_sweeps), int(bool(keep_states)), int(path), int(chunk_target), int(device))
+
+
+def _result_to_numpy(r: Result) -> dict:
+    n, W = r.n_blocks, r.n_words
+
+    def arr(ptr, count, dt, shape=None):
+        if not ptr or count == 0:
+            a = np.zeros(count, dtype=dt)
+        else:
+            a = np.ctypeslib.as_array((C.c_char * (count * np.dtype(dt).itemsize)).from_address(ptr))
+            a = np.frombuffer(a, dtype=dt).copy()
+        return a.reshape(shape) if shape else a
+
+    out = {
+        "h_in": arr(r.h_in, n * W, np.uint64, (n, W)),
+        "d_in": arr(r.d_in, n * W, np.uint64, (n, W)),
+        "acc_flag": arr(r.acc_flag, r.n_acc, np.uint8),
+        "edge_xfers": arr(r.edge_xfers, r.n_edge_xfers, XFER_DTYPE),
+        "exit_blocks": arr(r.exit_blocks, r.n_exits, np.int32),
+        "from_exit": arr(r.from_exit, r.n_exits * W, np.uint64, (r.n_exits, W)),
+        "path": r.path, "sweeps": r.sweeps,
+    }
+    if r.h_out:
+        out["h_out"] = arr(r.h_out, n * W, np.uint64, (n, W))
+        out["d_out"] = arr(r.d_out, n * W, np.uint64, (n, W))
+    return out
+
+
+def analyze(cfg, **opts) -> dict:
+    """One-shot analysis through ``ompdart_analyze`` (host buffers in and out)."""
+    lib = load()
+    inp = _Inputs(cfg)
+    o = _opts(**opts)
+    res = C.POINTER(Result)()
+    _check(lib.ompdart_analyze(C.byref(inp.c), C.byref(o), C.byref(res)))
+    try:
+        return _result_to_numpy(res.contents)
+    finally:
+        lib.ompdart_result_free(res)
+
+
+class Plan:
+    """A resident analysis: ingest once (``ompdart_plan_create``), then run
+    the device solver as often as wanted (``run`` enqueues, ``sync`` waits)."""
+
+    def __init__(self, cfg, **opts):
+        self._lib = load()
+        self._inp = _Inputs(cfg)
+        self._h = C.c_void_p()
+        _check(self._lib.ompdart_plan_create(C.byref(self._inp.c), C.byref(_opts(**opts)),
+                                             C.byref(self._h)))
+
+    def run(self, stream: int | None = None):
+        _check(self._lib.ompdart_plan_run(self._h, C.c_void_p(stream or 0)))
+
+    def sync(self):
+        _check(self._lib.ompdart_plan_sync(self._h))
+
+    def view(self) -> Result:
+        r = Result()
+        _check(self._lib.ompdart_plan_view(self._h, C.byref(r)))
+        return r
+
+    def fetch(self) -> dict:
+        res = C.POINTER(Result)()
+        _check(self._lib.ompdart_plan_fetch(self._h, C.byref(res)))
+        try:
+            return _result_to_numpy(res.contents)
+        finally:
+            self._lib.ompdart_result_free(res)
+
+    @property
+    def launches(self) -> int:
+        return int(self._lib.ompdart_plan_launches(self._h))
+
+    def close(self):
+        if self._h:
+            self._lib.ompdart_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,355 @@
+// api.cu -- the C ABI of libompdart.so (see include/ompdart.h).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/ompdart.h"
+#include "ingest.h"
+#include "plan.cuh"
+
+namespace ompdart {
+int enqueue_local_summary(const DevPlan &p, cudaStream_t s);
+int enqueue_sweep_solver(const DevPlan &p, cudaStream_t s, int n_fin);
+int enqueue_sweep_edges(const DevPlan &p, cudaStream_t s, int n_fin);
+int scan_supported(const Ingest &g);
+struct ScanState;
+ScanState *scan_create(const Ingest &g, DevPlan &p, cudaStream_t s, std::string *err);
+int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s);
+int enqueue_scan_edges(ScanState *st, const DevPlan &p, cudaStream_t s);
+void scan_destroy(ScanState *st);
+}  // namespace ompdart
+
+using namespace ompdart;
+
+namespace {
+thread_local std::string g_err;
+
+int set_err(int code, const std::string &msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_err(cudaError_t e, const char *what) {
+  return set_err(OMPDART_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+}  // namespace
+
+struct ompdart_plan {
+  Ingest g;
+  DevPlan dp{};
+  std::vector<void *> allocs;
+  cudaStream_t stream = nullptr;
+  cudaStream_t last_stream = nullptr;
+  int device = 0;
+  int path = 1;
+  int launches = 0;
+  int n_fin = 0;
+  int keep_states = 0;
+  ScanState *scan = nullptr;
+  int32_t *h_status = nullptr;  // pinned
+
+  template <class T>
+  T *dalloc(size_t n) {
+    void *ptr = nullptr;
+    if (cudaMalloc(&ptr, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) return nullptr;
+    allocs.push_back(ptr);
+    return static_cast<T *>(ptr);
+  }
+  template <class T>
+  T *upload(const T *src, size_t n) {
+    T *d = dalloc<T>(n);
+    if (d && n && cudaMemcpy(d, src, n * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
+    return d;
+  }
+  template <class T>
+  T *upload(const std::vector<T> &v) {
+    return upload(v.data(), v.size());
+  }
+  ~ompdart_plan() {
+    if (scan) scan_destroy(scan);
+    for (void *p : allocs) cudaFree(p);
+    if (stream) cudaStreamDestroy(stream);
+    if (h_status) cudaFreeHost(h_status);
+  }
+};
+
+namespace {
+
+int grow_xfers(ompdart_plan *P, int need) {
+  EdgeXfer *x = P->dalloc<EdgeXfer>((size_t)need);
+  if (!x) return set_err(OMPDART_E_NOMEM, "device allocation of transfer records failed");
+  P->dp.xfer = x;
+  P->dp.xfer_cap = need;
+  return OMPDART_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *ompdart_last_error(void) { return g_err.c_str(); }
+
+int ompdart_plan_create(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdart_plan **out) {
+  g_err.clear();
+  if (!out) return set_err(OMPDART_E_INVALID, "plan output pointer is NULL");
+  *out = nullptr;
+  ompdart_opts o{};
+  if (opts) o = *opts;
+  ompdart_plan *P = new (std::nothrow) ompdart_plan();
+  if (!P) return set_err(OMPDART_E_NOMEM, "host allocation failed");
+  std::string err;
+  int rc = ingest(cfg, &P->g, &err);
+  if (rc) {
+    delete P;
+    return set_err(rc, err);
+  }
+  for (int i = 0; i < P->g.A; ++i)
+    if (cfg->acc[i] >> 31) {
+      delete P;
+      return set_err(OMPDART_E_INVALID, "call pseudo-accesses are not accepted by this entry point");
+    }
+  const Ingest &g = P->g;
+  P->device = o.device;
+  P->keep_states = o.keep_states;
+  cudaError_t ce = cudaSetDevice(o.device);
+  if (ce != cudaSuccess) {
+    delete P;
+    return cuda_err(ce, "cudaSetDevice");
+  }
+  if ((ce = cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+    delete P;
+    return cuda_err(ce, "cudaStreamCreate");
+  }
+  if ((ce = cudaMallocHost(&P->h_status, ST_COUNT * sizeof(int32_t))) != cudaSuccess) {
+    delete P;
+    return cuda_err(ce, "cudaMallocHost");
+  }
+  const int W = g.W;
+  std::vector<uint64_t> top(W, ~0ull), eh(W), ed(W), xl(W);
+  if (g.V % 64) top[W - 1] = (1ull << (g.V % 64)) - 1;
+  for (int w = 0; w < W; ++w) {
+    eh[w] = (cfg->entry_host_valid ? cfg->entry_host_valid[w] : ~0ull) & top[w];
+    ed[w] = (cfg->entry_dev_valid ? cfg->entry_dev_valid[w] : 0ull) & top[w];
+    xl[w] = (cfg->exit_host_live ? cfg->exit_host_live[w] : ~0ull) & top[w];
+  }
+  std::vector<int32_t> fin_dst(g.fin_src.size());
+  for (int i = 0; i < g.M; ++i)
+    for (int k = g.fin_off[i]; k < g.fin_off[i + 1]; ++k) fin_dst[k] = g.order[i];
+  P->n_fin = (int)g.fin_src.size();
+
+  DevPlan &d = P->dp;
+  d.N = g.N; d.M = g.M; d.E = g.E; d.A = g.A; d.W = W; d.V = g.V; d.L = g.L; d.K = g.K;
+  d.X = (int)g.exit_blocks.size();
+  d.entry = g.entry;
+  d.max_sweeps = o.max_sweeps > 0 ? o.max_sweeps : (1 << 20);
+  const size_t NW = (size_t)g.N * W;
+  bool ok = true;
+  auto chk = [&](const void *p) { ok = ok && p != nullptr; };
+  chk(d.order = P->upload(g.order));
+  chk(d.pos = P->upload(g.pos));
+  chk(d.fin_off = P->upload(g.fin_off));
+  chk(d.fin_src = P->upload(g.fin_src));
+  chk(d.fin_eid = P->upload(g.fin_eid));
+  chk(d.fin_ent = P->upload(g.fin_ent));
+  chk(d.fin_dst = P->upload(fin_dst));
+  chk(d.out_off = P->upload(g.out_off));
+  chk(d.out_dst = P->upload(g.out_dst));
+  chk(d.is_exit = P->upload(g.is_exit));
+  chk(d.exit_blocks = P->upload(g.exit_blocks));
+  chk(d.acc_off = P->upload(cfg->acc_off, (size_t)g.N + 1));
+  chk(d.acc = P->upload(cfg->acc, (size_t)g.A));
+  chk(d.rec = P->dalloc<uint32_t>(g.A));
+  chk(d.loop_head = P->upload(g.loop_head));
+  chk(d.body_off = P->upload(g.body_off));
+  chk(d.body_blk = P->upload(g.body_blk));
+  chk(d.ent_loop = P->upload(g.ent_loop));
+  chk(d.ent_src = P->upload(g.ent_src));
+  chk(d.entry_h = P->upload(eh));
+  chk(d.entry_d = P->upload(ed));
+  chk(d.exit_live = P->upload(xl));
+  chk(d.top = P->upload(top));
+  chk(d.h_in = P->dalloc<uint64_t>(NW));
+  chk(d.d_in = P->dalloc<uint64_t>(NW));
+  chk(d.h_out = P->dalloc<uint64_t>(NW));
+  chk(d.d_out = P->dalloc<uint64_t>(NW));
+  chk(d.live = P->dalloc<uint64_t>(NW));
+  chk(d.mask_h = P->dalloc<uint64_t>((size_t)g.L * W));
+  chk(d.mask_d = P->dalloc<uint64_t>((size_t)g.L * W));
+  chk(d.ec_h = P->dalloc<uint64_t>((size_t)g.K * W));
+  chk(d.ec_d = P->dalloc<uint64_t>((size_t)g.K * W));
+  chk(d.acc_flag = P->dalloc<uint8_t>(g.A));
+  chk(d.from_exit = P->dalloc<uint64_t>((size_t)d.X * W));
+  chk(d.status = P->dalloc<int32_t>(ST_COUNT));
+  if (!ok) {
+    delete P;
+    return set_err(OMPDART_E_NOMEM, "device allocation failed");
+  }
+  int want = o.path;
+  if (want == 0) want = scan_supported(g) ? 2 : 1;
+  if (want == 2 && !scan_supported(g)) {
+    delete P;
+    return set_err(OMPDART_E_INVALID, "the chunked scan solver needs a reducible CFG whose loop bodies are "
+                                      "contiguous in loop order");
+  }
+  P->path = want;
+  if (want == 1) {
+    chk(d.hp_out = P->dalloc<uint64_t>(NW));
+    chk(d.ant_h = P->dalloc<uint64_t>(NW));
+    chk(d.ant_d = P->dalloc<uint64_t>(NW));
+    chk(d.lant = P->dalloc<uint64_t>(g.body_blk.size() * (size_t)W * 2));
+  } else {
+    P->scan = scan_create(g, d, P->stream, &err);
+    if (!P->scan) {
+      delete P;
+      return set_err(OMPDART_E_NOMEM, err);
+    }
+  }
+  // transfer records: start with room for a few per loop-entry edge and
+  // join; grown after a run that overflowed
+  const size_t cap0 = std::min<size_t>((size_t)P->n_fin * W + 1, std::max<size_t>(4096, ((size_t)g.K + g.M / 8) * 2));
+  chk(d.xfer = P->dalloc<EdgeXfer>(cap0));
+  d.xfer_cap = (int)cap0;
+  if (!ok) {
+    delete P;
+    return set_err(OMPDART_E_NOMEM, "device allocation failed");
+  }
+  *out = P;
+  return OMPDART_OK;
+}
+
+int ompdart_plan_run(ompdart_plan *P, void *stream) {
+  g_err.clear();
+  if (!P) return set_err(OMPDART_E_INVALID, "plan is NULL");
+  cudaStream_t s = stream ? (cudaStream_t)stream : P->stream;
+  P->last_stream = s;
+  cudaMemsetAsync(P->dp.status, 0, ST_COUNT * sizeof(int32_t), s);
+  int n = enqueue_local_summary(P->dp, s);
+  if (P->path == 1)
+    n += enqueue_sweep_solver(P->dp, s, P->n_fin);
+  else
+    n += enqueue_scan_solver(P->scan, P->dp, s);
+  P->launches = n;
+  cudaError_t ce = cudaGetLastError();
+  if (ce != cudaSuccess) return cuda_err(ce, "kernel launch");
+  return OMPDART_OK;
+}
+
+int ompdart_plan_sync(ompdart_plan *P) {
+  if (!P) return set_err(OMPDART_E_INVALID, "plan is NULL");
+  cudaStream_t s = P->last_stream ? P->last_stream : P->stream;
+  cudaError_t ce = cudaMemcpyAsync(P->h_status, P->dp.status, ST_COUNT * sizeof(int32_t),
+                                   cudaMemcpyDeviceToHost, s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) return cuda_err(ce, "device run");
+  if (P->h_status[ST_ERROR] == ERR_NOCONVERGE)
+    return set_err(OMPDART_E_NOCONVERGE, "a device fixed-point loop reached max_sweeps");
+  const int nrec = P->h_status[ST_NREC];
+  if (nrec > P->dp.xfer_cap) {
+    // the record buffer overflowed: enlarge it and redo the edge emission
+    int rc = grow_xfers(P, nrec + nrec / 4 + 16);
+    if (rc) return rc;
+    cudaMemsetAsync(P->dp.status + ST_NREC, 0, sizeof(int32_t), s);
+    if (P->path == 1)
+      enqueue_sweep_edges(P->dp, s, P->n_fin);
+    else
+      enqueue_scan_edges(P->scan, P->dp, s);
+    ce = cudaMemcpyAsync(P->h_status, P->dp.status, ST_COUNT * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return cuda_err(ce, "device run");
+  }
+  return OMPDART_OK;
+}
+
+int ompdart_plan_view(ompdart_plan *P, ompdart_result *v) {
+  if (!P || !v) return set_err(OMPDART_E_INVALID, "NULL argument");
+  const Ingest &g = P->g;
+  memset(v, 0, sizeof *v);
+  v->n_blocks = g.N; v->n_vars = g.V; v->n_words = g.W; v->n_edges = g.E; v->n_acc = g.A;
+  v->n_exits = P->dp.X;
+  v->mem = OMPDART_MEM_DEVICE;
+  v->h_in = P->dp.h_in; v->d_in = P->dp.d_in;
+  v->h_out = P->keep_states ? P->dp.h_out : nullptr;
+  v->d_out = P->keep_states ? P->dp.d_out : nullptr;
+  v->acc_flag = P->dp.acc_flag;
+  v->n_edge_xfers = std::min(P->h_status[ST_NREC], P->dp.xfer_cap);
+  v->edge_xfers = reinterpret_cast<ompdart_edge_xfer *>(P->dp.xfer);
+  v->exit_blocks = const_cast<int32_t *>(P->dp.exit_blocks);
+  v->from_exit = P->dp.from_exit;
+  v->path = P->path;
+  v->sweeps = P->h_status[ST_SWEEPS];
+  return OMPDART_OK;
+}
+
+int ompdart_plan_launches(const ompdart_plan *P) { return P ? P->launches : 0; }
+
+void ompdart_plan_destroy(ompdart_plan *P) { delete P; }
+
+void ompdart_result_free(ompdart_result *r) {
+  if (!r) return;
+  free(r->h_in); free(r->d_in); free(r->h_out); free(r->d_out); free(r->acc_flag);
+  free(r->edge_xfers); free(r->exit_blocks); free(r->from_exit);
+  free(r);
+}
+
+int ompdart_plan_fetch(ompdart_plan *P, ompdart_result **out) {
+  if (!P || !out) return set_err(OMPDART_E_INVALID, "NULL argument");
+  *out = nullptr;
+  ompdart_result v;
+  ompdart_plan_view(P, &v);
+  ompdart_result *r = (ompdart_result *)calloc(1, sizeof(ompdart_result));
+  if (!r) return set_err(OMPDART_E_NOMEM, "host allocation failed");
+  *r = v;
+  r->mem = OMPDART_MEM_HOST;
+  const size_t NW = (size_t)v.n_blocks * v.n_words;
+  r->h_in = (uint64_t *)malloc(NW * 8 + 8);
+  r->d_in = (uint64_t *)malloc(NW * 8 + 8);
+  r->h_out = v.h_out ? (uint64_t *)malloc(NW * 8 + 8) : nullptr;
+  r->d_out = v.d_out ? (uint64_t *)malloc(NW * 8 + 8) : nullptr;
+  r->acc_flag = (uint8_t *)malloc((size_t)v.n_acc + 1);
+  r->edge_xfers = (ompdart_edge_xfer *)malloc(sizeof(ompdart_edge_xfer) * ((size_t)v.n_edge_xfers + 1));
+  r->exit_blocks = (int32_t *)malloc(sizeof(int32_t) * ((size_t)v.n_exits + 1));
+  r->from_exit = (uint64_t *)malloc(8 * ((size_t)v.n_exits * v.n_words + 1));
+  bool ok = r->h_in && r->d_in && (!v.h_out || r->h_out) && (!v.d_out || r->d_out) && r->acc_flag &&
+            r->edge_xfers && r->exit_blocks && r->from_exit;
+  cudaStream_t s = P->last_stream ? P->last_stream : P->stream;
+  cudaError_t ce = cudaSuccess;
+  auto cp = [&](void *dst, const void *src, size_t n) {
+    if (ok && ce == cudaSuccess && n) ce = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, s);
+  };
+  cp(r->h_in, v.h_in, NW * 8);
+  cp(r->d_in, v.d_in, NW * 8);
+  if (v.h_out) cp(r->h_out, v.h_out, NW * 8);
+  if (v.d_out) cp(r->d_out, v.d_out, NW * 8);
+  cp(r->acc_flag, v.acc_flag, (size_t)v.n_acc);
+  cp(r->edge_xfers, v.edge_xfers, sizeof(ompdart_edge_xfer) * (size_t)v.n_edge_xfers);
+  cp(r->exit_blocks, v.exit_blocks, sizeof(int32_t) * (size_t)v.n_exits);
+  cp(r->from_exit, v.from_exit, 8 * (size_t)v.n_exits * v.n_words);
+  if (ok && ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (!ok || ce != cudaSuccess) {
+    ompdart_result_free(r);
+    return ok ? cuda_err(ce, "copy of results") : set_err(OMPDART_E_NOMEM, "host allocation failed");
+  }
+  *out = r;
+  return OMPDART_OK;
+}
+
+int ompdart_analyze(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdart_result **out) {
+  if (!out) return set_err(OMPDART_E_INVALID, "result output pointer is NULL");
+  *out = nullptr;
+  ompdart_plan *P = nullptr;
+  int rc = ompdart_plan_create(cfg, opts, &P);
+  if (rc) return rc;
+  rc = ompdart_plan_run(P, nullptr);
+  if (!rc) rc = ompdart_plan_sync(P);
+  if (!rc) rc = ompdart_plan_fetch(P, out);
+  ompdart_plan_destroy(P);
+  return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,452 @@
+// ingest.cpp -- host-side ingestion of one CFG (see ingest.h).
+#include "ingest.h"
+
+#include <algorithm>
+#include <cstring>
+
+namespace ompdart {
+
+namespace {
+
+constexpr int kNone = -1;
+
+bool fail(std::string *err, const char *msg) {
+  if (err) *err = msg;
+  return false;
+}
+
+bool check_format(const ompdart_cfg *c, std::string *err) {
+  if (!c) return fail(err, "cfg is NULL");
+  if (c->n_blocks < 1) return fail(err, "n_blocks must be >= 1");
+  if (c->n_vars < 1 || c->n_vars > (1 << 24)) return fail(err, "n_vars must be in [1, 2^24]");
+  if (c->entry < 0 || c->entry >= c->n_blocks) return fail(err, "entry out of range");
+  if (!c->succ_off || !c->acc_off) return fail(err, "succ_off / acc_off missing");
+  if (c->succ_off[0] != 0 || c->acc_off[0] != 0) return fail(err, "CSR offsets must start at 0");
+  for (int b = 0; b < c->n_blocks; ++b)
+    if (c->succ_off[b + 1] < c->succ_off[b] || c->acc_off[b + 1] < c->acc_off[b])
+      return fail(err, "CSR offsets must be non-decreasing");
+  const int E = c->succ_off[c->n_blocks], A = c->acc_off[c->n_blocks];
+  if ((E && !c->succ) || (A && !c->acc)) return fail(err, "succ / acc missing");
+  for (int e = 0; e < E; ++e) {
+    if (c->succ[e] < 0 || c->succ[e] >= c->n_blocks) return fail(err, "successor id out of range");
+    if (c->succ[e] == c->entry) return fail(err, "the entry block must have no predecessors");
+  }
+  for (int i = 0; i < A; ++i) {
+    const uint32_t a = c->acc[i];
+    if (a >> 31) {
+      if (!c->call_planes || (int)(a & 0x7FFFFFFFu) >= c->n_calls)
+        return fail(err, "call access without a matching call-table row");
+      continue;
+    }
+    if ((a >> 27) & 0xFu) return fail(err, "reserved access bits 27-30 must be zero");
+    if ((int)(a & 0xFFFFFFu) >= c->n_vars) return fail(err, "access variable out of range");
+    if (((a >> 24) & 3u) == 0) return fail(err, "access kind must be 1, 2 or 3");
+  }
+  return true;
+}
+
+// Lengauer-Tarjan immediate dominators over blocks reachable from `entry`.
+// preorder[] lists reachable blocks in DFS preorder; idom[entry] = entry.
+void lengauer_tarjan(int N, int entry, const std::vector<int32_t> &so, const int32_t *succ,
+                     const std::vector<int32_t> &po, const std::vector<int32_t> &psrc,
+                     std::vector<int32_t> *preorder_out, std::vector<int32_t> *idom_out) {
+  std::vector<int32_t> dfn(N, kNone), vert, parent(N, kNone);
+  vert.reserve(N);
+  {  // iterative DFS, preorder numbering
+    std::vector<std::pair<int32_t, int32_t>> st;
+    st.push_back({entry, so[entry]});
+    dfn[entry] = 0;
+    vert.push_back(entry);
+    while (!st.empty()) {
+      auto &top = st.back();
+      if (top.second < so[top.first + 1]) {
+        int t = succ[top.second++];
+        if (dfn[t] == kNone) {
+          dfn[t] = (int32_t)vert.size();
+          vert.push_back(t);
+          parent[t] = top.first;
+          st.push_back({t, so[t]});
+        }
+      } else {
+        st.pop_back();
+      }
+    }
+  }
+  const int n = (int)vert.size();
+  // work on dfs numbers 0..n-1
+  std::vector<int32_t> semi(n), label(n), anc(n, kNone), idom(n, kNone), par(n, kNone);
+  std::vector<int32_t> bucket_head(n, kNone), bucket_next(n, kNone);
+  for (int i = 0; i < n; ++i) {
+    semi[i] = i;
+    label[i] = i;
+    if (i) par[i] = dfn[parent[vert[i]]];
+  }
+  std::vector<int32_t> path;
+  auto eval = [&](int v) -> int {
+    if (anc[v] == kNone) return v;
+    // iterative path compression
+    path.clear();
+    int x = v;
+    while (anc[anc[x]] != kNone) {
+      path.push_back(x);
+      x = anc[x];
+    }
+    for (int k = (int)path.size() - 1; k >= 0; --k) {
+      int y = path[k];
+      if (semi[label[anc[y]]] < semi[label[y]]) label[y] = label[anc[y]];
+      anc[y] = anc[anc[y]];
+    }
+    return label[v];
+  };
+  for (int w = n - 1; w >= 1; --w) {
+    const int bw = vert[w];
+    for (int k = po[bw]; k < po[bw + 1]; ++k) {
+      int v = dfn[psrc[k]];
+      if (v == kNone) continue;  // unreachable predecessor
+      int u = eval(v);
+      if (semi[u] < semi[w]) semi[w] = semi[u];
+    }
+    // add w to bucket of its semidominator
+    bucket_next[w] = bucket_head[semi[w]];
+    bucket_head[semi[w]] = w;
+    anc[w] = par[w];  // link
+    for (int v = bucket_head[par[w]]; v != kNone; v = bucket_next[v]) {
+      int u = eval(v);
+      idom[v] = semi[u] < semi[v] ? u : par[w];
+    }
+    bucket_head[par[w]] = kNone;
+  }
+  for (int w = 1; w < n; ++w)
+    if (idom[w] != semi[w]) idom[w] = idom[idom[w]];
+  idom_out->assign(N, kNone);
+  (*idom_out)[entry] = entry;
+  for (int w = 1; w < n; ++w) (*idom_out)[vert[w]] = vert[idom[w]];
+  *preorder_out = std::move(vert);
+}
+
+}  // namespace
+
+int ingest(const ompdart_cfg *c, Ingest *g, std::string *err) {
+  if (!check_format(c, err)) return OMPDART_E_INVALID;
+  const int N = c->n_blocks;
+  g->N = N;
+  g->E = c->succ_off[N];
+  g->A = c->acc_off[N];
+  g->V = c->n_vars;
+  g->W = (c->n_vars + 63) / 64;
+  g->entry = c->entry;
+  std::vector<int32_t> so(c->succ_off, c->succ_off + N + 1);
+  const int32_t *succ = c->succ;
+
+  // predecessor CSR with edge ids
+  std::vector<int32_t> po(N + 1, 0), psrc(g->E), peid(g->E);
+  for (int e = 0; e < g->E; ++e) po[succ[e] + 1]++;
+  for (int b = 0; b < N; ++b) po[b + 1] += po[b];
+  {
+    std::vector<int32_t> fill(po.begin(), po.end() - 1);
+    for (int b = 0; b < N; ++b)
+      for (int e = so[b]; e < so[b + 1]; ++e) {
+        int k = fill[succ[e]]++;
+        psrc[k] = b;
+        peid[k] = e;
+      }
+  }
+
+  // dominators on the reachable subgraph
+  std::vector<int32_t> pre, idom;
+  lengauer_tarjan(N, c->entry, so, succ, po, psrc, &pre, &idom);
+  std::vector<uint8_t> reach(N, 0);
+  for (int b : pre) reach[b] = 1;
+
+  // dominator tree intervals: a dom b  <=>  tin[a] <= tin[b] && tout[b] <= tout[a]
+  std::vector<int32_t> tin(N, kNone), tout(N, kNone);
+  {
+    std::vector<int32_t> coff(N + 1, 0), kids(pre.size());
+    for (int b : pre)
+      if (b != c->entry) coff[idom[b] + 1]++;
+    for (int b = 0; b < N; ++b) coff[b + 1] += coff[b];
+    std::vector<int32_t> f(coff.begin(), coff.end() - 1);
+    for (int b : pre)
+      if (b != c->entry) kids[f[idom[b]]++] = b;
+    int clock = 0;
+    std::vector<std::pair<int32_t, int32_t>> st;
+    st.push_back({c->entry, coff[c->entry]});
+    tin[c->entry] = clock++;
+    while (!st.empty()) {
+      auto &t = st.back();
+      if (t.second < coff[t.first + 1]) {
+        int k = kids[t.second++];
+        tin[k] = clock++;
+        st.push_back({k, coff[k]});
+      } else {
+        tout[t.first] = clock++;
+        st.pop_back();
+      }
+    }
+  }
+  auto dominates = [&](int a, int b) { return tin[a] <= tin[b] && tout[b] <= tout[a]; };
+
+  // natural loops; headers in decreasing DFS preorder = inner loops first
+  std::vector<int32_t> dfn(N, kNone);
+  for (int i = 0; i < (int)pre.size(); ++i) dfn[pre[i]] = i;
+  std::vector<int32_t> headers;
+  for (int i = (int)pre.size() - 1; i >= 0; --i) {
+    int h = pre[i];
+    bool is_h = false;
+    for (int k = po[h]; k < po[h + 1] && !is_h; ++k)
+      if (reach[psrc[k]] && dominates(h, psrc[k])) is_h = true;
+    if (is_h) headers.push_back(h);
+  }
+  const int L = (int)headers.size();
+  std::vector<int32_t> lid_of_head(N, kNone);
+  for (int l = 0; l < L; ++l) lid_of_head[headers[l]] = l;
+  std::vector<std::vector<int32_t>> bodies(L);
+  std::vector<int32_t> inner(N, kNone), lparent(L, kNone), mark(N, kNone), stk;
+  for (int l = 0; l < L; ++l) {
+    int h = headers[l];
+    auto &bd = bodies[l];
+    bd.push_back(h);
+    mark[h] = l;
+    stk.clear();
+    for (int k = po[h]; k < po[h + 1]; ++k) {
+      int t = psrc[k];
+      if (reach[t] && dominates(h, t) && mark[t] != l) {
+        mark[t] = l;
+        stk.push_back(t);
+      }
+    }
+    while (!stk.empty()) {
+      int b = stk.back();
+      stk.pop_back();
+      bd.push_back(b);
+      for (int k = po[b]; k < po[b + 1]; ++k) {
+        int p = psrc[k];
+        if (reach[p] && mark[p] != l) {
+          mark[p] = l;
+          stk.push_back(p);
+        }
+      }
+    }
+    for (int b : bd) {
+      if (inner[b] == kNone) {
+        inner[b] = l;
+      } else if (b != h || inner[b] != l) {
+        // b belongs to an already-built (inner) loop: link that loop chain
+        int x = inner[b];
+        while (lparent[x] != kNone && lparent[x] != l) x = lparent[x];
+        if (x != l && lparent[x] == kNone) lparent[x] = l;
+      }
+    }
+  }
+  std::vector<int32_t> ldepth(L, 0);
+  for (int l = L - 1; l >= 0; --l) {  // outer loops have larger ids here
+    ldepth[l] = lparent[l] == kNone ? 1 : 0;
+  }
+  // depth by walking parents (parents have larger ids: processed later)
+  for (int l = 0; l < L; ++l) {
+    int d = 1;
+    for (int x = lparent[l]; x != kNone; x = lparent[x]) ++d;
+    ldepth[l] = d;
+  }
+  auto common_depth = [&](int a, int b) -> int {  // depth of the deepest loop holding both
+    int la = inner[a], lb = inner[b];
+    int da = la == kNone ? 0 : ldepth[la], db = lb == kNone ? 0 : ldepth[lb];
+    while (da > db) { la = lparent[la]; --da; }
+    while (db > da) { lb = lparent[lb]; --db; }
+    while (la != lb) { la = lparent[la]; lb = lparent[lb]; --da; }
+    return da;
+  };
+
+  // loop-ordered DFS: at every block visit successors that leave the most
+  // loops first, so that their subtrees finish first and every loop body
+  // ends up as one run of positions right after its header.
+  std::vector<int32_t> post;
+  post.reserve(pre.size());
+  {
+    std::vector<uint8_t> seen(N, 0);
+    std::vector<int32_t> sorted_succ(g->E);
+    for (int b = 0; b < N; ++b) {
+      if (!reach[b]) continue;
+      int n = so[b + 1] - so[b];
+      int32_t *dst = sorted_succ.data() + so[b];
+      for (int k = 0; k < n; ++k) dst[k] = succ[so[b] + k];
+      if (n > 1) {
+        std::vector<std::pair<int, int>> key(n);
+        for (int k = 0; k < n; ++k) key[k] = {common_depth(b, dst[k]), k};
+        std::stable_sort(key.begin(), key.end());
+        std::vector<int32_t> tmp(n);
+        for (int k = 0; k < n; ++k) tmp[k] = dst[key[k].second];
+        for (int k = 0; k < n; ++k) dst[k] = tmp[k];
+      }
+    }
+    std::vector<std::pair<int32_t, int32_t>> st;
+    st.push_back({c->entry, so[c->entry]});
+    seen[c->entry] = 1;
+    while (!st.empty()) {
+      auto &t = st.back();
+      if (t.second < so[t.first + 1]) {
+        int s = sorted_succ[t.second++];
+        if (!seen[s]) {
+          seen[s] = 1;
+          st.push_back({s, so[s]});
+        }
+      } else {
+        post.push_back(t.first);
+        st.pop_back();
+      }
+    }
+  }
+  const int M = (int)post.size();
+  g->M = M;
+  g->order.assign(post.rbegin(), post.rend());
+  g->pos.assign(N, kNone);
+  for (int i = 0; i < M; ++i) g->pos[g->order[i]] = i;
+
+  // reducibility: every retreating edge must be a back edge
+  g->reducible = true;
+  for (int i = 0; i < M && g->reducible; ++i) {
+    int u = g->order[i];
+    for (int e = so[u]; e < so[u + 1]; ++e) {
+      int v = succ[e];
+      if (g->pos[v] <= i && !dominates(v, u)) {
+        g->reducible = false;
+        break;
+      }
+    }
+  }
+
+  // loops renumbered by header position
+  std::vector<int32_t> perm(L);
+  for (int l = 0; l < L; ++l) perm[l] = l;
+  std::sort(perm.begin(), perm.end(), [&](int a, int b) { return g->pos[headers[a]] < g->pos[headers[b]]; });
+  std::vector<int32_t> newid(L);
+  for (int k = 0; k < L; ++k) newid[perm[k]] = k;
+  g->L = L;
+  g->loop_head.resize(L);
+  g->loop_parent.resize(L);
+  g->loop_depth.resize(L);
+  g->loop_end.resize(L);
+  g->body_off.assign(L + 1, 0);
+  g->body_blk.clear();
+  g->contiguous = true;
+  for (int k = 0; k < L; ++k) {
+    int l = perm[k];
+    g->loop_head[k] = headers[l];
+    g->loop_parent[k] = lparent[l] == kNone ? kNone : newid[lparent[l]];
+    g->loop_depth[k] = ldepth[l];
+    std::vector<int32_t> bd = bodies[l];
+    std::sort(bd.begin(), bd.end(), [&](int a, int b) { return g->pos[a] < g->pos[b]; });
+    int p0 = g->pos[bd.front()], p1 = g->pos[bd.back()];
+    if (bd.front() != headers[l] || p1 - p0 + 1 != (int)bd.size()) g->contiguous = false;
+    g->loop_end[k] = p1 + 1;
+    g->body_blk.insert(g->body_blk.end(), bd.begin(), bd.end());
+    g->body_off[k + 1] = (int32_t)g->body_blk.size();
+  }
+  g->inner_loop.assign(N, kNone);
+  for (int b = 0; b < N; ++b)
+    if (inner[b] != kNone) g->inner_loop[b] = newid[inner[b]];
+
+  // loop-entry edges: p -> header with p outside the body
+  g->ent_loop.clear();
+  g->ent_src.clear();
+  g->ent_eid.clear();
+  std::vector<int32_t> eid_ent(g->E, kNone);
+  for (int k = 0; k < L; ++k) {
+    int h = g->loop_head[k];
+    for (int q = po[h]; q < po[h + 1]; ++q) {
+      int p = psrc[q];
+      if (!reach[p]) continue;
+      // p outside body(k)  <=>  k is not an ancestor-or-self of inner(p)
+      bool inside = false;
+      for (int x = g->inner_loop[p]; x != kNone; x = g->loop_parent[x])
+        if (x == k) { inside = true; break; }
+      if (inside) continue;
+      eid_ent[peid[q]] = (int32_t)g->ent_loop.size();
+      g->ent_loop.push_back(k);
+      g->ent_src.push_back(p);
+      g->ent_eid.push_back(peid[q]);
+    }
+  }
+  g->K = (int)g->ent_loop.size();
+
+  // position-ordered edge lists
+  g->fin_off.assign(M + 1, 0);
+  g->out_off.assign(M + 1, 0);
+  g->is_exit.assign(M, 0);
+  g->fin_src.clear(); g->fin_eid.clear(); g->fin_ent.clear(); g->out_dst.clear();
+  g->exit_blocks.clear();
+  for (int i = 0; i < M; ++i) {
+    int b = g->order[i];
+    for (int q = po[b]; q < po[b + 1]; ++q) {
+      if (!reach[psrc[q]]) continue;
+      g->fin_src.push_back(psrc[q]);
+      g->fin_eid.push_back(peid[q]);
+      g->fin_ent.push_back(eid_ent[peid[q]]);
+    }
+    g->fin_off[i + 1] = (int32_t)g->fin_src.size();
+    for (int e = so[b]; e < so[b + 1]; ++e) g->out_dst.push_back(succ[e]);
+    g->out_off[i + 1] = (int32_t)g->out_dst.size();
+    g->is_exit[i] = so[b] == so[b + 1];
+  }
+  for (int b = 0; b < N; ++b)
+    if (reach[b] && so[b] == so[b + 1]) g->exit_blocks.push_back(b);
+  g->chunk_off.assign({0, M});
+  g->max_chunk = M;
+  return OMPDART_OK;
+}
+
+// Single-entry cut before position i (0 < i < M): every edge that crosses
+// it (source before i, target at or after i) targets order[i], and no edge
+// goes from at-or-after i back to before i.  Then the whole influence of
+// positions < i on positions >= i is one value -- the one entering order[i]
+// -- and the same holds for the backward problem in the other direction.
+void make_chunks(Ingest *g, int target) {
+  const int M = g->M;
+  g->chunk_off.clear();
+  g->chunk_off.push_back(0);
+  if (M <= 1 || target <= 0 || target >= M) {
+    g->chunk_off.push_back(M);
+    g->max_chunk = M;
+    return;
+  }
+  // fwd[i]: edges with pos(src) < i <= pos(dst), counted by difference
+  // arrays; into[i]: edges into order[i] from positions < i; back[i]:
+  // edges with pos(dst) < i <= pos(src).
+  std::vector<int64_t> fwd(M + 1, 0), back(M + 1, 0);
+  std::vector<int32_t> into(M, 0);
+  for (int j = 0; j < M; ++j) {
+    int u = g->order[j];
+    (void)u;
+    for (int k = g->out_off[j]; k < g->out_off[j + 1]; ++k) {
+      int pd = g->pos[g->out_dst[k]];
+      if (pd > j) {
+        fwd[j + 1]++;
+        fwd[pd + 1]--;
+        into[pd]++;
+      } else {
+        back[pd + 1]++;
+        back[j + 1]--;
+      }
+    }
+  }
+  std::vector<uint8_t> ok(M + 1, 0);
+  int64_t f = 0, bk = 0;
+  for (int i = 0; i <= M; ++i) {
+    f += fwd[i];
+    bk += back[i];
+    if (i > 0 && i < M) ok[i] = (bk == 0) && (f == into[i]);
+  }
+  int start = 0;
+  g->max_chunk = 0;
+  for (int i = 1; i < M; ++i) {
+    if (ok[i] && i - start >= target) {
+      g->chunk_off.push_back(i);
+      g->max_chunk = std::max(g->max_chunk, i - start);
+      start = i;
+    }
+  }
+  g->chunk_off.push_back(M);
+  g->max_chunk = std::max(g->max_chunk, M - start);
+}
+
+}  // namespace ompdart

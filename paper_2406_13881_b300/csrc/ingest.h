@@ -1,0 +1,63 @@
+// ingest.h -- host-side ingestion of one CFG (internal to libompdart).
+//
+// Turns the caller's CSR CFG into what the device solvers need:
+//   * validation of the input format (ompdart.h);
+//   * reachability, predecessor lists with edge ids;
+//   * dominators (Lengauer-Tarjan) and natural loops (Sec. IV-B: loops are
+//     recognised; Sec. IV-D: revisiting a node means a loop);
+//   * a loop-ordered reverse post-order: every natural-loop body is a
+//     contiguous run of positions starting at its header whenever the CFG
+//     allows it (the DFS leaves loops before it enters their bodies);
+//   * single-entry cut points of that order and the chunks built on them,
+//     used by the chunked scan solver.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ompdart.h"
+
+namespace ompdart {
+
+struct Ingest {
+  int N = 0, E = 0, A = 0, V = 0, W = 0, entry = 0;
+  int M = 0;                        // reachable blocks
+  std::vector<int32_t> order;       // [M] block at each position
+  std::vector<int32_t> pos;         // [N] position of each block, -1 if unreachable
+  // forward in-edges of each position (reachable sources only), CSR
+  std::vector<int32_t> fin_off;     // [M+1]
+  std::vector<int32_t> fin_src;     // source block
+  std::vector<int32_t> fin_eid;     // edge id
+  std::vector<int32_t> fin_ent;     // loop-entry edge index or -1
+  // out-edges of each position (reachable targets are all reachable), CSR
+  std::vector<int32_t> out_off;     // [M+1]
+  std::vector<int32_t> out_dst;     // target block
+  std::vector<uint8_t> is_exit;     // [M] no successor
+  std::vector<int32_t> exit_blocks; // reachable blocks without successors, ascending id
+  // natural loops (one per header), numbered by header position
+  int L = 0;
+  std::vector<int32_t> loop_head;   // [L] header block
+  std::vector<int32_t> loop_parent; // [L] enclosing loop or -1
+  std::vector<int32_t> loop_depth;  // [L] 1 = outermost
+  std::vector<int32_t> body_off;    // [L+1]
+  std::vector<int32_t> body_blk;    // blocks of each body, ascending position
+  std::vector<int32_t> inner_loop;  // [N] innermost loop of each block or -1
+  std::vector<int32_t> loop_end;    // [L] one past the last body position (contiguous order)
+  // loop-entry edges p->h (h header, p outside body(h)), reachable p only
+  int K = 0;
+  std::vector<int32_t> ent_loop, ent_src, ent_eid;
+  bool reducible = true;            // every retreating edge is a back edge
+  bool contiguous = true;           // every loop body is a run of positions
+  // chunks of the order for the scan solver: chunk c = positions
+  // [chunk_off[c], chunk_off[c+1]); each boundary is a single-entry cut
+  std::vector<int32_t> chunk_off;
+  int max_chunk = 0;
+};
+
+// Returns OMPDART_OK or OMPDART_E_INVALID (message in *err).
+int ingest(const ompdart_cfg *cfg, Ingest *g, std::string *err);
+
+// Build chunks of about `target` positions at single-entry cut points.
+void make_chunks(Ingest *g, int target);
+
+}  // namespace ompdart

@@ -1,0 +1,100 @@
+"""GPU parity: every output of libompdart (through the C ABI) equals the CPU
+oracle bit for bit -- states, per-access flags, edge transfers and exit
+transfers.  All of it is integer/bitwise work, so the tolerance is zero."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2406_13881_b300 import _native, workload as wl
+from compare import assert_matches_oracle
+import listings
+
+pytestmark = pytest.mark.gpu
+
+
+def run_both(g, **opts):
+    res = _native.analyze(g, **opts)
+    orc = oracle.solve(g)
+    return res, orc
+
+
+@pytest.mark.parametrize("path", [1, 0])
+@pytest.mark.parametrize("name", sorted(listings.load()))
+def test_paper_listings(name, path):
+    g, _ = listings.to_cfg(listings.load()[name])
+    res, orc = run_both(g, path=path, keep_states=True)
+    assert_matches_oracle(g, res, orc)
+
+
+@pytest.mark.parametrize("path", [1, 0])
+@pytest.mark.parametrize("seed", [1, 2, 3, 4, 5])
+def test_small_single_cfg(seed, path):
+    g = wl.single_small(seed)
+    res, orc = run_both(g, path=path, keep_states=True)
+    assert_matches_oracle(g, res, orc)
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_random_graphs_sweep_path(seed):
+    """Unstructured, often irreducible CFGs with unreachable blocks,
+    duplicate edges and self-loops; 1 to 3 words per plane."""
+    rng = np.random.default_rng(100 + seed)
+    n = int(rng.integers(1, 40))
+    nv = int(rng.choice([1, 5, 63, 64, 65, 130]))
+    g = wl.random_graph(None, n, nv, max_out=3, acc_max=6, rng=rng)
+    if seed % 3 == 1:
+        g.entry_dev_valid = rng.integers(0, 2**63, size=g.W, dtype=np.uint64)
+    if seed % 4 == 2:
+        g.exit_host_live = rng.integers(0, 2**63, size=g.W, dtype=np.uint64)
+    res, orc = run_both(g, path=1, keep_states=True)
+    assert_matches_oracle(g, res, orc)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_structured_multiword(seed):
+    g = wl.structured(500 + seed, 3000, [64, 200, 700, 1024, 4096, 77][seed],
+                      acc_min=1, acc_max=12, var_dist="zipf")
+    res, orc = run_both(g, keep_states=True)
+    assert_matches_oracle(g, res, orc)
+
+
+def test_edge_cases():
+    cases = [
+        wl.from_lists([[]], [[]], 1),                                       # one block, no access
+        wl.from_lists([[]], [[(0, 2, 1), (0, 1, 0), (1, 3, 1)]], 2),        # one block
+        wl.from_lists([[1, 1], [2], []], [[(0, 2, 1)], [(0, 1, 0)], []], 3),  # duplicate edge
+        wl.from_lists([[1], [1, 2], [], [2]], [[], [(0, 3, 1)], [(0, 1, 0)], [(0, 2, 0)]], 1),  # self loop, unreachable block 3
+        wl.from_lists([[1], []], [[(5, 1, 1)], [(5, 1, 0)]], 6, entry_dev_valid=wl.var_mask(6, [5]),
+                      entry_host_valid=wl.var_mask(6, [])),                   # valid only on the device
+    ]
+    for g in cases:
+        for path in (1, 0):
+            res, orc = run_both(g, path=path, keep_states=True)
+            assert_matches_oracle(g, res, orc)
+
+
+def test_bounded_loops_report_noconverge():
+    """A fixed point that needs two sweeps with max_sweeps = 1 returns
+    E_NOCONVERGE (the device loop stops and reports; nothing traps)."""
+    g = wl.from_lists([[1], [2, 3], [1], []], [[], [(0, 1, 1)], [(0, 2, 0)], []], 1)
+    with pytest.raises(_native.OmpdartError) as ei:
+        _native.analyze(g, path=1, max_sweeps=1)
+    assert ei.value.code == _native.E_NOCONVERGE
+    # and the library stays usable
+    res, orc = run_both(g, path=1)
+    assert_matches_oracle(g, res, orc)
+
+
+def test_plan_reuse_is_deterministic():
+    g = wl.single_small(7)
+    p = _native.Plan(g, keep_states=True)
+    outs = []
+    for _ in range(3):
+        p.run()
+        p.sync()
+        outs.append(p.fetch())
+    for o in outs[1:]:
+        for k in ("h_in", "d_in", "h_out", "d_out", "acc_flag", "from_exit"):
+            np.testing.assert_array_equal(o[k], outs[0][k])
+    assert p.launches > 0
+    p.close()
