@@ -1,0 +1,335 @@
+#!/usr/bin/env python
+"""Benchmark of the host/device validity data-flow on one B300.
+
+Workload: the single large CFG -- 2^20 basic blocks, mean out-degree ~1.3,
+loops nested up to 4 deep (~5% back edges), 4096 variables (64 uint64 words
+per state per block), ~20% of the blocks in kernel regions, 1-16 accesses
+per block (Zipf(1.1) variables, R:W = 70:30); seed 2; synthetic.
+
+One step = the whole analysis: local summaries, anticipation/liveness,
+plain host validity, loop masks, device validity, host validity and the
+emission of every transfer (per-access flags, edge records, exit
+transfers).  The metric is block x variable-word updates per second to
+the fixed point: n_blocks * n_words / step time.
+
+  value  -- device time of K steps (CUDA events on the launch stream),
+            inputs resident in HBM, state planes (512 MiB each) larger than
+            L2 so no flush is needed
+  e2e    -- the same metric through ompdart_analyze with host buffers
+            (ingestion, host->device copies, solve, device->host copies)
+  roofline, cpu_baseline, clocks, gpu_launches -- see the design doc
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "block·var-word updates/s to fixed point"
+UNIT = "updates/s"
+WORKLOAD = "single large CFG: 2^20 blocks, 4096 variables (64 words), seed 2"
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes per launch (the design's own traffic model)
+# ---------------------------------------------------------------------------
+
+def byte_model(st):
+    """Algorithmic DRAM bytes per launch of each kernel, from the workload
+    statistics.  Per position the chain kernels read one 64 B position
+    record, ~8 B per in/out edge, 4 B per access record and the block's
+    access offsets (together `struct`); dense planes are W words of 8 B per
+    block."""
+    N, M, E, A, W, K, L = (st[k] for k in ("N", "M", "E", "A", "W", "K", "L"))
+    G = (W + 63) // 64
+    plane = 8.0 * W * N
+    struct = G * (M * 64.0 + E * 8.0 + A * 4.0 + N * 8.0)
+    return {
+        "local_summary": A * 8.0 + N * 4.0,
+        "ant_summary": struct,
+        "ant_apply": struct + plane,                       # writes Live
+        "loop_masks": G * st["body"] * 80.0 + 2 * L * 8.0 * W,
+        "hp_summary": struct,
+        "hp_apply": struct + K * 8.0 * W,                  # plain host validity at loop-entry sources
+        "d_summary": struct + K * 8.0 * W,
+        "d_apply": struct + K * 8.0 * W + plane + K * 8.0 * W,   # writes D_in, device validity at sources
+        "h_summary": struct + K * 8.0 * W + 2 * plane,     # reads Live, D_in
+        "h_apply_emit": struct + 3 * K * 8.0 * W + 3 * plane + A * 5.0,  # reads Live, D_in; writes H_in, flags
+    }
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region (NVML reads only)
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    def __init__(self, index=0, period=0.01):
+        self.samples, self.reasons, self.max_mhz = [], set(), None
+        self.period, self.index = period, index
+        self._stop = threading.Event()
+        self._t = None
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            self.nv = pynvml
+            self.h = pynvml.nvmlDeviceGetHandleByIndex(index)
+            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
+        except Exception:
+            self.nv = None
+
+    def _run(self):
+        nv = self.nv
+        names = {
+            "hw_slowdown": getattr(nv, "nvmlClocksEventReasonHwSlowdown", 0x8),
+            "sw_thermal_slowdown": getattr(nv, "nvmlClocksEventReasonSwThermalSlowdown", 0x20),
+            "hw_thermal_slowdown": getattr(nv, "nvmlClocksEventReasonHwThermalSlowdown", 0x40),
+            "sw_power_cap": getattr(nv, "nvmlClocksEventReasonSwPowerCap", 0x4),
+        }
+        while not self._stop.is_set():
+            try:
+                self.samples.append(nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM))
+                try:
+                    r = nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
+                except Exception:
+                    r = nv.nvmlDeviceGetCurrentClocksThrottleReasons(self.h)
+                for k, bit in names.items():
+                    if r & bit:
+                        self.reasons.add(k)
+            except Exception:
+                pass
+            time.sleep(self.period)
+
+    def start(self):
+        if self.nv:
+            self._t = threading.Thread(target=self._run, daemon=True)
+            self._t.start()
+
+    def stop(self):
+        if self._t:
+            self._stop.set()
+            self._t.join()
+        return {"sm_mhz": statistics.median(self.samples) if self.samples else None,
+                "sm_max_mhz": self.max_mhz, "reasons": sorted(self.reasons),
+                "samples": len(self.samples)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded sample (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(g, words):
+    import oracle
+    from paper_2406_13881_b300 import workload as wl
+    oracle.build()
+    t_total = 0.0
+    for w in words:
+        sub, _ = wl.restrict_word(g, w)
+        t0 = time.perf_counter()
+        oracle.solve(sub, want=["h_in", "d_in", "to_edge", "from_edge", "from_exit", "acc_flag"])
+        t_total += time.perf_counter() - t0
+    value = g.n_blocks * len(words) / t_total
+    return value, t_total
+
+
+def cpu_info():
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except Exception:
+        pass
+    return model
+
+
+# ---------------------------------------------------------------------------
+
+def workload_stats(g, plan_ing=None):
+    import numpy as np
+    W = g.W
+    st = {"N": g.n_blocks, "M": g.n_blocks, "E": g.n_edges, "A": g.n_acc, "W": W,
+          "K": g.meta.get("loop_entry_edges", 0), "L": g.meta.get("headers", 0)}
+    loops = g.meta.get("loops", [])
+    st["body"] = float(sum(e - f + 1 for _, f, e, _ in loops))
+    return st
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2406_13881_b300 import _native, build, workload as wl
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    build.build()
+    g = wl.single_large(args.seed)
+    # loop-entry edge count for the byte model comes from the plan's ingestion;
+    # count it here from the generator's loops (every header's non-latch preds)
+    so, su = g.succ_off, g.succ
+    n = g.n_blocks
+    preds = np.zeros(n + 1, dtype=np.int64)
+    np.add.at(preds, su + 1, 1)
+    heads = np.array([h for h, _, _, _ in g.meta["loops"]], dtype=np.int64)
+    g.meta["loop_entry_edges"] = int((preds[heads + 1] - 1).sum()) if len(heads) else 0
+
+    plan = _native.Plan(g, device=local)
+    stream = torch.cuda.Stream(device=local)
+    sh = stream.cuda_stream
+    for _ in range(args.warmup):
+        plan.run(sh)
+        plan.sync()
+    launches_per_step = plan.launches
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    plan.profile(True)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        plan.run(sh)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    plan.sync()
+    clk = clocks.stop()
+    timings = plan.timings()
+    plan.profile(False)
+    ms = ev0.elapsed_time(ev1)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    ms_step = ms / args.steps
+    units = g.n_blocks * g.W
+    value = units * world * args.steps / (ms / 1e3)
+
+    out = None
+    if rank == 0:
+        # ---- roofline of the dominant kernel (CUDA events over the timed region)
+        st = workload_stats(g)
+        model = byte_model(st)
+        dom = max(timings.items(), key=lambda kv: kv[1][1])
+        name, (nl, tot_ms) = dom
+        avg_ms = tot_ms / max(1, nl)
+        peak, src = peaks()
+        bytes_ = model.get(name)
+        achieved = bytes_ / (avg_ms / 1e3) / 1e9 if bytes_ else None
+        roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src,
+                "algorithmic_bytes_per_launch": bytes_, "avg_launch_ms": avg_ms,
+                "kernels": {k: {"launches": v[0], "ms": round(v[1], 4),
+                                "share": round(v[1] / sum(x[1] for x in timings.values()), 4)}
+                            for k, v in sorted(timings.items(), key=lambda kv: -kv[1][1])}}
+        # ---- end to end through the public API with host buffers
+        e2e_t, h2d, d2h = [], 0, 0
+        for _ in range(args.e2e_steps):
+            t0 = time.perf_counter()
+            r = _native.analyze(g, device=local)
+            e2e_t.append(time.perf_counter() - t0)
+            h2d, d2h = r["h2d_bytes"], r["d2h_bytes"]
+        e2e_s = statistics.median(e2e_t)
+        # ---- CPU oracle on a bounded sample of word columns
+        words = list(range(0, 64, 64 // args.cpu_words))[: args.cpu_words]
+        cpu_val, cpu_s = oracle_sample(g, words)
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_blocks": g.n_blocks, "n_vars": g.n_vars, "n_words": g.W,
+                       "n_edges": g.n_edges, "n_acc": g.n_acc, "seed": args.seed,
+                       "solver": "chunked scan" if plan.view().path == 2 else "sweep",
+                       "l2": "no flush: every state plane (512 MiB) is larger than the 126 MB L2",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roof,
+            "cpu_baseline": {"value": cpu_val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d of 64 word columns of the same CFG, single-threaded C oracle, %.1f s"
+                                       % (len(words), cpu_s), "cpu": cpu_info()},
+            "e2e": {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_s,
+                    "path": "ompdart_analyze: host ingestion + copies + solve + copy back"},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+        }
+    plan.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle, as it stands, on the host cores, on
+    a bounded sample of the same workload (a few word columns per step)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    from paper_2406_13881_b300 import workload as wl
+    g = wl.single_large(args.seed)
+    words_per_step = 1
+    times = []
+    for i in range(args.warmup + args.steps):
+        w = (7 * i) % 64
+        _, t = oracle_sample(g, [w])
+        if i >= args.warmup:
+            times.append(t)
+    tot = sum(times)
+    value = g.n_blocks * words_per_step * len(times) / tot
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_blocks": g.n_blocks, "n_vars": g.n_vars, "seed": args.seed},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "one of 64 word columns of the CFG per step", "cpu": cpu_info()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-words", type=int, default=8)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

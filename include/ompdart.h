@@ -117,6 +117,8 @@ typedef struct {
   uint64_t *from_exit;         /* [n_exits*n_words]                            */
   int32_t path;                /* solver that ran: 1 sweep, 2 chunked scan      */
   int32_t sweeps;              /* device sweeps executed (diagnostic)           */
+  int64_t h2d_bytes;           /* bytes the plan copied host->device            */
+  int64_t d2h_bytes;           /* bytes copied device->host for this result     */
 } ompdart_result;
 
 typedef struct ompdart_plan ompdart_plan;
@@ -145,6 +147,21 @@ int ompdart_plan_fetch(ompdart_plan *plan, ompdart_result **out);
 
 /* Number of kernel launches one ompdart_plan_run enqueues. */
 int ompdart_plan_launches(const ompdart_plan *plan);
+
+/* Per-kernel device time.  After ompdart_plan_profile(plan, 1), every run
+   records a CUDA event on its stream before each kernel launch and after
+   the last; ompdart_plan_sync charges the time between consecutive events
+   to the kernel launched between them and accumulates it per kernel name.
+   ompdart_plan_timings copies up to `max' entries (name strings owned by
+   the plan) and sets *n to the number of distinct kernels.  Enabling or
+   disabling resets the totals. */
+typedef struct {
+  const char *name;
+  int32_t launches;
+  double ms;
+} ompdart_timing;
+int ompdart_plan_profile(ompdart_plan *plan, int enable);
+int ompdart_plan_timings(ompdart_plan *plan, ompdart_timing *out, int32_t max, int32_t *n);
 
 void ompdart_plan_destroy(ompdart_plan *plan);
 

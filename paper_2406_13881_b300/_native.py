@@ -59,10 +59,16 @@ class Result(C.Structure):
                 ("h_out", C.c_void_p), ("d_out", C.c_void_p), ("acc_flag", C.c_void_p),
                 ("n_edge_xfers", C.c_int32), ("edge_xfers", C.c_void_p),
                 ("exit_blocks", C.c_void_p), ("from_exit", C.c_void_p), ("path", C.c_int32),
-                ("sweeps", C.c_int32)]
+                ("sweeps", C.c_int32), ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64)]
+
+
+class Timing(C.Structure):
+    _fields_ = [("name", C.c_char_p), ("launches", C.c_int32), ("ms", C.c_double)]
 
 
 EXPORTS = {
+    "ompdart_plan_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "ompdart_plan_timings": (C.c_int, [C.c_void_p, C.POINTER(Timing), C.c_int32, C.POINTER(C.c_int32)]),
     "ompdart_plan_create": (C.c_int, [C.POINTER(Cfg), C.POINTER(Opts), C.POINTER(C.c_void_p)]),
     "ompdart_plan_run": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ompdart_plan_sync": (C.c_int, [C.c_void_p]),
@@ -143,7 +149,7 @@ def _result_to_numpy(r: Result) -> dict:
         "edge_xfers": arr(r.edge_xfers, r.n_edge_xfers, XFER_DTYPE),
         "exit_blocks": arr(r.exit_blocks, r.n_exits, np.int32),
         "from_exit": arr(r.from_exit, r.n_exits * W, np.uint64, (r.n_exits, W)),
-        "path": r.path, "sweeps": r.sweeps,
+        "path": r.path, "sweeps": r.sweeps, "h2d_bytes": int(r.h2d_bytes), "d2h_bytes": int(r.d2h_bytes),
     }
     if r.h_out:
         out["h_out"] = arr(r.h_out, n * W, np.uint64, (n, W))
@@ -193,6 +199,17 @@ class Plan:
             return _result_to_numpy(res.contents)
         finally:
             self._lib.ompdart_result_free(res)
+
+    def profile(self, enable: bool = True):
+        _check(self._lib.ompdart_plan_profile(self._h, int(bool(enable))))
+
+    def timings(self) -> dict:
+        """{kernel name: (launches, total ms)} accumulated since profile(True)."""
+        n = C.c_int32()
+        _check(self._lib.ompdart_plan_timings(self._h, None, 0, C.byref(n)))
+        arr = (Timing * max(1, n.value))()
+        _check(self._lib.ompdart_plan_timings(self._h, arr, n.value, C.byref(n)))
+        return {arr[i].name.decode(): (arr[i].launches, arr[i].ms) for i in range(n.value)}
 
     @property
     def launches(self) -> int:

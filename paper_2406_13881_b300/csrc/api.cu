@@ -14,14 +14,17 @@
 #include "plan.cuh"
 
 namespace ompdart {
-int enqueue_local_summary(const DevPlan &p, cudaStream_t s);
-int enqueue_sweep_solver(const DevPlan &p, cudaStream_t s, int n_fin);
+int enqueue_local_summary(const DevPlan &p, cudaStream_t s, Prof *pf);
+int enqueue_fill_unreachable(const DevPlan &p, cudaStream_t s, int keep_states, Prof *pf);
+int enqueue_sweep_solver(const DevPlan &p, cudaStream_t s, int n_fin, Prof *pf);
 int enqueue_sweep_edges(const DevPlan &p, cudaStream_t s, int n_fin);
 int scan_supported(const Ingest &g);
 struct ScanState;
-ScanState *scan_create(const Ingest &g, DevPlan &p, cudaStream_t s, std::string *err);
-int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s);
-int enqueue_scan_edges(ScanState *st, const DevPlan &p, cudaStream_t s);
+ScanState *scan_create(const Ingest &g, DevPlan &p, int chunk_target, int keep_states, std::string *err);
+bool scan_grow_streams(ScanState *st);
+long long scan_h2d_bytes(const ScanState *st);
+int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *pf);
+int enqueue_scan_edges(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *pf);
 void scan_destroy(ScanState *st);
 }  // namespace ompdart
 
@@ -51,8 +54,10 @@ struct ompdart_plan {
   int launches = 0;
   int n_fin = 0;
   int keep_states = 0;
+  long long h2d = 0;
   ScanState *scan = nullptr;
   int32_t *h_status = nullptr;  // pinned
+  Prof prof;
 
   template <class T>
   T *dalloc(size_t n) {
@@ -65,6 +70,7 @@ struct ompdart_plan {
   T *upload(const T *src, size_t n) {
     T *d = dalloc<T>(n);
     if (d && n && cudaMemcpy(d, src, n * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
+    h2d += (long long)(n * sizeof(T));
     return d;
   }
   template <class T>
@@ -162,6 +168,13 @@ int ompdart_plan_create(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdar
   chk(d.out_dst = P->upload(g.out_dst));
   chk(d.is_exit = P->upload(g.is_exit));
   chk(d.exit_blocks = P->upload(g.exit_blocks));
+  {
+    std::vector<int32_t> un;
+    for (int b = 0; b < g.N; ++b)
+      if (g.pos[b] < 0) un.push_back(b);
+    d.n_unreach = (int)un.size();
+    chk(d.unreach = P->upload(un));
+  }
   chk(d.acc_off = P->upload(cfg->acc_off, (size_t)g.N + 1));
   chk(d.acc = P->upload(cfg->acc, (size_t)g.A));
   chk(d.rec = P->dalloc<uint32_t>(g.A));
@@ -204,7 +217,7 @@ int ompdart_plan_create(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdar
     chk(d.ant_d = P->dalloc<uint64_t>(NW));
     chk(d.lant = P->dalloc<uint64_t>(g.body_blk.size() * (size_t)W * 2));
   } else {
-    P->scan = scan_create(g, d, P->stream, &err);
+    P->scan = scan_create(g, d, o.chunk_target, o.keep_states, &err);
     if (!P->scan) {
       delete P;
       return set_err(OMPDART_E_NOMEM, err);
@@ -229,11 +242,14 @@ int ompdart_plan_run(ompdart_plan *P, void *stream) {
   cudaStream_t s = stream ? (cudaStream_t)stream : P->stream;
   P->last_stream = s;
   cudaMemsetAsync(P->dp.status, 0, ST_COUNT * sizeof(int32_t), s);
-  int n = enqueue_local_summary(P->dp, s);
+  Prof *pf = P->prof.on ? &P->prof : nullptr;
+  if (pf) pf->collect_pending = true;
+  int n = enqueue_local_summary(P->dp, s, pf);
   if (P->path == 1)
-    n += enqueue_sweep_solver(P->dp, s, P->n_fin);
+    n += enqueue_sweep_solver(P->dp, s, P->n_fin, pf);
   else
-    n += enqueue_scan_solver(P->scan, P->dp, s);
+    n += enqueue_scan_solver(P->scan, P->dp, s, pf) + enqueue_fill_unreachable(P->dp, s, P->keep_states, pf);
+  if (pf) pf->close(s);
   P->launches = n;
   cudaError_t ce = cudaGetLastError();
   if (ce != cudaSuccess) return cuda_err(ce, "kernel launch");
@@ -247,8 +263,24 @@ int ompdart_plan_sync(ompdart_plan *P) {
                                    cudaMemcpyDeviceToHost, s);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
   if (ce != cudaSuccess) return cuda_err(ce, "device run");
+  if (P->prof.on && P->prof.collect_pending) {
+    P->prof.collect();
+    P->prof.collect_pending = false;
+  }
   if (P->h_status[ST_ERROR] == ERR_NOCONVERGE)
     return set_err(OMPDART_E_NOCONVERGE, "a device fixed-point loop reached max_sweeps");
+  if (P->path == 2 && P->h_status[ST_OVERFLOW]) {
+    // a per-warp record stream overflowed: size the streams and redo the
+    // host-validity pass (it is the one that emits)
+    if (!scan_grow_streams(P->scan)) return set_err(OMPDART_E_NOMEM, "growing transfer record streams failed");
+    cudaMemsetAsync(P->dp.status + ST_NREC, 0, 2 * sizeof(int32_t), s);
+    enqueue_scan_edges(P->scan, P->dp, s, nullptr);
+    ce = cudaMemcpyAsync(P->h_status, P->dp.status, ST_COUNT * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return cuda_err(ce, "device run");
+    if (P->h_status[ST_ERROR] == ERR_NOCONVERGE)
+      return set_err(OMPDART_E_NOCONVERGE, "a device fixed-point loop reached max_sweeps");
+  }
   const int nrec = P->h_status[ST_NREC];
   if (nrec > P->dp.xfer_cap) {
     // the record buffer overflowed: enlarge it and redo the edge emission
@@ -258,7 +290,7 @@ int ompdart_plan_sync(ompdart_plan *P) {
     if (P->path == 1)
       enqueue_sweep_edges(P->dp, s, P->n_fin);
     else
-      enqueue_scan_edges(P->scan, P->dp, s);
+      enqueue_scan_edges(P->scan, P->dp, s, nullptr);
     ce = cudaMemcpyAsync(P->h_status, P->dp.status, ST_COUNT * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
     if (ce != cudaSuccess) return cuda_err(ce, "device run");
@@ -283,10 +315,33 @@ int ompdart_plan_view(ompdart_plan *P, ompdart_result *v) {
   v->from_exit = P->dp.from_exit;
   v->path = P->path;
   v->sweeps = P->h_status[ST_SWEEPS];
+  v->h2d_bytes = P->h2d + scan_h2d_bytes(P->scan);
+  v->d2h_bytes = 0;
   return OMPDART_OK;
 }
 
 int ompdart_plan_launches(const ompdart_plan *P) { return P ? P->launches : 0; }
+
+int ompdart_plan_profile(ompdart_plan *P, int enable) {
+  if (!P) return set_err(OMPDART_E_INVALID, "plan is NULL");
+  P->prof.on = enable != 0;
+  for (double &x : P->prof.ms) x = 0.0;
+  for (int &x : P->prof.cnt) x = 0;
+  P->prof.used = 0;
+  return OMPDART_OK;
+}
+
+int ompdart_plan_timings(ompdart_plan *P, ompdart_timing *out, int32_t max, int32_t *n) {
+  if (!P || !n) return set_err(OMPDART_E_INVALID, "NULL argument");
+  const int k = (int)P->prof.names.size();
+  *n = k;
+  for (int i = 0; i < k && i < max && out; ++i) {
+    out[i].name = P->prof.names[i].c_str();
+    out[i].launches = P->prof.cnt[i];
+    out[i].ms = P->prof.ms[i];
+  }
+  return OMPDART_OK;
+}
 
 void ompdart_plan_destroy(ompdart_plan *P) { delete P; }
 
@@ -331,6 +386,9 @@ int ompdart_plan_fetch(ompdart_plan *P, ompdart_result **out) {
   cp(r->exit_blocks, v.exit_blocks, sizeof(int32_t) * (size_t)v.n_exits);
   cp(r->from_exit, v.from_exit, 8 * (size_t)v.n_exits * v.n_words);
   if (ok && ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  r->d2h_bytes = (long long)(2 + (v.h_out ? 2 : 0)) * NW * 8 + v.n_acc +
+                 (long long)sizeof(ompdart_edge_xfer) * v.n_edge_xfers + 4ll * v.n_exits +
+                 8ll * v.n_exits * v.n_words + 4ll * ST_COUNT;
   if (!ok || ce != cudaSuccess) {
     ompdart_result_free(r);
     return ok ? cuda_err(ce, "copy of results") : set_err(OMPDART_E_NOMEM, "host allocation failed");

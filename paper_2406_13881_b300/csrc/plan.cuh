@@ -1,6 +1,11 @@
 // plan.cuh -- the device-side view of one ingested CFG (internal).
 #pragma once
+#include <cuda_runtime.h>
+
 #include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
 
 #include "common.cuh"
 
@@ -24,6 +29,8 @@ struct DevPlan {
   const int32_t *out_dst;  // target block
   const uint8_t *is_exit;  // [M]
   const int32_t *exit_blocks;  // [X]
+  const int32_t *unreach;      // [N - M] blocks not reachable from the entry
+  int n_unreach;
   // accesses
   const int32_t *acc_off;  // [N+1]
   const uint32_t *acc;     // [A]
@@ -50,6 +57,64 @@ struct DevPlan {
   int xfer_cap;
   uint64_t *from_exit;     // [X*W]
   int32_t *status;         // [ST_COUNT]
+};
+
+// Optional per-launch timing: a CUDA event is recorded on the launch stream
+// before every kernel and once after the last; the time between two events
+// is charged to the kernel launched between them.
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> kid;
+  std::vector<std::string> names;
+  std::vector<double> ms;
+  std::vector<int> cnt;
+  int used = 0;
+  bool collect_pending = false;
+  void mark(cudaStream_t s, const char *name) {
+    if (!on) return;
+    if (used + 1 >= (int)ev.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      ev.push_back(e);
+      cudaEventCreate(&e);
+      ev.push_back(e);
+    }
+    int k = 0;
+    while (k < (int)names.size() && names[k] != name) ++k;
+    if (k == (int)names.size()) {
+      names.push_back(name);
+      ms.push_back(0.0);
+      cnt.push_back(0);
+    }
+    kid.resize(used + 1);
+    kid[used] = k;
+    cudaEventRecord(ev[used], s);
+    ++used;
+  }
+  void close(cudaStream_t s) {
+    if (!on || !used) return;
+    if (used >= (int)ev.size()) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      ev.push_back(e);
+    }
+    cudaEventRecord(ev[used], s);
+  }
+  // after the stream finished
+  void collect() {
+    for (int i = 0; i < used; ++i) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, ev[i], ev[i + 1]) == cudaSuccess) {
+        ms[kid[i]] += t;
+        cnt[kid[i]] += 1;
+      }
+    }
+    used = 0;
+  }
+  ~Prof() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+  }
 };
 
 }  // namespace ompdart

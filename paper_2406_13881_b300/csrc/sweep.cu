@@ -67,6 +67,21 @@ __global__ void k_fill_top(uint64_t *plane, int rows, int W, const uint64_t *top
     plane[i] = top[i % W];
 }
 
+// rows of blocks unreachable from the entry: every state plane all-ones
+__global__ void k_fill_unreachable(DevPlan p, int keep_states) {
+  const long long n = (long long)p.n_unreach * p.W;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int w = (int)(t % p.W);
+    const size_t o = (size_t)p.unreach[t / p.W] * p.W + w;
+    p.h_in[o] = p.top[w];
+    p.d_in[o] = p.top[w];
+    if (keep_states) {
+      p.h_out[o] = p.top[w];
+      p.d_out[o] = p.top[w];
+    }
+  }
+}
+
 // ---- backward anticipation (Sec. II-B liveness, Sec. IV-D region exit) -------
 // AntS_in[b] = UES[b] | (AntS_out[b] & ~Def[b]); AntS_out[b] = OR of the
 // successors' AntS_in, or the region-exit value (host: exit_host_live,
@@ -319,36 +334,52 @@ static int grid_for(long long n, int block) {
 }
 
 // Enqueue the local summary kernel.  Returns the number of launches.
-int enqueue_local_summary(const DevPlan &p, cudaStream_t s) {
+int enqueue_local_summary(const DevPlan &p, cudaStream_t s, Prof *pf) {
   const int threads = 256;
+  if (pf) pf->mark(s, "local_summary");
   k_local_summary<<<grid_for((long long)p.N * 32, threads), threads, 0, s>>>(p);
   return 1;
 }
 
+#define PROF(name) if (pf) pf->mark(s, name)
+
 // Enqueue the whole sweep solver (after the local summary): anticipation,
 // plain host validity, masks, device validity, host validity, emission.
-int enqueue_sweep_solver(const DevPlan &p, cudaStream_t s, int n_fin) {
+int enqueue_sweep_solver(const DevPlan &p, cudaStream_t s, int n_fin, Prof *pf) {
   const int T = 128;
   int n = 0;
   const long long NW = (long long)p.N * p.W;
   for (uint64_t *pl : {p.hp_out, p.d_in, p.d_out, p.h_in, p.h_out}) {
+    PROF("fill_top");
     k_fill_top<<<grid_for(NW, 256), 256, 0, s>>>(pl, p.N, p.W, p.top);
     ++n;
   }
   cudaMemsetAsync(p.ant_h, 0, NW * sizeof(uint64_t), s);
   cudaMemsetAsync(p.ant_d, 0, NW * sizeof(uint64_t), s);
   cudaMemsetAsync(p.acc_flag, 0, (size_t)p.A, s);
+  PROF("sweep_ant");
   k_sweep_ant<<<grid_for(p.W, T), T, 0, s>>>(p); ++n;
+  PROF("sweep_hp");
   k_sweep_fwd<PH_HP><<<grid_for(p.W, T), T, 0, s>>>(p); ++n;
-  if (p.L) { k_sweep_masks<<<grid_for((long long)p.L * p.W, T), T, 0, s>>>(p); ++n; }
-  if (p.K) { k_edge_const<PH_D><<<grid_for((long long)p.K * p.W, T), T, 0, s>>>(p); ++n; }
+  if (p.L) { PROF("sweep_masks"); k_sweep_masks<<<grid_for((long long)p.L * p.W, T), T, 0, s>>>(p); ++n; }
+  if (p.K) { PROF("edge_const_d"); k_edge_const<PH_D><<<grid_for((long long)p.K * p.W, T), T, 0, s>>>(p); ++n; }
+  PROF("sweep_d");
   k_sweep_fwd<PH_D><<<grid_for(p.W, T), T, 0, s>>>(p); ++n;
-  if (p.K) { k_edge_const<PH_H><<<grid_for((long long)p.K * p.W, T), T, 0, s>>>(p); ++n; }
+  if (p.K) { PROF("edge_const_h"); k_edge_const<PH_H><<<grid_for((long long)p.K * p.W, T), T, 0, s>>>(p); ++n; }
+  PROF("sweep_h");
   k_sweep_fwd<PH_H><<<grid_for(p.W, T), T, 0, s>>>(p); ++n;
+  PROF("emit_flags");
   k_emit_flags<<<grid_for(p.M, T), T, 0, s>>>(p); ++n;
-  if (n_fin) { k_emit_edges<<<grid_for((long long)n_fin * p.W, T), T, 0, s>>>(p, n_fin); ++n; }
-  if (p.X) { k_emit_exit<<<grid_for((long long)p.X * p.W, T), T, 0, s>>>(p); ++n; }
+  if (n_fin) { PROF("emit_edges"); k_emit_edges<<<grid_for((long long)n_fin * p.W, T), T, 0, s>>>(p, n_fin); ++n; }
+  if (p.X) { PROF("emit_exit"); k_emit_exit<<<grid_for((long long)p.X * p.W, T), T, 0, s>>>(p); ++n; }
   return n;
+}
+
+int enqueue_fill_unreachable(const DevPlan &p, cudaStream_t s, int keep_states, Prof *pf) {
+  if (!p.n_unreach) return 0;
+  PROF("fill_unreachable");
+  k_fill_unreachable<<<grid_for((long long)p.n_unreach * p.W, 256), 256, 0, s>>>(p, keep_states);
+  return 1;
 }
 
 // Re-run the edge emission alone (after the record buffer was enlarged).

@@ -30,7 +30,7 @@ def assert_matches_oracle(g, res, orc, words=None, acc_keep=None):
         np.testing.assert_array_equal(res["d_out"][:, cols], orc["d_out"], err_msg="d_out")
     flags = res["acc_flag"] if acc_keep is None else res["acc_flag"][acc_keep]
     np.testing.assert_array_equal(flags, orc["acc_flag"], err_msg="acc_flag")
-    to, fr = dense_edges(res, g.n_edges, W)
+    to, fr = dense_edges(res, g.n_edges, res["h_in"].shape[1])
     np.testing.assert_array_equal(to[:, cols], orc["to_edge"], err_msg="to_edge")
     np.testing.assert_array_equal(fr[:, cols], orc["from_edge"], err_msg="from_edge")
     fx = orc["from_exit"]

@@ -98,3 +98,72 @@ def test_plan_reuse_is_deterministic():
             np.testing.assert_array_equal(o[k], outs[0][k])
     assert p.launches > 0
     p.close()
+
+
+# --------------------------------------------------------------------------
+# chunked scan solver
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("target", [1, 3, 8, 40])
+@pytest.mark.parametrize("seed", range(8))
+def test_scan_path_many_chunks(seed, target):
+    """Structured CFGs cut into many small chunks: every carry, crossing
+    edge and loop re-run path of the scan solver is exercised."""
+    rng = np.random.default_rng(900 + seed)
+    nv = int(rng.choice([3, 64, 100, 200]))
+    g = wl.structured(900 + seed, int(rng.integers(20, 600)), nv, acc_min=0, acc_max=6,
+                      var_dist="uniform", max_loop_depth=4, p_while=0.12)
+    if seed % 2:
+        g.entry_dev_valid = rng.integers(0, 2**63, size=g.W, dtype=np.uint64)
+        g.exit_host_live = rng.integers(0, 2**63, size=g.W, dtype=np.uint64)
+    res = _native.analyze(g, path=2, chunk_target=target, keep_states=True)
+    assert res["path"] == 2
+    assert_matches_oracle(g, res, oracle.solve(g))
+
+
+@pytest.mark.parametrize("name", sorted(listings.load()))
+def test_scan_path_listings_one_block_chunks(name):
+    g, _ = listings.to_cfg(listings.load()[name])
+    res = _native.analyze(g, path=2, chunk_target=1, keep_states=True)
+    assert_matches_oracle(g, res, oracle.solve(g))
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_scan_equals_sweep(seed):
+    g = wl.structured(1300 + seed, 5000, 300, acc_min=1, acc_max=10)
+    a = _native.analyze(g, path=1, keep_states=True)
+    b = _native.analyze(g, path=2, keep_states=True)
+    for k in ("h_in", "d_in", "h_out", "d_out", "acc_flag", "from_exit"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    key = lambda r: sorted(zip(r["edge_xfers"]["edge"], r["edge_xfers"]["word"],
+                               r["edge_xfers"]["to_bits"], r["edge_xfers"]["from_bits"]))
+    assert key(a) == key(b)
+
+
+def test_unreachable_blocks_scan_path():
+    g = wl.from_lists([[1], [2], [], [1], [3]], [[(0, 2, 0)], [(0, 1, 1)], [], [(1, 2, 1)], [(0, 3, 1)]], 3)
+    res = _native.analyze(g, path=2, keep_states=True)
+    assert_matches_oracle(g, res, oracle.solve(g))
+
+
+@pytest.fixture(scope="module")
+def large_cfg():
+    return wl.single_large(2)
+
+
+@pytest.mark.slow
+def test_large_cfg_sampled_words(large_cfg):
+    """The 2^20-block, 4096-variable CFG in the launch configuration the
+    bench times (plan, run, view); word columns 0, 21 and 63 against the
+    oracle run on exactly those 64 variables."""
+    g = large_cfg
+    p = _native.Plan(g)
+    p.run()
+    p.sync()
+    res = p.fetch()
+    assert res["path"] == 2
+    for w in (0, 21, 63):
+        sub, keep = wl.restrict_word(g, w)
+        orc = oracle.solve(sub)
+        assert_matches_oracle(sub, res, orc, words=slice(w, w + 1), acc_keep=keep)
+    p.close()
