@@ -39,6 +39,10 @@ UNIT = "updates/s"
 WORKLOAD = "single large CFG: 2^20 blocks, 4096 variables (64 words), seed 2"
 
 
+def workload_name(n_blocks):
+    return WORKLOAD if n_blocks == 1 << 20 else WORKLOAD.replace("2^20", str(n_blocks))
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -81,54 +85,56 @@ def byte_model(st):
 # ---------------------------------------------------------------------------
 
 class ClockSampler:
-    def __init__(self, index=0, period=0.01):
-        self.samples, self.reasons, self.max_mhz = [], set(), None
-        self.period, self.index = period, index
-        self._stop = threading.Event()
-        self._t = None
-        try:
-            import pynvml
-            pynvml.nvmlInit()
-            self.nv = pynvml
-            self.h = pynvml.nvmlDeviceGetHandleByIndex(index)
-            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self.h, pynvml.NVML_CLOCK_SM)
-        except Exception:
-            self.nv = None
+    """Polls nvidia-smi (read-only queries) every 100 ms while running."""
 
-    def _run(self):
-        nv = self.nv
-        names = {
-            "hw_slowdown": getattr(nv, "nvmlClocksEventReasonHwSlowdown", 0x8),
-            "sw_thermal_slowdown": getattr(nv, "nvmlClocksEventReasonSwThermalSlowdown", 0x20),
-            "hw_thermal_slowdown": getattr(nv, "nvmlClocksEventReasonHwThermalSlowdown", 0x40),
-            "sw_power_cap": getattr(nv, "nvmlClocksEventReasonSwPowerCap", 0x4),
-        }
-        while not self._stop.is_set():
-            try:
-                self.samples.append(nv.nvmlDeviceGetClockInfo(self.h, nv.NVML_CLOCK_SM))
-                try:
-                    r = nv.nvmlDeviceGetCurrentClocksEventReasons(self.h)
-                except Exception:
-                    r = nv.nvmlDeviceGetCurrentClocksThrottleReasons(self.h)
-                for k, bit in names.items():
-                    if r & bit:
-                        self.reasons.add(k)
-            except Exception:
-                pass
-            time.sleep(self.period)
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.error = None
 
     def start(self):
-        if self.nv:
-            self._t = threading.Thread(target=self._run, daemon=True)
-            self._t.start()
+        import subprocess
+        import tempfile
+        self.out = tempfile.TemporaryFile(mode="w+")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception as e:  # noqa: BLE001
+            self.error = repr(e)
 
     def stop(self):
-        if self._t:
-            self._stop.set()
-            self._t.join()
-        return {"sm_mhz": statistics.median(self.samples) if self.samples else None,
-                "sm_max_mhz": self.max_mhz, "reasons": sorted(self.reasons),
-                "samples": len(self.samples)}
+        res = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            res["error"] = self.error
+            return res
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:  # noqa: BLE001
+            self.proc.kill()
+        self.out.seek(0)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+            except ValueError:
+                continue
+            for k, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(k)
+        res.update({"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                    "reasons": sorted(reasons), "samples": len(sm)})
+        return res
 
 
 # ---------------------------------------------------------------------------
@@ -187,7 +193,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     build.build()
-    g = wl.single_large(args.seed)
+    g = wl.single_large(args.seed, n_blocks=args.n_blocks)
     # loop-entry edge count for the byte model comes from the plan's ingestion;
     # count it here from the generator's loops (every header's non-latch preds)
     so, su = g.succ_off, g.succ
@@ -218,6 +224,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     plan.sync()
     clk = clocks.stop()
+    reruns = plan.view().sweeps
     timings = plan.timings()
     plan.profile(False)
     ms = ev0.elapsed_time(ev1)
@@ -249,21 +256,23 @@ def run_ours(args):
                                 "share": round(v[1] / sum(x[1] for x in timings.values()), 4)}
                             for k, v in sorted(timings.items(), key=lambda kv: -kv[1][1])}}
         # ---- end to end through the public API with host buffers
-        e2e_t, h2d, d2h = [], 0, 0
+        e2e_t, h2d, d2h = [float("nan")], 0, 0
+        if args.e2e_steps:
+            e2e_t = []
         for _ in range(args.e2e_steps):
             t0 = time.perf_counter()
             r = _native.analyze(g, device=local)
             e2e_t.append(time.perf_counter() - t0)
             h2d, d2h = r["h2d_bytes"], r["d2h_bytes"]
-        e2e_s = statistics.median(e2e_t)
+        e2e_s = statistics.median(e2e_t) if args.e2e_steps else None
         # ---- CPU oracle on a bounded sample of word columns
-        words = list(range(0, 64, 64 // args.cpu_words))[: args.cpu_words]
-        cpu_val, cpu_s = oracle_sample(g, words)
+        words = list(range(0, 64, 64 // max(1, args.cpu_words)))[: args.cpu_words]
+        cpu_val, cpu_s = oracle_sample(g, words) if words else (None, 0.0)
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n_blocks": g.n_blocks, "n_vars": g.n_vars, "n_words": g.W,
+            "config": {"workload": workload_name(g.n_blocks), "n_blocks": g.n_blocks, "n_vars": g.n_vars, "n_words": g.W,
                        "n_edges": g.n_edges, "n_acc": g.n_acc, "seed": args.seed,
                        "solver": "chunked scan" if plan.view().path == 2 else "sweep",
                        "l2": "no flush: every state plane (512 MiB) is larger than the 126 MB L2",
@@ -272,10 +281,11 @@ def run_ours(args):
             "cpu_baseline": {"value": cpu_val, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "%d of 64 word columns of the same CFG, single-threaded C oracle, %.1f s"
                                        % (len(words), cpu_s), "cpu": cpu_info()},
-            "e2e": {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": units / e2e_s if e2e_s else None, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "seconds_per_step": e2e_s,
                     "path": "ompdart_analyze: host ingestion + copies + solve + copy back"},
             "gpu_launches": launches_per_step * args.steps,
+            "loop_reruns_last_step": reruns,
             "clocks": clk,
         }
     plan.close()
@@ -323,6 +333,8 @@ def main():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-words", type=int, default=8)
+    ap.add_argument("--n-blocks", type=int, default=1 << 20,
+                    help="blocks of the workload (smaller only for profiler captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

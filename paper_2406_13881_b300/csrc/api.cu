@@ -20,7 +20,8 @@ int enqueue_sweep_solver(const DevPlan &p, cudaStream_t s, int n_fin, Prof *pf);
 int enqueue_sweep_edges(const DevPlan &p, cudaStream_t s, int n_fin);
 int scan_supported(const Ingest &g);
 struct ScanState;
-ScanState *scan_create(const Ingest &g, DevPlan &p, int chunk_target, int keep_states, std::string *err);
+ScanState *scan_create(const Ingest &g, const ompdart_cfg *cfg, DevPlan &p, int chunk_target, int keep_states,
+                       std::string *err);
 bool scan_grow_streams(ScanState *st);
 long long scan_h2d_bytes(const ScanState *st);
 int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *pf);
@@ -217,7 +218,7 @@ int ompdart_plan_create(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdar
     chk(d.ant_d = P->dalloc<uint64_t>(NW));
     chk(d.lant = P->dalloc<uint64_t>(g.body_blk.size() * (size_t)W * 2));
   } else {
-    P->scan = scan_create(g, d, o.chunk_target, o.keep_states, &err);
+    P->scan = scan_create(g, cfg, d, o.chunk_target, o.keep_states, &err);
     if (!P->scan) {
       delete P;
       return set_err(OMPDART_E_NOMEM, err);
@@ -244,9 +245,9 @@ int ompdart_plan_run(ompdart_plan *P, void *stream) {
   cudaMemsetAsync(P->dp.status, 0, ST_COUNT * sizeof(int32_t), s);
   Prof *pf = P->prof.on ? &P->prof : nullptr;
   if (pf) pf->collect_pending = true;
-  int n = enqueue_local_summary(P->dp, s, pf);
+  int n = 0;
   if (P->path == 1)
-    n += enqueue_sweep_solver(P->dp, s, P->n_fin, pf);
+    n += enqueue_local_summary(P->dp, s, pf) + enqueue_sweep_solver(P->dp, s, P->n_fin, pf);
   else
     n += enqueue_scan_solver(P->scan, P->dp, s, pf) + enqueue_fill_unreachable(P->dp, s, P->keep_states, pf);
   if (pf) pf->close(s);

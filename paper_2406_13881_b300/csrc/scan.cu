@@ -36,7 +36,9 @@ namespace ompdart {
 namespace {
 
 constexpr int CARRY = -2;      // slot id: the chunk's incoming carry
-constexpr int SH_SLOTS = 16;   // slots per plane kept in shared memory
+constexpr int PREV = -3;       // slot id: the value of the position walked just before
+constexpr int SH_WORDS = 1024; // shared-memory words per warp for slots (8 KiB)
+constexpr int WPC = 4;         // warps per CTA of the chain kernels
 constexpr int MAX_DEPTH = 31;  // loop nesting depth the chain handles
 // bound on loop re-runs per chunk walk: each loop of a reducible CFG needs
 // at most one re-run per entry, so 8 per position is far beyond any valid
@@ -48,12 +50,13 @@ enum ModeKind { M_SUM = 0, M_APPLY = 1, M_LANT = 2 };
 
 struct PosMeta {  // one per position, 64 B
   int32_t blk;
-  int32_t fin_beg, out_beg, acc_beg, srcent_beg, bend_beg;
+  int32_t fin_beg, out_beg, acc_beg, srcent_beg, bend_beg;  // acc_beg: in caller order
   int16_t nfin, nout, nacc, nsrcent, nbend, fslot, bslot, pad0;
   int32_t head_loop;      // loop whose header is this position, else -1
   uint32_t latch_levels;  // bit d: back edge to the header of the level-d loop
   int32_t exit_idx;       // index in exit_blocks, else -1
-  int32_t pad1, pad2, pad3;
+  int32_t pacc_beg;       // first access of the block in position order
+  int32_t pad2, pad3;
 };
 static_assert(sizeof(PosMeta) == 64, "PosMeta layout");
 
@@ -83,8 +86,11 @@ struct ScanDev {
   const LoopMeta *loops;
   const ChunkMeta *chunks;
   const CarrySrc *csrc;
-  const int32_t *fin_slot, *fin_ent;
-  const int32_t *out_slot, *out_pos;
+  const int2 *fin_pk;   // per forward in-edge {source slot or CARRY, loop-entry edge or -1}
+  const int2 *out_pk;   // per backward out-edge {target slot or CARRY, target position}
+  const uint32_t *acc_p;  // accesses in position order
+  uint32_t *rec_p;        // summary records in position order
+  int sh_slots;           // slots per plane held in shared memory
   const int32_t *lat_slot;
   const int32_t *bend_loop;
   const int32_t *srcent;
@@ -197,6 +203,14 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
   for (auto &v : ends)
     std::sort(v.begin(), v.end(), [&](int a, int b) { return g.loop_depth[a] < g.loop_depth[b]; });
 
+  // positions the walks may jump to (a loop body walked again): forward to
+  // the header, backward to the last body position.  Only at other positions
+  // is "the position walked just before" the neighbouring position.
+  std::vector<uint8_t> fwd_target(M, 0), bwd_target(M, 0);
+  for (int l = 0; l < L; ++l) {
+    fwd_target[g.pos[g.loop_head[l]]] = 1;
+    bwd_target[g.loop_end[l] - 1] = 1;
+  }
   fin_slot.assign(g.fin_src.size(), -1);
   out_slot.assign(g.out_dst.size(), -1);
   out_pos.assign(g.out_dst.size(), -1);
@@ -204,6 +218,10 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
   int max_f = 0, max_b = 0;
   // loop containing a block but not another: outermost such
   auto contains = [&](int l, int p) { return p >= g.pos[g.loop_head[l]] && p < g.loop_end[l]; };
+  auto outermost = [&](int l) {
+    while (g.loop_parent[l] >= 0) l = g.loop_parent[l];
+    return l;
+  };
   for (int c = 0; c < C; ++c) {
     const int s = g.chunk_off[c], e = g.chunk_off[c + 1];
     ChunkMeta &cm = chunks[c];
@@ -218,6 +236,7 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
       int a = i, z = -1;
       for (int k = g.out_off[i]; k < g.out_off[i + 1]; ++k) {
         const int pt = g.pos[g.out_dst[k]];
+        if (pt == i + 1 && pt < e && !fwd_target[pt]) continue;  // read from registers
         if (pt >= e) {
           z = std::max(z, e);
         } else if (pt > i) {
@@ -229,8 +248,11 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
             if (err) *err = "retreating edge into a non-header";
             return false;
           }
-          a = std::min(a, pt);
-          z = std::max(z, g.loop_end[l] - 1);
+          // a latch value survives until its loop is re-entered from an
+          // enclosing loop walked again: reserve it over the outermost one
+          const int lo = outermost(l);
+          a = std::min(a, g.pos[g.loop_head[lo]]);
+          z = std::max(z, g.loop_end[lo] - 1);
         }
       }
       (void)b;
@@ -261,6 +283,7 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
       for (int k = g.fin_off[i]; k < g.fin_off[i + 1]; ++k) {
         const int p = g.fin_src[k], pp = g.pos[p];
         if (pp < s) continue;  // crossing edge: read as the carry of chunk c-1
+        if (pp == i - 1 && i < e && !bwd_target[pp]) continue;  // read from registers
         if (pp < i) {
           int lo = pp;
           for (int x = g.inner_loop[p]; x >= 0; x = g.loop_parent[x]) {
@@ -270,9 +293,10 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
           a = std::min(a, lo);
           z = std::max(z, i);
         } else {
-          const int l = head_loop_of_pos[i];
-          a = std::min(a, i);
-          z = std::max(z, g.loop_end[l] - 1);
+          // the header's value, read by its latches, survives re-entries
+          const int lo = outermost(head_loop_of_pos[i]);
+          a = std::min(a, g.pos[g.loop_head[lo]]);
+          z = std::max(z, g.loop_end[lo] - 1);
         }
       }
       (void)b;
@@ -310,7 +334,7 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
     for (int i = s; i < e; ++i) {
       for (int k = g.fin_off[i]; k < g.fin_off[i + 1]; ++k) {
         const int pp = g.pos[g.fin_src[k]];
-        fin_slot[k] = pp < s ? CARRY : fslot[pp];
+        fin_slot[k] = pp < s ? CARRY : (pp == i - 1 && !fwd_target[i]) ? PREV : fslot[pp];
         if (pp >= i) {  // back edge: the source is a latch of loop head_loop_of_pos[i]
           const int l = head_loop_of_pos[i];
           meta[pp].latch_levels |= 1u << (g.loop_depth[l] - 1);
@@ -319,7 +343,7 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
       for (int k = g.out_off[i]; k < g.out_off[i + 1]; ++k) {
         const int pt = g.pos[g.out_dst[k]];
         out_pos[k] = pt;
-        out_slot[k] = pt >= e ? CARRY : bslot[pt];
+        out_slot[k] = pt >= e ? CARRY : (pt == i + 1 && !bwd_target[i]) ? PREV : bslot[pt];
       }
     }
     // carry sources: edges into position e from this chunk
@@ -369,6 +393,87 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
 
 namespace {
 
+constexpr int WIN = 32;        // positions per metadata window
+constexpr int EDGE_CAP = 256;  // edge entries a window holds
+constexpr int REC_CAP = 512;   // access records a window holds
+
+// Per-warp cache of a run of positions: their metadata, their edge entries
+// and their access records (all stored in position order in HBM, so each
+// window is a few coalesced loads instead of dependent loads per position).
+struct Win {
+  PosMeta meta[WIN];
+  int2 edge[EDGE_CAP];    // forward: {slot, loop-entry edge}; backward: {slot, target position}
+  uint32_t rec[REC_CAP];  // summary records
+  int mbase, ws, we, e0, r0, big;
+  uint32_t *acc;          // raw access words (emission only), REC_CAP entries
+};
+
+struct WinRegs {  // warp-uniform copy of the window bounds
+  int mbase = 0, ws = 0, we = 0, e0 = 0, r0 = 0;
+  bool big = false;
+};
+
+// Load the window containing position i: forward [i, i+WIN) clipped to hi,
+// backward (i-WIN, i] clipped to lo; shrunk so its edges and records fit.
+// A single position too large for the buffers is read from HBM directly.
+template <bool FWD, bool ACC>
+__device__ void load_window(Win &w, WinRegs &r, const ScanDev &sd, int i, int lo, int hi, int lane) {
+  const unsigned FULL = 0xffffffffu;
+  const int mbase = FWD ? i : max(i - WIN + 1, lo);
+  const int n = FWD ? min(WIN, hi - i) : (i + 1 - mbase);
+  int eb = 0, ee = 0, rb = 0, re = 0;
+  if (lane < n) {
+    const PosMeta pm = sd.meta[mbase + lane];
+    w.meta[lane] = pm;
+    eb = FWD ? pm.fin_beg : pm.out_beg;
+    ee = eb + (FWD ? pm.nfin : pm.nout);
+    rb = pm.pacc_beg;
+    re = rb + pm.nacc;
+  }
+  const int kcur = FWD ? 0 : n - 1;
+  const int ea = __shfl_sync(FULL, FWD ? eb : ee, kcur);
+  const int ra = __shfl_sync(FULL, FWD ? rb : re, kcur);
+  const bool fits = lane < n && (FWD ? (ee - ea <= EDGE_CAP && re - ra <= REC_CAP)
+                                     : (ea - eb <= EDGE_CAP && ra - rb <= REC_CAP));
+  const unsigned fm = __ballot_sync(FULL, fits);
+  int ws, we;
+  if (FWD) {
+    const int keep = (~fm == 0u) ? 32 : (__ffs(~fm) - 1);
+    ws = i;
+    we = i + keep;
+  } else {
+    const unsigned x = (n == 32) ? fm : (fm << (32 - n));
+    const int keep = (~x == 0u) ? 32 : __clz(~x);
+    ws = i + 1 - keep;
+    we = i + 1;
+  }
+  const bool big = we == ws;
+  if (big) { ws = i; we = i + 1; }
+  const int k0 = ws - mbase, k1 = we - 1 - mbase;
+  const int e0 = __shfl_sync(FULL, eb, k0), e1 = __shfl_sync(FULL, ee, k1);
+  const int r0 = __shfl_sync(FULL, rb, k0), r1 = __shfl_sync(FULL, re, k1);
+  if (!big) {
+    const int2 *src = FWD ? sd.fin_pk : sd.out_pk;
+    for (int j = lane; j < e1 - e0; j += 32) w.edge[j] = src[e0 + j];
+    for (int j = lane; j < r1 - r0; j += 32) {
+      w.rec[j] = sd.rec_p[r0 + j];
+      if (ACC) w.acc[j] = sd.acc_p[r0 + j];
+    }
+  }
+  __syncwarp();
+  r.mbase = mbase; r.ws = ws; r.we = we; r.e0 = e0; r.r0 = r0; r.big = big;
+}
+
+__device__ __forceinline__ int2 win_edge(const Win &w, const WinRegs &r, const int2 *g, int k) {
+  return r.big ? g[k] : w.edge[k - r.e0];
+}
+__device__ __forceinline__ uint32_t win_rec(const Win &w, const WinRegs &r, const ScanDev &sd, int k) {
+  return r.big ? sd.rec_p[k] : w.rec[k - r.r0];
+}
+__device__ __forceinline__ uint32_t win_acc(const Win &w, const WinRegs &r, const ScanDev &sd, int k) {
+  return r.big ? sd.acc_p[k] : w.acc[k - r.r0];
+}
+
 struct Lane {
   int lane, wg, w0;     // w0: first of the lane's two words (global word index)
   uint64_t top0, top1;  // valid-variable masks of the two words
@@ -376,11 +481,12 @@ struct Lane {
 
 template <int NP>
 struct Slots {
-  uint64_t *sh;     // [SH_SLOTS][NP][64]
+  uint64_t *sh;     // [nsh][NP][64]
   uint64_t *spill;  // [extra][NP][64]
+  int nsh;
   __device__ ulonglong2 *at(int slot, int plane, int lane) const {
-    if (slot < SH_SLOTS) return reinterpret_cast<ulonglong2 *>(sh + ((size_t)(slot * NP + plane) * 64) + 2 * lane);
-    return reinterpret_cast<ulonglong2 *>(spill + ((size_t)((slot - SH_SLOTS) * NP + plane) * 64) + 2 * lane);
+    if (slot < nsh) return reinterpret_cast<ulonglong2 *>(sh + ((size_t)(slot * NP + plane) * 64) + 2 * lane);
+    return reinterpret_cast<ulonglong2 *>(spill + ((size_t)((slot - nsh) * NP + plane) * 64) + 2 * lane);
   }
 };
 
@@ -391,89 +497,144 @@ __device__ __forceinline__ void st_word(uint64_t *plane, size_t row, int W, int 
   if (w < W) plane[row * W + w] = v;
 }
 
-// Apply a block's summary records to the lane's two words of each plane.
-//   ANT planes (H, D): local: UE -> 1, else write -> 0; coefficient: both -> 0
+// shared memory per warp (words):
+//   slots [nsh][np][64] | emission scratch 128 | node value [np][64] |
+//   kill sets 128 | window | raw accesses REC_CAP/2 (emitting pass only)
+// each part a multiple of 16 words (128 B): slots and the node value are
+// read and written as 16-byte ulonglong2 and must stay 16-byte aligned
+constexpr size_t WIN_WORDS = ((sizeof(Win) + 127) / 128) * 16;
+__host__ __device__ inline size_t warp_smem_words(int nsh, int np, bool acc) {
+  return (size_t)nsh * np * 64 + 128 + (size_t)np * 64 + 128 + WIN_WORDS + (acc ? REC_CAP / 2 : 0);
+}
+static_assert(WIN_WORDS % 16 == 0 && WIN_WORDS * 8 >= sizeof(Win), "window layout");
+static_assert(alignof(Win) <= 16 && (REC_CAP / 2) % 16 == 0, "window alignment");
+
+struct WarpMem {
+  uint64_t *slots, *hd, *cur, *kill;
+  Win *win;
+};
+template <int NP, bool ACC>
+__device__ __forceinline__ WarpMem carve(uint64_t *smem, int warp_in_cta, int nsh) {
+  uint64_t *b = smem + (size_t)warp_in_cta * warp_smem_words(nsh, NP, ACC);
+  WarpMem m;
+  m.slots = b;
+  m.hd = b + (size_t)nsh * NP * 64;
+  m.cur = m.hd + 128;
+  m.kill = m.cur + NP * 64;
+  m.win = reinterpret_cast<Win *>(m.kill + 128);
+  m.win->acc = ACC ? reinterpret_cast<uint32_t *>(m.kill + 128 + WIN_WORDS) : nullptr;
+  return m;
+}
+
+// Apply a block's summary records to the node value z (two words of each
+// plane per lane), through the warp's shared copy `cur`: lane r takes
+// record r; records of one block are for distinct variables, so only lanes
+// whose records fall in the same word take turns.
+//   liveness (AntH | AntD share the kill "any write", so their union is one
+//   problem): local: read in either space first -> 1, else write -> 0;
+//   coefficient: both -> 0.  LANT: separate H and D planes.
 //   forward planes (stale sets): local: GEN -> 0 (valid), KILL -> 1 (stale);
 //   coefficient: both -> 0.
+// In LANT mode the kills of the block are also ORed into `kill` ([H|D][64]).
 template <int PH, int MODE, int NP>
-__device__ __forceinline__ void apply_records(const DevPlan &p, const PosMeta &m, const Lane &L, uint64_t (&z)[NP][2],
-                                              uint64_t &koh0, uint64_t &koh1, uint64_t &kod0, uint64_t &kod1) {
-  const uint32_t *rec = p.rec + p.acc_off[m.blk];
-  const int na = p.acc_off[m.blk + 1] - p.acc_off[m.blk];
-  for (int r = 0; r < na; ++r) {
-    const uint32_t rc = __ldg(rec + r);
-    if (rc == REC_NONE) continue;
-    const int lw = (int)((rc & 0xFFFFFFu) >> 6) - L.wg * 64;
-    if ((unsigned)lw >= 64u || (lw >> 1) != L.lane) continue;
+__device__ __forceinline__ void apply_records(const ScanDev &sd, const Win &w, const WinRegs &wr, const PosMeta &m,
+                                              const Lane &L, uint64_t (&z)[NP][2], uint64_t *cur, uint64_t *kill) {
+  if (m.nacc == 0) return;
+  const unsigned FULL = 0xffffffffu;
+#pragma unroll
+  for (int pl = 0; pl < NP; ++pl)
+    *reinterpret_cast<ulonglong2 *>(cur + pl * 64 + 2 * L.lane) = make_ulonglong2(z[pl][0], z[pl][1]);
+  __syncwarp();
+  for (int base = 0; base < m.nacc; base += 32) {
+    const int r = base + L.lane;
+    const uint32_t rc = r < m.nacc ? win_rec(w, wr, sd, m.pacc_beg + r) : REC_NONE;
+    int lw = -1;
+    if (rc != REC_NONE) {
+      lw = (int)((rc & 0xFFFFFFu) >> 6) - L.wg * 64;
+      if ((unsigned)lw >= 64u) lw = -1;
+    }
+    const unsigned grp = __match_any_sync(FULL, lw);
+    const int rank = __popc(grp & ((1u << L.lane) - 1u));
+    const int rounds = (int)__reduce_max_sync(FULL, lw >= 0 ? (unsigned)__popc(grp) : 0u);
     const uint64_t bit = 1ull << (rc & 63u);
-    const int j = lw & 1;
-    if (PH == K_ANT) {
-      // planes: SUM: [H local, H coef, D local, D coef]; APPLY/LANT: [H, D]
-      const bool uh = rc & R_UH, ud = rc & R_UD, df = rc & R_DF;
-      if (MODE == M_SUM) {
-        z[0][j] = uh ? (z[0][j] | bit) : df ? (z[0][j] & ~bit) : z[0][j];
-        if (uh || df) z[1][j] &= ~bit;
-        z[2][j] = ud ? (z[2][j] | bit) : df ? (z[2][j] & ~bit) : z[2][j];
-        if (ud || df) z[3][j] &= ~bit;
-      } else {
-        z[0][j] = uh ? (z[0][j] | bit) : df ? (z[0][j] & ~bit) : z[0][j];
-        z[1][j] = ud ? (z[1][j] | bit) : df ? (z[1][j] & ~bit) : z[1][j];
-        if (MODE == M_LANT) {
-          if (rc & R_KH) { if (j) koh1 |= bit; else koh0 |= bit; }
-          if (rc & R_KD) { if (j) kod1 |= bit; else kod0 |= bit; }
+    for (int t = 0; t < rounds; ++t) {
+      if (lw >= 0 && rank == t) {
+        if (PH == K_ANT) {
+          const bool uh = rc & R_UH, ud = rc & R_UD, df = rc & R_DF;
+          if (MODE == M_LANT) {  // [H, D] anticipation, and the kills of the body
+            uint64_t *h = cur + lw, *d = cur + 64 + lw;
+            *h = uh ? (*h | bit) : df ? (*h & ~bit) : *h;
+            *d = ud ? (*d | bit) : df ? (*d & ~bit) : *d;
+            if (rc & R_KH) kill[lw] |= bit;
+            if (rc & R_KD) kill[64 + lw] |= bit;
+          } else {  // Live: a read in either space before any write
+            const bool ue = uh || ud;
+            cur[lw] = ue ? (cur[lw] | bit) : df ? (cur[lw] & ~bit) : cur[lw];
+            if (MODE == M_SUM && (ue || df)) cur[64 + lw] &= ~bit;
+          }
+        } else {
+          const uint32_t GEN = PH == K_D ? R_GD : R_GH, KILL = PH == K_D ? R_KD : R_KH;
+          if (rc & GEN) cur[lw] &= ~bit;
+          else if (rc & KILL) cur[lw] |= bit;
+          if (MODE == M_SUM && (rc & (GEN | KILL))) cur[64 + lw] &= ~bit;
         }
       }
-    } else {
-      const uint32_t GEN = PH == K_D ? R_GD : R_GH, KILL = PH == K_D ? R_KD : R_KH;
-      if (rc & GEN) z[0][j] &= ~bit;
-      else if (rc & KILL) z[0][j] |= bit;
-      if (MODE == M_SUM && (rc & (GEN | KILL))) z[1][j] &= ~bit;
+      __syncwarp();
     }
+  }
+#pragma unroll
+  for (int pl = 0; pl < NP; ++pl) {
+    const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(cur + pl * 64 + 2 * L.lane);
+    z[pl][0] = v.x;
+    z[pl][1] = v.y;
   }
 }
 
 // The H-phase emission for one position (apply mode): per-access flags,
 // in-chunk edge records, exit transfers.
-__device__ void emit_position(const DevPlan &p, const ScanDev &sd, const Lane &L, const PosMeta &m,
-                              const Slots<1> &sl, const uint64_t zin[2], const uint64_t zout[2],
-                              const uint64_t din[2], const uint64_t live[2], uint64_t *hd, int stream,
-                              int &rec_count) {
+__device__ void emit_position(const DevPlan &p, const ScanDev &sd, const Win &w, const WinRegs &wr, const Lane &L,
+                              const PosMeta &m, const Slots<1> &sl, const uint64_t zin[2], const uint64_t zout[2],
+                              const uint64_t din[2], const uint64_t live[2], const uint64_t prev[2], uint64_t *hd,
+                              int stream, int &rec_count) {
   const int W = p.W, lane = L.lane;
   // ---- access flags: replay the block from its entry states
-  hd[2 * lane] = ~zin[0] & L.top0;
-  hd[2 * lane + 1] = ~zin[1] & L.top1;
-  hd[64 + 2 * lane] = din[0];
-  hd[64 + 2 * lane + 1] = din[1];
-  __syncwarp();
-  const int a0 = p.acc_off[m.blk], a1 = p.acc_off[m.blk + 1];
-  for (int j = a0 + lane; j < a1; j += 32) {
-    const uint32_t a = p.acc[j];
-    const int v = acc_var(a), lw = (v >> 6) - L.wg * 64;
-    if ((unsigned)lw >= 64u) continue;
-    const uint64_t bit = 1ull << (v & 63);
-    bool h = (hd[lw] & bit) != 0, d = (hd[64 + lw] & bit) != 0;
-    uint8_t flag = 0;
-    for (int q = a0; q <= j; ++q) {
-      const uint32_t x = p.acc[q];
-      if (acc_var(x) != v) continue;
-      const int kind = acc_kind(x), dev = acc_space(x);
-      if (kind & 1) {
-        if (dev && !d) { d = true; if (q == j) flag = 1; }
-        if (!dev && !h) { h = true; if (q == j) flag = 2; }
+  if (m.nacc) {
+    hd[2 * lane] = ~zin[0] & L.top0;
+    hd[2 * lane + 1] = ~zin[1] & L.top1;
+    hd[64 + 2 * lane] = din[0];
+    hd[64 + 2 * lane + 1] = din[1];
+    __syncwarp();
+    const int a0 = m.pacc_beg, na = m.nacc;
+    for (int j = lane; j < na; j += 32) {
+      const uint32_t a = win_acc(w, wr, sd, a0 + j);
+      const int v = acc_var(a), lw = (v >> 6) - L.wg * 64;
+      if ((unsigned)lw >= 64u) continue;
+      const uint64_t bit = 1ull << (v & 63);
+      bool h = (hd[lw] & bit) != 0, d = (hd[64 + lw] & bit) != 0;
+      uint8_t flag = 0;
+      for (int q = 0; q <= j; ++q) {
+        const uint32_t x = win_acc(w, wr, sd, a0 + q);
+        if (acc_var(x) != v) continue;
+        const int kind = acc_kind(x), dev = acc_space(x);
+        if (kind & 1) {
+          if (dev && !d) { d = true; if (q == j) flag = 1; }
+          if (!dev && !h) { h = true; if (q == j) flag = 2; }
+        }
+        if (kind & 2) { if (dev) { d = true; h = false; } else { h = true; d = false; } }
       }
-      if (kind & 2) { if (dev) { d = true; h = false; } else { h = true; d = false; } }
+      p.acc_flag[m.acc_beg + j] = flag;
     }
-    p.acc_flag[j] = flag;
+    __syncwarp();
   }
-  __syncwarp();
   // ---- edge transfers on in-chunk in-edges
   const uint64_t c0 = live[0] & ~din[0], c1 = live[1] & ~din[1];
   for (int q = 0; q < m.nfin; ++q) {
     const int k = m.fin_beg + q;
-    const int slot = sd.fin_slot[k];
+    const int2 fe = win_edge(w, wr, sd.fin_pk, k);
+    const int slot = fe.x;
     if (slot == CARRY) continue;
-    const int ent = sd.fin_ent[k];
-    const ulonglong2 zs = *sl.at(slot, 0, lane);
+    const int ent = fe.y;
+    const ulonglong2 zs = slot == PREV ? make_ulonglong2(prev[0], prev[1]) : *sl.at(slot, 0, lane);
     uint64_t to0 = 0, to1 = 0, fr0, fr1;
     uint64_t e0 = zs.x, e1 = zs.y;
     if (ent >= 0) {
@@ -507,7 +668,7 @@ __device__ void emit_position(const DevPlan &p, const ScanDev &sd, const Lane &L
   }
   // ---- region exit
   if (m.exit_idx >= 0) {
-    st_word(p.from_exit, m.exit_idx, W, L.w0, p.exit_live[min(L.w0, W - 1)] & zout[0] & L.top0);
+    if (L.w0 < W) st_word(p.from_exit, m.exit_idx, W, L.w0, p.exit_live[L.w0] & zout[0] & L.top0);
     if (L.w0 + 1 < W) st_word(p.from_exit, m.exit_idx, W, L.w0 + 1, p.exit_live[L.w0 + 1] & zout[1] & L.top1);
   }
 }
@@ -518,6 +679,7 @@ __device__ void emit_position(const DevPlan &p, const ScanDev &sd, const Lane &L
 template <int PH, int MODE>
 __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan p, ScanDev sd) {
   constexpr int NP = MODE == M_SUM ? 2 : 1;
+  constexpr bool ACC = MODE == M_APPLY && PH == K_H;
   extern __shared__ __align__(16) uint64_t smem[];
   const int warp_in_cta = threadIdx.x >> 5;
   const int gw = blockIdx.x * (blockDim.x >> 5) + warp_in_cta;
@@ -530,9 +692,12 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan p, ScanDev sd) {
   L.w0 = wg * 64 + 2 * L.lane;
   L.top0 = L.w0 < W ? p.top[L.w0] : 0;
   L.top1 = L.w0 + 1 < W ? p.top[L.w0 + 1] : 0;
-  uint64_t *wsm = smem + (size_t)warp_in_cta * (SH_SLOTS * NP * 64 + 128);
-  Slots<NP> sl{wsm, sd.spill + (size_t)gw * sd.spill_stride};
-  uint64_t *hd = wsm + SH_SLOTS * NP * 64;
+  const WarpMem wm = carve<NP, ACC>(smem, warp_in_cta, sd.sh_slots);
+  Slots<NP> sl{wm.slots, sd.spill + (size_t)gw * sd.spill_stride, sd.sh_slots};
+  uint64_t *hd = wm.hd;
+  Win &w = *wm.win;
+  WinRegs wr;
+  wr.ws = wr.we = 0;
   const ChunkMeta cm = sd.chunks[c];
   const uint64_t *ec = PH == K_D ? p.ec_d : p.ec_h;
   // carry into this chunk, per plane
@@ -552,24 +717,51 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan p, ScanDev sd) {
   int depth = 0;
   uint32_t dirty = 0;
   int reruns = 0;
-  uint64_t dummy = 0;
-  uint64_t z[NP][2], zo[NP][2];
+  uint64_t z[NP][2], zo[NP][2], pv[NP][2] = {};
+  int top_pend = -1;  // end of the innermost open loop (warp-uniform)
   uint64_t din[2] = {0, 0}, lv[2] = {0, 0};
+  uint64_t pdin[2] = {0, 0}, plv[2] = {0, 0};
+  int ppos = -1;  // position whose dense rows are prefetched in pdin/plv
+  int hwm = cm.s - 1;  // highest position walked so far
   int i = cm.s;
   while (i < cm.e) {
-    const PosMeta m = sd.meta[i];
+    if (i < wr.ws || i >= wr.we) load_window<true, ACC>(w, wr, sd, i, cm.s, cm.e, L.lane);
+    const PosMeta m = w.meta[i - wr.mbase];
+    if (PH == K_H) {
+      // dense rows of this position (prefetched one position ahead)
+      if (ppos == i) {
+        lv[0] = plv[0]; lv[1] = plv[1]; din[0] = pdin[0]; din[1] = pdin[1];
+      } else {
+        lv[0] = ld_word(p.live, m.blk, W, L.w0); lv[1] = ld_word(p.live, m.blk, W, L.w0 + 1);
+        din[0] = ld_word(p.d_in, m.blk, W, L.w0); din[1] = ld_word(p.d_in, m.blk, W, L.w0 + 1);
+      }
+      ppos = -1;
+      if (i + 1 < wr.we) {
+        const int nb = w.meta[i + 1 - wr.mbase].blk;
+        plv[0] = ld_word(p.live, nb, W, L.w0); plv[1] = ld_word(p.live, nb, W, L.w0 + 1);
+        pdin[0] = ld_word(p.d_in, nb, W, L.w0); pdin[1] = ld_word(p.d_in, nb, W, L.w0 + 1);
+        ppos = i + 1;
+      }
+    }
     if (m.head_loop >= 0) {
       const LoopMeta lm = sd.loops[m.head_loop];
-      if (lm.depth > depth) {  // fresh entry: latch values start from nothing
+      if (lm.depth > depth) {  // entering the loop from outside
         st_loop[depth] = m.head_loop;
         st_rec[depth] = rec_count;
         dirty &= ~(1u << depth);
         ++depth;
-        for (int q = 0; q < lm.lat_cnt; ++q) {
-          const int s = sd.lat_slot[lm.lat_beg + q];
-          for (int pl = 0; pl < NP; ++pl) *sl.at(s, pl, L.lane) = make_ulonglong2(0ull, 0ull);
+        top_pend = lm.pend;
+        // first visit in this walk: the back edges carry nothing yet.  A
+        // re-entry (an enclosing body walked again) keeps the latch values
+        // of the previous visit: they are below the new fixed point and the
+        // header = entry | old latches is then exact in one walk.
+        if (i > hwm) {
+          for (int q = 0; q < lm.lat_cnt; ++q) {
+            const int s = sd.lat_slot[lm.lat_beg + q];
+            for (int pl = 0; pl < NP; ++pl) *sl.at(s, pl, L.lane) = make_ulonglong2(0ull, 0ull);
+          }
+          __syncwarp();
         }
-        __syncwarp();
       }
     }
     // ---- value entering the block
@@ -580,14 +772,16 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan p, ScanDev sd) {
       for (int pl = 0; pl < NP; ++pl) { z[pl][0] = cin[pl][0]; z[pl][1] = cin[pl][1]; }
     }
     for (int q = 0; q < m.nfin; ++q) {
-      const int k = m.fin_beg + q;
-      const int slot = sd.fin_slot[k];
+      const int2 fe = win_edge(w, wr, sd.fin_pk, m.fin_beg + q);
+      const int slot = fe.x;
       if (slot == CARRY) continue;  // already in z via cin
-      uint64_t m0 = ~0ull, m1 = ~0ull;
-      if (PH != K_HP) {
-        const int ent = sd.fin_ent[k];
-        if (ent >= 0) { m0 = ~ld_word(ec, ent, W, L.w0); m1 = ~ld_word(ec, ent, W, L.w0 + 1); }
+      if (slot == PREV) {           // the position walked just before
+#pragma unroll
+        for (int pl = 0; pl < NP; ++pl) { z[pl][0] |= pv[pl][0]; z[pl][1] |= pv[pl][1]; }
+        continue;
       }
+      uint64_t m0 = ~0ull, m1 = ~0ull;
+      if (PH != K_HP && fe.y >= 0) { m0 = ~ld_word(ec, fe.y, W, L.w0); m1 = ~ld_word(ec, fe.y, W, L.w0 + 1); }
 #pragma unroll
       for (int pl = 0; pl < NP; ++pl) {
         const ulonglong2 v = *sl.at(slot, pl, L.lane);
@@ -603,16 +797,13 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan p, ScanDev sd) {
       for (int pl = 0; pl < NP; ++pl) *sl.at(hs, pl, L.lane) = make_ulonglong2(z[pl][0], z[pl][1]);
     }
     if (PH == K_H) {  // live and stale on the device -> resolved toward the host
-      const size_t row = (size_t)m.blk;
-      lv[0] = ld_word(p.live, row, W, L.w0); lv[1] = ld_word(p.live, row, W, L.w0 + 1);
-      din[0] = ld_word(p.d_in, row, W, L.w0); din[1] = ld_word(p.d_in, row, W, L.w0 + 1);
       const uint64_t b0 = ~(lv[0] & ~din[0]), b1 = ~(lv[1] & ~din[1]);
 #pragma unroll
       for (int pl = 0; pl < NP; ++pl) { z[pl][0] &= b0; z[pl][1] &= b1; }
     }
 #pragma unroll
     for (int pl = 0; pl < NP; ++pl) { zo[pl][0] = z[pl][0]; zo[pl][1] = z[pl][1]; }
-    apply_records<PH, MODE, NP>(p, m, L, zo, dummy, dummy, dummy, dummy);
+    apply_records<PH, MODE, NP>(sd, w, wr, m, L, zo, wm.cur, wm.kill);
     // ---- a latch whose value adds to an open loop's header marks it dirty
     if (m.latch_levels) {
       uint32_t lvmask = m.latch_levels;
@@ -634,6 +825,12 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan p, ScanDev sd) {
 #pragma unroll
       for (int pl = 0; pl < NP; ++pl) *sl.at(m.fslot, pl, L.lane) = make_ulonglong2(zo[pl][0], zo[pl][1]);
     }
+    uint64_t pvo[NP][2];
+#pragma unroll
+    for (int pl = 0; pl < NP; ++pl) {
+      pvo[pl][0] = pv[pl][0]; pvo[pl][1] = pv[pl][1];
+      pv[pl][0] = zo[pl][0]; pv[pl][1] = zo[pl][1];
+    }
     // ---- outputs
     if (MODE == M_APPLY) {
       const size_t row = (size_t)m.blk;
@@ -653,7 +850,8 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan p, ScanDev sd) {
           st_word(p.h_out, row, W, L.w0 + 1, ~zo[0][1] & L.top1);
         }
         __syncwarp();
-        emit_position(p, sd, L, m, *reinterpret_cast<Slots<1> *>(&sl), z[0], zo[0], din, lv, hd, stream, rec_count);
+        emit_position(p, sd, w, wr, L, m, *reinterpret_cast<Slots<1> *>(&sl), z[0], zo[0], din, lv, pvo[0], hd,
+                      stream, rec_count);
       }
       if ((PH == K_HP || PH == K_D) && m.nsrcent) {
         uint64_t *dst = PH == K_HP ? sd.hp_src : sd.d_src;
@@ -667,18 +865,18 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan p, ScanDev sd) {
     __syncwarp();
     // ---- close loops ending here; walk a body again if its header grew
     bool jumped = false;
-    while (depth > 0) {
-      const LoopMeta lt = sd.loops[st_loop[depth - 1]];
-      if (lt.pend - 1 != i) break;
+    while (depth > 0 && top_pend - 1 == i) {
       if (dirty & (1u << (depth - 1))) {
         dirty &= ~(1u << (depth - 1));
         rec_count = st_rec[depth - 1];
-        i = lt.ph;
+        i = sd.loops[st_loop[depth - 1]].ph;
         jumped = true;
         break;
       }
       --depth;
+      top_pend = depth > 0 ? sd.loops[st_loop[depth - 1]].pend : -1;
     }
+    hwm = max(hwm, i);
     if (jumped) {
       if (++reruns > rerun_cap(cm.e - cm.s)) {
         if (L.lane == 0) atomicExch(&p.status[ST_ERROR], ERR_NOCONVERGE);
@@ -688,6 +886,7 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan p, ScanDev sd) {
       ++i;
     }
   }
+  if (L.lane == 0 && reruns) atomicAdd(&p.status[ST_SWEEPS], reruns);
   // ---- what leaves the chunk: the carry into the next chunk's first block
   if (MODE == M_SUM || (MODE == M_APPLY && PH == K_H)) {
     uint64_t co[NP][2];
@@ -724,11 +923,17 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan p, ScanDev sd) {
 // backward chain (anticipation; loop-restricted anticipation for the masks)
 // --------------------------------------------------------------------------------------
 template <int MODE>
-__device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, const Slots<(MODE == M_SUM ? 4 : 2)> &sl,
-                          int s, int e, int base_depth, int lo_pos, bool use_carry,
-                          const uint64_t (&cin)[(MODE == M_SUM ? 4 : 2)][2], uint64_t (&zlast)[(MODE == M_SUM ? 4 : 2)][2],
-                          uint64_t &koh0, uint64_t &koh1, uint64_t &kod0, uint64_t &kod1) {
-  constexpr int NP = MODE == M_SUM ? 4 : 2;
+struct BwdPlanes {  // SUM: [Live local, Live coefficient]; APPLY: [Live]; LANT: [H, D]
+  static constexpr int NP = MODE == M_APPLY ? 1 : 2;
+};
+
+template <int MODE>
+__device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, const WarpMem &wm,
+                          const Slots<BwdPlanes<MODE>::NP> &sl, int s, int e, int base_depth, int lo_pos,
+                          bool use_carry, const uint64_t (&cin)[BwdPlanes<MODE>::NP][2],
+                          uint64_t (&zlast)[BwdPlanes<MODE>::NP][2]) {
+  Win &w = *wm.win;
+  constexpr int NP = BwdPlanes<MODE>::NP;
   const int W = p.W;
   const uint64_t xl0 = L.w0 < W ? p.exit_live[L.w0] : 0, xl1 = L.w0 + 1 < W ? p.exit_live[L.w0 + 1] : 0;
   int st_loop[MAX_DEPTH + 1];
@@ -736,9 +941,15 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
   uint32_t dirty = 0;
   int reruns = 0;
   uint64_t z[NP][2];
+  WinRegs wr;
+  wr.ws = wr.we = 0;
+  int lwm = e;  // lowest position walked so far
+  int top_ph = -1;  // header of the innermost open loop (warp-uniform)
+  uint64_t pv[NP][2] = {};
   int i = e - 1;
   while (i >= s) {
-    const PosMeta m = sd.meta[i];
+    if (i < wr.ws || i >= wr.we) load_window<false, false>(w, wr, sd, i, s, e, L.lane);
+    const PosMeta m = w.meta[i - wr.mbase];
     // enter loops whose range ends here (outer first)
     for (int q = 0; q < m.nbend; ++q) {
       const int l = sd.bend_loop[m.bend_beg + q];
@@ -747,10 +958,15 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
       st_loop[lm.depth - 1] = l;
       dirty &= ~(1u << (lm.depth - 1));
       depth = lm.depth;
-      const int hs = sd.meta[lm.ph].bslot;
-      if (hs >= 0)
-        for (int pl = 0; pl < NP; ++pl) *sl.at(hs, pl, L.lane) = make_ulonglong2(0ull, 0ull);
-      __syncwarp();
+      top_ph = lm.ph;
+      // first visit: the header's value, read by the latches, starts from
+      // nothing; a re-entry keeps the previous visit's value
+      if (i < lwm) {
+        const int hs = sd.meta[lm.ph].bslot;
+        if (hs >= 0)
+          for (int pl = 0; pl < NP; ++pl) *sl.at(hs, pl, L.lane) = make_ulonglong2(0ull, 0ull);
+        __syncwarp();
+      }
     }
 #pragma unroll
     for (int pl = 0; pl < NP; ++pl) z[pl][0] = z[pl][1] = 0;
@@ -759,11 +975,15 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
       z[0][1] = xl1;
     }
     for (int q = 0; q < m.nout; ++q) {
-      const int k = m.out_beg + q;
-      const int slot = sd.out_slot[k];
+      const int2 oe = win_edge(w, wr, sd.out_pk, m.out_beg + q);
+      const int slot = oe.x;
       if (MODE == M_LANT) {
-        const int pt = sd.out_pos[k];
-        if (pt <= lo_pos || pt >= e) continue;  // back to the loop header or out of the body
+        if (oe.y <= lo_pos || oe.y >= e) continue;  // back to the loop header or out of the body
+      }
+      if (slot == PREV) {  // the position walked just before
+#pragma unroll
+        for (int pl = 0; pl < NP; ++pl) { z[pl][0] |= pv[pl][0]; z[pl][1] |= pv[pl][1]; }
+        continue;
       }
       if (slot == CARRY) {
         if (use_carry) {
@@ -779,10 +999,10 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
         z[pl][1] |= v.y;
       }
     }
-    apply_records<K_ANT, MODE, NP>(p, m, L, z, koh0, koh1, kod0, kod1);
+    apply_records<K_ANT, MODE, NP>(sd, w, wr, m, L, z, wm.cur, wm.kill);
     if (m.bslot >= 0) {
       bool changed = false;
-      const bool is_top_header = depth > base_depth && sd.loops[st_loop[depth - 1]].ph == i;
+      const bool is_top_header = depth > base_depth && top_ph == i;
 #pragma unroll
       for (int pl = 0; pl < NP; ++pl) {
         ulonglong2 *ptr = sl.at(m.bslot, pl, L.lane);
@@ -795,24 +1015,27 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
       if (is_top_header && __any_sync(0xffffffffu, changed)) dirty |= 1u << (depth - 1);
     }
     if (MODE == M_APPLY) {
-      st_word(p.live, m.blk, W, L.w0, z[0][0] | z[1][0]);
-      st_word(p.live, m.blk, W, L.w0 + 1, z[0][1] | z[1][1]);
+      st_word(p.live, m.blk, W, L.w0, z[0][0]);
+      st_word(p.live, m.blk, W, L.w0 + 1, z[0][1]);
     }
     __syncwarp();
 #pragma unroll
-    for (int pl = 0; pl < NP; ++pl) { zlast[pl][0] = z[pl][0]; zlast[pl][1] = z[pl][1]; }
+    for (int pl = 0; pl < NP; ++pl) {
+      zlast[pl][0] = pv[pl][0] = z[pl][0];
+      zlast[pl][1] = pv[pl][1] = z[pl][1];
+    }
     bool jumped = false;
-    while (depth > base_depth) {
-      const LoopMeta lt = sd.loops[st_loop[depth - 1]];
-      if (lt.ph != i) break;
+    while (depth > base_depth && top_ph == i) {
       if (dirty & (1u << (depth - 1))) {
         dirty &= ~(1u << (depth - 1));
-        i = lt.pend - 1;
+        i = sd.loops[st_loop[depth - 1]].pend - 1;
         jumped = true;
         break;
       }
       --depth;
+      top_ph = depth > base_depth ? sd.loops[st_loop[depth - 1]].ph : -1;
     }
+    lwm = min(lwm, i);
     if (jumped) {
       if (++reruns > rerun_cap(e - s)) {
         if (L.lane == 0) atomicExch(&p.status[ST_ERROR], ERR_NOCONVERGE);
@@ -822,11 +1045,12 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
       --i;
     }
   }
+  if (L.lane == 0 && reruns) atomicAdd(&p.status[ST_SWEEPS], reruns);
 }
 
 template <int MODE>
 __global__ void __launch_bounds__(128) k_bwd_chain(DevPlan p, ScanDev sd) {
-  constexpr int NP = MODE == M_SUM ? 4 : 2;
+  constexpr int NP = BwdPlanes<MODE>::NP;
   extern __shared__ __align__(16) uint64_t smem[];
   const int warp_in_cta = threadIdx.x >> 5;
   const int gw = blockIdx.x * (blockDim.x >> 5) + warp_in_cta;
@@ -839,74 +1063,96 @@ __global__ void __launch_bounds__(128) k_bwd_chain(DevPlan p, ScanDev sd) {
   L.w0 = wg * 64 + 2 * L.lane;
   L.top0 = L.w0 < W ? p.top[L.w0] : 0;
   L.top1 = L.w0 + 1 < W ? p.top[L.w0 + 1] : 0;
-  uint64_t *wsm = smem + (size_t)warp_in_cta * (SH_SLOTS * NP * 64);
-  Slots<NP> sl{wsm, sd.spill + (size_t)gw * sd.spill_stride};
+  const WarpMem wm = carve<NP, false>(smem, warp_in_cta, sd.sh_slots);
+  Slots<NP> sl{wm.slots, sd.spill + (size_t)gw * sd.spill_stride, sd.sh_slots};
   const ChunkMeta cm = sd.chunks[c];
   uint64_t cin[NP][2], zl[NP][2];
-  uint64_t koh0 = 0, koh1 = 0, kod0 = 0, kod1 = 0;
   if (MODE == M_LANT) {
 #pragma unroll
     for (int pl = 0; pl < NP; ++pl) cin[pl][0] = cin[pl][1] = 0;
     for (int l = cm.loop_beg; l < cm.loop_end; ++l) {
       const LoopMeta lm = sd.loops[l];
-      koh0 = koh1 = kod0 = kod1 = 0;
-      bwd_range<MODE>(p, sd, L, sl, lm.ph, lm.pend, lm.depth, lm.ph, false, cin, zl, koh0, koh1, kod0, kod1);
-      st_word(p.mask_h, l, W, L.w0, zl[0][0] & ~koh0 & L.top0);
-      st_word(p.mask_h, l, W, L.w0 + 1, zl[0][1] & ~koh1 & L.top1);
-      st_word(p.mask_d, l, W, L.w0, zl[1][0] & ~kod0 & L.top0);
-      st_word(p.mask_d, l, W, L.w0 + 1, zl[1][1] & ~kod1 & L.top1);
+      *reinterpret_cast<ulonglong2 *>(wm.kill + 2 * L.lane) = make_ulonglong2(0ull, 0ull);
+      *reinterpret_cast<ulonglong2 *>(wm.kill + 64 + 2 * L.lane) = make_ulonglong2(0ull, 0ull);
+      __syncwarp();
+      bwd_range<MODE>(p, sd, L, wm, sl, lm.ph, lm.pend, lm.depth, lm.ph, false, cin, zl);
+      const ulonglong2 kh = *reinterpret_cast<const ulonglong2 *>(wm.kill + 2 * L.lane);
+      const ulonglong2 kd = *reinterpret_cast<const ulonglong2 *>(wm.kill + 64 + 2 * L.lane);
+      st_word(p.mask_h, l, W, L.w0, zl[0][0] & ~kh.x & L.top0);
+      st_word(p.mask_h, l, W, L.w0 + 1, zl[0][1] & ~kh.y & L.top1);
+      st_word(p.mask_d, l, W, L.w0, zl[1][0] & ~kd.x & L.top0);
+      st_word(p.mask_d, l, W, L.w0 + 1, zl[1][1] & ~kd.y & L.top1);
+      __syncwarp();
     }
     return;
   }
-  // carry: anticipation entering the next chunk's first block
+  // carry: liveness entering the next chunk's first block
   if (MODE == M_SUM) {
     cin[0][0] = cin[0][1] = 0;
-    cin[1][0] = L.top0; cin[1][1] = L.top1;
-    cin[2][0] = cin[2][1] = 0;
-    cin[3][0] = L.top0; cin[3][1] = L.top1;
+    cin[1][0] = L.top0;
+    cin[1][1] = L.top1;
   } else {
-    const size_t CW = (size_t)sd.C;
     cin[0][0] = ld_word(sd.carry, c, W, L.w0);
     cin[0][1] = ld_word(sd.carry, c, W, L.w0 + 1);
-    cin[1][0] = ld_word(sd.carry + CW * W, c, W, L.w0);
-    cin[1][1] = ld_word(sd.carry + CW * W, c, W, L.w0 + 1);
   }
-  bwd_range<MODE>(p, sd, L, sl, cm.s, cm.e, 0, -1, true, cin, zl, koh0, koh1, kod0, kod1);
+  bwd_range<MODE>(p, sd, L, wm, sl, cm.s, cm.e, 0, -1, true, cin, zl);
   if (MODE == M_SUM) {
-    const size_t CW = (size_t)sd.C * W;
     st_word(sd.gsum, c, W, L.w0, zl[0][0]);
     st_word(sd.gsum, c, W, L.w0 + 1, zl[0][1]);
     st_word(sd.psum, c, W, L.w0, zl[1][0]);
     st_word(sd.psum, c, W, L.w0 + 1, zl[1][1]);
-    st_word(sd.gsum + CW, c, W, L.w0, zl[2][0]);
-    st_word(sd.gsum + CW, c, W, L.w0 + 1, zl[2][1]);
-    st_word(sd.psum + CW, c, W, L.w0, zl[3][0]);
-    st_word(sd.psum + CW, c, W, L.w0 + 1, zl[3][1]);
+  }
+}
+
+// local summary records in position order (one thread per position)
+__global__ void k_local_summary_pos(ScanDev sd, int M) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+    const int a0 = sd.meta[i].pacc_beg;
+    const int a1 = a0 + sd.meta[i].nacc;
+    for (int j = a0; j < a1; ++j) {
+      // a lone thread walks the block as lane 0 of a one-lane "warp"
+      summarize_one(sd.acc_p, sd.rec_p, a0, a1, j);
+    }
   }
 }
 
 // --------------------------------------------------------------------------------------
 // scan of the chunk maps: carry[c] for every chunk (one thread per word and plane)
 // --------------------------------------------------------------------------------------
-__global__ void k_scan_carry(ScanDev sd, int W, int planes, int backward, const uint64_t *init0,
-                             const uint64_t *init1) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= planes * W) return;
-  const int pl = t / W, w = t % W;
-  const size_t off = (size_t)pl * sd.C * W;
-  const uint64_t *G = sd.gsum + off, *P = sd.psum + off;
-  uint64_t *car = sd.carry + off;
-  uint64_t x = init0 ? (pl == 0 ? init0[w] : init1[w]) : 0ull;
-  if (!backward) {
-    for (int c = 0; c < sd.C; ++c) {
-      car[(size_t)c * W + w] = x;
-      x = G[(size_t)c * W + w] | (x & P[(size_t)c * W + w]);
+// One CTA per word column: thread t composes the maps of a contiguous run
+// of chunks, thread 0 scans the runs' maps, then every thread walks its run
+// again to write each chunk's carry.  Map composition: first (g1, p1), then
+// (g2, p2) gives (g2 | (g1 & p2), p1 & p2).
+__global__ void __launch_bounds__(256) k_scan_carry(ScanDev sd, int W, int backward, const uint64_t *init) {
+  __shared__ uint64_t sg[256], sp[256];
+  const int w = blockIdx.x, t = threadIdx.x, T = blockDim.x;
+  const int C = sd.C, per = (C + T - 1) / T;
+  const int b = t * per, e = min(C, b + per);
+  auto chunk = [&](int k) { return backward ? C - 1 - k : k; };  // k-th chunk in walk order
+  uint64_t g = 0, pp = ~0ull;
+  for (int k = b; k < e; ++k) {
+    const int c = chunk(k);
+    const uint64_t gc = sd.gsum[(size_t)c * W + w], pc = sd.psum[(size_t)c * W + w];
+    g = gc | (g & pc);
+    pp &= pc;
+  }
+  sg[t] = g;
+  sp[t] = pp;
+  __syncthreads();
+  if (t == 0) {
+    uint64_t x = init ? init[w] : 0ull;  // carry entering run 0
+    for (int r = 0; r < T; ++r) {
+      const uint64_t gr = sg[r], pr = sp[r];
+      sg[r] = x;  // carry entering run r
+      x = gr | (x & pr);
     }
-  } else {
-    for (int c = sd.C - 1; c >= 0; --c) {
-      car[(size_t)c * W + w] = x;
-      x = G[(size_t)c * W + w] | (x & P[(size_t)c * W + w]);
-    }
+  }
+  __syncthreads();
+  uint64_t x = sg[t];
+  for (int k = b; k < e; ++k) {
+    const int c = chunk(k);
+    sd.carry[(size_t)c * W + w] = x;
+    x = sd.gsum[(size_t)c * W + w] | (x & sd.psum[(size_t)c * W + w]);
   }
 }
 
@@ -1059,7 +1305,8 @@ static bool scan_set_streams(ScanState *st) {
   return true;
 }
 
-ScanState *scan_create(const Ingest &g, DevPlan &p, int chunk_target, int keep_states, std::string *err) {
+ScanState *scan_create(const Ingest &g, const ompdart_cfg *cfg, DevPlan &p, int chunk_target, int keep_states,
+                       std::string *err) {
   ScanState *st = new ScanState();
   std::vector<PosMeta> meta;
   std::vector<LoopMeta> loops;
@@ -1072,16 +1319,24 @@ ScanState *scan_create(const Ingest &g, DevPlan &p, int chunk_target, int keep_s
     delete st;
     return nullptr;
   }
-  std::vector<int32_t> acc_off_h(g.N + 1);
-  if (cudaMemcpy(acc_off_h.data(), p.acc_off, sizeof(int32_t) * (g.N + 1), cudaMemcpyDeviceToHost) != cudaSuccess) {
-    if (err) *err = "copy of access offsets failed";
-    delete st;
-    return nullptr;
-  }
+  // accesses in position order, and each position's first access there
+  std::vector<uint32_t> acc_p;
+  acc_p.reserve(g.A);
   for (int i = 0; i < g.M; ++i) {
-    meta[i].acc_beg = acc_off_h[meta[i].blk];
-    meta[i].nacc = (int16_t)std::min(32767, acc_off_h[meta[i].blk + 1] - acc_off_h[meta[i].blk]);
+    const int b = meta[i].blk, a0 = cfg->acc_off[b], a1 = cfg->acc_off[b + 1];
+    if (a1 - a0 > 32767) {
+      if (err) *err = "a block with more than 32767 accesses";
+      delete st;
+      return nullptr;
+    }
+    meta[i].acc_beg = a0;
+    meta[i].nacc = (int16_t)(a1 - a0);
+    meta[i].pacc_beg = (int32_t)acc_p.size();
+    acc_p.insert(acc_p.end(), cfg->acc + a0, cfg->acc + a1);
   }
+  std::vector<int2> fin_pk(fin_slot.size()), out_pk(out_slot.size());
+  for (size_t k = 0; k < fin_pk.size(); ++k) fin_pk[k] = make_int2(fin_slot[k], g.fin_ent[k]);
+  for (size_t k = 0; k < out_pk.size(); ++k) out_pk[k] = make_int2(out_slot[k], out_pos[k]);
   const int W = p.W, C = st->C, G = (W + 63) / 64;
   st->G = G;
   ScanDev &sd = st->sd;
@@ -1096,17 +1351,15 @@ ScanState *scan_create(const Ingest &g, DevPlan &p, int chunk_target, int keep_s
   chk(sd.loops = st->up(loops));
   chk(sd.chunks = st->up(chunks));
   chk(sd.csrc = st->up(csrc));
-  chk(sd.fin_slot = st->up(fin_slot));
-  std::vector<int32_t> fin_ent(g.fin_ent.begin(), g.fin_ent.end());
-  chk(sd.fin_ent = st->up(fin_ent));
-  chk(sd.out_slot = st->up(out_slot));
-  chk(sd.out_pos = st->up(out_pos));
+  chk(sd.fin_pk = st->up(fin_pk));
+  chk(sd.out_pk = st->up(out_pk));
+  chk(sd.acc_p = st->up(acc_p));
+  chk(sd.rec_p = st->alloc<uint32_t>(acc_p.size()));
   chk(sd.lat_slot = st->up(lat_slot));
   chk(sd.bend_loop = st->up(bend_loop));
   chk(sd.srcent = st->up(srcent));
   const int max_slots = std::max(st->fslots, st->bslots);
-  const int extra = std::max(0, max_slots - SH_SLOTS);
-  sd.spill_stride = extra * 4 * 64;  // room for up to 4 planes
+  sd.spill_stride = max_slots * 4 * 64;  // worst case: every slot of 4 planes spilled
   chk(sd.spill = st->alloc<uint64_t>((size_t)std::max(1, sd.spill_stride) * C * G));
   chk(sd.gsum = st->alloc<uint64_t>((size_t)2 * C * W));
   chk(sd.psum = st->alloc<uint64_t>((size_t)2 * C * W));
@@ -1139,15 +1392,18 @@ ScanState *scan_create(const Ingest &g, DevPlan &p, int chunk_target, int keep_s
     delete st;
     return nullptr;
   }
-  set_smem(k_fwd_chain<K_HP, M_SUM>, 4 * (SH_SLOTS * 2 * 64 + 128) * 8);
-  set_smem(k_fwd_chain<K_D, M_SUM>, 4 * (SH_SLOTS * 2 * 64 + 128) * 8);
-  set_smem(k_fwd_chain<K_H, M_SUM>, 4 * (SH_SLOTS * 2 * 64 + 128) * 8);
-  set_smem(k_fwd_chain<K_HP, M_APPLY>, 4 * (SH_SLOTS * 1 * 64 + 128) * 8);
-  set_smem(k_fwd_chain<K_D, M_APPLY>, 4 * (SH_SLOTS * 1 * 64 + 128) * 8);
-  set_smem(k_fwd_chain<K_H, M_APPLY>, 4 * (SH_SLOTS * 1 * 64 + 128) * 8);
-  set_smem(k_bwd_chain<M_SUM>, 4 * (SH_SLOTS * 4 * 64) * 8);
-  set_smem(k_bwd_chain<M_APPLY>, 4 * (SH_SLOTS * 2 * 64) * 8);
-  set_smem(k_bwd_chain<M_LANT>, 4 * (SH_SLOTS * 2 * 64) * 8);
+  {
+    auto b = [](int np, bool acc) { return (size_t)WPC * warp_smem_words(SH_WORDS / (64 * np), np, acc) * 8; };
+    set_smem(k_fwd_chain<K_HP, M_APPLY>, b(1, false));
+    set_smem(k_fwd_chain<K_D, M_APPLY>, b(1, false));
+    set_smem(k_fwd_chain<K_H, M_APPLY>, b(1, true));
+    set_smem(k_fwd_chain<K_HP, M_SUM>, b(2, false));
+    set_smem(k_fwd_chain<K_D, M_SUM>, b(2, false));
+    set_smem(k_fwd_chain<K_H, M_SUM>, b(2, false));
+    set_smem(k_bwd_chain<M_APPLY>, b(1, false));
+    set_smem(k_bwd_chain<M_LANT>, b(2, false));
+    set_smem(k_bwd_chain<M_SUM>, b(2, false));
+  }
   return st;
 }
 
@@ -1177,65 +1433,83 @@ static int run_emission_tail(ScanState *st, const DevPlan &p, cudaStream_t s, Pr
   return 3;
 }
 
+// launch helper: slots held in shared memory for a kernel with `np` planes
+// over values needing `need` slots
+struct ChainLaunch {
+  int grid;
+  size_t smem;
+  ScanDev sd;
+};
+static ChainLaunch chain_cfg(const ScanDev &base, int need, int np, bool acc = false) {
+  ChainLaunch c;
+  c.sd = base;
+  c.sd.sh_slots = std::min(need, SH_WORDS / (64 * np));
+  const int nw = base.C * base.G;
+  c.grid = (nw + WPC - 1) / WPC;
+  c.smem = (size_t)WPC * warp_smem_words(c.sd.sh_slots, np, acc) * 8;
+  return c;
+}
+
 int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *pf) {
   ScanDev &sd = st->sd;
-  const int W = p.W, nw = sd.C * sd.G;
-  const int wpc = 4;  // warps per CTA
-  const int grid = (nw + wpc - 1) / wpc;
+  const int W = p.W;
   uint64_t *init = st->init;
   int n = 0;
-  const size_t sm1 = wpc * (SH_SLOTS * 1 * 64 + 128) * 8, sm2 = wpc * (SH_SLOTS * 2 * 64 + 128) * 8;
-  const size_t smb4 = wpc * (SH_SLOTS * 4 * 64) * 8, smb2 = wpc * (SH_SLOTS * 2 * 64) * 8;
+  const ChainLaunch bs = chain_cfg(sd, st->bslots, 2), ba = chain_cfg(sd, st->bslots, 1),
+                    bl = chain_cfg(sd, st->bslots, 2);
+  const ChainLaunch fs = chain_cfg(sd, st->fslots, 2), fa = chain_cfg(sd, st->fslots, 1);
+  const ChainLaunch fe = chain_cfg(sd, st->fslots, 1, true);
+  const int T = 32 * WPC;
   cudaMemsetAsync(p.acc_flag, 0, (size_t)p.A, s);
-  // ---- anticipation and liveness (backward)
-  PROF("ant_summary");
-  k_bwd_chain<M_SUM><<<grid, 128, smb4, s>>>(p, sd); ++n;
-  PROF("ant_scan");
-  k_scan_carry<<<grid_of(2 * W, 128), 128, 0, s>>>(sd, W, 2, 1, nullptr, nullptr); ++n;
-  PROF("ant_apply");
-  k_bwd_chain<M_APPLY><<<grid, 128, smb2, s>>>(p, sd); ++n;
+  PROF("local_summary");
+  k_local_summary_pos<<<grid_of((long long)p.M, 256), 256, 0, s>>>(sd, p.M); ++n;
+  // ---- liveness (backward)
+  PROF("live_summary");
+  k_bwd_chain<M_SUM><<<bs.grid, T, bs.smem, s>>>(p, bs.sd); ++n;
+  PROF("live_scan");
+  k_scan_carry<<<W, 256, 0, s>>>(sd, W, 1, nullptr); ++n;
+  PROF("live_apply");
+  k_bwd_chain<M_APPLY><<<ba.grid, T, ba.smem, s>>>(p, ba.sd); ++n;
   // ---- loop masks: need within the loop body, kills anywhere in it
-  if (p.L) { PROF("loop_masks"); k_bwd_chain<M_LANT><<<grid, 128, smb2, s>>>(p, sd); ++n; }
+  if (p.L) { PROF("loop_masks"); k_bwd_chain<M_LANT><<<bl.grid, T, bl.smem, s>>>(p, bl.sd); ++n; }
   // ---- plain host validity
   PROF("entry_stale");
   k_entry_stale<<<grid_of(W, 128), 128, 0, s>>>(p.entry_h, p.top, init, W); ++n;
   PROF("hp_summary");
-  k_fwd_chain<K_HP, M_SUM><<<grid, 128, sm2, s>>>(p, sd); ++n;
+  k_fwd_chain<K_HP, M_SUM><<<fs.grid, T, fs.smem, s>>>(p, fs.sd); ++n;
   PROF("fwd_scan");
-  k_scan_carry<<<grid_of(W, 128), 128, 0, s>>>(sd, W, 1, 0, init, init); ++n;
+  k_scan_carry<<<W, 256, 0, s>>>(sd, W, 0, init); ++n;
   PROF("hp_apply");
-  k_fwd_chain<K_HP, M_APPLY><<<grid, 128, sm1, s>>>(p, sd); ++n;
+  k_fwd_chain<K_HP, M_APPLY><<<fa.grid, T, fa.smem, s>>>(p, fa.sd); ++n;
   if (p.K) { PROF("edge_const"); k_scan_edge_const<<<grid_of((long long)p.K * W, 256), 256, 0, s>>>(p, sd, 0); ++n; }
   // ---- device validity
   PROF("entry_stale");
   k_entry_stale<<<grid_of(W, 128), 128, 0, s>>>(p.entry_d, p.top, init, W); ++n;
   PROF("d_summary");
-  k_fwd_chain<K_D, M_SUM><<<grid, 128, sm2, s>>>(p, sd); ++n;
+  k_fwd_chain<K_D, M_SUM><<<fs.grid, T, fs.smem, s>>>(p, fs.sd); ++n;
   PROF("fwd_scan");
-  k_scan_carry<<<grid_of(W, 128), 128, 0, s>>>(sd, W, 1, 0, init, init); ++n;
+  k_scan_carry<<<W, 256, 0, s>>>(sd, W, 0, init); ++n;
   PROF("d_apply");
-  k_fwd_chain<K_D, M_APPLY><<<grid, 128, sm1, s>>>(p, sd); ++n;
+  k_fwd_chain<K_D, M_APPLY><<<fa.grid, T, fa.smem, s>>>(p, fa.sd); ++n;
   if (p.K) { PROF("edge_const"); k_scan_edge_const<<<grid_of((long long)p.K * W, 256), 256, 0, s>>>(p, sd, 1); ++n; }
   // ---- host validity and emission
   PROF("entry_stale");
   k_entry_stale<<<grid_of(W, 128), 128, 0, s>>>(p.entry_h, p.top, init, W); ++n;
   PROF("h_summary");
-  k_fwd_chain<K_H, M_SUM><<<grid, 128, sm2, s>>>(p, sd); ++n;
+  k_fwd_chain<K_H, M_SUM><<<fs.grid, T, fs.smem, s>>>(p, fs.sd); ++n;
   PROF("fwd_scan");
-  k_scan_carry<<<grid_of(W, 128), 128, 0, s>>>(sd, W, 1, 0, init, init); ++n;
+  k_scan_carry<<<W, 256, 0, s>>>(sd, W, 0, init); ++n;
   PROF("h_apply_emit");
-  k_fwd_chain<K_H, M_APPLY><<<grid, 128, sm1, s>>>(p, sd); ++n;
+  k_fwd_chain<K_H, M_APPLY><<<fe.grid, T, fe.smem, s>>>(p, fe.sd); ++n;
   n += run_emission_tail(st, p, s, pf);
   return n;
 }
 
 int enqueue_scan_edges(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *pf) {
   // after the record buffers grew: redo the host-validity apply pass and the gather
-  ScanDev &sd = st->sd;
-  const int nw = sd.C * sd.G, wpc = 4, grid = (nw + wpc - 1) / wpc;
-  const size_t sm1 = wpc * (SH_SLOTS * 1 * 64 + 128) * 8;
+  const ChainLaunch fe = chain_cfg(st->sd, st->fslots, 1, true);
   PROF("h_apply_emit");
-  k_fwd_chain<K_H, M_APPLY><<<grid, 128, sm1, s>>>(p, sd);
+  k_fwd_chain<K_H, M_APPLY><<<fe.grid, 32 * WPC, fe.smem, s>>>(p, fe.sd);
   return 1 + run_emission_tail(st, p, s, pf);
 }
 

@@ -12,51 +12,12 @@
 namespace ompdart {
 
 // ---- local summary (Sec. IV-D validity rules per block) ---------------------
-// One warp per block; lane j takes the accesses j, j+32, ...  The first
-// access to a variable writes the record: the variable's net effect on the
-// host and device copies, whether a host/device read sees the value from
-// before the block, and whether the block writes it.
+// One warp per block (see summarize_block).
 __global__ void k_local_summary(DevPlan p) {
   const int lane = threadIdx.x & 31;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < p.N; b += nwarps) {
-    const int a0 = p.acc_off[b], a1 = p.acc_off[b + 1];
-    for (int i = a0 + lane; i < a1; i += 32) {
-      const int v = acc_var(p.acc[i]);
-      bool first = true;
-      for (int j = a0; j < i; ++j)
-        if (acc_var(p.acc[j]) == v) { first = false; break; }
-      if (!first) { p.rec[i] = REC_NONE; continue; }
-      // position (1-based) of the last event touching each copy and what it
-      // was; position of the first read per space and of the first write
-      int last_h = 0, last_d = 0;       // 1 = copy made valid, 2 = made stale
-      int first_rh = 0, first_rd = 0, first_w = 0, t = 0;
-      for (int j = i; j < a1; ++j) {
-        const uint32_t a = p.acc[j];
-        if (acc_var(a) != v) continue;
-        const int kind = acc_kind(a), dev = acc_space(a);
-        if (kind & 1) {                 // read: it gets a valid copy in its space
-          ++t;
-          if (dev) { last_d = 1; if (!first_rd) first_rd = t; }
-          else     { last_h = 1; if (!first_rh) first_rh = t; }
-        }
-        if (kind & 2) {                 // write: own copy valid, other stale
-          ++t;
-          if (dev) { last_d = 1; last_h = 2; } else { last_h = 1; last_d = 2; }
-          if (!first_w) first_w = t;
-        }
-      }
-      uint32_t r = (uint32_t)v;
-      if (last_h == 1) r |= R_GH;
-      if (last_h == 2) r |= R_KH;
-      if (last_d == 1) r |= R_GD;
-      if (last_d == 2) r |= R_KD;
-      if (first_rh && (!first_w || first_rh < first_w)) r |= R_UH;
-      if (first_rd && (!first_w || first_rd < first_w)) r |= R_UD;
-      if (first_w) r |= R_DF;
-      p.rec[i] = r;
-    }
-  }
+  for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < p.N; b += nwarps)
+    summarize_block(p.acc, p.rec, p.acc_off[b], p.acc_off[b + 1], lane);
 }
 
 // fill every row of a plane with `top` (all variables set, padding clear)
