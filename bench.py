@@ -203,7 +203,7 @@ def run_ours(args):
     heads = np.array([h for h, _, _, _ in g.meta["loops"]], dtype=np.int64)
     g.meta["loop_entry_edges"] = int((preds[heads + 1] - 1).sum()) if len(heads) else 0
 
-    plan = _native.Plan(g, device=local)
+    plan = _native.Plan(g, device=local, chunk_target=args.chunk_target)
     stream = torch.cuda.Stream(device=local)
     sh = stream.cuda_stream
     for _ in range(args.warmup):
@@ -333,6 +333,8 @@ def main():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-words", type=int, default=8)
+    ap.add_argument("--chunk-target", type=int, default=0,
+                    help="positions per chunk of the scan solver (0 = the library's choice)")
     ap.add_argument("--n-blocks", type=int, default=1 << 20,
                     help="blocks of the workload (smaller only for profiler captures)")
     args = ap.parse_args()

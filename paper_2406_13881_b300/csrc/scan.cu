@@ -37,7 +37,7 @@ namespace {
 
 constexpr int CARRY = -2;      // slot id: the chunk's incoming carry
 constexpr int PREV = -3;       // slot id: the value of the position walked just before
-constexpr int SH_WORDS = 1024; // shared-memory words per warp for slots (8 KiB)
+constexpr int SH_WORDS = 512;  // shared-memory words per warp for slots (4 KiB)
 constexpr int WPC = 4;         // warps per CTA of the chain kernels
 constexpr int MAX_DEPTH = 31;  // loop nesting depth the chain handles
 // bound on loop re-runs per chunk walk: each loop of a reducible CFG needs
@@ -393,9 +393,9 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
 
 namespace {
 
-constexpr int WIN = 32;        // positions per metadata window
-constexpr int EDGE_CAP = 256;  // edge entries a window holds
-constexpr int REC_CAP = 512;   // access records a window holds
+constexpr int WIN = 16;        // positions per metadata window
+constexpr int EDGE_CAP = 128;  // edge entries a window holds
+constexpr int REC_CAP = 256;   // access records a window holds
 
 // Per-warp cache of a run of positions: their metadata, their edge entries
 // and their access records (all stored in position order in HBM, so each
@@ -498,19 +498,19 @@ __device__ __forceinline__ void st_word(uint64_t *plane, size_t row, int W, int 
 }
 
 // shared memory per warp (words):
-//   slots [nsh][np][64] | emission scratch 128 | node value [np][64] |
+//   slots [nsh][np][64] | emission scratch 128 | mask table [2][2*np][64] |
 //   kill sets 128 | window | raw accesses REC_CAP/2 (emitting pass only)
-// each part a multiple of 16 words (128 B): slots and the node value are
-// read and written as 16-byte ulonglong2 and must stay 16-byte aligned
+// each part a multiple of 16 words (128 B): slots and masks are read and
+// written as 16-byte ulonglong2 and must stay 16-byte aligned
 constexpr size_t WIN_WORDS = ((sizeof(Win) + 127) / 128) * 16;
 __host__ __device__ inline size_t warp_smem_words(int nsh, int np, bool acc) {
-  return (size_t)nsh * np * 64 + 128 + (size_t)np * 64 + 128 + WIN_WORDS + (acc ? REC_CAP / 2 : 0);
+  return (size_t)nsh * np * 64 + 128 + (size_t)4 * np * 64 + 128 + WIN_WORDS + (acc ? REC_CAP / 2 : 0);
 }
 static_assert(WIN_WORDS % 16 == 0 && WIN_WORDS * 8 >= sizeof(Win), "window layout");
 static_assert(alignof(Win) <= 16 && (REC_CAP / 2) % 16 == 0, "window alignment");
 
 struct WarpMem {
-  uint64_t *slots, *hd, *cur, *kill;
+  uint64_t *slots, *hd, *tbl, *kill;
   Win *win;
 };
 template <int NP, bool ACC>
@@ -519,75 +519,76 @@ __device__ __forceinline__ WarpMem carve(uint64_t *smem, int warp_in_cta, int ns
   WarpMem m;
   m.slots = b;
   m.hd = b + (size_t)nsh * NP * 64;
-  m.cur = m.hd + 128;
-  m.kill = m.cur + NP * 64;
+  m.tbl = m.hd + 128;
+  m.kill = m.tbl + 4 * NP * 64;
   m.win = reinterpret_cast<Win *>(m.kill + 128);
   m.win->acc = ACC ? reinterpret_cast<uint32_t *>(m.kill + 128 + WIN_WORDS) : nullptr;
   return m;
 }
 
-// Apply a block's summary records to the node value z (two words of each
-// plane per lane), through the warp's shared copy `cur`: lane r takes
-// record r; records of one block are for distinct variables, so only lanes
-// whose records fall in the same word take turns.
+// A block's summary records as set/clear masks: lane r takes record r and
+// ORs its bit into the mask table (mask 2*pl = bits the block sets in plane
+// pl, 2*pl+1 = bits it clears); the lanes owning the words then apply
+// z = (z & ~clear) | set.  Records of one block are for distinct variables,
+// so the order of the ORs does not matter.  Building the masks needs
+// nothing of the value flowing in, so the walk builds the next position's
+// masks while the current value is still being computed.
 //   liveness (AntH | AntD share the kill "any write", so their union is one
-//   problem): local: read in either space first -> 1, else write -> 0;
-//   coefficient: both -> 0.  LANT: separate H and D planes.
-//   forward planes (stale sets): local: GEN -> 0 (valid), KILL -> 1 (stale);
-//   coefficient: both -> 0.
-// In LANT mode the kills of the block are also ORed into `kill` ([H|D][64]).
-template <int PH, int MODE, int NP>
-__device__ __forceinline__ void apply_records(const ScanDev &sd, const Win &w, const WinRegs &wr, const PosMeta &m,
-                                              const Lane &L, uint64_t (&z)[NP][2], uint64_t *cur, uint64_t *kill) {
-  if (m.nacc == 0) return;
-  const unsigned FULL = 0xffffffffu;
-#pragma unroll
-  for (int pl = 0; pl < NP; ++pl)
-    *reinterpret_cast<ulonglong2 *>(cur + pl * 64 + 2 * L.lane) = make_ulonglong2(z[pl][0], z[pl][1]);
-  __syncwarp();
-  for (int base = 0; base < m.nacc; base += 32) {
-    const int r = base + L.lane;
-    const uint32_t rc = r < m.nacc ? win_rec(w, wr, sd, m.pacc_beg + r) : REC_NONE;
-    int lw = -1;
-    if (rc != REC_NONE) {
-      lw = (int)((rc & 0xFFFFFFu) >> 6) - L.wg * 64;
-      if ((unsigned)lw >= 64u) lw = -1;
-    }
-    const unsigned grp = __match_any_sync(FULL, lw);
-    const int rank = __popc(grp & ((1u << L.lane) - 1u));
-    const int rounds = (int)__reduce_max_sync(FULL, lw >= 0 ? (unsigned)__popc(grp) : 0u);
-    const uint64_t bit = 1ull << (rc & 63u);
-    for (int t = 0; t < rounds; ++t) {
-      if (lw >= 0 && rank == t) {
-        if (PH == K_ANT) {
-          const bool uh = rc & R_UH, ud = rc & R_UD, df = rc & R_DF;
-          if (MODE == M_LANT) {  // [H, D] anticipation, and the kills of the body
-            uint64_t *h = cur + lw, *d = cur + 64 + lw;
-            *h = uh ? (*h | bit) : df ? (*h & ~bit) : *h;
-            *d = ud ? (*d | bit) : df ? (*d & ~bit) : *d;
-            if (rc & R_KH) kill[lw] |= bit;
-            if (rc & R_KD) kill[64 + lw] |= bit;
-          } else {  // Live: a read in either space before any write
-            const bool ue = uh || ud;
-            cur[lw] = ue ? (cur[lw] | bit) : df ? (cur[lw] & ~bit) : cur[lw];
-            if (MODE == M_SUM && (ue || df)) cur[64 + lw] &= ~bit;
-          }
-        } else {
-          const uint32_t GEN = PH == K_D ? R_GD : R_GH, KILL = PH == K_D ? R_KD : R_KH;
-          if (rc & GEN) cur[lw] &= ~bit;
-          else if (rc & KILL) cur[lw] |= bit;
-          if (MODE == M_SUM && (rc & (GEN | KILL))) cur[64 + lw] &= ~bit;
-        }
+//   problem): local: read in either space first -> set, else write -> clear;
+//   coefficient: both -> clear.  LANT: separate H and D planes, and the
+//   block's kills ORed into `kill` ([H|D][64]).
+//   forward planes (stale sets): local: GEN -> clear (valid), KILL -> set
+//   (stale); coefficient: both -> clear.
+template <int PH, int MODE>
+__device__ __forceinline__ void prep_masks(const ScanDev &sd, const Win &w, const WinRegs &wr, const PosMeta &m,
+                                           const Lane &L, uint64_t *tb, uint64_t *kill) {
+  for (int r = L.lane; r < m.nacc; r += 32) {
+    const uint32_t rc = win_rec(w, wr, sd, m.pacc_beg + r);
+    if (rc == REC_NONE) continue;
+    const int lw = (int)((rc & 0xFFFFFFu) >> 6) - L.wg * 64;
+    if ((unsigned)lw >= 64u) continue;
+    unsigned long long *t = reinterpret_cast<unsigned long long *>(tb) + lw;
+    const unsigned long long bit = 1ull << (rc & 63u);
+    if (PH == K_ANT) {
+      const bool uh = rc & R_UH, ud = rc & R_UD, df = rc & R_DF;
+      if (MODE == M_LANT) {
+        if (uh) atomicOr(t, bit); else if (df) atomicOr(t + 64, bit);
+        if (ud) atomicOr(t + 128, bit); else if (df) atomicOr(t + 192, bit);
+        if (rc & R_KH) atomicOr(reinterpret_cast<unsigned long long *>(kill) + lw, bit);
+        if (rc & R_KD) atomicOr(reinterpret_cast<unsigned long long *>(kill) + 64 + lw, bit);
+      } else {
+        const bool ue = uh || ud;
+        if (ue) atomicOr(t, bit); else if (df) atomicOr(t + 64, bit);
+        if (MODE == M_SUM && (ue || df)) atomicOr(t + 192, bit);
       }
-      __syncwarp();
+    } else {
+      const uint32_t GEN = PH == K_D ? R_GD : R_GH, KILL = PH == K_D ? R_KD : R_KH;
+      if (rc & GEN) atomicOr(t + 64, bit); else if (rc & KILL) atomicOr(t, bit);
+      if (MODE == M_SUM && (rc & (GEN | KILL))) atomicOr(t + 192, bit);
     }
   }
+}
+
+// apply the lane's words of the prepared masks and clear them
+template <int NP>
+__device__ __forceinline__ void take_masks(uint64_t *tb, int lane, uint64_t (&z)[NP][2]) {
 #pragma unroll
   for (int pl = 0; pl < NP; ++pl) {
-    const ulonglong2 v = *reinterpret_cast<const ulonglong2 *>(cur + pl * 64 + 2 * L.lane);
-    z[pl][0] = v.x;
-    z[pl][1] = v.y;
+    ulonglong2 *st = reinterpret_cast<ulonglong2 *>(tb + (2 * pl) * 64 + 2 * lane);
+    ulonglong2 *cl = reinterpret_cast<ulonglong2 *>(tb + (2 * pl + 1) * 64 + 2 * lane);
+    const ulonglong2 a = *st, b = *cl;
+    z[pl][0] = (z[pl][0] & ~b.x) | a.x;
+    z[pl][1] = (z[pl][1] & ~b.y) | a.y;
+    *st = make_ulonglong2(0ull, 0ull);
+    *cl = make_ulonglong2(0ull, 0ull);
   }
+}
+
+// clear the lane's words of a prepared table that will not be used
+template <int NP>
+__device__ __forceinline__ void drop_masks(uint64_t *tb, int lane) {
+#pragma unroll
+  for (int q = 0; q < 2 * NP; ++q) *reinterpret_cast<ulonglong2 *>(tb + q * 64 + 2 * lane) = make_ulonglong2(0ull, 0ull);
 }
 
 // The H-phase emission for one position (apply mode): per-access flags,
@@ -719,6 +720,11 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan p, ScanDev sd) {
   int reruns = 0;
   uint64_t z[NP][2], zo[NP][2], pv[NP][2] = {};
   int top_pend = -1;  // end of the innermost open loop (warp-uniform)
+  constexpr int TBW = 2 * NP * 64;  // words of one mask table
+  int pbuf = 0, prep_pos = -1;      // table holding the built masks of prep_pos
+  drop_masks<NP>(wm.tbl, L.lane);   // shared memory starts undefined: the
+  drop_masks<NP>(wm.tbl + TBW, L.lane);  // masks are built by ORing into zeros
+  __syncwarp();
   uint64_t din[2] = {0, 0}, lv[2] = {0, 0};
   uint64_t pdin[2] = {0, 0}, plv[2] = {0, 0};
   int ppos = -1;  // position whose dense rows are prefetched in pdin/plv
@@ -727,6 +733,14 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan p, ScanDev sd) {
   while (i < cm.e) {
     if (i < wr.ws || i >= wr.we) load_window<true, ACC>(w, wr, sd, i, cm.s, cm.e, L.lane);
     const PosMeta m = w.meta[i - wr.mbase];
+    if (prep_pos != i) {  // masks of this position not built yet (start, window edge, loop jump)
+      if (prep_pos >= 0) {
+        drop_masks<NP>(wm.tbl + pbuf * TBW, L.lane);
+        __syncwarp();
+      }
+      prep_masks<PH, MODE>(sd, w, wr, m, L, wm.tbl + pbuf * TBW, wm.kill);
+      prep_pos = i;
+    }
     if (PH == K_H) {
       // dense rows of this position (prefetched one position ahead)
       if (ppos == i) {
@@ -803,7 +817,16 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan p, ScanDev sd) {
     }
 #pragma unroll
     for (int pl = 0; pl < NP; ++pl) { zo[pl][0] = z[pl][0]; zo[pl][1] = z[pl][1]; }
-    apply_records<PH, MODE, NP>(sd, w, wr, m, L, zo, wm.cur, wm.kill);
+    __syncwarp();
+    take_masks<NP>(wm.tbl + pbuf * TBW, L.lane, zo);
+    // build the next position's masks while this value is finished
+    if (i + 1 < wr.we) {
+      pbuf ^= 1;
+      prep_masks<PH, MODE>(sd, w, wr, w.meta[i + 1 - wr.mbase], L, wm.tbl + pbuf * TBW, wm.kill);
+      prep_pos = i + 1;
+    } else {
+      prep_pos = -1;
+    }
     // ---- a latch whose value adds to an open loop's header marks it dirty
     if (m.latch_levels) {
       uint32_t lvmask = m.latch_levels;
@@ -946,10 +969,23 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
   int lwm = e;  // lowest position walked so far
   int top_ph = -1;  // header of the innermost open loop (warp-uniform)
   uint64_t pv[NP][2] = {};
+  constexpr int TBW = 2 * NP * 64;  // words of one mask table
+  int pbuf = 0, prep_pos = -1;      // table holding the built masks of prep_pos
+  drop_masks<NP>(wm.tbl, L.lane);   // shared memory starts undefined: the
+  drop_masks<NP>(wm.tbl + TBW, L.lane);  // masks are built by ORing into zeros
+  __syncwarp();
   int i = e - 1;
   while (i >= s) {
     if (i < wr.ws || i >= wr.we) load_window<false, false>(w, wr, sd, i, s, e, L.lane);
     const PosMeta m = w.meta[i - wr.mbase];
+    if (prep_pos != i) {
+      if (prep_pos >= 0) {
+        drop_masks<NP>(wm.tbl + pbuf * TBW, L.lane);
+        __syncwarp();
+      }
+      prep_masks<K_ANT, MODE>(sd, w, wr, m, L, wm.tbl + pbuf * TBW, wm.kill);
+      prep_pos = i;
+    }
     // enter loops whose range ends here (outer first)
     for (int q = 0; q < m.nbend; ++q) {
       const int l = sd.bend_loop[m.bend_beg + q];
@@ -999,7 +1035,15 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
         z[pl][1] |= v.y;
       }
     }
-    apply_records<K_ANT, MODE, NP>(sd, w, wr, m, L, z, wm.cur, wm.kill);
+    __syncwarp();
+    take_masks<NP>(wm.tbl + pbuf * TBW, L.lane, z);
+    if (i - 1 >= wr.ws && i - 1 >= s) {
+      pbuf ^= 1;
+      prep_masks<K_ANT, MODE>(sd, w, wr, w.meta[i - 1 - wr.mbase], L, wm.tbl + pbuf * TBW, wm.kill);
+      prep_pos = i - 1;
+    } else {
+      prep_pos = -1;
+    }
     if (m.bslot >= 0) {
       bool changed = false;
       const bool is_top_header = depth > base_depth && top_ph == i;
