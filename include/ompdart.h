@@ -119,6 +119,10 @@ typedef struct {
   int32_t sweeps;              /* device sweeps executed (diagnostic)           */
   int64_t h2d_bytes;           /* bytes the plan copied host->device            */
   int64_t d2h_bytes;           /* bytes copied device->host for this result     */
+  uint64_t *live_in;           /* [n_blocks*n_words] or NULL (keep_states):
+                                  variables the host or the device may read
+                                  before they are written, from the block entry
+                                  on (Sec. II-B); zero for unreachable blocks   */
 } ompdart_result;
 
 typedef struct ompdart_plan ompdart_plan;
@@ -173,6 +177,27 @@ void ompdart_result_free(ompdart_result *res);
 
 /* Text of the calling thread's last error ("" if none). */
 const char *ompdart_last_error(void);
+
+/* Liveness of one CFG, allocating nothing (no paper counterpart: an
+   addition for callers that cannot allocate device memory, for instance
+   code running inside another runtime's memory pool, or that must not
+   trigger the implicit synchronisation of cudaMalloc/cudaFree).
+   Every argument is already in device memory, in the INPUT FORMAT above;
+   exit_host_live may be NULL (all live).  On return live_in[n_blocks*W]
+   holds, per block, the variables the host or the device may read before
+   they are written from the block's entry on (the same plane as
+   ompdart_result.live_in); unreachable blocks are zero.
+   Limits: n_blocks <= 65536, n_vars <= 4096, accesses <= 2^20; larger
+   inputs return OMPDART_E_BUDGET with a message, call pseudo-accesses
+   OMPDART_E_INVALID.  Scratch: one static device array of 4.2 MiB per
+   device, resident until the process exits; its device address is looked
+   up (cudaGetSymbolAddress) on the first call on each device, which should
+   come before any stream capture.  Calls share that array: calls that
+   overlap on the GPU race and must be serialised by the caller.  The call
+   enqueues on `stream' (cudaStream_t) and waits for it. */
+int ompdart_liveness_noalloc(int32_t n_blocks, int32_t n_vars, int32_t entry, const int32_t *succ_off,
+                             const int32_t *succ, const int32_t *acc_off, const uint32_t *acc,
+                             const uint64_t *exit_host_live, uint64_t *live_in, void *stream);
 
 #ifdef __cplusplus
 }

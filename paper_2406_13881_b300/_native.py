@@ -59,7 +59,8 @@ class Result(C.Structure):
                 ("h_out", C.c_void_p), ("d_out", C.c_void_p), ("acc_flag", C.c_void_p),
                 ("n_edge_xfers", C.c_int32), ("edge_xfers", C.c_void_p),
                 ("exit_blocks", C.c_void_p), ("from_exit", C.c_void_p), ("path", C.c_int32),
-                ("sweeps", C.c_int32), ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64)]
+                ("sweeps", C.c_int32), ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64),
+                ("live_in", C.c_void_p)]
 
 
 class Timing(C.Structure):
@@ -79,6 +80,8 @@ EXPORTS = {
     "ompdart_analyze": (C.c_int, [C.POINTER(Cfg), C.POINTER(Opts), C.POINTER(C.POINTER(Result))]),
     "ompdart_result_free": (None, [C.POINTER(Result)]),
     "ompdart_last_error": (C.c_char_p, []),
+    "ompdart_liveness_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
 
 
@@ -154,6 +157,8 @@ def _result_to_numpy(r: Result) -> dict:
     if r.h_out:
         out["h_out"] = arr(r.h_out, n * W, np.uint64, (n, W))
         out["d_out"] = arr(r.d_out, n * W, np.uint64, (n, W))
+    if r.live_in:
+        out["live_in"] = arr(r.live_in, n * W, np.uint64, (n, W))
     return out
 
 
@@ -168,6 +173,14 @@ def analyze(cfg, **opts) -> dict:
         return _result_to_numpy(res.contents)
     finally:
         lib.ompdart_result_free(res)
+
+
+def liveness_noalloc(n_blocks, n_vars, entry, succ_off, succ, acc_off, acc, exit_host_live, live_in,
+                     stream=0):
+    """``ompdart_liveness_noalloc``: every array argument is a device
+    pointer (int); the call allocates nothing."""
+    _check(load().ompdart_liveness_noalloc(int(n_blocks), int(n_vars), int(entry), succ_off, succ, acc_off, acc,
+                                           exit_host_live, live_in, C.c_void_p(stream or 0)))
 
 
 class Plan:

@@ -11,7 +11,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libompdart.so")
-SOURCES = ["api.cu", "sweep.cu", "scan.cu", "ingest.cpp"]
+SOURCES = ["api.cu", "sweep.cu", "scan.cu", "noalloc.cu", "ingest.cpp"]
 HEADERS = ["common.cuh", "plan.cuh", "ingest.h", os.path.join("..", "..", "include", "ompdart.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

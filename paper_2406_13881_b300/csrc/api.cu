@@ -33,6 +33,13 @@ using namespace ompdart;
 
 namespace {
 thread_local std::string g_err;
+}  // namespace
+
+namespace ompdart {
+void set_last_error_text(const std::string &msg) { g_err = msg; }
+}  // namespace ompdart
+
+namespace {
 
 int set_err(int code, const std::string &msg) {
   g_err = msg;
@@ -249,7 +256,8 @@ int ompdart_plan_run(ompdart_plan *P, void *stream) {
   if (P->path == 1)
     n += enqueue_local_summary(P->dp, s, pf) + enqueue_sweep_solver(P->dp, s, P->n_fin, pf);
   else
-    n += enqueue_scan_solver(P->scan, P->dp, s, pf) + enqueue_fill_unreachable(P->dp, s, P->keep_states, pf);
+    n += enqueue_scan_solver(P->scan, P->dp, s, pf);
+  n += enqueue_fill_unreachable(P->dp, s, P->keep_states, pf);
   if (pf) pf->close(s);
   P->launches = n;
   cudaError_t ce = cudaGetLastError();
@@ -318,6 +326,7 @@ int ompdart_plan_view(ompdart_plan *P, ompdart_result *v) {
   v->sweeps = P->h_status[ST_SWEEPS];
   v->h2d_bytes = P->h2d + scan_h2d_bytes(P->scan);
   v->d2h_bytes = 0;
+  v->live_in = P->keep_states ? P->dp.live : nullptr;
   return OMPDART_OK;
 }
 
@@ -349,7 +358,7 @@ void ompdart_plan_destroy(ompdart_plan *P) { delete P; }
 void ompdart_result_free(ompdart_result *r) {
   if (!r) return;
   free(r->h_in); free(r->d_in); free(r->h_out); free(r->d_out); free(r->acc_flag);
-  free(r->edge_xfers); free(r->exit_blocks); free(r->from_exit);
+  free(r->edge_xfers); free(r->exit_blocks); free(r->from_exit); free(r->live_in);
   free(r);
 }
 
@@ -371,8 +380,9 @@ int ompdart_plan_fetch(ompdart_plan *P, ompdart_result **out) {
   r->edge_xfers = (ompdart_edge_xfer *)malloc(sizeof(ompdart_edge_xfer) * ((size_t)v.n_edge_xfers + 1));
   r->exit_blocks = (int32_t *)malloc(sizeof(int32_t) * ((size_t)v.n_exits + 1));
   r->from_exit = (uint64_t *)malloc(8 * ((size_t)v.n_exits * v.n_words + 1));
+  r->live_in = v.live_in ? (uint64_t *)malloc(NW * 8 + 8) : nullptr;
   bool ok = r->h_in && r->d_in && (!v.h_out || r->h_out) && (!v.d_out || r->d_out) && r->acc_flag &&
-            r->edge_xfers && r->exit_blocks && r->from_exit;
+            r->edge_xfers && r->exit_blocks && r->from_exit && (!v.live_in || r->live_in);
   cudaStream_t s = P->last_stream ? P->last_stream : P->stream;
   cudaError_t ce = cudaSuccess;
   auto cp = [&](void *dst, const void *src, size_t n) {
@@ -386,8 +396,9 @@ int ompdart_plan_fetch(ompdart_plan *P, ompdart_result **out) {
   cp(r->edge_xfers, v.edge_xfers, sizeof(ompdart_edge_xfer) * (size_t)v.n_edge_xfers);
   cp(r->exit_blocks, v.exit_blocks, sizeof(int32_t) * (size_t)v.n_exits);
   cp(r->from_exit, v.from_exit, 8 * (size_t)v.n_exits * v.n_words);
+  if (v.live_in) cp(r->live_in, v.live_in, NW * 8);
   if (ok && ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-  r->d2h_bytes = (long long)(2 + (v.h_out ? 2 : 0)) * NW * 8 + v.n_acc +
+  r->d2h_bytes = (long long)(2 + (v.h_out ? 2 : 0) + (v.live_in ? 1 : 0)) * NW * 8 + v.n_acc +
                  (long long)sizeof(ompdart_edge_xfer) * v.n_edge_xfers + 4ll * v.n_exits +
                  8ll * v.n_exits * v.n_words + 4ll * ST_COUNT;
   if (!ok || ce != cudaSuccess) {

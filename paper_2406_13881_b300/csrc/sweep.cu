@@ -28,7 +28,8 @@ __global__ void k_fill_top(uint64_t *plane, int rows, int W, const uint64_t *top
     plane[i] = top[i % W];
 }
 
-// rows of blocks unreachable from the entry: every state plane all-ones
+// rows of blocks unreachable from the entry: every state plane all-ones,
+// liveness zero
 __global__ void k_fill_unreachable(DevPlan p, int keep_states) {
   const long long n = (long long)p.n_unreach * p.W;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
@@ -36,6 +37,7 @@ __global__ void k_fill_unreachable(DevPlan p, int keep_states) {
     const size_t o = (size_t)p.unreach[t / p.W] * p.W + w;
     p.h_in[o] = p.top[w];
     p.d_in[o] = p.top[w];
+    p.live[o] = 0;
     if (keep_states) {
       p.h_out[o] = p.top[w];
       p.d_out[o] = p.top[w];

@@ -28,6 +28,8 @@ def assert_matches_oracle(g, res, orc, words=None, acc_keep=None):
     if "h_out" in res:
         np.testing.assert_array_equal(res["h_out"][:, cols], orc["h_out"], err_msg="h_out")
         np.testing.assert_array_equal(res["d_out"][:, cols], orc["d_out"], err_msg="d_out")
+    if "live_in" in res:
+        np.testing.assert_array_equal(res["live_in"][:, cols], orc["live_in"], err_msg="live_in")
     flags = res["acc_flag"] if acc_keep is None else res["acc_flag"][acc_keep]
     np.testing.assert_array_equal(flags, orc["acc_flag"], err_msg="acc_flag")
     to, fr = dense_edges(res, g.n_edges, res["h_in"].shape[1])
