@@ -57,26 +57,28 @@ def peaks():
 # ---------------------------------------------------------------------------
 
 def byte_model(st):
-    """Algorithmic DRAM bytes per launch of each kernel, from the workload
-    statistics.  Per position the chain kernels read one 64 B position
-    record, ~8 B per in/out edge, 4 B per access record and the block's
-    access offsets (together `struct`); dense planes are W words of 8 B per
-    block."""
+    """Algorithmic DRAM bytes per launch of each kernel of the chunked scan
+    solver, from the workload statistics (the design's minimal traffic: each
+    structure read once per walk, each dense plane read or written once).
+    A chain walk reads per position its 64 B position record, 8 B per edge
+    entry and 4 B per access record (`walk`); a dense plane is W words of
+    8 B per block; loop-entry edge constants are W words per edge."""
     N, M, E, A, W, K, L = (st[k] for k in ("N", "M", "E", "A", "W", "K", "L"))
     G = (W + 63) // 64
     plane = 8.0 * W * N
-    struct = G * (M * 64.0 + E * 8.0 + A * 4.0 + N * 8.0)
+    edge_plane = 8.0 * W * K
+    walk = G * (M * 64.0 + E * 8.0 + A * 4.0)
     return {
-        "local_summary": A * 8.0 + N * 4.0,
-        "ant_summary": struct,
-        "ant_apply": struct + plane,                       # writes Live
-        "loop_masks": G * st["body"] * 80.0 + 2 * L * 8.0 * W,
-        "hp_summary": struct,
-        "hp_apply": struct + K * 8.0 * W,                  # plain host validity at loop-entry sources
-        "d_summary": struct + K * 8.0 * W,
-        "d_apply": struct + K * 8.0 * W + plane + K * 8.0 * W,   # writes D_in, device validity at sources
-        "h_summary": struct + K * 8.0 * W + 2 * plane,     # reads Live, D_in
-        "h_apply_emit": struct + 3 * K * 8.0 * W + 3 * plane + A * 5.0,  # reads Live, D_in; writes H_in, flags
+        "local_summary": M * 64.0 + A * 8.0,                 # accesses in, records out
+        "live_summary": walk,
+        "live_apply": walk + plane,                          # writes Live
+        "loop_masks": G * st["body"] * (64.0 + 4.0 * A / max(1, M) + 8.0 * E / max(1, M)) + 2 * L * 8.0 * W,
+        "hp_summary": walk,
+        "hp_apply": walk + edge_plane,                       # plain host validity at loop-entry sources
+        "d_summary": walk + edge_plane,                      # reads the hoisted `to' constants
+        "d_apply": walk + 2 * edge_plane + plane,            # writes D_in and device validity at sources
+        "h_summary": walk + edge_plane + 2 * plane,          # reads Live, D_in
+        "h_apply_emit": walk + G * A * 4.0 + 3 * edge_plane + 3 * plane + A * 1.0,  # + writes H_in, flags
     }
 
 

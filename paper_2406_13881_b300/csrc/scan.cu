@@ -1357,7 +1357,9 @@ ScanState *scan_create(const Ingest &g, const ompdart_cfg *cfg, DevPlan &p, int 
   std::vector<ChunkMeta> chunks;
   std::vector<CarrySrc> csrc;
   std::vector<int32_t> fin_slot, out_slot, out_pos, lat_slot, bend_loop, srcent;
-  if (chunk_target <= 0) chunk_target = g.M <= 4096 ? std::max(64, g.M / 8) : 512;
+  // short chunks give more independent walks (one warp each); 128
+  // positions was the fastest target on the 2^20-block CFG
+  if (chunk_target <= 0) chunk_target = g.M <= 2048 ? std::max(32, g.M / 8) : 128;
   if (!build_meta(g, chunk_target, st, meta, loops, chunks, csrc, fin_slot, out_slot, out_pos, lat_slot, bend_loop,
                   srcent, err)) {
     delete st;
