@@ -98,6 +98,12 @@ typedef struct {
   int32_t path;         /* 0 auto, 1 general sweep solver, 2 chunked scan solver   */
   int32_t chunk_target; /* blocks per chunk for the scan solver; 0 = automatic     */
   int32_t device;       /* CUDA device ordinal                                     */
+  int32_t warps_per_cta; /* warps per CTA of the scan solver's walk kernels, 1-8;
+                            0 = automatic (4, or the batch autotuner's choice)    */
+  int32_t tune;         /* batches: nonzero = let the autotuner pick chunk_target
+                           and warps_per_cta per arena (ompdart_batch_create)     */
+  int32_t no_graph;     /* batches: nonzero = launch kernels directly instead of
+                           replaying a captured CUDA graph                        */
 } ompdart_opts;
 
 typedef struct {
@@ -177,6 +183,64 @@ void ompdart_result_free(ompdart_result *res);
 
 /* Text of the calling thread's last error ("" if none). */
 const char *ompdart_last_error(void);
+
+/* ---- batches: many independent CFGs in one device run ------------------
+   (no paper counterpart: the paper's tool analyses one translation unit at
+   a time, Sec. V; a batch runs the same analysis for thousands of CFGs at
+   once.)  The CFGs are grouped by word count W; every group becomes one
+   arena: its CFGs laid end to end in one plan of the chunked scan solver
+   (chunks never span two CFGs, each CFG starts from its own entry values
+   and ends at its own region exit).  A CFG that solver cannot take
+   (irreducible, or loop bodies not contiguous in loop order) gets a plan
+   of its own with the general sweep solver.  A run is one CUDA graph: the
+   arenas' kernel sequences are captured once on forked streams, so they
+   overlap on the GPU, and every later run replays the graph.  The walk
+   kernels of an arena are persistent: each warp takes (chunk, word group)
+   items from a device work queue, longest chunks first. */
+typedef struct ompdart_batch ompdart_batch;
+
+/* Ingest n CFGs (host threads, one CFG per task) and upload the arenas.
+   status[n] (may be NULL) receives each CFG's ingestion code; a CFG that
+   fails (OMPDART_E_INVALID, ...) is left out and the rest proceed.  With
+   opts->tune the autotuner times candidate (chunk_target, warps_per_cta)
+   pairs on a sample of each arena and builds the arena with the fastest;
+   choices are cached per (W, size class) for the life of the process.
+   Returns OMPDART_OK unless the batch itself could not be built (n < 0,
+   NULL pointers, allocation failure: OMPDART_E_NOMEM). */
+int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts *opts, ompdart_batch **batch,
+                         int32_t *status);
+
+/* Enqueue one run of every CFG of the batch on `stream' (cudaStream_t,
+   NULL = the batch's own stream) and return. */
+int ompdart_batch_run(ompdart_batch *batch, void *stream);
+
+/* Wait for the last run.  status[n] (may be NULL): per CFG OMPDART_OK, its
+   ingestion error, or OMPDART_E_NOCONVERGE.  Returns OMPDART_OK, or the
+   error of the device run itself (OMPDART_E_CUDA, OMPDART_E_NOMEM). */
+int ompdart_batch_sync(ompdart_batch *batch, int32_t *status);
+
+/* Results of CFG i of the last run, as for ompdart_plan_view (device
+   pointers into the batch's arenas, edge ids local to CFG i) and
+   ompdart_plan_fetch (host copy, ompdart_result_free).  A CFG whose status
+   is an error returns that error. */
+int ompdart_batch_view(ompdart_batch *batch, int32_t i, ompdart_result *view);
+int ompdart_batch_fetch(ompdart_batch *batch, int32_t i, ompdart_result **out);
+
+/* Batch shape: number of arenas (each one device plan over many CFGs),
+   number of CFGs on a plan of their own, kernel launches per run, and per
+   arena its W, CFG count, chunk_target and warps_per_cta (arrays of at
+   least max entries; NULL to skip). */
+int ompdart_batch_info(const ompdart_batch *batch, int32_t *n_arenas, int32_t *n_solo, int32_t *launches,
+                       int32_t max, int32_t *arena_w, int32_t *arena_cfgs, int32_t *arena_chunk,
+                       int32_t *arena_wpc);
+
+void ompdart_batch_destroy(ompdart_batch *batch);
+
+/* One call: batch, run, copy every CFG's outputs to host memory.
+   outs[n] receives library-owned results (NULL for a CFG whose status is
+   an error); status[n] (may be NULL) as for ompdart_batch_sync. */
+int ompdart_analyze_batch(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts *opts, ompdart_result **outs,
+                          int32_t *status);
 
 /* Liveness of one CFG, allocating nothing (no paper counterpart: an
    addition for callers that cannot allocate device memory, for instance

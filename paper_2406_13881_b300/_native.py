@@ -40,7 +40,8 @@ class Cfg(C.Structure):
 
 class Opts(C.Structure):
     _fields_ = [("max_sweeps", C.c_int32), ("keep_states", C.c_int32), ("path", C.c_int32),
-                ("chunk_target", C.c_int32), ("device", C.c_int32)]
+                ("chunk_target", C.c_int32), ("device", C.c_int32), ("warps_per_cta", C.c_int32),
+                ("tune", C.c_int32), ("no_graph", C.c_int32)]
 
 
 class EdgeXfer(C.Structure):
@@ -80,6 +81,18 @@ EXPORTS = {
     "ompdart_analyze": (C.c_int, [C.POINTER(Cfg), C.POINTER(Opts), C.POINTER(C.POINTER(Result))]),
     "ompdart_result_free": (None, [C.POINTER(Result)]),
     "ompdart_last_error": (C.c_char_p, []),
+    "ompdart_batch_create": (C.c_int, [C.POINTER(Cfg), C.c_int32, C.POINTER(Opts), C.POINTER(C.c_void_p),
+                                       C.c_void_p]),
+    "ompdart_batch_run": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ompdart_batch_sync": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ompdart_batch_view": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(Result)]),
+    "ompdart_batch_fetch": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.POINTER(Result))]),
+    "ompdart_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                     C.POINTER(C.c_int32), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_void_p]),
+    "ompdart_batch_destroy": (None, [C.c_void_p]),
+    "ompdart_analyze_batch": (C.c_int, [C.POINTER(Cfg), C.c_int32, C.POINTER(Opts),
+                                        C.POINTER(C.POINTER(Result)), C.c_void_p]),
     "ompdart_liveness_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
@@ -130,8 +143,10 @@ class _Inputs:
                      0 if self.calls is None else int(self.calls.size // (7 * self.W)))
 
 
-def _opts(max_sweeps=0, keep_states=False, path=0, chunk_target=0, device=0):
-    return Opts(int(max_sweeps), int(bool(keep_states)), int(path), int(chunk_target), int(device))
+def _opts(max_sweeps=0, keep_states=False, path=0, chunk_target=0, device=0, warps_per_cta=0, tune=False,
+          no_graph=False):
+    return Opts(int(max_sweeps), int(bool(keep_states)), int(path), int(chunk_target), int(device),
+                int(warps_per_cta), int(bool(tune)), int(bool(no_graph)))
 
 
 def _result_to_numpy(r: Result) -> dict:
@@ -238,3 +253,97 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+class _BatchInputs:
+    """The C structs of many CFGs (and the numpy arrays they point at)."""
+
+    def __init__(self, cfgs):
+        self.inp = [_Inputs(c) for c in cfgs]
+        self.arr = (Cfg * max(1, len(self.inp)))()
+        for i, x in enumerate(self.inp):
+            self.arr[i] = x.c
+        self.n = len(self.inp)
+
+
+class Batch:
+    """Many independent CFGs analysed per device run (``ompdart_batch_*``):
+    ``status`` after construction holds each CFG's ingestion code, ``run``
+    enqueues one run of every CFG (a replayed CUDA graph unless
+    ``no_graph``), ``sync`` waits and returns the per-CFG status array."""
+
+    def __init__(self, cfgs, **opts):
+        self._lib = load()
+        self._inp = _BatchInputs(cfgs)
+        self._h = C.c_void_p()
+        self.status = np.zeros(max(1, self._inp.n), dtype=np.int32)[: self._inp.n]
+        _check(self._lib.ompdart_batch_create(self._inp.arr, self._inp.n, C.byref(_opts(**opts)),
+                                              C.byref(self._h), self.status.ctypes.data))
+
+    def __len__(self):
+        return self._inp.n
+
+    def run(self, stream: int | None = None):
+        _check(self._lib.ompdart_batch_run(self._h, C.c_void_p(stream or 0)))
+
+    def sync(self) -> np.ndarray:
+        st = np.zeros(max(1, self._inp.n), dtype=np.int32)
+        _check(self._lib.ompdart_batch_sync(self._h, st.ctypes.data))
+        self.status = st[: self._inp.n]
+        return self.status
+
+    def view(self, i: int) -> Result:
+        r = Result()
+        _check(self._lib.ompdart_batch_view(self._h, int(i), C.byref(r)))
+        return r
+
+    def fetch(self, i: int) -> dict:
+        res = C.POINTER(Result)()
+        _check(self._lib.ompdart_batch_fetch(self._h, int(i), C.byref(res)))
+        try:
+            return _result_to_numpy(res.contents)
+        finally:
+            self._lib.ompdart_result_free(res)
+
+    def info(self) -> dict:
+        na, ns, nl = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(self._lib.ompdart_batch_info(self._h, C.byref(na), C.byref(ns), C.byref(nl), 0, None, None, None,
+                                            None))
+        k = max(1, na.value)
+        w, n, ch, wp = (np.zeros(k, np.int32) for _ in range(4))
+        _check(self._lib.ompdart_batch_info(self._h, C.byref(na), C.byref(ns), C.byref(nl), k, w.ctypes.data,
+                                            n.ctypes.data, ch.ctypes.data, wp.ctypes.data))
+        arenas = [dict(W=int(w[i]), cfgs=int(n[i]), chunk_target=int(ch[i]), warps_per_cta=int(wp[i]))
+                  for i in range(na.value)]
+        return {"arenas": arenas, "solo": ns.value, "launches": nl.value}
+
+    def close(self):
+        if self._h:
+            self._lib.ompdart_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def analyze_batch(cfgs, **opts):
+    """``ompdart_analyze_batch``: host buffers in and out.  Returns
+    (results, status): results[i] is a dict as from ``analyze`` or None
+    where status[i] is an error code."""
+    lib = load()
+    inp = _BatchInputs(cfgs)
+    outs = (C.POINTER(Result) * max(1, inp.n))()
+    st = np.zeros(max(1, inp.n), dtype=np.int32)
+    _check(lib.ompdart_analyze_batch(inp.arr, inp.n, C.byref(_opts(**opts)), outs, st.ctypes.data))
+    res = []
+    try:
+        for i in range(inp.n):
+            res.append(_result_to_numpy(outs[i].contents) if outs[i] else None)
+    finally:
+        for i in range(inp.n):
+            if outs[i]:
+                lib.ompdart_result_free(outs[i])
+    return res, st[: inp.n]

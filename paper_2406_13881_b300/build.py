@@ -11,8 +11,8 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libompdart.so")
-SOURCES = ["api.cu", "sweep.cu", "scan.cu", "noalloc.cu", "ingest.cpp"]
-HEADERS = ["common.cuh", "plan.cuh", "ingest.h", os.path.join("..", "..", "include", "ompdart.h")]
+SOURCES = ["api.cu", "batch.cu", "sweep.cu", "scan.cu", "noalloc.cu", "ingest.cpp"]
+HEADERS = ["common.cuh", "plan.cuh", "ingest.h", "solver.h", os.path.join("..", "..", "include", "ompdart.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -36,7 +36,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     tmp = LIB + ".tmp%d" % os.getpid()
     cmd = [_nvcc(), "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
-           "-Xptxas", "-warn-spills", "-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES]
+           "-Xptxas", "-warn-spills", "-lpthread", "-o", tmp] + [os.path.join(CSRC, s) for s in SOURCES]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.check_call(cmd, cwd=CSRC)

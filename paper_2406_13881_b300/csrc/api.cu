@@ -10,24 +10,7 @@
 #include <vector>
 
 #include "../../include/ompdart.h"
-#include "ingest.h"
-#include "plan.cuh"
-
-namespace ompdart {
-int enqueue_local_summary(const DevPlan &p, cudaStream_t s, Prof *pf);
-int enqueue_fill_unreachable(const DevPlan &p, cudaStream_t s, int keep_states, Prof *pf);
-int enqueue_sweep_solver(const DevPlan &p, cudaStream_t s, int n_fin, Prof *pf);
-int enqueue_sweep_edges(const DevPlan &p, cudaStream_t s, int n_fin);
-int scan_supported(const Ingest &g);
-struct ScanState;
-ScanState *scan_create(const Ingest &g, const ompdart_cfg *cfg, DevPlan &p, int chunk_target, int keep_states,
-                       std::string *err);
-bool scan_grow_streams(ScanState *st);
-long long scan_h2d_bytes(const ScanState *st);
-int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *pf);
-int enqueue_scan_edges(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *pf);
-void scan_destroy(ScanState *st);
-}  // namespace ompdart
+#include "solver.h"
 
 using namespace ompdart;
 
@@ -49,109 +32,36 @@ int set_err(int code, const std::string &msg) {
 int cuda_err(cudaError_t e, const char *what) {
   return set_err(OMPDART_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
+
 }  // namespace
 
-struct ompdart_plan {
-  Ingest g;
-  DevPlan dp{};
-  std::vector<void *> allocs;
-  cudaStream_t stream = nullptr;
-  cudaStream_t last_stream = nullptr;
-  int device = 0;
-  int path = 1;
-  int launches = 0;
-  int n_fin = 0;
-  int keep_states = 0;
-  long long h2d = 0;
-  ScanState *scan = nullptr;
-  int32_t *h_status = nullptr;  // pinned
-  Prof prof;
+// ==================================================================================
+// the device plan core (one CFG, or a batch of CFGs of equal word count)
+// ==================================================================================
+namespace ompdart {
 
-  template <class T>
-  T *dalloc(size_t n) {
-    void *ptr = nullptr;
-    if (cudaMalloc(&ptr, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) return nullptr;
-    allocs.push_back(ptr);
-    return static_cast<T *>(ptr);
-  }
-  template <class T>
-  T *upload(const T *src, size_t n) {
-    T *d = dalloc<T>(n);
-    if (d && n && cudaMemcpy(d, src, n * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
-    h2d += (long long)(n * sizeof(T));
-    return d;
-  }
-  template <class T>
-  T *upload(const std::vector<T> &v) {
-    return upload(v.data(), v.size());
-  }
-  ~ompdart_plan() {
-    if (scan) scan_destroy(scan);
-    for (void *p : allocs) cudaFree(p);
-    if (stream) cudaStreamDestroy(stream);
-    if (h_status) cudaFreeHost(h_status);
-  }
-};
-
-namespace {
-
-int grow_xfers(ompdart_plan *P, int need) {
-  EdgeXfer *x = P->dalloc<EdgeXfer>((size_t)need);
-  if (!x) return set_err(OMPDART_E_NOMEM, "device allocation of transfer records failed");
-  P->dp.xfer = x;
-  P->dp.xfer_cap = need;
-  return OMPDART_OK;
+PlanCore::~PlanCore() {
+  if (scan) scan_destroy(scan);
+  for (void *p : allocs) cudaFree(p);
 }
 
-}  // namespace
-
-extern "C" {
-
-const char *ompdart_last_error(void) { return g_err.c_str(); }
-
-int ompdart_plan_create(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdart_plan **out) {
-  g_err.clear();
-  if (!out) return set_err(OMPDART_E_INVALID, "plan output pointer is NULL");
-  *out = nullptr;
-  ompdart_opts o{};
-  if (opts) o = *opts;
-  ompdart_plan *P = new (std::nothrow) ompdart_plan();
-  if (!P) return set_err(OMPDART_E_NOMEM, "host allocation failed");
-  std::string err;
-  int rc = ingest(cfg, &P->g, &err);
-  if (rc) {
-    delete P;
-    return set_err(rc, err);
-  }
-  for (int i = 0; i < P->g.A; ++i)
-    if (cfg->acc[i] >> 31) {
-      delete P;
-      return set_err(OMPDART_E_INVALID, "call pseudo-accesses are not accepted by this entry point");
-    }
-  const Ingest &g = P->g;
-  P->device = o.device;
-  P->keep_states = o.keep_states;
-  cudaError_t ce = cudaSetDevice(o.device);
-  if (ce != cudaSuccess) {
-    delete P;
-    return cuda_err(ce, "cudaSetDevice");
-  }
-  if ((ce = cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking)) != cudaSuccess) {
-    delete P;
-    return cuda_err(ce, "cudaStreamCreate");
-  }
-  if ((ce = cudaMallocHost(&P->h_status, ST_COUNT * sizeof(int32_t))) != cudaSuccess) {
-    delete P;
-    return cuda_err(ce, "cudaMallocHost");
-  }
-  const int W = g.W;
-  std::vector<uint64_t> top(W, ~0ull), eh(W), ed(W), xl(W);
-  if (g.V % 64) top[W - 1] = (1ull << (g.V % 64)) - 1;
+void boundary_rows(const ompdart_cfg *cfg, int W, std::vector<uint64_t> *top, std::vector<uint64_t> *eh,
+                   std::vector<uint64_t> *ed, std::vector<uint64_t> *xl) {
   for (int w = 0; w < W; ++w) {
-    eh[w] = (cfg->entry_host_valid ? cfg->entry_host_valid[w] : ~0ull) & top[w];
-    ed[w] = (cfg->entry_dev_valid ? cfg->entry_dev_valid[w] : 0ull) & top[w];
-    xl[w] = (cfg->exit_host_live ? cfg->exit_host_live[w] : ~0ull) & top[w];
+    const uint64_t t = (w == W - 1 && cfg->n_vars % 64) ? (1ull << (cfg->n_vars % 64)) - 1 : ~0ull;
+    top->push_back(t);
+    eh->push_back((cfg->entry_host_valid ? cfg->entry_host_valid[w] : ~0ull) & t);
+    ed->push_back((cfg->entry_dev_valid ? cfg->entry_dev_valid[w] : 0ull) & t);
+    xl->push_back((cfg->exit_host_live ? cfg->exit_host_live[w] : ~0ull) & t);
   }
+}
+
+int core_build(PlanCore *P, const int32_t *acc_off, const uint32_t *acc, const std::vector<uint64_t> &top,
+               const std::vector<uint64_t> &eh, const std::vector<uint64_t> &ed, const std::vector<uint64_t> &xl,
+               int n_cfg, const std::vector<int32_t> &unreach_cfg, const ompdart_opts &o, std::string *err) {
+  const Ingest &g = P->g;
+  P->keep_states = o.keep_states;
+  const int W = g.W;
   std::vector<int32_t> fin_dst(g.fin_src.size());
   for (int i = 0; i < g.M; ++i)
     for (int k = g.fin_off[i]; k < g.fin_off[i + 1]; ++k) fin_dst[k] = g.order[i];
@@ -161,6 +71,7 @@ int ompdart_plan_create(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdar
   d.N = g.N; d.M = g.M; d.E = g.E; d.A = g.A; d.W = W; d.V = g.V; d.L = g.L; d.K = g.K;
   d.X = (int)g.exit_blocks.size();
   d.entry = g.entry;
+  d.n_cfg = n_cfg;
   d.max_sweeps = o.max_sweeps > 0 ? o.max_sweeps : (1 << 20);
   const size_t NW = (size_t)g.N * W;
   bool ok = true;
@@ -182,9 +93,11 @@ int ompdart_plan_create(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdar
       if (g.pos[b] < 0) un.push_back(b);
     d.n_unreach = (int)un.size();
     chk(d.unreach = P->upload(un));
+    d.unreach_cfg = nullptr;
+    if (!unreach_cfg.empty()) chk(d.unreach_cfg = P->upload(unreach_cfg));
   }
-  chk(d.acc_off = P->upload(cfg->acc_off, (size_t)g.N + 1));
-  chk(d.acc = P->upload(cfg->acc, (size_t)g.A));
+  chk(d.acc_off = P->upload(acc_off, (size_t)g.N + 1));
+  chk(d.acc = P->upload(acc, (size_t)g.A));
   chk(d.rec = P->dalloc<uint32_t>(g.A));
   chk(d.loop_head = P->upload(g.loop_head));
   chk(d.body_off = P->upload(g.body_off));
@@ -197,8 +110,10 @@ int ompdart_plan_create(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdar
   chk(d.top = P->upload(top));
   chk(d.h_in = P->dalloc<uint64_t>(NW));
   chk(d.d_in = P->dalloc<uint64_t>(NW));
-  chk(d.h_out = P->dalloc<uint64_t>(NW));
-  chk(d.d_out = P->dalloc<uint64_t>(NW));
+  if (o.keep_states) {
+    chk(d.h_out = P->dalloc<uint64_t>(NW));
+    chk(d.d_out = P->dalloc<uint64_t>(NW));
+  }
   chk(d.live = P->dalloc<uint64_t>(NW));
   chk(d.mask_h = P->dalloc<uint64_t>((size_t)g.L * W));
   chk(d.mask_d = P->dalloc<uint64_t>((size_t)g.L * W));
@@ -208,28 +123,37 @@ int ompdart_plan_create(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdar
   chk(d.from_exit = P->dalloc<uint64_t>((size_t)d.X * W));
   chk(d.status = P->dalloc<int32_t>(ST_COUNT));
   if (!ok) {
-    delete P;
-    return set_err(OMPDART_E_NOMEM, "device allocation failed");
+    *err = "device allocation failed";
+    return OMPDART_E_NOMEM;
   }
   int want = o.path;
   if (want == 0) want = scan_supported(g) ? 2 : 1;
   if (want == 2 && !scan_supported(g)) {
-    delete P;
-    return set_err(OMPDART_E_INVALID, "the chunked scan solver needs a reducible CFG whose loop bodies are "
-                                      "contiguous in loop order");
+    *err = "the chunked scan solver needs a reducible CFG whose loop bodies are contiguous in loop order";
+    return OMPDART_E_INVALID;
+  }
+  if (n_cfg > 1 && want != 2) {
+    *err = "a batch plan needs the scan solver";
+    return OMPDART_E_INVALID;
   }
   P->path = want;
   if (want == 1) {
+    if (!o.keep_states) {  // the sweep solver reads the exit states
+      chk(d.h_out = P->dalloc<uint64_t>(NW));
+      chk(d.d_out = P->dalloc<uint64_t>(NW));
+    }
     chk(d.hp_out = P->dalloc<uint64_t>(NW));
     chk(d.ant_h = P->dalloc<uint64_t>(NW));
     chk(d.ant_d = P->dalloc<uint64_t>(NW));
     chk(d.lant = P->dalloc<uint64_t>(g.body_blk.size() * (size_t)W * 2));
   } else {
-    P->scan = scan_create(g, cfg, d, o.chunk_target, o.keep_states, &err);
-    if (!P->scan) {
-      delete P;
-      return set_err(OMPDART_E_NOMEM, err);
+    chk(P->cfg_err = P->dalloc<int32_t>(n_cfg));
+    if (!ok) {
+      *err = "device allocation failed";
+      return OMPDART_E_NOMEM;
     }
+    P->scan = scan_create(g, acc_off, acc, P->cfg_err, d, o.chunk_target, o.keep_states, err, o.warps_per_cta);
+    if (!P->scan) return OMPDART_E_NOMEM;
   }
   // transfer records: start with room for a few per loop-entry edge and
   // join; grown after a run that overflowed
@@ -237,8 +161,191 @@ int ompdart_plan_create(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdar
   chk(d.xfer = P->dalloc<EdgeXfer>(cap0));
   d.xfer_cap = (int)cap0;
   if (!ok) {
+    *err = "device allocation failed";
+    return OMPDART_E_NOMEM;
+  }
+  return OMPDART_OK;
+}
+
+int core_enqueue(PlanCore *P, cudaStream_t s, Prof *pf) {
+  cudaMemsetAsync(P->dp.status, 0, ST_COUNT * sizeof(int32_t), s);
+  if (P->cfg_err) cudaMemsetAsync(P->cfg_err, 0, sizeof(int32_t) * P->dp.n_cfg, s);
+  int n = 0;
+  if (P->path == 1)
+    n += enqueue_local_summary(P->dp, s, pf) + enqueue_sweep_solver(P->dp, s, P->n_fin, pf);
+  else
+    n += enqueue_scan_solver(P->scan, P->dp, s, pf);
+  n += enqueue_fill_unreachable(P->dp, s, P->keep_states, pf);
+  return n;
+}
+
+int core_finish(PlanCore *P, cudaStream_t s, int32_t *h_status, bool *rerun) {
+  cudaError_t ce;
+  if (P->path == 2 && h_status[ST_OVERFLOW]) {
+    // a per-warp record stream overflowed: size the streams and redo the
+    // host-validity pass (it is the one that emits)
+    if (!scan_grow_streams(P->scan)) return set_err(OMPDART_E_NOMEM, "growing transfer record streams failed");
+    *rerun = true;
+    cudaMemsetAsync(P->dp.status + ST_NREC, 0, 2 * sizeof(int32_t), s);
+    enqueue_scan_edges(P->scan, P->dp, s, nullptr);
+    ce = cudaMemcpyAsync(h_status, P->dp.status, ST_COUNT * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return cuda_err(ce, "device run");
+  }
+  const int nrec = h_status[ST_NREC];
+  if (nrec > P->dp.xfer_cap) {
+    // the record buffer overflowed: enlarge it and redo the edge emission
+    const int need = nrec + nrec / 4 + 16;
+    EdgeXfer *x = P->dalloc<EdgeXfer>((size_t)need);
+    if (!x) return set_err(OMPDART_E_NOMEM, "device allocation of transfer records failed");
+    P->dp.xfer = x;
+    P->dp.xfer_cap = need;
+    *rerun = true;
+    cudaMemsetAsync(P->dp.status + ST_NREC, 0, sizeof(int32_t), s);
+    if (P->path == 1)
+      enqueue_sweep_edges(P->dp, s, P->n_fin);
+    else
+      enqueue_scan_edges(P->scan, P->dp, s, nullptr);
+    ce = cudaMemcpyAsync(h_status, P->dp.status, ST_COUNT * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    if (ce != cudaSuccess) return cuda_err(ce, "device run");
+  }
+  return OMPDART_OK;
+}
+
+void core_view(const PlanCore &P, const int32_t *h_status, ompdart_result *v) {
+  const Ingest &g = P.g;
+  memset(v, 0, sizeof *v);
+  v->n_blocks = g.N; v->n_vars = g.V; v->n_words = g.W; v->n_edges = g.E; v->n_acc = g.A;
+  v->n_exits = P.dp.X;
+  v->mem = OMPDART_MEM_DEVICE;
+  v->h_in = P.dp.h_in; v->d_in = P.dp.d_in;
+  v->h_out = P.keep_states ? P.dp.h_out : nullptr;
+  v->d_out = P.keep_states ? P.dp.d_out : nullptr;
+  v->acc_flag = P.dp.acc_flag;
+  v->n_edge_xfers = std::min(h_status[ST_NREC], P.dp.xfer_cap);
+  v->edge_xfers = reinterpret_cast<ompdart_edge_xfer *>(P.dp.xfer);
+  v->exit_blocks = const_cast<int32_t *>(P.dp.exit_blocks);
+  v->from_exit = P.dp.from_exit;
+  v->path = P.path;
+  v->sweeps = h_status[ST_SWEEPS];
+  v->h2d_bytes = P.h2d + scan_h2d_bytes(P.scan);
+  v->d2h_bytes = 0;
+  v->live_in = P.keep_states ? P.dp.live : nullptr;
+}
+
+int result_copy(const ompdart_result &v, bool device, cudaStream_t s, ompdart_result **out) {
+  *out = nullptr;
+  ompdart_result *r = (ompdart_result *)calloc(1, sizeof(ompdart_result));
+  if (!r) return set_err(OMPDART_E_NOMEM, "host allocation failed");
+  *r = v;
+  r->mem = OMPDART_MEM_HOST;
+  const size_t NW = (size_t)v.n_blocks * v.n_words;
+  r->h_in = (uint64_t *)malloc(NW * 8 + 8);
+  r->d_in = (uint64_t *)malloc(NW * 8 + 8);
+  r->h_out = v.h_out ? (uint64_t *)malloc(NW * 8 + 8) : nullptr;
+  r->d_out = v.d_out ? (uint64_t *)malloc(NW * 8 + 8) : nullptr;
+  r->acc_flag = (uint8_t *)malloc((size_t)v.n_acc + 1);
+  r->edge_xfers = (ompdart_edge_xfer *)malloc(sizeof(ompdart_edge_xfer) * ((size_t)v.n_edge_xfers + 1));
+  r->exit_blocks = (int32_t *)malloc(sizeof(int32_t) * ((size_t)v.n_exits + 1));
+  r->from_exit = (uint64_t *)malloc(8 * ((size_t)v.n_exits * v.n_words + 1));
+  r->live_in = v.live_in ? (uint64_t *)malloc(NW * 8 + 8) : nullptr;
+  bool ok = r->h_in && r->d_in && (!v.h_out || r->h_out) && (!v.d_out || r->d_out) && r->acc_flag &&
+            r->edge_xfers && r->exit_blocks && r->from_exit && (!v.live_in || r->live_in);
+  cudaError_t ce = cudaSuccess;
+  auto cp = [&](void *dst, const void *src, size_t n) {
+    if (!ok || !n) return;
+    if (!device)
+      memcpy(dst, src, n);
+    else if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, s);
+  };
+  cp(r->h_in, v.h_in, NW * 8);
+  cp(r->d_in, v.d_in, NW * 8);
+  if (v.h_out) cp(r->h_out, v.h_out, NW * 8);
+  if (v.d_out) cp(r->d_out, v.d_out, NW * 8);
+  cp(r->acc_flag, v.acc_flag, (size_t)v.n_acc);
+  cp(r->edge_xfers, v.edge_xfers, sizeof(ompdart_edge_xfer) * (size_t)v.n_edge_xfers);
+  cp(r->exit_blocks, v.exit_blocks, sizeof(int32_t) * (size_t)v.n_exits);
+  cp(r->from_exit, v.from_exit, 8 * (size_t)v.n_exits * v.n_words);
+  if (v.live_in) cp(r->live_in, v.live_in, NW * 8);
+  if (device && ok && ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  r->d2h_bytes = device ? (long long)(2 + (v.h_out ? 2 : 0) + (v.live_in ? 1 : 0)) * NW * 8 + v.n_acc +
+                              (long long)sizeof(ompdart_edge_xfer) * v.n_edge_xfers + 4ll * v.n_exits +
+                              8ll * v.n_exits * v.n_words + 4ll * ST_COUNT
+                        : 0;
+  if (!ok || ce != cudaSuccess) {
+    ompdart_result_free(r);
+    return ok ? cuda_err(ce, "copy of results") : set_err(OMPDART_E_NOMEM, "host allocation failed");
+  }
+  *out = r;
+  return OMPDART_OK;
+}
+
+int set_error(int code, const std::string &msg) { return set_err(code, msg); }
+
+}  // namespace ompdart
+
+// ==================================================================================
+// single-CFG plan
+// ==================================================================================
+struct ompdart_plan {
+  PlanCore core;
+  cudaStream_t stream = nullptr;
+  cudaStream_t last_stream = nullptr;
+  int device = 0;
+  int launches = 0;
+  int32_t *h_status = nullptr;  // pinned
+  Prof prof;
+  ~ompdart_plan() {
+    if (stream) cudaStreamDestroy(stream);
+    if (h_status) cudaFreeHost(h_status);
+  }
+};
+
+extern "C" {
+
+const char *ompdart_last_error(void) { return g_err.c_str(); }
+
+int ompdart_plan_create(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdart_plan **out) {
+  g_err.clear();
+  if (!out) return set_err(OMPDART_E_INVALID, "plan output pointer is NULL");
+  *out = nullptr;
+  ompdart_opts o{};
+  if (opts) o = *opts;
+  ompdart_plan *P = new (std::nothrow) ompdart_plan();
+  if (!P) return set_err(OMPDART_E_NOMEM, "host allocation failed");
+  std::string err;
+  int rc = ingest(cfg, &P->core.g, &err);
+  if (rc) {
     delete P;
-    return set_err(OMPDART_E_NOMEM, "device allocation failed");
+    return set_err(rc, err);
+  }
+  for (int i = 0; i < P->core.g.A; ++i)
+    if (cfg->acc[i] >> 31) {
+      delete P;
+      return set_err(OMPDART_E_INVALID, "call pseudo-accesses are not accepted by this entry point");
+    }
+  P->device = o.device;
+  cudaError_t ce = cudaSetDevice(o.device);
+  if (ce != cudaSuccess) {
+    delete P;
+    return cuda_err(ce, "cudaSetDevice");
+  }
+  if ((ce = cudaStreamCreateWithFlags(&P->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+    delete P;
+    return cuda_err(ce, "cudaStreamCreate");
+  }
+  if ((ce = cudaMallocHost(&P->h_status, ST_COUNT * sizeof(int32_t))) != cudaSuccess) {
+    delete P;
+    return cuda_err(ce, "cudaMallocHost");
+  }
+  std::vector<uint64_t> top, eh, ed, xl;
+  boundary_rows(cfg, P->core.g.W, &top, &eh, &ed, &xl);
+  rc = core_build(&P->core, cfg->acc_off, cfg->acc, top, eh, ed, xl, 1, {}, o, &err);
+  if (rc) {
+    delete P;
+    return set_err(rc, err);
   }
   *out = P;
   return OMPDART_OK;
@@ -249,17 +356,10 @@ int ompdart_plan_run(ompdart_plan *P, void *stream) {
   if (!P) return set_err(OMPDART_E_INVALID, "plan is NULL");
   cudaStream_t s = stream ? (cudaStream_t)stream : P->stream;
   P->last_stream = s;
-  cudaMemsetAsync(P->dp.status, 0, ST_COUNT * sizeof(int32_t), s);
   Prof *pf = P->prof.on ? &P->prof : nullptr;
   if (pf) pf->collect_pending = true;
-  int n = 0;
-  if (P->path == 1)
-    n += enqueue_local_summary(P->dp, s, pf) + enqueue_sweep_solver(P->dp, s, P->n_fin, pf);
-  else
-    n += enqueue_scan_solver(P->scan, P->dp, s, pf);
-  n += enqueue_fill_unreachable(P->dp, s, P->keep_states, pf);
+  P->launches = core_enqueue(&P->core, s, pf);
   if (pf) pf->close(s);
-  P->launches = n;
   cudaError_t ce = cudaGetLastError();
   if (ce != cudaSuccess) return cuda_err(ce, "kernel launch");
   return OMPDART_OK;
@@ -268,7 +368,7 @@ int ompdart_plan_run(ompdart_plan *P, void *stream) {
 int ompdart_plan_sync(ompdart_plan *P) {
   if (!P) return set_err(OMPDART_E_INVALID, "plan is NULL");
   cudaStream_t s = P->last_stream ? P->last_stream : P->stream;
-  cudaError_t ce = cudaMemcpyAsync(P->h_status, P->dp.status, ST_COUNT * sizeof(int32_t),
+  cudaError_t ce = cudaMemcpyAsync(P->h_status, P->core.dp.status, ST_COUNT * sizeof(int32_t),
                                    cudaMemcpyDeviceToHost, s);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
   if (ce != cudaSuccess) return cuda_err(ce, "device run");
@@ -278,55 +378,17 @@ int ompdart_plan_sync(ompdart_plan *P) {
   }
   if (P->h_status[ST_ERROR] == ERR_NOCONVERGE)
     return set_err(OMPDART_E_NOCONVERGE, "a device fixed-point loop reached max_sweeps");
-  if (P->path == 2 && P->h_status[ST_OVERFLOW]) {
-    // a per-warp record stream overflowed: size the streams and redo the
-    // host-validity pass (it is the one that emits)
-    if (!scan_grow_streams(P->scan)) return set_err(OMPDART_E_NOMEM, "growing transfer record streams failed");
-    cudaMemsetAsync(P->dp.status + ST_NREC, 0, 2 * sizeof(int32_t), s);
-    enqueue_scan_edges(P->scan, P->dp, s, nullptr);
-    ce = cudaMemcpyAsync(P->h_status, P->dp.status, ST_COUNT * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-    if (ce != cudaSuccess) return cuda_err(ce, "device run");
-    if (P->h_status[ST_ERROR] == ERR_NOCONVERGE)
-      return set_err(OMPDART_E_NOCONVERGE, "a device fixed-point loop reached max_sweeps");
-  }
-  const int nrec = P->h_status[ST_NREC];
-  if (nrec > P->dp.xfer_cap) {
-    // the record buffer overflowed: enlarge it and redo the edge emission
-    int rc = grow_xfers(P, nrec + nrec / 4 + 16);
-    if (rc) return rc;
-    cudaMemsetAsync(P->dp.status + ST_NREC, 0, sizeof(int32_t), s);
-    if (P->path == 1)
-      enqueue_sweep_edges(P->dp, s, P->n_fin);
-    else
-      enqueue_scan_edges(P->scan, P->dp, s, nullptr);
-    ce = cudaMemcpyAsync(P->h_status, P->dp.status, ST_COUNT * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-    if (ce != cudaSuccess) return cuda_err(ce, "device run");
-  }
+  bool rerun = false;
+  int rc = core_finish(&P->core, s, P->h_status, &rerun);
+  if (rc) return rc;
+  if (P->h_status[ST_ERROR] == ERR_NOCONVERGE)
+    return set_err(OMPDART_E_NOCONVERGE, "a device fixed-point loop reached max_sweeps");
   return OMPDART_OK;
 }
 
 int ompdart_plan_view(ompdart_plan *P, ompdart_result *v) {
   if (!P || !v) return set_err(OMPDART_E_INVALID, "NULL argument");
-  const Ingest &g = P->g;
-  memset(v, 0, sizeof *v);
-  v->n_blocks = g.N; v->n_vars = g.V; v->n_words = g.W; v->n_edges = g.E; v->n_acc = g.A;
-  v->n_exits = P->dp.X;
-  v->mem = OMPDART_MEM_DEVICE;
-  v->h_in = P->dp.h_in; v->d_in = P->dp.d_in;
-  v->h_out = P->keep_states ? P->dp.h_out : nullptr;
-  v->d_out = P->keep_states ? P->dp.d_out : nullptr;
-  v->acc_flag = P->dp.acc_flag;
-  v->n_edge_xfers = std::min(P->h_status[ST_NREC], P->dp.xfer_cap);
-  v->edge_xfers = reinterpret_cast<ompdart_edge_xfer *>(P->dp.xfer);
-  v->exit_blocks = const_cast<int32_t *>(P->dp.exit_blocks);
-  v->from_exit = P->dp.from_exit;
-  v->path = P->path;
-  v->sweeps = P->h_status[ST_SWEEPS];
-  v->h2d_bytes = P->h2d + scan_h2d_bytes(P->scan);
-  v->d2h_bytes = 0;
-  v->live_in = P->keep_states ? P->dp.live : nullptr;
+  core_view(P->core, P->h_status, v);
   return OMPDART_OK;
 }
 
@@ -366,47 +428,8 @@ int ompdart_plan_fetch(ompdart_plan *P, ompdart_result **out) {
   if (!P || !out) return set_err(OMPDART_E_INVALID, "NULL argument");
   *out = nullptr;
   ompdart_result v;
-  ompdart_plan_view(P, &v);
-  ompdart_result *r = (ompdart_result *)calloc(1, sizeof(ompdart_result));
-  if (!r) return set_err(OMPDART_E_NOMEM, "host allocation failed");
-  *r = v;
-  r->mem = OMPDART_MEM_HOST;
-  const size_t NW = (size_t)v.n_blocks * v.n_words;
-  r->h_in = (uint64_t *)malloc(NW * 8 + 8);
-  r->d_in = (uint64_t *)malloc(NW * 8 + 8);
-  r->h_out = v.h_out ? (uint64_t *)malloc(NW * 8 + 8) : nullptr;
-  r->d_out = v.d_out ? (uint64_t *)malloc(NW * 8 + 8) : nullptr;
-  r->acc_flag = (uint8_t *)malloc((size_t)v.n_acc + 1);
-  r->edge_xfers = (ompdart_edge_xfer *)malloc(sizeof(ompdart_edge_xfer) * ((size_t)v.n_edge_xfers + 1));
-  r->exit_blocks = (int32_t *)malloc(sizeof(int32_t) * ((size_t)v.n_exits + 1));
-  r->from_exit = (uint64_t *)malloc(8 * ((size_t)v.n_exits * v.n_words + 1));
-  r->live_in = v.live_in ? (uint64_t *)malloc(NW * 8 + 8) : nullptr;
-  bool ok = r->h_in && r->d_in && (!v.h_out || r->h_out) && (!v.d_out || r->d_out) && r->acc_flag &&
-            r->edge_xfers && r->exit_blocks && r->from_exit && (!v.live_in || r->live_in);
-  cudaStream_t s = P->last_stream ? P->last_stream : P->stream;
-  cudaError_t ce = cudaSuccess;
-  auto cp = [&](void *dst, const void *src, size_t n) {
-    if (ok && ce == cudaSuccess && n) ce = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, s);
-  };
-  cp(r->h_in, v.h_in, NW * 8);
-  cp(r->d_in, v.d_in, NW * 8);
-  if (v.h_out) cp(r->h_out, v.h_out, NW * 8);
-  if (v.d_out) cp(r->d_out, v.d_out, NW * 8);
-  cp(r->acc_flag, v.acc_flag, (size_t)v.n_acc);
-  cp(r->edge_xfers, v.edge_xfers, sizeof(ompdart_edge_xfer) * (size_t)v.n_edge_xfers);
-  cp(r->exit_blocks, v.exit_blocks, sizeof(int32_t) * (size_t)v.n_exits);
-  cp(r->from_exit, v.from_exit, 8 * (size_t)v.n_exits * v.n_words);
-  if (v.live_in) cp(r->live_in, v.live_in, NW * 8);
-  if (ok && ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-  r->d2h_bytes = (long long)(2 + (v.h_out ? 2 : 0) + (v.live_in ? 1 : 0)) * NW * 8 + v.n_acc +
-                 (long long)sizeof(ompdart_edge_xfer) * v.n_edge_xfers + 4ll * v.n_exits +
-                 8ll * v.n_exits * v.n_words + 4ll * ST_COUNT;
-  if (!ok || ce != cudaSuccess) {
-    ompdart_result_free(r);
-    return ok ? cuda_err(ce, "copy of results") : set_err(OMPDART_E_NOMEM, "host allocation failed");
-  }
-  *out = r;
-  return OMPDART_OK;
+  core_view(P->core, P->h_status, &v);
+  return result_copy(v, true, P->last_stream ? P->last_stream : P->stream, out);
 }
 
 int ompdart_analyze(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdart_result **out) {

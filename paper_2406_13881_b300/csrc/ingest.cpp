@@ -392,7 +392,62 @@ int ingest(const ompdart_cfg *c, Ingest *g, std::string *err) {
     if (reach[b] && so[b] == so[b + 1]) g->exit_blocks.push_back(b);
   g->chunk_off.assign({0, M});
   g->max_chunk = M;
+  g->cfg_pos_off.assign({0, M});
   return OMPDART_OK;
+}
+
+void concat_ingests(const std::vector<const Ingest *> &parts, Ingest *o) {
+  *o = Ingest();
+  o->cfg_pos_off.push_back(0);
+  o->fin_off.push_back(0);
+  o->out_off.push_back(0);
+  o->body_off.push_back(0);
+  for (const Ingest *g : parts) {
+    const int bo = o->N, eo = o->E, ao = o->A, po = o->M, lo = o->L, ko = o->K;
+    o->N += g->N;
+    o->E += g->E;
+    o->A += g->A;
+    o->M += g->M;
+    o->L += g->L;
+    o->K += g->K;
+    o->V = g->V;
+    o->W = g->W;
+    for (int b : g->order) o->order.push_back(b + bo);
+    for (int p : g->pos) o->pos.push_back(p < 0 ? -1 : p + po);
+    for (int i = 0; i < g->M; ++i) {
+      for (int k = g->fin_off[i]; k < g->fin_off[i + 1]; ++k) {
+        o->fin_src.push_back(g->fin_src[k] + bo);
+        o->fin_eid.push_back(g->fin_eid[k]);  // edge ids stay local to their CFG
+        o->fin_ent.push_back(g->fin_ent[k] < 0 ? -1 : g->fin_ent[k] + ko);
+      }
+      o->fin_off.push_back((int32_t)o->fin_src.size());
+      for (int k = g->out_off[i]; k < g->out_off[i + 1]; ++k) o->out_dst.push_back(g->out_dst[k] + bo);
+      o->out_off.push_back((int32_t)o->out_dst.size());
+      o->is_exit.push_back(g->is_exit[i]);
+    }
+    for (int b : g->exit_blocks) o->exit_blocks.push_back(b + bo);
+    for (int l = 0; l < g->L; ++l) {
+      o->loop_head.push_back(g->loop_head[l] + bo);
+      o->loop_parent.push_back(g->loop_parent[l] < 0 ? -1 : g->loop_parent[l] + lo);
+      o->loop_depth.push_back(g->loop_depth[l]);
+      o->loop_end.push_back(g->loop_end[l] + po);
+      for (int q = g->body_off[l]; q < g->body_off[l + 1]; ++q) o->body_blk.push_back(g->body_blk[q] + bo);
+      o->body_off.push_back((int32_t)o->body_blk.size());
+    }
+    for (int x : g->inner_loop) o->inner_loop.push_back(x < 0 ? -1 : x + lo);
+    for (int k = 0; k < g->K; ++k) {
+      o->ent_loop.push_back(g->ent_loop[k] + lo);
+      o->ent_src.push_back(g->ent_src[k] + bo);
+      o->ent_eid.push_back(g->ent_eid[k] + eo);
+    }
+    o->reducible = o->reducible && g->reducible;
+    o->contiguous = o->contiguous && g->contiguous;
+    o->cfg_pos_off.push_back(o->M);
+    (void)ao;
+  }
+  o->entry = parts.empty() ? 0 : parts[0]->entry;
+  o->chunk_off.assign({0, o->M});
+  o->max_chunk = o->M;
 }
 
 // Single-entry cut before position i (0 < i < M): every edge that crosses
@@ -404,11 +459,7 @@ void make_chunks(Ingest *g, int target) {
   const int M = g->M;
   g->chunk_off.clear();
   g->chunk_off.push_back(0);
-  if (M <= 1 || target <= 0 || target >= M) {
-    g->chunk_off.push_back(M);
-    g->max_chunk = M;
-    return;
-  }
+  if (target <= 0) target = M + 1;  // one chunk per CFG
   // fwd[i]: edges with pos(src) < i <= pos(dst), counted by difference
   // arrays; into[i]: edges into order[i] from positions < i; back[i]:
   // edges with pos(dst) < i <= pos(src).
@@ -436,10 +487,15 @@ void make_chunks(Ingest *g, int target) {
     bk += back[i];
     if (i > 0 && i < M) ok[i] = (bk == 0) && (f == into[i]);
   }
+  // the boundaries between the CFGs of a batch are always cuts (no edge
+  // crosses them)
+  std::vector<uint8_t> force(M + 1, 0);
+  for (int x : g->cfg_pos_off)
+    if (x > 0 && x < M) force[x] = 1;
   int start = 0;
   g->max_chunk = 0;
   for (int i = 1; i < M; ++i) {
-    if (ok[i] && i - start >= target) {
+    if (force[i] || (ok[i] && i - start >= target)) {
       g->chunk_off.push_back(i);
       g->max_chunk = std::max(g->max_chunk, i - start);
       start = i;

@@ -52,7 +52,16 @@ struct Ingest {
   // [chunk_off[c], chunk_off[c+1]); each boundary is a single-entry cut
   std::vector<int32_t> chunk_off;
   int max_chunk = 0;
+  // a batch of independent CFGs laid end to end: CFG k owns positions
+  // [cfg_pos_off[k], cfg_pos_off[k+1]) (one CFG: {0, M})
+  std::vector<int32_t> cfg_pos_off;
 };
+
+// Lay independent ingested CFGs end to end: block, position, loop and
+// loop-entry ids are offset per part; edge ids (fin_eid) stay local to
+// their part.  Every part must have been ingested on its own with the same
+// W; edges never cross parts.
+void concat_ingests(const std::vector<const Ingest *> &parts, Ingest *out);
 
 // Returns OMPDART_OK or OMPDART_E_INVALID (message in *err).
 int ingest(const ompdart_cfg *cfg, Ingest *g, std::string *err);

@@ -16,6 +16,7 @@ namespace ompdart {
 // stated otherwise.
 struct DevPlan {
   int N, M, E, A, W, V, L, K, X, entry;
+  int n_cfg;  // CFGs in this plan (a batch); boundary rows below are per CFG
   int max_sweeps;
   // traversal order (reachable blocks only)
   const int32_t *order;    // [M] block at position
@@ -30,6 +31,7 @@ struct DevPlan {
   const uint8_t *is_exit;  // [M]
   const int32_t *exit_blocks;  // [X]
   const int32_t *unreach;      // [N - M] blocks not reachable from the entry
+  const int32_t *unreach_cfg;  // [N - M] CFG of each (a batch), or null: CFG 0
   int n_unreach;
   // accesses
   const int32_t *acc_off;  // [N+1]
@@ -41,7 +43,7 @@ struct DevPlan {
   const int32_t *body_blk;   // blocks of each body, ascending position
   const int32_t *ent_loop;   // [K]
   const int32_t *ent_src;    // [K]
-  // boundary conditions [W]
+  // boundary conditions and valid-variable masks, [n_cfg][W] each
   const uint64_t *entry_h, *entry_d, *exit_live, *top;
   // state planes [N*W]
   uint64_t *h_in, *d_in, *h_out, *d_out;

@@ -72,8 +72,10 @@ struct ChunkMeta {
   int32_t s, e;             // positions [s, e)
   int32_t carry_beg, carry_cnt;
   int32_t loop_beg, loop_end;
-  int32_t pad0, pad1;
+  int32_t cfg;              // which CFG of a batch the chunk belongs to
+  int32_t flags;            // CH_FIRST / CH_LAST: first / last chunk of its CFG
 };
+constexpr int32_t CH_FIRST = 1, CH_LAST = 2;
 
 struct CarrySrc {  // an edge from this chunk into the next chunk's first block
   int32_t slot, ent, fin_k, pad;
@@ -105,7 +107,11 @@ struct ScanDev {
   EdgeXfer *stream;    // record streams
   int n_streams;
   int keep_states;
+  const int32_t *work;  // [C] chunks by decreasing length: the order warps take them in
+  int32_t *queue;       // [Q_SLOTS] work-queue heads, one per chain launch of a run
+  int32_t *cfg_err;     // [n_cfg] set to 1 for a CFG whose walk hit the re-run cap, or null
 };
+constexpr int Q_SLOTS = 16;
 
 // ---- host side: per-chunk metadata and slot colouring -------------------------------
 
@@ -139,8 +145,16 @@ int colour(std::vector<Interval> &iv, std::vector<int32_t> &slot_of) {
 
 }  // namespace
 
+// launch shape of one persistent chain kernel
+struct ChainShape {
+  int grid = 1, wpc = 4, sh_slots = 0;
+  size_t smem = 0;
+};
+enum ChainKind { CK_BSUM, CK_BAPPLY, CK_BLANT, CK_FSUM, CK_FAPPLY, CK_FEMIT, CK_COUNT };
+
 struct ScanState {
-  int C = 0, G = 0, fslots = 0, bslots = 0, n_streams = 0, n_apply_streams = 0;
+  int C = 0, G = 0, fslots = 0, bslots = 0, n_streams = 0;
+  ChainShape shape[CK_COUNT];
   int n_csrc = 0;
   long long total_cap = 0;
   long long h2d = 0;
@@ -227,6 +241,8 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
     ChunkMeta &cm = chunks[c];
     cm.s = s;
     cm.e = e;
+    cm.cfg = (int32_t)(std::upper_bound(g.cfg_pos_off.begin(), g.cfg_pos_off.end(), s) - g.cfg_pos_off.begin()) - 1;
+    cm.flags = (s == g.cfg_pos_off[cm.cfg] ? CH_FIRST : 0) | (e == g.cfg_pos_off[cm.cfg + 1] ? CH_LAST : 0);
     // ---- forward values
     std::vector<Interval> iv;
     const int nval = e - s;  // ids: [0, nval) positions, [nval, nval + nloops) header in-values
@@ -596,7 +612,7 @@ __device__ __forceinline__ void drop_masks(uint64_t *tb, int lane) {
 __device__ void emit_position(const DevPlan &p, const ScanDev &sd, const Win &w, const WinRegs &wr, const Lane &L,
                               const PosMeta &m, const Slots<1> &sl, const uint64_t zin[2], const uint64_t zout[2],
                               const uint64_t din[2], const uint64_t live[2], const uint64_t prev[2], uint64_t *hd,
-                              int stream, int &rec_count) {
+                              int stream, int &rec_count, int cfg) {
   const int W = p.W, lane = L.lane;
   // ---- access flags: replay the block from its entry states
   if (m.nacc) {
@@ -669,32 +685,30 @@ __device__ void emit_position(const DevPlan &p, const ScanDev &sd, const Win &w,
   }
   // ---- region exit
   if (m.exit_idx >= 0) {
-    if (L.w0 < W) st_word(p.from_exit, m.exit_idx, W, L.w0, p.exit_live[L.w0] & zout[0] & L.top0);
-    if (L.w0 + 1 < W) st_word(p.from_exit, m.exit_idx, W, L.w0 + 1, p.exit_live[L.w0 + 1] & zout[1] & L.top1);
+    const uint64_t *xl = p.exit_live + (size_t)cfg * W;
+    if (L.w0 < W) st_word(p.from_exit, m.exit_idx, W, L.w0, xl[L.w0] & zout[0] & L.top0);
+    if (L.w0 + 1 < W) st_word(p.from_exit, m.exit_idx, W, L.w0 + 1, xl[L.w0 + 1] & zout[1] & L.top1);
   }
 }
 
 // --------------------------------------------------------------------------------------
 // forward chain (Hp, D, H): positions ascending
 // --------------------------------------------------------------------------------------
+// One warp walks chunk c for the 64-word group wg.
 template <int PH, int MODE>
-__global__ void __launch_bounds__(128) k_fwd_chain(DevPlan p, ScanDev sd) {
+__device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, const WarpMem &wm, uint64_t *spill,
+                                         int c, int wg) {
   constexpr int NP = MODE == M_SUM ? 2 : 1;
   constexpr bool ACC = MODE == M_APPLY && PH == K_H;
-  extern __shared__ __align__(16) uint64_t smem[];
-  const int warp_in_cta = threadIdx.x >> 5;
-  const int gw = blockIdx.x * (blockDim.x >> 5) + warp_in_cta;
-  if (gw >= sd.C * sd.G) return;
-  const int c = gw / sd.G, wg = gw % sd.G;
   const int W = p.W;
   Lane L;
   L.lane = threadIdx.x & 31;
   L.wg = wg;
   L.w0 = wg * 64 + 2 * L.lane;
-  L.top0 = L.w0 < W ? p.top[L.w0] : 0;
-  L.top1 = L.w0 + 1 < W ? p.top[L.w0 + 1] : 0;
-  const WarpMem wm = carve<NP, ACC>(smem, warp_in_cta, sd.sh_slots);
-  Slots<NP> sl{wm.slots, sd.spill + (size_t)gw * sd.spill_stride, sd.sh_slots};
+  const uint64_t *tp = p.top + (size_t)sd.chunks[c].cfg * W;  // this CFG's valid-variable mask
+  L.top0 = L.w0 < W ? tp[L.w0] : 0;
+  L.top1 = L.w0 + 1 < W ? tp[L.w0 + 1] : 0;
+  Slots<NP> sl{wm.slots, spill, sd.sh_slots};
   uint64_t *hd = wm.hd;
   Win &w = *wm.win;
   WinRegs wr;
@@ -711,7 +725,7 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan p, ScanDev sd) {
     cin[0][0] = ld_word(sd.carry, c, W, L.w0);
     cin[0][1] = ld_word(sd.carry, c, W, L.w0 + 1);
   }
-  const int stream = c * sd.G + wg;
+  const int stream = 2 * (c * sd.G + wg);  // odd streams: crossing edges (k_cross_emit)
   int rec_count = 0;
   int st_loop[MAX_DEPTH + 1];
   int st_rec[MAX_DEPTH + 1];
@@ -874,7 +888,7 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan p, ScanDev sd) {
         }
         __syncwarp();
         emit_position(p, sd, w, wr, L, m, *reinterpret_cast<Slots<1> *>(&sl), z[0], zo[0], din, lv, pvo[0], hd,
-                      stream, rec_count);
+                      stream, rec_count, cm.cfg);
       }
       if ((PH == K_HP || PH == K_D) && m.nsrcent) {
         uint64_t *dst = PH == K_HP ? sd.hp_src : sd.d_src;
@@ -902,7 +916,10 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan p, ScanDev sd) {
     hwm = max(hwm, i);
     if (jumped) {
       if (++reruns > rerun_cap(cm.e - cm.s)) {
-        if (L.lane == 0) atomicExch(&p.status[ST_ERROR], ERR_NOCONVERGE);
+        if (L.lane == 0) {
+          atomicExch(&p.status[ST_ERROR], ERR_NOCONVERGE);
+          if (sd.cfg_err) atomicExch(&sd.cfg_err[cm.cfg], 1);
+        }
         break;
       }
     } else {
@@ -942,6 +959,32 @@ __global__ void __launch_bounds__(128) k_fwd_chain(DevPlan p, ScanDev sd) {
   if (MODE == M_APPLY && PH == K_H && L.lane == 0) sd.rec_cnt[stream] = rec_count;
 }
 
+// Take the next (chunk, word group) item of a launch's work queue: lane 0
+// bumps the queue head, the warp shares the value.
+__device__ __forceinline__ int next_item(const ScanDev &sd, int qslot) {
+  int item = 0;
+  if ((threadIdx.x & 31) == 0) item = atomicAdd(&sd.queue[qslot], 1);
+  return __shfl_sync(0xffffffffu, item, 0);
+}
+
+// Persistent forward chain: each warp takes items (longest chunks first)
+// from the launch's work queue until none is left.
+template <int PH, int MODE>
+__global__ void __launch_bounds__(256) k_fwd_chain(DevPlan p, ScanDev sd, int qslot) {
+  constexpr int NP = MODE == M_SUM ? 2 : 1;
+  constexpr bool ACC = MODE == M_APPLY && PH == K_H;
+  extern __shared__ __align__(16) uint64_t smem[];
+  const int warp_in_cta = threadIdx.x >> 5;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + warp_in_cta;
+  const WarpMem wm = carve<NP, ACC>(smem, warp_in_cta, sd.sh_slots);
+  uint64_t *spill = sd.spill + (size_t)gw * sd.spill_stride;
+  const int n_items = sd.C * sd.G;
+  for (int item = next_item(sd, qslot); item < n_items; item = next_item(sd, qslot)) {
+    fwd_walk<PH, MODE>(p, sd, wm, spill, sd.work[item / sd.G], item % sd.G);
+    __syncwarp();
+  }
+}
+
 // --------------------------------------------------------------------------------------
 // backward chain (anticipation; loop-restricted anticipation for the masks)
 // --------------------------------------------------------------------------------------
@@ -954,11 +997,12 @@ template <int MODE>
 __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, const WarpMem &wm,
                           const Slots<BwdPlanes<MODE>::NP> &sl, int s, int e, int base_depth, int lo_pos,
                           bool use_carry, const uint64_t (&cin)[BwdPlanes<MODE>::NP][2],
-                          uint64_t (&zlast)[BwdPlanes<MODE>::NP][2]) {
+                          uint64_t (&zlast)[BwdPlanes<MODE>::NP][2], int cfg) {
   Win &w = *wm.win;
   constexpr int NP = BwdPlanes<MODE>::NP;
   const int W = p.W;
-  const uint64_t xl0 = L.w0 < W ? p.exit_live[L.w0] : 0, xl1 = L.w0 + 1 < W ? p.exit_live[L.w0 + 1] : 0;
+  const uint64_t *xlr = p.exit_live + (size_t)cfg * W;
+  const uint64_t xl0 = L.w0 < W ? xlr[L.w0] : 0, xl1 = L.w0 + 1 < W ? xlr[L.w0 + 1] : 0;
   int st_loop[MAX_DEPTH + 1];
   int depth = base_depth;
   uint32_t dirty = 0;
@@ -1082,7 +1126,10 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
     lwm = min(lwm, i);
     if (jumped) {
       if (++reruns > rerun_cap(e - s)) {
-        if (L.lane == 0) atomicExch(&p.status[ST_ERROR], ERR_NOCONVERGE);
+        if (L.lane == 0) {
+          atomicExch(&p.status[ST_ERROR], ERR_NOCONVERGE);
+          if (sd.cfg_err) atomicExch(&sd.cfg_err[cfg], 1);
+        }
         return;
       }
     } else {
@@ -1093,22 +1140,18 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(128) k_bwd_chain(DevPlan p, ScanDev sd) {
+__device__ __forceinline__ void bwd_walk(const DevPlan &p, const ScanDev &sd, const WarpMem &wm, uint64_t *spill,
+                                         int c, int wg) {
   constexpr int NP = BwdPlanes<MODE>::NP;
-  extern __shared__ __align__(16) uint64_t smem[];
-  const int warp_in_cta = threadIdx.x >> 5;
-  const int gw = blockIdx.x * (blockDim.x >> 5) + warp_in_cta;
-  if (gw >= sd.C * sd.G) return;
-  const int c = gw / sd.G, wg = gw % sd.G;
   const int W = p.W;
   Lane L;
   L.lane = threadIdx.x & 31;
   L.wg = wg;
   L.w0 = wg * 64 + 2 * L.lane;
-  L.top0 = L.w0 < W ? p.top[L.w0] : 0;
-  L.top1 = L.w0 + 1 < W ? p.top[L.w0 + 1] : 0;
-  const WarpMem wm = carve<NP, false>(smem, warp_in_cta, sd.sh_slots);
-  Slots<NP> sl{wm.slots, sd.spill + (size_t)gw * sd.spill_stride, sd.sh_slots};
+  const uint64_t *tp = p.top + (size_t)sd.chunks[c].cfg * W;  // this CFG's valid-variable mask
+  L.top0 = L.w0 < W ? tp[L.w0] : 0;
+  L.top1 = L.w0 + 1 < W ? tp[L.w0 + 1] : 0;
+  Slots<NP> sl{wm.slots, spill, sd.sh_slots};
   const ChunkMeta cm = sd.chunks[c];
   uint64_t cin[NP][2], zl[NP][2];
   if (MODE == M_LANT) {
@@ -1119,7 +1162,7 @@ __global__ void __launch_bounds__(128) k_bwd_chain(DevPlan p, ScanDev sd) {
       *reinterpret_cast<ulonglong2 *>(wm.kill + 2 * L.lane) = make_ulonglong2(0ull, 0ull);
       *reinterpret_cast<ulonglong2 *>(wm.kill + 64 + 2 * L.lane) = make_ulonglong2(0ull, 0ull);
       __syncwarp();
-      bwd_range<MODE>(p, sd, L, wm, sl, lm.ph, lm.pend, lm.depth, lm.ph, false, cin, zl);
+      bwd_range<MODE>(p, sd, L, wm, sl, lm.ph, lm.pend, lm.depth, lm.ph, false, cin, zl, cm.cfg);
       const ulonglong2 kh = *reinterpret_cast<const ulonglong2 *>(wm.kill + 2 * L.lane);
       const ulonglong2 kd = *reinterpret_cast<const ulonglong2 *>(wm.kill + 64 + 2 * L.lane);
       st_word(p.mask_h, l, W, L.w0, zl[0][0] & ~kh.x & L.top0);
@@ -1139,12 +1182,28 @@ __global__ void __launch_bounds__(128) k_bwd_chain(DevPlan p, ScanDev sd) {
     cin[0][0] = ld_word(sd.carry, c, W, L.w0);
     cin[0][1] = ld_word(sd.carry, c, W, L.w0 + 1);
   }
-  bwd_range<MODE>(p, sd, L, wm, sl, cm.s, cm.e, 0, -1, true, cin, zl);
+  bwd_range<MODE>(p, sd, L, wm, sl, cm.s, cm.e, 0, -1, true, cin, zl, cm.cfg);
   if (MODE == M_SUM) {
     st_word(sd.gsum, c, W, L.w0, zl[0][0]);
     st_word(sd.gsum, c, W, L.w0 + 1, zl[0][1]);
     st_word(sd.psum, c, W, L.w0, zl[1][0]);
     st_word(sd.psum, c, W, L.w0 + 1, zl[1][1]);
+  }
+}
+
+// persistent backward chain (same work queue scheme as the forward one)
+template <int MODE>
+__global__ void __launch_bounds__(256) k_bwd_chain(DevPlan p, ScanDev sd, int qslot) {
+  constexpr int NP = BwdPlanes<MODE>::NP;
+  extern __shared__ __align__(16) uint64_t smem[];
+  const int warp_in_cta = threadIdx.x >> 5;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + warp_in_cta;
+  const WarpMem wm = carve<NP, false>(smem, warp_in_cta, sd.sh_slots);
+  uint64_t *spill = sd.spill + (size_t)gw * sd.spill_stride;
+  const int n_items = sd.C * sd.G;
+  for (int item = next_item(sd, qslot); item < n_items; item = next_item(sd, qslot)) {
+    bwd_walk<MODE>(p, sd, wm, spill, sd.work[item / sd.G], item % sd.G);
+    __syncwarp();
   }
 }
 
@@ -1166,16 +1225,27 @@ __global__ void k_local_summary_pos(ScanDev sd, int M) {
 // One CTA per word column: thread t composes the maps of a contiguous run
 // of chunks, thread 0 scans the runs' maps, then every thread walks its run
 // again to write each chunk's carry.  Map composition: first (g1, p1), then
-// (g2, p2) gives (g2 | (g1 & p2), p1 & p2).
+// (g2, p2) gives (g2 | (g1 & p2), p1 & p2).  The first chunk (in walk
+// order) of each CFG of a batch starts from that CFG's own boundary value:
+// the forward entry value, or nothing for the backward problem -- the map
+// (init, 0) applied before the chunk's own map.
 __global__ void __launch_bounds__(256) k_scan_carry(ScanDev sd, int W, int backward, const uint64_t *init) {
   __shared__ uint64_t sg[256], sp[256];
   const int w = blockIdx.x, t = threadIdx.x, T = blockDim.x;
   const int C = sd.C, per = (C + T - 1) / T;
   const int b = t * per, e = min(C, b + per);
+  const int32_t rflag = backward ? CH_LAST : CH_FIRST;
   auto chunk = [&](int k) { return backward ? C - 1 - k : k; };  // k-th chunk in walk order
+  auto reset_val = [&](int c) -> uint64_t {
+    return backward || !init ? 0ull : init[(size_t)sd.chunks[c].cfg * W + w];
+  };
   uint64_t g = 0, pp = ~0ull;
   for (int k = b; k < e; ++k) {
     const int c = chunk(k);
+    if (sd.chunks[c].flags & rflag) {
+      g = reset_val(c);
+      pp = 0;
+    }
     const uint64_t gc = sd.gsum[(size_t)c * W + w], pc = sd.psum[(size_t)c * W + w];
     g = gc | (g & pc);
     pp &= pc;
@@ -1184,7 +1254,7 @@ __global__ void __launch_bounds__(256) k_scan_carry(ScanDev sd, int W, int backw
   sp[t] = pp;
   __syncthreads();
   if (t == 0) {
-    uint64_t x = init ? init[w] : 0ull;  // carry entering run 0
+    uint64_t x = 0;  // every walk starts at a CFG's first chunk, which resets
     for (int r = 0; r < T; ++r) {
       const uint64_t gr = sg[r], pr = sp[r];
       sg[r] = x;  // carry entering run r
@@ -1195,15 +1265,16 @@ __global__ void __launch_bounds__(256) k_scan_carry(ScanDev sd, int W, int backw
   uint64_t x = sg[t];
   for (int k = b; k < e; ++k) {
     const int c = chunk(k);
+    if (sd.chunks[c].flags & rflag) x = reset_val(c);
     sd.carry[(size_t)c * W + w] = x;
     x = sd.gsum[(size_t)c * W + w] | (x & sd.psum[(size_t)c * W + w]);
   }
 }
 
-// initial stale sets at the entry block (forward problems): ~valid & top
-__global__ void k_entry_stale(const uint64_t *valid, const uint64_t *top, uint64_t *out, int W) {
-  const int w = blockIdx.x * blockDim.x + threadIdx.x;
-  if (w < W) out[w] = ~valid[w] & top[w];
+// initial stale sets at the entry block of each CFG (forward problems): ~valid & top
+__global__ void k_entry_stale(const uint64_t *valid, const uint64_t *top, uint64_t *out, int W, int n_cfg) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t < (long long)W * n_cfg) out[t] = ~valid[t] & top[t];
 }
 
 // loop-entry edge constants (hoisted transfers): device = mask_d & plain
@@ -1221,11 +1292,11 @@ __global__ void k_scan_edge_const(DevPlan p, ScanDev sd, int which) {
 
 // edge transfers on edges that cross a chunk boundary (into the first block
 // of chunk c from chunk c-1), from the sources' stored host-stale sets
-__global__ void k_cross_emit(DevPlan p, ScanDev sd, int stream0) {
+__global__ void k_cross_emit(DevPlan p, ScanDev sd) {
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (gw >= sd.C * sd.G) return;
   const int c = gw / sd.G, wg = gw % sd.G, lane = threadIdx.x & 31, W = p.W;
-  const int stream = stream0 + gw;
+  const int stream = 2 * gw + 1;  // right after the chunk's own apply stream
   int cnt = 0;
   if (c + 1 < sd.C) {
     const ChunkMeta cm = sd.chunks[c];
@@ -1349,8 +1420,31 @@ static bool scan_set_streams(ScanState *st) {
   return true;
 }
 
-ScanState *scan_create(const Ingest &g, const ompdart_cfg *cfg, DevPlan &p, int chunk_target, int keep_states,
-                       std::string *err) {
+namespace {
+// warps of one CTA of a chain kernel: 1..8, default 4
+int clamp_wpc(int wpc) { return wpc <= 0 ? WPC : std::min(8, std::max(1, wpc)); }
+
+// Shape of a persistent chain launch: as many CTAs as can be resident at
+// once (never more than the items need), slots in shared memory up to
+// SH_WORDS words per plane group.
+template <class K>
+ChainShape chain_shape(K kern, int need, int np, bool acc, int wpc, int n_items, int n_sm) {
+  ChainShape c;
+  c.wpc = wpc;
+  c.sh_slots = std::min(need, SH_WORDS / (64 * np));
+  c.smem = (size_t)wpc * warp_smem_words(c.sh_slots, np, acc) * 8;
+  set_smem(kern, c.smem);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpc, c.smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const long long need_ctas = ((long long)n_items + wpc - 1) / wpc;
+  c.grid = (int)std::max<long long>(1, std::min<long long>(need_ctas, (long long)per_sm * n_sm));
+  return c;
+}
+}  // namespace
+
+ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *acc, int32_t *cfg_err, DevPlan &p,
+                       int chunk_target, int keep_states, std::string *err, int wpc) {
   ScanState *st = new ScanState();
   std::vector<PosMeta> meta;
   std::vector<LoopMeta> loops;
@@ -1369,7 +1463,7 @@ ScanState *scan_create(const Ingest &g, const ompdart_cfg *cfg, DevPlan &p, int 
   std::vector<uint32_t> acc_p;
   acc_p.reserve(g.A);
   for (int i = 0; i < g.M; ++i) {
-    const int b = meta[i].blk, a0 = cfg->acc_off[b], a1 = cfg->acc_off[b + 1];
+    const int b = meta[i].blk, a0 = acc_off[b], a1 = acc_off[b + 1];
     if (a1 - a0 > 32767) {
       if (err) *err = "a block with more than 32767 accesses";
       delete st;
@@ -1378,7 +1472,7 @@ ScanState *scan_create(const Ingest &g, const ompdart_cfg *cfg, DevPlan &p, int 
     meta[i].acc_beg = a0;
     meta[i].nacc = (int16_t)(a1 - a0);
     meta[i].pacc_beg = (int32_t)acc_p.size();
-    acc_p.insert(acc_p.end(), cfg->acc + a0, cfg->acc + a1);
+    acc_p.insert(acc_p.end(), acc + a0, acc + a1);
   }
   std::vector<int2> fin_pk(fin_slot.size()), out_pk(out_slot.size());
   for (size_t k = 0; k < fin_pk.size(); ++k) fin_pk[k] = make_int2(fin_slot[k], g.fin_ent[k]);
@@ -1391,6 +1485,13 @@ ScanState *scan_create(const Ingest &g, const ompdart_cfg *cfg, DevPlan &p, int 
   sd.fslots = st->fslots;
   sd.bslots = st->bslots;
   sd.keep_states = keep_states;
+  sd.cfg_err = cfg_err;
+  // work order: longest chunks first (their walks bound the launch)
+  std::vector<int32_t> work(C);
+  for (int c = 0; c < C; ++c) work[c] = c;
+  std::stable_sort(work.begin(), work.end(), [&](int a, int b) {
+    return chunks[a].e - chunks[a].s > chunks[b].e - chunks[b].s;
+  });
   bool ok = true;
   auto chk = [&](const void *x) { ok = ok && x; };
   chk(sd.meta = st->up(meta));
@@ -1404,32 +1505,56 @@ ScanState *scan_create(const Ingest &g, const ompdart_cfg *cfg, DevPlan &p, int 
   chk(sd.lat_slot = st->up(lat_slot));
   chk(sd.bend_loop = st->up(bend_loop));
   chk(sd.srcent = st->up(srcent));
+  chk(sd.work = st->up(work));
+  chk(sd.queue = st->alloc<int32_t>(Q_SLOTS));
+  // launch shapes (persistent: the grid is what fits on the GPU at once)
+  {
+    wpc = clamp_wpc(wpc);
+    int dev = 0, n_sm = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    const int items = C * G;
+    st->shape[CK_BSUM] = chain_shape(k_bwd_chain<M_SUM>, st->bslots, 2, false, wpc, items, n_sm);
+    st->shape[CK_BAPPLY] = chain_shape(k_bwd_chain<M_APPLY>, st->bslots, 1, false, wpc, items, n_sm);
+    st->shape[CK_BLANT] = chain_shape(k_bwd_chain<M_LANT>, st->bslots, 2, false, wpc, items, n_sm);
+    st->shape[CK_FSUM] = chain_shape(k_fwd_chain<K_HP, M_SUM>, st->fslots, 2, false, wpc, items, n_sm);
+    chain_shape(k_fwd_chain<K_D, M_SUM>, st->fslots, 2, false, wpc, items, n_sm);
+    chain_shape(k_fwd_chain<K_H, M_SUM>, st->fslots, 2, false, wpc, items, n_sm);
+    st->shape[CK_FAPPLY] = chain_shape(k_fwd_chain<K_HP, M_APPLY>, st->fslots, 1, false, wpc, items, n_sm);
+    chain_shape(k_fwd_chain<K_D, M_APPLY>, st->fslots, 1, false, wpc, items, n_sm);
+    st->shape[CK_FEMIT] = chain_shape(k_fwd_chain<K_H, M_APPLY>, st->fslots, 1, true, wpc, items, n_sm);
+  }
+  int max_warps = 1;
+  for (const ChainShape &c : st->shape) max_warps = std::max(max_warps, c.grid * c.wpc);
   const int max_slots = std::max(st->fslots, st->bslots);
   sd.spill_stride = max_slots * 4 * 64;  // worst case: every slot of 4 planes spilled
-  chk(sd.spill = st->alloc<uint64_t>((size_t)std::max(1, sd.spill_stride) * C * G));
+  chk(sd.spill = st->alloc<uint64_t>((size_t)std::max(1, sd.spill_stride) * max_warps));
   chk(sd.gsum = st->alloc<uint64_t>((size_t)2 * C * W));
   chk(sd.psum = st->alloc<uint64_t>((size_t)2 * C * W));
+  if (ok) {  // chunks that end a CFG never write their map: keep it defined
+    cudaMemset(sd.gsum, 0, sizeof(uint64_t) * 2 * C * W);
+    cudaMemset(sd.psum, 0, sizeof(uint64_t) * 2 * C * W);
+  }
   chk(sd.carry = st->alloc<uint64_t>((size_t)2 * C * W));
   chk(sd.hp_src = st->alloc<uint64_t>((size_t)std::max(1, g.K) * W));
   chk(sd.d_src = st->alloc<uint64_t>((size_t)std::max(1, g.K) * W));
   st->n_csrc = (int)csrc.size();
   chk(sd.xval = st->alloc<uint64_t>((size_t)std::max(1, st->n_csrc) * W));
-  // record streams: one per apply warp, then one per crossing warp
-  st->n_apply_streams = C * G;
+  // record streams: per (chunk, word group) the apply walk's stream, then
+  // the crossing edges' stream, so each chunk's records are contiguous
   st->n_streams = 2 * C * G;
   sd.n_streams = st->n_streams;
   st->h_rec_cap.assign(st->n_streams, 0);
   for (int c = 0; c < C; ++c)
     for (int wg = 0; wg < G; ++wg) {
       const int len = chunks[c].e - chunks[c].s;
-      st->h_rec_cap[c * G + wg] = 64 + len;
-      st->h_rec_cap[C * G + c * G + wg] = 8 + 2 * chunks[c].carry_cnt * 64;
+      st->h_rec_cap[2 * (c * G + wg)] = 64 + len;
+      st->h_rec_cap[2 * (c * G + wg) + 1] = 8 + 2 * chunks[c].carry_cnt * 64;
     }
   chk(st->d_rec_cap = st->alloc<int32_t>(st->n_streams));
   chk(st->d_rec_base = st->alloc<int32_t>(st->n_streams));
   chk(sd.rec_cnt = st->alloc<int32_t>(st->n_streams + 1));
   chk(st->offs = st->alloc<int32_t>(st->n_streams + 1));
-  chk(st->init = st->alloc<uint64_t>((size_t)W));
+  chk(st->init = st->alloc<uint64_t>((size_t)W * p.n_cfg));
   if (ok) ok = scan_set_streams(st);
   sd.rec_cap = st->d_rec_cap;
   sd.rec_base = st->d_rec_base;
@@ -1437,18 +1562,6 @@ ScanState *scan_create(const Ingest &g, const ompdart_cfg *cfg, DevPlan &p, int 
     if (err) *err = "device allocation for the scan solver failed";
     delete st;
     return nullptr;
-  }
-  {
-    auto b = [](int np, bool acc) { return (size_t)WPC * warp_smem_words(SH_WORDS / (64 * np), np, acc) * 8; };
-    set_smem(k_fwd_chain<K_HP, M_APPLY>, b(1, false));
-    set_smem(k_fwd_chain<K_D, M_APPLY>, b(1, false));
-    set_smem(k_fwd_chain<K_H, M_APPLY>, b(1, true));
-    set_smem(k_fwd_chain<K_HP, M_SUM>, b(2, false));
-    set_smem(k_fwd_chain<K_D, M_SUM>, b(2, false));
-    set_smem(k_fwd_chain<K_H, M_SUM>, b(2, false));
-    set_smem(k_bwd_chain<M_APPLY>, b(1, false));
-    set_smem(k_bwd_chain<M_LANT>, b(2, false));
-    set_smem(k_bwd_chain<M_SUM>, b(2, false));
   }
   return st;
 }
@@ -1471,7 +1584,7 @@ static int run_emission_tail(ScanState *st, const DevPlan &p, cudaStream_t s, Pr
   int32_t *offs = st->offs;
   const int nw = sd.C * sd.G;
   PROF("cross_emit");
-  k_cross_emit<<<grid_of((long long)nw * 32, 128), 128, 0, s>>>(p, sd, st->n_apply_streams);
+  k_cross_emit<<<grid_of((long long)nw * 32, 128), 128, 0, s>>>(p, sd);
   PROF("streams_prefix");
   k_streams_prefix<<<1, 1024, 0, s>>>(sd, offs, p.status);
   PROF("streams_copy");
@@ -1479,84 +1592,90 @@ static int run_emission_tail(ScanState *st, const DevPlan &p, cudaStream_t s, Pr
   return 3;
 }
 
-// launch helper: slots held in shared memory for a kernel with `np` planes
-// over values needing `need` slots
-struct ChainLaunch {
-  int grid;
-  size_t smem;
-  ScanDev sd;
-};
-static ChainLaunch chain_cfg(const ScanDev &base, int need, int np, bool acc = false) {
-  ChainLaunch c;
-  c.sd = base;
-  c.sd.sh_slots = std::min(need, SH_WORDS / (64 * np));
-  const int nw = base.C * base.G;
-  c.grid = (nw + WPC - 1) / WPC;
-  c.smem = (size_t)WPC * warp_smem_words(c.sd.sh_slots, np, acc) * 8;
-  return c;
+// launch a persistent chain kernel with its shape; qslot: its work-queue head
+template <class K>
+void chain_launch(K kern, const ChainShape &cs, const DevPlan &p, const ScanDev &sd, int qslot, cudaStream_t s) {
+  ScanDev sd2 = sd;
+  sd2.sh_slots = cs.sh_slots;
+  kern<<<cs.grid, 32 * cs.wpc, cs.smem, s>>>(p, sd2, qslot);
 }
+#define CHAIN(kern, kind, qslot) (chain_launch(kern, st->shape[kind], p, sd, qslot, s), ++n)
 
 int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *pf) {
   ScanDev &sd = st->sd;
   const int W = p.W;
   uint64_t *init = st->init;
   int n = 0;
-  const ChainLaunch bs = chain_cfg(sd, st->bslots, 2), ba = chain_cfg(sd, st->bslots, 1),
-                    bl = chain_cfg(sd, st->bslots, 2);
-  const ChainLaunch fs = chain_cfg(sd, st->fslots, 2), fa = chain_cfg(sd, st->fslots, 1);
-  const ChainLaunch fe = chain_cfg(sd, st->fslots, 1, true);
-  const int T = 32 * WPC;
   cudaMemsetAsync(p.acc_flag, 0, (size_t)p.A, s);
+  cudaMemsetAsync(sd.queue, 0, sizeof(int32_t) * Q_SLOTS, s);
   PROF("local_summary");
   k_local_summary_pos<<<grid_of((long long)p.M, 256), 256, 0, s>>>(sd, p.M); ++n;
   // ---- liveness (backward)
   PROF("live_summary");
-  k_bwd_chain<M_SUM><<<bs.grid, T, bs.smem, s>>>(p, bs.sd); ++n;
+  CHAIN(k_bwd_chain<M_SUM>, CK_BSUM, 0);
   PROF("live_scan");
   k_scan_carry<<<W, 256, 0, s>>>(sd, W, 1, nullptr); ++n;
   PROF("live_apply");
-  k_bwd_chain<M_APPLY><<<ba.grid, T, ba.smem, s>>>(p, ba.sd); ++n;
+  CHAIN(k_bwd_chain<M_APPLY>, CK_BAPPLY, 1);
   // ---- loop masks: need within the loop body, kills anywhere in it
-  if (p.L) { PROF("loop_masks"); k_bwd_chain<M_LANT><<<bl.grid, T, bl.smem, s>>>(p, bl.sd); ++n; }
+  if (p.L) { PROF("loop_masks"); CHAIN(k_bwd_chain<M_LANT>, CK_BLANT, 2); }
   // ---- plain host validity
   PROF("entry_stale");
-  k_entry_stale<<<grid_of(W, 128), 128, 0, s>>>(p.entry_h, p.top, init, W); ++n;
+  k_entry_stale<<<grid_of((long long)W * p.n_cfg, 128), 128, 0, s>>>(p.entry_h, p.top, init, W, p.n_cfg); ++n;
   PROF("hp_summary");
-  k_fwd_chain<K_HP, M_SUM><<<fs.grid, T, fs.smem, s>>>(p, fs.sd); ++n;
+  CHAIN((k_fwd_chain<K_HP, M_SUM>), CK_FSUM, 3);
   PROF("fwd_scan");
   k_scan_carry<<<W, 256, 0, s>>>(sd, W, 0, init); ++n;
   PROF("hp_apply");
-  k_fwd_chain<K_HP, M_APPLY><<<fa.grid, T, fa.smem, s>>>(p, fa.sd); ++n;
+  CHAIN((k_fwd_chain<K_HP, M_APPLY>), CK_FAPPLY, 4);
   if (p.K) { PROF("edge_const"); k_scan_edge_const<<<grid_of((long long)p.K * W, 256), 256, 0, s>>>(p, sd, 0); ++n; }
   // ---- device validity
   PROF("entry_stale");
-  k_entry_stale<<<grid_of(W, 128), 128, 0, s>>>(p.entry_d, p.top, init, W); ++n;
+  k_entry_stale<<<grid_of((long long)W * p.n_cfg, 128), 128, 0, s>>>(p.entry_d, p.top, init, W, p.n_cfg); ++n;
   PROF("d_summary");
-  k_fwd_chain<K_D, M_SUM><<<fs.grid, T, fs.smem, s>>>(p, fs.sd); ++n;
+  CHAIN((k_fwd_chain<K_D, M_SUM>), CK_FSUM, 5);
   PROF("fwd_scan");
   k_scan_carry<<<W, 256, 0, s>>>(sd, W, 0, init); ++n;
   PROF("d_apply");
-  k_fwd_chain<K_D, M_APPLY><<<fa.grid, T, fa.smem, s>>>(p, fa.sd); ++n;
+  CHAIN((k_fwd_chain<K_D, M_APPLY>), CK_FAPPLY, 6);
   if (p.K) { PROF("edge_const"); k_scan_edge_const<<<grid_of((long long)p.K * W, 256), 256, 0, s>>>(p, sd, 1); ++n; }
   // ---- host validity and emission
   PROF("entry_stale");
-  k_entry_stale<<<grid_of(W, 128), 128, 0, s>>>(p.entry_h, p.top, init, W); ++n;
+  k_entry_stale<<<grid_of((long long)W * p.n_cfg, 128), 128, 0, s>>>(p.entry_h, p.top, init, W, p.n_cfg); ++n;
   PROF("h_summary");
-  k_fwd_chain<K_H, M_SUM><<<fs.grid, T, fs.smem, s>>>(p, fs.sd); ++n;
+  CHAIN((k_fwd_chain<K_H, M_SUM>), CK_FSUM, 7);
   PROF("fwd_scan");
   k_scan_carry<<<W, 256, 0, s>>>(sd, W, 0, init); ++n;
   PROF("h_apply_emit");
-  k_fwd_chain<K_H, M_APPLY><<<fe.grid, T, fe.smem, s>>>(p, fe.sd); ++n;
+  CHAIN((k_fwd_chain<K_H, M_APPLY>), CK_FEMIT, 8);
   n += run_emission_tail(st, p, s, pf);
   return n;
 }
 
 int enqueue_scan_edges(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *pf) {
   // after the record buffers grew: redo the host-validity apply pass and the gather
-  const ChainLaunch fe = chain_cfg(st->sd, st->fslots, 1, true);
+  ScanDev &sd = st->sd;
+  int n = 0;
+  cudaMemsetAsync(sd.queue + 9, 0, sizeof(int32_t), s);
   PROF("h_apply_emit");
-  k_fwd_chain<K_H, M_APPLY><<<fe.grid, 32 * WPC, fe.smem, s>>>(p, fe.sd);
-  return 1 + run_emission_tail(st, p, s, pf);
+  CHAIN((k_fwd_chain<K_H, M_APPLY>), CK_FEMIT, 9);
+  return n + run_emission_tail(st, p, s, pf);
+}
+
+#undef CHAIN
+
+// first gathered record of each chunk (and the total at index C), after a
+// completed run: the offsets of the chunk's first stream
+bool scan_chunk_record_offsets(const ScanState *st, cudaStream_t s, std::vector<int32_t> *out, int32_t total) {
+  std::vector<int32_t> offs(st->n_streams);
+  if (st->n_streams &&
+      (cudaMemcpyAsync(offs.data(), st->offs, sizeof(int32_t) * st->n_streams, cudaMemcpyDeviceToHost, s) !=
+           cudaSuccess ||
+       cudaStreamSynchronize(s) != cudaSuccess))
+    return false;
+  out->assign(st->C + 1, total);
+  for (int c = 0; c < st->C; ++c) (*out)[c] = offs[(size_t)2 * c * st->G];
+  return true;
 }
 
 void scan_destroy(ScanState *st) { delete st; }

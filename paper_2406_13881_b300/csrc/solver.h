@@ -1,0 +1,104 @@
+// solver.h -- internal interfaces between the files of libompdart.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/ompdart.h"
+#include "ingest.h"
+#include "plan.cuh"
+
+namespace ompdart {
+
+// ---- api.cu: thread-local error text of ompdart_last_error
+void set_last_error_text(const std::string &msg);
+int set_error(int code, const std::string &msg);  // sets the text, returns code
+
+// ---- sweep.cu: the general solver (any CFG, one CFG per plan)
+int enqueue_local_summary(const DevPlan &p, cudaStream_t s, Prof *pf);
+int enqueue_fill_unreachable(const DevPlan &p, cudaStream_t s, int keep_states, Prof *pf);
+int enqueue_sweep_solver(const DevPlan &p, cudaStream_t s, int n_fin, Prof *pf);
+int enqueue_sweep_edges(const DevPlan &p, cudaStream_t s, int n_fin);
+
+// ---- scan.cu: the chunked scan solver (reducible CFGs with contiguous
+// loop bodies; one CFG or a batch of CFGs laid end to end)
+int scan_supported(const Ingest &g);
+struct ScanState;
+// acc_off/acc: accesses of the plan's blocks (CSR over g's block ids);
+// cfg_err: device [n_cfg] per-CFG error flags or null; wpc: warps per CTA
+// of the chain kernels (0 = default)
+ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *acc, int32_t *cfg_err, DevPlan &p,
+                       int chunk_target, int keep_states, std::string *err, int wpc);
+bool scan_grow_streams(ScanState *st);
+long long scan_h2d_bytes(const ScanState *st);
+int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *pf);
+int enqueue_scan_edges(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *pf);
+// after a completed run: index of the first gathered transfer record of
+// every chunk, and `total` at index C
+bool scan_chunk_record_offsets(const ScanState *st, cudaStream_t s, std::vector<int32_t> *out, int32_t total);
+void scan_destroy(ScanState *st);
+
+// ---- api.cu: one device plan over one CFG or a batch of CFGs of equal
+// word count (shared by the single-CFG plan and the batch)
+struct PlanCore {
+  Ingest g;
+  DevPlan dp{};
+  std::vector<void *> allocs;
+  int path = 1;  // 1 sweep, 2 scan
+  int n_fin = 0;
+  int keep_states = 0;
+  long long h2d = 0;
+  ScanState *scan = nullptr;
+  int32_t *cfg_err = nullptr;  // device [n_cfg] (scan path)
+
+  template <class T>
+  T *dalloc(size_t n) {
+    void *ptr = nullptr;
+    if (cudaMalloc(&ptr, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) return nullptr;
+    allocs.push_back(ptr);
+    return static_cast<T *>(ptr);
+  }
+  template <class T>
+  T *upload(const T *src, size_t n) {
+    T *d = dalloc<T>(n);
+    if (d && n && cudaMemcpy(d, src, n * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) return nullptr;
+    h2d += (long long)(n * sizeof(T));
+    return d;
+  }
+  template <class T>
+  T *upload(const std::vector<T> &v) {
+    return upload(v.data(), v.size());
+  }
+  PlanCore() = default;
+  PlanCore(const PlanCore &) = delete;
+  PlanCore &operator=(const PlanCore &) = delete;
+  ~PlanCore();
+};
+
+// Boundary rows of one CFG (Sec. IV-D entry states and region-exit
+// liveness), padding bits cleared: appended to top, eh, ed, xl.
+void boundary_rows(const ompdart_cfg *cfg, int W, std::vector<uint64_t> *top, std::vector<uint64_t> *eh,
+                   std::vector<uint64_t> *ed, std::vector<uint64_t> *xl);
+
+// Upload c->g (ingested; a batch concatenated) and its accesses, choose the
+// solver (path 0 auto, 1 sweep, 2 scan; a batch must take the scan) and
+// allocate every plane.  unreach_cfg: CFG of each unreachable block in
+// ascending block order (empty for one CFG).  Returns an OMPDART_* code.
+int core_build(PlanCore *c, const int32_t *acc_off, const uint32_t *acc, const std::vector<uint64_t> &top,
+               const std::vector<uint64_t> &eh, const std::vector<uint64_t> &ed, const std::vector<uint64_t> &xl,
+               int n_cfg, const std::vector<int32_t> &unreach_cfg, const ompdart_opts &o, std::string *err);
+// Enqueue one full run on s; returns the number of kernels launched.
+int core_enqueue(PlanCore *c, cudaStream_t s, Prof *pf);
+// After the stream finished a run (h_status: its ST_COUNT status words):
+// regrow overflowed record buffers and redo the emission (synchronously).
+// *rerun is set when buffers changed (captured graphs must be rebuilt).
+int core_finish(PlanCore *c, cudaStream_t s, int32_t *h_status, bool *rerun);
+// Device view of a core's results (h_status: the status words of its last run).
+void core_view(const PlanCore &c, const int32_t *h_status, ompdart_result *v);
+// Copy the arrays a view points at (device memory if `device`, else host)
+// into a new host result (ompdart_result_free).
+int result_copy(const ompdart_result &v, bool device, cudaStream_t s, ompdart_result **out);
+
+}  // namespace ompdart

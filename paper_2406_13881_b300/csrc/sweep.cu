@@ -34,13 +34,15 @@ __global__ void k_fill_unreachable(DevPlan p, int keep_states) {
   const long long n = (long long)p.n_unreach * p.W;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const int w = (int)(t % p.W);
-    const size_t o = (size_t)p.unreach[t / p.W] * p.W + w;
-    p.h_in[o] = p.top[w];
-    p.d_in[o] = p.top[w];
+    const long long u = t / p.W;
+    const size_t o = (size_t)p.unreach[u] * p.W + w;
+    const uint64_t top = p.top[(size_t)(p.unreach_cfg ? p.unreach_cfg[u] : 0) * p.W + w];
+    p.h_in[o] = top;
+    p.d_in[o] = top;
     p.live[o] = 0;
     if (keep_states) {
-      p.h_out[o] = p.top[w];
-      p.d_out[o] = p.top[w];
+      p.h_out[o] = top;
+      p.d_out[o] = top;
     }
   }
 }
