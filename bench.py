@@ -20,6 +20,12 @@ the fixed point: n_blocks * n_words / step time.
   roofline, cpu_baseline, clocks, gpu_launches -- see the design doc
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+  --workload batch: the 10,000-CFG batch (block counts lognormal, median
+  512, clipped 16-65,536; 64/256/1024/2048 variables; seed 3) through
+  ompdart_batch_* (arenas per word count, one captured CUDA graph per run),
+  beside the plain form that runs one plan per CFG (one launch sequence
+  and one wait per CFG); CFGs/s and p50/p99 latency for both.
 """
 from __future__ import annotations
 
@@ -297,6 +303,141 @@ def run_ours(args):
     return out
 
 
+def percentile(xs, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q)) if len(xs) else None
+
+
+def run_batch(args):
+    """Batched analysis of config-3-shaped CFGs vs one plan per CFG."""
+    import numpy as np
+    import torch
+    from paper_2406_13881_b300 import _native, build, workload as wl
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    torch.cuda.set_device(local)
+    build.build()
+    t0 = time.perf_counter()
+    cfgs = wl.batch(args.batch_seed, n_cfgs=args.n_cfgs)
+    t_gen = time.perf_counter() - t0
+    units = sum(g.n_blocks * g.W for g in cfgs)
+    t0 = time.perf_counter()
+    b = _native.Batch(cfgs, device=local, tune=args.tune, chunk_target=args.chunk_target)
+    t_create = time.perf_counter() - t0
+    assert (b.status == 0).all()
+    info = b.info()
+    stream = torch.cuda.Stream(device=local)
+    sh = stream.cuda_stream
+    for _ in range(args.warmup):
+        b.run(sh)
+        assert (b.sync() == 0).all()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs[0].record(stream)
+    for k in range(args.steps):
+        b.run(sh)
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    b.sync()
+    clk = clocks.stop()
+    info = b.info()  # launches per run are known once it has run
+    step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    ms = sum(step_ms)
+    # latency of a batch as the caller sees it: run() to sync() returning
+    lat_b = []
+    for _ in range(max(3, min(args.steps, 10))):
+        t0 = time.perf_counter()
+        b.run(sh)
+        b.sync()
+        lat_b.append(1e3 * (time.perf_counter() - t0))
+    b.close()
+    # ---- the plain form: one plan per CFG, one launch sequence and one wait per CFG
+    n_plain = len(cfgs) if args.plain_cfgs <= 0 else min(args.plain_cfgs, len(cfgs))
+    plans = [_native.Plan(g, device=local) for g in cfgs[:n_plain]]
+    for p in plans[: min(50, n_plain)]:
+        p.run(sh)
+        p.sync()
+    lat_p = []
+    t_all = time.perf_counter()
+    for p in plans:
+        t0 = time.perf_counter()
+        p.run(sh)
+        p.sync()
+        lat_p.append(1e3 * (time.perf_counter() - t0))
+    t_all = time.perf_counter() - t_all
+    # and all plans enqueued back to back, one wait at the end
+    torch.cuda.synchronize()
+    t_async = time.perf_counter()
+    for p in plans:
+        p.run(sh)
+    torch.cuda.synchronize()
+    t_async = time.perf_counter() - t_async
+    plain_launches = sum(p.launches for p in plans)
+    for p in plans:
+        p.close()
+    # ---- end to end: ompdart_analyze_batch with host buffers
+    t0 = time.perf_counter()
+    res, st = _native.analyze_batch(cfgs, device=local)
+    e2e_s = time.perf_counter() - t0
+    h2d = sum(r["h2d_bytes"] for r in res if r is not None)
+    d2h = sum(r["d2h_bytes"] for r in res if r is not None)
+    del res
+    # ---- CPU oracle on a bounded sample of the same CFGs
+    import oracle
+    oracle.build()
+    t_cpu, n_cpu, u_cpu = 0.0, 0, 0
+    for g in cfgs[:: max(1, len(cfgs) // 400)]:
+        t0 = time.perf_counter()
+        oracle.solve(g, want=["h_in", "d_in", "to_edge", "from_edge", "from_exit", "acc_flag"])
+        t_cpu += time.perf_counter() - t0
+        n_cpu += 1
+        u_cpu += g.n_blocks * g.W
+        if t_cpu > args.cpu_seconds:
+            break
+    value = units * args.steps / (ms / 1e3)
+    cps = len(cfgs) * args.steps / (ms / 1e3)
+    if rank != 0:
+        return None
+    return {
+        "metric": "block·var-word updates/s to fixed point; CFGs/s and p50/p99 vs per-CFG launch",
+        "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "batched: %d independent CFGs, blocks lognormal (median 512, clipped 16-65536), "
+                               "variables uniform in {64, 256, 1024, 2048}, seed %d" % (len(cfgs), args.batch_seed),
+                   "n_cfgs": len(cfgs), "blocks": int(sum(g.n_blocks for g in cfgs)), "block_words": int(units),
+                   "accesses": int(sum(g.n_acc for g in cfgs)), "arenas": info["arenas"], "solo_plans": info["solo"],
+                   "autotuned": bool(args.tune),
+                   "l2": "no flush: the arenas' state planes (%.1f GB) are larger than the 126 MB L2"
+                         % (3 * 8 * units / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "cfgs_per_s": cps,
+        "batch_latency_ms": {"p50": percentile(lat_b, 50), "p99": percentile(lat_b, 99),
+                             "device_p50": percentile(step_ms, 50), "device_p99": percentile(step_ms, 99),
+                             "note": "every CFG of a batch completes with the batch"},
+        "plain_per_cfg": {"cfgs": n_plain, "cfgs_per_s": n_plain / t_all, "p50_ms": percentile(lat_p, 50),
+                          "p99_ms": percentile(lat_p, 99), "max_ms": max(lat_p),
+                          "enqueued_back_to_back_cfgs_per_s": n_plain / t_async,
+                          "launches_per_pass": plain_launches,
+                          "form": "one ompdart_plan per CFG: plan_run + plan_sync per CFG (latency = their wall time)"},
+        "speedup_vs_plain": cps / (n_plain / t_all),
+        "host_seconds": {"generate": t_gen, "batch_create": t_create},
+        "cpu_baseline": {"value": u_cpu / t_cpu, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "cfgs_per_s": n_cpu / t_cpu,
+                         "sample": "%d CFGs (every %d-th), single-threaded C oracle, %.1f s"
+                                   % (n_cpu, max(1, len(cfgs) // 400), t_cpu), "cpu": cpu_info()},
+        "e2e": {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "seconds_per_step": e2e_s, "cfgs_per_s": len(cfgs) / e2e_s,
+                "path": "ompdart_analyze_batch: host ingestion + copies + solve + copy back"},
+        "gpu_launches": info["launches"] * args.steps,
+        "clocks": clk,
+    }
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle, as it stands, on the host cores, on
     a bounded sample of the same workload (a few word columns per step)."""
@@ -339,10 +480,22 @@ def main():
                     help="positions per chunk of the scan solver (0 = the library's choice)")
     ap.add_argument("--n-blocks", type=int, default=1 << 20,
                     help="blocks of the workload (smaller only for profiler captures)")
+    ap.add_argument("--workload", choices=["single", "batch"], default="single")
+    ap.add_argument("--n-cfgs", type=int, default=10000, help="CFGs of the batch workload")
+    ap.add_argument("--batch-seed", type=int, default=3)
+    ap.add_argument("--tune", type=int, default=1, help="batch: autotune the arenas' launch shapes")
+    ap.add_argument("--plain-cfgs", type=int, default=0,
+                    help="batch: CFGs timed in the one-plan-per-CFG form (0 = all)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
-    out = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.impl == "reference":
+        out = run_reference(args)
+    elif args.workload == "batch":
+        out = run_batch(args)
+    else:
+        out = run_ours(args)
     if out is not None:
         print(json.dumps(out))
 

@@ -238,7 +238,9 @@ void ompdart_batch_destroy(ompdart_batch *batch);
 
 /* One call: batch, run, copy every CFG's outputs to host memory.
    outs[n] receives library-owned results (NULL for a CFG whose status is
-   an error); status[n] (may be NULL) as for ompdart_batch_sync. */
+   an error); status[n] (may be NULL) as for ompdart_batch_sync.  Each
+   result's h2d_bytes / d2h_bytes is its share (by blocks) of its arena's
+   copies. */
 int ompdart_analyze_batch(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts *opts, ompdart_result **outs,
                           int32_t *status);
 

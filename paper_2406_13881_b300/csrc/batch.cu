@@ -193,7 +193,7 @@ double time_core(PlanCore *c, cudaStream_t s, int reps) {
 }
 
 // Pick (chunk_target, wpc) for an arena of `members`: coordinate search
-// over chunk targets at 4 warps per CTA, then over warps per CTA at the
+// over chunk targets (16..512) at 4 warps per CTA, then over warps per CTA at the
 // best target, each candidate a trial arena over a sample of about 2^18
 // positions (every step-th CFG), timed on the device.
 void tune_arena(Arena *a, const std::vector<int32_t> &members, std::vector<Ingest> &ing, const ompdart_cfg *cfgs,
@@ -224,7 +224,7 @@ void tune_arena(Arena *a, const std::vector<int32_t> &members, std::vector<Inges
   };
   int best_chunk = 128, best_wpc = 4;
   double best = 1e30;
-  for (int chunk : {64, 128, 256, 512}) {
+  for (int chunk : {16, 32, 64, 128, 256, 512}) {
     const double t = trial(chunk, 4);
     if (t < best) {
       best = t;
@@ -549,11 +549,15 @@ int ompdart_analyze_batch(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts
     rc = result_copy(whole, true, B->last_stream, &host);
     if (rc) return rc;
     const size_t W = a.W;
+    const double blocks = std::max(1, a.blk_off.back());
     for (size_t k = 0; k < a.members.size(); ++k) {
       const int i = a.members[k];
       if (B->run_status[i]) continue;
       ompdart_result v;
       arena_view(a, (int)k, &v);
+      // this CFG's share of the arena's host<->device copies
+      const double share = (a.blk_off[k + 1] - a.blk_off[k]) / blocks;
+      const long long h2d = (long long)(share * v.h2d_bytes), d2h = (long long)(share * host->d2h_bytes);
       const size_t b0 = (size_t)a.blk_off[k] * W;
       v.h_in = host->h_in + b0;
       v.d_in = host->d_in + b0;
@@ -566,6 +570,8 @@ int ompdart_analyze_batch(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts
       v.from_exit = host->from_exit + (size_t)a.x_off[k] * W;
       rc = result_copy(v, false, nullptr, &outs[i]);
       if (rc) break;
+      outs[i]->h2d_bytes = h2d;
+      outs[i]->d2h_bytes = d2h;
     }
     ompdart_result_free(host);
     if (rc) return rc;
