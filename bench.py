@@ -438,6 +438,86 @@ def run_batch(args):
     }
 
 
+def serve_pool(seed, n_small, n_large, large_blocks):
+    """Request pool of the serving workload: batch-shaped CFGs (lognormal
+    blocks, 64-2048 variables) and a few single-large-shaped CFGs (same
+    generator parameters, `large_blocks` blocks, 4096 variables)."""
+    from paper_2406_13881_b300 import workload as wl
+    small = wl.batch(seed, n_cfgs=n_small)
+    large = [wl.single_large(seed + 100 + k, n_blocks=large_blocks) for k in range(n_large)]
+    return small, large
+
+
+def run_serve(args):
+    """Poisson request streams through the serving loop at several arrival
+    rates, beside the plain form (one plan and launch sequence per request)."""
+    import numpy as np
+    import torch
+    from paper_2406_13881_b300 import _native, build
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(local)
+    build.build()
+    small, large = serve_pool(args.batch_seed, args.pool, 2, args.large_blocks)
+    rng = np.random.default_rng(args.batch_seed)
+
+    def draw(n):
+        pick_large = rng.random(n) < args.large_frac
+        cfgs = [large[rng.integers(len(large))] if pl else small[rng.integers(len(small))] for pl in pick_large]
+        return cfgs
+
+    def one(rate, n, max_batch, max_inflight):
+        cfgs = draw(n)
+        arrival = np.cumsum(rng.exponential(1e6 / rate, size=n))
+        srv = _native.Server(hbm_budget_bytes=args.budget_gb << 30, max_batch=max_batch,
+                             max_inflight=max_inflight, device=local)
+        t0 = time.perf_counter()
+        tickets = srv.replay(cfgs, arrival)
+        t_sub = time.perf_counter() - t0
+        srv.drain()
+        wall = time.perf_counter() - t0
+        lats, fails = [], 0
+        for t in tickets:
+            st, lat, _ = srv.wait(t, want_result=False)
+            lats.append(lat)
+            fails += st != 0
+        stats = srv.stats()
+        srv.close()
+        units = sum(g.n_blocks * g.W for g in cfgs)
+        return {"rate_req_s": rate, "requests": n, "offered_req_s": n / (arrival[-1] / 1e6),
+                "submitted_req_s": n / t_sub, "cfgs_per_s": n / wall, "updates_per_s": units / wall,
+                "p50_ms": percentile(lats, 50), "p99_ms": percentile(lats, 99), "max_ms": max(lats),
+                "failed": int(fails), "batches": stats["batches"], "mean_batch": stats["mean_batch"],
+                "peak_device_bytes": stats["peak_bytes"], "wall_s": wall}
+
+    # warm the library (first CUDA context, pool) outside the measurements
+    one(1000, 50, 4096, 2)
+    served, plain = [], []
+    for rate in args.rates:
+        n = int(min(args.max_requests, max(200, rate * args.seconds)))
+        served.append(one(rate, n, 4096, args.inflight))
+        plain.append(one(rate, int(min(n, args.plain_requests)), 1, 1))
+    top = served[-1]
+    if rank != 0:
+        return None
+    return {
+        "metric": "block·var-word updates/s to fixed point; CFGs/s and p50/p99 vs per-CFG launch",
+        "value": top["updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": len(args.rates), "warmup": 1,
+        "ms_per_step": 1e3 * top["wall_s"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "serving: Poisson request streams of batch-shaped CFGs (lognormal blocks, median 512; "
+                               "64-2048 variables) with %.1f%% single-large-shaped CFGs (%d blocks, 4096 variables)"
+                               % (100 * args.large_frac, args.large_blocks),
+                   "pool": {"small": len(small), "large": len(large)}, "rates_req_s": args.rates,
+                   "hbm_budget_gb": args.budget_gb, "max_inflight": args.inflight,
+                   "parallelism": "single GPU"},
+        "served": served,
+        "plain_per_cfg": plain,
+        "note": "value = updates/s completed at the highest rate; latency = submission to result on the host",
+    }
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle, as it stands, on the host cores, on
     a bounded sample of the same workload (a few word columns per step)."""
@@ -480,7 +560,16 @@ def main():
                     help="positions per chunk of the scan solver (0 = the library's choice)")
     ap.add_argument("--n-blocks", type=int, default=1 << 20,
                     help="blocks of the workload (smaller only for profiler captures)")
-    ap.add_argument("--workload", choices=["single", "batch"], default="single")
+    ap.add_argument("--workload", choices=["single", "batch", "serve"], default="single")
+    ap.add_argument("--rates", type=lambda x: [int(v) for v in x.split(",")], default=[1000, 10000, 100000])
+    ap.add_argument("--seconds", type=float, default=2.0, help="serve: seconds of arrivals per rate")
+    ap.add_argument("--max-requests", type=int, default=100000)
+    ap.add_argument("--plain-requests", type=int, default=1500)
+    ap.add_argument("--pool", type=int, default=2000)
+    ap.add_argument("--large-frac", type=float, default=0.002)
+    ap.add_argument("--large-blocks", type=int, default=1 << 16)
+    ap.add_argument("--budget-gb", type=int, default=40)
+    ap.add_argument("--inflight", type=int, default=2)
     ap.add_argument("--n-cfgs", type=int, default=10000, help="CFGs of the batch workload")
     ap.add_argument("--batch-seed", type=int, default=3)
     ap.add_argument("--tune", type=int, default=1, help="batch: autotune the arenas' launch shapes")
@@ -494,6 +583,8 @@ def main():
         out = run_reference(args)
     elif args.workload == "batch":
         out = run_batch(args)
+    elif args.workload == "serve":
+        out = run_serve(args)
     else:
         out = run_ours(args)
     if out is not None:

@@ -244,6 +244,65 @@ void ompdart_batch_destroy(ompdart_batch *batch);
 int ompdart_analyze_batch(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts *opts, ompdart_result **outs,
                           int32_t *status);
 
+/* ---- serving: continuous batching of analysis requests -----------------
+   (no paper counterpart: the paper's tool runs once per translation unit;
+   this is the request loop of a service that analyses CFGs as they
+   arrive.)  A worker thread admits pending requests in arrival order into
+   batches (ompdart_batch_*) while at most max_inflight batches are on the
+   GPU and the estimated device bytes of all admitted work stay within
+   hbm_budget_bytes; a batch is ingested and uploaded while earlier ones
+   run and is launched on its own stream, so batches overlap on the device.
+   When a batch finishes, its results are copied to the host, its device
+   memory is released and the next pending requests are admitted.
+   A serving batch runs once, so its kernels are launched directly (no
+   graph capture).  max_batch = 1 is the plain form: one plan and one
+   launch sequence per request. */
+typedef struct ompdart_server ompdart_server;
+typedef struct {
+  int64_t hbm_budget_bytes; /* device bytes admitted work may hold; 0 = 40 GiB     */
+  int32_t max_batch;        /* CFGs per batch; 0 = 4096                             */
+  int32_t max_inflight;     /* batches on the GPU at once; 0 = 2                    */
+  int32_t device;           /* CUDA device ordinal                                  */
+  int32_t keep_results;     /* nonzero: copy each result to the host for the waiter */
+  ompdart_opts opts;        /* analysis options of every batch                      */
+} ompdart_server_opts;
+
+typedef struct {
+  int64_t submitted, completed, failed, batches;
+  double mean_batch;               /* CFGs per batch                              */
+  double p50_ms, p99_ms, max_ms;   /* latency: submission to result on the host   */
+  int64_t peak_bytes, bytes_in_use; /* device bytes held by admitted batches       */
+} ompdart_server_stats;
+
+int ompdart_server_create(const ompdart_server_opts *opts, ompdart_server **server);
+
+/* Queue one CFG (copied; the caller may reuse its buffers) and return its
+   ticket at once.  Malformed CFGs are reported by the wait (status). */
+int ompdart_server_submit(ompdart_server *server, const ompdart_cfg *cfg, int64_t *ticket);
+
+/* Submit cfgs[i] at arrival_us[i] microseconds after the call (a load
+   generator for capacity tests: sleeps and spins on the host clock); the
+   tickets go to tickets[n].  Returns when the last one is submitted. */
+int ompdart_server_replay(ompdart_server *server, const ompdart_cfg *cfgs, int32_t n, const double *arrival_us,
+                          int64_t *tickets);
+
+/* Wait up to timeout_ms (< 0: no limit) for a ticket: its status, its
+   latency (submission to result on the host) and, if out is not NULL and
+   keep_results was set, its result (caller-owned, ompdart_result_free).
+   OMPDART_E_TIMEOUT if it is not done in time (the ticket stays valid);
+   a collected ticket is forgotten.  For a failed request, the calling
+   thread's ompdart_last_error() says why. */
+int ompdart_server_wait(ompdart_server *server, int64_t ticket, int32_t timeout_ms, ompdart_result **out,
+                        int32_t *status, double *latency_ms);
+
+/* Wait until every submitted request is done (OMPDART_E_TIMEOUT after
+   timeout_ms, < 0: no limit). */
+int ompdart_server_drain(ompdart_server *server, int32_t timeout_ms);
+int ompdart_server_get_stats(ompdart_server *server, ompdart_server_stats *out);
+
+/* Finish every submitted request, then stop the worker and free all. */
+void ompdart_server_destroy(ompdart_server *server);
+
 /* Liveness of one CFG, allocating nothing (no paper counterpart: an
    addition for callers that cannot allocate device memory, for instance
    code running inside another runtime's memory pool, or that must not

@@ -6,11 +6,11 @@ only).  ``workload`` draws the seeded synthetic CFGs.
 """
 from . import workload  # noqa: F401
 
-__all__ = ["workload", "analyze", "analyze_batch", "Plan", "Batch", "OmpdartError"]
+__all__ = ["workload", "analyze", "analyze_batch", "Plan", "Batch", "Server", "OmpdartError"]
 
 
 def __getattr__(name):
-    if name in ("analyze", "analyze_batch", "Plan", "Batch", "OmpdartError", "load"):
+    if name in ("analyze", "analyze_batch", "Plan", "Batch", "Server", "OmpdartError", "load"):
         from . import _native
         return getattr(_native, name)
     raise AttributeError(name)

@@ -64,6 +64,18 @@ class Result(C.Structure):
                 ("live_in", C.c_void_p)]
 
 
+class ServerOpts(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_int64), ("max_batch", C.c_int32), ("max_inflight", C.c_int32),
+                ("device", C.c_int32), ("keep_results", C.c_int32), ("opts", Opts)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
+                ("batches", C.c_int64), ("mean_batch", C.c_double), ("p50_ms", C.c_double),
+                ("p99_ms", C.c_double), ("max_ms", C.c_double), ("peak_bytes", C.c_int64),
+                ("bytes_in_use", C.c_int64)]
+
+
 class Timing(C.Structure):
     _fields_ = [("name", C.c_char_p), ("launches", C.c_int32), ("ms", C.c_double)]
 
@@ -93,6 +105,14 @@ EXPORTS = {
     "ompdart_batch_destroy": (None, [C.c_void_p]),
     "ompdart_analyze_batch": (C.c_int, [C.POINTER(Cfg), C.c_int32, C.POINTER(Opts),
                                         C.POINTER(C.POINTER(Result)), C.c_void_p]),
+    "ompdart_server_create": (C.c_int, [C.POINTER(ServerOpts), C.POINTER(C.c_void_p)]),
+    "ompdart_server_submit": (C.c_int, [C.c_void_p, C.POINTER(Cfg), C.POINTER(C.c_int64)]),
+    "ompdart_server_replay": (C.c_int, [C.c_void_p, C.POINTER(Cfg), C.c_int32, C.c_void_p, C.c_void_p]),
+    "ompdart_server_wait": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.POINTER(C.POINTER(Result)),
+                                      C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
+    "ompdart_server_drain": (C.c_int, [C.c_void_p, C.c_int32]),
+    "ompdart_server_get_stats": (C.c_int, [C.c_void_p, C.POINTER(ServerStats)]),
+    "ompdart_server_destroy": (None, [C.c_void_p]),
     "ompdart_liveness_noalloc": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
 }
@@ -347,3 +367,64 @@ def analyze_batch(cfgs, **opts):
             if outs[i]:
                 lib.ompdart_result_free(outs[i])
     return res, st[: inp.n]
+
+
+class Server:
+    """The serving loop (``ompdart_server_*``): ``submit`` queues a CFG and
+    returns its ticket, ``wait`` returns (status, latency ms, result dict or
+    None), ``replay`` submits many CFGs at given arrival times."""
+
+    def __init__(self, hbm_budget_bytes=0, max_batch=0, max_inflight=0, device=0, keep_results=True, **opts):
+        self._lib = load()
+        so = ServerOpts(int(hbm_budget_bytes), int(max_batch), int(max_inflight), int(device),
+                        int(bool(keep_results)), _opts(device=device, **opts))
+        self._h = C.c_void_p()
+        self._keep = []
+        _check(self._lib.ompdart_server_create(C.byref(so), C.byref(self._h)))
+
+    def submit(self, cfg) -> int:
+        inp = _Inputs(cfg)
+        t = C.c_int64()
+        _check(self._lib.ompdart_server_submit(self._h, C.byref(inp.c), C.byref(t)))
+        return t.value
+
+    def replay(self, cfgs, arrival_us) -> np.ndarray:
+        """Submit cfgs[i] at arrival_us[i] microseconds from now (native
+        timing loop; releases the GIL)."""
+        bi = _BatchInputs(cfgs)
+        arr = np.ascontiguousarray(arrival_us, dtype=np.float64)
+        tickets = np.zeros(max(1, bi.n), dtype=np.int64)
+        _check(self._lib.ompdart_server_replay(self._h, bi.arr, bi.n, arr.ctypes.data, tickets.ctypes.data))
+        return tickets[: bi.n]
+
+    def wait(self, ticket, timeout_ms=-1, want_result=True):
+        res = C.POINTER(Result)()
+        st, lat = C.c_int32(), C.c_double()
+        _check(self._lib.ompdart_server_wait(self._h, int(ticket), int(timeout_ms),
+                                             C.byref(res) if want_result else None, C.byref(st), C.byref(lat)))
+        out = None
+        if want_result and res:
+            try:
+                out = _result_to_numpy(res.contents)
+            finally:
+                self._lib.ompdart_result_free(res)
+        return st.value, lat.value, out
+
+    def drain(self, timeout_ms=-1):
+        _check(self._lib.ompdart_server_drain(self._h, int(timeout_ms)))
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(self._lib.ompdart_server_get_stats(self._h, C.byref(s)))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if self._h:
+            self._lib.ompdart_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

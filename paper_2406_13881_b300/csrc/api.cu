@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -40,9 +41,33 @@ int cuda_err(cudaError_t e, const char *what) {
 // ==================================================================================
 namespace ompdart {
 
+void pool_setup() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess) return;
+    for (int d = 0; d < n; ++d) {
+      cudaMemPool_t pool;
+      if (cudaDeviceGetDefaultMemPool(&pool, d) != cudaSuccess) continue;
+      uint64_t keep = ~0ull;  // this process's pool keeps freed memory for reuse
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+  });
+}
+
 PlanCore::~PlanCore() {
   if (scan) scan_destroy(scan);
-  for (void *p : allocs) cudaFree(p);
+  for (void *p : allocs) dev_free(p);
+}
+
+long long estimate_device_bytes(const ompdart_cfg &c, int keep_states) {
+  const long long N = c.n_blocks, W = (c.n_vars + 63) / 64;
+  const long long E = c.succ_off ? c.succ_off[N] : 0, A = c.acc_off ? c.acc_off[N] : 0;
+  const long long planes = (3 + (keep_states ? 2 : 0)) * N * W * 8;
+  const long long meta = N * (64 + 6 * 4) + E * (2 * 8 + 5 * 4) + A * (4 * 3 + 1);
+  const long long chunks = (N / 16 + 1) * W * 8 * 6;  // chunk maps and carries
+  const long long xfer = (N / 4 + 64) * 2 * 24 + (N / 8 + 8) * W * 8 * 4;
+  return planes + meta + chunks + xfer + (1 << 16);
 }
 
 void boundary_rows(const ompdart_cfg *cfg, int W, std::vector<uint64_t> *top, std::vector<uint64_t> *eh,
@@ -164,6 +189,13 @@ int core_build(PlanCore *P, const int32_t *acc_off, const uint32_t *acc, const s
     *err = "device allocation failed";
     return OMPDART_E_NOMEM;
   }
+  // the pool allocations are ordered on this thread's default stream: let
+  // them complete before any other stream uses them
+  if (cudaStreamSynchronize(cudaStreamPerThread) != cudaSuccess) {
+    *err = "device allocation failed";
+    return OMPDART_E_NOMEM;
+  }
+  if (P->scan) P->dev_bytes += scan_device_bytes(P->scan);
   return OMPDART_OK;
 }
 
@@ -197,7 +229,8 @@ int core_finish(PlanCore *P, cudaStream_t s, int32_t *h_status, bool *rerun) {
     // the record buffer overflowed: enlarge it and redo the edge emission
     const int need = nrec + nrec / 4 + 16;
     EdgeXfer *x = P->dalloc<EdgeXfer>((size_t)need);
-    if (!x) return set_err(OMPDART_E_NOMEM, "device allocation of transfer records failed");
+    if (!x || cudaStreamSynchronize(cudaStreamPerThread) != cudaSuccess)
+      return set_err(OMPDART_E_NOMEM, "device allocation of transfer records failed");
     P->dp.xfer = x;
     P->dp.xfer_cap = need;
     *rerun = true;
@@ -298,6 +331,9 @@ struct ompdart_plan {
   int32_t *h_status = nullptr;  // pinned
   Prof prof;
   ~ompdart_plan() {
+    // the plan's memory goes back to the pool: its last run must be done
+    if (last_stream) cudaStreamSynchronize(last_stream);
+    if (stream) cudaStreamSynchronize(stream);
     if (stream) cudaStreamDestroy(stream);
     if (h_status) cudaFreeHost(h_status);
   }
@@ -356,6 +392,7 @@ int ompdart_plan_run(ompdart_plan *P, void *stream) {
   if (!P) return set_err(OMPDART_E_INVALID, "plan is NULL");
   cudaStream_t s = stream ? (cudaStream_t)stream : P->stream;
   P->last_stream = s;
+  (void)cudaGetLastError();  // clear a stale "not ready" of an earlier query
   Prof *pf = P->prof.on ? &P->prof : nullptr;
   if (pf) pf->collect_pending = true;
   P->launches = core_enqueue(&P->core, s, pf);

@@ -38,8 +38,8 @@ struct Arena {
   std::vector<int32_t> blk_off, acc_base, x_off, chunk_beg;  // [members + 1]
   std::vector<int32_t> n_vars, n_edges;                      // [members]
   int32_t *exit_local = nullptr;  // device [X]: exit blocks as ids local to their CFG
-  int32_t *h_status = nullptr;    // pinned [ST_COUNT]
-  int32_t *h_err = nullptr;       // pinned [members]
+  int32_t *h_status = nullptr;    // host [ST_COUNT]
+  int32_t *h_err = nullptr;       // host [members]
   std::vector<int32_t> rec_off;   // [members + 1] gathered record range per CFG
   int rec_run = -1;               // run whose records rec_off describes
 };
@@ -47,7 +47,7 @@ struct Arena {
 struct Solo {  // a CFG on a plan of its own
   PlanCore core;
   int32_t member = -1;
-  int32_t *h_status = nullptr;  // pinned [ST_COUNT]
+  int32_t *h_status = nullptr;  // host [ST_COUNT]
 };
 
 struct Where {
@@ -77,7 +77,7 @@ struct ompdart_batch {
   std::vector<Where> where;
   std::vector<std::unique_ptr<Arena>> arenas;
   std::vector<std::unique_ptr<Solo>> solos;
-  std::vector<void *> pinned;
+  std::vector<std::unique_ptr<int32_t[]>> host;
   cudaStream_t stream = nullptr, last_stream = nullptr;
   std::vector<cudaStream_t> side;  // one per plan, at most kSide
   cudaEvent_t fork = nullptr;
@@ -89,12 +89,11 @@ struct ompdart_batch {
   int runs = 0;
   bool ran = false;
 
-  int32_t *pinned_ints(size_t n) {
-    void *p = nullptr;
-    if (cudaMallocHost(&p, std::max<size_t>(n, 1) * sizeof(int32_t)) != cudaSuccess) return nullptr;
-    memset(p, 0, std::max<size_t>(n, 1) * sizeof(int32_t));
-    pinned.push_back(p);
-    return static_cast<int32_t *>(p);
+  // host status words (pageable: a batch is created and destroyed often by
+  // the serving loop, and freeing pinned memory can wait for the device)
+  int32_t *host_ints(size_t n) {
+    host.emplace_back(new (std::nothrow) int32_t[std::max<size_t>(n, 1)]());
+    return host.back().get();
   }
   void drop_graph() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -104,10 +103,13 @@ struct ompdart_batch {
     graph_ok = false;
   }
   ~ompdart_batch() {
+    // the arenas' memory goes back to the pool: every run must be done
+    if (last_stream) cudaStreamSynchronize(last_stream);
+    for (cudaStream_t s : side) cudaStreamSynchronize(s);
+    if (stream) cudaStreamSynchronize(stream);
     drop_graph();
     arenas.clear();
     solos.clear();
-    for (void *p : pinned) cudaFreeHost(p);
     for (cudaStream_t s : side) cudaStreamDestroy(s);
     for (cudaEvent_t e : join) cudaEventDestroy(e);
     if (fork) cudaEventDestroy(fork);
@@ -366,9 +368,9 @@ int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts 
     if (o.tune) tune_arena(a.get(), kv.second, ing, cfgs, o, B->stream);
     int rc = build_arena(a.get(), kv.second, ing, cfgs, o, &err);
     if (rc) return set_error(rc, err);
-    a->h_status = B->pinned_ints(ST_COUNT);
-    a->h_err = B->pinned_ints(a->members.size());
-    if (!a->h_status || !a->h_err) return set_error(OMPDART_E_NOMEM, "pinned host allocation failed");
+    a->h_status = B->host_ints(ST_COUNT);
+    a->h_err = B->host_ints(a->members.size());
+    if (!a->h_status || !a->h_err) return set_error(OMPDART_E_NOMEM, "host allocation failed");
     const int idx = (int)B->arenas.size();
     for (size_t k = 0; k < a->members.size(); ++k) B->where[a->members[k]] = Where{1, idx, (int)k};
     for (int m : kv.second) ing[m] = Ingest();  // the arena holds the concatenation
@@ -385,8 +387,8 @@ int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts 
     os.path = 1;
     int rc = core_build(&p->core, cfgs[i].acc_off, cfgs[i].acc, top, eh, ed, xl, 1, {}, os, &err);
     if (rc) return set_error(rc, err);
-    p->h_status = B->pinned_ints(ST_COUNT);
-    if (!p->h_status) return set_error(OMPDART_E_NOMEM, "pinned host allocation failed");
+    p->h_status = B->host_ints(ST_COUNT);
+    if (!p->h_status) return set_error(OMPDART_E_NOMEM, "host allocation failed");
     B->where[i] = Where{2, (int)B->solos.size(), 0};
     B->solos.push_back(std::move(p));
   }
@@ -412,6 +414,9 @@ int ompdart_batch_run(ompdart_batch *B, void *stream) {
   if (!B) return set_error(OMPDART_E_INVALID, "batch is NULL");
   cudaStream_t s = stream ? (cudaStream_t)stream : B->stream;
   B->last_stream = s;
+  // start from a clean per-thread error state: a query that answered "not
+  // ready" (a poll of an earlier run) leaves that code behind
+  (void)cudaGetLastError();
   cudaError_t ce;
   if (B->arenas.empty() && B->solos.empty()) {  // nothing to run (empty batch, or every CFG rejected)
     B->launches = 0;
@@ -537,6 +542,25 @@ int ompdart_analyze_batch(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts
   rc = ompdart_batch_run(B, nullptr);
   if (!rc) rc = ompdart_batch_sync(B, status);
   if (rc) return rc;
+  return batch_fetch_all(B, outs);
+}
+
+}  // extern "C"
+
+namespace ompdart {
+
+cudaStream_t batch_stream(const ompdart_batch *B) { return B->stream; }
+
+long long batch_device_bytes(const ompdart_batch *B) {
+  long long b = 0;
+  for (auto &a : B->arenas) b += a->core.dev_bytes;
+  for (auto &p : B->solos) b += p->core.dev_bytes;
+  return b;
+}
+
+int batch_fetch_all(ompdart_batch *B, ompdart_result **outs) {
+  int rc = OMPDART_OK;
+  for (int i = 0; i < B->n; ++i) outs[i] = nullptr;
   // bulk copies: every arena's arrays in one piece, then split per CFG
   for (auto &ap : B->arenas) {
     Arena &a = *ap;
@@ -584,4 +608,4 @@ int ompdart_analyze_batch(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts
   return OMPDART_OK;
 }
 
-}  // extern "C"
+}  // namespace ompdart

@@ -11,6 +11,23 @@
 
 namespace ompdart {
 
+// Device memory of plans comes from the stream-ordered allocator (the
+// device's default memory pool, allocations and frees ordered on the
+// calling thread's default stream): freeing a finished plan does not
+// synchronise the device, so other plans' kernels keep running.  Callers
+// synchronise cudaStreamPerThread before another stream touches new
+// memory, and free only memory no stream still uses.
+void pool_setup();  // once per process: keep freed pool memory for reuse
+inline void *dev_malloc(size_t bytes) {
+  pool_setup();
+  void *p = nullptr;
+  if (cudaMallocAsync(&p, bytes ? bytes : 1, cudaStreamPerThread) != cudaSuccess) return nullptr;
+  return p;
+}
+inline void dev_free(void *p) {
+  if (p) cudaFreeAsync(p, cudaStreamPerThread);
+}
+
 // Plain struct of device pointers, passed by value to every kernel.
 // Planes are row-major [rows][W] uint64, rows indexed by block id unless
 // stated otherwise.

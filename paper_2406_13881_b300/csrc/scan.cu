@@ -165,14 +165,17 @@ struct ScanState {
   int32_t *offs = nullptr;         // stream offsets in the gathered result
   uint64_t *init = nullptr;        // [W] stale set entering the first chunk
   EdgeXfer *stream_buf = nullptr;
+  long long bytes = 0;  // device bytes held
   ~ScanState() {
-    for (void *p : allocs) cudaFree(p);
+    for (void *p : allocs) dev_free(p);
   }
   template <class T>
   T *alloc(size_t n) {
-    void *p = nullptr;
-    if (cudaMalloc(&p, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) return nullptr;
+    const size_t b = std::max<size_t>(n, 1) * sizeof(T);
+    void *p = dev_malloc(b);
+    if (!p) return nullptr;
     allocs.push_back(p);
+    bytes += (long long)b;
     return (T *)p;
   }
   template <class T>
@@ -1405,12 +1408,13 @@ static bool scan_set_streams(ScanState *st) {
     tot += st->h_rec_cap[i];
   }
   if (tot >= (1ll << 31)) return false;
-  if (st->stream_buf) {
-    cudaFree(st->stream_buf);
+  if (st->stream_buf) {  // the buffer's last user (a finished run) is done
+    dev_free(st->stream_buf);
+    st->bytes -= (long long)sizeof(EdgeXfer) * std::max<long long>(st->total_cap, 1);
     st->allocs.erase(std::find(st->allocs.begin(), st->allocs.end(), (void *)st->stream_buf));
   }
   st->stream_buf = st->alloc<EdgeXfer>((size_t)tot);
-  if (!st->stream_buf) return false;
+  if (!st->stream_buf || cudaStreamSynchronize(cudaStreamPerThread) != cudaSuccess) return false;
   st->total_cap = tot;
   st->sd.stream = st->stream_buf;
   if (cudaMemcpy(st->d_rec_cap, st->h_rec_cap.data(), sizeof(int32_t) * st->n_streams, cudaMemcpyHostToDevice) !=
@@ -1433,7 +1437,10 @@ ChainShape chain_shape(K kern, int need, int np, bool acc, int wpc, int n_items,
   c.wpc = wpc;
   c.sh_slots = std::min(need, SH_WORDS / (64 * np));
   c.smem = (size_t)wpc * warp_smem_words(c.sh_slots, np, acc) * 8;
-  set_smem(kern, c.smem);
+  // the attribute belongs to the kernel, not to this plan: always the
+  // largest size any plan launches with (8 warps, every slot in shared
+  // memory), so plans alive at the same time never shrink it for each other
+  set_smem(kern, (size_t)8 * warp_smem_words(SH_WORDS / (64 * np), np, acc) * 8);
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpc, c.smem) != cudaSuccess || per_sm < 1)
     per_sm = 1;
@@ -1525,8 +1532,10 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   }
   int max_warps = 1;
   for (const ChainShape &c : st->shape) max_warps = std::max(max_warps, c.grid * c.wpc);
-  const int max_slots = std::max(st->fslots, st->bslots);
-  sd.spill_stride = max_slots * 4 * 64;  // worst case: every slot of 4 planes spilled
+  // slots beyond those a kernel keeps in shared memory (at least
+  // SH_WORDS / 128 of them, 2 planes at most) spill to a per-warp area
+  const int max_slots = std::max(st->fslots, st->bslots), min_sh = SH_WORDS / (64 * 2);
+  sd.spill_stride = std::max(1, max_slots - min_sh) * 2 * 64;
   chk(sd.spill = st->alloc<uint64_t>((size_t)std::max(1, sd.spill_stride) * max_warps));
   chk(sd.gsum = st->alloc<uint64_t>((size_t)2 * C * W));
   chk(sd.psum = st->alloc<uint64_t>((size_t)2 * C * W));
@@ -1681,5 +1690,7 @@ bool scan_chunk_record_offsets(const ScanState *st, cudaStream_t s, std::vector<
 void scan_destroy(ScanState *st) { delete st; }
 
 long long scan_h2d_bytes(const ScanState *st) { return st ? st->h2d : 0; }
+
+long long scan_device_bytes(const ScanState *st) { return st ? st->bytes : 0; }
 
 }  // namespace ompdart

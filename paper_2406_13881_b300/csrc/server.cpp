@@ -1,0 +1,374 @@
+// server.cpp -- the serving loop (ompdart_server_*): continuous batching of
+// analysis requests over the batched analysis, admitted by a device-memory
+// budget.
+//
+// One worker thread owns the GPU side.  Each turn it
+//   1. retires batches whose completion event fired: per-CFG status, host
+//      copies of the results, the batch's device memory back to the pool
+//      and to the budget, latencies recorded, waiters woken;
+//   2. admits pending requests in arrival order into a new batch while the
+//      number of batches on the GPU is below max_inflight, the batch is
+//      below max_batch CFGs and the estimated device bytes of everything
+//      admitted stay within the budget (a request larger than the whole
+//      budget fails with OMPDART_E_BUDGET); the batch is ingested and
+//      uploaded on the host while earlier batches run, then launched on its
+//      own stream, so batches overlap on the device.
+// Submitting copies the request, so callers may reuse their buffers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/ompdart.h"
+#include "solver.h"
+
+using namespace ompdart;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+  int64_t id = 0;
+  std::vector<int32_t> so, su, ao;
+  std::vector<uint32_t> acc;
+  std::vector<uint64_t> eh, ed, xl, calls;
+  ompdart_cfg cfg{};
+  long long est = 0;
+  Clock::time_point t_submit, t_done;
+  int status = OMPDART_OK;
+  std::string err;  // why it failed
+  ompdart_result *res = nullptr;
+  bool done = false;
+};
+using ReqPtr = std::shared_ptr<Request>;
+
+struct InFlight {
+  ompdart_batch *b = nullptr;
+  std::vector<ReqPtr> reqs;
+  long long bytes = 0;
+  cudaEvent_t ev = nullptr;
+};
+
+double ms_between(Clock::time_point a, Clock::time_point b) {
+  return std::chrono::duration<double, std::milli>(b - a).count();
+}
+
+}  // namespace
+
+struct ompdart_server {
+  ompdart_server_opts o{};
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<ReqPtr> pending;
+  std::map<int64_t, ReqPtr> live;  // submitted and not yet collected by a wait
+  std::vector<InFlight> inflight;  // worker thread only
+  int n_inflight = 0;              // guarded by mu (for drain)
+  std::thread worker;
+  bool stop = false;
+  int64_t next_id = 1;
+  long long bytes_in_use = 0, peak_bytes = 0;
+  int64_t submitted = 0, completed = 0, failed = 0, batches = 0, batched_cfgs = 0;
+  std::vector<double> lat_ms;
+};
+
+namespace {
+
+void finish_request(ompdart_server *S, const ReqPtr &r, int status, ompdart_result *res, Clock::time_point now,
+                    const std::string &err = std::string()) {
+  r->status = status;
+  r->err = err;
+  r->res = res;
+  r->t_done = now;
+  r->done = true;
+  S->lat_ms.push_back(ms_between(r->t_submit, now));
+  if (status == OMPDART_OK)
+    ++S->completed;
+  else
+    ++S->failed;
+}
+
+// Retire a batch whose work is done (the event fired or failed).
+void retire(ompdart_server *S, InFlight &f, cudaError_t q) {
+  const size_t n = f.reqs.size();
+  std::vector<int32_t> st(n, OMPDART_OK);
+  std::vector<ompdart_result *> outs(n, nullptr);
+  int rc = q == cudaSuccess ? ompdart_batch_sync(f.b, st.data())
+                            : set_error(OMPDART_E_CUDA, std::string("batch run: ") + cudaGetErrorString(q));
+  if (!rc && S->o.keep_results) rc = batch_fetch_all(f.b, outs.data());
+  const std::string err = rc ? ompdart_last_error() : "";
+  ompdart_batch_destroy(f.b);
+  cudaEventDestroy(f.ev);
+  const Clock::time_point now = Clock::now();
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->bytes_in_use -= f.bytes;
+  --S->n_inflight;
+  for (size_t k = 0; k < n; ++k) {
+    if (rc && outs[k]) {
+      ompdart_result_free(outs[k]);
+      outs[k] = nullptr;
+    }
+    const int code = rc ? rc : st[k];
+    finish_request(S, f.reqs[k], code, outs[k], now, rc ? err : code ? "the CFG was rejected or did not converge" : "");
+  }
+  S->cv_done.notify_all();
+}
+
+// Build and launch one batch of admitted requests (reserved: their estimate).
+void launch(ompdart_server *S, std::vector<ReqPtr> &take, long long reserved) {
+  const int n = (int)take.size();
+  std::vector<ompdart_cfg> cfgs(n);
+  for (int k = 0; k < n; ++k) cfgs[k] = take[k]->cfg;
+  std::vector<int32_t> st(n, OMPDART_OK);
+  ompdart_batch *b = nullptr;
+  int rc = ompdart_batch_create(cfgs.data(), n, &S->o.opts, &b, st.data());
+  cudaEvent_t ev = nullptr;
+  if (!rc) rc = ompdart_batch_run(b, nullptr);
+  if (!rc && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) rc = OMPDART_E_CUDA;
+  if (!rc && cudaEventRecord(ev, batch_stream(b)) != cudaSuccess) rc = OMPDART_E_CUDA;
+  if (rc) {
+    const std::string err = ompdart_last_error();
+    if (ev) cudaEventDestroy(ev);
+    if (b) ompdart_batch_destroy(b);
+    const Clock::time_point now = Clock::now();
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->bytes_in_use -= reserved;
+    --S->n_inflight;
+    for (int k = 0; k < n; ++k) finish_request(S, take[k], rc, nullptr, now, err);
+    S->cv_done.notify_all();
+    return;
+  }
+  const long long actual = batch_device_bytes(b);
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->bytes_in_use += actual - reserved;  // charge what the batch really holds
+    S->peak_bytes = std::max(S->peak_bytes, S->bytes_in_use);
+    ++S->batches;
+    S->batched_cfgs += n;
+  }
+  InFlight f;
+  f.b = b;
+  f.reqs = std::move(take);
+  f.bytes = actual;
+  f.ev = ev;
+  S->inflight.push_back(std::move(f));
+}
+
+void worker_main(ompdart_server *S) {
+  cudaSetDevice(S->o.device);
+  for (;;) {
+    bool progressed = false;
+    for (size_t i = 0; i < S->inflight.size();) {
+      const cudaError_t q = cudaEventQuery(S->inflight[i].ev);
+      if (q == cudaErrorNotReady) {
+        (void)cudaGetLastError();  // "not ready" is an answer, not an error
+        ++i;
+        continue;
+      }
+      retire(S, S->inflight[i], q);
+      S->inflight.erase(S->inflight.begin() + (long)i);
+      progressed = true;
+    }
+    std::vector<ReqPtr> take;
+    long long est = 0;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      if (S->stop && S->pending.empty() && S->inflight.empty()) break;
+      const Clock::time_point now = Clock::now();
+      if ((int)S->inflight.size() < S->o.max_inflight) {
+        while (!S->pending.empty() && (int)take.size() < S->o.max_batch) {
+          const ReqPtr r = S->pending.front();
+          if (r->est > S->o.hbm_budget_bytes) {  // can never fit
+            S->pending.pop_front();
+            finish_request(S, r, OMPDART_E_BUDGET, nullptr, now,
+                           "the request needs more device memory than the whole budget");
+            S->cv_done.notify_all();
+            continue;
+          }
+          if (S->bytes_in_use + est + r->est > S->o.hbm_budget_bytes) break;
+          est += r->est;
+          take.push_back(r);
+          S->pending.pop_front();
+        }
+        if (!take.empty()) {
+          S->bytes_in_use += est;
+          ++S->n_inflight;
+        }
+      }
+      if (take.empty() && !progressed) {
+        if (S->inflight.empty())
+          S->cv_work.wait(lk, [&] { return S->stop || !S->pending.empty(); });
+        else
+          S->cv_work.wait_for(lk, std::chrono::microseconds(20));
+        continue;
+      }
+    }
+    if (!take.empty()) launch(S, take, est);
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int ompdart_server_create(const ompdart_server_opts *opts, ompdart_server **out) {
+  set_last_error_text("");
+  if (!out) return set_error(OMPDART_E_INVALID, "server output pointer is NULL");
+  *out = nullptr;
+  ompdart_server *S = new (std::nothrow) ompdart_server();
+  if (!S) return set_error(OMPDART_E_NOMEM, "host allocation failed");
+  if (opts) S->o = *opts;
+  if (S->o.hbm_budget_bytes <= 0) S->o.hbm_budget_bytes = 40ll << 30;
+  if (S->o.max_batch <= 0) S->o.max_batch = 4096;
+  if (S->o.max_inflight <= 0) S->o.max_inflight = 2;
+  S->o.opts.device = S->o.device;
+  // a serving batch runs once: capturing it into a graph would cost more
+  // than it saves, so its kernels are launched directly
+  S->o.opts.no_graph = 1;
+  if (cudaSetDevice(S->o.device) != cudaSuccess) {
+    delete S;
+    return set_error(OMPDART_E_CUDA, "cudaSetDevice failed");
+  }
+  S->worker = std::thread(worker_main, S);
+  *out = S;
+  return OMPDART_OK;
+}
+
+int ompdart_server_submit(ompdart_server *S, const ompdart_cfg *c, int64_t *ticket) {
+  if (!S || !c || !ticket) return set_error(OMPDART_E_INVALID, "NULL argument");
+  if (c->n_blocks < 1 || !c->succ_off || !c->acc_off || c->n_vars < 1)
+    return set_error(OMPDART_E_INVALID, "malformed CFG header");
+  ReqPtr r = std::make_shared<Request>();
+  const int N = c->n_blocks, W = (c->n_vars + 63) / 64;
+  const int E = c->succ_off[N], A = c->acc_off[N];
+  if (E < 0 || A < 0 || (E && !c->succ) || (A && !c->acc)) return set_error(OMPDART_E_INVALID, "malformed CSR");
+  r->so.assign(c->succ_off, c->succ_off + N + 1);
+  r->su.assign(c->succ, c->succ + E);
+  r->ao.assign(c->acc_off, c->acc_off + N + 1);
+  r->acc.assign(c->acc, c->acc + A);
+  if (c->entry_host_valid) r->eh.assign(c->entry_host_valid, c->entry_host_valid + W);
+  if (c->entry_dev_valid) r->ed.assign(c->entry_dev_valid, c->entry_dev_valid + W);
+  if (c->exit_host_live) r->xl.assign(c->exit_host_live, c->exit_host_live + W);
+  if (c->call_planes && c->n_calls > 0) r->calls.assign(c->call_planes, c->call_planes + (size_t)c->n_calls * 7 * W);
+  r->cfg = *c;
+  r->cfg.succ_off = r->so.data();
+  r->cfg.succ = r->su.data();
+  r->cfg.acc_off = r->ao.data();
+  r->cfg.acc = r->acc.data();
+  r->cfg.entry_host_valid = c->entry_host_valid ? r->eh.data() : nullptr;
+  r->cfg.entry_dev_valid = c->entry_dev_valid ? r->ed.data() : nullptr;
+  r->cfg.exit_host_live = c->exit_host_live ? r->xl.data() : nullptr;
+  r->cfg.call_planes = r->calls.empty() ? nullptr : r->calls.data();
+  r->est = estimate_device_bytes(r->cfg, S->o.opts.keep_states);
+  std::lock_guard<std::mutex> lk(S->mu);
+  if (S->stop) return set_error(OMPDART_E_INVALID, "server is shutting down");
+  r->id = S->next_id++;
+  r->t_submit = Clock::now();
+  S->pending.push_back(r);
+  S->live[r->id] = r;
+  ++S->submitted;
+  *ticket = r->id;
+  S->cv_work.notify_one();
+  return OMPDART_OK;
+}
+
+int ompdart_server_replay(ompdart_server *S, const ompdart_cfg *cfgs, int32_t n, const double *arrival_us,
+                          int64_t *tickets) {
+  if (!S || (n > 0 && (!cfgs || !arrival_us || !tickets))) return set_error(OMPDART_E_INVALID, "NULL argument");
+  const Clock::time_point t0 = Clock::now();
+  for (int i = 0; i < n; ++i) {
+    const Clock::time_point due = t0 + std::chrono::duration_cast<Clock::duration>(
+                                           std::chrono::duration<double, std::micro>(arrival_us[i]));
+    while (Clock::now() < due) {
+      const auto left = due - Clock::now();
+      if (left > std::chrono::microseconds(200)) std::this_thread::sleep_for(left - std::chrono::microseconds(100));
+    }
+    tickets[i] = -1;
+    const int rc = ompdart_server_submit(S, &cfgs[i], &tickets[i]);
+    if (rc) return rc;
+  }
+  return OMPDART_OK;
+}
+
+int ompdart_server_wait(ompdart_server *S, int64_t ticket, int32_t timeout_ms, ompdart_result **out,
+                        int32_t *status, double *latency_ms) {
+  if (!S) return set_error(OMPDART_E_INVALID, "server is NULL");
+  if (out) *out = nullptr;
+  std::unique_lock<std::mutex> lk(S->mu);
+  auto it = S->live.find(ticket);
+  if (it == S->live.end()) return set_error(OMPDART_E_INVALID, "unknown or already collected ticket");
+  ReqPtr r = it->second;
+  const auto pred = [&] { return r->done; };
+  if (timeout_ms < 0)
+    S->cv_done.wait(lk, pred);
+  else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred))
+    return set_error(OMPDART_E_TIMEOUT, "the request is not done yet");
+  if (status) *status = r->status;
+  if (latency_ms) *latency_ms = ms_between(r->t_submit, r->t_done);
+  set_last_error_text(r->err);  // why the request failed, for ompdart_last_error
+  if (out)
+    *out = r->res;
+  else if (r->res)
+    ompdart_result_free(r->res);
+  r->res = nullptr;
+  S->live.erase(it);
+  return OMPDART_OK;
+}
+
+int ompdart_server_drain(ompdart_server *S, int32_t timeout_ms) {
+  if (!S) return set_error(OMPDART_E_INVALID, "server is NULL");
+  std::unique_lock<std::mutex> lk(S->mu);
+  const auto pred = [&] { return S->pending.empty() && S->n_inflight == 0; };
+  if (timeout_ms < 0)
+    S->cv_done.wait(lk, pred);
+  else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred))
+    return set_error(OMPDART_E_TIMEOUT, "requests still pending");
+  return OMPDART_OK;
+}
+
+int ompdart_server_get_stats(ompdart_server *S, ompdart_server_stats *out) {
+  if (!S || !out) return set_error(OMPDART_E_INVALID, "NULL argument");
+  std::lock_guard<std::mutex> lk(S->mu);
+  memset(out, 0, sizeof *out);
+  out->submitted = S->submitted;
+  out->completed = S->completed;
+  out->failed = S->failed;
+  out->batches = S->batches;
+  out->mean_batch = S->batches ? (double)S->batched_cfgs / S->batches : 0.0;
+  out->peak_bytes = S->peak_bytes;
+  out->bytes_in_use = S->bytes_in_use;
+  std::vector<double> l = S->lat_ms;
+  if (!l.empty()) {
+    std::sort(l.begin(), l.end());
+    auto q = [&](double p) { return l[std::min(l.size() - 1, (size_t)(p * (l.size() - 1) + 0.5))]; };
+    out->p50_ms = q(0.50);
+    out->p99_ms = q(0.99);
+    out->max_ms = l.back();
+  }
+  return OMPDART_OK;
+}
+
+void ompdart_server_destroy(ompdart_server *S) {
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv_work.notify_all();
+  if (S->worker.joinable()) S->worker.join();  // finishes what was submitted
+  for (auto &kv : S->live)
+    if (kv.second->res) ompdart_result_free(kv.second->res);
+  delete S;
+}
+
+}  // extern "C"

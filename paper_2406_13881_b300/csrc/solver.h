@@ -38,6 +38,7 @@ int enqueue_scan_edges(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *pf
 // after a completed run: index of the first gathered transfer record of
 // every chunk, and `total` at index C
 bool scan_chunk_record_offsets(const ScanState *st, cudaStream_t s, std::vector<int32_t> *out, int32_t total);
+long long scan_device_bytes(const ScanState *st);
 void scan_destroy(ScanState *st);
 
 // ---- api.cu: one device plan over one CFG or a batch of CFGs of equal
@@ -53,11 +54,15 @@ struct PlanCore {
   ScanState *scan = nullptr;
   int32_t *cfg_err = nullptr;  // device [n_cfg] (scan path)
 
+  long long dev_bytes = 0;  // device bytes this core holds (with its scan state)
+
   template <class T>
   T *dalloc(size_t n) {
-    void *ptr = nullptr;
-    if (cudaMalloc(&ptr, std::max<size_t>(n, 1) * sizeof(T)) != cudaSuccess) return nullptr;
+    const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+    void *ptr = dev_malloc(bytes);
+    if (!ptr) return nullptr;
     allocs.push_back(ptr);
+    dev_bytes += (long long)bytes;
     return static_cast<T *>(ptr);
   }
   template <class T>
@@ -100,5 +105,14 @@ void core_view(const PlanCore &c, const int32_t *h_status, ompdart_result *v);
 // Copy the arrays a view points at (device memory if `device`, else host)
 // into a new host result (ompdart_result_free).
 int result_copy(const ompdart_result &v, bool device, cudaStream_t s, ompdart_result **out);
+
+// ---- batch.cu helpers for the serving loop
+// host copies of every CFG's results after ompdart_batch_sync (outs[n];
+// NULL where a CFG's status is an error)
+int batch_fetch_all(ompdart_batch *B, ompdart_result **outs);
+long long batch_device_bytes(const ompdart_batch *B);
+cudaStream_t batch_stream(const ompdart_batch *B);
+// device bytes a plan of this CFG is expected to hold (admission estimate)
+long long estimate_device_bytes(const ompdart_cfg &c, int keep_states);
 
 }  // namespace ompdart
