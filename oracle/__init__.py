@@ -55,6 +55,8 @@ _OUT_FIELDS = [
     ("d_out", "NW", np.uint64), ("hm", "NW", np.uint64), ("h_in", "NW", np.uint64),
     ("h_out", "NW", np.uint64), ("to_edge", "EW", np.uint64), ("from_edge", "EW", np.uint64),
     ("from_exit", "NW", np.uint64), ("acc_flag", "A", np.uint8),
+    ("call_to", "SW", np.uint64), ("call_from", "SW", np.uint64), ("call_entry_h", "SW", np.uint64),
+    ("call_entry_d", "SW", np.uint64), ("call_exit_live", "SW", np.uint64),
 ]
 
 
@@ -73,12 +75,48 @@ def _load():
             lib = C.CDLL(build())
             lib.oracle_solve.argtypes = [C.POINTER(_Cfg), C.POINTER(_Out)]
             lib.oracle_solve.restype = C.c_int
+            lib.oracle_summarize.argtypes = [C.POINTER(_Cfg), C.c_void_p]
+            lib.oracle_summarize.restype = C.c_int
             _lib = lib
     return _lib
 
 
 def _ptr(a):
     return None if a is None else a.ctypes.data
+
+
+def _cfg_struct(g):
+    n, nv = int(g["n_blocks"]), int(g["n_vars"])
+    W = (nv + 63) // 64
+    keep = {
+        "so": np.ascontiguousarray(g["succ_off"], dtype=np.int32),
+        "s": np.ascontiguousarray(g["succ"], dtype=np.int32),
+        "ao": np.ascontiguousarray(g["acc_off"], dtype=np.int32),
+        "acc": np.ascontiguousarray(g["acc"], dtype=np.uint32),
+    }
+    for key in ("entry_host_valid", "entry_dev_valid", "exit_host_live", "call_planes"):
+        v = g.get(key)
+        keep[key] = None if v is None else np.ascontiguousarray(v, dtype=np.uint64)
+    calls = keep["call_planes"]
+    c = _Cfg(n, nv, int(g.get("entry", 0)), _ptr(keep["so"]), _ptr(keep["s"]), _ptr(keep["ao"]),
+             _ptr(keep["acc"]), _ptr(keep["entry_host_valid"]), _ptr(keep["entry_dev_valid"]),
+             _ptr(keep["exit_host_live"]), _ptr(calls), 0 if calls is None else int(calls.size // (7 * W)))
+    return c, keep
+
+
+def summarize(cfg) -> np.ndarray:
+    """Side-effect summary of a callee in its own variable numbering:
+    [7, W] planes ReqH, ReqD, GenH, KillH, GenD, KillD, MustDef (see
+    oracle_summarize in oracle.h)."""
+    lib = _load()
+    g = cfg if isinstance(cfg, dict) else cfg.__dict__
+    W = (int(g["n_vars"]) + 63) // 64
+    c, _keep = _cfg_struct(g)
+    out = np.zeros((7, W), dtype=np.uint64)
+    rc = lib.oracle_summarize(C.byref(c), out.ctypes.data)
+    if rc != 0:
+        raise OracleError("oracle_summarize returned %d" % rc)
+    return out
 
 
 def solve(cfg, want=None) -> dict:
@@ -106,7 +144,8 @@ def solve(cfg, want=None) -> dict:
     c = _Cfg(n, nv, int(g.get("entry", 0)), _ptr(so), _ptr(s), _ptr(ao), _ptr(acc),
              _ptr(ehv), _ptr(edv), _ptr(xhl), _ptr(calls),
              0 if calls is None else int(calls.size // (7 * W)))
-    sizes = {"N": (n,), "E": (E,), "A": (A,), "NW": (n, W), "EW": (E, W)}
+    S = int(np.count_nonzero(acc >> np.uint32(31)))
+    sizes = {"N": (n,), "E": (E,), "A": (A,), "NW": (n, W), "EW": (E, W), "SW": (S, W)}
     res, ptrs = {}, {}
     want = None if want is None else set(want)
     for name, kind, dt in _OUT_FIELDS:

@@ -511,8 +511,11 @@ static int natural_loops(const graph *g, const uint64_t *KH, const uint64_t *KD,
  * the other space stale.  This covers both the transfers at the top of the
  * block (upward-exposed reads) and those after a write in the other space
  * inside the block. */
+/* call-site rows: site k = the k-th call access in access order */
+typedef struct { uint64_t *to, *from, *entry_h, *entry_d, *exit_live; } call_rows;
+
 static void access_flags(const oracle_cfg *c, const graph *g, const uint64_t *h_in, const uint64_t *d_in,
-                         uint8_t *flag) {
+                         uint8_t *flag, const int32_t *site_of, call_rows *cr) {
   int W = g->W;
   uint64_t *h = xcalloc((size_t)W, sizeof(uint64_t)), *d = xcalloc((size_t)W, sizeof(uint64_t));
   memset(flag, 0, (size_t)g->A);
@@ -523,12 +526,21 @@ static void access_flags(const oracle_cfg *c, const graph *g, const uint64_t *h_
     for (int i = g->ao[b]; i < g->ao[b + 1]; ++i) {
       uint32_t a = g->acc[i];
       if (a_is_call(a)) {
-        /* a call row needs per-variable transfers: reported through the
-           call-site planes, not this byte; replay its effect only */
+        /* the callee's requirements are met right before the call (`from'
+           for ReqH stale on the host, `to' for ReqD stale on the device),
+           then its net effect applies */
         int r = a_call_row(a);
+        size_t o = (size_t)site_of[i] * W;
         for (int w = 0; w < W; ++w) {
           uint64_t rqh = call_plane(c, W, r, 0)[w], rqd = call_plane(c, W, r, 1)[w];
+          uint64_t fr = rqh & ~h[w], to = rqd & ~d[w];
+          if (fr) flag[i] |= 2;
+          if (to) flag[i] |= 1;
           h[w] |= rqh; d[w] |= rqd;
+          if (cr->to) cr->to[o + w] = to;
+          if (cr->from) cr->from[o + w] = fr;
+          if (cr->entry_h) cr->entry_h[o + w] = h[w];
+          if (cr->entry_d) cr->entry_d[o + w] = d[w];
           h[w] = call_plane(c, W, r, 2)[w] | (h[w] & ~call_plane(c, W, r, 3)[w]);
           d[w] = call_plane(c, W, r, 4)[w] | (d[w] & ~call_plane(c, W, r, 5)[w]);
         }
@@ -543,6 +555,44 @@ static void access_flags(const oracle_cfg *c, const graph *g, const uint64_t *h_
     }
   }
   free(h); free(d);
+}
+
+/* Liveness right after each call (Live = AntH | AntD, Sec. II-B): from Live
+   at the block exit (OR of the successors' Live_in, or exit_host_live at a
+   region exit), fold the block's later accesses backward: a read in either
+   space makes the variable live, a write ends it; a call makes ReqH | ReqD
+   live after ending what it must write. */
+static void call_exit_live(const oracle_cfg *c, const graph *g, const uint64_t *LV, const uint64_t *xlive,
+                           const int32_t *site_of, uint64_t *rows) {
+  int W = g->W;
+  uint64_t *x = xcalloc((size_t)W, sizeof(uint64_t));
+  for (int b = 0; b < g->N; ++b) {
+    if (!g->reach[b]) continue;
+    int has_call = 0;
+    for (int i = g->ao[b]; i < g->ao[b + 1]; ++i) has_call |= a_is_call(g->acc[i]);
+    if (!has_call) continue;
+    if (g->so[b] == g->so[b + 1]) {
+      for (int w = 0; w < W; ++w) x[w] = xlive[w];
+    } else {
+      memset(x, 0, (size_t)W * sizeof(uint64_t));
+      for (int e = g->so[b]; e < g->so[b + 1]; ++e)
+        for (int w = 0; w < W; ++w) x[w] |= LV[(size_t)g->s[e] * W + w];
+    }
+    for (int i = g->ao[b + 1] - 1; i >= g->ao[b]; --i) {
+      uint32_t a = g->acc[i];
+      if (a_is_call(a)) {
+        int r = a_call_row(a);
+        memcpy(rows + (size_t)site_of[i] * W, x, (size_t)W * sizeof(uint64_t));
+        for (int w = 0; w < W; ++w)
+          x[w] = call_plane(c, W, r, 0)[w] | call_plane(c, W, r, 1)[w] | (x[w] & ~call_plane(c, W, r, 6)[w]);
+        continue;
+      }
+      int v = a_var(a), k = a_kind(a);
+      if (k & A_KIND_W) set_bit(x, v, 0);
+      if (k & A_KIND_R) set_bit(x, v, 1);
+    }
+  }
+  free(x);
 }
 
 int oracle_solve(const oracle_cfg *c, oracle_out *out) {
@@ -620,7 +670,21 @@ int oracle_solve(const oracle_cfg *c, oracle_out *out) {
     if (g.so[b] == g.so[b + 1])
       for (int w = 0; w < W; ++w) FX[(size_t)b * W + w] = xlive[w] & ~HO[(size_t)b * W + w];
   }
-  access_flags(c, &g, HI, DI, fl);
+  {
+    int32_t *site_of = xcalloc((size_t)g.A, sizeof(int32_t));
+    int S = 0;
+    for (int i = 0; i < g.A; ++i) site_of[i] = a_is_call(g.acc[i]) ? S++ : -1;
+    call_rows cr = {out->call_to, out->call_from, out->call_entry_h, out->call_entry_d, out->call_exit_live};
+    size_t SW = (size_t)S * W * sizeof(uint64_t);
+    if (cr.to) memset(cr.to, 0, SW);
+    if (cr.from) memset(cr.from, 0, SW);
+    if (cr.entry_h) memset(cr.entry_h, 0, SW);
+    if (cr.entry_d) memset(cr.entry_d, 0, SW);
+    if (cr.exit_live) memset(cr.exit_live, 0, SW);
+    access_flags(c, &g, HI, DI, fl, site_of, &cr);
+    if (cr.exit_live) call_exit_live(c, &g, LV, xlive, site_of, cr.exit_live);
+    free(site_of);
+  }
 
   /* copy out */
 #define CP(dst, src, n) do { if (dst) memcpy((dst), (src), (n) * sizeof(*(src))); } while (0)
@@ -642,6 +706,68 @@ int oracle_solve(const oracle_cfg *c, oracle_out *out) {
 done:
   for (int i = 0; i < 26; ++i) free(pl[i]);
   free(hdr); free(ent); free(TE); free(FE); free(fl); free(init_h); free(init_d); free(xlive);
+  free_graph(&g);
+  return rc;
+}
+
+/* ---- callee summaries (Sec. IV-C side effects) ----------------------------
+ * Requirements: anticipation at the entry with nothing live after the exit.
+ * Net effects: plain validity (the local rule along paths, no transfers)
+ * from an all-stale and from an all-valid entry, met over the reachable
+ * exits.  Must-writes: forward must problem "written so far", met over the
+ * reachable exits. */
+int oracle_summarize(const oracle_cfg *c, uint64_t *planes) {
+  int rc = validate(c);
+  if (rc) return rc;
+  graph g;
+  if ((rc = build_graph(c, &g))) { free_graph(&g); return rc; }
+  int N = g.N, W = g.W;
+  size_t NW = (size_t)N * W;
+  uint64_t *pl[14];
+  for (int i = 0; i < 14; ++i) pl[i] = xcalloc(NW, sizeof(uint64_t));
+  uint64_t *zero = xcalloc((size_t)W, sizeof(uint64_t)), *nokill = pl[13];
+  uint64_t *GH = pl[0], *KH = pl[1], *GD = pl[2], *KD = pl[3], *UH = pl[4], *UD = pl[5], *DF = pl[6];
+  uint64_t *AH = pl[7], *AD = pl[8], *XI = pl[9], *XO = pl[10];
+  local_rule(c, &g, GH, KH, GD, KD, UH, UD, DF);
+  memset(planes, 0, (size_t)7 * W * sizeof(uint64_t));
+  if ((rc = anticipation(&g, UH, DF, NULL, AH)) || (rc = anticipation(&g, UD, DF, NULL, AD))) goto done;
+  for (int w = 0; w < W; ++w) {
+    planes[0 * W + w] = AH[(size_t)g.entry * W + w];
+    planes[1 * W + w] = AD[(size_t)g.entry * W + w];
+  }
+  {
+    int n_exit = 0;
+    for (int b = 0; b < N; ++b) n_exit += g.reach[b] && g.so[b] == g.so[b + 1];
+    if (!n_exit) { rc = ORACLE_OK; goto done; }
+    /* met over exits: Gen = AND of valid (entry all stale); Kill = OR of
+       stale (entry all valid); MustDef = AND of written (entry nothing) */
+    const uint64_t *gens[2] = {GH, GD}, *kills[2] = {KH, KD};
+    for (int S = 0; S < 2; ++S) {
+      fwd_problem P0 = {gens[S], kills[S], zero, NULL, NULL, NULL, NULL, XI, XO, NULL};
+      if ((rc = forward_must(&g, &P0))) goto done;
+      uint64_t *gen = planes + (size_t)(2 + 2 * S) * W, *kill = planes + (size_t)(3 + 2 * S) * W;
+      for (int w = 0; w < W; ++w) gen[w] = g.top[w];
+      for (int b = 0; b < N; ++b)
+        if (g.reach[b] && g.so[b] == g.so[b + 1])
+          for (int w = 0; w < W; ++w) gen[w] &= XO[(size_t)b * W + w];
+      fwd_problem P1 = {gens[S], kills[S], g.top, NULL, NULL, NULL, NULL, XI, XO, NULL};
+      if ((rc = forward_must(&g, &P1))) goto done;
+      for (int b = 0; b < N; ++b)
+        if (g.reach[b] && g.so[b] == g.so[b + 1])
+          for (int w = 0; w < W; ++w) kill[w] |= g.top[w] & ~XO[(size_t)b * W + w];
+    }
+    fwd_problem PM = {DF, nokill, zero, NULL, NULL, NULL, NULL, XI, XO, NULL};
+    if ((rc = forward_must(&g, &PM))) goto done;
+    uint64_t *md = planes + (size_t)6 * W;
+    for (int w = 0; w < W; ++w) md[w] = g.top[w];
+    for (int b = 0; b < N; ++b)
+      if (g.reach[b] && g.so[b] == g.so[b + 1])
+        for (int w = 0; w < W; ++w) md[w] &= XO[(size_t)b * W + w];
+  }
+  rc = ORACLE_OK;
+done:
+  for (int i = 0; i < 14; ++i) free(pl[i]);
+  free(zero);
   free_graph(&g);
   return rc;
 }

@@ -75,10 +75,31 @@ typedef struct {
   uint64_t *d_in, *d_out, *hm, *h_in, *h_out;    /* [N*W] */
   uint64_t *to_edge, *from_edge;                 /* [E*W] */
   uint64_t *from_exit;                           /* [N*W], rows of exits */
-  uint8_t *acc_flag;                             /* [A]: 0, 1 = to, 2 = from */
+  uint8_t *acc_flag;                             /* [A]: 0, 1 = to, 2 = from;
+                                                    a call: 1 | 2 as needed */
+  /* call sites, numbered by access index order (S = number of call
+     accesses; rows of calls in unreachable blocks stay zero): */
+  uint64_t *call_to, *call_from;                 /* [S*W] transfers right before the call */
+  uint64_t *call_entry_h, *call_entry_d;         /* [S*W] validity the callee starts from */
+  uint64_t *call_exit_live;                      /* [S*W] Live (AntH | AntD) right after it */
 } oracle_out;
 
 int oracle_solve(const oracle_cfg *cfg, oracle_out *out);
+
+/* Side-effect summary of a callee (Sec. IV-C: per function, which data it
+   reads or writes on the host or the device), in the callee's own variable
+   numbering, written to planes[7*W] in the order
+     ReqH    AntH at the entry with nothing live after the exit: read on the
+             host before any write on some path;
+     ReqD    the same on the device;
+     GenH    valid on the host at every reachable exit whatever held at the
+             entry (plain validity: the local rule along paths, no transfers);
+     KillH   stale on the host at some reachable exit although valid
+             everywhere at the entry;
+     GenD, KillD  the same for the device;
+     MustDef written on every path from the entry to a reachable exit.
+   A callee with no reachable exit gets all-zero Gen/Kill/MustDef. */
+int oracle_summarize(const oracle_cfg *callee, uint64_t *planes);
 
 
 #ifdef __cplusplus

@@ -41,6 +41,14 @@ int cuda_err(cudaError_t e, const char *what) {
 // ==================================================================================
 namespace ompdart {
 
+bool trace_on() {
+  static const bool on = [] {
+    const char *e = std::getenv("OMPDART_TRACE");
+    return e && *e && *e != '0';
+  }();
+  return on;
+}
+
 void pool_setup() {
   static std::once_flag once;
   std::call_once(once, [] {
@@ -84,6 +92,7 @@ void boundary_rows(const ompdart_cfg *cfg, int W, std::vector<uint64_t> *top, st
 int core_build(PlanCore *P, const int32_t *acc_off, const uint32_t *acc, const std::vector<uint64_t> &top,
                const std::vector<uint64_t> &eh, const std::vector<uint64_t> &ed, const std::vector<uint64_t> &xl,
                int n_cfg, const std::vector<int32_t> &unreach_cfg, const ompdart_opts &o, std::string *err) {
+  TraceScope trace("core_build", P->g.M);
   const Ingest &g = P->g;
   P->keep_states = o.keep_states;
   const int W = g.W;

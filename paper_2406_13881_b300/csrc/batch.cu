@@ -128,6 +128,7 @@ int build_arena(Arena *a, const std::vector<int32_t> &members, std::vector<Inges
   std::vector<const Ingest *> parts;
   parts.reserve(members.size());
   for (int m : members) parts.push_back(&ing[m]);
+  TraceScope trace_cat("arena concat", (long long)members.size());
   concat_ingests(parts, &a->core.g);
   const int W = a->core.g.W;
   a->W = W;
@@ -155,6 +156,7 @@ int build_arena(Arena *a, const std::vector<int32_t> &members, std::vector<Inges
     a->acc_base.push_back((int32_t)acc.size());
     a->x_off.push_back(a->x_off.back() + (int32_t)g.exit_blocks.size());
   }
+  trace_cat.next("arena core", (long long)members.size());
   ompdart_opts oa = o;
   oa.path = 2;
   oa.chunk_target = a->chunk_target;
@@ -324,6 +326,7 @@ int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts 
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming);
   if (ce != cudaSuccess) return set_error(OMPDART_E_CUDA, std::string("CUDA setup: ") + cudaGetErrorString(ce));
   // ---- ingestion, one CFG per task
+  TraceScope trace_ingest("batch ingest", n);
   std::vector<Ingest> ing(n);
   B->ingest_status.assign(n, OMPDART_OK);
   B->where.assign(n, Where{});
@@ -349,6 +352,7 @@ int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts 
     work();
     for (auto &t : pool) t.join();
   }
+  trace_ingest.next("batch arenas", n);
   // ---- grouping
   std::map<int, std::vector<int32_t>> by_w;
   std::vector<int32_t> solo_ids;

@@ -30,6 +30,7 @@
 
 #include "ingest.h"
 #include "plan.cuh"
+#include "solver.h"
 
 namespace ompdart {
 
@@ -1461,11 +1462,13 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   // short chunks give more independent walks (one warp each); 128
   // positions was the fastest target on the 2^20-block CFG
   if (chunk_target <= 0) chunk_target = g.M <= 2048 ? std::max(32, g.M / 8) : 128;
+  TraceScope trace_bm("scan build_meta", g.M);
   if (!build_meta(g, chunk_target, st, meta, loops, chunks, csrc, fin_slot, out_slot, out_pos, lat_slot, bend_loop,
                   srcent, err)) {
     delete st;
     return nullptr;
   }
+  trace_bm.next("scan uploads", g.M);
   // accesses in position order, and each position's first access there
   std::vector<uint32_t> acc_p;
   acc_p.reserve(g.A);

@@ -2,7 +2,9 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <chrono>
 #include <cstdint>
+#include <cstdio>
 #include <string>
 #include <vector>
 
@@ -11,6 +13,32 @@
 #include "plan.cuh"
 
 namespace ompdart {
+
+// ---- host-side tracing: with OMPDART_TRACE=1 in the environment, phases
+// of plan and batch construction print their wall time to stderr
+bool trace_on();
+struct TraceScope {
+  const char *name;
+  long long n;
+  std::chrono::steady_clock::time_point t0;
+  explicit TraceScope(const char *nm, long long count = -1)
+      : name(nm), n(count), t0(std::chrono::steady_clock::now()) {}
+  // report the phase so far and start the next one
+  void next(const char *nm, long long count = -1) {
+    report();
+    name = nm;
+    n = count;
+    t0 = std::chrono::steady_clock::now();
+  }
+  ~TraceScope() { report(); }
+
+ private:
+  void report() const {
+    if (!trace_on()) return;
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    std::fprintf(stderr, "[ompdart] %-22s %9.3f ms  (%lld)\n", name, ms, n);
+  }
+};
 
 // ---- api.cu: thread-local error text of ompdart_last_error
 void set_last_error_text(const std::string &msg);
