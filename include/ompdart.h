@@ -44,6 +44,22 @@
  *       words with a nonzero transfer appear.
  *   exit_blocks [n_exits], from_exit [n_exits*W]: `from' at the end of each
  *       reachable block without successors (region exit liveness).
+ *   Call sites (Sec. IV-C), one per call pseudo-access in access order:
+ *       call_to / call_from [n_call_sites*W]: the callee's requirements met
+ *       right before the call (ReqD stale on the device -> `to', ReqH stale
+ *       on the host -> `from'); acc_flag of the call access is 1 | 2 as
+ *       either is nonzero; call_entry_h / call_entry_d: the validity the
+ *       callee starts from (the context for its own analysis);
+ *       call_exit_live: variables live (read in either space before being
+ *       written) right after the call.
+ *
+ * CALLS
+ *   A call pseudo-access applies row r of the call table: requirements
+ *   first (ReqH / ReqD: the callee reads them there before writing them),
+ *   then the net effect (GenS valid, else KillS stale, else unchanged;
+ *   MustDef ends liveness), as ompdart_summarize_callee computes them.  CFGs
+ *   with calls take the chunked scan solver (reducible CFG, loop bodies
+ *   contiguous in loop order); others return OMPDART_E_INVALID.
  *
  * ERRORS
  *   Every call returns OMPDART_OK (0) or a negative code; the text of the
@@ -129,6 +145,11 @@ typedef struct {
                                   variables the host or the device may read
                                   before they are written, from the block entry
                                   on (Sec. II-B); zero for unreachable blocks   */
+  int32_t n_call_sites;        /* call pseudo-accesses (see CALLS)             */
+  int32_t *call_site_acc;      /* [n_call_sites] access index of each          */
+  uint64_t *call_to, *call_from;          /* [n_call_sites*n_words]            */
+  uint64_t *call_entry_h, *call_entry_d;  /* [n_call_sites*n_words]            */
+  uint64_t *call_exit_live;               /* [n_call_sites*n_words]            */
 } ompdart_result;
 
 typedef struct ompdart_plan ompdart_plan;

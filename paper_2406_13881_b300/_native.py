@@ -61,7 +61,9 @@ class Result(C.Structure):
                 ("n_edge_xfers", C.c_int32), ("edge_xfers", C.c_void_p),
                 ("exit_blocks", C.c_void_p), ("from_exit", C.c_void_p), ("path", C.c_int32),
                 ("sweeps", C.c_int32), ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64),
-                ("live_in", C.c_void_p)]
+                ("live_in", C.c_void_p), ("n_call_sites", C.c_int32), ("call_site_acc", C.c_void_p),
+                ("call_to", C.c_void_p), ("call_from", C.c_void_p), ("call_entry_h", C.c_void_p),
+                ("call_entry_d", C.c_void_p), ("call_exit_live", C.c_void_p)]
 
 
 class ServerOpts(C.Structure):
@@ -194,6 +196,10 @@ def _result_to_numpy(r: Result) -> dict:
         out["d_out"] = arr(r.d_out, n * W, np.uint64, (n, W))
     if r.live_in:
         out["live_in"] = arr(r.live_in, n * W, np.uint64, (n, W))
+    S = r.n_call_sites
+    out["call_site_acc"] = arr(r.call_site_acc, S, np.int32)
+    for k in ("call_to", "call_from", "call_entry_h", "call_entry_d", "call_exit_live"):
+        out[k] = arr(getattr(r, k), S * W, np.uint64, (S, W))
     return out
 
 

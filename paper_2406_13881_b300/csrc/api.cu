@@ -89,9 +89,10 @@ void boundary_rows(const ompdart_cfg *cfg, int W, std::vector<uint64_t> *top, st
   }
 }
 
-int core_build(PlanCore *P, const int32_t *acc_off, const uint32_t *acc, const std::vector<uint64_t> &top,
-               const std::vector<uint64_t> &eh, const std::vector<uint64_t> &ed, const std::vector<uint64_t> &xl,
-               int n_cfg, const std::vector<int32_t> &unreach_cfg, const ompdart_opts &o, std::string *err) {
+int core_build(PlanCore *P, const int32_t *acc_off, const uint32_t *acc, const CallHost &calls,
+               const std::vector<uint64_t> &top, const std::vector<uint64_t> &eh, const std::vector<uint64_t> &ed,
+               const std::vector<uint64_t> &xl, int n_cfg, const std::vector<int32_t> &unreach_cfg,
+               const ompdart_opts &o, std::string *err) {
   TraceScope trace("core_build", P->g.M);
   const Ingest &g = P->g;
   P->keep_states = o.keep_states;
@@ -160,6 +161,51 @@ int core_build(PlanCore *P, const int32_t *acc_off, const uint32_t *acc, const s
     *err = "device allocation failed";
     return OMPDART_E_NOMEM;
   }
+  // ---- call sites (Sec. IV-C): every call access; the reachable blocks holding them
+  {
+    std::vector<int32_t> site_acc, cblk, cblk_site0, cblk_rowbase, cblk_cfg;
+    for (int b = 0; b < g.N; ++b) {
+      int first = -1;
+      for (int i = acc_off[b]; i < acc_off[b + 1]; ++i)
+        if (acc[i] >> 31) {
+          if (first < 0) first = (int)site_acc.size();
+          site_acc.push_back(i);
+        }
+      if (first < 0 || g.pos[b] < 0) continue;
+      const int cfg = (int)(std::upper_bound(g.cfg_pos_off.begin(), g.cfg_pos_off.end(), g.pos[b]) -
+                            g.cfg_pos_off.begin()) - 1;
+      cblk.push_back(b);
+      cblk_site0.push_back(first);
+      cblk_rowbase.push_back(calls.row_base.empty() ? 0 : calls.row_base[cfg]);
+      cblk_cfg.push_back(cfg);
+    }
+    d.n_sites = (int)site_acc.size();
+    d.n_cblk = (int)cblk.size();
+    if (d.n_sites) {
+      if (!scan_supported(g) || o.path == 1) {
+        *err = "CFGs with call pseudo-accesses need the chunked scan solver (a reducible CFG whose loop bodies "
+               "are contiguous in loop order)";
+        return OMPDART_E_INVALID;
+      }
+      const size_t SW = (size_t)d.n_sites * W;
+      chk(d.calls = P->upload(calls.planes, (size_t)calls.rows * 7 * W));
+      chk(d.site_acc = P->upload(site_acc));
+      chk(d.cblk = P->upload(cblk));
+      chk(d.cblk_site0 = P->upload(cblk_site0));
+      chk(d.cblk_rowbase = P->upload(cblk_rowbase));
+      chk(d.cblk_cfg = P->upload(cblk_cfg));
+      chk(d.call_to = P->dalloc<uint64_t>(SW));
+      chk(d.call_from = P->dalloc<uint64_t>(SW));
+      chk(d.call_entry_h = P->dalloc<uint64_t>(SW));
+      chk(d.call_entry_d = P->dalloc<uint64_t>(SW));
+      chk(d.call_exit_live = P->dalloc<uint64_t>(SW));
+      if (!ok) {
+        *err = "device allocation failed";
+        return OMPDART_E_NOMEM;
+      }
+    }
+    P->site_acc = std::move(site_acc);
+  }
   int want = o.path;
   if (want == 0) want = scan_supported(g) ? 2 : 1;
   if (want == 2 && !scan_supported(g)) {
@@ -186,7 +232,8 @@ int core_build(PlanCore *P, const int32_t *acc_off, const uint32_t *acc, const s
       *err = "device allocation failed";
       return OMPDART_E_NOMEM;
     }
-    P->scan = scan_create(g, acc_off, acc, P->cfg_err, d, o.chunk_target, o.keep_states, err, o.warps_per_cta);
+    P->scan = scan_create(g, acc_off, acc, calls, P->cfg_err, d, o.chunk_target, o.keep_states, err,
+                          o.warps_per_cta);
     if (!P->scan) return OMPDART_E_NOMEM;
   }
   // transfer records: start with room for a few per loop-entry edge and
@@ -215,7 +262,7 @@ int core_enqueue(PlanCore *P, cudaStream_t s, Prof *pf) {
   if (P->path == 1)
     n += enqueue_local_summary(P->dp, s, pf) + enqueue_sweep_solver(P->dp, s, P->n_fin, pf);
   else
-    n += enqueue_scan_solver(P->scan, P->dp, s, pf);
+    n += enqueue_scan_solver(P->scan, P->dp, s, pf) + enqueue_call_sites(P->dp, s, pf);
   n += enqueue_fill_unreachable(P->dp, s, P->keep_states, pf);
   return n;
 }
@@ -274,6 +321,13 @@ void core_view(const PlanCore &P, const int32_t *h_status, ompdart_result *v) {
   v->h2d_bytes = P.h2d + scan_h2d_bytes(P.scan);
   v->d2h_bytes = 0;
   v->live_in = P.keep_states ? P.dp.live : nullptr;
+  v->n_call_sites = P.dp.n_sites;
+  v->call_site_acc = const_cast<int32_t *>(P.dp.site_acc);
+  v->call_to = P.dp.call_to;
+  v->call_from = P.dp.call_from;
+  v->call_entry_h = P.dp.call_entry_h;
+  v->call_entry_d = P.dp.call_entry_d;
+  v->call_exit_live = P.dp.call_exit_live;
 }
 
 int result_copy(const ompdart_result &v, bool device, cudaStream_t s, ompdart_result **out) {
@@ -292,8 +346,17 @@ int result_copy(const ompdart_result &v, bool device, cudaStream_t s, ompdart_re
   r->exit_blocks = (int32_t *)malloc(sizeof(int32_t) * ((size_t)v.n_exits + 1));
   r->from_exit = (uint64_t *)malloc(8 * ((size_t)v.n_exits * v.n_words + 1));
   r->live_in = v.live_in ? (uint64_t *)malloc(NW * 8 + 8) : nullptr;
+  const size_t SW = (size_t)v.n_call_sites * v.n_words;
+  r->call_site_acc = (int32_t *)malloc(sizeof(int32_t) * ((size_t)v.n_call_sites + 1));
+  uint64_t **crows[5] = {&r->call_to, &r->call_from, &r->call_entry_h, &r->call_entry_d, &r->call_exit_live};
+  const uint64_t *csrc[5] = {v.call_to, v.call_from, v.call_entry_h, v.call_entry_d, v.call_exit_live};
+  bool rows_ok = r->call_site_acc != nullptr;
+  for (int k = 0; k < 5; ++k) {
+    *crows[k] = (uint64_t *)malloc(8 * (SW + 1));
+    rows_ok = rows_ok && *crows[k];
+  }
   bool ok = r->h_in && r->d_in && (!v.h_out || r->h_out) && (!v.d_out || r->d_out) && r->acc_flag &&
-            r->edge_xfers && r->exit_blocks && r->from_exit && (!v.live_in || r->live_in);
+            r->edge_xfers && r->exit_blocks && r->from_exit && (!v.live_in || r->live_in) && rows_ok;
   cudaError_t ce = cudaSuccess;
   auto cp = [&](void *dst, const void *src, size_t n) {
     if (!ok || !n) return;
@@ -311,10 +374,12 @@ int result_copy(const ompdart_result &v, bool device, cudaStream_t s, ompdart_re
   cp(r->exit_blocks, v.exit_blocks, sizeof(int32_t) * (size_t)v.n_exits);
   cp(r->from_exit, v.from_exit, 8 * (size_t)v.n_exits * v.n_words);
   if (v.live_in) cp(r->live_in, v.live_in, NW * 8);
+  cp(r->call_site_acc, v.call_site_acc, sizeof(int32_t) * (size_t)v.n_call_sites);
+  for (int k = 0; k < 5; ++k) cp(*crows[k], csrc[k], 8 * SW);
   if (device && ok && ce == cudaSuccess) ce = cudaStreamSynchronize(s);
   r->d2h_bytes = device ? (long long)(2 + (v.h_out ? 2 : 0) + (v.live_in ? 1 : 0)) * NW * 8 + v.n_acc +
                               (long long)sizeof(ompdart_edge_xfer) * v.n_edge_xfers + 4ll * v.n_exits +
-                              8ll * v.n_exits * v.n_words + 4ll * ST_COUNT
+                              8ll * v.n_exits * v.n_words + 4ll * ST_COUNT + 4ll * v.n_call_sites + 40ll * SW
                         : 0;
   if (!ok || ce != cudaSuccess) {
     ompdart_result_free(r);
@@ -366,11 +431,6 @@ int ompdart_plan_create(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdar
     delete P;
     return set_err(rc, err);
   }
-  for (int i = 0; i < P->core.g.A; ++i)
-    if (cfg->acc[i] >> 31) {
-      delete P;
-      return set_err(OMPDART_E_INVALID, "call pseudo-accesses are not accepted by this entry point");
-    }
   P->device = o.device;
   cudaError_t ce = cudaSetDevice(o.device);
   if (ce != cudaSuccess) {
@@ -387,7 +447,10 @@ int ompdart_plan_create(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdar
   }
   std::vector<uint64_t> top, eh, ed, xl;
   boundary_rows(cfg, P->core.g.W, &top, &eh, &ed, &xl);
-  rc = core_build(&P->core, cfg->acc_off, cfg->acc, top, eh, ed, xl, 1, {}, o, &err);
+  CallHost calls;
+  calls.planes = cfg->call_planes;
+  calls.rows = cfg->call_planes ? cfg->n_calls : 0;
+  rc = core_build(&P->core, cfg->acc_off, cfg->acc, calls, top, eh, ed, xl, 1, {}, o, &err);
   if (rc) {
     delete P;
     return set_err(rc, err);
@@ -467,6 +530,8 @@ void ompdart_result_free(ompdart_result *r) {
   if (!r) return;
   free(r->h_in); free(r->d_in); free(r->h_out); free(r->d_out); free(r->acc_flag);
   free(r->edge_xfers); free(r->exit_blocks); free(r->from_exit); free(r->live_in);
+  free(r->call_site_acc); free(r->call_to); free(r->call_from); free(r->call_entry_h); free(r->call_entry_d);
+  free(r->call_exit_live);
   free(r);
 }
 

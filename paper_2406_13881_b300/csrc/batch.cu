@@ -37,6 +37,8 @@ struct Arena {
   std::vector<int32_t> members;                              // batch index of each CFG, arena order
   std::vector<int32_t> blk_off, acc_base, x_off, chunk_beg;  // [members + 1]
   std::vector<int32_t> n_vars, n_edges;                      // [members]
+  std::vector<int32_t> site_off;                             // [members + 1] call sites of each CFG
+  int32_t *site_local = nullptr;  // device [sites]: access index within its CFG
   int32_t *exit_local = nullptr;  // device [X]: exit blocks as ids local to their CFG
   int32_t *h_status = nullptr;    // host [ST_COUNT]
   int32_t *h_err = nullptr;       // host [members]
@@ -132,9 +134,11 @@ int build_arena(Arena *a, const std::vector<int32_t> &members, std::vector<Inges
   concat_ingests(parts, &a->core.g);
   const int W = a->core.g.W;
   a->W = W;
-  std::vector<int32_t> acc_off{0}, unreach_cfg, exit_local;
+  std::vector<int32_t> acc_off{0}, unreach_cfg, exit_local, site_local;
   std::vector<uint32_t> acc;
-  std::vector<uint64_t> top, eh, ed, xl;
+  std::vector<uint64_t> top, eh, ed, xl, table;
+  CallHost calls;
+  a->site_off.assign(1, 0);
   acc_off.reserve(a->core.g.N + 1);
   acc.reserve(a->core.g.A);
   a->blk_off.assign(1, 0);
@@ -150,6 +154,14 @@ int build_arena(Arena *a, const std::vector<int32_t> &members, std::vector<Inges
     for (int b = 0; b < g.N; ++b)
       if (g.pos[b] < 0) unreach_cfg.push_back((int32_t)k);
     exit_local.insert(exit_local.end(), g.exit_blocks.begin(), g.exit_blocks.end());
+    calls.row_base.push_back(calls.rows);
+    if (c.call_planes && c.n_calls > 0) {
+      table.insert(table.end(), c.call_planes, c.call_planes + (size_t)c.n_calls * 7 * W);
+      calls.rows += c.n_calls;
+    }
+    for (int i = 0; i < c.acc_off[g.N]; ++i)
+      if (c.acc[i] >> 31) site_local.push_back(i);
+    a->site_off.push_back((int32_t)site_local.size());
     a->n_vars.push_back(c.n_vars);
     a->n_edges.push_back(g.E);
     a->blk_off.push_back(a->blk_off.back() + g.N);
@@ -161,8 +173,9 @@ int build_arena(Arena *a, const std::vector<int32_t> &members, std::vector<Inges
   oa.path = 2;
   oa.chunk_target = a->chunk_target;
   oa.warps_per_cta = a->wpc;
-  int rc = core_build(&a->core, acc_off.data(), acc.data(), top, eh, ed, xl, (int)members.size(), unreach_cfg, oa,
-                      err);
+  calls.planes = table.empty() ? nullptr : table.data();
+  int rc = core_build(&a->core, acc_off.data(), acc.data(), calls, top, eh, ed, xl, (int)members.size(),
+                      unreach_cfg, oa, err);
   if (rc) return rc;
   const std::vector<int32_t> &co = a->core.g.chunk_off, &cp = a->core.g.cfg_pos_off;
   a->chunk_beg.resize(members.size() + 1);
@@ -170,7 +183,8 @@ int build_arena(Arena *a, const std::vector<int32_t> &members, std::vector<Inges
     a->chunk_beg[k] = (int32_t)(std::lower_bound(co.begin(), co.end(), cp[k]) - co.begin());
   a->chunk_beg[members.size()] = (int32_t)co.size() - 1;
   a->exit_local = a->core.upload(exit_local);
-  if (!a->exit_local) {
+  a->site_local = a->core.upload(site_local);
+  if (!a->exit_local || !a->site_local) {
     *err = "device allocation failed";
     return OMPDART_E_NOMEM;
   }
@@ -301,6 +315,17 @@ void arena_view(const Arena &a, int k, ompdart_result *v) {
   v->from_exit = d.from_exit + (size_t)a.x_off[k] * W;
   v->path = a.core.path;
   v->sweeps = a.h_status[ST_SWEEPS];
+  const int s0 = a.site_off[k];
+  v->n_call_sites = a.site_off[k + 1] - s0;
+  v->call_site_acc = a.site_local + s0;
+  if (v->n_call_sites) {
+    const size_t o = (size_t)s0 * W;
+    v->call_to = d.call_to + o;
+    v->call_from = d.call_from + o;
+    v->call_entry_h = d.call_entry_h + o;
+    v->call_entry_d = d.call_entry_d + o;
+    v->call_exit_live = d.call_exit_live + o;
+  }
   v->h2d_bytes = a.core.h2d + scan_h2d_bytes(a.core.scan);
   v->d2h_bytes = 0;
 }
@@ -336,12 +361,6 @@ int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts 
       for (int i = next++; i < n; i = next++) {
         std::string e;
         int rc = ingest(&cfgs[i], &ing[i], &e);
-        if (!rc)
-          for (int a = 0; a < ing[i].A; ++a)
-            if (cfgs[i].acc[a] >> 31) {
-              rc = OMPDART_E_INVALID;  // call pseudo-accesses: not in a batch
-              break;
-            }
         B->ingest_status[i] = rc;
       }
     };
@@ -389,7 +408,15 @@ int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts 
     boundary_rows(&cfgs[i], p->core.g.W, &top, &eh, &ed, &xl);
     ompdart_opts os = o;
     os.path = 1;
-    int rc = core_build(&p->core, cfgs[i].acc_off, cfgs[i].acc, top, eh, ed, xl, 1, {}, os, &err);
+    CallHost calls;
+    calls.planes = cfgs[i].call_planes;
+    calls.rows = cfgs[i].call_planes ? cfgs[i].n_calls : 0;
+    int rc = core_build(&p->core, cfgs[i].acc_off, cfgs[i].acc, calls, top, eh, ed, xl, 1, {}, os, &err);
+    if (rc == OMPDART_E_INVALID) {  // this CFG alone (calls without the scan solver)
+      B->ingest_status[i] = rc;
+      B->where[i] = Where{};
+      continue;
+    }
     if (rc) return set_error(rc, err);
     p->h_status = B->host_ints(ST_COUNT);
     if (!p->h_status) return set_error(OMPDART_E_NOMEM, "host allocation failed");
@@ -576,6 +603,13 @@ int batch_fetch_all(ompdart_batch *B, ompdart_result **outs) {
     ompdart_result *host = nullptr;
     rc = result_copy(whole, true, B->last_stream, &host);
     if (rc) return rc;
+    std::vector<int32_t> host_sites(a.site_off.back() + 1);
+    if (a.site_off.back() &&
+        cudaMemcpy(host_sites.data(), a.site_local, sizeof(int32_t) * a.site_off.back(), cudaMemcpyDeviceToHost) !=
+            cudaSuccess) {
+      ompdart_result_free(host);
+      return set_error(OMPDART_E_CUDA, "copy of call sites failed");
+    }
     const size_t W = a.W;
     const double blocks = std::max(1, a.blk_off.back());
     for (size_t k = 0; k < a.members.size(); ++k) {
@@ -596,6 +630,15 @@ int batch_fetch_all(ompdart_batch *B, ompdart_result **outs) {
       v.edge_xfers = host->edge_xfers + a.rec_off[k];
       v.exit_blocks = host->exit_blocks + a.x_off[k];
       v.from_exit = host->from_exit + (size_t)a.x_off[k] * W;
+      v.call_site_acc = host_sites.data() + a.site_off[k];
+      if (v.n_call_sites) {
+        const size_t o = (size_t)a.site_off[k] * W;
+        v.call_to = host->call_to + o;
+        v.call_from = host->call_from + o;
+        v.call_entry_h = host->call_entry_h + o;
+        v.call_entry_d = host->call_entry_d + o;
+        v.call_exit_live = host->call_exit_live + o;
+      }
       rc = result_copy(v, false, nullptr, &outs[i]);
       if (rc) break;
       outs[i]->h2d_bytes = h2d;

@@ -76,6 +76,16 @@ struct DevPlan {
   int xfer_cap;
   uint64_t *from_exit;     // [X*W]
   int32_t *status;         // [ST_COUNT]
+  // call sites (Sec. IV-C), in access order; call blocks: reachable blocks
+  // holding at least one call pseudo-access
+  int n_sites, n_cblk;
+  const uint64_t *calls;        // [rows][7][W] call table
+  const int32_t *site_acc;      // [n_sites] access index
+  const int32_t *cblk;          // [n_cblk] block
+  const int32_t *cblk_site0;    // [n_cblk] its first call site
+  const int32_t *cblk_rowbase;  // [n_cblk] first table row of its CFG
+  const int32_t *cblk_cfg;      // [n_cblk] its CFG (boundary rows)
+  uint64_t *call_to, *call_from, *call_entry_h, *call_entry_d, *call_exit_live;  // [n_sites][W]
 };
 
 // Optional per-launch timing: a CUDA event is recorded on the launch stream

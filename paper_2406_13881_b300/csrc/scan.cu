@@ -37,6 +37,7 @@ namespace ompdart {
 namespace {
 
 constexpr int CARRY = -2;      // slot id: the chunk's incoming carry
+constexpr int BACK_EDGE = -2;  // in-edge tag: a back edge (its transfers are emitted at the latch)
 constexpr int PREV = -3;       // slot id: the value of the position walked just before
 constexpr int SH_WORDS = 512;  // shared-memory words per warp for slots (4 KiB)
 constexpr int WPC = 4;         // warps per CTA of the chain kernels
@@ -52,13 +53,18 @@ enum ModeKind { M_SUM = 0, M_APPLY = 1, M_LANT = 2 };
 struct PosMeta {  // one per position, 64 B
   int32_t blk;
   int32_t fin_beg, out_beg, acc_beg, srcent_beg, bend_beg;  // acc_beg: in caller order
-  int16_t nfin, nout, nacc, nsrcent, nbend, fslot, bslot, pad0;
+  int16_t nfin, nout, nacc, nsrcent, nbend, fslot, bslot, nlb;  // nlb: back edges leaving here
   int32_t head_loop;      // loop whose header is this position, else -1
   uint32_t latch_levels;  // bit d: back edge to the header of the level-d loop
   int32_t exit_idx;       // index in exit_blocks, else -1
   int32_t pacc_beg;       // first access of the block in position order
-  int32_t pad2, pad3;
+  int32_t flags;          // PM_RECORDS: the block's summary records are given
+  int32_t lb_beg;         // first of this position's back edges in latch_be
 };
+// a block with call pseudo-accesses: its entries in the position-ordered
+// access stream are already summary records (folded on the host with the
+// callees' rows), and its access flags come from the call-site pass
+constexpr int32_t PM_RECORDS = 1;
 static_assert(sizeof(PosMeta) == 64, "PosMeta layout");
 
 struct LoopMeta {
@@ -97,6 +103,7 @@ struct ScanDev {
   const int32_t *lat_slot;
   const int32_t *bend_loop;
   const int32_t *srcent;
+  const int2 *latch_be;  // back edges by latch position: {edge id, header block}
   uint64_t *spill;     // per warp spill area
   int spill_stride;    // words per warp
   uint64_t *gsum, *psum;   // [planes][C][W] chunk maps
@@ -201,7 +208,8 @@ namespace {
 bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta> &meta, std::vector<LoopMeta> &loops,
                 std::vector<ChunkMeta> &chunks, std::vector<CarrySrc> &csrc, std::vector<int32_t> &fin_slot,
                 std::vector<int32_t> &out_slot, std::vector<int32_t> &out_pos, std::vector<int32_t> &lat_slot,
-                std::vector<int32_t> &bend_loop, std::vector<int32_t> &srcent, std::string *err) {
+                std::vector<int32_t> &bend_loop, std::vector<int32_t> &srcent, std::vector<int2> &latch_be,
+                std::string *err) {
   Ingest &gm = const_cast<Ingest &>(g);
   make_chunks(&gm, target);
   const int M = g.M, C = (int)g.chunk_off.size() - 1, L = g.L;
@@ -374,6 +382,30 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
         if (pp < e) csrc.push_back(CarrySrc{fslot[pp], g.fin_ent[k], k, 0});
       }
     chunks[c].carry_cnt = (int32_t)csrc.size() - chunks[c].carry_beg;
+  }
+  // back edges by latch: their transfers are emitted when the latch's final
+  // value is known (the header is walked before its latches)
+  {
+    std::vector<std::pair<int32_t, int2>> be;
+    for (int i = 0; i < M; ++i)
+      for (int k = g.fin_off[i]; k < g.fin_off[i + 1]; ++k) {
+        const int pp = g.pos[g.fin_src[k]];
+        if (pp >= i) be.push_back({pp, make_int2(g.fin_eid[k], g.order[i])});
+      }
+    std::stable_sort(be.begin(), be.end(), [](const std::pair<int32_t, int2> &a, const std::pair<int32_t, int2> &b) {
+      return a.first < b.first;
+    });
+    latch_be.clear();
+    for (size_t q = 0; q < be.size(); ++q) {
+      PosMeta &m = meta[be[q].first];
+      if (m.nlb == 0) m.lb_beg = (int32_t)latch_be.size();
+      if (m.nlb == 32000) {
+        if (err) *err = "too many back edges from one block";
+        return false;
+      }
+      ++m.nlb;
+      latch_be.push_back(be[q].second);
+    }
   }
   for (int l = 0; l < L; ++l) {
     LoopMeta &lm = loops[l];
@@ -611,15 +643,49 @@ __device__ __forceinline__ void drop_masks(uint64_t *tb, int lane) {
   for (int q = 0; q < 2 * NP; ++q) *reinterpret_cast<ulonglong2 *>(tb + q * 64 + 2 * lane) = make_ulonglong2(0ull, 0ull);
 }
 
+// Append the nonzero words of one edge's transfers to the warp's record
+// stream (lanes hold words w0, w0 + 1; warp-uniform call).
+__device__ __forceinline__ void push_edge_records(const ScanDev &sd, int stream, int &rec_count, int eid, int w0,
+                                                  uint64_t to0, uint64_t fr0, uint64_t to1, uint64_t fr1,
+                                                  int lane) {
+  const bool n0 = (to0 | fr0) != 0, n1 = (to1 | fr1) != 0;
+  const unsigned b0 = __ballot_sync(0xffffffffu, n0), b1 = __ballot_sync(0xffffffffu, n1);
+  if (!(b0 | b1)) return;
+  const unsigned below = (1u << lane) - 1u;
+  const int base = rec_count;
+  const int cap = sd.rec_cap[stream];
+  EdgeXfer *out = sd.stream + sd.rec_base[stream];
+  int idx = base + __popc(b0 & below) + __popc(b1 & below);
+  if (n0) { if (idx < cap) out[idx] = EdgeXfer{eid, w0, to0, fr0}; ++idx; }
+  if (n1) { if (idx < cap) out[idx] = EdgeXfer{eid, w0 + 1, to1, fr1}; }
+  rec_count = base + __popc(b0) + __popc(b1);
+}
+
+// Transfers on the back edges leaving a latch, from its final value zo
+// (stale on the host): the header's conflicts (live there, valid on the
+// device at no entry of it) the latch leaves stale on the host come back
+// to the host on that edge.  Back edges are never loop-entry edges.
+__device__ void emit_back_edges(const DevPlan &p, const ScanDev &sd, const Lane &L, const PosMeta &m,
+                                const uint64_t zo[2], int stream, int &rec_count) {
+  const int W = p.W;
+  for (int q = 0; q < m.nlb; ++q) {
+    const int2 be = sd.latch_be[m.lb_beg + q];  // {edge id, header block}
+    const uint64_t c0 = ld_word(p.live, be.y, W, L.w0) & ~ld_word(p.d_in, be.y, W, L.w0);
+    const uint64_t c1 = ld_word(p.live, be.y, W, L.w0 + 1) & ~ld_word(p.d_in, be.y, W, L.w0 + 1);
+    push_edge_records(sd, stream, rec_count, be.x, L.w0, 0, c0 & zo[0], 0, c1 & zo[1], L.lane);
+  }
+}
+
 // The H-phase emission for one position (apply mode): per-access flags,
-// in-chunk edge records, exit transfers.
+// in-chunk edge records (back edges excepted: emit_back_edges), exit
+// transfers.
 __device__ void emit_position(const DevPlan &p, const ScanDev &sd, const Win &w, const WinRegs &wr, const Lane &L,
                               const PosMeta &m, const Slots<1> &sl, const uint64_t zin[2], const uint64_t zout[2],
                               const uint64_t din[2], const uint64_t live[2], const uint64_t prev[2], uint64_t *hd,
                               int stream, int &rec_count, int cfg) {
   const int W = p.W, lane = L.lane;
   // ---- access flags: replay the block from its entry states
-  if (m.nacc) {
+  if (m.nacc && !(m.flags & PM_RECORDS)) {
     hd[2 * lane] = ~zin[0] & L.top0;
     hd[2 * lane + 1] = ~zin[1] & L.top1;
     hd[64 + 2 * lane] = din[0];
@@ -653,7 +719,7 @@ __device__ void emit_position(const DevPlan &p, const ScanDev &sd, const Win &w,
     const int k = m.fin_beg + q;
     const int2 fe = win_edge(w, wr, sd.fin_pk, k);
     const int slot = fe.x;
-    if (slot == CARRY) continue;
+    if (slot == CARRY || fe.y == BACK_EDGE) continue;
     const int ent = fe.y;
     const ulonglong2 zs = slot == PREV ? make_ulonglong2(prev[0], prev[1]) : *sl.at(slot, 0, lane);
     uint64_t to0 = 0, to1 = 0, fr0, fr1;
@@ -672,20 +738,7 @@ __device__ void emit_position(const DevPlan &p, const ScanDev &sd, const Win &w,
     }
     fr0 |= c0 & e0;
     fr1 |= c1 & e1;
-    const bool n0 = (to0 | fr0) != 0, n1 = (to1 | fr1) != 0;
-    const unsigned b0 = __ballot_sync(0xffffffffu, n0), b1 = __ballot_sync(0xffffffffu, n1);
-    if (b0 | b1) {
-      const int eid = p.fin_eid[k];
-      const unsigned below = (1u << lane) - 1u;
-      const int off0 = __popc(b0 & below) + __popc(b1 & below);
-      const int base = rec_count;
-      const int cap = sd.rec_cap[stream];
-      EdgeXfer *out = sd.stream + sd.rec_base[stream];
-      int idx = base + off0;
-      if (n0) { if (idx < cap) out[idx] = EdgeXfer{eid, L.w0, to0, fr0}; ++idx; }
-      if (n1) { if (idx < cap) out[idx] = EdgeXfer{eid, L.w0 + 1, to1, fr1}; }
-      rec_count = base + __popc(b0) + __popc(b1);
-    }
+    push_edge_records(sd, stream, rec_count, p.fin_eid[k], L.w0, to0, fr0, to1, fr1, lane);
   }
   // ---- region exit
   if (m.exit_idx >= 0) {
@@ -893,6 +946,7 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
         __syncwarp();
         emit_position(p, sd, w, wr, L, m, *reinterpret_cast<Slots<1> *>(&sl), z[0], zo[0], din, lv, pvo[0], hd,
                       stream, rec_count, cm.cfg);
+        if (m.nlb) emit_back_edges(p, sd, L, m, zo[0], stream, rec_count);
       }
       if ((PH == K_HP || PH == K_D) && m.nsrcent) {
         uint64_t *dst = PH == K_HP ? sd.hp_src : sd.d_src;
@@ -1216,6 +1270,10 @@ __global__ void k_local_summary_pos(ScanDev sd, int M) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
     const int a0 = sd.meta[i].pacc_beg;
     const int a1 = a0 + sd.meta[i].nacc;
+    if (sd.meta[i].flags & PM_RECORDS) {  // records given: copy them
+      for (int j = a0; j < a1; ++j) sd.rec_p[j] = sd.acc_p[j];
+      continue;
+    }
     for (int j = a0; j < a1; ++j) {
       // a lone thread walks the block as lane 0 of a one-lane "warp"
       summarize_one(sd.acc_p, sd.rec_p, a0, a1, j);
@@ -1451,20 +1509,90 @@ ChainShape chain_shape(K kern, int need, int np, bool acc, int wpc, int n_items,
 }
 }  // namespace
 
-ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *acc, int32_t *cfg_err, DevPlan &p,
-                       int chunk_target, int keep_states, std::string *err, int wpc) {
+// Summary records of a block with call pseudo-accesses, folded on the host
+// by the local rule (Sec. IV-D) with each call contributing its callee's
+// reads first, then its net effect (Sec. IV-C): one record per variable the
+// block touches, in the device record format.  `idx` is scratch of size V
+// filled with -1 (restored on return).
+static void fold_call_block(const uint32_t *acc, int a0, int a1, const CallHost &calls, int row_base, int W,
+                            std::vector<int32_t> &idx, std::vector<uint32_t> *out) {
+  struct St { int32_t v; uint8_t last[2], ue[2], def; };
+  std::vector<St> st;
+  auto at = [&](int v) -> St & {
+    if (idx[v] < 0) {
+      idx[v] = (int32_t)st.size();
+      st.push_back(St{v, {0, 0}, {0, 0}, 0});
+    }
+    return st[idx[v]];
+  };
+  auto read = [](St &x, int S) {
+    x.last[S] = 1;
+    if (!x.ue[S]) x.ue[S] = 1;
+  };
+  auto wrote = [](St &x) {
+    if (!x.ue[0]) x.ue[0] = 2;
+    if (!x.ue[1]) x.ue[1] = 2;
+    x.def = 1;
+  };
+  for (int i = a0; i < a1; ++i) {
+    const uint32_t a = acc[i];
+    if (a >> 31) {
+      const uint64_t *row = calls.planes + (size_t)(row_base + (int)(a & 0x7FFFFFFFu)) * 7 * W;
+      for (int w = 0; w < W; ++w) {
+        uint64_t any = 0;
+        for (int k = 0; k < 7; ++k) any |= row[(size_t)k * W + w];
+        while (any) {
+          const int bit = __builtin_ctzll(any);
+          any &= any - 1;
+          const uint64_t m = 1ull << bit;
+          St &x = at(w * 64 + bit);
+          if (row[0 * W + w] & m) read(x, 0);
+          if (row[1 * W + w] & m) read(x, 1);
+          if (row[2 * W + w] & m) x.last[0] = 1; else if (row[3 * W + w] & m) x.last[0] = 2;
+          if (row[4 * W + w] & m) x.last[1] = 1; else if (row[5 * W + w] & m) x.last[1] = 2;
+          if (row[6 * W + w] & m) wrote(x);
+        }
+      }
+      continue;
+    }
+    St &x = at((int)(a & 0xFFFFFFu));
+    const int kind = (int)((a >> 24) & 3u), S = (int)((a >> 26) & 1u);
+    if (kind & 1) read(x, S);
+    if (kind & 2) {
+      x.last[S] = 1;
+      x.last[1 - S] = 2;
+      wrote(x);
+    }
+  }
+  for (const St &x : st) {
+    uint32_t r = (uint32_t)x.v;
+    if (x.last[0] == 1) r |= R_GH;
+    if (x.last[0] == 2) r |= R_KH;
+    if (x.last[1] == 1) r |= R_GD;
+    if (x.last[1] == 2) r |= R_KD;
+    if (x.ue[0] == 1) r |= R_UH;
+    if (x.ue[1] == 1) r |= R_UD;
+    if (x.def) r |= R_DF;
+    out->push_back(r);
+    idx[x.v] = -1;
+  }
+}
+
+ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *acc, const CallHost &calls,
+                       int32_t *cfg_err, DevPlan &p, int chunk_target, int keep_states, std::string *err, int wpc) {
   ScanState *st = new ScanState();
   std::vector<PosMeta> meta;
   std::vector<LoopMeta> loops;
   std::vector<ChunkMeta> chunks;
   std::vector<CarrySrc> csrc;
   std::vector<int32_t> fin_slot, out_slot, out_pos, lat_slot, bend_loop, srcent;
+  std::vector<int2> latch_be;
   // short chunks give more independent walks (one warp each); 128
   // positions was the fastest target on the 2^20-block CFG
   if (chunk_target <= 0) chunk_target = g.M <= 2048 ? std::max(32, g.M / 8) : 128;
   TraceScope trace_bm("scan build_meta", g.M);
   if (!build_meta(g, chunk_target, st, meta, loops, chunks, csrc, fin_slot, out_slot, out_pos, lat_slot, bend_loop,
-                  srcent, err)) {
+                  srcent, latch_be, err)) {
     delete st;
     return nullptr;
   }
@@ -1472,20 +1600,35 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   // accesses in position order, and each position's first access there
   std::vector<uint32_t> acc_p;
   acc_p.reserve(g.A);
+  std::vector<int32_t> var_idx;
   for (int i = 0; i < g.M; ++i) {
     const int b = meta[i].blk, a0 = acc_off[b], a1 = acc_off[b + 1];
-    if (a1 - a0 > 32767) {
-      if (err) *err = "a block with more than 32767 accesses";
+    bool has_call = false;
+    for (int k = a0; k < a1 && calls.rows; ++k) has_call |= (acc[k] >> 31) != 0;
+    meta[i].acc_beg = a0;
+    meta[i].pacc_beg = (int32_t)acc_p.size();
+    meta[i].flags = 0;
+    if (has_call) {
+      if (var_idx.empty()) var_idx.assign((size_t)p.W * 64, -1);
+      const int cfg = (int)(std::upper_bound(g.cfg_pos_off.begin(), g.cfg_pos_off.end(), i) - g.cfg_pos_off.begin()) - 1;
+      fold_call_block(acc, a0, a1, calls, calls.row_base.empty() ? 0 : calls.row_base[cfg], p.W, var_idx, &acc_p);
+      meta[i].flags = PM_RECORDS;
+    } else {
+      acc_p.insert(acc_p.end(), acc + a0, acc + a1);
+    }
+    const size_t n = acc_p.size() - (size_t)meta[i].pacc_beg;
+    if (n > 32767) {
+      if (err) *err = "a block with more than 32767 accesses (or variables touched by its calls)";
       delete st;
       return nullptr;
     }
-    meta[i].acc_beg = a0;
-    meta[i].nacc = (int16_t)(a1 - a0);
-    meta[i].pacc_beg = (int32_t)acc_p.size();
-    acc_p.insert(acc_p.end(), acc + a0, acc + a1);
+    meta[i].nacc = (int16_t)n;
   }
   std::vector<int2> fin_pk(fin_slot.size()), out_pk(out_slot.size());
-  for (size_t k = 0; k < fin_pk.size(); ++k) fin_pk[k] = make_int2(fin_slot[k], g.fin_ent[k]);
+  // in-edge entries: {source slot, loop-entry edge or -1, or BACK_EDGE}
+  for (int i = 0; i < g.M; ++i)
+    for (int k = g.fin_off[i]; k < g.fin_off[i + 1]; ++k)
+      fin_pk[k] = make_int2(fin_slot[k], g.pos[g.fin_src[k]] >= i ? BACK_EDGE : g.fin_ent[k]);
   for (size_t k = 0; k < out_pk.size(); ++k) out_pk[k] = make_int2(out_slot[k], out_pos[k]);
   const int W = p.W, C = st->C, G = (W + 63) / 64;
   st->G = G;
@@ -1515,6 +1658,7 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   chk(sd.lat_slot = st->up(lat_slot));
   chk(sd.bend_loop = st->up(bend_loop));
   chk(sd.srcent = st->up(srcent));
+  chk(sd.latch_be = st->up(latch_be));
   chk(sd.work = st->up(work));
   chk(sd.queue = st->alloc<int32_t>(Q_SLOTS));
   // launch shapes (persistent: the grid is what fits on the GPU at once)

@@ -50,6 +50,18 @@ int enqueue_fill_unreachable(const DevPlan &p, cudaStream_t s, int keep_states, 
 int enqueue_sweep_solver(const DevPlan &p, cudaStream_t s, int n_fin, Prof *pf);
 int enqueue_sweep_edges(const DevPlan &p, cudaStream_t s, int n_fin);
 
+// Call table of a plan (Sec. IV-C): rows of 7 planes of W words (ReqH,
+// ReqD, GenH, KillH, GenD, KillD, MustDef) on the host; a batch lays its
+// CFGs' tables end to end and a call access's row is local to its CFG.
+struct CallHost {
+  const uint64_t *planes = nullptr;  // [rows][7][W]
+  int rows = 0;
+  std::vector<int32_t> row_base;     // per CFG of the plan (empty: 0)
+};
+
+// ---- calls.cu: the call-site pass (after the host-validity pass)
+int enqueue_call_sites(const DevPlan &p, cudaStream_t s, Prof *pf);
+
 // ---- scan.cu: the chunked scan solver (reducible CFGs with contiguous
 // loop bodies; one CFG or a batch of CFGs laid end to end)
 int scan_supported(const Ingest &g);
@@ -57,8 +69,8 @@ struct ScanState;
 // acc_off/acc: accesses of the plan's blocks (CSR over g's block ids);
 // cfg_err: device [n_cfg] per-CFG error flags or null; wpc: warps per CTA
 // of the chain kernels (0 = default)
-ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *acc, int32_t *cfg_err, DevPlan &p,
-                       int chunk_target, int keep_states, std::string *err, int wpc);
+ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *acc, const CallHost &calls,
+                       int32_t *cfg_err, DevPlan &p, int chunk_target, int keep_states, std::string *err, int wpc);
 bool scan_grow_streams(ScanState *st);
 long long scan_h2d_bytes(const ScanState *st);
 int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *pf);
@@ -81,6 +93,7 @@ struct PlanCore {
   long long h2d = 0;
   ScanState *scan = nullptr;
   int32_t *cfg_err = nullptr;  // device [n_cfg] (scan path)
+  std::vector<int32_t> site_acc;   // host copy: access index of each call site
 
   long long dev_bytes = 0;  // device bytes this core holds (with its scan state)
 
@@ -119,9 +132,10 @@ void boundary_rows(const ompdart_cfg *cfg, int W, std::vector<uint64_t> *top, st
 // solver (path 0 auto, 1 sweep, 2 scan; a batch must take the scan) and
 // allocate every plane.  unreach_cfg: CFG of each unreachable block in
 // ascending block order (empty for one CFG).  Returns an OMPDART_* code.
-int core_build(PlanCore *c, const int32_t *acc_off, const uint32_t *acc, const std::vector<uint64_t> &top,
-               const std::vector<uint64_t> &eh, const std::vector<uint64_t> &ed, const std::vector<uint64_t> &xl,
-               int n_cfg, const std::vector<int32_t> &unreach_cfg, const ompdart_opts &o, std::string *err);
+int core_build(PlanCore *c, const int32_t *acc_off, const uint32_t *acc, const CallHost &calls,
+               const std::vector<uint64_t> &top, const std::vector<uint64_t> &eh, const std::vector<uint64_t> &ed,
+               const std::vector<uint64_t> &xl, int n_cfg, const std::vector<int32_t> &unreach_cfg,
+               const ompdart_opts &o, std::string *err);
 // Enqueue one full run on s; returns the number of kernels launched.
 int core_enqueue(PlanCore *c, cudaStream_t s, Prof *pf);
 // After the stream finished a run (h_status: its ST_COUNT status words):

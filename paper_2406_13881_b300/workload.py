@@ -53,6 +53,9 @@ class CFG:
     entry_host_valid: np.ndarray | None = None
     entry_dev_valid: np.ndarray | None = None
     exit_host_live: np.ndarray | None = None
+    # call table (Sec. IV-C): [n_calls, 7, W] rows ReqH, ReqD, GenH, KillH,
+    # GenD, KillD, MustDef for call pseudo-accesses (bit 31 | row)
+    call_planes: np.ndarray | None = None
     meta: dict = dataclasses.field(default_factory=dict)
 
     @property

@@ -41,3 +41,8 @@ def assert_matches_oracle(g, res, orc, words=None, acc_keep=None):
     others = np.ones(g.n_blocks, dtype=bool)
     others[ex] = False
     assert not fx[others].any(), "oracle exit transfer at a block the library does not list"
+    if "call_to" in orc and len(orc["call_to"]):
+        sites = np.flatnonzero(np.asarray(g.acc, dtype=np.uint32) >> np.uint32(31))
+        np.testing.assert_array_equal(res["call_site_acc"], sites, err_msg="call_site_acc")
+        for k in ("call_to", "call_from", "call_entry_h", "call_entry_d", "call_exit_live"):
+            np.testing.assert_array_equal(res[k][:, cols], orc[k], err_msg=k)

@@ -140,6 +140,20 @@ def test_scan_equals_sweep(seed):
     assert key(a) == key(b)
 
 
+def test_back_edge_transfer_without_loop_rerun():
+    """A loop header whose entries disagree (host-valid on one, device-valid
+    on the other) and whose latch leaves the host copy stale: the latch
+    does not grow the header's meet, so no body re-walk happens, yet the
+    back edge needs its own `from' (emitted from the latch's final value)."""
+    g = wl.from_lists([[1, 2], [3], [3], [4, 5], [3], []],
+                      [[], [(0, 2, 0)], [(0, 2, 1)], [(0, 1, 0)], [(0, 2, 1)], []], 1)
+    for target in (0, 1, 2):
+        res = _native.analyze(g, path=2, chunk_target=target, keep_states=True)
+        orc = oracle.solve(g)
+        assert orc["from_edge"][4].any()  # the back edge 4 -> 3 carries a `from'
+        assert_matches_oracle(g, res, orc)
+
+
 def test_unreachable_blocks_scan_path():
     g = wl.from_lists([[1], [2], [], [1], [3]], [[(0, 2, 0)], [(0, 1, 1)], [], [(1, 2, 1)], [(0, 3, 1)]], 3)
     res = _native.analyze(g, path=2, keep_states=True)
