@@ -150,7 +150,7 @@ def test_back_edge_transfer_without_loop_rerun():
     for target in (0, 1, 2):
         res = _native.analyze(g, path=2, chunk_target=target, keep_states=True)
         orc = oracle.solve(g)
-        assert orc["from_edge"][4].any()  # the back edge 4 -> 3 carries a `from'
+        assert orc["from_edge"][6].any()  # edge 6 = the back edge 4 -> 3 carries a `from'
         assert_matches_oracle(g, res, orc)
 
 
