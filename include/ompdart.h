@@ -265,6 +265,87 @@ void ompdart_batch_destroy(ompdart_batch *batch);
 int ompdart_analyze_batch(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts *opts, ompdart_result **outs,
                           int32_t *status);
 
+/* ---- interprocedural: callee summaries (Sec. IV-C) -----------------------
+   The paper's side-effect analysis records, per function, which data it
+   reads or writes on the host or the device and applies that at every call
+   site.  A summary is 7 planes of the callee's W words, in the call-table
+   row order: ReqH, ReqD (anticipated at the entry with nothing live after
+   the exit: read in that space before being written, on some path), GenH,
+   KillH, GenD, KillD (plain validity at the reachable exits, the local rule
+   along paths without transfers: Gen = valid at every exit from an
+   all-stale entry, Kill = stale at some exit from an all-valid entry),
+   MustDef (written on every path to a reachable exit).  A callee without a
+   reachable exit gets zero Gen/Kill/MustDef.  Callees may hold calls
+   themselves (their own call tables); any CFG shape is accepted. */
+
+/* Summaries of n callees in one device run: rows[i] receives 7 * W_i words
+   in callee i's own numbering; status[i] (may be NULL) its code
+   (OMPDART_E_INVALID for a malformed CFG, OMPDART_E_NOCONVERGE if
+   opts->max_sweeps ran out).  Returns OMPDART_OK unless the run failed. */
+int ompdart_summarize_batch(const ompdart_cfg *callees, int32_t n, const ompdart_opts *opts, uint64_t *const *rows,
+                            int32_t *status);
+
+/* One callee's summary mapped into a caller's numbering, ready to be a row
+   of the caller's call table: var_map[v] (callee variable v) is the caller
+   variable it denotes (a global, or the actual argument of a pointer
+   parameter) or -1 (a local, dropped); NULL = identity.  caller_row
+   receives 7 * ceil(caller_n_vars / 64) words.  Callee variables that
+   denote the same caller variable combine pessimistically: Req, Kill and
+   MustDef by OR, Gen by AND (a kill overrides a gen). */
+int ompdart_summarize_callee(const ompdart_cfg *callee, const int32_t *var_map, int32_t caller_n_vars,
+                             uint64_t *caller_row, const ompdart_opts *opts);
+
+/* ---- interprocedural: a whole program ----------------------------------
+   Functions and their call sites.  Function f's CFG holds its calls as
+   call pseudo-accesses whose row index k (bits 0-30) names its k-th call
+   site, site_off[f] + k; its call_planes are ignored (the driver fills the
+   table from the callees' summaries).  Site s calls site_callee[s];
+   var_map[map_off[s] ...] gives, per callee variable, the caller variable
+   it denotes (a global, or the actual argument of a pointer parameter) or
+   -1 (a local of the callee).  The call graph must be acyclic.
+   ompdart_analyze_program
+     1. computes the summaries bottom-up, one device run per call-DAG height
+        (leaves first), each call site's row being its callee's summary
+        mapped into the caller (as ompdart_summarize_callee);
+     2. analyses every function top-down, one batch per height: a function
+        nobody calls runs in its own boundary rows; a called function runs
+        once per distinct context its call sites pass on: the caller's state
+        at the call (call_entry_h / call_entry_d as the callee's entry rows,
+        call_exit_live as its exit_host_live) mapped into the callee's
+        numbering (a callee local starts valid on the host only and is dead
+        after the exit).  A site passes on at most max_contexts contexts
+        (0 = 4): sorted, the excess merged into the last by the meet
+        (validity AND, liveness OR). */
+typedef struct {
+  int32_t n_funcs;
+  const ompdart_cfg *funcs;    /* [n_funcs]                                     */
+  const int32_t *site_off;     /* [n_funcs+1]                                   */
+  const int32_t *site_callee;  /* [n_sites]                                     */
+  const int32_t *map_off;      /* [n_sites+1]                                   */
+  const int32_t *var_map;      /* [map_off[n_sites]]                            */
+  int32_t max_contexts;        /* per call site; 0 = 4                          */
+} ompdart_program;
+
+typedef struct {
+  int32_t func;                /* the function analysed                          */
+  int32_t status;              /* OMPDART_OK or why it has no (exact) result     */
+  uint64_t *entry_h, *entry_d, *exit_live; /* [W_func] its context               */
+  ompdart_result *result;      /* host result (NULL if the analysis failed)      */
+} ompdart_instance;
+
+typedef struct {
+  int32_t n_instances;
+  ompdart_instance *inst;      /* grouped by height, highest first               */
+  int32_t levels;              /* call-DAG heights                                */
+  int32_t *height;             /* [n_funcs]                                       */
+  int32_t *status;             /* [n_funcs] summary status                        */
+  uint64_t *summaries;         /* 7 * W_f words per function, in its numbering    */
+  int64_t *summary_off;        /* [n_funcs]                                       */
+} ompdart_program_result;
+
+int ompdart_analyze_program(const ompdart_program *prog, const ompdart_opts *opts, ompdart_program_result **out);
+void ompdart_program_result_free(ompdart_program_result *res);
+
 /* ---- serving: continuous batching of analysis requests -----------------
    (no paper counterpart: the paper's tool runs once per translation unit;
    this is the request loop of a service that analyses CFGs as they

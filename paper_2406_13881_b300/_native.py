@@ -78,6 +78,23 @@ class ServerStats(C.Structure):
                 ("bytes_in_use", C.c_int64)]
 
 
+class Program(C.Structure):
+    _fields_ = [("n_funcs", C.c_int32), ("funcs", C.POINTER(Cfg)), ("site_off", C.c_void_p),
+                ("site_callee", C.c_void_p), ("map_off", C.c_void_p), ("var_map", C.c_void_p),
+                ("max_contexts", C.c_int32)]
+
+
+class Instance(C.Structure):
+    _fields_ = [("func", C.c_int32), ("status", C.c_int32), ("entry_h", C.c_void_p), ("entry_d", C.c_void_p),
+                ("exit_live", C.c_void_p), ("result", C.POINTER(Result))]
+
+
+class ProgramResult(C.Structure):
+    _fields_ = [("n_instances", C.c_int32), ("inst", C.POINTER(Instance)), ("levels", C.c_int32),
+                ("height", C.c_void_p), ("status", C.c_void_p), ("summaries", C.c_void_p),
+                ("summary_off", C.c_void_p)]
+
+
 class Timing(C.Structure):
     _fields_ = [("name", C.c_char_p), ("launches", C.c_int32), ("ms", C.c_double)]
 
@@ -107,6 +124,10 @@ EXPORTS = {
     "ompdart_batch_destroy": (None, [C.c_void_p]),
     "ompdart_analyze_batch": (C.c_int, [C.POINTER(Cfg), C.c_int32, C.POINTER(Opts),
                                         C.POINTER(C.POINTER(Result)), C.c_void_p]),
+    "ompdart_summarize_batch": (C.c_int, [C.POINTER(Cfg), C.c_int32, C.POINTER(Opts), C.c_void_p, C.c_void_p]),
+    "ompdart_summarize_callee": (C.c_int, [C.POINTER(Cfg), C.c_void_p, C.c_int32, C.c_void_p, C.POINTER(Opts)]),
+    "ompdart_analyze_program": (C.c_int, [C.POINTER(Program), C.POINTER(Opts), C.POINTER(C.POINTER(ProgramResult))]),
+    "ompdart_program_result_free": (None, [C.POINTER(ProgramResult)]),
     "ompdart_server_create": (C.c_int, [C.POINTER(ServerOpts), C.POINTER(C.c_void_p)]),
     "ompdart_server_submit": (C.c_int, [C.c_void_p, C.POINTER(Cfg), C.POINTER(C.c_int64)]),
     "ompdart_server_replay": (C.c_int, [C.c_void_p, C.POINTER(Cfg), C.c_int32, C.c_void_p, C.c_void_p]),
@@ -434,3 +455,69 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def summarize_batch(cfgs, **opts):
+    """``ompdart_summarize_batch``: ([7, W_i] summary or None, status) per callee."""
+    lib = load()
+    bi = _BatchInputs(cfgs)
+    outs = [np.zeros((7, x.W), dtype=np.uint64) for x in bi.inp]
+    ptrs = (C.c_void_p * max(1, bi.n))(*[o.ctypes.data for o in outs])
+    st = np.zeros(max(1, bi.n), dtype=np.int32)
+    _check(lib.ompdart_summarize_batch(bi.arr, bi.n, C.byref(_opts(**opts)), ptrs, st.ctypes.data))
+    return [o if s == 0 else None for o, s in zip(outs, st[: bi.n])], st[: bi.n]
+
+
+def summarize_callee(cfg, var_map, caller_n_vars, **opts) -> np.ndarray:
+    """``ompdart_summarize_callee``: the callee's summary as a [7, W_caller]
+    call-table row of the caller (var_map: caller variable per callee
+    variable, -1 to drop; None = identity)."""
+    lib = load()
+    inp = _Inputs(cfg)
+    row = np.zeros((7, (int(caller_n_vars) + 63) // 64), dtype=np.uint64)
+    vm = None if var_map is None else np.ascontiguousarray(var_map, dtype=np.int32)
+    _check(lib.ompdart_summarize_callee(C.byref(inp.c), None if vm is None else vm.ctypes.data, int(caller_n_vars),
+                                        row.ctypes.data, C.byref(_opts(**opts))))
+    return row
+
+
+def _u64(ptr, n):
+    if not ptr or n == 0:
+        return np.zeros(n, dtype=np.uint64)
+    return np.frombuffer((C.c_char * (8 * n)).from_address(ptr), dtype=np.uint64).copy()
+
+
+def analyze_program(funcs, site_off, site_callee, var_maps, max_contexts=0, **opts) -> dict:
+    """``ompdart_analyze_program``: funcs are CFGs whose call accesses name
+    their k-th call site (site_off[f] + k); var_maps[s] maps site s's callee
+    variables to caller variables (-1 for a local).  Returns
+    {"instances": [(func, (entry_h, entry_d, exit_live), status, result)],
+     "summaries": [[7, W_f] per function], "height": [...], "levels": n}."""
+    lib = load()
+    bi = _BatchInputs(funcs)
+    so = np.ascontiguousarray(site_off, dtype=np.int32)
+    sc = np.ascontiguousarray(site_callee, dtype=np.int32)
+    mo = np.zeros(len(var_maps) + 1, dtype=np.int32)
+    mo[1:] = np.cumsum([len(m) for m in var_maps])
+    vm = np.ascontiguousarray(np.concatenate([np.asarray(m, dtype=np.int32) for m in var_maps])
+                              if var_maps else np.zeros(0, np.int32))
+    prog = Program(bi.n, C.cast(bi.arr, C.POINTER(Cfg)), so.ctypes.data, sc.ctypes.data, mo.ctypes.data,
+                   vm.ctypes.data, int(max_contexts))
+    res = C.POINTER(ProgramResult)()
+    _check(lib.ompdart_analyze_program(C.byref(prog), C.byref(_opts(**opts)), C.byref(res)))
+    try:
+        r = res.contents
+        F = bi.n
+        height = np.frombuffer((C.c_char * (4 * max(F, 1))).from_address(r.height), dtype=np.int32)[:F].copy()
+        soff = np.frombuffer((C.c_char * (8 * max(F, 1))).from_address(r.summary_off), dtype=np.int64)[:F].copy()
+        sums = [_u64(r.summaries + 8 * int(soff[f]), 7 * bi.inp[f].W).reshape(7, -1) if r.summaries else None
+                for f in range(F)]
+        inst = []
+        for i in range(r.n_instances):
+            x = r.inst[i]
+            W = bi.inp[x.func].W
+            ctx = (_u64(x.entry_h, W), _u64(x.entry_d, W), _u64(x.exit_live, W))
+            inst.append((x.func, ctx, x.status, _result_to_numpy(x.result.contents) if x.result else None))
+        return {"instances": inst, "summaries": sums, "height": height, "levels": r.levels}
+    finally:
+        lib.ompdart_program_result_free(res)

@@ -157,4 +157,8 @@ cudaStream_t batch_stream(const ompdart_batch *B);
 // device bytes a plan of this CFG is expected to hold (admission estimate)
 long long estimate_device_bytes(const ompdart_cfg &c, int keep_states);
 
+// ---- summary.cu: callee summaries (rows[i]: 7 * W_i words, callee numbering)
+int summarize_run(const ompdart_cfg *cfgs, int n, const ompdart_opts &o, uint64_t *const *rows, int32_t *status);
+void map_summary(const uint64_t *sum, int callee_vars, const int32_t *var_map, int caller_vars, uint64_t *row);
+
 }  // namespace ompdart

@@ -431,3 +431,74 @@ def restrict_word(g: CFG, w: int) -> tuple[CFG, np.ndarray]:
     h = CFG(g.n_blocks, nv, g.entry, g.succ_off, g.succ, ao, acc, g.region,
             sl(g.entry_host_valid), sl(g.entry_dev_valid), sl(g.exit_host_live))
     return h, keep
+
+
+# --------------------------------------------------------------------------
+# interprocedural workload: a call graph of functions
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Program:
+    """Functions (CFGs over globals + their pointer parameters) and call
+    sites: function f's k-th call site is site site_off[f] + k, named by the
+    call pseudo-access with row k; site s calls site_callee[s] and
+    var_maps[s][v] is the caller variable callee variable v denotes."""
+    funcs: list
+    site_off: np.ndarray
+    site_callee: np.ndarray
+    var_maps: list
+    n_globals: int
+    level: np.ndarray
+    meta: dict = dataclasses.field(default_factory=dict)
+
+
+def call_graph(seed=4, n_funcs=2000, max_depth=8, fanout=(1, 6), blocks=(32, 4096), median_blocks=256,
+               n_globals=512, max_formals=4) -> Program:
+    """A call DAG of n_funcs functions over n_globals globals: each function
+    sits on a level 0..max_depth-1 (level 0 are the roots; the last level
+    are leaves) and every non-leaf calls 1..6 functions of deeper levels
+    (most often the next one).  A function has 0..max_formals pointer
+    parameters (variables n_globals.. of its own numbering); each call
+    passes, per parameter, a random global or one of the caller's own
+    parameters.  Each function's CFG is structured with lognormal block
+    counts (median `median_blocks`, clipped to `blocks`), 1-8 accesses per
+    block (uniform variables, R:W = 70:30, ~20% target blocks in 3 runs) and
+    its calls inserted at random places of random blocks."""
+    rng = np.random.default_rng(seed)
+    level = np.sort(rng.integers(0, max_depth, size=n_funcs))
+    level[: max(1, n_funcs // 50)] = 0
+    by_level = [np.flatnonzero(level == L) for L in range(max_depth)]
+    n_formals = rng.integers(0, max_formals + 1, size=n_funcs)
+    sizes = batch_sizes(rng, n_funcs, median=median_blocks, lo=blocks[0], hi=blocks[1])
+    funcs, site_callee, var_maps, site_off = [], [], [], [0]
+    for f in range(n_funcs):
+        nv = n_globals + int(n_formals[f])
+        g = structured(None, int(sizes[f]), nv, p_if_then=0.11, p_if_else=0.125, p_while=0.065, body_mean=2.0,
+                       max_depth=5, max_loop_depth=3, region_mode="count", target_frac=0.2, n_regions=3,
+                       region_max_depth=2, acc_min=1, acc_max=8, var_dist="uniform", p_write=0.3, rng=rng)
+        L = int(level[f])
+        deeper = [x for x in range(L + 1, max_depth) if len(by_level[x])]
+        callees = []
+        if deeper:
+            for _ in range(int(rng.integers(fanout[0], fanout[1] + 1))):
+                nxt = deeper[0] if rng.random() < 0.7 else deeper[int(rng.integers(0, len(deeper)))]
+                callees.append(int(rng.choice(by_level[nxt])))
+        accs = [list(g.acc[g.acc_off[b]:g.acc_off[b + 1]]) for b in range(g.n_blocks)]
+        for k, c in enumerate(callees):
+            b = int(rng.integers(0, g.n_blocks))
+            accs[b].insert(int(rng.integers(0, len(accs[b]) + 1)), np.uint32(0x80000000 | k))
+            vm = np.arange(n_globals + int(n_formals[c]), dtype=np.int32)
+            for j in range(int(n_formals[c])):  # actual of each pointer parameter
+                vm[n_globals + j] = int(rng.integers(0, nv)) if rng.random() < 0.5 or nv == n_globals \
+                    else n_globals + int(rng.integers(0, nv - n_globals))
+            site_callee.append(c)
+            var_maps.append(vm)
+        ao = np.zeros(g.n_blocks + 1, dtype=np.int32)
+        ao[1:] = np.cumsum([len(x) for x in accs])
+        h = CFG(g.n_blocks, nv, 0, g.succ_off, g.succ, ao, np.array([a for x in accs for a in x], dtype=np.uint32),
+                g.region)
+        h.meta = dict(g.meta, n_acc=int(ao[-1]), calls=len(callees), level=L)
+        funcs.append(h)
+        site_off.append(len(site_callee))
+    return Program(funcs, np.array(site_off, dtype=np.int32), np.array(site_callee, dtype=np.int32), var_maps,
+                   n_globals, level, dict(seed=seed, n_funcs=n_funcs, max_depth=max_depth))
