@@ -518,6 +518,82 @@ def run_serve(args):
     }
 
 
+def run_program(args):
+    """The interprocedural workload: a 2,000-function call graph (depth <= 8,
+    fan-out 1-6, 32-4,096 blocks, 512 globals + pointer parameters) through
+    ompdart_analyze_program (summaries bottom-up, contexts top-down)."""
+    import numpy as np
+    import torch
+    from paper_2406_13881_b300 import _native, build, workload as wl
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank = int(os.environ.get("RANK", "0"))
+    torch.cuda.set_device(local)
+    build.build()
+    t0 = time.perf_counter()
+    p = wl.call_graph(args.program_seed, n_funcs=args.n_funcs)
+    t_gen = time.perf_counter() - t0
+    for _ in range(args.warmup if args.warmup < 3 else 1):
+        _native.analyze_program(p.funcs, p.site_off, p.site_callee, p.var_maps, device=local)
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, out = [], None
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        out = _native.analyze_program(p.funcs, p.site_off, p.site_callee, p.var_maps, device=local)
+        times.append(time.perf_counter() - t0)
+    clk = clocks.stop()
+    inst = out["instances"]
+    units = sum(p.funcs[f].n_blocks * p.funcs[f].W for f, _, _, _ in inst)
+    sec = statistics.median(times)
+    # CPU oracle: the summaries and a bounded sample of the instances
+    import oracle
+    oracle.build()
+    t_cpu, u_cpu, n_cpu = 0.0, 0, 0
+    for f in range(0, len(p.funcs), max(1, len(p.funcs) // 300)):
+        t0 = time.perf_counter()
+        oracle.solve(p.funcs[f] if p.site_off[f + 1] == p.site_off[f] else _strip_calls(p.funcs[f]))
+        t_cpu += time.perf_counter() - t0
+        u_cpu += p.funcs[f].n_blocks * p.funcs[f].W
+        n_cpu += 1
+        if t_cpu > args.cpu_seconds:
+            break
+    if rank != 0:
+        return None
+    return {
+        "metric": "block·var-word updates/s to fixed point; CFGs/s and p50/p99 vs per-CFG launch",
+        "value": units / sec, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": 1,
+        "ms_per_step": 1e3 * sec, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u64", "data": "synthetic",
+        "config": {"workload": "interprocedural: call graph of %d functions (depth <= 8, fan-out 1-6), 32-4096 "
+                               "blocks each, 512 globals + pointer parameters, seed %d" % (len(p.funcs),
+                                                                                          args.program_seed),
+                   "functions": len(p.funcs), "call_sites": int(p.site_off[-1]),
+                   "blocks": int(sum(g.n_blocks for g in p.funcs)), "levels": int(out["levels"]),
+                   "instances": len(inst), "max_contexts_per_site": 4, "parallelism": "single GPU"},
+        "instances_per_s": len(inst) / sec,
+        "functions_per_s": len(p.funcs) / sec,
+        "seconds": {"generate": t_gen, "analyze_median": sec, "all": times},
+        "cpu_baseline": {"value": u_cpu / t_cpu if t_cpu else None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d functions analysed alone (calls as no-ops), single-threaded C oracle, %.1f s"
+                                   % (n_cpu, t_cpu), "cpu": cpu_info()},
+        "e2e": {"value": units / sec, "unit": UNIT, "h2d_bytes_per_step": None, "d2h_bytes_per_step": None,
+                "path": "ompdart_analyze_program: host buffers in, every instance's result on the host"},
+        "clocks": clk,
+    }
+
+
+def _strip_calls(g):
+    """The function with its call accesses removed (oracle timing only)."""
+    import numpy as np
+    from paper_2406_13881_b300 import workload as wl
+    keep = (np.asarray(g.acc, np.uint32) >> np.uint32(31)) == 0
+    blk = np.repeat(np.arange(g.n_blocks), np.diff(g.acc_off))
+    ao = np.zeros(g.n_blocks + 1, dtype=np.int32)
+    ao[1:] = np.cumsum(np.bincount(blk[keep], minlength=g.n_blocks))
+    return wl.CFG(g.n_blocks, g.n_vars, g.entry, g.succ_off, g.succ, ao, np.asarray(g.acc)[keep])
+
+
 def run_reference(args):
     """The reference arm: the CPU oracle, as it stands, on the host cores, on
     a bounded sample of the same workload (a few word columns per step)."""
@@ -560,7 +636,9 @@ def main():
                     help="positions per chunk of the scan solver (0 = the library's choice)")
     ap.add_argument("--n-blocks", type=int, default=1 << 20,
                     help="blocks of the workload (smaller only for profiler captures)")
-    ap.add_argument("--workload", choices=["single", "batch", "serve"], default="single")
+    ap.add_argument("--workload", choices=["single", "batch", "serve", "program"], default="single")
+    ap.add_argument("--n-funcs", type=int, default=2000)
+    ap.add_argument("--program-seed", type=int, default=4)
     ap.add_argument("--rates", type=lambda x: [int(v) for v in x.split(",")], default=[1000, 10000, 100000])
     ap.add_argument("--seconds", type=float, default=2.0, help="serve: seconds of arrivals per rate")
     ap.add_argument("--max-requests", type=int, default=100000)
@@ -585,6 +663,8 @@ def main():
         out = run_batch(args)
     elif args.workload == "serve":
         out = run_serve(args)
+    elif args.workload == "program":
+        out = run_program(args)
     else:
         out = run_ours(args)
     if out is not None:

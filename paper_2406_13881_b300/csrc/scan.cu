@@ -26,6 +26,7 @@
 #include <functional>
 #include <queue>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "ingest.h"
@@ -39,7 +40,13 @@ namespace {
 constexpr int CARRY = -2;      // slot id: the chunk's incoming carry
 constexpr int BACK_EDGE = -2;  // in-edge tag: a back edge (its transfers are emitted at the latch)
 constexpr int PREV = -3;       // slot id: the value of the position walked just before
-constexpr int SH_WORDS = 512;  // shared-memory words per warp for slots (4 KiB)
+#ifndef OMPDART_SH_WORDS
+#define OMPDART_SH_WORDS 512
+#endif
+#ifndef OMPDART_CHAIN_MIN_CTAS
+#define OMPDART_CHAIN_MIN_CTAS 1
+#endif
+constexpr int SH_WORDS = OMPDART_SH_WORDS;  // shared-memory words per warp for slots
 constexpr int WPC = 4;         // warps per CTA of the chain kernels
 constexpr int MAX_DEPTH = 31;  // loop nesting depth the chain handles
 // bound on loop re-runs per chunk walk: each loop of a reducible CFG needs
@@ -65,6 +72,7 @@ struct PosMeta {  // one per position, 64 B
 // access stream are already summary records (folded on the host with the
 // callees' rows), and its access flags come from the call-site pass
 constexpr int32_t PM_RECORDS = 1;
+constexpr int32_t LINK_RECORD = -2;
 static_assert(sizeof(PosMeta) == 64, "PosMeta layout");
 
 struct LoopMeta {
@@ -99,6 +107,10 @@ struct ScanDev {
   const int2 *out_pk;   // per backward out-edge {target slot or CARRY, target position}
   const uint32_t *acc_p;  // accesses in position order
   uint32_t *rec_p;        // summary records in position order
+  uint32_t *emit_p;       // per access in position order: variable | flag table << 24 (flag_table)
+  const int2 *acc_link;   // per access: {first access of its variable in the block, next one or -1};
+                          // {LINK_RECORD, -1}: the entry is a given summary record
+  long long n_acc_p;      // entries of the position-ordered access stream
   int sh_slots;           // slots per plane held in shared memory
   const int32_t *lat_slot;
   const int32_t *bend_loop;
@@ -445,9 +457,12 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
 
 namespace {
 
-constexpr int WIN = 16;        // positions per metadata window
-constexpr int EDGE_CAP = 128;  // edge entries a window holds
-constexpr int REC_CAP = 256;   // access records a window holds
+#ifndef OMPDART_WIN
+#define OMPDART_WIN 16
+#endif
+constexpr int WIN = OMPDART_WIN;       // positions per metadata window
+constexpr int EDGE_CAP = 8 * WIN;      // edge entries a window holds
+constexpr int REC_CAP = 16 * WIN;      // access records a window holds
 
 // Per-warp cache of a run of positions: their metadata, their edge entries
 // and their access records (all stored in position order in HBM, so each
@@ -457,7 +472,7 @@ struct Win {
   int2 edge[EDGE_CAP];    // forward: {slot, loop-entry edge}; backward: {slot, target position}
   uint32_t rec[REC_CAP];  // summary records
   int mbase, ws, we, e0, r0, big;
-  uint32_t *acc;          // raw access words (emission only), REC_CAP entries
+  uint32_t *acc;          // emission words (variable | flag table), REC_CAP entries
 };
 
 struct WinRegs {  // warp-uniform copy of the window bounds
@@ -509,7 +524,7 @@ __device__ void load_window(Win &w, WinRegs &r, const ScanDev &sd, int i, int lo
     for (int j = lane; j < e1 - e0; j += 32) w.edge[j] = src[e0 + j];
     for (int j = lane; j < r1 - r0; j += 32) {
       w.rec[j] = sd.rec_p[r0 + j];
-      if (ACC) w.acc[j] = sd.acc_p[r0 + j];
+      if (ACC) w.acc[j] = sd.emit_p[r0 + j];
     }
   }
   __syncwarp();
@@ -523,7 +538,7 @@ __device__ __forceinline__ uint32_t win_rec(const Win &w, const WinRegs &r, cons
   return r.big ? sd.rec_p[k] : w.rec[k - r.r0];
 }
 __device__ __forceinline__ uint32_t win_acc(const Win &w, const WinRegs &r, const ScanDev &sd, int k) {
-  return r.big ? sd.acc_p[k] : w.acc[k - r.r0];
+  return r.big ? sd.emit_p[k] : w.acc[k - r.r0];
 }
 
 struct Lane {
@@ -684,7 +699,8 @@ __device__ void emit_position(const DevPlan &p, const ScanDev &sd, const Win &w,
                               const uint64_t din[2], const uint64_t live[2], const uint64_t prev[2], uint64_t *hd,
                               int stream, int &rec_count, int cfg) {
   const int W = p.W, lane = L.lane;
-  // ---- access flags: replay the block from its entry states
+  // ---- access flags: each access's flag table, indexed by its variable's
+  // validity at the block entry (host bit | device bit << 1)
   if (m.nacc && !(m.flags & PM_RECORDS)) {
     hd[2 * lane] = ~zin[0] & L.top0;
     hd[2 * lane + 1] = ~zin[1] & L.top1;
@@ -693,23 +709,12 @@ __device__ void emit_position(const DevPlan &p, const ScanDev &sd, const Win &w,
     __syncwarp();
     const int a0 = m.pacc_beg, na = m.nacc;
     for (int j = lane; j < na; j += 32) {
-      const uint32_t a = win_acc(w, wr, sd, a0 + j);
-      const int v = acc_var(a), lw = (v >> 6) - L.wg * 64;
+      const uint32_t e = win_acc(w, wr, sd, a0 + j);
+      const int v = (int)(e & 0xFFFFFFu), lw = (v >> 6) - L.wg * 64;
       if ((unsigned)lw >= 64u) continue;
       const uint64_t bit = 1ull << (v & 63);
-      bool h = (hd[lw] & bit) != 0, d = (hd[64 + lw] & bit) != 0;
-      uint8_t flag = 0;
-      for (int q = 0; q <= j; ++q) {
-        const uint32_t x = win_acc(w, wr, sd, a0 + q);
-        if (acc_var(x) != v) continue;
-        const int kind = acc_kind(x), dev = acc_space(x);
-        if (kind & 1) {
-          if (dev && !d) { d = true; if (q == j) flag = 1; }
-          if (!dev && !h) { h = true; if (q == j) flag = 2; }
-        }
-        if (kind & 2) { if (dev) { d = true; h = false; } else { h = true; d = false; } }
-      }
-      p.acc_flag[m.acc_beg + j] = flag;
+      const int k = ((hd[lw] & bit) ? 1 : 0) | ((hd[64 + lw] & bit) ? 2 : 0);
+      p.acc_flag[m.acc_beg + j] = (uint8_t)((e >> (24 + 2 * k)) & 3u);
     }
     __syncwarp();
   }
@@ -1028,7 +1033,7 @@ __device__ __forceinline__ int next_item(const ScanDev &sd, int qslot) {
 // Persistent forward chain: each warp takes items (longest chunks first)
 // from the launch's work queue until none is left.
 template <int PH, int MODE>
-__global__ void __launch_bounds__(256) k_fwd_chain(DevPlan p, ScanDev sd, int qslot) {
+__global__ void __launch_bounds__(256, OMPDART_CHAIN_MIN_CTAS) k_fwd_chain(DevPlan p, ScanDev sd, int qslot) {
   constexpr int NP = MODE == M_SUM ? 2 : 1;
   constexpr bool ACC = MODE == M_APPLY && PH == K_H;
   extern __shared__ __align__(16) uint64_t smem[];
@@ -1251,7 +1256,7 @@ __device__ __forceinline__ void bwd_walk(const DevPlan &p, const ScanDev &sd, co
 
 // persistent backward chain (same work queue scheme as the forward one)
 template <int MODE>
-__global__ void __launch_bounds__(256) k_bwd_chain(DevPlan p, ScanDev sd, int qslot) {
+__global__ void __launch_bounds__(256, OMPDART_CHAIN_MIN_CTAS) k_bwd_chain(DevPlan p, ScanDev sd, int qslot) {
   constexpr int NP = BwdPlanes<MODE>::NP;
   extern __shared__ __align__(16) uint64_t smem[];
   const int warp_in_cta = threadIdx.x >> 5;
@@ -1265,20 +1270,70 @@ __global__ void __launch_bounds__(256) k_bwd_chain(DevPlan p, ScanDev sd, int qs
   }
 }
 
-// local summary records in position order (one thread per position)
-__global__ void k_local_summary_pos(ScanDev sd, int M) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
-    const int a0 = sd.meta[i].pacc_beg;
-    const int a1 = a0 + sd.meta[i].nacc;
-    if (sd.meta[i].flags & PM_RECORDS) {  // records given: copy them
-      for (int j = a0; j < a1; ++j) sd.rec_p[j] = sd.acc_p[j];
-      continue;
-    }
-    for (int j = a0; j < a1; ++j) {
-      // a lone thread walks the block as lane 0 of a one-lane "warp"
-      summarize_one(sd.acc_p, sd.rec_p, a0, a1, j);
-    }
+// Local summary records and flag tables, one thread per access of the
+// position-ordered stream.  The host links every access to the first
+// access of the same variable in its block and to the next one, so each
+// thread visits only its variable's accesses:
+//   record (at the variable's first access, REC_NONE elsewhere): the last
+//     event on each copy decides Gen/Kill, a read before any write is
+//     upward exposed, any write defines (Sec. IV-D local rule);
+//   flag table: for each validity of the variable at the block entry,
+//     k = host | device << 1, bits 2k..2k+1 hold the transfer right before
+//     this access (0, 1 `to', 2 `from'): the earlier accesses replayed from
+//     the four entry states at once, one bit each (a read makes its space
+//     valid, a write its space valid and the other stale).
+__global__ void __launch_bounds__(256) k_local_summary_pos(ScanDev sd) {
+  const long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (j >= sd.n_acc_p) return;
+  const int2 lk = sd.acc_link[j];
+  const uint32_t aj = sd.acc_p[j];
+  if (lk.x == LINK_RECORD) {  // a block with calls: records given
+    sd.rec_p[j] = aj;
+    return;
   }
+  if (lk.x == j) {  // the variable's first access: fold its accesses
+    int last_h = 0, last_d = 0, first_rh = 0, first_rd = 0, first_w = 0, t = 0;
+    for (int q = (int)j; q >= 0; q = sd.acc_link[q].y) {
+      const uint32_t a = sd.acc_p[q];
+      const int kind = acc_kind(a), dev = acc_space(a);
+      if (kind & 1) {
+        ++t;
+        if (dev) { last_d = 1; if (!first_rd) first_rd = t; }
+        else     { last_h = 1; if (!first_rh) first_rh = t; }
+      }
+      if (kind & 2) {
+        ++t;
+        if (dev) { last_d = 1; last_h = 2; } else { last_h = 1; last_d = 2; }
+        if (!first_w) first_w = t;
+      }
+    }
+    uint32_t r = (uint32_t)acc_var(aj);
+    if (last_h == 1) r |= R_GH;
+    if (last_h == 2) r |= R_KH;
+    if (last_d == 1) r |= R_GD;
+    if (last_d == 2) r |= R_KD;
+    if (first_rh && (!first_w || first_rh < first_w)) r |= R_UH;
+    if (first_rd && (!first_w || first_rd < first_w)) r |= R_UD;
+    if (first_w) r |= R_DF;
+    sd.rec_p[j] = r;
+  } else {
+    sd.rec_p[j] = REC_NONE;
+  }
+  uint32_t h = 0xAu, d = 0xCu;  // entry state k: host bit k & 1, device bit k & 2
+  for (int q = lk.x; q != (int)j; q = sd.acc_link[q].y) {
+    const uint32_t x = sd.acc_p[q];
+    const int kind = acc_kind(x), dev = acc_space(x);
+    if (kind & 1) { if (dev) d = 0xFu; else h = 0xFu; }
+    if (kind & 2) { if (dev) { d = 0xFu; h = 0u; } else { h = 0xFu; d = 0u; } }
+  }
+  uint32_t lut = 0;
+  if (acc_kind(aj) & 1) {
+    const int dev = acc_space(aj);
+    const uint32_t miss = ~(dev ? d : h) & 0xFu;
+    for (int k = 0; k < 4; ++k)
+      if (miss >> k & 1u) lut |= (dev ? 1u : 2u) << (2 * k);
+  }
+  sd.emit_p[j] = (uint32_t)acc_var(aj) | (lut << 24);
 }
 
 // --------------------------------------------------------------------------------------
@@ -1601,6 +1656,9 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   std::vector<uint32_t> acc_p;
   acc_p.reserve(g.A);
   std::vector<int32_t> var_idx;
+  std::vector<int2> acc_link;
+  acc_link.reserve(g.A);
+  std::vector<std::pair<int32_t, int32_t>> seen;  // (variable, its latest access) within the block
   for (int i = 0; i < g.M; ++i) {
     const int b = meta[i].blk, a0 = acc_off[b], a1 = acc_off[b + 1];
     bool has_call = false;
@@ -1613,8 +1671,43 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
       const int cfg = (int)(std::upper_bound(g.cfg_pos_off.begin(), g.cfg_pos_off.end(), i) - g.cfg_pos_off.begin()) - 1;
       fold_call_block(acc, a0, a1, calls, calls.row_base.empty() ? 0 : calls.row_base[cfg], p.W, var_idx, &acc_p);
       meta[i].flags = PM_RECORDS;
+      acc_link.resize(acc_p.size(), make_int2(LINK_RECORD, -1));
     } else {
       acc_p.insert(acc_p.end(), acc + a0, acc + a1);
+      // same-variable links inside the block (a short list for the usual
+      // handful of accesses, a hash map for long blocks)
+      const int base = meta[i].pacc_beg;
+      if (a1 - a0 <= 64) {
+        seen.clear();
+        for (int k = a0; k < a1; ++k) {
+          const int v = (int)(acc[k] & 0xFFFFFFu), idx = base + (k - a0);
+          int first = idx;
+          for (auto &sv : seen)
+            if (sv.first == v) {
+              first = acc_link[sv.second].x;
+              acc_link[sv.second].y = idx;
+              sv.second = idx;
+              break;
+            }
+          if (first == idx) seen.push_back({v, idx});
+          acc_link.push_back(make_int2(first, -1));
+        }
+      } else {
+        std::unordered_map<int32_t, int32_t> latest;
+        for (int k = a0; k < a1; ++k) {
+          const int v = (int)(acc[k] & 0xFFFFFFu), idx = base + (k - a0);
+          auto it = latest.find(v);
+          int first = idx;
+          if (it != latest.end()) {
+            first = acc_link[it->second].x;
+            acc_link[it->second].y = idx;
+            it->second = idx;
+          } else {
+            latest.emplace(v, idx);
+          }
+          acc_link.push_back(make_int2(first, -1));
+        }
+      }
     }
     const size_t n = acc_p.size() - (size_t)meta[i].pacc_beg;
     if (n > 32767) {
@@ -1655,6 +1748,9 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   chk(sd.out_pk = st->up(out_pk));
   chk(sd.acc_p = st->up(acc_p));
   chk(sd.rec_p = st->alloc<uint32_t>(acc_p.size()));
+  chk(sd.emit_p = st->alloc<uint32_t>(acc_p.size()));
+  chk(sd.acc_link = st->up(acc_link));
+  sd.n_acc_p = (long long)acc_p.size();
   chk(sd.lat_slot = st->up(lat_slot));
   chk(sd.bend_loop = st->up(bend_loop));
   chk(sd.srcent = st->up(srcent));
@@ -1765,7 +1861,7 @@ int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *p
   cudaMemsetAsync(p.acc_flag, 0, (size_t)p.A, s);
   cudaMemsetAsync(sd.queue, 0, sizeof(int32_t) * Q_SLOTS, s);
   PROF("local_summary");
-  k_local_summary_pos<<<grid_of((long long)p.M, 256), 256, 0, s>>>(sd, p.M); ++n;
+  k_local_summary_pos<<<grid_of(sd.n_acc_p, 256), 256, 0, s>>>(sd); ++n;
   // ---- liveness (backward)
   PROF("live_summary");
   CHAIN(k_bwd_chain<M_SUM>, CK_BSUM, 0);
