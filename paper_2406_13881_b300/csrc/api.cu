@@ -145,10 +145,9 @@ int core_build(PlanCore *P, const int32_t *acc_off, const uint32_t *acc, const C
   chk(d.top = P->upload(top));
   chk(d.h_in = P->dalloc<uint64_t>(NW));
   chk(d.d_in = P->dalloc<uint64_t>(NW));
-  if (o.keep_states) {
-    chk(d.h_out = P->dalloc<uint64_t>(NW));
-    chk(d.d_out = P->dalloc<uint64_t>(NW));
-  }
+  // host validity at block exits: the scan solver's emission reads it
+  chk(d.h_out = P->dalloc<uint64_t>(NW));
+  if (o.keep_states) chk(d.d_out = P->dalloc<uint64_t>(NW));
   chk(d.live = P->dalloc<uint64_t>(NW));
   chk(d.mask_h = P->dalloc<uint64_t>((size_t)g.L * W));
   chk(d.mask_d = P->dalloc<uint64_t>((size_t)g.L * W));
@@ -218,10 +217,7 @@ int core_build(PlanCore *P, const int32_t *acc_off, const uint32_t *acc, const C
   }
   P->path = want;
   if (want == 1) {
-    if (!o.keep_states) {  // the sweep solver reads the exit states
-      chk(d.h_out = P->dalloc<uint64_t>(NW));
-      chk(d.d_out = P->dalloc<uint64_t>(NW));
-    }
+    if (!o.keep_states) chk(d.d_out = P->dalloc<uint64_t>(NW));  // the sweep solver reads the exit states
     chk(d.hp_out = P->dalloc<uint64_t>(NW));
     chk(d.ant_h = P->dalloc<uint64_t>(NW));
     chk(d.ant_d = P->dalloc<uint64_t>(NW));

@@ -121,6 +121,15 @@ struct ScanDev {
   uint64_t *gsum, *psum;   // [planes][C][W] chunk maps
   uint64_t *carry;         // [planes][C][W] carry into each chunk
   uint64_t *hp_src, *d_src;  // [K][W] plain host / device validity at loop-entry sources
+  // affine pairs the summary walks leave per position: value = G | (carry & P)
+  // with the carry into the position's chunk (resolved by k_resolve_*)
+  uint64_t *pair_g, *pair_p;    // [N][W] by block: Live_in, D_in stale, or H_out stale
+  uint64_t *pair_g2, *pair_p2;  // [N][W] D_out stale (kept states only), else null
+  uint64_t *src_g, *src_p;      // [K][W] out value at each loop-entry edge's source
+  const int32_t *pos_chunk;     // [M] chunk of each position
+  const int32_t *src_pos;       // [K] position of each loop-entry edge's source
+  const int2 *emit_rng;         // [n_emit] position ranges of the emission items (within one chunk)
+  int n_emit;
   uint64_t *xval;      // [n_carry_src][W] host-stale sets of crossing-edge sources
   int32_t *rec_cnt;    // [streams]
   const int32_t *rec_base, *rec_cap;  // [streams]
@@ -183,6 +192,7 @@ struct ScanState {
   std::vector<int32_t> h_rec_cap;  // host copy of capacities
   int32_t *d_rec_cap = nullptr, *d_rec_base = nullptr;
   int32_t *offs = nullptr;         // stream offsets in the gathered result
+  std::vector<int32_t> chunk_item0;  // [C+1] first emission item of each chunk
   uint64_t *init = nullptr;        // [W] stale set entering the first chunk
   EdgeXfer *stream_buf = nullptr;
   long long bytes = 0;  // device bytes held
@@ -930,7 +940,37 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
       pvo[pl][0] = pv[pl][0]; pvo[pl][1] = pv[pl][1];
       pv[pl][0] = zo[pl][0]; pv[pl][1] = zo[pl][1];
     }
-    // ---- outputs
+    // ---- outputs: the summary walk leaves each position's affine pairs
+    if (MODE == M_SUM && sd.pair_g) {
+      const size_t row = (size_t)m.blk;
+      if (PH == K_D) {  // device validity at the block entry (and exit, kept states)
+        st_word(sd.pair_g, row, W, L.w0, z[0][0]);
+        st_word(sd.pair_g, row, W, L.w0 + 1, z[0][1]);
+        st_word(sd.pair_p, row, W, L.w0, z[1][0]);
+        st_word(sd.pair_p, row, W, L.w0 + 1, z[1][1]);
+        if (sd.pair_g2) {
+          st_word(sd.pair_g2, row, W, L.w0, zo[0][0]);
+          st_word(sd.pair_g2, row, W, L.w0 + 1, zo[0][1]);
+          st_word(sd.pair_p2, row, W, L.w0, zo[1][0]);
+          st_word(sd.pair_p2, row, W, L.w0 + 1, zo[1][1]);
+        }
+      }
+      if (PH == K_H) {  // host validity at the block exit
+        st_word(sd.pair_g, row, W, L.w0, zo[0][0]);
+        st_word(sd.pair_g, row, W, L.w0 + 1, zo[0][1]);
+        st_word(sd.pair_p, row, W, L.w0, zo[1][0]);
+        st_word(sd.pair_p, row, W, L.w0 + 1, zo[1][1]);
+      }
+      if ((PH == K_HP || PH == K_D) && m.nsrcent) {  // at loop-entry sources
+        for (int q = 0; q < m.nsrcent; ++q) {
+          const int k = sd.srcent[m.srcent_beg + q];
+          st_word(sd.src_g, k, W, L.w0, zo[0][0]);
+          st_word(sd.src_g, k, W, L.w0 + 1, zo[0][1]);
+          st_word(sd.src_p, k, W, L.w0, zo[1][0]);
+          st_word(sd.src_p, k, W, L.w0 + 1, zo[1][1]);
+        }
+      }
+    }
     if (MODE == M_APPLY) {
       const size_t row = (size_t)m.blk;
       if (PH == K_D) {
@@ -1169,6 +1209,12 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
       st_word(p.live, m.blk, W, L.w0, z[0][0]);
       st_word(p.live, m.blk, W, L.w0 + 1, z[0][1]);
     }
+    if (MODE == M_SUM && sd.pair_g) {  // Live_in as an affine pair of the chunk's carry
+      st_word(sd.pair_g, m.blk, W, L.w0, z[0][0]);
+      st_word(sd.pair_g, m.blk, W, L.w0 + 1, z[0][1]);
+      st_word(sd.pair_p, m.blk, W, L.w0, z[1][0]);
+      st_word(sd.pair_p, m.blk, W, L.w0 + 1, z[1][1]);
+    }
     __syncwarp();
 #pragma unroll
     for (int pl = 0; pl < NP; ++pl) {
@@ -1334,6 +1380,141 @@ __global__ void __launch_bounds__(256) k_local_summary_pos(ScanDev sd) {
       if (miss >> k & 1u) lut |= (dev ? 1u : 2u) << (2 * k);
   }
   sd.emit_p[j] = (uint32_t)acc_var(aj) | (lut << 24);
+}
+
+// --------------------------------------------------------------------------------------
+// resolve: every position's value from its pair and its chunk's carry
+// --------------------------------------------------------------------------------------
+enum ResolveKind { RV_LIVE = 0, RV_VALID = 1 };  // liveness as is; stale sets to valid sets
+
+// out[b] = G[b] | (carry[chunk] & P[b]), converted for RV_VALID to ~x & top
+// (the CFG's valid-variable mask).  A thread takes two consecutive words
+// of a row (16-byte accesses when W is even); the grid strides over
+// (position, word pair).
+template <int KIND>
+__global__ void __launch_bounds__(256) k_resolve(DevPlan p, ScanDev sd, const uint64_t *G, const uint64_t *P,
+                                                 uint64_t *out) {
+  const int W = p.W, W2 = (W + 1) >> 1;
+  const long long n = (long long)p.M * W2;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(t / W2), w = 2 * (int)(t % W2);
+    const int b = p.order[i], c = sd.pos_chunk[i];
+    const size_t o = (size_t)b * W + w, oc = (size_t)c * W + w;
+    const uint64_t *tp = p.top + (size_t)sd.chunks[c].cfg * W + w;
+    if ((W & 1) == 0) {
+      const ulonglong2 g = *reinterpret_cast<const ulonglong2 *>(G + o);
+      const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(P + o);
+      const ulonglong2 k = *reinterpret_cast<const ulonglong2 *>(sd.carry + oc);
+      ulonglong2 x = make_ulonglong2(g.x | (k.x & q.x), g.y | (k.y & q.y));
+      if (KIND == RV_VALID) x = make_ulonglong2(~x.x & tp[0], ~x.y & tp[1]);
+      *reinterpret_cast<ulonglong2 *>(out + o) = x;
+    } else {
+      for (int u = 0; u < 2 && w + u < W; ++u) {
+        const uint64_t x = G[o + u] | (sd.carry[oc + u] & P[o + u]);
+        out[o + u] = KIND == RV_LIVE ? x : ~x & tp[u];
+      }
+    }
+  }
+}
+
+// the same for the out values at loop-entry sources ([K][W]), as valid sets
+__global__ void k_resolve_src(DevPlan p, ScanDev sd, uint64_t *out) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int W = p.W;
+  if (t >= (long long)p.K * W) return;
+  const int k = (int)(t / W), w = (int)(t % W);
+  const int c = sd.pos_chunk[sd.src_pos[k]];
+  const uint64_t x = sd.src_g[t] | (sd.carry[(size_t)c * W + w] & sd.src_p[t]);
+  out[t] = ~x & p.top[(size_t)sd.chunks[c].cfg * W + w];
+}
+
+// --------------------------------------------------------------------------------------
+// emission (Table II; Sec. IV-D), from the final states, one warp per
+// (chunk, word group), positions in order (no dependency between them):
+//   H_in = (OR over in-edges of the source's host-stale set, less the
+//          hoisted `from' of a loop-entry edge) minus the conflicts (live,
+//          valid on the device at no entry) resolved toward the host;
+//          the CFG's entry starts from its entry row;
+//   per in-edge p->b: `to' = hoisted device need not valid at p (loop
+//          entries), `from' = hoisted host need stale at p (loop entries)
+//          or a conflict the edge leaves stale on the host;
+//   per access: its flag table at the variable's entry validity;
+//   region exit: live after the exit and stale on the host.
+// --------------------------------------------------------------------------------------
+constexpr int EMIT_WARPS = 4;
+constexpr int EMIT_SPAN = 8;  // positions per emission item (its own record stream)
+__global__ void __launch_bounds__(32 * EMIT_WARPS) k_emit(DevPlan p, ScanDev sd, const uint64_t *init) {
+  __shared__ uint64_t hd_all[EMIT_WARPS][128];
+  const int gw = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
+  if (gw >= sd.n_emit * sd.G) return;
+  const int item = gw / sd.G, wg = gw % sd.G, lane = threadIdx.x & 31, W = p.W;
+  uint64_t *hd = hd_all[threadIdx.x >> 5];
+  const int2 rng = sd.emit_rng[item];
+  const ChunkMeta cm = sd.chunks[sd.pos_chunk[rng.x]];
+  const int w0 = wg * 64 + 2 * lane;
+  const uint64_t *tp = p.top + (size_t)cm.cfg * W;
+  const uint64_t top0 = w0 < W ? tp[w0] : 0, top1 = w0 + 1 < W ? tp[w0 + 1] : 0;
+  const uint64_t *xl = p.exit_live + (size_t)cm.cfg * W;
+  const int stream = item * sd.G + wg;
+  int rec_count = 0;
+  for (int i = rng.x; i < rng.y; ++i) {
+    const PosMeta m = sd.meta[i];
+    const size_t b = (size_t)m.blk;
+    const uint64_t lv0 = ld_word(p.live, b, W, w0), lv1 = ld_word(p.live, b, W, w0 + 1);
+    const uint64_t di0 = ld_word(p.d_in, b, W, w0), di1 = ld_word(p.d_in, b, W, w0 + 1);
+    const uint64_t c0 = lv0 & ~di0, c1 = lv1 & ~di1;
+    uint64_t z0 = 0, z1 = 0;
+    if (m.nfin == 0) {  // the CFG's entry
+      z0 = ld_word(init, cm.cfg, W, w0);
+      z1 = ld_word(init, cm.cfg, W, w0 + 1);
+    }
+    for (int q = 0; q < m.nfin; ++q) {
+      const int k = m.fin_beg + q;
+      const int ent = sd.fin_pk[k].y;  // loop-entry edge, -1, or BACK_EDGE
+      const size_t src = (size_t)p.fin_src[k];
+      const uint64_t s0 = ~ld_word(p.h_out, src, W, w0) & top0, s1 = ~ld_word(p.h_out, src, W, w0 + 1) & top1;
+      uint64_t m0 = 0, m1 = 0, to0 = 0, to1 = 0;
+      if (ent >= 0) {
+        m0 = ld_word(p.ec_h, ent, W, w0);
+        m1 = ld_word(p.ec_h, ent, W, w0 + 1);
+        to0 = ld_word(p.ec_d, ent, W, w0) & ~ld_word(sd.d_src, ent, W, w0);
+        to1 = ld_word(p.ec_d, ent, W, w0 + 1) & ~ld_word(sd.d_src, ent, W, w0 + 1);
+      }
+      const uint64_t e0 = s0 & ~m0, e1 = s1 & ~m1;
+      z0 |= e0;
+      z1 |= e1;
+      push_edge_records(sd, stream, rec_count, p.fin_eid[k], w0, to0, (m0 & s0) | (c0 & e0), to1,
+                        (m1 & s1) | (c1 & e1), lane);
+    }
+    z0 &= ~c0;
+    z1 &= ~c1;
+    const uint64_t hi0 = ~z0 & top0, hi1 = ~z1 & top1;
+    st_word(p.h_in, b, W, w0, hi0);
+    st_word(p.h_in, b, W, w0 + 1, hi1);
+    if (m.nacc && !(m.flags & PM_RECORDS)) {  // flag table at the entry validity
+      hd[2 * lane] = hi0;
+      hd[2 * lane + 1] = hi1;
+      hd[64 + 2 * lane] = di0;
+      hd[64 + 2 * lane + 1] = di1;
+      __syncwarp();
+      for (int j = lane; j < m.nacc; j += 32) {
+        const uint32_t e = sd.emit_p[m.pacc_beg + j];
+        const int v = (int)(e & 0xFFFFFFu), lw = (v >> 6) - wg * 64;
+        if ((unsigned)lw >= 64u) continue;
+        const uint64_t bit = 1ull << (v & 63);
+        const int kk = ((hd[lw] & bit) ? 1 : 0) | ((hd[64 + lw] & bit) ? 2 : 0);
+        p.acc_flag[m.acc_beg + j] = (uint8_t)((e >> (24 + 2 * kk)) & 3u);
+      }
+      __syncwarp();
+    }
+    if (m.exit_idx >= 0) {  // region exit: live after it and stale on the host
+      if (w0 < W) st_word(p.from_exit, m.exit_idx, W, w0, xl[w0] & ~ld_word(p.h_out, b, W, w0) & top0);
+      if (w0 + 1 < W)
+        st_word(p.from_exit, m.exit_idx, W, w0 + 1, xl[w0 + 1] & ~ld_word(p.h_out, b, W, w0 + 1) & top1);
+    }
+  }
+  if (lane == 0) sd.rec_cnt[stream] = rec_count;
 }
 
 // --------------------------------------------------------------------------------------
@@ -1642,9 +1823,9 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   std::vector<CarrySrc> csrc;
   std::vector<int32_t> fin_slot, out_slot, out_pos, lat_slot, bend_loop, srcent;
   std::vector<int2> latch_be;
-  // short chunks give more independent walks (one warp each); 128
-  // positions was the fastest target on the 2^20-block CFG
-  if (chunk_target <= 0) chunk_target = g.M <= 2048 ? std::max(32, g.M / 8) : 128;
+  // short chunks give more independent walks (one warp each) and shorter
+  // longest walks; 32 positions measured fastest on the 2^20-block CFG
+  if (chunk_target <= 0) chunk_target = 32;
   TraceScope trace_bm("scan build_meta", g.M);
   if (!build_meta(g, chunk_target, st, meta, loops, chunks, csrc, fin_slot, out_slot, out_pos, lat_slot, bend_loop,
                   srcent, latch_be, err)) {
@@ -1791,17 +1972,43 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   chk(sd.d_src = st->alloc<uint64_t>((size_t)std::max(1, g.K) * W));
   st->n_csrc = (int)csrc.size();
   chk(sd.xval = st->alloc<uint64_t>((size_t)std::max(1, st->n_csrc) * W));
-  // record streams: per (chunk, word group) the apply walk's stream, then
-  // the crossing edges' stream, so each chunk's records are contiguous
-  st->n_streams = 2 * C * G;
+  // emission items: runs of at most EMIT_SPAN positions inside one chunk,
+  // each with a record stream per word group, in position order, so each
+  // chunk's (and each CFG's) records are contiguous
+  std::vector<int2> emit_rng;
+  st->chunk_item0.assign(C + 1, 0);
+  for (int c = 0; c < C; ++c) {
+    st->chunk_item0[c] = (int32_t)emit_rng.size();
+    for (int i = chunks[c].s; i < chunks[c].e; i += EMIT_SPAN)
+      emit_rng.push_back(make_int2(i, std::min(chunks[c].e, i + EMIT_SPAN)));
+  }
+  st->chunk_item0[C] = (int32_t)emit_rng.size();
+  sd.n_emit = (int)emit_rng.size();
+  chk(sd.emit_rng = st->up(emit_rng));
+  st->n_streams = sd.n_emit * G;
   sd.n_streams = st->n_streams;
   st->h_rec_cap.assign(st->n_streams, 0);
-  for (int c = 0; c < C; ++c)
-    for (int wg = 0; wg < G; ++wg) {
-      const int len = chunks[c].e - chunks[c].s;
-      st->h_rec_cap[2 * (c * G + wg)] = 64 + len;
-      st->h_rec_cap[2 * (c * G + wg) + 1] = 8 + 2 * chunks[c].carry_cnt * 64;
+  for (int k = 0; k < sd.n_emit; ++k)
+    for (int wg = 0; wg < G; ++wg) st->h_rec_cap[k * G + wg] = 32 + 2 * (emit_rng[k].y - emit_rng[k].x);
+  // affine pairs of the summary walks and where each position's carry comes from
+  {
+    std::vector<int32_t> pos_chunk(g.M), src_pos(std::max(1, g.K), 0);
+    for (int c = 0; c < C; ++c)
+      for (int i = chunks[c].s; i < chunks[c].e; ++i) pos_chunk[i] = c;
+    for (int k = 0; k < g.K; ++k) src_pos[k] = g.pos[g.ent_src[k]];
+    chk(sd.pos_chunk = st->up(pos_chunk));
+    chk(sd.src_pos = st->up(src_pos));
+    const size_t NW = (size_t)g.N * W, KW = (size_t)std::max(1, g.K) * W;
+    chk(sd.pair_g = st->alloc<uint64_t>(NW));
+    chk(sd.pair_p = st->alloc<uint64_t>(NW));
+    sd.pair_g2 = sd.pair_p2 = nullptr;
+    if (keep_states) {
+      chk(sd.pair_g2 = st->alloc<uint64_t>(NW));
+      chk(sd.pair_p2 = st->alloc<uint64_t>(NW));
     }
+    chk(sd.src_g = st->alloc<uint64_t>(KW));
+    chk(sd.src_p = st->alloc<uint64_t>(KW));
+  }
   chk(st->d_rec_cap = st->alloc<int32_t>(st->n_streams));
   chk(st->d_rec_base = st->alloc<int32_t>(st->n_streams));
   chk(sd.rec_cnt = st->alloc<int32_t>(st->n_streams + 1));
@@ -1831,12 +2038,13 @@ bool scan_grow_streams(ScanState *st) {
 
 #define PROF(name) if (pf) pf->mark(s, name)
 
-static int run_emission_tail(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *pf) {
+// the emission pass and the gather of its record streams
+static int run_emission(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *pf) {
   ScanDev &sd = st->sd;
   int32_t *offs = st->offs;
-  const int nw = sd.C * sd.G;
-  PROF("cross_emit");
-  k_cross_emit<<<grid_of((long long)nw * 32, 128), 128, 0, s>>>(p, sd);
+  const long long nw = (long long)sd.n_emit * sd.G;
+  PROF("emit");
+  k_emit<<<grid_of(nw * 32, 32 * EMIT_WARPS), 32 * EMIT_WARPS, 0, s>>>(p, sd, st->init);
   PROF("streams_prefix");
   k_streams_prefix<<<1, 1024, 0, s>>>(sd, offs, p.status);
   PROF("streams_copy");
@@ -1853,34 +2061,43 @@ void chain_launch(K kern, const ChainShape &cs, const DevPlan &p, const ScanDev 
 }
 #define CHAIN(kern, kind, qslot) (chain_launch(kern, st->shape[kind], p, sd, qslot, s), ++n)
 
+// One run: local summaries; per phase a summary walk that leaves every
+// position's affine pair, the scan of the chunk maps, and a parallel resolve
+// of the pairs with the carries; then the emission from the final states.
 int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *pf) {
   ScanDev &sd = st->sd;
   const int W = p.W;
   uint64_t *init = st->init;
   int n = 0;
+  const long long nw = (long long)p.M * W, kw = (long long)p.K * W;
   cudaMemsetAsync(p.acc_flag, 0, (size_t)p.A, s);
   cudaMemsetAsync(sd.queue, 0, sizeof(int32_t) * Q_SLOTS, s);
   PROF("local_summary");
   k_local_summary_pos<<<grid_of(sd.n_acc_p, 256), 256, 0, s>>>(sd); ++n;
   // ---- liveness (backward)
+  ScanDev sl = sd;  // liveness pairs only
+  sl.pair_g2 = sl.pair_p2 = nullptr;
   PROF("live_summary");
-  CHAIN(k_bwd_chain<M_SUM>, CK_BSUM, 0);
+  chain_launch(k_bwd_chain<M_SUM>, st->shape[CK_BSUM], p, sl, 0, s); ++n;
   PROF("live_scan");
   k_scan_carry<<<W, 256, 0, s>>>(sd, W, 1, nullptr); ++n;
-  PROF("live_apply");
-  CHAIN(k_bwd_chain<M_APPLY>, CK_BAPPLY, 1);
+  PROF("live_resolve");
+  k_resolve<RV_LIVE><<<grid_of((nw + 1) / 2, 256), 256, 0, s>>>(p, sd, sd.pair_g, sd.pair_p, p.live); ++n;
   // ---- loop masks: need within the loop body, kills anywhere in it
   if (p.L) { PROF("loop_masks"); CHAIN(k_bwd_chain<M_LANT>, CK_BLANT, 2); }
-  // ---- plain host validity
+  // ---- plain host validity (needed at loop-entry sources only)
   PROF("entry_stale");
   k_entry_stale<<<grid_of((long long)W * p.n_cfg, 128), 128, 0, s>>>(p.entry_h, p.top, init, W, p.n_cfg); ++n;
   PROF("hp_summary");
   CHAIN((k_fwd_chain<K_HP, M_SUM>), CK_FSUM, 3);
   PROF("fwd_scan");
   k_scan_carry<<<W, 256, 0, s>>>(sd, W, 0, init); ++n;
-  PROF("hp_apply");
-  CHAIN((k_fwd_chain<K_HP, M_APPLY>), CK_FAPPLY, 4);
-  if (p.K) { PROF("edge_const"); k_scan_edge_const<<<grid_of((long long)p.K * W, 256), 256, 0, s>>>(p, sd, 0); ++n; }
+  if (p.K) {
+    PROF("src_resolve");
+    k_resolve_src<<<grid_of(kw, 256), 256, 0, s>>>(p, sd, sd.hp_src); ++n;
+    PROF("edge_const");
+    k_scan_edge_const<<<grid_of(kw, 256), 256, 0, s>>>(p, sd, 0); ++n;
+  }
   // ---- device validity
   PROF("entry_stale");
   k_entry_stale<<<grid_of((long long)W * p.n_cfg, 128), 128, 0, s>>>(p.entry_d, p.top, init, W, p.n_cfg); ++n;
@@ -1888,30 +2105,32 @@ int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *p
   CHAIN((k_fwd_chain<K_D, M_SUM>), CK_FSUM, 5);
   PROF("fwd_scan");
   k_scan_carry<<<W, 256, 0, s>>>(sd, W, 0, init); ++n;
-  PROF("d_apply");
-  CHAIN((k_fwd_chain<K_D, M_APPLY>), CK_FAPPLY, 6);
-  if (p.K) { PROF("edge_const"); k_scan_edge_const<<<grid_of((long long)p.K * W, 256), 256, 0, s>>>(p, sd, 1); ++n; }
-  // ---- host validity and emission
+  PROF("d_resolve");
+  k_resolve<RV_VALID><<<grid_of((nw + 1) / 2, 256), 256, 0, s>>>(p, sd, sd.pair_g, sd.pair_p, p.d_in); ++n;
+  if (sd.pair_g2) { k_resolve<RV_VALID><<<grid_of((nw + 1) / 2, 256), 256, 0, s>>>(p, sd, sd.pair_g2, sd.pair_p2, p.d_out); ++n; }
+  if (p.K) {
+    PROF("src_resolve");
+    k_resolve_src<<<grid_of(kw, 256), 256, 0, s>>>(p, sd, sd.d_src); ++n;
+    PROF("edge_const");
+    k_scan_edge_const<<<grid_of(kw, 256), 256, 0, s>>>(p, sd, 1); ++n;
+  }
+  // ---- host validity (its exit states), then the emission
   PROF("entry_stale");
   k_entry_stale<<<grid_of((long long)W * p.n_cfg, 128), 128, 0, s>>>(p.entry_h, p.top, init, W, p.n_cfg); ++n;
   PROF("h_summary");
   CHAIN((k_fwd_chain<K_H, M_SUM>), CK_FSUM, 7);
   PROF("fwd_scan");
   k_scan_carry<<<W, 256, 0, s>>>(sd, W, 0, init); ++n;
-  PROF("h_apply_emit");
-  CHAIN((k_fwd_chain<K_H, M_APPLY>), CK_FEMIT, 8);
-  n += run_emission_tail(st, p, s, pf);
+  PROF("h_resolve");
+  k_resolve<RV_VALID><<<grid_of((nw + 1) / 2, 256), 256, 0, s>>>(p, sd, sd.pair_g, sd.pair_p, p.h_out); ++n;
+  n += run_emission(st, p, s, pf);
   return n;
 }
 
 int enqueue_scan_edges(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *pf) {
-  // after the record buffers grew: redo the host-validity apply pass and the gather
-  ScanDev &sd = st->sd;
-  int n = 0;
-  cudaMemsetAsync(sd.queue + 9, 0, sizeof(int32_t), s);
-  PROF("h_apply_emit");
-  CHAIN((k_fwd_chain<K_H, M_APPLY>), CK_FEMIT, 9);
-  return n + run_emission_tail(st, p, s, pf);
+  // after the record buffers grew: redo the emission and the gather (the
+  // entry rows in `init' are still the host-validity ones)
+  return run_emission(st, p, s, pf);
 }
 
 #undef CHAIN
@@ -1926,7 +2145,7 @@ bool scan_chunk_record_offsets(const ScanState *st, cudaStream_t s, std::vector<
        cudaStreamSynchronize(s) != cudaSuccess))
     return false;
   out->assign(st->C + 1, total);
-  for (int c = 0; c < st->C; ++c) (*out)[c] = offs[(size_t)2 * c * st->G];
+  for (int c = 0; c < st->C; ++c) (*out)[c] = offs[(size_t)st->chunk_item0[c] * st->G];
   return true;
 }
 
