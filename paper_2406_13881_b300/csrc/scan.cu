@@ -38,7 +38,6 @@ namespace ompdart {
 namespace {
 
 constexpr int CARRY = -2;      // slot id: the chunk's incoming carry
-constexpr int BACK_EDGE = -2;  // in-edge tag: a back edge (its transfers are emitted at the latch)
 constexpr int PREV = -3;       // slot id: the value of the position walked just before
 #ifndef OMPDART_SH_WORDS
 #define OMPDART_SH_WORDS 512
@@ -55,18 +54,18 @@ constexpr int MAX_DEPTH = 31;  // loop nesting depth the chain handles
 __host__ __device__ inline int rerun_cap(int len) { return 8 * len + 64; }
 
 enum PhaseKind { K_ANT = 0, K_HP = 1, K_D = 2, K_H = 3 };
-enum ModeKind { M_SUM = 0, M_APPLY = 1, M_LANT = 2 };
+enum ModeKind { M_SUM = 0, M_LANT = 2 };  // summary walk; loop-restricted anticipation
 
 struct PosMeta {  // one per position, 64 B
   int32_t blk;
   int32_t fin_beg, out_beg, acc_beg, srcent_beg, bend_beg;  // acc_beg: in caller order
-  int16_t nfin, nout, nacc, nsrcent, nbend, fslot, bslot, nlb;  // nlb: back edges leaving here
+  int16_t nfin, nout, nacc, nsrcent, nbend, fslot, bslot, pad0;
   int32_t head_loop;      // loop whose header is this position, else -1
   uint32_t latch_levels;  // bit d: back edge to the header of the level-d loop
   int32_t exit_idx;       // index in exit_blocks, else -1
   int32_t pacc_beg;       // first access of the block in position order
   int32_t flags;          // PM_RECORDS: the block's summary records are given
-  int32_t lb_beg;         // first of this position's back edges in latch_be
+  int32_t pad3;
 };
 // a block with call pseudo-accesses: its entries in the position-ordered
 // access stream are already summary records (folded on the host with the
@@ -115,7 +114,6 @@ struct ScanDev {
   const int32_t *lat_slot;
   const int32_t *bend_loop;
   const int32_t *srcent;
-  const int2 *latch_be;  // back edges by latch position: {edge id, header block}
   uint64_t *spill;     // per warp spill area
   int spill_stride;    // words per warp
   uint64_t *gsum, *psum;   // [planes][C][W] chunk maps
@@ -130,7 +128,6 @@ struct ScanDev {
   const int32_t *src_pos;       // [K] position of each loop-entry edge's source
   const int2 *emit_rng;         // [n_emit] position ranges of the emission items (within one chunk)
   int n_emit;
-  uint64_t *xval;      // [n_carry_src][W] host-stale sets of crossing-edge sources
   int32_t *rec_cnt;    // [streams]
   const int32_t *rec_base, *rec_cap;  // [streams]
   EdgeXfer *stream;    // record streams
@@ -179,12 +176,11 @@ struct ChainShape {
   int grid = 1, wpc = 4, sh_slots = 0;
   size_t smem = 0;
 };
-enum ChainKind { CK_BSUM, CK_BAPPLY, CK_BLANT, CK_FSUM, CK_FAPPLY, CK_FEMIT, CK_COUNT };
+enum ChainKind { CK_BSUM, CK_BLANT, CK_FSUM, CK_COUNT };
 
 struct ScanState {
   int C = 0, G = 0, fslots = 0, bslots = 0, n_streams = 0;
   ChainShape shape[CK_COUNT];
-  int n_csrc = 0;
   long long total_cap = 0;
   long long h2d = 0;
   std::vector<void *> allocs;
@@ -192,6 +188,7 @@ struct ScanState {
   std::vector<int32_t> h_rec_cap;  // host copy of capacities
   int32_t *d_rec_cap = nullptr, *d_rec_base = nullptr;
   int32_t *offs = nullptr;         // stream offsets in the gathered result
+  int32_t *part = nullptr;         // per-CTA sums of the stream prefix
   std::vector<int32_t> chunk_item0;  // [C+1] first emission item of each chunk
   uint64_t *init = nullptr;        // [W] stale set entering the first chunk
   EdgeXfer *stream_buf = nullptr;
@@ -230,8 +227,7 @@ namespace {
 bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta> &meta, std::vector<LoopMeta> &loops,
                 std::vector<ChunkMeta> &chunks, std::vector<CarrySrc> &csrc, std::vector<int32_t> &fin_slot,
                 std::vector<int32_t> &out_slot, std::vector<int32_t> &out_pos, std::vector<int32_t> &lat_slot,
-                std::vector<int32_t> &bend_loop, std::vector<int32_t> &srcent, std::vector<int2> &latch_be,
-                std::string *err) {
+                std::vector<int32_t> &bend_loop, std::vector<int32_t> &srcent, std::string *err) {
   Ingest &gm = const_cast<Ingest &>(g);
   make_chunks(&gm, target);
   const int M = g.M, C = (int)g.chunk_off.size() - 1, L = g.L;
@@ -405,30 +401,6 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
       }
     chunks[c].carry_cnt = (int32_t)csrc.size() - chunks[c].carry_beg;
   }
-  // back edges by latch: their transfers are emitted when the latch's final
-  // value is known (the header is walked before its latches)
-  {
-    std::vector<std::pair<int32_t, int2>> be;
-    for (int i = 0; i < M; ++i)
-      for (int k = g.fin_off[i]; k < g.fin_off[i + 1]; ++k) {
-        const int pp = g.pos[g.fin_src[k]];
-        if (pp >= i) be.push_back({pp, make_int2(g.fin_eid[k], g.order[i])});
-      }
-    std::stable_sort(be.begin(), be.end(), [](const std::pair<int32_t, int2> &a, const std::pair<int32_t, int2> &b) {
-      return a.first < b.first;
-    });
-    latch_be.clear();
-    for (size_t q = 0; q < be.size(); ++q) {
-      PosMeta &m = meta[be[q].first];
-      if (m.nlb == 0) m.lb_beg = (int32_t)latch_be.size();
-      if (m.nlb == 32000) {
-        if (err) *err = "too many back edges from one block";
-        return false;
-      }
-      ++m.nlb;
-      latch_be.push_back(be[q].second);
-    }
-  }
   for (int l = 0; l < L; ++l) {
     LoopMeta &lm = loops[l];
     lm.ph = g.pos[g.loop_head[l]];
@@ -482,7 +454,6 @@ struct Win {
   int2 edge[EDGE_CAP];    // forward: {slot, loop-entry edge}; backward: {slot, target position}
   uint32_t rec[REC_CAP];  // summary records
   int mbase, ws, we, e0, r0, big;
-  uint32_t *acc;          // emission words (variable | flag table), REC_CAP entries
 };
 
 struct WinRegs {  // warp-uniform copy of the window bounds
@@ -493,7 +464,7 @@ struct WinRegs {  // warp-uniform copy of the window bounds
 // Load the window containing position i: forward [i, i+WIN) clipped to hi,
 // backward (i-WIN, i] clipped to lo; shrunk so its edges and records fit.
 // A single position too large for the buffers is read from HBM directly.
-template <bool FWD, bool ACC>
+template <bool FWD>
 __device__ void load_window(Win &w, WinRegs &r, const ScanDev &sd, int i, int lo, int hi, int lane) {
   const unsigned FULL = 0xffffffffu;
   const int mbase = FWD ? i : max(i - WIN + 1, lo);
@@ -532,10 +503,7 @@ __device__ void load_window(Win &w, WinRegs &r, const ScanDev &sd, int i, int lo
   if (!big) {
     const int2 *src = FWD ? sd.fin_pk : sd.out_pk;
     for (int j = lane; j < e1 - e0; j += 32) w.edge[j] = src[e0 + j];
-    for (int j = lane; j < r1 - r0; j += 32) {
-      w.rec[j] = sd.rec_p[r0 + j];
-      if (ACC) w.acc[j] = sd.emit_p[r0 + j];
-    }
+    for (int j = lane; j < r1 - r0; j += 32) w.rec[j] = sd.rec_p[r0 + j];
   }
   __syncwarp();
   r.mbase = mbase; r.ws = ws; r.we = we; r.e0 = e0; r.r0 = r0; r.big = big;
@@ -547,10 +515,6 @@ __device__ __forceinline__ int2 win_edge(const Win &w, const WinRegs &r, const i
 __device__ __forceinline__ uint32_t win_rec(const Win &w, const WinRegs &r, const ScanDev &sd, int k) {
   return r.big ? sd.rec_p[k] : w.rec[k - r.r0];
 }
-__device__ __forceinline__ uint32_t win_acc(const Win &w, const WinRegs &r, const ScanDev &sd, int k) {
-  return r.big ? sd.emit_p[k] : w.acc[k - r.r0];
-}
-
 struct Lane {
   int lane, wg, w0;     // w0: first of the lane's two words (global word index)
   uint64_t top0, top1;  // valid-variable masks of the two words
@@ -575,31 +539,28 @@ __device__ __forceinline__ void st_word(uint64_t *plane, size_t row, int W, int 
 }
 
 // shared memory per warp (words):
-//   slots [nsh][np][64] | emission scratch 128 | mask table [2][2*np][64] |
-//   kill sets 128 | window | raw accesses REC_CAP/2 (emitting pass only)
+//   slots [nsh][np][64] | mask table [2][2*np][64] | kill sets 128 | window
 // each part a multiple of 16 words (128 B): slots and masks are read and
 // written as 16-byte ulonglong2 and must stay 16-byte aligned
 constexpr size_t WIN_WORDS = ((sizeof(Win) + 127) / 128) * 16;
-__host__ __device__ inline size_t warp_smem_words(int nsh, int np, bool acc) {
-  return (size_t)nsh * np * 64 + 128 + (size_t)4 * np * 64 + 128 + WIN_WORDS + (acc ? REC_CAP / 2 : 0);
+__host__ __device__ inline size_t warp_smem_words(int nsh, int np) {
+  return (size_t)nsh * np * 64 + (size_t)4 * np * 64 + 128 + WIN_WORDS;
 }
 static_assert(WIN_WORDS % 16 == 0 && WIN_WORDS * 8 >= sizeof(Win), "window layout");
-static_assert(alignof(Win) <= 16 && (REC_CAP / 2) % 16 == 0, "window alignment");
+static_assert(alignof(Win) <= 16, "window alignment");
 
 struct WarpMem {
-  uint64_t *slots, *hd, *tbl, *kill;
+  uint64_t *slots, *tbl, *kill;
   Win *win;
 };
-template <int NP, bool ACC>
+template <int NP>
 __device__ __forceinline__ WarpMem carve(uint64_t *smem, int warp_in_cta, int nsh) {
-  uint64_t *b = smem + (size_t)warp_in_cta * warp_smem_words(nsh, NP, ACC);
+  uint64_t *b = smem + (size_t)warp_in_cta * warp_smem_words(nsh, NP);
   WarpMem m;
   m.slots = b;
-  m.hd = b + (size_t)nsh * NP * 64;
-  m.tbl = m.hd + 128;
+  m.tbl = b + (size_t)nsh * NP * 64;
   m.kill = m.tbl + 4 * NP * 64;
   m.win = reinterpret_cast<Win *>(m.kill + 128);
-  m.win->acc = ACC ? reinterpret_cast<uint32_t *>(m.kill + 128 + WIN_WORDS) : nullptr;
   return m;
 }
 
@@ -686,92 +647,15 @@ __device__ __forceinline__ void push_edge_records(const ScanDev &sd, int stream,
   rec_count = base + __popc(b0) + __popc(b1);
 }
 
-// Transfers on the back edges leaving a latch, from its final value zo
-// (stale on the host): the header's conflicts (live there, valid on the
-// device at no entry of it) the latch leaves stale on the host come back
-// to the host on that edge.  Back edges are never loop-entry edges.
-__device__ void emit_back_edges(const DevPlan &p, const ScanDev &sd, const Lane &L, const PosMeta &m,
-                                const uint64_t zo[2], int stream, int &rec_count) {
-  const int W = p.W;
-  for (int q = 0; q < m.nlb; ++q) {
-    const int2 be = sd.latch_be[m.lb_beg + q];  // {edge id, header block}
-    const uint64_t c0 = ld_word(p.live, be.y, W, L.w0) & ~ld_word(p.d_in, be.y, W, L.w0);
-    const uint64_t c1 = ld_word(p.live, be.y, W, L.w0 + 1) & ~ld_word(p.d_in, be.y, W, L.w0 + 1);
-    push_edge_records(sd, stream, rec_count, be.x, L.w0, 0, c0 & zo[0], 0, c1 & zo[1], L.lane);
-  }
-}
-
-// The H-phase emission for one position (apply mode): per-access flags,
-// in-chunk edge records (back edges excepted: emit_back_edges), exit
-// transfers.
-__device__ void emit_position(const DevPlan &p, const ScanDev &sd, const Win &w, const WinRegs &wr, const Lane &L,
-                              const PosMeta &m, const Slots<1> &sl, const uint64_t zin[2], const uint64_t zout[2],
-                              const uint64_t din[2], const uint64_t live[2], const uint64_t prev[2], uint64_t *hd,
-                              int stream, int &rec_count, int cfg) {
-  const int W = p.W, lane = L.lane;
-  // ---- access flags: each access's flag table, indexed by its variable's
-  // validity at the block entry (host bit | device bit << 1)
-  if (m.nacc && !(m.flags & PM_RECORDS)) {
-    hd[2 * lane] = ~zin[0] & L.top0;
-    hd[2 * lane + 1] = ~zin[1] & L.top1;
-    hd[64 + 2 * lane] = din[0];
-    hd[64 + 2 * lane + 1] = din[1];
-    __syncwarp();
-    const int a0 = m.pacc_beg, na = m.nacc;
-    for (int j = lane; j < na; j += 32) {
-      const uint32_t e = win_acc(w, wr, sd, a0 + j);
-      const int v = (int)(e & 0xFFFFFFu), lw = (v >> 6) - L.wg * 64;
-      if ((unsigned)lw >= 64u) continue;
-      const uint64_t bit = 1ull << (v & 63);
-      const int k = ((hd[lw] & bit) ? 1 : 0) | ((hd[64 + lw] & bit) ? 2 : 0);
-      p.acc_flag[m.acc_beg + j] = (uint8_t)((e >> (24 + 2 * k)) & 3u);
-    }
-    __syncwarp();
-  }
-  // ---- edge transfers on in-chunk in-edges
-  const uint64_t c0 = live[0] & ~din[0], c1 = live[1] & ~din[1];
-  for (int q = 0; q < m.nfin; ++q) {
-    const int k = m.fin_beg + q;
-    const int2 fe = win_edge(w, wr, sd.fin_pk, k);
-    const int slot = fe.x;
-    if (slot == CARRY || fe.y == BACK_EDGE) continue;
-    const int ent = fe.y;
-    const ulonglong2 zs = slot == PREV ? make_ulonglong2(prev[0], prev[1]) : *sl.at(slot, 0, lane);
-    uint64_t to0 = 0, to1 = 0, fr0, fr1;
-    uint64_t e0 = zs.x, e1 = zs.y;
-    if (ent >= 0) {
-      const uint64_t eh0 = ld_word(p.ec_h, ent, W, L.w0), eh1 = ld_word(p.ec_h, ent, W, L.w0 + 1);
-      const uint64_t ed0 = ld_word(p.ec_d, ent, W, L.w0), ed1 = ld_word(p.ec_d, ent, W, L.w0 + 1);
-      to0 = ed0 & ~ld_word(sd.d_src, ent, W, L.w0);
-      to1 = ed1 & ~ld_word(sd.d_src, ent, W, L.w0 + 1);
-      fr0 = eh0 & zs.x;
-      fr1 = eh1 & zs.y;
-      e0 &= ~eh0;
-      e1 &= ~eh1;
-    } else {
-      fr0 = fr1 = 0;
-    }
-    fr0 |= c0 & e0;
-    fr1 |= c1 & e1;
-    push_edge_records(sd, stream, rec_count, p.fin_eid[k], L.w0, to0, fr0, to1, fr1, lane);
-  }
-  // ---- region exit
-  if (m.exit_idx >= 0) {
-    const uint64_t *xl = p.exit_live + (size_t)cfg * W;
-    if (L.w0 < W) st_word(p.from_exit, m.exit_idx, W, L.w0, xl[L.w0] & zout[0] & L.top0);
-    if (L.w0 + 1 < W) st_word(p.from_exit, m.exit_idx, W, L.w0 + 1, xl[L.w0 + 1] & zout[1] & L.top1);
-  }
-}
-
 // --------------------------------------------------------------------------------------
 // forward chain (Hp, D, H): positions ascending
 // --------------------------------------------------------------------------------------
 // One warp walks chunk c for the 64-word group wg.
-template <int PH, int MODE>
+template <int PH>
 __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, const WarpMem &wm, uint64_t *spill,
                                          int c, int wg) {
-  constexpr int NP = MODE == M_SUM ? 2 : 1;
-  constexpr bool ACC = MODE == M_APPLY && PH == K_H;
+  constexpr int NP = 2;  // the chunk's affine map: local plane (carry 0), coefficient plane (carry all)
+  constexpr int MODE = M_SUM;
   const int W = p.W;
   Lane L;
   L.lane = threadIdx.x & 31;
@@ -781,26 +665,17 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
   L.top0 = L.w0 < W ? tp[L.w0] : 0;
   L.top1 = L.w0 + 1 < W ? tp[L.w0 + 1] : 0;
   Slots<NP> sl{wm.slots, spill, sd.sh_slots};
-  uint64_t *hd = wm.hd;
   Win &w = *wm.win;
   WinRegs wr;
   wr.ws = wr.we = 0;
   const ChunkMeta cm = sd.chunks[c];
   const uint64_t *ec = PH == K_D ? p.ec_d : p.ec_h;
-  // carry into this chunk, per plane
+  // the identity map enters the chunk: (local 0, coefficient all)
   uint64_t cin[NP][2];
-  if (MODE == M_SUM) {
-    cin[0][0] = cin[0][1] = 0;
-    cin[1][0] = L.top0;
-    cin[1][1] = L.top1;
-  } else {
-    cin[0][0] = ld_word(sd.carry, c, W, L.w0);
-    cin[0][1] = ld_word(sd.carry, c, W, L.w0 + 1);
-  }
-  const int stream = 2 * (c * sd.G + wg);  // odd streams: crossing edges (k_cross_emit)
-  int rec_count = 0;
+  cin[0][0] = cin[0][1] = 0;
+  cin[1][0] = L.top0;
+  cin[1][1] = L.top1;
   int st_loop[MAX_DEPTH + 1];
-  int st_rec[MAX_DEPTH + 1];
   int depth = 0;
   uint32_t dirty = 0;
   int reruns = 0;
@@ -817,7 +692,7 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
   int hwm = cm.s - 1;  // highest position walked so far
   int i = cm.s;
   while (i < cm.e) {
-    if (i < wr.ws || i >= wr.we) load_window<true, ACC>(w, wr, sd, i, cm.s, cm.e, L.lane);
+    if (i < wr.ws || i >= wr.we) load_window<true>(w, wr, sd, i, cm.s, cm.e, L.lane);
     const PosMeta m = w.meta[i - wr.mbase];
     if (prep_pos != i) {  // masks of this position not built yet (start, window edge, loop jump)
       if (prep_pos >= 0) {
@@ -847,7 +722,6 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
       const LoopMeta lm = sd.loops[m.head_loop];
       if (lm.depth > depth) {  // entering the loop from outside
         st_loop[depth] = m.head_loop;
-        st_rec[depth] = rec_count;
         dirty &= ~(1u << depth);
         ++depth;
         top_pend = lm.pend;
@@ -934,14 +808,13 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
 #pragma unroll
       for (int pl = 0; pl < NP; ++pl) *sl.at(m.fslot, pl, L.lane) = make_ulonglong2(zo[pl][0], zo[pl][1]);
     }
-    uint64_t pvo[NP][2];
 #pragma unroll
     for (int pl = 0; pl < NP; ++pl) {
-      pvo[pl][0] = pv[pl][0]; pvo[pl][1] = pv[pl][1];
-      pv[pl][0] = zo[pl][0]; pv[pl][1] = zo[pl][1];
+      pv[pl][0] = zo[pl][0];
+      pv[pl][1] = zo[pl][1];
     }
-    // ---- outputs: the summary walk leaves each position's affine pairs
-    if (MODE == M_SUM && sd.pair_g) {
+    // ---- outputs: each position's affine pairs
+    {
       const size_t row = (size_t)m.blk;
       if (PH == K_D) {  // device validity at the block entry (and exit, kept states)
         st_word(sd.pair_g, row, W, L.w0, z[0][0]);
@@ -971,44 +844,12 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
         }
       }
     }
-    if (MODE == M_APPLY) {
-      const size_t row = (size_t)m.blk;
-      if (PH == K_D) {
-        st_word(p.d_in, row, W, L.w0, ~z[0][0] & L.top0);
-        st_word(p.d_in, row, W, L.w0 + 1, ~z[0][1] & L.top1);
-        if (sd.keep_states) {
-          st_word(p.d_out, row, W, L.w0, ~zo[0][0] & L.top0);
-          st_word(p.d_out, row, W, L.w0 + 1, ~zo[0][1] & L.top1);
-        }
-      }
-      if (PH == K_H) {
-        st_word(p.h_in, row, W, L.w0, ~z[0][0] & L.top0);
-        st_word(p.h_in, row, W, L.w0 + 1, ~z[0][1] & L.top1);
-        if (sd.keep_states) {
-          st_word(p.h_out, row, W, L.w0, ~zo[0][0] & L.top0);
-          st_word(p.h_out, row, W, L.w0 + 1, ~zo[0][1] & L.top1);
-        }
-        __syncwarp();
-        emit_position(p, sd, w, wr, L, m, *reinterpret_cast<Slots<1> *>(&sl), z[0], zo[0], din, lv, pvo[0], hd,
-                      stream, rec_count, cm.cfg);
-        if (m.nlb) emit_back_edges(p, sd, L, m, zo[0], stream, rec_count);
-      }
-      if ((PH == K_HP || PH == K_D) && m.nsrcent) {
-        uint64_t *dst = PH == K_HP ? sd.hp_src : sd.d_src;
-        for (int q = 0; q < m.nsrcent; ++q) {
-          const int k = sd.srcent[m.srcent_beg + q];
-          st_word(dst, k, W, L.w0, ~zo[0][0] & L.top0);
-          st_word(dst, k, W, L.w0 + 1, ~zo[0][1] & L.top1);
-        }
-      }
-    }
     __syncwarp();
     // ---- close loops ending here; walk a body again if its header grew
     bool jumped = false;
     while (depth > 0 && top_pend - 1 == i) {
       if (dirty & (1u << (depth - 1))) {
         dirty &= ~(1u << (depth - 1));
-        rec_count = st_rec[depth - 1];
         i = sd.loops[st_loop[depth - 1]].ph;
         jumped = true;
         break;
@@ -1030,36 +871,27 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
     }
   }
   if (L.lane == 0 && reruns) atomicAdd(&p.status[ST_SWEEPS], reruns);
-  // ---- what leaves the chunk: the carry into the next chunk's first block
-  if (MODE == M_SUM || (MODE == M_APPLY && PH == K_H)) {
-    uint64_t co[NP][2];
+  // ---- what leaves the chunk: its map of the carry into the next chunk
+  uint64_t co[NP][2];
 #pragma unroll
-    for (int pl = 0; pl < NP; ++pl) co[pl][0] = co[pl][1] = 0;
-    for (int q = 0; q < cm.carry_cnt; ++q) {
-      const CarrySrc cs = sd.csrc[cm.carry_beg + q];
-      if (MODE == M_SUM) {
-        uint64_t m0 = ~0ull, m1 = ~0ull;
-        if (PH != K_HP && cs.ent >= 0) { m0 = ~ld_word(ec, cs.ent, W, L.w0); m1 = ~ld_word(ec, cs.ent, W, L.w0 + 1); }
+  for (int pl = 0; pl < NP; ++pl) co[pl][0] = co[pl][1] = 0;
+  for (int q = 0; q < cm.carry_cnt; ++q) {
+    const CarrySrc cs = sd.csrc[cm.carry_beg + q];
+    uint64_t m0 = ~0ull, m1 = ~0ull;
+    if (PH != K_HP && cs.ent >= 0) { m0 = ~ld_word(ec, cs.ent, W, L.w0); m1 = ~ld_word(ec, cs.ent, W, L.w0 + 1); }
 #pragma unroll
-        for (int pl = 0; pl < NP; ++pl) {
-          const ulonglong2 v = *sl.at(cs.slot, pl, L.lane);
-          co[pl][0] |= v.x & m0;
-          co[pl][1] |= v.y & m1;
-        }
-      } else {
-        const ulonglong2 v = *sl.at(cs.slot, 0, L.lane);
-        st_word(sd.xval, cm.carry_beg + q, W, L.w0, v.x);
-        st_word(sd.xval, cm.carry_beg + q, W, L.w0 + 1, v.y);
-      }
-    }
-    if (MODE == M_SUM && cm.carry_cnt) {
-      st_word(sd.gsum, c, W, L.w0, co[0][0]);
-      st_word(sd.gsum, c, W, L.w0 + 1, co[0][1]);
-      st_word(sd.psum, c, W, L.w0, co[1][0]);
-      st_word(sd.psum, c, W, L.w0 + 1, co[1][1]);
+    for (int pl = 0; pl < NP; ++pl) {
+      const ulonglong2 v = *sl.at(cs.slot, pl, L.lane);
+      co[pl][0] |= v.x & m0;
+      co[pl][1] |= v.y & m1;
     }
   }
-  if (MODE == M_APPLY && PH == K_H && L.lane == 0) sd.rec_cnt[stream] = rec_count;
+  if (cm.carry_cnt) {
+    st_word(sd.gsum, c, W, L.w0, co[0][0]);
+    st_word(sd.gsum, c, W, L.w0 + 1, co[0][1]);
+    st_word(sd.psum, c, W, L.w0, co[1][0]);
+    st_word(sd.psum, c, W, L.w0 + 1, co[1][1]);
+  }
 }
 
 // Take the next (chunk, word group) item of a launch's work queue: lane 0
@@ -1072,18 +904,16 @@ __device__ __forceinline__ int next_item(const ScanDev &sd, int qslot) {
 
 // Persistent forward chain: each warp takes items (longest chunks first)
 // from the launch's work queue until none is left.
-template <int PH, int MODE>
+template <int PH>
 __global__ void __launch_bounds__(256, OMPDART_CHAIN_MIN_CTAS) k_fwd_chain(DevPlan p, ScanDev sd, int qslot) {
-  constexpr int NP = MODE == M_SUM ? 2 : 1;
-  constexpr bool ACC = MODE == M_APPLY && PH == K_H;
   extern __shared__ __align__(16) uint64_t smem[];
   const int warp_in_cta = threadIdx.x >> 5;
   const int gw = blockIdx.x * (blockDim.x >> 5) + warp_in_cta;
-  const WarpMem wm = carve<NP, ACC>(smem, warp_in_cta, sd.sh_slots);
+  const WarpMem wm = carve<2>(smem, warp_in_cta, sd.sh_slots);
   uint64_t *spill = sd.spill + (size_t)gw * sd.spill_stride;
   const int n_items = sd.C * sd.G;
   for (int item = next_item(sd, qslot); item < n_items; item = next_item(sd, qslot)) {
-    fwd_walk<PH, MODE>(p, sd, wm, spill, sd.work[item / sd.G], item % sd.G);
+    fwd_walk<PH>(p, sd, wm, spill, sd.work[item / sd.G], item % sd.G);
     __syncwarp();
   }
 }
@@ -1092,8 +922,8 @@ __global__ void __launch_bounds__(256, OMPDART_CHAIN_MIN_CTAS) k_fwd_chain(DevPl
 // backward chain (anticipation; loop-restricted anticipation for the masks)
 // --------------------------------------------------------------------------------------
 template <int MODE>
-struct BwdPlanes {  // SUM: [Live local, Live coefficient]; APPLY: [Live]; LANT: [H, D]
-  static constexpr int NP = MODE == M_APPLY ? 1 : 2;
+struct BwdPlanes {  // SUM: [Live local, Live coefficient]; LANT: [H, D]
+  static constexpr int NP = 2;
 };
 
 template <int MODE>
@@ -1123,7 +953,7 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
   __syncwarp();
   int i = e - 1;
   while (i >= s) {
-    if (i < wr.ws || i >= wr.we) load_window<false, false>(w, wr, sd, i, s, e, L.lane);
+    if (i < wr.ws || i >= wr.we) load_window<false>(w, wr, sd, i, s, e, L.lane);
     const PosMeta m = w.meta[i - wr.mbase];
     if (prep_pos != i) {
       if (prep_pos >= 0) {
@@ -1205,11 +1035,7 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
       }
       if (is_top_header && __any_sync(0xffffffffu, changed)) dirty |= 1u << (depth - 1);
     }
-    if (MODE == M_APPLY) {
-      st_word(p.live, m.blk, W, L.w0, z[0][0]);
-      st_word(p.live, m.blk, W, L.w0 + 1, z[0][1]);
-    }
-    if (MODE == M_SUM && sd.pair_g) {  // Live_in as an affine pair of the chunk's carry
+    if (MODE == M_SUM) {  // Live_in as an affine pair of the chunk's carry
       st_word(sd.pair_g, m.blk, W, L.w0, z[0][0]);
       st_word(sd.pair_g, m.blk, W, L.w0 + 1, z[0][1]);
       st_word(sd.pair_p, m.blk, W, L.w0, z[1][0]);
@@ -1282,22 +1108,15 @@ __device__ __forceinline__ void bwd_walk(const DevPlan &p, const ScanDev &sd, co
     }
     return;
   }
-  // carry: liveness entering the next chunk's first block
-  if (MODE == M_SUM) {
-    cin[0][0] = cin[0][1] = 0;
-    cin[1][0] = L.top0;
-    cin[1][1] = L.top1;
-  } else {
-    cin[0][0] = ld_word(sd.carry, c, W, L.w0);
-    cin[0][1] = ld_word(sd.carry, c, W, L.w0 + 1);
-  }
+  // the identity map of the liveness entering from the next chunk
+  cin[0][0] = cin[0][1] = 0;
+  cin[1][0] = L.top0;
+  cin[1][1] = L.top1;
   bwd_range<MODE>(p, sd, L, wm, sl, cm.s, cm.e, 0, -1, true, cin, zl, cm.cfg);
-  if (MODE == M_SUM) {
-    st_word(sd.gsum, c, W, L.w0, zl[0][0]);
-    st_word(sd.gsum, c, W, L.w0 + 1, zl[0][1]);
-    st_word(sd.psum, c, W, L.w0, zl[1][0]);
-    st_word(sd.psum, c, W, L.w0 + 1, zl[1][1]);
-  }
+  st_word(sd.gsum, c, W, L.w0, zl[0][0]);
+  st_word(sd.gsum, c, W, L.w0 + 1, zl[0][1]);
+  st_word(sd.psum, c, W, L.w0, zl[1][0]);
+  st_word(sd.psum, c, W, L.w0 + 1, zl[1][1]);
 }
 
 // persistent backward chain (same work queue scheme as the forward one)
@@ -1307,7 +1126,7 @@ __global__ void __launch_bounds__(256, OMPDART_CHAIN_MIN_CTAS) k_bwd_chain(DevPl
   extern __shared__ __align__(16) uint64_t smem[];
   const int warp_in_cta = threadIdx.x >> 5;
   const int gw = blockIdx.x * (blockDim.x >> 5) + warp_in_cta;
-  const WarpMem wm = carve<NP, false>(smem, warp_in_cta, sd.sh_slots);
+  const WarpMem wm = carve<NP>(smem, warp_in_cta, sd.sh_slots);
   uint64_t *spill = sd.spill + (size_t)gw * sd.spill_stride;
   const int n_items = sd.C * sd.G;
   for (int item = next_item(sd, qslot); item < n_items; item = next_item(sd, qslot)) {
@@ -1471,7 +1290,7 @@ __global__ void __launch_bounds__(32 * EMIT_WARPS) k_emit(DevPlan p, ScanDev sd,
     }
     for (int q = 0; q < m.nfin; ++q) {
       const int k = m.fin_beg + q;
-      const int ent = sd.fin_pk[k].y;  // loop-entry edge, -1, or BACK_EDGE
+      const int ent = sd.fin_pk[k].y;  // loop-entry edge or -1
       const size_t src = (size_t)p.fin_src[k];
       const uint64_t s0 = ~ld_word(p.h_out, src, W, w0) & top0, s1 = ~ld_word(p.h_out, src, W, w0 + 1) & top1;
       uint64_t m0 = 0, m1 = 0, to0 = 0, to1 = 0;
@@ -1520,23 +1339,32 @@ __global__ void __launch_bounds__(32 * EMIT_WARPS) k_emit(DevPlan p, ScanDev sd,
 // --------------------------------------------------------------------------------------
 // scan of the chunk maps: carry[c] for every chunk (one thread per word and plane)
 // --------------------------------------------------------------------------------------
-// One CTA per word column: thread t composes the maps of a contiguous run
-// of chunks, thread 0 scans the runs' maps, then every thread walks its run
-// again to write each chunk's carry.  Map composition: first (g1, p1), then
-// (g2, p2) gives (g2 | (g1 & p2), p1 & p2).  The first chunk (in walk
-// order) of each CFG of a batch starts from that CFG's own boundary value:
-// the forward entry value, or nothing for the backward problem -- the map
-// (init, 0) applied before the chunk's own map.
-__global__ void __launch_bounds__(256) k_scan_carry(ScanDev sd, int W, int backward, const uint64_t *init) {
-  __shared__ uint64_t sg[256], sp[256];
-  const int w = blockIdx.x, t = threadIdx.x, T = blockDim.x;
-  const int C = sd.C, per = (C + T - 1) / T;
+// One CTA of SCAN_T threads per word column: thread t composes the maps of
+// a contiguous run of chunks (walk order), the CTA scans the runs' maps in
+// parallel, then every thread walks its run again to write each chunk's
+// carry.  Map composition: first (g1, p1), then (g2, p2) gives
+// (g2 | (g1 & p2), p1 & p2).  The first chunk (in walk order) of each CFG
+// of a batch starts from that CFG's own boundary value -- the forward entry
+// value, or nothing for the backward problem -- so in the run maps it acts
+// as a constant map.
+constexpr int SCAN_T = 1024;
+__device__ __forceinline__ void compose_after(uint64_t &g, uint64_t &p, uint64_t g1, uint64_t p1) {
+  // (g1, p1) first, then the current (g, p)
+  g = g | (g1 & p);
+  p = p1 & p;
+}
+
+__global__ void __launch_bounds__(SCAN_T) k_scan_carry(ScanDev sd, int W, int backward, const uint64_t *init) {
+  __shared__ uint64_t wg_s[SCAN_T / 32], wp_s[SCAN_T / 32];
+  const int w = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int C = sd.C, per = (C + SCAN_T - 1) / SCAN_T;
   const int b = t * per, e = min(C, b + per);
   const int32_t rflag = backward ? CH_LAST : CH_FIRST;
   auto chunk = [&](int k) { return backward ? C - 1 - k : k; };  // k-th chunk in walk order
   auto reset_val = [&](int c) -> uint64_t {
     return backward || !init ? 0ull : init[(size_t)sd.chunks[c].cfg * W + w];
   };
+  // 1. the run's map
   uint64_t g = 0, pp = ~0ull;
   for (int k = b; k < e; ++k) {
     const int c = chunk(k);
@@ -1548,19 +1376,32 @@ __global__ void __launch_bounds__(256) k_scan_carry(ScanDev sd, int W, int backw
     g = gc | (g & pc);
     pp &= pc;
   }
-  sg[t] = g;
-  sp[t] = pp;
-  __syncthreads();
-  if (t == 0) {
-    uint64_t x = 0;  // every walk starts at a CFG's first chunk, which resets
-    for (int r = 0; r < T; ++r) {
-      const uint64_t gr = sg[r], pr = sp[r];
-      sg[r] = x;  // carry entering run r
-      x = gr | (x & pr);
-    }
+  // 2. inclusive scan of the run maps: within the warp, then over warps
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint64_t g1 = __shfl_up_sync(0xffffffffu, g, d), p1 = __shfl_up_sync(0xffffffffu, pp, d);
+    if (lane >= d) compose_after(g, pp, g1, p1);
+  }
+  if (lane == 31) {
+    wg_s[wid] = g;
+    wp_s[wid] = pp;
   }
   __syncthreads();
-  uint64_t x = sg[t];
+  if (wid == 0) {
+    uint64_t a = wg_s[lane], q = wp_s[lane];
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint64_t g1 = __shfl_up_sync(0xffffffffu, a, d), p1 = __shfl_up_sync(0xffffffffu, q, d);
+      if (lane >= d) compose_after(a, q, g1, p1);
+    }
+    wg_s[lane] = a;
+    wp_s[lane] = q;
+  }
+  __syncthreads();
+  if (wid > 0) compose_after(g, pp, wg_s[wid - 1], wp_s[wid - 1]);
+  // carry entering run t: the inclusive map of runs < t applied to nothing
+  // (every walk starts at a CFG's first chunk, which resets)
+  uint64_t x = __shfl_up_sync(0xffffffffu, g, 1);
+  if (lane == 0) x = wid > 0 ? wg_s[wid - 1] : 0ull;
+  // 3. every chunk's carry
   for (int k = b; k < e; ++k) {
     const int c = chunk(k);
     if (sd.chunks[c].flags & rflag) x = reset_val(c);
@@ -1588,86 +1429,80 @@ __global__ void k_scan_edge_const(DevPlan p, ScanDev sd, int which) {
     p.ec_h[t] = p.mask_h[(size_t)l * p.W + w] & sd.d_src[t];
 }
 
-// edge transfers on edges that cross a chunk boundary (into the first block
-// of chunk c from chunk c-1), from the sources' stored host-stale sets
-__global__ void k_cross_emit(DevPlan p, ScanDev sd) {
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (gw >= sd.C * sd.G) return;
-  const int c = gw / sd.G, wg = gw % sd.G, lane = threadIdx.x & 31, W = p.W;
-  const int stream = 2 * gw + 1;  // right after the chunk's own apply stream
-  int cnt = 0;
-  if (c + 1 < sd.C) {
-    const ChunkMeta cm = sd.chunks[c];
-    const int dst = sd.meta[cm.e].blk;
-    const int w0 = wg * 64 + 2 * lane;
-    const uint64_t lv0 = ld_word(p.live, dst, W, w0), lv1 = ld_word(p.live, dst, W, w0 + 1);
-    const uint64_t di0 = ld_word(p.d_in, dst, W, w0), di1 = ld_word(p.d_in, dst, W, w0 + 1);
-    const uint64_t c0 = lv0 & ~di0, c1 = lv1 & ~di1;
-    EdgeXfer *out = sd.stream + sd.rec_base[stream];
-    const int cap = sd.rec_cap[stream];
-    for (int q = 0; q < cm.carry_cnt; ++q) {
-      const CarrySrc cs = sd.csrc[cm.carry_beg + q];
-      const uint64_t zs0 = ld_word(sd.xval, cm.carry_beg + q, W, w0), zs1 = ld_word(sd.xval, cm.carry_beg + q, W, w0 + 1);
-      uint64_t to0 = 0, to1 = 0, fr0 = 0, fr1 = 0, e0 = zs0, e1 = zs1;
-      if (cs.ent >= 0) {
-        const uint64_t eh0 = ld_word(p.ec_h, cs.ent, W, w0), eh1 = ld_word(p.ec_h, cs.ent, W, w0 + 1);
-        to0 = ld_word(p.ec_d, cs.ent, W, w0) & ~ld_word(sd.d_src, cs.ent, W, w0);
-        to1 = ld_word(p.ec_d, cs.ent, W, w0 + 1) & ~ld_word(sd.d_src, cs.ent, W, w0 + 1);
-        fr0 = eh0 & zs0;
-        fr1 = eh1 & zs1;
-        e0 &= ~eh0;
-        e1 &= ~eh1;
-      }
-      fr0 |= c0 & e0;
-      fr1 |= c1 & e1;
-      const bool n0 = (to0 | fr0) != 0, n1 = (to1 | fr1) != 0;
-      const unsigned b0 = __ballot_sync(0xffffffffu, n0), b1 = __ballot_sync(0xffffffffu, n1);
-      if (b0 | b1) {
-        const int eid = p.fin_eid[cs.fin_k];
-        const unsigned below = (1u << lane) - 1u;
-        int idx = cnt + __popc(b0 & below) + __popc(b1 & below);
-        if (n0) { if (idx < cap) out[idx] = EdgeXfer{eid, w0, to0, fr0}; ++idx; }
-        if (n1) { if (idx < cap) out[idx] = EdgeXfer{eid, w0 + 1, to1, fr1}; }
-        cnt += __popc(b0) + __popc(b1);
-      }
-    }
+// gather the record streams into the result array: per-CTA sums of the
+// streams' counts, a scan of those sums, per-CTA offsets, then the copy
+constexpr int PF_T = 1024, PF_PER = 4, PF_TILE = PF_T * PF_PER;  // streams per prefix CTA
+
+__device__ __forceinline__ int block_exclusive_sum(int v, int *total) {
+  __shared__ int ws[PF_T / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = v;
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
   }
-  if (lane == 0) sd.rec_cnt[stream] = cnt;
+  if (lane == 31) ws[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int a = ws[lane];
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, a, d);
+      if (lane >= d) a += y;
+    }
+    ws[lane] = a;
+  }
+  __syncthreads();
+  const int before = (wid ? ws[wid - 1] : 0) + x - v;
+  *total = ws[PF_T / 32 - 1];
+  __syncthreads();
+  return before;
 }
 
-// gather the record streams into the result array (single CTA prefix, then copy)
-__global__ void k_streams_prefix(ScanDev sd, int32_t *offs, int32_t *status) {
-  __shared__ int32_t part[1024];
-  __shared__ int overflow;
-  const int t = threadIdx.x, n = sd.n_streams;
-  if (t == 0) overflow = 0;
-  __syncthreads();
-  // each thread sums a contiguous range
-  const int per = (n + blockDim.x - 1) / blockDim.x;
-  const int b = t * per, e = min(n, b + per);
+__global__ void __launch_bounds__(PF_T) k_streams_sums(ScanDev sd, int32_t *part, int32_t *status) {
+  const int base = blockIdx.x * PF_TILE + threadIdx.x * PF_PER;
   int sum = 0;
-  for (int i = b; i < e; ++i) {
+  bool over = false;
+  for (int u = 0; u < PF_PER; ++u) {
+    const int i = base + u;
+    if (i >= sd.n_streams) break;
     const int cnt = sd.rec_cnt[i];
-    if (cnt > sd.rec_cap[i]) overflow = 1;
+    over |= cnt > sd.rec_cap[i];
     sum += cnt;
   }
-  part[t] = sum;
-  __syncthreads();
-  if (t == 0) {
-    int run = 0;
-    for (int i = 0; i < (int)blockDim.x; ++i) {
-      const int x = part[i];
-      part[i] = run;
-      run += x;
-    }
-    status[ST_NREC] = run;
-    if (overflow) status[ST_OVERFLOW] = 1;
+  if (over) atomicExch(&status[ST_OVERFLOW], 1);
+  int total = 0;
+  block_exclusive_sum(sum, &total);
+  if (threadIdx.x == 0) part[blockIdx.x] = total;
+}
+
+// one CTA: exclusive scan of the per-CTA sums (in tiles of PF_T), total
+__global__ void __launch_bounds__(PF_T) k_streams_top(int32_t *part, int n_parts, int32_t *status) {
+  int run = 0;
+  for (int base = 0; base < n_parts; base += PF_T) {
+    const int i = base + threadIdx.x;
+    const int v = i < n_parts ? part[i] : 0;
+    int total = 0;
+    const int before = block_exclusive_sum(v, &total);
+    if (i < n_parts) part[i] = run + before;
+    run += total;
   }
-  __syncthreads();
-  int run = part[t];
-  for (int i = b; i < e; ++i) {
-    offs[i] = run;
-    run += sd.rec_cnt[i];
+  if (threadIdx.x == 0) status[ST_NREC] = run;
+}
+
+__global__ void __launch_bounds__(PF_T) k_streams_offsets(ScanDev sd, const int32_t *part, int32_t *offs) {
+  const int base = blockIdx.x * PF_TILE + threadIdx.x * PF_PER;
+  int cnt[PF_PER], sum = 0;
+  for (int u = 0; u < PF_PER; ++u) {
+    const int i = base + u;
+    cnt[u] = i < sd.n_streams ? sd.rec_cnt[i] : 0;
+    sum += cnt[u];
+  }
+  int total = 0;
+  int run = part[blockIdx.x] + block_exclusive_sum(sum, &total);
+  for (int u = 0; u < PF_PER; ++u) {
+    const int i = base + u;
+    if (i < sd.n_streams) offs[i] = run;
+    run += cnt[u];
   }
 }
 
@@ -1727,15 +1562,15 @@ int clamp_wpc(int wpc) { return wpc <= 0 ? WPC : std::min(8, std::max(1, wpc)); 
 // once (never more than the items need), slots in shared memory up to
 // SH_WORDS words per plane group.
 template <class K>
-ChainShape chain_shape(K kern, int need, int np, bool acc, int wpc, int n_items, int n_sm) {
+ChainShape chain_shape(K kern, int need, int np, int wpc, int n_items, int n_sm) {
   ChainShape c;
   c.wpc = wpc;
   c.sh_slots = std::min(need, SH_WORDS / (64 * np));
-  c.smem = (size_t)wpc * warp_smem_words(c.sh_slots, np, acc) * 8;
+  c.smem = (size_t)wpc * warp_smem_words(c.sh_slots, np) * 8;
   // the attribute belongs to the kernel, not to this plan: always the
   // largest size any plan launches with (8 warps, every slot in shared
   // memory), so plans alive at the same time never shrink it for each other
-  set_smem(kern, (size_t)8 * warp_smem_words(SH_WORDS / (64 * np), np, acc) * 8);
+  set_smem(kern, (size_t)8 * warp_smem_words(SH_WORDS / (64 * np), np) * 8);
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpc, c.smem) != cudaSuccess || per_sm < 1)
     per_sm = 1;
@@ -1822,13 +1657,12 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   std::vector<ChunkMeta> chunks;
   std::vector<CarrySrc> csrc;
   std::vector<int32_t> fin_slot, out_slot, out_pos, lat_slot, bend_loop, srcent;
-  std::vector<int2> latch_be;
   // short chunks give more independent walks (one warp each) and shorter
   // longest walks; 32 positions measured fastest on the 2^20-block CFG
   if (chunk_target <= 0) chunk_target = 32;
   TraceScope trace_bm("scan build_meta", g.M);
   if (!build_meta(g, chunk_target, st, meta, loops, chunks, csrc, fin_slot, out_slot, out_pos, lat_slot, bend_loop,
-                  srcent, latch_be, err)) {
+                  srcent, err)) {
     delete st;
     return nullptr;
   }
@@ -1899,10 +1733,8 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     meta[i].nacc = (int16_t)n;
   }
   std::vector<int2> fin_pk(fin_slot.size()), out_pk(out_slot.size());
-  // in-edge entries: {source slot, loop-entry edge or -1, or BACK_EDGE}
-  for (int i = 0; i < g.M; ++i)
-    for (int k = g.fin_off[i]; k < g.fin_off[i + 1]; ++k)
-      fin_pk[k] = make_int2(fin_slot[k], g.pos[g.fin_src[k]] >= i ? BACK_EDGE : g.fin_ent[k]);
+  // in-edge entries: {source slot, loop-entry edge or -1}
+  for (size_t k = 0; k < fin_pk.size(); ++k) fin_pk[k] = make_int2(fin_slot[k], g.fin_ent[k]);
   for (size_t k = 0; k < out_pk.size(); ++k) out_pk[k] = make_int2(out_slot[k], out_pos[k]);
   const int W = p.W, C = st->C, G = (W + 63) / 64;
   st->G = G;
@@ -1935,7 +1767,6 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   chk(sd.lat_slot = st->up(lat_slot));
   chk(sd.bend_loop = st->up(bend_loop));
   chk(sd.srcent = st->up(srcent));
-  chk(sd.latch_be = st->up(latch_be));
   chk(sd.work = st->up(work));
   chk(sd.queue = st->alloc<int32_t>(Q_SLOTS));
   // launch shapes (persistent: the grid is what fits on the GPU at once)
@@ -1944,15 +1775,11 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     int dev = 0, n_sm = 148;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     const int items = C * G;
-    st->shape[CK_BSUM] = chain_shape(k_bwd_chain<M_SUM>, st->bslots, 2, false, wpc, items, n_sm);
-    st->shape[CK_BAPPLY] = chain_shape(k_bwd_chain<M_APPLY>, st->bslots, 1, false, wpc, items, n_sm);
-    st->shape[CK_BLANT] = chain_shape(k_bwd_chain<M_LANT>, st->bslots, 2, false, wpc, items, n_sm);
-    st->shape[CK_FSUM] = chain_shape(k_fwd_chain<K_HP, M_SUM>, st->fslots, 2, false, wpc, items, n_sm);
-    chain_shape(k_fwd_chain<K_D, M_SUM>, st->fslots, 2, false, wpc, items, n_sm);
-    chain_shape(k_fwd_chain<K_H, M_SUM>, st->fslots, 2, false, wpc, items, n_sm);
-    st->shape[CK_FAPPLY] = chain_shape(k_fwd_chain<K_HP, M_APPLY>, st->fslots, 1, false, wpc, items, n_sm);
-    chain_shape(k_fwd_chain<K_D, M_APPLY>, st->fslots, 1, false, wpc, items, n_sm);
-    st->shape[CK_FEMIT] = chain_shape(k_fwd_chain<K_H, M_APPLY>, st->fslots, 1, true, wpc, items, n_sm);
+    st->shape[CK_BSUM] = chain_shape(k_bwd_chain<M_SUM>, st->bslots, 2, wpc, items, n_sm);
+    st->shape[CK_BLANT] = chain_shape(k_bwd_chain<M_LANT>, st->bslots, 2, wpc, items, n_sm);
+    st->shape[CK_FSUM] = chain_shape(k_fwd_chain<K_HP>, st->fslots, 2, wpc, items, n_sm);
+    chain_shape(k_fwd_chain<K_D>, st->fslots, 2, wpc, items, n_sm);
+    chain_shape(k_fwd_chain<K_H>, st->fslots, 2, wpc, items, n_sm);
   }
   int max_warps = 1;
   for (const ChainShape &c : st->shape) max_warps = std::max(max_warps, c.grid * c.wpc);
@@ -1970,8 +1797,6 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   chk(sd.carry = st->alloc<uint64_t>((size_t)2 * C * W));
   chk(sd.hp_src = st->alloc<uint64_t>((size_t)std::max(1, g.K) * W));
   chk(sd.d_src = st->alloc<uint64_t>((size_t)std::max(1, g.K) * W));
-  st->n_csrc = (int)csrc.size();
-  chk(sd.xval = st->alloc<uint64_t>((size_t)std::max(1, st->n_csrc) * W));
   // emission items: runs of at most EMIT_SPAN positions inside one chunk,
   // each with a record stream per word group, in position order, so each
   // chunk's (and each CFG's) records are contiguous
@@ -2013,6 +1838,7 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   chk(st->d_rec_base = st->alloc<int32_t>(st->n_streams));
   chk(sd.rec_cnt = st->alloc<int32_t>(st->n_streams + 1));
   chk(st->offs = st->alloc<int32_t>(st->n_streams + 1));
+  chk(st->part = st->alloc<int32_t>(st->n_streams / PF_TILE + 2));
   chk(st->init = st->alloc<uint64_t>((size_t)W * p.n_cfg));
   if (ok) ok = scan_set_streams(st);
   sd.rec_cap = st->d_rec_cap;
@@ -2046,10 +1872,13 @@ static int run_emission(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *p
   PROF("emit");
   k_emit<<<grid_of(nw * 32, 32 * EMIT_WARPS), 32 * EMIT_WARPS, 0, s>>>(p, sd, st->init);
   PROF("streams_prefix");
-  k_streams_prefix<<<1, 1024, 0, s>>>(sd, offs, p.status);
+  const int n_parts = (sd.n_streams + PF_TILE - 1) / PF_TILE;
+  k_streams_sums<<<std::max(1, n_parts), PF_T, 0, s>>>(sd, st->part, p.status);
+  k_streams_top<<<1, PF_T, 0, s>>>(st->part, n_parts, p.status);
+  k_streams_offsets<<<std::max(1, n_parts), PF_T, 0, s>>>(sd, st->part, offs);
   PROF("streams_copy");
   k_streams_copy<<<grid_of((long long)sd.n_streams * 32, 256), 256, 0, s>>>(sd, offs, p.xfer, p.xfer_cap);
-  return 3;
+  return 5;
 }
 
 // launch a persistent chain kernel with its shape; qslot: its work-queue head
@@ -2080,7 +1909,7 @@ int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *p
   PROF("live_summary");
   chain_launch(k_bwd_chain<M_SUM>, st->shape[CK_BSUM], p, sl, 0, s); ++n;
   PROF("live_scan");
-  k_scan_carry<<<W, 256, 0, s>>>(sd, W, 1, nullptr); ++n;
+  k_scan_carry<<<W, SCAN_T, 0, s>>>(sd, W, 1, nullptr); ++n;
   PROF("live_resolve");
   k_resolve<RV_LIVE><<<grid_of((nw + 1) / 2, 256), 256, 0, s>>>(p, sd, sd.pair_g, sd.pair_p, p.live); ++n;
   // ---- loop masks: need within the loop body, kills anywhere in it
@@ -2089,9 +1918,9 @@ int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *p
   PROF("entry_stale");
   k_entry_stale<<<grid_of((long long)W * p.n_cfg, 128), 128, 0, s>>>(p.entry_h, p.top, init, W, p.n_cfg); ++n;
   PROF("hp_summary");
-  CHAIN((k_fwd_chain<K_HP, M_SUM>), CK_FSUM, 3);
+  CHAIN(k_fwd_chain<K_HP>, CK_FSUM, 3);
   PROF("fwd_scan");
-  k_scan_carry<<<W, 256, 0, s>>>(sd, W, 0, init); ++n;
+  k_scan_carry<<<W, SCAN_T, 0, s>>>(sd, W, 0, init); ++n;
   if (p.K) {
     PROF("src_resolve");
     k_resolve_src<<<grid_of(kw, 256), 256, 0, s>>>(p, sd, sd.hp_src); ++n;
@@ -2102,9 +1931,9 @@ int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *p
   PROF("entry_stale");
   k_entry_stale<<<grid_of((long long)W * p.n_cfg, 128), 128, 0, s>>>(p.entry_d, p.top, init, W, p.n_cfg); ++n;
   PROF("d_summary");
-  CHAIN((k_fwd_chain<K_D, M_SUM>), CK_FSUM, 5);
+  CHAIN(k_fwd_chain<K_D>, CK_FSUM, 5);
   PROF("fwd_scan");
-  k_scan_carry<<<W, 256, 0, s>>>(sd, W, 0, init); ++n;
+  k_scan_carry<<<W, SCAN_T, 0, s>>>(sd, W, 0, init); ++n;
   PROF("d_resolve");
   k_resolve<RV_VALID><<<grid_of((nw + 1) / 2, 256), 256, 0, s>>>(p, sd, sd.pair_g, sd.pair_p, p.d_in); ++n;
   if (sd.pair_g2) { k_resolve<RV_VALID><<<grid_of((nw + 1) / 2, 256), 256, 0, s>>>(p, sd, sd.pair_g2, sd.pair_p2, p.d_out); ++n; }
@@ -2118,9 +1947,9 @@ int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *p
   PROF("entry_stale");
   k_entry_stale<<<grid_of((long long)W * p.n_cfg, 128), 128, 0, s>>>(p.entry_h, p.top, init, W, p.n_cfg); ++n;
   PROF("h_summary");
-  CHAIN((k_fwd_chain<K_H, M_SUM>), CK_FSUM, 7);
+  CHAIN(k_fwd_chain<K_H>, CK_FSUM, 7);
   PROF("fwd_scan");
-  k_scan_carry<<<W, 256, 0, s>>>(sd, W, 0, init); ++n;
+  k_scan_carry<<<W, SCAN_T, 0, s>>>(sd, W, 0, init); ++n;
   PROF("h_resolve");
   k_resolve<RV_VALID><<<grid_of((nw + 1) / 2, 256), 256, 0, s>>>(p, sd, sd.pair_g, sd.pair_p, p.h_out); ++n;
   n += run_emission(st, p, s, pf);
