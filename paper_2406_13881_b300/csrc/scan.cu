@@ -40,7 +40,7 @@ namespace {
 constexpr int CARRY = -2;      // slot id: the chunk's incoming carry
 constexpr int PREV = -3;       // slot id: the value of the position walked just before
 #ifndef OMPDART_SH_WORDS
-#define OMPDART_SH_WORDS 512
+#define OMPDART_SH_WORDS 256
 #endif
 #ifndef OMPDART_CHAIN_MIN_CTAS
 #define OMPDART_CHAIN_MIN_CTAS 1
@@ -121,7 +121,8 @@ struct ScanDev {
   uint64_t *hp_src, *d_src;  // [K][W] plain host / device validity at loop-entry sources
   // affine pairs the summary walks leave per position: value = G | (carry & P)
   // with the carry into the position's chunk (resolved by k_resolve_*)
-  uint64_t *pair_g, *pair_p;    // [N][W] by block: Live_in, D_in stale, or H_out stale
+  uint64_t *pair_g, *pair_p;    // [N][W] by block: Live_in, later H_out stale
+  uint64_t *pair_gd, *pair_pd;  // [N][W] D_in stale (the device phase runs beside liveness)
   uint64_t *pair_g2, *pair_p2;  // [N][W] D_out stale (kept states only), else null
   uint64_t *src_g, *src_p;      // [K][W] out value at each loop-entry edge's source
   const int32_t *pos_chunk;     // [M] chunk of each position
@@ -193,7 +194,17 @@ struct ScanState {
   uint64_t *init = nullptr;        // [W] stale set entering the first chunk
   EdgeXfer *stream_buf = nullptr;
   long long bytes = 0;  // device bytes held
+  // a run forks: loop masks and liveness on two side streams beside the
+  // plain-host / device / host pipeline on the caller's stream (their walks'
+  // tails overlap); each branch has its own spill region and chunk maps
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  size_t spill_region = 0;  // words per branch
   ~ScanState() {
+    for (cudaStream_t x : side)
+      if (x) cudaStreamDestroy(x);
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
     for (void *p : allocs) dev_free(p);
   }
   template <class T>
@@ -817,10 +828,10 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
     {
       const size_t row = (size_t)m.blk;
       if (PH == K_D) {  // device validity at the block entry (and exit, kept states)
-        st_word(sd.pair_g, row, W, L.w0, z[0][0]);
-        st_word(sd.pair_g, row, W, L.w0 + 1, z[0][1]);
-        st_word(sd.pair_p, row, W, L.w0, z[1][0]);
-        st_word(sd.pair_p, row, W, L.w0 + 1, z[1][1]);
+        st_word(sd.pair_gd, row, W, L.w0, z[0][0]);
+        st_word(sd.pair_gd, row, W, L.w0 + 1, z[0][1]);
+        st_word(sd.pair_pd, row, W, L.w0, z[1][0]);
+        st_word(sd.pair_pd, row, W, L.w0 + 1, z[1][1]);
         if (sd.pair_g2) {
           st_word(sd.pair_g2, row, W, L.w0, zo[0][0]);
           st_word(sd.pair_g2, row, W, L.w0 + 1, zo[0][1]);
@@ -1745,12 +1756,18 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   sd.bslots = st->bslots;
   sd.keep_states = keep_states;
   sd.cfg_err = cfg_err;
-  // work order: longest chunks first (their walks bound the launch)
+  // work order: costliest chunks first (their walks bound the launch); a
+  // position inside d nested loops may be walked up to about 2^d times
   std::vector<int32_t> work(C);
-  for (int c = 0; c < C; ++c) work[c] = c;
-  std::stable_sort(work.begin(), work.end(), [&](int a, int b) {
-    return chunks[a].e - chunks[a].s > chunks[b].e - chunks[b].s;
-  });
+  std::vector<long long> cost(C, 0);
+  for (int c = 0; c < C; ++c) {
+    work[c] = c;
+    for (int i = chunks[c].s; i < chunks[c].e; ++i) {
+      const int l = g.inner_loop[g.order[i]];
+      cost[c] += 1ll << std::min(l >= 0 ? g.loop_depth[l] : 0, 4);
+    }
+  }
+  std::stable_sort(work.begin(), work.end(), [&](int a, int b) { return cost[a] > cost[b]; });
   bool ok = true;
   auto chk = [&](const void *x) { ok = ok && x; };
   chk(sd.meta = st->up(meta));
@@ -1787,7 +1804,8 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   // SH_WORDS / 128 of them, 2 planes at most) spill to a per-warp area
   const int max_slots = std::max(st->fslots, st->bslots), min_sh = SH_WORDS / (64 * 2);
   sd.spill_stride = std::max(1, max_slots - min_sh) * 2 * 64;
-  chk(sd.spill = st->alloc<uint64_t>((size_t)std::max(1, sd.spill_stride) * max_warps));
+  st->spill_region = (size_t)std::max(1, sd.spill_stride) * max_warps;
+  chk(sd.spill = st->alloc<uint64_t>(st->spill_region * 3));  // one region per branch of a run
   chk(sd.gsum = st->alloc<uint64_t>((size_t)2 * C * W));
   chk(sd.psum = st->alloc<uint64_t>((size_t)2 * C * W));
   if (ok) {  // chunks that end a CFG never write their map: keep it defined
@@ -1826,6 +1844,8 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     const size_t NW = (size_t)g.N * W, KW = (size_t)std::max(1, g.K) * W;
     chk(sd.pair_g = st->alloc<uint64_t>(NW));
     chk(sd.pair_p = st->alloc<uint64_t>(NW));
+    chk(sd.pair_gd = st->alloc<uint64_t>(NW));
+    chk(sd.pair_pd = st->alloc<uint64_t>(NW));
     sd.pair_g2 = sd.pair_p2 = nullptr;
     if (keep_states) {
       chk(sd.pair_g2 = st->alloc<uint64_t>(NW));
@@ -1841,6 +1861,8 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   chk(st->part = st->alloc<int32_t>(st->n_streams / PF_TILE + 2));
   chk(st->init = st->alloc<uint64_t>((size_t)W * p.n_cfg));
   if (ok) ok = scan_set_streams(st);
+  for (int k = 0; k < 2 && ok; ++k) ok = cudaStreamCreateWithFlags(&st->side[k], cudaStreamNonBlocking) == cudaSuccess;
+  for (int k = 0; k < 3 && ok; ++k) ok = cudaEventCreateWithFlags(&st->ev[k], cudaEventDisableTiming) == cudaSuccess;
   sd.rec_cap = st->d_rec_cap;
   sd.rec_base = st->d_rec_base;
   if (!ok) {
@@ -1888,70 +1910,99 @@ void chain_launch(K kern, const ChainShape &cs, const DevPlan &p, const ScanDev 
   sd2.sh_slots = cs.sh_slots;
   kern<<<cs.grid, 32 * cs.wpc, cs.smem, s>>>(p, sd2, qslot);
 }
-#define CHAIN(kern, kind, qslot) (chain_launch(kern, st->shape[kind], p, sd, qslot, s), ++n)
 
 // One run: local summaries; per phase a summary walk that leaves every
 // position's affine pair, the scan of the chunk maps, and a parallel resolve
 // of the pairs with the carries; then the emission from the final states.
+// The phases that need nothing of each other run on separate streams so
+// the tails of their walks overlap:
+//   side 0: loop masks;   side 1: liveness;
+//   caller's stream: plain host validity, device validity (after the masks),
+//                    host validity and emission (after liveness).
+// With per-kernel profiling on, everything runs on the caller's stream.
 int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *pf) {
   ScanDev &sd = st->sd;
-  const int W = p.W;
+  const int W = p.W, C = sd.C;
   uint64_t *init = st->init;
   int n = 0;
   const long long nw = (long long)p.M * W, kw = (long long)p.K * W;
+  const bool fork = pf == nullptr;
+  cudaStream_t s_lant = fork ? st->side[0] : s, s_live = fork ? st->side[1] : s;
+  // per-branch views: own spill region and chunk maps
+  ScanDev sl = sd, sm = sd, sq = sd;  // liveness, masks, the main pipeline
+  sl.spill = sd.spill + st->spill_region;
+  sm.spill = sd.spill;
+  sq.spill = sd.spill + 2 * st->spill_region;
+  sq.gsum = sd.gsum + (size_t)C * W;
+  sq.psum = sd.psum + (size_t)C * W;
+  sq.carry = sd.carry + (size_t)C * W;
   cudaMemsetAsync(p.acc_flag, 0, (size_t)p.A, s);
   cudaMemsetAsync(sd.queue, 0, sizeof(int32_t) * Q_SLOTS, s);
   PROF("local_summary");
   k_local_summary_pos<<<grid_of(sd.n_acc_p, 256), 256, 0, s>>>(sd); ++n;
-  // ---- liveness (backward)
-  ScanDev sl = sd;  // liveness pairs only
-  sl.pair_g2 = sl.pair_p2 = nullptr;
-  PROF("live_summary");
-  chain_launch(k_bwd_chain<M_SUM>, st->shape[CK_BSUM], p, sl, 0, s); ++n;
-  PROF("live_scan");
-  k_scan_carry<<<W, SCAN_T, 0, s>>>(sd, W, 1, nullptr); ++n;
-  PROF("live_resolve");
-  k_resolve<RV_LIVE><<<grid_of((nw + 1) / 2, 256), 256, 0, s>>>(p, sd, sd.pair_g, sd.pair_p, p.live); ++n;
+  if (fork) {
+    cudaEventRecord(st->ev[0], s);
+    cudaStreamWaitEvent(s_lant, st->ev[0], 0);
+    cudaStreamWaitEvent(s_live, st->ev[0], 0);
+  }
   // ---- loop masks: need within the loop body, kills anywhere in it
-  if (p.L) { PROF("loop_masks"); CHAIN(k_bwd_chain<M_LANT>, CK_BLANT, 2); }
+  if (p.L) {
+    PROF("loop_masks");
+    chain_launch(k_bwd_chain<M_LANT>, st->shape[CK_BLANT], p, sm, 2, s_lant); ++n;
+  }
+  // ---- liveness (backward)
+  PROF("live_summary");
+  chain_launch(k_bwd_chain<M_SUM>, st->shape[CK_BSUM], p, sl, 0, s_live); ++n;
+  PROF("live_scan");
+  k_scan_carry<<<W, SCAN_T, 0, s_live>>>(sl, W, 1, nullptr); ++n;
+  PROF("live_resolve");
+  k_resolve<RV_LIVE><<<grid_of((nw + 1) / 2, 256), 256, 0, s_live>>>(p, sl, sl.pair_g, sl.pair_p, p.live); ++n;
+  if (fork) {
+    cudaEventRecord(st->ev[1], s_lant);
+    cudaEventRecord(st->ev[2], s_live);
+  }
   // ---- plain host validity (needed at loop-entry sources only)
   PROF("entry_stale");
   k_entry_stale<<<grid_of((long long)W * p.n_cfg, 128), 128, 0, s>>>(p.entry_h, p.top, init, W, p.n_cfg); ++n;
   PROF("hp_summary");
-  CHAIN(k_fwd_chain<K_HP>, CK_FSUM, 3);
+  chain_launch(k_fwd_chain<K_HP>, st->shape[CK_FSUM], p, sq, 3, s); ++n;
   PROF("fwd_scan");
-  k_scan_carry<<<W, SCAN_T, 0, s>>>(sd, W, 0, init); ++n;
+  k_scan_carry<<<W, SCAN_T, 0, s>>>(sq, W, 0, init); ++n;
+  if (fork) cudaStreamWaitEvent(s, st->ev[1], 0);  // the masks
   if (p.K) {
     PROF("src_resolve");
-    k_resolve_src<<<grid_of(kw, 256), 256, 0, s>>>(p, sd, sd.hp_src); ++n;
+    k_resolve_src<<<grid_of(kw, 256), 256, 0, s>>>(p, sq, sq.hp_src); ++n;
     PROF("edge_const");
-    k_scan_edge_const<<<grid_of(kw, 256), 256, 0, s>>>(p, sd, 0); ++n;
+    k_scan_edge_const<<<grid_of(kw, 256), 256, 0, s>>>(p, sq, 0); ++n;
   }
   // ---- device validity
   PROF("entry_stale");
   k_entry_stale<<<grid_of((long long)W * p.n_cfg, 128), 128, 0, s>>>(p.entry_d, p.top, init, W, p.n_cfg); ++n;
   PROF("d_summary");
-  CHAIN(k_fwd_chain<K_D>, CK_FSUM, 5);
+  chain_launch(k_fwd_chain<K_D>, st->shape[CK_FSUM], p, sq, 5, s); ++n;
   PROF("fwd_scan");
-  k_scan_carry<<<W, SCAN_T, 0, s>>>(sd, W, 0, init); ++n;
+  k_scan_carry<<<W, SCAN_T, 0, s>>>(sq, W, 0, init); ++n;
   PROF("d_resolve");
-  k_resolve<RV_VALID><<<grid_of((nw + 1) / 2, 256), 256, 0, s>>>(p, sd, sd.pair_g, sd.pair_p, p.d_in); ++n;
-  if (sd.pair_g2) { k_resolve<RV_VALID><<<grid_of((nw + 1) / 2, 256), 256, 0, s>>>(p, sd, sd.pair_g2, sd.pair_p2, p.d_out); ++n; }
+  k_resolve<RV_VALID><<<grid_of((nw + 1) / 2, 256), 256, 0, s>>>(p, sq, sq.pair_gd, sq.pair_pd, p.d_in); ++n;
+  if (sq.pair_g2) {
+    k_resolve<RV_VALID><<<grid_of((nw + 1) / 2, 256), 256, 0, s>>>(p, sq, sq.pair_g2, sq.pair_p2, p.d_out); ++n;
+  }
   if (p.K) {
     PROF("src_resolve");
-    k_resolve_src<<<grid_of(kw, 256), 256, 0, s>>>(p, sd, sd.d_src); ++n;
+    k_resolve_src<<<grid_of(kw, 256), 256, 0, s>>>(p, sq, sq.d_src); ++n;
     PROF("edge_const");
-    k_scan_edge_const<<<grid_of(kw, 256), 256, 0, s>>>(p, sd, 1); ++n;
+    k_scan_edge_const<<<grid_of(kw, 256), 256, 0, s>>>(p, sq, 1); ++n;
   }
   // ---- host validity (its exit states), then the emission
+  if (fork) cudaStreamWaitEvent(s, st->ev[2], 0);  // liveness
   PROF("entry_stale");
   k_entry_stale<<<grid_of((long long)W * p.n_cfg, 128), 128, 0, s>>>(p.entry_h, p.top, init, W, p.n_cfg); ++n;
   PROF("h_summary");
-  CHAIN(k_fwd_chain<K_H>, CK_FSUM, 7);
+  chain_launch(k_fwd_chain<K_H>, st->shape[CK_FSUM], p, sq, 7, s); ++n;
   PROF("fwd_scan");
-  k_scan_carry<<<W, SCAN_T, 0, s>>>(sd, W, 0, init); ++n;
+  k_scan_carry<<<W, SCAN_T, 0, s>>>(sq, W, 0, init); ++n;
   PROF("h_resolve");
-  k_resolve<RV_VALID><<<grid_of((nw + 1) / 2, 256), 256, 0, s>>>(p, sd, sd.pair_g, sd.pair_p, p.h_out); ++n;
+  k_resolve<RV_VALID><<<grid_of((nw + 1) / 2, 256), 256, 0, s>>>(p, sq, sq.pair_g, sq.pair_p, p.h_out); ++n;
   n += run_emission(st, p, s, pf);
   return n;
 }
@@ -1962,7 +2013,6 @@ int enqueue_scan_edges(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *pf
   return run_emission(st, p, s, pf);
 }
 
-#undef CHAIN
 
 // first gathered record of each chunk (and the total at index C), after a
 // completed run: the offsets of the chunk's first stream
