@@ -79,7 +79,7 @@ struct LoopMeta {
   int16_t hslot, depth;
   int32_t lat_beg;    // latch slots to clear on a fresh entry
   int32_t lat_cnt;
-  int32_t pad;
+  int32_t cfg;        // the CFG of a batch it belongs to
 };
 
 struct ChunkMeta {
@@ -134,7 +134,9 @@ struct ScanDev {
   EdgeXfer *stream;    // record streams
   int n_streams;
   int keep_states;
-  const int32_t *work;  // [C] chunks by decreasing length: the order warps take them in
+  const int32_t *work;  // [C] chunks by decreasing cost: the order warps take them in
+  const int32_t *lant_work;  // [L] loops by decreasing body length (loop-mask walks)
+  int n_loops;
   int32_t *queue;       // [Q_SLOTS] work-queue heads, one per chain launch of a run
   int32_t *cfg_err;     // [n_cfg] set to 1 for a CFG whose walk hit the re-run cap, or null
 };
@@ -414,6 +416,8 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
   }
   for (int l = 0; l < L; ++l) {
     LoopMeta &lm = loops[l];
+    lm.cfg = (int32_t)(std::upper_bound(g.cfg_pos_off.begin(), g.cfg_pos_off.end(), g.pos[g.loop_head[l]]) -
+                       g.cfg_pos_off.begin()) - 1;
     lm.ph = g.pos[g.loop_head[l]];
     lm.pend = g.loop_end[l];
     lm.hslot = (int16_t)hslot[l];
@@ -1100,25 +1104,6 @@ __device__ __forceinline__ void bwd_walk(const DevPlan &p, const ScanDev &sd, co
   Slots<NP> sl{wm.slots, spill, sd.sh_slots};
   const ChunkMeta cm = sd.chunks[c];
   uint64_t cin[NP][2], zl[NP][2];
-  if (MODE == M_LANT) {
-#pragma unroll
-    for (int pl = 0; pl < NP; ++pl) cin[pl][0] = cin[pl][1] = 0;
-    for (int l = cm.loop_beg; l < cm.loop_end; ++l) {
-      const LoopMeta lm = sd.loops[l];
-      *reinterpret_cast<ulonglong2 *>(wm.kill + 2 * L.lane) = make_ulonglong2(0ull, 0ull);
-      *reinterpret_cast<ulonglong2 *>(wm.kill + 64 + 2 * L.lane) = make_ulonglong2(0ull, 0ull);
-      __syncwarp();
-      bwd_range<MODE>(p, sd, L, wm, sl, lm.ph, lm.pend, lm.depth, lm.ph, false, cin, zl, cm.cfg);
-      const ulonglong2 kh = *reinterpret_cast<const ulonglong2 *>(wm.kill + 2 * L.lane);
-      const ulonglong2 kd = *reinterpret_cast<const ulonglong2 *>(wm.kill + 64 + 2 * L.lane);
-      st_word(p.mask_h, l, W, L.w0, zl[0][0] & ~kh.x & L.top0);
-      st_word(p.mask_h, l, W, L.w0 + 1, zl[0][1] & ~kh.y & L.top1);
-      st_word(p.mask_d, l, W, L.w0, zl[1][0] & ~kd.x & L.top0);
-      st_word(p.mask_d, l, W, L.w0 + 1, zl[1][1] & ~kd.y & L.top1);
-      __syncwarp();
-    }
-    return;
-  }
   // the identity map of the liveness entering from the next chunk
   cin[0][0] = cin[0][1] = 0;
   cin[1][0] = L.top0;
@@ -1130,7 +1115,37 @@ __device__ __forceinline__ void bwd_walk(const DevPlan &p, const ScanDev &sd, co
   st_word(sd.psum, c, W, L.w0 + 1, zl[1][1]);
 }
 
-// persistent backward chain (same work queue scheme as the forward one)
+// The loop masks of loop l for the 64-word group wg: anticipation
+// restricted to its body (one iteration from the header) and the kills
+// anywhere in the body, by one walk of the body (Sec. IV-D loop rule).
+__device__ __forceinline__ void lant_walk(const DevPlan &p, const ScanDev &sd, const WarpMem &wm, uint64_t *spill,
+                                          int l, int wg) {
+  constexpr int NP = 2;
+  const int W = p.W;
+  const LoopMeta lm = sd.loops[l];
+  Lane L;
+  L.lane = threadIdx.x & 31;
+  L.wg = wg;
+  L.w0 = wg * 64 + 2 * L.lane;
+  const uint64_t *tp = p.top + (size_t)lm.cfg * W;
+  L.top0 = L.w0 < W ? tp[L.w0] : 0;
+  L.top1 = L.w0 + 1 < W ? tp[L.w0 + 1] : 0;
+  Slots<NP> sl{wm.slots, spill, sd.sh_slots};
+  uint64_t cin[NP][2] = {}, zl[NP][2];
+  *reinterpret_cast<ulonglong2 *>(wm.kill + 2 * L.lane) = make_ulonglong2(0ull, 0ull);
+  *reinterpret_cast<ulonglong2 *>(wm.kill + 64 + 2 * L.lane) = make_ulonglong2(0ull, 0ull);
+  __syncwarp();
+  bwd_range<M_LANT>(p, sd, L, wm, sl, lm.ph, lm.pend, lm.depth, lm.ph, false, cin, zl, lm.cfg);
+  const ulonglong2 kh = *reinterpret_cast<const ulonglong2 *>(wm.kill + 2 * L.lane);
+  const ulonglong2 kd = *reinterpret_cast<const ulonglong2 *>(wm.kill + 64 + 2 * L.lane);
+  st_word(p.mask_h, l, W, L.w0, zl[0][0] & ~kh.x & L.top0);
+  st_word(p.mask_h, l, W, L.w0 + 1, zl[0][1] & ~kh.y & L.top1);
+  st_word(p.mask_d, l, W, L.w0, zl[1][0] & ~kd.x & L.top0);
+  st_word(p.mask_d, l, W, L.w0 + 1, zl[1][1] & ~kd.y & L.top1);
+}
+
+// persistent backward chain (same work queue scheme as the forward one);
+// the loop-mask walks take one loop per item
 template <int MODE>
 __global__ void __launch_bounds__(256, OMPDART_CHAIN_MIN_CTAS) k_bwd_chain(DevPlan p, ScanDev sd, int qslot) {
   constexpr int NP = BwdPlanes<MODE>::NP;
@@ -1139,9 +1154,12 @@ __global__ void __launch_bounds__(256, OMPDART_CHAIN_MIN_CTAS) k_bwd_chain(DevPl
   const int gw = blockIdx.x * (blockDim.x >> 5) + warp_in_cta;
   const WarpMem wm = carve<NP>(smem, warp_in_cta, sd.sh_slots);
   uint64_t *spill = sd.spill + (size_t)gw * sd.spill_stride;
-  const int n_items = sd.C * sd.G;
+  const int n_items = (MODE == M_LANT ? sd.n_loops : sd.C) * sd.G;
   for (int item = next_item(sd, qslot); item < n_items; item = next_item(sd, qslot)) {
-    bwd_walk<MODE>(p, sd, wm, spill, sd.work[item / sd.G], item % sd.G);
+    if (MODE == M_LANT)
+      lant_walk(p, sd, wm, spill, sd.lant_work[item / sd.G], item % sd.G);
+    else
+      bwd_walk<MODE>(p, sd, wm, spill, sd.work[item / sd.G], item % sd.G);
     __syncwarp();
   }
 }
@@ -1768,6 +1786,12 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     }
   }
   std::stable_sort(work.begin(), work.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  std::vector<int32_t> lant_work(g.L);
+  for (int l = 0; l < g.L; ++l) lant_work[l] = l;
+  std::stable_sort(lant_work.begin(), lant_work.end(), [&](int a, int b) {
+    return loops[a].pend - loops[a].ph > loops[b].pend - loops[b].ph;
+  });
+  sd.n_loops = g.L;
   bool ok = true;
   auto chk = [&](const void *x) { ok = ok && x; };
   chk(sd.meta = st->up(meta));
@@ -1785,6 +1809,7 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   chk(sd.bend_loop = st->up(bend_loop));
   chk(sd.srcent = st->up(srcent));
   chk(sd.work = st->up(work));
+  chk(sd.lant_work = st->up(lant_work));
   chk(sd.queue = st->alloc<int32_t>(Q_SLOTS));
   // launch shapes (persistent: the grid is what fits on the GPU at once)
   {
@@ -1793,7 +1818,7 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     const int items = C * G;
     st->shape[CK_BSUM] = chain_shape(k_bwd_chain<M_SUM>, st->bslots, 2, wpc, items, n_sm);
-    st->shape[CK_BLANT] = chain_shape(k_bwd_chain<M_LANT>, st->bslots, 2, wpc, items, n_sm);
+    st->shape[CK_BLANT] = chain_shape(k_bwd_chain<M_LANT>, st->bslots, 2, wpc, std::max(1, g.L) * G, n_sm);
     st->shape[CK_FSUM] = chain_shape(k_fwd_chain<K_HP>, st->fslots, 2, wpc, items, n_sm);
     chain_shape(k_fwd_chain<K_D>, st->fslots, 2, wpc, items, n_sm);
     chain_shape(k_fwd_chain<K_H>, st->fslots, 2, wpc, items, n_sm);
