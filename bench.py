@@ -49,6 +49,14 @@ def workload_name(n_blocks):
     return WORKLOAD if n_blocks == 1 << 20 else WORKLOAD.replace("2^20", str(n_blocks))
 
 
+# DRAM traffic per launch from ncu captures of the current kernels (see
+# profiles/): dram__bytes_read.sum + dram__bytes_write.sum on the 2^18-block
+# version of the workload, scaled to the bench's launch by block-words
+MEASURED_TRAFFIC = {
+    "live_summary": {"bytes_2e18": 46.233856e6 + 334.327808e6, "profile": "profiles/live_summary_walk_2e18.md"},
+}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -263,8 +271,12 @@ def run_ours(args):
         peak, src = peaks()
         bytes_ = model.get(name)
         achieved = bytes_ / (avg_ms / 1e3) / 1e9 if bytes_ else None
+        meas = MEASURED_TRAFFIC.get(name)
+        traffic = meas["bytes_2e18"] * (g.n_blocks * g.W) / float((1 << 18) * 64) if meas else None
         roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
+                "traffic_source": ("ncu, 2^18-block capture scaled by block-words: " + meas["profile"]) if meas
+                else None,
                 "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src,
                 "algorithmic_bytes_per_launch": bytes_, "avg_launch_ms": avg_ms,
                 "kernels": {k: {"launches": v[0], "ms": round(v[1], 4),
