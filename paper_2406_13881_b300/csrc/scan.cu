@@ -56,7 +56,7 @@ __host__ __device__ inline int rerun_cap(int len) { return 8 * len + 64; }
 enum PhaseKind { K_ANT = 0, K_HP = 1, K_D = 2, K_H = 3 };
 enum ModeKind { M_SUM = 0, M_LANT = 2 };  // summary walk; loop-restricted anticipation
 
-struct PosMeta {  // one per position, 64 B
+struct PosMeta {  // one per position, 80 B
   int32_t blk;
   int32_t fin_beg, out_beg, acc_beg, srcent_beg, bend_beg;  // acc_beg: in caller order
   int16_t nfin, nout, nacc, nsrcent, nbend, fslot, bslot, pad0;
@@ -66,13 +66,19 @@ struct PosMeta {  // one per position, 64 B
   int32_t pacc_beg;       // first access of the block in position order
   int32_t flags;          // PM_RECORDS: the block's summary records are given
   int32_t pad3;
+  // a header position: its loop's body end, header slot, depth and latch
+  // slots (kept here so the walks need no loop record at a header)
+  int32_t head_pend;
+  int16_t head_hslot, head_depth;
+  int32_t head_lat_beg;
+  int16_t head_lat_cnt, pad5;
 };
 // a block with call pseudo-accesses: its entries in the position-ordered
 // access stream are already summary records (folded on the host with the
 // callees' rows), and its access flags come from the call-site pass
 constexpr int32_t PM_RECORDS = 1;
 constexpr int32_t LINK_RECORD = -2;
-static_assert(sizeof(PosMeta) == 64, "PosMeta layout");
+static_assert(sizeof(PosMeta) == 80, "PosMeta layout");
 
 struct LoopMeta {
   int32_t ph, pend;   // body = positions [ph, pend)
@@ -430,6 +436,12 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
         lat_slot.push_back(fslot[pp]);
     }
     lm.lat_cnt = (int32_t)lat_slot.size() - lm.lat_beg;
+    PosMeta &hm = meta[lm.ph];
+    hm.head_pend = lm.pend;
+    hm.head_hslot = lm.hslot;
+    hm.head_depth = lm.depth;
+    hm.head_lat_beg = lm.lat_beg;
+    hm.head_lat_cnt = (int16_t)lm.lat_cnt;
   }
   st->C = C;
   st->fslots = std::max(max_f, 1);
@@ -690,7 +702,8 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
   cin[0][0] = cin[0][1] = 0;
   cin[1][0] = L.top0;
   cin[1][1] = L.top1;
-  int st_loop[MAX_DEPTH + 1];
+  // open loops, innermost last: header position, body end, header slot
+  int st_ph[MAX_DEPTH + 1], st_pend[MAX_DEPTH + 1], st_hs[MAX_DEPTH + 1];
   int depth = 0;
   uint32_t dirty = 0;
   int reruns = 0;
@@ -734,19 +747,20 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
       }
     }
     if (m.head_loop >= 0) {
-      const LoopMeta lm = sd.loops[m.head_loop];
-      if (lm.depth > depth) {  // entering the loop from outside
-        st_loop[depth] = m.head_loop;
+      if (m.head_depth > depth) {  // entering the loop from outside
+        st_ph[depth] = i;
+        st_pend[depth] = m.head_pend;
+        st_hs[depth] = m.head_hslot;
         dirty &= ~(1u << depth);
         ++depth;
-        top_pend = lm.pend;
+        top_pend = m.head_pend;
         // first visit in this walk: the back edges carry nothing yet.  A
         // re-entry (an enclosing body walked again) keeps the latch values
         // of the previous visit: they are below the new fixed point and the
         // header = entry | old latches is then exact in one walk.
         if (i > hwm) {
-          for (int q = 0; q < lm.lat_cnt; ++q) {
-            const int s = sd.lat_slot[lm.lat_beg + q];
+          for (int q = 0; q < m.head_lat_cnt; ++q) {
+            const int s = sd.lat_slot[m.head_lat_beg + q];
             for (int pl = 0; pl < NP; ++pl) *sl.at(s, pl, L.lane) = make_ulonglong2(0ull, 0ull);
           }
           __syncwarp();
@@ -781,7 +795,7 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
     // a header remembers the meet of its in-edges (before the node's own
     // mask): a latch that adds to it makes the loop body run again
     if (m.head_loop >= 0) {
-      const int hs = sd.loops[m.head_loop].hslot;
+      const int hs = m.head_hslot;
 #pragma unroll
       for (int pl = 0; pl < NP; ++pl) *sl.at(hs, pl, L.lane) = make_ulonglong2(z[pl][0], z[pl][1]);
     }
@@ -809,7 +823,7 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
         const int lvl = __ffs(lvmask) - 1;
         lvmask &= lvmask - 1;
         if (lvl >= depth) continue;
-        const int hs = sd.loops[st_loop[lvl]].hslot;
+        const int hs = st_hs[lvl];
         bool grow = false;
 #pragma unroll
         for (int pl = 0; pl < NP; ++pl) {
@@ -865,12 +879,12 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
     while (depth > 0 && top_pend - 1 == i) {
       if (dirty & (1u << (depth - 1))) {
         dirty &= ~(1u << (depth - 1));
-        i = sd.loops[st_loop[depth - 1]].ph;
+        i = st_ph[depth - 1];
         jumped = true;
         break;
       }
       --depth;
-      top_pend = depth > 0 ? sd.loops[st_loop[depth - 1]].pend : -1;
+      top_pend = depth > 0 ? st_pend[depth - 1] : -1;
     }
     hwm = max(hwm, i);
     if (jumped) {
@@ -951,7 +965,7 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
   const int W = p.W;
   const uint64_t *xlr = p.exit_live + (size_t)cfg * W;
   const uint64_t xl0 = L.w0 < W ? xlr[L.w0] : 0, xl1 = L.w0 + 1 < W ? xlr[L.w0 + 1] : 0;
-  int st_loop[MAX_DEPTH + 1];
+  int st_ph[MAX_DEPTH + 1], st_pend[MAX_DEPTH + 1];  // open loops: header position, body end
   int depth = base_depth;
   uint32_t dirty = 0;
   int reruns = 0;
@@ -983,7 +997,8 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
       const int l = sd.bend_loop[m.bend_beg + q];
       const LoopMeta lm = sd.loops[l];
       if (lm.depth <= depth) continue;
-      st_loop[lm.depth - 1] = l;
+      st_ph[lm.depth - 1] = lm.ph;
+      st_pend[lm.depth - 1] = lm.pend;
       dirty &= ~(1u << (lm.depth - 1));
       depth = lm.depth;
       top_ph = lm.ph;
@@ -1066,12 +1081,12 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
     while (depth > base_depth && top_ph == i) {
       if (dirty & (1u << (depth - 1))) {
         dirty &= ~(1u << (depth - 1));
-        i = sd.loops[st_loop[depth - 1]].pend - 1;
+        i = st_pend[depth - 1] - 1;
         jumped = true;
         break;
       }
       --depth;
-      top_ph = depth > base_depth ? sd.loops[st_loop[depth - 1]].ph : -1;
+      top_ph = depth > base_depth ? st_ph[depth - 1] : -1;
     }
     lwm = min(lwm, i);
     if (jumped) {
