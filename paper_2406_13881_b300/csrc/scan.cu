@@ -118,7 +118,7 @@ struct ScanDev {
   long long n_acc_p;      // entries of the position-ordered access stream
   int sh_slots;           // slots per plane held in shared memory
   const int32_t *lat_slot;
-  const int32_t *bend_loop;
+  const int4 *bend_info;  // per loop ending at a position: {depth, header position, body end, header's backward slot}
   const int32_t *srcent;
   uint64_t *spill;     // per warp spill area
   int spill_stride;    // words per warp
@@ -994,18 +994,17 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
     }
     // enter loops whose range ends here (outer first)
     for (int q = 0; q < m.nbend; ++q) {
-      const int l = sd.bend_loop[m.bend_beg + q];
-      const LoopMeta lm = sd.loops[l];
-      if (lm.depth <= depth) continue;
-      st_ph[lm.depth - 1] = lm.ph;
-      st_pend[lm.depth - 1] = lm.pend;
-      dirty &= ~(1u << (lm.depth - 1));
-      depth = lm.depth;
-      top_ph = lm.ph;
+      const int4 bi = sd.bend_info[m.bend_beg + q];  // {depth, header position, body end, header slot}
+      if (bi.x <= depth) continue;
+      st_ph[bi.x - 1] = bi.y;
+      st_pend[bi.x - 1] = bi.z;
+      dirty &= ~(1u << (bi.x - 1));
+      depth = bi.x;
+      top_ph = bi.y;
       // first visit: the header's value, read by the latches, starts from
       // nothing; a re-entry keeps the previous visit's value
       if (i < lwm) {
-        const int hs = sd.meta[lm.ph].bslot;
+        const int hs = bi.w;
         if (hs >= 0)
           for (int pl = 0; pl < NP; ++pl) *sl.at(hs, pl, L.lane) = make_ulonglong2(0ull, 0ull);
         __syncwarp();
@@ -1306,7 +1305,10 @@ __global__ void k_resolve_src(DevPlan p, ScanDev sd, uint64_t *out) {
 //   region exit: live after the exit and stale on the host.
 // --------------------------------------------------------------------------------------
 constexpr int EMIT_WARPS = 4;
-constexpr int EMIT_SPAN = 8;  // positions per emission item (its own record stream)
+#ifndef OMPDART_EMIT_SPAN
+#define OMPDART_EMIT_SPAN 8
+#endif
+constexpr int EMIT_SPAN = OMPDART_EMIT_SPAN;  // positions per emission item (its own record stream)
 __global__ void __launch_bounds__(32 * EMIT_WARPS) k_emit(DevPlan p, ScanDev sd, const uint64_t *init) {
   __shared__ uint64_t hd_all[EMIT_WARPS][128];
   const int gw = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
@@ -1821,7 +1823,14 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   chk(sd.acc_link = st->up(acc_link));
   sd.n_acc_p = (long long)acc_p.size();
   chk(sd.lat_slot = st->up(lat_slot));
-  chk(sd.bend_loop = st->up(bend_loop));
+  {
+    std::vector<int4> bend_info(bend_loop.size());
+    for (size_t q = 0; q < bend_loop.size(); ++q) {
+      const LoopMeta &lm = loops[bend_loop[q]];
+      bend_info[q] = make_int4(lm.depth, lm.ph, lm.pend, meta[lm.ph].bslot);
+    }
+    chk(sd.bend_info = st->up(bend_info));
+  }
   chk(sd.srcent = st->up(srcent));
   chk(sd.work = st->up(work));
   chk(sd.lant_work = st->up(lant_work));
