@@ -74,6 +74,7 @@
  */
 #ifndef OMPDART_H
 #define OMPDART_H
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -150,6 +151,9 @@ typedef struct {
   uint64_t *call_to, *call_from;          /* [n_call_sites*n_words]            */
   uint64_t *call_entry_h, *call_entry_d;  /* [n_call_sites*n_words]            */
   uint64_t *call_exit_live;               /* [n_call_sites*n_words]            */
+  void *host_block;            /* library-internal: the host allocation that
+                                  holds a host result's arrays (shared by the
+                                  results of one batch arena); NULL in views  */
 } ompdart_result;
 
 typedef struct ompdart_plan ompdart_plan;
@@ -201,6 +205,11 @@ void ompdart_plan_destroy(ompdart_plan *plan);
 int ompdart_analyze(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdart_result **out);
 
 void ompdart_result_free(ompdart_result *res);
+
+/* Host results of at least 1 MiB live in page-locked memory that is kept
+   for reuse once freed (up to OMPDART_HOST_CACHE_MB, default 4096 MiB, of
+   cached blocks).  Releases every cached block; returns the bytes released. */
+size_t ompdart_host_cache_trim(void);
 
 /* Text of the calling thread's last error ("" if none). */
 const char *ompdart_last_error(void);

@@ -63,7 +63,7 @@ class Result(C.Structure):
                 ("sweeps", C.c_int32), ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64),
                 ("live_in", C.c_void_p), ("n_call_sites", C.c_int32), ("call_site_acc", C.c_void_p),
                 ("call_to", C.c_void_p), ("call_from", C.c_void_p), ("call_entry_h", C.c_void_p),
-                ("call_entry_d", C.c_void_p), ("call_exit_live", C.c_void_p)]
+                ("call_entry_d", C.c_void_p), ("call_exit_live", C.c_void_p), ("host_block", C.c_void_p)]
 
 
 class ServerOpts(C.Structure):
@@ -111,6 +111,7 @@ EXPORTS = {
     "ompdart_plan_destroy": (None, [C.c_void_p]),
     "ompdart_analyze": (C.c_int, [C.POINTER(Cfg), C.POINTER(Opts), C.POINTER(C.POINTER(Result))]),
     "ompdart_result_free": (None, [C.POINTER(Result)]),
+    "ompdart_host_cache_trim": (C.c_size_t, []),
     "ompdart_last_error": (C.c_char_p, []),
     "ompdart_batch_create": (C.c_int, [C.POINTER(Cfg), C.c_int32, C.POINTER(Opts), C.POINTER(C.c_void_p),
                                        C.c_void_p]),
@@ -192,15 +193,42 @@ def _opts(max_sweeps=0, keep_states=False, path=0, chunk_target=0, device=0, war
                 int(warps_per_cta), int(bool(tune)), int(bool(no_graph)))
 
 
-def _result_to_numpy(r: Result) -> dict:
+class _Owned:
+    """A library-owned host result, freed (ompdart_result_free) once the
+    last numpy view into its arrays is gone."""
+
+    __slots__ = ("_free", "_ptr")
+
+    def __init__(self, lib, ptr):
+        self._free, self._ptr = lib.ompdart_result_free, ptr
+
+    def __del__(self):
+        try:
+            self._free(self._ptr)
+        except Exception:  # interpreter shutdown
+            pass
+
+
+def _owned_result(lib, ptr) -> dict:
+    """Numpy views (no copy) of a host result that ``ptr`` owns."""
+    return _result_to_numpy(ptr.contents, _Owned(lib, ptr))
+
+
+def _result_to_numpy(r: Result, owner: "_Owned | None" = None) -> dict:
+    """Arrays of a host result: views that keep ``owner`` alive when given,
+    else copies (the caller frees the result)."""
     n, W = r.n_blocks, r.n_words
 
     def arr(ptr, count, dt, shape=None):
         if not ptr or count == 0:
             a = np.zeros(count, dtype=dt)
         else:
-            a = np.ctypeslib.as_array((C.c_char * (count * np.dtype(dt).itemsize)).from_address(ptr))
-            a = np.frombuffer(a, dtype=dt).copy()
+            buf = (C.c_char * (count * np.dtype(dt).itemsize)).from_address(ptr)
+            if owner is not None:
+                buf._owner = owner
+                a = np.frombuffer(buf, dtype=dt)
+            else:
+                a = np.frombuffer(buf, dtype=dt).copy()
         return a.reshape(shape) if shape else a
 
     out = {
@@ -231,10 +259,7 @@ def analyze(cfg, **opts) -> dict:
     o = _opts(**opts)
     res = C.POINTER(Result)()
     _check(lib.ompdart_analyze(C.byref(inp.c), C.byref(o), C.byref(res)))
-    try:
-        return _result_to_numpy(res.contents)
-    finally:
-        lib.ompdart_result_free(res)
+    return _owned_result(lib, res)
 
 
 def liveness_noalloc(n_blocks, n_vars, entry, succ_off, succ, acc_off, acc, exit_host_live, live_in,
@@ -270,10 +295,7 @@ class Plan:
     def fetch(self) -> dict:
         res = C.POINTER(Result)()
         _check(self._lib.ompdart_plan_fetch(self._h, C.byref(res)))
-        try:
-            return _result_to_numpy(res.contents)
-        finally:
-            self._lib.ompdart_result_free(res)
+        return _owned_result(self._lib, res)
 
     def profile(self, enable: bool = True):
         _check(self._lib.ompdart_plan_profile(self._h, int(bool(enable))))
@@ -347,10 +369,7 @@ class Batch:
     def fetch(self, i: int) -> dict:
         res = C.POINTER(Result)()
         _check(self._lib.ompdart_batch_fetch(self._h, int(i), C.byref(res)))
-        try:
-            return _result_to_numpy(res.contents)
-        finally:
-            self._lib.ompdart_result_free(res)
+        return _owned_result(self._lib, res)
 
     def info(self) -> dict:
         na, ns, nl = C.c_int32(), C.c_int32(), C.c_int32()
@@ -385,14 +404,8 @@ def analyze_batch(cfgs, **opts):
     outs = (C.POINTER(Result) * max(1, inp.n))()
     st = np.zeros(max(1, inp.n), dtype=np.int32)
     _check(lib.ompdart_analyze_batch(inp.arr, inp.n, C.byref(_opts(**opts)), outs, st.ctypes.data))
-    res = []
-    try:
-        for i in range(inp.n):
-            res.append(_result_to_numpy(outs[i].contents) if outs[i] else None)
-    finally:
-        for i in range(inp.n):
-            if outs[i]:
-                lib.ompdart_result_free(outs[i])
+    owners = [_Owned(lib, outs[i]) if outs[i] else None for i in range(inp.n)]
+    res = [_result_to_numpy(o._ptr.contents, o) if o is not None else None for o in owners]
     return res, st[: inp.n]
 
 
@@ -431,10 +444,7 @@ class Server:
                                              C.byref(res) if want_result else None, C.byref(st), C.byref(lat)))
         out = None
         if want_result and res:
-            try:
-                out = _result_to_numpy(res.contents)
-            finally:
-                self._lib.ompdart_result_free(res)
+            out = _owned_result(self._lib, res)
         return st.value, lat.value, out
 
     def drain(self, timeout_ms=-1):

@@ -328,61 +328,81 @@ void core_view(const PlanCore &P, const int32_t *h_status, ompdart_result *v) {
 
 int result_copy(const ompdart_result &v, bool device, cudaStream_t s, ompdart_result **out) {
   *out = nullptr;
-  ompdart_result *r = (ompdart_result *)calloc(1, sizeof(ompdart_result));
-  if (!r) return set_err(OMPDART_E_NOMEM, "host allocation failed");
+  const size_t NW = (size_t)v.n_blocks * v.n_words, SW = (size_t)v.n_call_sites * v.n_words;
+  // one host block: every array at a 64-byte aligned offset
+  struct Part {
+    void **dst;
+    const void *src;
+    size_t bytes;
+  };
+  ompdart_result r = v;
+  r.mem = OMPDART_MEM_HOST;
+  r.host_block = nullptr;
+  Part parts[] = {
+      {(void **)&r.h_in, v.h_in, NW * 8},
+      {(void **)&r.d_in, v.d_in, NW * 8},
+      {(void **)&r.h_out, v.h_out, v.h_out ? NW * 8 : 0},
+      {(void **)&r.d_out, v.d_out, v.d_out ? NW * 8 : 0},
+      {(void **)&r.live_in, v.live_in, v.live_in ? NW * 8 : 0},
+      {(void **)&r.acc_flag, v.acc_flag, (size_t)v.n_acc},
+      {(void **)&r.edge_xfers, v.edge_xfers, sizeof(ompdart_edge_xfer) * (size_t)v.n_edge_xfers},
+      {(void **)&r.exit_blocks, v.exit_blocks, sizeof(int32_t) * (size_t)v.n_exits},
+      {(void **)&r.from_exit, v.from_exit, 8 * (size_t)v.n_exits * v.n_words},
+      {(void **)&r.call_site_acc, v.call_site_acc, sizeof(int32_t) * (size_t)v.n_call_sites},
+      {(void **)&r.call_to, v.call_to, 8 * SW},
+      {(void **)&r.call_from, v.call_from, 8 * SW},
+      {(void **)&r.call_entry_h, v.call_entry_h, 8 * SW},
+      {(void **)&r.call_entry_d, v.call_entry_d, 8 * SW},
+      {(void **)&r.call_exit_live, v.call_exit_live, 8 * SW},
+  };
+  size_t total = 0;
+  for (const Part &p : parts) total += (p.bytes + 63) & ~size_t(63);
+  HostBlock *blk = host_block_new(total + 64);
+  if (!blk) return set_err(OMPDART_E_NOMEM, "host allocation failed");
+  char *base = (char *)host_block_ptr(blk);
+  size_t off = 0;
+  cudaError_t ce = cudaSuccess;
+  for (const Part &p : parts) {
+    // optional arrays stay NULL when absent; the others point into the
+    // block even when empty
+    const bool optional = p.dst == (void **)&r.h_out || p.dst == (void **)&r.d_out || p.dst == (void **)&r.live_in;
+    if (optional && !p.src) {
+      *p.dst = nullptr;
+      continue;
+    }
+    *p.dst = base + off;
+    if (p.bytes && p.src) {
+      if (!device)
+        memcpy(base + off, p.src, p.bytes);
+      else if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(base + off, p.src, p.bytes, cudaMemcpyDeviceToHost, s);
+    }
+    off += (p.bytes + 63) & ~size_t(63);
+  }
+  if (device && ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) {
+    host_block_release(blk);
+    return cuda_err(ce, "copy of results");
+  }
+  r.d2h_bytes = device ? (long long)(2 + (v.h_out ? 2 : 0) + (v.live_in ? 1 : 0)) * NW * 8 + v.n_acc +
+                             (long long)sizeof(ompdart_edge_xfer) * v.n_edge_xfers + 4ll * v.n_exits +
+                             8ll * v.n_exits * v.n_words + 4ll * ST_COUNT + 4ll * v.n_call_sites + 40ll * SW
+                       : 0;
+  ompdart_result *res = result_in_block(r, blk);
+  host_block_release(blk);  // the result holds its own reference
+  if (!res) return set_err(OMPDART_E_NOMEM, "host allocation failed");
+  *out = res;
+  return OMPDART_OK;
+}
+
+ompdart_result *result_in_block(const ompdart_result &v, HostBlock *block) {
+  ompdart_result *r = (ompdart_result *)malloc(sizeof(ompdart_result));
+  if (!r) return nullptr;
   *r = v;
   r->mem = OMPDART_MEM_HOST;
-  const size_t NW = (size_t)v.n_blocks * v.n_words;
-  r->h_in = (uint64_t *)malloc(NW * 8 + 8);
-  r->d_in = (uint64_t *)malloc(NW * 8 + 8);
-  r->h_out = v.h_out ? (uint64_t *)malloc(NW * 8 + 8) : nullptr;
-  r->d_out = v.d_out ? (uint64_t *)malloc(NW * 8 + 8) : nullptr;
-  r->acc_flag = (uint8_t *)malloc((size_t)v.n_acc + 1);
-  r->edge_xfers = (ompdart_edge_xfer *)malloc(sizeof(ompdart_edge_xfer) * ((size_t)v.n_edge_xfers + 1));
-  r->exit_blocks = (int32_t *)malloc(sizeof(int32_t) * ((size_t)v.n_exits + 1));
-  r->from_exit = (uint64_t *)malloc(8 * ((size_t)v.n_exits * v.n_words + 1));
-  r->live_in = v.live_in ? (uint64_t *)malloc(NW * 8 + 8) : nullptr;
-  const size_t SW = (size_t)v.n_call_sites * v.n_words;
-  r->call_site_acc = (int32_t *)malloc(sizeof(int32_t) * ((size_t)v.n_call_sites + 1));
-  uint64_t **crows[5] = {&r->call_to, &r->call_from, &r->call_entry_h, &r->call_entry_d, &r->call_exit_live};
-  const uint64_t *csrc[5] = {v.call_to, v.call_from, v.call_entry_h, v.call_entry_d, v.call_exit_live};
-  bool rows_ok = r->call_site_acc != nullptr;
-  for (int k = 0; k < 5; ++k) {
-    *crows[k] = (uint64_t *)malloc(8 * (SW + 1));
-    rows_ok = rows_ok && *crows[k];
-  }
-  bool ok = r->h_in && r->d_in && (!v.h_out || r->h_out) && (!v.d_out || r->d_out) && r->acc_flag &&
-            r->edge_xfers && r->exit_blocks && r->from_exit && (!v.live_in || r->live_in) && rows_ok;
-  cudaError_t ce = cudaSuccess;
-  auto cp = [&](void *dst, const void *src, size_t n) {
-    if (!ok || !n) return;
-    if (!device)
-      memcpy(dst, src, n);
-    else if (ce == cudaSuccess)
-      ce = cudaMemcpyAsync(dst, src, n, cudaMemcpyDeviceToHost, s);
-  };
-  cp(r->h_in, v.h_in, NW * 8);
-  cp(r->d_in, v.d_in, NW * 8);
-  if (v.h_out) cp(r->h_out, v.h_out, NW * 8);
-  if (v.d_out) cp(r->d_out, v.d_out, NW * 8);
-  cp(r->acc_flag, v.acc_flag, (size_t)v.n_acc);
-  cp(r->edge_xfers, v.edge_xfers, sizeof(ompdart_edge_xfer) * (size_t)v.n_edge_xfers);
-  cp(r->exit_blocks, v.exit_blocks, sizeof(int32_t) * (size_t)v.n_exits);
-  cp(r->from_exit, v.from_exit, 8 * (size_t)v.n_exits * v.n_words);
-  if (v.live_in) cp(r->live_in, v.live_in, NW * 8);
-  cp(r->call_site_acc, v.call_site_acc, sizeof(int32_t) * (size_t)v.n_call_sites);
-  for (int k = 0; k < 5; ++k) cp(*crows[k], csrc[k], 8 * SW);
-  if (device && ok && ce == cudaSuccess) ce = cudaStreamSynchronize(s);
-  r->d2h_bytes = device ? (long long)(2 + (v.h_out ? 2 : 0) + (v.live_in ? 1 : 0)) * NW * 8 + v.n_acc +
-                              (long long)sizeof(ompdart_edge_xfer) * v.n_edge_xfers + 4ll * v.n_exits +
-                              8ll * v.n_exits * v.n_words + 4ll * ST_COUNT + 4ll * v.n_call_sites + 40ll * SW
-                        : 0;
-  if (!ok || ce != cudaSuccess) {
-    ompdart_result_free(r);
-    return ok ? cuda_err(ce, "copy of results") : set_err(OMPDART_E_NOMEM, "host allocation failed");
-  }
-  *out = r;
-  return OMPDART_OK;
+  r->host_block = block;
+  host_block_ref(block);
+  return r;
 }
 
 int set_error(int code, const std::string &msg) { return set_err(code, msg); }
@@ -422,7 +442,9 @@ int ompdart_plan_create(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdar
   ompdart_plan *P = new (std::nothrow) ompdart_plan();
   if (!P) return set_err(OMPDART_E_NOMEM, "host allocation failed");
   std::string err;
+  TraceScope trace("ingest", cfg ? cfg->n_blocks : 0);
   int rc = ingest(cfg, &P->core.g, &err);
+  trace.next("plan rows");
   if (rc) {
     delete P;
     return set_err(rc, err);
@@ -524,10 +546,7 @@ void ompdart_plan_destroy(ompdart_plan *P) { delete P; }
 
 void ompdart_result_free(ompdart_result *r) {
   if (!r) return;
-  free(r->h_in); free(r->d_in); free(r->h_out); free(r->d_out); free(r->acc_flag);
-  free(r->edge_xfers); free(r->exit_blocks); free(r->from_exit); free(r->live_in);
-  free(r->call_site_acc); free(r->call_to); free(r->call_from); free(r->call_entry_h); free(r->call_entry_d);
-  free(r->call_exit_live);
+  host_block_release(static_cast<HostBlock *>(r->host_block));
   free(r);
 }
 
@@ -543,11 +562,15 @@ int ompdart_analyze(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdart_re
   if (!out) return set_err(OMPDART_E_INVALID, "result output pointer is NULL");
   *out = nullptr;
   ompdart_plan *P = nullptr;
+  TraceScope trace("plan create", cfg ? cfg->n_blocks : 0);
   int rc = ompdart_plan_create(cfg, opts, &P);
   if (rc) return rc;
+  trace.next("plan run+sync");
   rc = ompdart_plan_run(P, nullptr);
   if (!rc) rc = ompdart_plan_sync(P);
+  trace.next("plan fetch");
   if (!rc) rc = ompdart_plan_fetch(P, out);
+  trace.next("plan destroy");
   ompdart_plan_destroy(P);
   return rc;
 }

@@ -383,20 +383,50 @@ int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts 
       solo_ids.push_back(i);
   }
   std::string err;
-  for (auto &kv : by_w) {
-    std::unique_ptr<Arena> a(new (std::nothrow) Arena());
-    if (!a) return set_error(OMPDART_E_NOMEM, "host allocation failed");
-    a->chunk_target = o.chunk_target;
-    a->wpc = o.warps_per_cta;
-    if (o.tune) tune_arena(a.get(), kv.second, ing, cfgs, o, B->stream);
-    int rc = build_arena(a.get(), kv.second, ing, cfgs, o, &err);
-    if (rc) return set_error(rc, err);
+  // arenas: tuned one after another (trials are timed on the device), then
+  // laid out and uploaded in parallel, one host thread per arena
+  std::vector<std::pair<int, std::vector<int32_t>>> groups(by_w.begin(), by_w.end());
+  const int n_ar = (int)groups.size();
+  std::vector<std::unique_ptr<Arena>> built(n_ar);
+  for (int g = 0; g < n_ar; ++g) {
+    built[g].reset(new (std::nothrow) Arena());
+    if (!built[g]) return set_error(OMPDART_E_NOMEM, "host allocation failed");
+    built[g]->chunk_target = o.chunk_target;
+    built[g]->wpc = o.warps_per_cta;
+    if (o.tune) tune_arena(built[g].get(), groups[g].second, ing, cfgs, o, B->stream);
+  }
+  {
+    std::vector<int> rcs(n_ar, OMPDART_OK);
+    std::vector<std::string> errs(n_ar);
+    std::atomic<int> next{0};
+    auto work = [&](bool main_thread) {
+      if (!main_thread && cudaSetDevice(o.device) != cudaSuccess) {
+        for (int g = next++; g < n_ar; g = next++) {
+          rcs[g] = OMPDART_E_CUDA;
+          errs[g] = "CUDA setup in a build thread failed";
+        }
+        return;
+      }
+      for (int g = next++; g < n_ar; g = next++)
+        rcs[g] = build_arena(built[g].get(), groups[g].second, ing, cfgs, o, &errs[g]);
+    };
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int T = std::min(n_ar, (int)std::min(hw, 16u));
+    std::vector<std::thread> pool;
+    for (int t = 1; t < T; ++t) pool.emplace_back(work, false);
+    work(true);
+    for (auto &t : pool) t.join();
+    for (int g = 0; g < n_ar; ++g)
+      if (rcs[g]) return set_error(rcs[g], errs[g]);
+  }
+  for (int g = 0; g < n_ar; ++g) {
+    std::unique_ptr<Arena> a = std::move(built[g]);
     a->h_status = B->host_ints(ST_COUNT);
     a->h_err = B->host_ints(a->members.size());
     if (!a->h_status || !a->h_err) return set_error(OMPDART_E_NOMEM, "host allocation failed");
     const int idx = (int)B->arenas.size();
     for (size_t k = 0; k < a->members.size(); ++k) B->where[a->members[k]] = Where{1, idx, (int)k};
-    for (int m : kv.second) ing[m] = Ingest();  // the arena holds the concatenation
+    for (int m : groups[g].second) ing[m] = Ingest();  // the arena holds the concatenation
     B->arenas.push_back(std::move(a));
   }
   for (int i : solo_ids) {
@@ -570,10 +600,14 @@ int ompdart_analyze_batch(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts
   int rc = ompdart_batch_create(cfgs, n, opts, &B, status);
   if (rc) return rc;
   std::unique_ptr<ompdart_batch> hold(B);
+  TraceScope trace("batch run+sync", n);
   rc = ompdart_batch_run(B, nullptr);
   if (!rc) rc = ompdart_batch_sync(B, status);
   if (rc) return rc;
-  return batch_fetch_all(B, outs);
+  trace.next("batch fetch", n);
+  rc = batch_fetch_all(B, outs);
+  trace.next("batch destroy", n);
+  return rc;
 }
 
 }  // extern "C"
@@ -592,24 +626,22 @@ long long batch_device_bytes(const ompdart_batch *B) {
 int batch_fetch_all(ompdart_batch *B, ompdart_result **outs) {
   int rc = OMPDART_OK;
   for (int i = 0; i < B->n; ++i) outs[i] = nullptr;
-  // bulk copies: every arena's arrays in one piece, then split per CFG
+  // one bulk copy per arena into one host block; each CFG's result is a
+  // view into it (the block lives until the last of them is freed)
   for (auto &ap : B->arenas) {
     Arena &a = *ap;
     rc = arena_records(B, &a);
     if (rc) return rc;
     ompdart_result whole;
     core_view(a.core, a.h_status, &whole);
+    if (whole.n_call_sites != a.site_off.back())
+      return set_error(OMPDART_E_INVALID, "internal: arena call sites out of step");
     whole.exit_blocks = a.exit_local;
+    whole.call_site_acc = a.site_local;  // access index within each CFG
     ompdart_result *host = nullptr;
     rc = result_copy(whole, true, B->last_stream, &host);
     if (rc) return rc;
-    std::vector<int32_t> host_sites(a.site_off.back() + 1);
-    if (a.site_off.back() &&
-        cudaMemcpy(host_sites.data(), a.site_local, sizeof(int32_t) * a.site_off.back(), cudaMemcpyDeviceToHost) !=
-            cudaSuccess) {
-      ompdart_result_free(host);
-      return set_error(OMPDART_E_CUDA, "copy of call sites failed");
-    }
+    HostBlock *blk = static_cast<HostBlock *>(host->host_block);
     const size_t W = a.W;
     const double blocks = std::max(1, a.blk_off.back());
     for (size_t k = 0; k < a.members.size(); ++k) {
@@ -619,7 +651,6 @@ int batch_fetch_all(ompdart_batch *B, ompdart_result **outs) {
       arena_view(a, (int)k, &v);
       // this CFG's share of the arena's host<->device copies
       const double share = (a.blk_off[k + 1] - a.blk_off[k]) / blocks;
-      const long long h2d = (long long)(share * v.h2d_bytes), d2h = (long long)(share * host->d2h_bytes);
       const size_t b0 = (size_t)a.blk_off[k] * W;
       v.h_in = host->h_in + b0;
       v.d_in = host->d_in + b0;
@@ -630,19 +661,20 @@ int batch_fetch_all(ompdart_batch *B, ompdart_result **outs) {
       v.edge_xfers = host->edge_xfers + a.rec_off[k];
       v.exit_blocks = host->exit_blocks + a.x_off[k];
       v.from_exit = host->from_exit + (size_t)a.x_off[k] * W;
-      v.call_site_acc = host_sites.data() + a.site_off[k];
-      if (v.n_call_sites) {
-        const size_t o = (size_t)a.site_off[k] * W;
-        v.call_to = host->call_to + o;
-        v.call_from = host->call_from + o;
-        v.call_entry_h = host->call_entry_h + o;
-        v.call_entry_d = host->call_entry_d + o;
-        v.call_exit_live = host->call_exit_live + o;
+      v.call_site_acc = host->call_site_acc + a.site_off[k];
+      const size_t o = (size_t)a.site_off[k] * W;
+      v.call_to = host->call_to + o;
+      v.call_from = host->call_from + o;
+      v.call_entry_h = host->call_entry_h + o;
+      v.call_entry_d = host->call_entry_d + o;
+      v.call_exit_live = host->call_exit_live + o;
+      v.h2d_bytes = (long long)(share * v.h2d_bytes);
+      v.d2h_bytes = (long long)(share * host->d2h_bytes);
+      outs[i] = result_in_block(v, blk);
+      if (!outs[i]) {
+        rc = set_error(OMPDART_E_NOMEM, "host allocation failed");
+        break;
       }
-      rc = result_copy(v, false, nullptr, &outs[i]);
-      if (rc) break;
-      outs[i]->h2d_bytes = h2d;
-      outs[i]->d2h_bytes = d2h;
     }
     ompdart_result_free(host);
     if (rc) return rc;

@@ -14,6 +14,8 @@
 
 namespace ompdart {
 
+struct HostBlock;
+
 // ---- host-side tracing: with OMPDART_TRACE=1 in the environment, phases
 // of plan and batch construction print their wall time to stderr
 bool trace_on();
@@ -145,8 +147,18 @@ int core_finish(PlanCore *c, cudaStream_t s, int32_t *h_status, bool *rerun);
 // Device view of a core's results (h_status: the status words of its last run).
 void core_view(const PlanCore &c, const int32_t *h_status, ompdart_result *v);
 // Copy the arrays a view points at (device memory if `device`, else host)
-// into a new host result (ompdart_result_free).
+// into a new host result (ompdart_result_free) whose arrays share one host block.
 int result_copy(const ompdart_result &v, bool device, cudaStream_t s, ompdart_result **out);
+// A new host result whose arrays are v's, all inside `block` (one more
+// reference to it); NULL if the host allocation fails.
+ompdart_result *result_in_block(const ompdart_result &v, HostBlock *block);
+
+// ---- hostmem.cpp: reference-counted host blocks for host results
+// (page-locked and cached once released when large)
+HostBlock *host_block_new(size_t bytes);  // one reference; NULL on failure
+void *host_block_ptr(HostBlock *b);
+void host_block_ref(HostBlock *b);
+void host_block_release(HostBlock *b);  // frees or caches at the last reference
 
 // ---- batch.cu helpers for the serving loop
 // host copies of every CFG's results after ompdart_batch_sync (outs[n];
