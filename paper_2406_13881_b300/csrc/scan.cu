@@ -39,6 +39,7 @@ namespace {
 
 constexpr int CARRY = -2;      // slot id: the chunk's incoming carry
 constexpr int PREV = -3;       // slot id: the value of the position walked just before
+constexpr int BACK = -4;       // slot id (forward in-edges): a back edge, closed at the loop's end
 #ifndef OMPDART_SH_WORDS
 #define OMPDART_SH_WORDS 256
 #endif
@@ -61,17 +62,17 @@ struct PosMeta {  // one per position, 80 B
   int32_t fin_beg, out_beg, acc_beg, srcent_beg, bend_beg;  // acc_beg: in caller order
   int16_t nfin, nout, nacc, nsrcent, nbend, fslot, bslot, pad0;
   int32_t head_loop;      // loop whose header is this position, else -1
-  uint32_t latch_levels;  // bit d: back edge to the header of the level-d loop
+  int32_t pad4;
   int32_t exit_idx;       // index in exit_blocks, else -1
   int32_t pacc_beg;       // first access of the block in position order
   int32_t flags;          // PM_RECORDS: the block's summary records are given
   int32_t pad3;
-  // a header position: its loop's body end, header slot, depth and latch
-  // slots (kept here so the walks need no loop record at a header)
+  // a header position: its loop's body end, header slot and depth (kept
+  // here so the walks need no loop record at a header)
   int32_t head_pend;
   int16_t head_hslot, head_depth;
-  int32_t head_lat_beg;
-  int16_t head_lat_cnt, pad5;
+  int32_t pad6;
+  int16_t pad7, pad5;
 };
 // a block with call pseudo-accesses: its entries in the position-ordered
 // access stream are already summary records (folded on the host with the
@@ -83,9 +84,11 @@ static_assert(sizeof(PosMeta) == 80, "PosMeta layout");
 struct LoopMeta {
   int32_t ph, pend;   // body = positions [ph, pend)
   int16_t hslot, depth;
-  int32_t lat_beg;    // latch slots to clear on a fresh entry
+  int32_t lat_beg;    // latch slots (forward): their values close the loop
   int32_t lat_cnt;
   int32_t cfg;        // the CFG of a batch it belongs to
+  int32_t xs_beg;     // forward slots read after the body ends (exit sources)
+  int32_t xs_cnt;
 };
 
 struct ChunkMeta {
@@ -118,6 +121,7 @@ struct ScanDev {
   long long n_acc_p;      // entries of the position-ordered access stream
   int sh_slots;           // slots per plane held in shared memory
   const int32_t *lat_slot;
+  const int32_t *exit_slot;  // per loop (xs_beg, xs_cnt): forward slots of its exit sources
   const int4 *bend_info;  // per loop ending at a position: {depth, header position, body end, header's backward slot}
   const int32_t *srcent;
   uint64_t *spill;     // per warp spill area
@@ -132,6 +136,12 @@ struct ScanDev {
   uint64_t *pair_g2, *pair_p2;  // [N][W] D_out stale (kept states only), else null
   uint64_t *src_g, *src_p;      // [K][W] out value at each loop-entry edge's source
   const int32_t *pos_chunk;     // [M] chunk of each position
+  // forward walks take each loop body once, relative to the header's value;
+  // at the loop's end the header's fixed point (relative to the enclosing
+  // level) goes to hdr_*, and the resolve composes up the loop tree
+  uint64_t *hdr_g, *hdr_p;      // [L][W] header value, plane at 0 / at top of the enclosing level
+  const int32_t *pos_loop;      // [M] innermost loop holding each position, or -1
+  const int32_t *loop_up;       // [L] enclosing loop, or -1
   const int32_t *src_pos;       // [K] position of each loop-entry edge's source
   const int2 *emit_rng;         // [n_emit] position ranges of the emission items (within one chunk)
   int n_emit;
@@ -246,7 +256,8 @@ namespace {
 bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta> &meta, std::vector<LoopMeta> &loops,
                 std::vector<ChunkMeta> &chunks, std::vector<CarrySrc> &csrc, std::vector<int32_t> &fin_slot,
                 std::vector<int32_t> &out_slot, std::vector<int32_t> &out_pos, std::vector<int32_t> &lat_slot,
-                std::vector<int32_t> &bend_loop, std::vector<int32_t> &srcent, std::string *err) {
+                std::vector<int32_t> &bend_loop, std::vector<int32_t> &srcent, std::vector<int32_t> &exit_slot,
+                std::string *err) {
   Ingest &gm = const_cast<Ingest &>(g);
   make_chunks(&gm, target);
   const int M = g.M, C = (int)g.chunk_off.size() - 1, L = g.L;
@@ -391,19 +402,13 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
     m.bend_beg = (int32_t)bend_loop.size();
     for (int l : ends[i]) bend_loop.push_back(l);
     m.nbend = (int16_t)(bend_loop.size() - m.bend_beg);
-    m.latch_levels = 0;
-    // find chunk of i for the slot ids of in-edges
   }
   for (int c = 0; c < C; ++c) {
     const int s = chunks[c].s, e = chunks[c].e;
     for (int i = s; i < e; ++i) {
       for (int k = g.fin_off[i]; k < g.fin_off[i + 1]; ++k) {
         const int pp = g.pos[g.fin_src[k]];
-        fin_slot[k] = pp < s ? CARRY : (pp == i - 1 && !fwd_target[i]) ? PREV : fslot[pp];
-        if (pp >= i) {  // back edge: the source is a latch of loop head_loop_of_pos[i]
-          const int l = head_loop_of_pos[i];
-          meta[pp].latch_levels |= 1u << (g.loop_depth[l] - 1);
-        }
+        fin_slot[k] = pp < s ? CARRY : pp >= i ? BACK : (pp == i - 1 && !fwd_target[i]) ? PREV : fslot[pp];
       }
       for (int k = g.out_off[i]; k < g.out_off[i + 1]; ++k) {
         const int pt = g.pos[g.out_dst[k]];
@@ -436,12 +441,24 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
         lat_slot.push_back(fslot[pp]);
     }
     lm.lat_cnt = (int32_t)lat_slot.size() - lm.lat_beg;
+    // exit sources: body positions whose value a position after the body
+    // (or the next chunk's carry) reads from their slot
+    const int ce = chunks[std::upper_bound(g.chunk_off.begin(), g.chunk_off.end(), lm.ph) - g.chunk_off.begin() - 1].e;
+    lm.xs_beg = (int32_t)exit_slot.size();
+    for (int q = lm.ph; q < lm.pend; ++q) {
+      if (fslot[q] < 0) continue;
+      bool read_after = false;
+      for (int k = g.out_off[q]; k < g.out_off[q + 1] && !read_after; ++k) {
+        const int pt = g.pos[g.out_dst[k]];
+        read_after = pt >= lm.pend && (pt >= ce || !(pt == q + 1 && !fwd_target[pt]));
+      }
+      if (read_after) exit_slot.push_back(fslot[q]);
+    }
+    lm.xs_cnt = (int32_t)exit_slot.size() - lm.xs_beg;
     PosMeta &hm = meta[lm.ph];
     hm.head_pend = lm.pend;
     hm.head_hslot = lm.hslot;
     hm.head_depth = lm.depth;
-    hm.head_lat_beg = lm.lat_beg;
-    hm.head_lat_cnt = (int16_t)lm.lat_cnt;
   }
   st->C = C;
   st->fslots = std::max(max_f, 1);
@@ -677,6 +694,52 @@ __device__ __forceinline__ void push_edge_records(const ScanDev &sd, int stream,
 // --------------------------------------------------------------------------------------
 // forward chain (Hp, D, H): positions ascending
 // --------------------------------------------------------------------------------------
+// v relative to a header value h (v = v0 | (h & v1)), h relative to the
+// enclosing level: v relative to the enclosing level
+template <class T>  // uint64_t or the members of ulonglong2
+__device__ __forceinline__ void compose_pair(T &v0, T &v1, uint64_t h0, uint64_t h1) {
+  const T a = v0 | (h0 & v1), b = v0 | (h1 & v1);
+  v0 = a;
+  v1 = b;
+}
+
+// End of loop l's body in a forward walk (stale sets grow along paths, so
+// the header's value is the least fixed point of h = e | L(h), with e the
+// meet of its entry edges and L the latches' values; the latches are
+// affine in h, L(h) = A | (h & B), hence h = e | A: Kam-Ullman rapidity
+// in closed form).  The body was walked relative to h; the header's value
+// is stored for the resolve, and the values still to be read after the
+// body (exit sources, the previous position) are re-expressed in the
+// enclosing level.
+__device__ __forceinline__ void close_loop(const ScanDev &sd, const Slots<2> &sl, const Lane &L, int W, int l,
+                                           int hs, uint64_t (&pv)[2][2]) {
+  const LoopMeta lm = sd.loops[l];
+  uint64_t a0 = 0, a1 = 0;
+  for (int q = 0; q < lm.lat_cnt; ++q) {
+    const ulonglong2 v = *sl.at(sd.lat_slot[lm.lat_beg + q], 0, L.lane);
+    a0 |= v.x;
+    a1 |= v.y;
+  }
+  const ulonglong2 e0 = *sl.at(hs, 0, L.lane), e1 = *sl.at(hs, 1, L.lane);
+  const uint64_t h00 = e0.x | a0, h01 = e0.y | a1, h10 = e1.x | a0, h11 = e1.y | a1;
+  st_word(sd.hdr_g, l, W, L.w0, h00);
+  st_word(sd.hdr_g, l, W, L.w0 + 1, h01);
+  st_word(sd.hdr_p, l, W, L.w0, h10);
+  st_word(sd.hdr_p, l, W, L.w0 + 1, h11);
+  for (int q = 0; q < lm.xs_cnt; ++q) {
+    const int x = sd.exit_slot[lm.xs_beg + q];
+    ulonglong2 *g = sl.at(x, 0, L.lane), *pp = sl.at(x, 1, L.lane);
+    ulonglong2 v0 = *g, v1 = *pp;
+    compose_pair(v0.x, v1.x, h00, h10);
+    compose_pair(v0.y, v1.y, h01, h11);
+    *g = v0;
+    *pp = v1;
+  }
+  compose_pair(pv[0][0], pv[1][0], h00, h10);
+  compose_pair(pv[0][1], pv[1][1], h01, h11);
+  __syncwarp();
+}
+
 // One warp walks chunk c for the 64-word group wg.
 template <int PH>
 __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, const WarpMem &wm, uint64_t *spill,
@@ -702,11 +765,9 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
   cin[0][0] = cin[0][1] = 0;
   cin[1][0] = L.top0;
   cin[1][1] = L.top1;
-  // open loops, innermost last: header position, body end, header slot
-  int st_ph[MAX_DEPTH + 1], st_pend[MAX_DEPTH + 1], st_hs[MAX_DEPTH + 1];
+  // open loops, innermost last: loop, body end, header slot
+  int st_l[MAX_DEPTH + 1], st_pend[MAX_DEPTH + 1], st_hs[MAX_DEPTH + 1];
   int depth = 0;
-  uint32_t dirty = 0;
-  int reruns = 0;
   uint64_t z[NP][2], zo[NP][2], pv[NP][2] = {};
   int top_pend = -1;  // end of the innermost open loop (warp-uniform)
   constexpr int TBW = 2 * NP * 64;  // words of one mask table
@@ -717,12 +778,10 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
   uint64_t din[2] = {0, 0}, lv[2] = {0, 0};
   uint64_t pdin[2] = {0, 0}, plv[2] = {0, 0};
   int ppos = -1;  // position whose dense rows are prefetched in pdin/plv
-  int hwm = cm.s - 1;  // highest position walked so far
-  int i = cm.s;
-  while (i < cm.e) {
+  for (int i = cm.s; i < cm.e; ++i) {
     if (i < wr.ws || i >= wr.we) load_window<true>(w, wr, sd, i, cm.s, cm.e, L.lane);
     const PosMeta m = w.meta[i - wr.mbase];
-    if (prep_pos != i) {  // masks of this position not built yet (start, window edge, loop jump)
+    if (prep_pos != i) {  // masks of this position not built yet (start, window edge)
       if (prep_pos >= 0) {
         drop_masks<NP>(wm.tbl + pbuf * TBW, L.lane);
         __syncwarp();
@@ -746,26 +805,12 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
         ppos = i + 1;
       }
     }
-    if (m.head_loop >= 0) {
-      if (m.head_depth > depth) {  // entering the loop from outside
-        st_ph[depth] = i;
-        st_pend[depth] = m.head_pend;
-        st_hs[depth] = m.head_hslot;
-        dirty &= ~(1u << depth);
-        ++depth;
-        top_pend = m.head_pend;
-        // first visit in this walk: the back edges carry nothing yet.  A
-        // re-entry (an enclosing body walked again) keeps the latch values
-        // of the previous visit: they are below the new fixed point and the
-        // header = entry | old latches is then exact in one walk.
-        if (i > hwm) {
-          for (int q = 0; q < m.head_lat_cnt; ++q) {
-            const int s = sd.lat_slot[m.head_lat_beg + q];
-            for (int pl = 0; pl < NP; ++pl) *sl.at(s, pl, L.lane) = make_ulonglong2(0ull, 0ull);
-          }
-          __syncwarp();
-        }
-      }
+    if (m.head_loop >= 0) {  // a loop opens: its body is walked once
+      st_l[depth] = m.head_loop;
+      st_pend[depth] = m.head_pend;
+      st_hs[depth] = m.head_hslot;
+      ++depth;
+      top_pend = m.head_pend;
     }
     // ---- value entering the block
 #pragma unroll
@@ -777,8 +822,8 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
     for (int q = 0; q < m.nfin; ++q) {
       const int2 fe = win_edge(w, wr, sd.fin_pk, m.fin_beg + q);
       const int slot = fe.x;
-      if (slot == CARRY) continue;  // already in z via cin
-      if (slot == PREV) {           // the position walked just before
+      if (slot == CARRY || slot == BACK) continue;  // in z via cin / closed at the loop's end
+      if (slot == PREV) {                           // the position walked just before
 #pragma unroll
         for (int pl = 0; pl < NP; ++pl) { z[pl][0] |= pv[pl][0]; z[pl][1] |= pv[pl][1]; }
         continue;
@@ -792,12 +837,15 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
         z[pl][1] |= v.y & m1;
       }
     }
-    // a header remembers the meet of its in-edges (before the node's own
-    // mask): a latch that adds to it makes the loop body run again
+    // a header keeps the meet of its entry edges (enclosing level) for the
+    // loop's end; the body is walked relative to the header's value
     if (m.head_loop >= 0) {
       const int hs = m.head_hslot;
 #pragma unroll
       for (int pl = 0; pl < NP; ++pl) *sl.at(hs, pl, L.lane) = make_ulonglong2(z[pl][0], z[pl][1]);
+      z[0][0] = z[0][1] = 0;
+      z[1][0] = L.top0;
+      z[1][1] = L.top1;
     }
     if (PH == K_H) {  // live and stale on the device -> resolved toward the host
       const uint64_t b0 = ~(lv[0] & ~din[0]), b1 = ~(lv[1] & ~din[1]);
@@ -815,23 +863,6 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
       prep_pos = i + 1;
     } else {
       prep_pos = -1;
-    }
-    // ---- a latch whose value adds to an open loop's header marks it dirty
-    if (m.latch_levels) {
-      uint32_t lvmask = m.latch_levels;
-      while (lvmask) {
-        const int lvl = __ffs(lvmask) - 1;
-        lvmask &= lvmask - 1;
-        if (lvl >= depth) continue;
-        const int hs = st_hs[lvl];
-        bool grow = false;
-#pragma unroll
-        for (int pl = 0; pl < NP; ++pl) {
-          const ulonglong2 h = *sl.at(hs, pl, L.lane);
-          grow |= ((zo[pl][0] & ~h.x) | (zo[pl][1] & ~h.y)) != 0;
-        }
-        if (__any_sync(0xffffffffu, grow)) dirty |= 1u << lvl;
-      }
     }
     if (m.fslot >= 0) {
 #pragma unroll
@@ -874,32 +905,13 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
       }
     }
     __syncwarp();
-    // ---- close loops ending here; walk a body again if its header grew
-    bool jumped = false;
+    // ---- close the loops ending here
     while (depth > 0 && top_pend - 1 == i) {
-      if (dirty & (1u << (depth - 1))) {
-        dirty &= ~(1u << (depth - 1));
-        i = st_ph[depth - 1];
-        jumped = true;
-        break;
-      }
       --depth;
+      close_loop(sd, sl, L, W, st_l[depth], st_hs[depth], pv);
       top_pend = depth > 0 ? st_pend[depth - 1] : -1;
     }
-    hwm = max(hwm, i);
-    if (jumped) {
-      if (++reruns > rerun_cap(cm.e - cm.s)) {
-        if (L.lane == 0) {
-          atomicExch(&p.status[ST_ERROR], ERR_NOCONVERGE);
-          if (sd.cfg_err) atomicExch(&sd.cfg_err[cm.cfg], 1);
-        }
-        break;
-      }
-    } else {
-      ++i;
-    }
   }
-  if (L.lane == 0 && reruns) atomicAdd(&p.status[ST_SWEEPS], reruns);
   // ---- what leaves the chunk: its map of the carry into the next chunk
   uint64_t co[NP][2];
 #pragma unroll
@@ -1250,9 +1262,11 @@ __global__ void __launch_bounds__(256) k_local_summary_pos(ScanDev sd) {
 enum ResolveKind { RV_LIVE = 0, RV_VALID = 1 };  // liveness as is; stale sets to valid sets
 
 // out[b] = G[b] | (carry[chunk] & P[b]), converted for RV_VALID to ~x & top
-// (the CFG's valid-variable mask).  A thread takes two consecutive words
-// of a row (16-byte accesses when W is even); the grid strides over
-// (position, word pair).
+// (the CFG's valid-variable mask).  A forward (RV_VALID) pair is relative
+// to the header value of the innermost loop holding the position: it is
+// first composed with the header values up the loop tree.  A thread takes
+// two consecutive words of a row (16-byte accesses when W is even); the
+// grid strides over (position, word pair).
 template <int KIND>
 __global__ void __launch_bounds__(256) k_resolve(DevPlan p, ScanDev sd, const uint64_t *G, const uint64_t *P,
                                                  uint64_t *out) {
@@ -1265,15 +1279,26 @@ __global__ void __launch_bounds__(256) k_resolve(DevPlan p, ScanDev sd, const ui
     const size_t o = (size_t)b * W + w, oc = (size_t)c * W + w;
     const uint64_t *tp = p.top + (size_t)sd.chunks[c].cfg * W + w;
     if ((W & 1) == 0) {
-      const ulonglong2 g = *reinterpret_cast<const ulonglong2 *>(G + o);
-      const ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(P + o);
+      ulonglong2 g = *reinterpret_cast<const ulonglong2 *>(G + o);
+      ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(P + o);
+      if (KIND == RV_VALID)
+        for (int l = sd.pos_loop[i]; l >= 0; l = sd.loop_up[l]) {
+          const ulonglong2 h0 = *reinterpret_cast<const ulonglong2 *>(sd.hdr_g + (size_t)l * W + w);
+          const ulonglong2 h1 = *reinterpret_cast<const ulonglong2 *>(sd.hdr_p + (size_t)l * W + w);
+          compose_pair(g.x, q.x, h0.x, h1.x);
+          compose_pair(g.y, q.y, h0.y, h1.y);
+        }
       const ulonglong2 k = *reinterpret_cast<const ulonglong2 *>(sd.carry + oc);
       ulonglong2 x = make_ulonglong2(g.x | (k.x & q.x), g.y | (k.y & q.y));
       if (KIND == RV_VALID) x = make_ulonglong2(~x.x & tp[0], ~x.y & tp[1]);
       *reinterpret_cast<ulonglong2 *>(out + o) = x;
     } else {
       for (int u = 0; u < 2 && w + u < W; ++u) {
-        const uint64_t x = G[o + u] | (sd.carry[oc + u] & P[o + u]);
+        uint64_t g = G[o + u], q = P[o + u];
+        if (KIND == RV_VALID)
+          for (int l = sd.pos_loop[i]; l >= 0; l = sd.loop_up[l])
+            compose_pair(g, q, sd.hdr_g[(size_t)l * W + w + u], sd.hdr_p[(size_t)l * W + w + u]);
+        const uint64_t x = g | (sd.carry[oc + u] & q);
         out[o + u] = KIND == RV_LIVE ? x : ~x & tp[u];
       }
     }
@@ -1286,8 +1311,11 @@ __global__ void k_resolve_src(DevPlan p, ScanDev sd, uint64_t *out) {
   const int W = p.W;
   if (t >= (long long)p.K * W) return;
   const int k = (int)(t / W), w = (int)(t % W);
-  const int c = sd.pos_chunk[sd.src_pos[k]];
-  const uint64_t x = sd.src_g[t] | (sd.carry[(size_t)c * W + w] & sd.src_p[t]);
+  const int i = sd.src_pos[k], c = sd.pos_chunk[i];
+  uint64_t g = sd.src_g[t], q = sd.src_p[t];
+  for (int l = sd.pos_loop[i]; l >= 0; l = sd.loop_up[l])
+    compose_pair(g, q, sd.hdr_g[(size_t)l * W + w], sd.hdr_p[(size_t)l * W + w]);
+  const uint64_t x = g | (sd.carry[(size_t)c * W + w] & q);
   out[t] = ~x & p.top[(size_t)sd.chunks[c].cfg * W + w];
 }
 
@@ -1702,13 +1730,13 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   std::vector<LoopMeta> loops;
   std::vector<ChunkMeta> chunks;
   std::vector<CarrySrc> csrc;
-  std::vector<int32_t> fin_slot, out_slot, out_pos, lat_slot, bend_loop, srcent;
+  std::vector<int32_t> fin_slot, out_slot, out_pos, lat_slot, bend_loop, srcent, exit_slot;
   // short chunks give more independent walks (one warp each) and shorter
   // longest walks; 32 positions measured fastest on the 2^20-block CFG
   if (chunk_target <= 0) chunk_target = 32;
   TraceScope trace_bm("scan build_meta", g.M);
   if (!build_meta(g, chunk_target, st, meta, loops, chunks, csrc, fin_slot, out_slot, out_pos, lat_slot, bend_loop,
-                  srcent, err)) {
+                  srcent, exit_slot, err)) {
     delete st;
     return nullptr;
   }
@@ -1823,6 +1851,7 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   chk(sd.acc_link = st->up(acc_link));
   sd.n_acc_p = (long long)acc_p.size();
   chk(sd.lat_slot = st->up(lat_slot));
+  chk(sd.exit_slot = st->up(exit_slot));
   {
     std::vector<int4> bend_info(bend_loop.size());
     for (size_t q = 0; q < bend_loop.size(); ++q) {
@@ -1890,6 +1919,12 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     for (int k = 0; k < g.K; ++k) src_pos[k] = g.pos[g.ent_src[k]];
     chk(sd.pos_chunk = st->up(pos_chunk));
     chk(sd.src_pos = st->up(src_pos));
+    std::vector<int32_t> pos_loop(g.M);
+    for (int i = 0; i < g.M; ++i) pos_loop[i] = g.inner_loop[g.order[i]];
+    chk(sd.pos_loop = st->up(pos_loop));
+    chk(sd.loop_up = st->up(g.loop_parent));
+    chk(sd.hdr_g = st->alloc<uint64_t>((size_t)std::max(1, g.L) * W));
+    chk(sd.hdr_p = st->alloc<uint64_t>((size_t)std::max(1, g.L) * W));
     const size_t NW = (size_t)g.N * W, KW = (size_t)std::max(1, g.K) * W;
     chk(sd.pair_g = st->alloc<uint64_t>(NW));
     chk(sd.pair_p = st->alloc<uint64_t>(NW));
