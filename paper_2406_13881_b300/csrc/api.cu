@@ -71,7 +71,10 @@ PlanCore::~PlanCore() {
 long long estimate_device_bytes(const ompdart_cfg &c, int keep_states) {
   const long long N = c.n_blocks, W = (c.n_vars + 63) / 64;
   const long long E = c.succ_off ? c.succ_off[N] : 0, A = c.acc_off ? c.acc_off[N] : 0;
-  const long long planes = (3 + (keep_states ? 2 : 0)) * N * W * 8;
+  // state planes (h_in, d_in, h_out, live), the walks' pairs (two per
+  // phase and liveness's header plane), kept states (d_out and its pair);
+  // loop header rows for at most one loop per 8 blocks
+  const long long planes = (9 + (keep_states ? 3 : 0)) * N * W * 8 + 4 * (N / 8 + 1) * W * 8;
   const long long meta = N * (64 + 6 * 4) + E * (2 * 8 + 5 * 4) + A * (4 * 3 + 1);
   const long long chunks = (N / 16 + 1) * W * 8 * 6;  // chunk maps and carries
   const long long xfer = (N / 4 + 64) * 2 * 24 + (N / 8 + 8) * W * 8 * 4;

@@ -134,6 +134,12 @@ struct ScanDev {
   uint64_t *pair_g, *pair_p;    // [N][W] by block: Live_in, later H_out stale
   uint64_t *pair_gd, *pair_pd;  // [N][W] D_in stale (the device phase runs beside liveness)
   uint64_t *pair_g2, *pair_p2;  // [N][W] D_out stale (kept states only), else null
+  // liveness walks an outermost loop once, with a third plane: the part of
+  // a body position's value that comes from the header's own value A
+  // (Live = G | (carry & P) | (A & PA)); at the header A's fixed point goes
+  // to hdrl_* and the resolve folds it in
+  uint64_t *pair_a;             // [N][W] PA of positions inside a loop
+  uint64_t *hdrl_g, *hdrl_p;    // [L][W] liveness at an outermost loop's header (pair of the carry)
   uint64_t *src_g, *src_p;      // [K][W] out value at each loop-entry edge's source
   const int32_t *pos_chunk;     // [M] chunk of each position
   // forward walks take each loop body once, relative to the header's value;
@@ -641,7 +647,10 @@ __device__ __forceinline__ void prep_masks(const ScanDev &sd, const Win &w, cons
       } else {
         const bool ue = uh || ud;
         if (ue) atomicOr(t, bit); else if (df) atomicOr(t + 64, bit);
-        if (MODE == M_SUM && (ue || df)) atomicOr(t + 192, bit);
+        if (MODE == M_SUM && (ue || df)) {
+          atomicOr(t + 192, bit);  // coefficient of the carry
+          atomicOr(t + 320, bit);  // coefficient of the outermost open loop's header value
+        }
       }
     } else {
       const uint32_t GEN = PH == K_D ? R_GD : R_GH, KILL = PH == K_D ? R_KD : R_KH;
@@ -963,8 +972,8 @@ __global__ void __launch_bounds__(256, OMPDART_CHAIN_MIN_CTAS) k_fwd_chain(DevPl
 // backward chain (anticipation; loop-restricted anticipation for the masks)
 // --------------------------------------------------------------------------------------
 template <int MODE>
-struct BwdPlanes {  // SUM: [Live local, Live coefficient]; LANT: [H, D]
-  static constexpr int NP = 2;
+struct BwdPlanes {  // SUM: [Live local, carry coefficient, header coefficient]; LANT: [H, D]
+  static constexpr int NP = MODE == M_SUM ? 3 : 2;
 };
 
 template <int MODE>
@@ -1014,11 +1023,15 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
       depth = bi.x;
       top_ph = bi.y;
       // first visit: the header's value, read by the latches, starts from
-      // nothing; a re-entry keeps the previous visit's value
+      // nothing (liveness, outermost loop: the latches read A itself, the
+      // header coefficient plane all ones); a re-entry keeps the previous
+      // visit's value
       if (i < lwm) {
         const int hs = bi.w;
+        const bool sym = MODE == M_SUM && bi.x == base_depth + 1;
         if (hs >= 0)
-          for (int pl = 0; pl < NP; ++pl) *sl.at(hs, pl, L.lane) = make_ulonglong2(0ull, 0ull);
+          for (int pl = 0; pl < NP; ++pl)
+            *sl.at(hs, pl, L.lane) = sym && pl == 2 ? make_ulonglong2(L.top0, L.top1) : make_ulonglong2(0ull, 0ull);
         __syncwarp();
       }
     }
@@ -1062,25 +1075,40 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
     } else {
       prep_pos = -1;
     }
+    const bool is_top_header = depth > base_depth && top_ph == i;
+    // liveness at an outermost loop's header: A = G | (carry & P) | (A & PA)
+    // has the least solution A = G | (carry & P) (so no second walk); the
+    // value leaves the loop without the header plane
+    const bool sym_close = MODE == M_SUM && is_top_header && depth == base_depth + 1;
+    if (MODE == M_SUM && sym_close) {
+      st_word(sd.hdrl_g, m.head_loop, W, L.w0, z[0][0]);
+      st_word(sd.hdrl_g, m.head_loop, W, L.w0 + 1, z[0][1]);
+      st_word(sd.hdrl_p, m.head_loop, W, L.w0, z[1][0]);
+      st_word(sd.hdrl_p, m.head_loop, W, L.w0 + 1, z[1][1]);
+      z[NP - 1][0] = z[NP - 1][1] = 0;
+    }
     if (m.bslot >= 0) {
       bool changed = false;
-      const bool is_top_header = depth > base_depth && top_ph == i;
 #pragma unroll
       for (int pl = 0; pl < NP; ++pl) {
         ulonglong2 *ptr = sl.at(m.bslot, pl, L.lane);
-        if (is_top_header) {
+        if (is_top_header && !sym_close) {
           const ulonglong2 old = *ptr;
           changed |= (old.x != z[pl][0]) || (old.y != z[pl][1]);
         }
         *ptr = make_ulonglong2(z[pl][0], z[pl][1]);
       }
-      if (is_top_header && __any_sync(0xffffffffu, changed)) dirty |= 1u << (depth - 1);
+      if (is_top_header && !sym_close && __any_sync(0xffffffffu, changed)) dirty |= 1u << (depth - 1);
     }
-    if (MODE == M_SUM) {  // Live_in as an affine pair of the chunk's carry
+    if (MODE == M_SUM) {  // Live_in as an affine pair of the chunk's carry (and A inside a loop)
       st_word(sd.pair_g, m.blk, W, L.w0, z[0][0]);
       st_word(sd.pair_g, m.blk, W, L.w0 + 1, z[0][1]);
       st_word(sd.pair_p, m.blk, W, L.w0, z[1][0]);
       st_word(sd.pair_p, m.blk, W, L.w0 + 1, z[1][1]);
+      if (depth > base_depth) {
+        st_word(sd.pair_a, m.blk, W, L.w0, z[NP - 1][0]);
+        st_word(sd.pair_a, m.blk, W, L.w0 + 1, z[NP - 1][1]);
+      }
     }
     __syncwarp();
 #pragma unroll
@@ -1129,9 +1157,8 @@ __device__ __forceinline__ void bwd_walk(const DevPlan &p, const ScanDev &sd, co
   L.top1 = L.w0 + 1 < W ? tp[L.w0 + 1] : 0;
   Slots<NP> sl{wm.slots, spill, sd.sh_slots};
   const ChunkMeta cm = sd.chunks[c];
-  uint64_t cin[NP][2], zl[NP][2];
+  uint64_t cin[NP][2] = {}, zl[NP][2];
   // the identity map of the liveness entering from the next chunk
-  cin[0][0] = cin[0][1] = 0;
   cin[1][0] = L.top0;
   cin[1][1] = L.top1;
   bwd_range<MODE>(p, sd, L, wm, sl, cm.s, cm.e, 0, -1, true, cin, zl, cm.cfg);
@@ -1264,7 +1291,9 @@ enum ResolveKind { RV_LIVE = 0, RV_VALID = 1 };  // liveness as is; stale sets t
 // out[b] = G[b] | (carry[chunk] & P[b]), converted for RV_VALID to ~x & top
 // (the CFG's valid-variable mask).  A forward (RV_VALID) pair is relative
 // to the header value of the innermost loop holding the position: it is
-// first composed with the header values up the loop tree.  A thread takes
+// first composed with the header values up the loop tree.  A liveness pair
+// inside a loop first takes in its outermost loop's header value A
+// through PA (G |= A_G & PA, P |= A_P & PA).  A thread takes
 // two consecutive words of a row (16-byte accesses when W is even); the
 // grid strides over (position, word pair).
 template <int KIND>
@@ -1281,6 +1310,15 @@ __global__ void __launch_bounds__(256) k_resolve(DevPlan p, ScanDev sd, const ui
     if ((W & 1) == 0) {
       ulonglong2 g = *reinterpret_cast<const ulonglong2 *>(G + o);
       ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(P + o);
+      if (KIND == RV_LIVE && sd.pos_loop[i] >= 0) {
+        int l = sd.pos_loop[i];
+        while (sd.loop_up[l] >= 0) l = sd.loop_up[l];
+        const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(sd.pair_a + o);
+        const ulonglong2 h0 = *reinterpret_cast<const ulonglong2 *>(sd.hdrl_g + (size_t)l * W + w);
+        const ulonglong2 h1 = *reinterpret_cast<const ulonglong2 *>(sd.hdrl_p + (size_t)l * W + w);
+        g = make_ulonglong2(g.x | (h0.x & a.x), g.y | (h0.y & a.y));
+        q = make_ulonglong2(q.x | (h1.x & a.x), q.y | (h1.y & a.y));
+      }
       if (KIND == RV_VALID)
         for (int l = sd.pos_loop[i]; l >= 0; l = sd.loop_up[l]) {
           const ulonglong2 h0 = *reinterpret_cast<const ulonglong2 *>(sd.hdr_g + (size_t)l * W + w);
@@ -1295,6 +1333,13 @@ __global__ void __launch_bounds__(256) k_resolve(DevPlan p, ScanDev sd, const ui
     } else {
       for (int u = 0; u < 2 && w + u < W; ++u) {
         uint64_t g = G[o + u], q = P[o + u];
+        if (KIND == RV_LIVE && sd.pos_loop[i] >= 0) {
+          int l = sd.pos_loop[i];
+          while (sd.loop_up[l] >= 0) l = sd.loop_up[l];
+          const uint64_t a = sd.pair_a[o + u];
+          g |= sd.hdrl_g[(size_t)l * W + w + u] & a;
+          q |= sd.hdrl_p[(size_t)l * W + w + u] & a;
+        }
         if (KIND == RV_VALID)
           for (int l = sd.pos_loop[i]; l >= 0; l = sd.loop_up[l])
             compose_pair(g, q, sd.hdr_g[(size_t)l * W + w + u], sd.hdr_p[(size_t)l * W + w + u]);
@@ -1870,7 +1915,7 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     int dev = 0, n_sm = 148;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     const int items = C * G;
-    st->shape[CK_BSUM] = chain_shape(k_bwd_chain<M_SUM>, st->bslots, 2, wpc, items, n_sm);
+    st->shape[CK_BSUM] = chain_shape(k_bwd_chain<M_SUM>, st->bslots, BwdPlanes<M_SUM>::NP, wpc, items, n_sm);
     st->shape[CK_BLANT] = chain_shape(k_bwd_chain<M_LANT>, st->bslots, 2, wpc, std::max(1, g.L) * G, n_sm);
     st->shape[CK_FSUM] = chain_shape(k_fwd_chain<K_HP>, st->fslots, 2, wpc, items, n_sm);
     chain_shape(k_fwd_chain<K_D>, st->fslots, 2, wpc, items, n_sm);
@@ -1878,10 +1923,14 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   }
   int max_warps = 1;
   for (const ChainShape &c : st->shape) max_warps = std::max(max_warps, c.grid * c.wpc);
-  // slots beyond those a kernel keeps in shared memory (at least
-  // SH_WORDS / 128 of them, 2 planes at most) spill to a per-warp area
-  const int max_slots = std::max(st->fslots, st->bslots), min_sh = SH_WORDS / (64 * 2);
-  sd.spill_stride = std::max(1, max_slots - min_sh) * 2 * 64;
+  // slots beyond those a kernel keeps in shared memory spill to a per-warp area
+  {
+    const int fwd = std::max(0, st->fslots - SH_WORDS / (64 * 2)) * 2 * 64;
+    const int lant = std::max(0, st->bslots - SH_WORDS / (64 * 2)) * 2 * 64;
+    const int NPS = BwdPlanes<M_SUM>::NP;
+    const int live = std::max(0, st->bslots - SH_WORDS / (64 * NPS)) * NPS * 64;
+    sd.spill_stride = std::max({64, fwd, lant, live});
+  }
   st->spill_region = (size_t)std::max(1, sd.spill_stride) * max_warps;
   chk(sd.spill = st->alloc<uint64_t>(st->spill_region * 3));  // one region per branch of a run
   chk(sd.gsum = st->alloc<uint64_t>((size_t)2 * C * W));
@@ -1925,7 +1974,10 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     chk(sd.loop_up = st->up(g.loop_parent));
     chk(sd.hdr_g = st->alloc<uint64_t>((size_t)std::max(1, g.L) * W));
     chk(sd.hdr_p = st->alloc<uint64_t>((size_t)std::max(1, g.L) * W));
+    chk(sd.hdrl_g = st->alloc<uint64_t>((size_t)std::max(1, g.L) * W));
+    chk(sd.hdrl_p = st->alloc<uint64_t>((size_t)std::max(1, g.L) * W));
     const size_t NW = (size_t)g.N * W, KW = (size_t)std::max(1, g.K) * W;
+    chk(sd.pair_a = st->alloc<uint64_t>(NW));
     chk(sd.pair_g = st->alloc<uint64_t>(NW));
     chk(sd.pair_p = st->alloc<uint64_t>(NW));
     chk(sd.pair_gd = st->alloc<uint64_t>(NW));
