@@ -52,9 +52,7 @@ def workload_name(n_blocks):
 # DRAM traffic per launch from ncu captures of the current kernels (see
 # profiles/): dram__bytes_read.sum + dram__bytes_write.sum on the 2^18-block
 # version of the workload, scaled to the bench's launch by block-words
-MEASURED_TRAFFIC = {
-    "live_summary": {"bytes_2e18": 46.233856e6 + 334.327808e6, "profile": "profiles/live_summary_walk_2e18.md"},
-}
+MEASURED_TRAFFIC = {}
 
 
 def peaks():
@@ -81,19 +79,25 @@ def byte_model(st):
     G = (W + 63) // 64
     plane = 8.0 * W * N
     edge_plane = 8.0 * W * K
+    in_loop = 8.0 * W * st["in_loop"]                  # a plane's rows of the blocks inside loops
+    hdr = 2 * 8.0 * W * L                               # one header pair per loop
+    hdr_top = 2 * 8.0 * W * st["L_top"]
     walk = G * (M * 64.0 + E * 8.0 + A * 4.0)
-    resolve = 3 * plane + 8.0 * M                       # two pair planes in, one plane out
+    # two pair planes in, one plane out; forward pairs also take the loop
+    # tree (a loop id per position and loop, each header pair once)
+    resolve = 3 * plane + 8.0 * M
+    fwd_resolve = resolve + 4.0 * (M + L) + hdr
     return {
         "local_summary": A * 20.0,                      # access, link in; record, emission word out
-        "live_summary": walk + 2 * plane,               # writes the Live pairs
-        "live_resolve": resolve,
+        "live_summary": walk + 2 * plane + in_loop + hdr_top,  # Live pairs, the header plane inside loops
+        "live_resolve": resolve + in_loop + 4.0 * (M + L) + hdr_top,
         "loop_masks": G * st["body"] * (64.0 + 4.0 * A / max(1, M) + 8.0 * E / max(1, M)) + 2 * L * 8.0 * W,
-        "hp_summary": walk + 2 * edge_plane,            # pairs at loop-entry sources
+        "hp_summary": walk + 2 * edge_plane + hdr,      # pairs at loop-entry sources, header pairs
         "src_resolve": 3 * edge_plane,
-        "d_summary": walk + 3 * edge_plane + 2 * plane,  # reads `to' constants; writes D_in pairs
-        "d_resolve": resolve,
-        "h_summary": walk + edge_plane + 4 * plane,     # reads Live, D_in; writes H_out pairs
-        "h_resolve": resolve,
+        "d_summary": walk + 3 * edge_plane + 2 * plane + hdr,  # reads `to' constants; writes D_in pairs
+        "d_resolve": fwd_resolve,
+        "h_summary": walk + edge_plane + 4 * plane + hdr,  # reads Live, D_in; writes H_out pairs
+        "h_resolve": fwd_resolve,
         "emit": 4 * plane + E * 8.0 * W + M * 64.0 + E * 16.0 + A * 9.0 + 3 * edge_plane,
     }
 
@@ -191,10 +195,13 @@ def cpu_info():
 def workload_stats(g, plan_ing=None):
     import numpy as np
     W = g.W
-    st = {"N": g.n_blocks, "M": g.n_blocks, "E": g.n_edges, "A": g.n_acc, "W": W,
-          "K": g.meta.get("loop_entry_edges", 0), "L": g.meta.get("headers", 0)}
     loops = g.meta.get("loops", [])
+    st = {"N": g.n_blocks, "M": g.n_blocks, "E": g.n_edges, "A": g.n_acc, "W": W,
+          "K": g.meta.get("loop_entry_edges", 0), "L": len(loops)}
     st["body"] = float(sum(e - f + 1 for _, f, e, _ in loops))
+    # blocks inside some loop (the bodies of the outermost loops) and those loops
+    st["in_loop"] = float(sum(e - h for h, _, e, d in loops if d == 1))
+    st["L_top"] = sum(1 for *_, d in loops if d == 1)
     return st
 
 

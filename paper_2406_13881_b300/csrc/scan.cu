@@ -283,14 +283,12 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
   for (auto &v : ends)
     std::sort(v.begin(), v.end(), [&](int a, int b) { return g.loop_depth[a] < g.loop_depth[b]; });
 
-  // positions the walks may jump to (a loop body walked again): forward to
-  // the header, backward to the last body position.  Only at other positions
-  // is "the position walked just before" the neighbouring position.
-  std::vector<uint8_t> fwd_target(M, 0), bwd_target(M, 0);
-  for (int l = 0; l < L; ++l) {
-    fwd_target[g.pos[g.loop_head[l]]] = 1;
-    bwd_target[g.loop_end[l] - 1] = 1;
-  }
+  // positions the backward walks may jump to (a loop body walked again):
+  // the last body position.  Only at other positions is "the position
+  // walked just before" the neighbouring one.  The forward walks take every
+  // position once, in order.
+  std::vector<uint8_t> bwd_target(M, 0);
+  for (int l = 0; l < L; ++l) bwd_target[g.loop_end[l] - 1] = 1;
   fin_slot.assign(g.fin_src.size(), -1);
   out_slot.assign(g.out_dst.size(), -1);
   out_pos.assign(g.out_dst.size(), -1);
@@ -318,23 +316,18 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
       int a = i, z = -1;
       for (int k = g.out_off[i]; k < g.out_off[i + 1]; ++k) {
         const int pt = g.pos[g.out_dst[k]];
-        if (pt == i + 1 && pt < e && !fwd_target[pt]) continue;  // read from registers
+        if (pt == i + 1 && pt < e) continue;  // read from registers
         if (pt >= e) {
           z = std::max(z, e);
         } else if (pt > i) {
-          const int l = head_loop_of_pos[pt];
-          z = std::max(z, l >= 0 ? g.loop_end[l] - 1 : pt);
-        } else {
+          z = std::max(z, pt);
+        } else {  // a latch: read when its loop closes, at the body's last position
           const int l = head_loop_of_pos[pt];
           if (l < 0) {
             if (err) *err = "retreating edge into a non-header";
             return false;
           }
-          // a latch value survives until its loop is re-entered from an
-          // enclosing loop walked again: reserve it over the outermost one
-          const int lo = outermost(l);
-          a = std::min(a, g.pos[g.loop_head[lo]]);
-          z = std::max(z, g.loop_end[lo] - 1);
+          z = std::max(z, g.loop_end[l] - 1);
         }
       }
       (void)b;
@@ -414,7 +407,7 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
     for (int i = s; i < e; ++i) {
       for (int k = g.fin_off[i]; k < g.fin_off[i + 1]; ++k) {
         const int pp = g.pos[g.fin_src[k]];
-        fin_slot[k] = pp < s ? CARRY : pp >= i ? BACK : (pp == i - 1 && !fwd_target[i]) ? PREV : fslot[pp];
+        fin_slot[k] = pp < s ? CARRY : pp >= i ? BACK : pp == i - 1 ? PREV : fslot[pp];
       }
       for (int k = g.out_off[i]; k < g.out_off[i + 1]; ++k) {
         const int pt = g.pos[g.out_dst[k]];
@@ -447,8 +440,9 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
         lat_slot.push_back(fslot[pp]);
     }
     lm.lat_cnt = (int32_t)lat_slot.size() - lm.lat_beg;
-    // exit sources: body positions whose value a position after the body
-    // (or the next chunk's carry) reads from their slot
+    // exit sources: body positions whose value is read from their slot
+    // outside the body: after it (or as the next chunk's carry), or at an
+    // enclosing loop's end (a back edge to an enclosing header)
     const int ce = chunks[std::upper_bound(g.chunk_off.begin(), g.chunk_off.end(), lm.ph) - g.chunk_off.begin() - 1].e;
     lm.xs_beg = (int32_t)exit_slot.size();
     for (int q = lm.ph; q < lm.pend; ++q) {
@@ -456,7 +450,7 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
       bool read_after = false;
       for (int k = g.out_off[q]; k < g.out_off[q + 1] && !read_after; ++k) {
         const int pt = g.pos[g.out_dst[k]];
-        read_after = pt >= lm.pend && (pt >= ce || !(pt == q + 1 && !fwd_target[pt]));
+        read_after = (pt >= lm.pend || pt < lm.ph) && (pt >= ce || pt != q + 1);
       }
       if (read_after) exit_slot.push_back(fslot[q]);
     }
@@ -832,13 +826,14 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
       const int2 fe = win_edge(w, wr, sd.fin_pk, m.fin_beg + q);
       const int slot = fe.x;
       if (slot == CARRY || slot == BACK) continue;  // in z via cin / closed at the loop's end
-      if (slot == PREV) {                           // the position walked just before
-#pragma unroll
-        for (int pl = 0; pl < NP; ++pl) { z[pl][0] |= pv[pl][0]; z[pl][1] |= pv[pl][1]; }
-        continue;
-      }
+      // a loop-entry edge leaves out what is hoisted to it (Sec. IV-D)
       uint64_t m0 = ~0ull, m1 = ~0ull;
       if (PH != K_HP && fe.y >= 0) { m0 = ~ld_word(ec, fe.y, W, L.w0); m1 = ~ld_word(ec, fe.y, W, L.w0 + 1); }
+      if (slot == PREV) {  // the position walked just before
+#pragma unroll
+        for (int pl = 0; pl < NP; ++pl) { z[pl][0] |= pv[pl][0] & m0; z[pl][1] |= pv[pl][1] & m1; }
+        continue;
+      }
 #pragma unroll
       for (int pl = 0; pl < NP; ++pl) {
         const ulonglong2 v = *sl.at(slot, pl, L.lane);

@@ -154,6 +154,27 @@ def test_back_edge_transfer_without_loop_rerun():
         assert_matches_oracle(g, res, orc)
 
 
+def test_continue_to_enclosing_loop():
+    """Back edges from inside an inner loop to the enclosing loop's header
+    (a `continue' of the outer loop) and an inner latch, under random
+    accesses to a few variables: the value along the outer back edge leaves
+    the inner loop before the outer loop closes."""
+    succ = [[1], [2, 7], [3], [4, 6], [5, 1], [3], [1], []]
+    rng = np.random.default_rng(11)
+    for _ in range(40):
+        accs = [[] for _ in succ]
+        for b in range(1, 8):
+            for v in range(3):
+                if rng.random() < 0.45:
+                    accs[b].append((v, int(rng.integers(1, 4)), int(rng.integers(0, 2))))
+        g = wl.from_lists(succ, accs, 3)
+        orc = oracle.solve(g)
+        for target in (0, 1, 2):
+            res = _native.analyze(g, path=2, chunk_target=target, keep_states=True)
+            assert res["path"] == 2
+            assert_matches_oracle(g, res, orc)
+
+
 def test_unreachable_blocks_scan_path():
     g = wl.from_lists([[1], [2], [], [1], [3]], [[(0, 2, 0)], [(0, 1, 1)], [], [(1, 2, 1)], [(0, 3, 1)]], 3)
     res = _native.analyze(g, path=2, keep_states=True)
