@@ -265,18 +265,20 @@ int ingest(const ompdart_cfg *c, Ingest *g, std::string *err) {
   {
     std::vector<uint8_t> seen(N, 0);
     std::vector<int32_t> sorted_succ(g->E);
+    std::vector<std::pair<int, int32_t>> key;
     for (int b = 0; b < N; ++b) {
       if (!reach[b]) continue;
       int n = so[b + 1] - so[b];
       int32_t *dst = sorted_succ.data() + so[b];
       for (int k = 0; k < n; ++k) dst[k] = succ[so[b] + k];
-      if (n > 1) {
-        std::vector<std::pair<int, int>> key(n);
-        for (int k = 0; k < n; ++k) key[k] = {common_depth(b, dst[k]), k};
-        std::stable_sort(key.begin(), key.end());
-        std::vector<int32_t> tmp(n);
-        for (int k = 0; k < n; ++k) tmp[k] = dst[key[k].second];
-        for (int k = 0; k < n; ++k) dst[k] = tmp[k];
+      if (n > 1) {  // stable: equal depths keep the successor order
+        key.resize(n);
+        for (int k = 0; k < n; ++k) key[k] = {common_depth(b, dst[k]), dst[k]};
+        std::stable_sort(key.begin(), key.end(),
+                         [](const std::pair<int, int32_t> &x, const std::pair<int, int32_t> &y) {
+                           return x.first < y.first;
+                         });
+        for (int k = 0; k < n; ++k) dst[k] = key[k].second;
       }
     }
     std::vector<std::pair<int32_t, int32_t>> st;
@@ -334,7 +336,7 @@ int ingest(const ompdart_cfg *c, Ingest *g, std::string *err) {
     g->loop_head[k] = headers[l];
     g->loop_parent[k] = lparent[l] == kNone ? kNone : newid[lparent[l]];
     g->loop_depth[k] = ldepth[l];
-    std::vector<int32_t> bd = bodies[l];
+    std::vector<int32_t> &bd = bodies[l];  // not needed in build order any more
     std::sort(bd.begin(), bd.end(), [&](int a, int b) { return g->pos[a] < g->pos[b]; });
     int p0 = g->pos[bd.front()], p1 = g->pos[bd.back()];
     if (bd.front() != headers[l] || p1 - p0 + 1 != (int)bd.size()) g->contiguous = false;
@@ -374,6 +376,7 @@ int ingest(const ompdart_cfg *c, Ingest *g, std::string *err) {
   g->out_off.assign(M + 1, 0);
   g->is_exit.assign(M, 0);
   g->fin_src.clear(); g->fin_eid.clear(); g->fin_ent.clear(); g->out_dst.clear();
+  g->fin_src.reserve(g->E); g->fin_eid.reserve(g->E); g->fin_ent.reserve(g->E); g->out_dst.reserve(g->E);
   g->exit_blocks.clear();
   for (int i = 0; i < M; ++i) {
     int b = g->order[i];

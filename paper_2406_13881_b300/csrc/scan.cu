@@ -22,10 +22,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <functional>
 #include <queue>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -170,28 +172,52 @@ struct Interval {
   int a, b, id;
 };
 
-// Interval colouring: intervals sharing no position may share a slot.
-int colour(std::vector<Interval> &iv, std::vector<int32_t> &slot_of) {
-  std::sort(iv.begin(), iv.end(), [](const Interval &x, const Interval &y) { return x.a < y.a; });
-  std::priority_queue<std::pair<int, int>, std::vector<std::pair<int, int>>, std::greater<>> active;
-  std::priority_queue<int, std::vector<int>, std::greater<>> freeq;
-  int n = 0;
-  for (const Interval &x : iv) {
-    while (!active.empty() && active.top().first < x.a) {
-      freeq.push(active.top().second);
-      active.pop();
+// Interval colouring: intervals sharing no position may share a slot
+// (lowest free slot first).  The heaps are the caller's scratch.
+struct Colouring {
+  std::vector<std::pair<int, int>> active;  // min-heap of (end, slot)
+  std::vector<int> freeq;                   // min-heap of free slots
+  int run(std::vector<Interval> &iv, std::vector<int32_t> &slot_of) {
+    std::sort(iv.begin(), iv.end(), [](const Interval &x, const Interval &y) { return x.a < y.a; });
+    active.clear();
+    freeq.clear();
+    const std::greater<> gt;
+    int n = 0;
+    for (const Interval &x : iv) {
+      while (!active.empty() && active.front().first < x.a) {
+        freeq.push_back(active.front().second);
+        std::push_heap(freeq.begin(), freeq.end(), gt);
+        std::pop_heap(active.begin(), active.end(), gt);
+        active.pop_back();
+      }
+      int s;
+      if (freeq.empty()) {
+        s = n++;
+      } else {
+        s = freeq.front();
+        std::pop_heap(freeq.begin(), freeq.end(), gt);
+        freeq.pop_back();
+      }
+      slot_of[x.id] = s;
+      active.push_back({x.b, s});
+      std::push_heap(active.begin(), active.end(), gt);
     }
-    int s;
-    if (freeq.empty()) {
-      s = n++;
-    } else {
-      s = freeq.top();
-      freeq.pop();
-    }
-    slot_of[x.id] = s;
-    active.push({x.b, s});
+    return n;
   }
-  return n;
+};
+
+// f(t, lo, hi) for t < T over [0, n) split in T contiguous ranges, on up to
+// `max_threads` host threads (the calling thread takes t = 0); returns T
+template <class F>
+int parallel_ranges(int n, int min_per_thread, int max_threads, F f) {
+  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  const int T = std::max(1, std::min({hw, max_threads, n / std::max(1, min_per_thread)}));
+  std::vector<std::thread> pool;
+  for (int t = 1; t < T; ++t)
+    pool.emplace_back(f, t, (int)((long long)n * t / T), (int)((long long)n * (t + 1) / T));
+  f(0, 0, (int)((long long)n / T));
+  for (auto &x : pool) x.join();
+  return T;
 }
 
 }  // namespace
@@ -274,14 +300,26 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
   for (int l = 0; l < L; ++l) head_loop_of_pos[g.pos[g.loop_head[l]]] = l;
   std::vector<int32_t> exit_idx(g.N, -1);
   for (size_t x = 0; x < g.exit_blocks.size(); ++x) exit_idx[g.exit_blocks[x]] = (int32_t)x;
-  // loop-entry edges by source block
-  std::vector<std::vector<int32_t>> ent_by_src(g.N);
-  for (int k = 0; k < g.K; ++k) ent_by_src[g.ent_src[k]].push_back(k);
-  // loops ending at each position, outer first
-  std::vector<std::vector<int32_t>> ends(M);
-  for (int l = 0; l < L; ++l) ends[g.loop_end[l] - 1].push_back(l);
-  for (auto &v : ends)
-    std::sort(v.begin(), v.end(), [&](int a, int b) { return g.loop_depth[a] < g.loop_depth[b]; });
+  // loop-entry edges by source block, loops ending at each position (outer
+  // first): both as offset lists
+  std::vector<int32_t> ebs_off(g.N + 1, 0), ebs(g.K), end_off(M + 1, 0), end_l(L);
+  for (int k = 0; k < g.K; ++k) ebs_off[g.ent_src[k] + 1]++;
+  for (int b = 0; b < g.N; ++b) ebs_off[b + 1] += ebs_off[b];
+  {
+    std::vector<int32_t> f(ebs_off.begin(), ebs_off.end() - 1);
+    for (int k = 0; k < g.K; ++k) ebs[f[g.ent_src[k]]++] = k;
+  }
+  for (int l = 0; l < L; ++l) end_off[g.loop_end[l]]++;
+  for (int i = 0; i < M; ++i) end_off[i + 1] += end_off[i];
+  {
+    std::vector<int32_t> f(end_off.begin(), end_off.end() - 1);
+    for (int l = 0; l < L; ++l) end_l[f[g.loop_end[l] - 1]++] = l;
+    for (int i = 0; i < M; ++i)
+      if (end_off[i + 1] - end_off[i] > 1)
+        std::sort(end_l.begin() + end_off[i], end_l.begin() + end_off[i + 1],
+                  [&](int a, int b) { return g.loop_depth[a] < g.loop_depth[b]; });
+  }
+  bend_loop.assign(end_l.begin(), end_l.end());
 
   // positions the backward walks may jump to (a loop body walked again):
   // the last body position.  Only at other positions is "the position
@@ -293,14 +331,21 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
   out_slot.assign(g.out_dst.size(), -1);
   out_pos.assign(g.out_dst.size(), -1);
   std::vector<int32_t> fslot(M, -1), bslot(M, -1), hslot(L, -1);
-  int max_f = 0, max_b = 0;
   // loop containing a block but not another: outermost such
   auto contains = [&](int l, int p) { return p >= g.pos[g.loop_head[l]] && p < g.loop_end[l]; };
   auto outermost = [&](int l) {
     while (g.loop_parent[l] >= 0) l = g.loop_parent[l];
     return l;
   };
-  for (int c = 0; c < C; ++c) {
+  // ---- per chunk: slots by interval colouring (chunks are independent)
+  struct ChunkScratch {
+    std::vector<Interval> iv;
+    std::vector<int32_t> loc_loops, so, sb;
+    Colouring col;
+    int max_f = 0, max_b = 0;
+    bool bad = false;
+  };
+  auto colour_chunk = [&](int c, ChunkScratch &x) {
     const int s = g.chunk_off[c], e = g.chunk_off[c + 1];
     ChunkMeta &cm = chunks[c];
     cm.s = s;
@@ -308,7 +353,8 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
     cm.cfg = (int32_t)(std::upper_bound(g.cfg_pos_off.begin(), g.cfg_pos_off.end(), s) - g.cfg_pos_off.begin()) - 1;
     cm.flags = (s == g.cfg_pos_off[cm.cfg] ? CH_FIRST : 0) | (e == g.cfg_pos_off[cm.cfg + 1] ? CH_LAST : 0);
     // ---- forward values
-    std::vector<Interval> iv;
+    std::vector<Interval> &iv = x.iv;
+    iv.clear();
     const int nval = e - s;  // ids: [0, nval) positions, [nval, nval + nloops) header in-values
     int lb = L, le = -1;
     for (int i = s; i < e; ++i) {
@@ -324,8 +370,8 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
         } else {  // a latch: read when its loop closes, at the body's last position
           const int l = head_loop_of_pos[pt];
           if (l < 0) {
-            if (err) *err = "retreating edge into a non-header";
-            return false;
+            x.bad = true;
+            return;
           }
           z = std::max(z, g.loop_end[l] - 1);
         }
@@ -338,7 +384,8 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
         le = std::max(le, l);
       }
     }
-    std::vector<int32_t> loc_loops;
+    std::vector<int32_t> &loc_loops = x.loc_loops;
+    loc_loops.clear();
     if (le >= 0)
       for (int l = lb; l <= le; ++l) {
         loc_loops.push_back(l);
@@ -346,8 +393,9 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
       }
     cm.loop_beg = le >= 0 ? lb : 0;
     cm.loop_end = le >= 0 ? le + 1 : 0;
-    std::vector<int32_t> so(nval + loc_loops.size(), -1);
-    max_f = std::max(max_f, colour(iv, so));
+    std::vector<int32_t> &so = x.so;
+    so.assign(nval + loc_loops.size(), -1);
+    x.max_f = std::max(x.max_f, x.col.run(iv, so));
     for (int i = s; i < e; ++i) fslot[i] = so[i - s];
     for (size_t q = 0; q < loc_loops.size(); ++q) hslot[loc_loops[q]] = so[nval + q];
     // ---- backward values
@@ -377,9 +425,25 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
       (void)b;
       if (z >= 0) iv.push_back({a, z, i - s});
     }
-    std::vector<int32_t> sb(nval, -1);
-    max_b = std::max(max_b, colour(iv, sb));
+    std::vector<int32_t> &sb = x.sb;
+    sb.assign(nval, -1);
+    x.max_b = std::max(x.max_b, x.col.run(iv, sb));
     for (int i = s; i < e; ++i) bslot[i] = sb[i - s];
+  };
+  int max_f = 0, max_b = 0;
+  {
+    std::vector<ChunkScratch> xs(8);
+    parallel_ranges(C, 256, 8, [&](int t, int lo, int hi) {
+      for (int c = lo; c < hi && !xs[t].bad; ++c) colour_chunk(c, xs[t]);
+    });
+    for (const ChunkScratch &x : xs) {
+      if (x.bad) {
+        if (err) *err = "retreating edge into a non-header";
+        return false;
+      }
+      max_f = std::max(max_f, x.max_f);
+      max_b = std::max(max_b, x.max_b);
+    }
   }
   // ---- per position records
   for (int i = 0; i < M; ++i) {
@@ -396,11 +460,10 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
     m.head_loop = head_loop_of_pos[i];
     m.exit_idx = exit_idx[b];
     m.srcent_beg = (int32_t)srcent.size();
-    for (int k : ent_by_src[b]) srcent.push_back(k);
+    srcent.insert(srcent.end(), ebs.begin() + ebs_off[b], ebs.begin() + ebs_off[b + 1]);
     m.nsrcent = (int16_t)(srcent.size() - m.srcent_beg);
-    m.bend_beg = (int32_t)bend_loop.size();
-    for (int l : ends[i]) bend_loop.push_back(l);
-    m.nbend = (int16_t)(bend_loop.size() - m.bend_beg);
+    m.bend_beg = end_off[i];
+    m.nbend = (int16_t)(end_off[i + 1] - end_off[i]);
   }
   for (int c = 0; c < C; ++c) {
     const int s = chunks[c].s, e = chunks[c].e;
@@ -1781,31 +1844,70 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     return nullptr;
   }
   trace_bm.next("scan uploads", g.M);
-  // accesses in position order, and each position's first access there
-  std::vector<uint32_t> acc_p;
-  acc_p.reserve(g.A);
-  std::vector<int32_t> var_idx;
-  std::vector<int2> acc_link;
-  acc_link.reserve(g.A);
-  std::vector<std::pair<int32_t, int32_t>> seen;  // (variable, its latest access) within the block
-  for (int i = 0; i < g.M; ++i) {
-    const int b = meta[i].blk, a0 = acc_off[b], a1 = acc_off[b + 1];
-    bool has_call = false;
-    for (int k = a0; k < a1 && calls.rows; ++k) has_call |= (acc[k] >> 31) != 0;
-    meta[i].acc_beg = a0;
-    meta[i].pacc_beg = (int32_t)acc_p.size();
-    meta[i].flags = 0;
-    if (has_call) {
-      if (var_idx.empty()) var_idx.assign((size_t)p.W * 64, -1);
-      const int cfg = (int)(std::upper_bound(g.cfg_pos_off.begin(), g.cfg_pos_off.end(), i) - g.cfg_pos_off.begin()) - 1;
-      fold_call_block(acc, a0, a1, calls, calls.row_base.empty() ? 0 : calls.row_base[cfg], p.W, var_idx, &acc_p);
-      meta[i].flags = PM_RECORDS;
-      acc_link.resize(acc_p.size(), make_int2(LINK_RECORD, -1));
-    } else {
-      acc_p.insert(acc_p.end(), acc + a0, acc + a1);
-      // same-variable links inside the block (a short list for the usual
-      // handful of accesses, a hash map for long blocks)
-      const int base = meta[i].pacc_beg;
+  // accesses in position order: a block's own accesses with same-variable
+  // links inside the block (a short list for the usual handful of accesses,
+  // a hash map for long blocks), or, for a block with calls, its folded
+  // summary records.  Positions are independent once their offsets are
+  // known: a first parallel pass sizes them (folding the call blocks into
+  // per-thread buffers), a second fills them, over the same ranges.
+  constexpr int kThreads = 8, kMinPos = 4096;
+  struct Folded {
+    std::vector<uint32_t> recs;
+    std::vector<std::pair<int32_t, int32_t>> at;  // (position, first record), in position order
+    std::vector<int32_t> var_idx;
+  };
+  std::vector<Folded> fold(kThreads);
+  std::vector<int32_t> cnt(g.M + 1, 0);
+  std::atomic<bool> too_big{false};
+  parallel_ranges(g.M, kMinPos, kThreads, [&](int t, int lo, int hi) {
+    Folded &fd = fold[t];
+    for (int i = lo; i < hi; ++i) {
+      const int b = meta[i].blk, a0 = acc_off[b], a1 = acc_off[b + 1];
+      bool has_call = false;
+      for (int k = a0; k < a1 && calls.rows; ++k) has_call |= (acc[k] >> 31) != 0;
+      int n = a1 - a0;
+      if (has_call) {
+        if (fd.var_idx.empty()) fd.var_idx.assign((size_t)p.W * 64, -1);
+        const int cfg =
+            (int)(std::upper_bound(g.cfg_pos_off.begin(), g.cfg_pos_off.end(), i) - g.cfg_pos_off.begin()) - 1;
+        const size_t r0 = fd.recs.size();
+        fold_call_block(acc, a0, a1, calls, calls.row_base.empty() ? 0 : calls.row_base[cfg], p.W, fd.var_idx,
+                        &fd.recs);
+        fd.at.push_back({i, (int32_t)r0});
+        n = (int)(fd.recs.size() - r0);
+      }
+      if (n > 32767) too_big = true;
+      cnt[i + 1] = n;
+    }
+  });
+  if (too_big) {
+    if (err) *err = "a block with more than 32767 accesses (or variables touched by its calls)";
+    delete st;
+    return nullptr;
+  }
+  for (int i = 0; i < g.M; ++i) cnt[i + 1] += cnt[i];
+  std::vector<uint32_t> acc_p(cnt[g.M]);
+  std::vector<int2> acc_link(cnt[g.M]);
+  parallel_ranges(g.M, kMinPos, kThreads, [&](int t, int lo, int hi) {
+    const Folded &fd = fold[t];
+    size_t next_fold = 0;
+    std::vector<std::pair<int32_t, int32_t>> seen;  // (variable, its latest access) within the block
+    std::unordered_map<int32_t, int32_t> latest;
+    for (int i = lo; i < hi; ++i) {
+      const int b = meta[i].blk, a0 = acc_off[b], a1 = acc_off[b + 1], base = cnt[i];
+      PosMeta &m = meta[i];
+      m.acc_beg = a0;
+      m.pacc_beg = base;
+      m.nacc = (int16_t)(cnt[i + 1] - base);
+      m.flags = 0;
+      if (next_fold < fd.at.size() && fd.at[next_fold].first == i) {
+        const int r0 = fd.at[next_fold++].second;
+        std::copy(fd.recs.begin() + r0, fd.recs.begin() + r0 + m.nacc, acc_p.begin() + base);
+        std::fill(acc_link.begin() + base, acc_link.begin() + base + m.nacc, make_int2(LINK_RECORD, -1));
+        m.flags = PM_RECORDS;
+        continue;
+      }
+      std::copy(acc + a0, acc + a1, acc_p.begin() + base);
       if (a1 - a0 <= 64) {
         seen.clear();
         for (int k = a0; k < a1; ++k) {
@@ -1819,10 +1921,10 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
               break;
             }
           if (first == idx) seen.push_back({v, idx});
-          acc_link.push_back(make_int2(first, -1));
+          acc_link[idx] = make_int2(first, -1);
         }
       } else {
-        std::unordered_map<int32_t, int32_t> latest;
+        latest.clear();
         for (int k = a0; k < a1; ++k) {
           const int v = (int)(acc[k] & 0xFFFFFFu), idx = base + (k - a0);
           auto it = latest.find(v);
@@ -1834,18 +1936,11 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
           } else {
             latest.emplace(v, idx);
           }
-          acc_link.push_back(make_int2(first, -1));
+          acc_link[idx] = make_int2(first, -1);
         }
       }
     }
-    const size_t n = acc_p.size() - (size_t)meta[i].pacc_beg;
-    if (n > 32767) {
-      if (err) *err = "a block with more than 32767 accesses (or variables touched by its calls)";
-      delete st;
-      return nullptr;
-    }
-    meta[i].nacc = (int16_t)n;
-  }
+  });
   std::vector<int2> fin_pk(fin_slot.size()), out_pk(out_slot.size());
   // in-edge entries: {source slot, loop-entry edge or -1}
   for (size_t k = 0; k < fin_pk.size(); ++k) fin_pk[k] = make_int2(fin_slot[k], g.fin_ent[k]);
