@@ -206,9 +206,11 @@ int ompdart_analyze(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdart_re
 
 void ompdart_result_free(ompdart_result *res);
 
-/* Host results of at least 1 MiB live in page-locked memory that is kept
-   for reuse once freed (up to OMPDART_HOST_CACHE_MB, default 4096 MiB, of
-   cached blocks).  Releases every cached block; returns the bytes released. */
+/* Host results of at least 1 MiB live in memory kept for reuse once freed
+   (up to OMPDART_HOST_CACHE_MB, default 4096 MiB, of cached blocks per
+   kind): page-locked for a plan's result (ompdart_plan_fetch,
+   ompdart_analyze), pageable for batch and serving results.  Releases
+   every cached block; returns the bytes released. */
 size_t ompdart_host_cache_trim(void);
 
 /* Text of the calling thread's last error ("" if none). */

@@ -329,7 +329,7 @@ void core_view(const PlanCore &P, const int32_t *h_status, ompdart_result *v) {
   v->call_exit_live = P.dp.call_exit_live;
 }
 
-int result_copy(const ompdart_result &v, bool device, cudaStream_t s, ompdart_result **out) {
+int result_copy(const ompdart_result &v, bool pin, cudaStream_t s, ompdart_result **out) {
   *out = nullptr;
   const size_t NW = (size_t)v.n_blocks * v.n_words, SW = (size_t)v.n_call_sites * v.n_words;
   // one host block: every array at a 64-byte aligned offset
@@ -360,7 +360,7 @@ int result_copy(const ompdart_result &v, bool device, cudaStream_t s, ompdart_re
   };
   size_t total = 0;
   for (const Part &p : parts) total += (p.bytes + 63) & ~size_t(63);
-  HostBlock *blk = host_block_new(total + 64);
+  HostBlock *blk = host_block_new(total + 64, pin);
   if (!blk) return set_err(OMPDART_E_NOMEM, "host allocation failed");
   char *base = (char *)host_block_ptr(blk);
   size_t off = 0;
@@ -374,23 +374,18 @@ int result_copy(const ompdart_result &v, bool device, cudaStream_t s, ompdart_re
       continue;
     }
     *p.dst = base + off;
-    if (p.bytes && p.src) {
-      if (!device)
-        memcpy(base + off, p.src, p.bytes);
-      else if (ce == cudaSuccess)
-        ce = cudaMemcpyAsync(base + off, p.src, p.bytes, cudaMemcpyDeviceToHost, s);
-    }
+    if (p.bytes && p.src && ce == cudaSuccess)
+      ce = cudaMemcpyAsync(base + off, p.src, p.bytes, cudaMemcpyDeviceToHost, s);
     off += (p.bytes + 63) & ~size_t(63);
   }
-  if (device && ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
   if (ce != cudaSuccess) {
     host_block_release(blk);
     return cuda_err(ce, "copy of results");
   }
-  r.d2h_bytes = device ? (long long)(2 + (v.h_out ? 2 : 0) + (v.live_in ? 1 : 0)) * NW * 8 + v.n_acc +
-                             (long long)sizeof(ompdart_edge_xfer) * v.n_edge_xfers + 4ll * v.n_exits +
-                             8ll * v.n_exits * v.n_words + 4ll * ST_COUNT + 4ll * v.n_call_sites + 40ll * SW
-                       : 0;
+  r.d2h_bytes = (long long)(2 + (v.h_out ? 2 : 0) + (v.live_in ? 1 : 0)) * NW * 8 + v.n_acc +
+                (long long)sizeof(ompdart_edge_xfer) * v.n_edge_xfers + 4ll * v.n_exits + 8ll * v.n_exits * v.n_words +
+                4ll * ST_COUNT + 4ll * v.n_call_sites + 40ll * SW;
   ompdart_result *res = result_in_block(r, blk);
   host_block_release(blk);  // the result holds its own reference
   if (!res) return set_err(OMPDART_E_NOMEM, "host allocation failed");
@@ -558,7 +553,7 @@ int ompdart_plan_fetch(ompdart_plan *P, ompdart_result **out) {
   *out = nullptr;
   ompdart_result v;
   core_view(P->core, P->h_status, &v);
-  return result_copy(v, true, P->last_stream ? P->last_stream : P->stream, out);
+  return result_copy(v, true, P->last_stream ? P->last_stream : P->stream, out);  // one large block: page-locked
 }
 
 int ompdart_analyze(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdart_result **out) {

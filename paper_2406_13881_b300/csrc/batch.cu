@@ -571,7 +571,7 @@ int ompdart_batch_fetch(ompdart_batch *B, int32_t i, ompdart_result **out) {
   ompdart_result v;
   int rc = ompdart_batch_view(B, i, &v);
   if (rc) return rc;
-  return result_copy(v, true, B->last_stream, out);
+  return result_copy(v, false, B->last_stream, out);
 }
 
 int ompdart_batch_info(const ompdart_batch *B, int32_t *n_arenas, int32_t *n_solo, int32_t *launches, int32_t max,
@@ -639,7 +639,7 @@ int batch_fetch_all(ompdart_batch *B, ompdart_result **outs) {
     whole.exit_blocks = a.exit_local;
     whole.call_site_acc = a.site_local;  // access index within each CFG
     ompdart_result *host = nullptr;
-    rc = result_copy(whole, true, B->last_stream, &host);
+    rc = result_copy(whole, false, B->last_stream, &host);
     if (rc) return rc;
     HostBlock *blk = static_cast<HostBlock *>(host->host_block);
     const size_t W = a.W;

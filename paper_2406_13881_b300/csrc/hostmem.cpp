@@ -1,13 +1,18 @@
 // Host blocks that hold the arrays of host results.
 //
 // A result copied to the host lives in one block: one allocation, one DMA
-// target per array.  Blocks of at least kPinMin bytes are page-locked
-// (device->host copies then run at link speed instead of through the
-// driver's staging buffers and first-touch page faults) and, once released,
-// kept in a size-keyed cache up to a byte cap, so a caller that analyses
-// again reuses them without pinning new pages.  Smaller blocks are plain
-// heap memory.  A block is reference counted: the results of a batch are
-// views into their arena's block and the last one freed releases it.
+// target per array.  Blocks of at least kCacheMin bytes are rounded up to
+// a size class and, once released, kept per class up to a byte cap, so a
+// caller that analyses again (or a serving loop whose batches differ in
+// size) reuses memory whose pages are already there.  Two kinds:
+//   page-locked (a plan's result: one large block, copied back at link
+//     speed; pinning new pages is slow, about 1 GB/s, so only reuse pays,
+//     and freeing them waits for the device, so it happens past the cap);
+//   pageable (batches and serving: many blocks of varying size, copied
+//     through the driver's staging buffers).
+// Smaller blocks are plain heap memory.  A block is reference counted: the
+// results of a batch are views into their arena's block and the last one
+// freed releases it.
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -23,19 +28,29 @@ struct HostBlock {
   void *ptr = nullptr;
   size_t bytes = 0;
   bool pinned = false;
+  bool cached = false;  // returns to the cache of its kind when released
   std::atomic<int> refs{1};
 };
 
 namespace {
 
-constexpr size_t kPinMin = size_t(1) << 20;
+constexpr size_t kCacheMin = size_t(1) << 20;
 
 struct Cache {
   std::mutex mu;
-  std::multimap<size_t, void *> free_blocks;  // pinned, by size
-  size_t cached = 0;
+  std::multimap<size_t, void *> free_blocks[2];  // [pageable, page-locked], by size class
+  size_t cached[2] = {0, 0};
   size_t cap = 0;
 };
+
+// four classes per power of two (at most 25% over the size asked for)
+size_t size_class(size_t bytes) {
+  size_t p = kCacheMin;
+  while (2 * p < bytes) p <<= 1;
+  for (size_t m = 4; m <= 8; ++m)
+    if (p / 4 * m >= bytes) return p / 4 * m;
+  return 2 * p;
+}
 
 // never destroyed: releases may come from static destructors of callers
 Cache &cache() {
@@ -51,31 +66,35 @@ Cache &cache() {
 
 }  // namespace
 
-HostBlock *host_block_new(size_t bytes) {
+HostBlock *host_block_new(size_t bytes, bool pin) {
   HostBlock *b = new (std::nothrow) HostBlock();
   if (!b) return nullptr;
   b->bytes = bytes ? bytes : 1;
-  if (b->bytes >= kPinMin) {
+  if (b->bytes >= kCacheMin) {
     Cache &c = cache();
+    b->bytes = size_class(b->bytes);
+    b->cached = true;
     {
-      // best fit among cached blocks no more than twice the size asked for
       std::lock_guard<std::mutex> lk(c.mu);
-      auto it = c.free_blocks.lower_bound(b->bytes);
-      if (it != c.free_blocks.end() && it->first <= 2 * b->bytes) {
+      auto &fb = c.free_blocks[pin];
+      auto it = fb.find(b->bytes);
+      if (it != fb.end()) {
         b->ptr = it->second;
-        b->bytes = it->first;
-        c.cached -= it->first;
-        c.free_blocks.erase(it);
-        b->pinned = true;
+        b->pinned = pin;
+        c.cached[pin] -= it->first;
+        fb.erase(it);
         return b;
       }
     }
-    if (cudaHostAlloc(&b->ptr, b->bytes, cudaHostAllocPortable) == cudaSuccess) {
-      b->pinned = true;
-      return b;
+    if (pin) {
+      TraceScope trace("page-locked alloc", (long long)b->bytes);
+      if (cudaHostAlloc(&b->ptr, b->bytes, cudaHostAllocPortable) == cudaSuccess) {
+        b->pinned = true;
+        return b;
+      }
+      cudaGetLastError();  // fall back to pageable memory
+      b->ptr = nullptr;
     }
-    cudaGetLastError();  // fall back to pageable memory
-    b->ptr = nullptr;
   }
   b->ptr = std::malloc(b->bytes);
   if (!b->ptr) {
@@ -93,17 +112,23 @@ void host_block_ref(HostBlock *b) {
 
 void host_block_release(HostBlock *b) {
   if (!b || b->refs.fetch_sub(1, std::memory_order_acq_rel) != 1) return;
-  if (b->pinned) {
+  bool keep = false;
+  if (b->cached) {
     Cache &c = cache();
     std::lock_guard<std::mutex> lk(c.mu);
-    if (c.cached + b->bytes <= c.cap) {
-      c.free_blocks.emplace(b->bytes, b->ptr);
-      c.cached += b->bytes;
-    } else {
-      cudaFreeHost(b->ptr);
+    if (c.cached[b->pinned] + b->bytes <= c.cap) {
+      c.free_blocks[b->pinned].emplace(b->bytes, b->ptr);
+      c.cached[b->pinned] += b->bytes;
+      keep = true;
     }
-  } else {
-    std::free(b->ptr);
+  }
+  if (!keep) {
+    if (b->pinned) {
+      TraceScope trace("page-locked free", (long long)b->bytes);
+      cudaFreeHost(b->ptr);
+    } else {
+      std::free(b->ptr);
+    }
   }
   delete b;
 }
@@ -116,10 +141,13 @@ size_t ompdart_host_cache_trim(void) {
   using namespace ompdart;
   Cache &c = cache();
   std::lock_guard<std::mutex> lk(c.mu);
-  const size_t n = c.cached;
-  for (auto &kv : c.free_blocks) cudaFreeHost(kv.second);
-  c.free_blocks.clear();
-  c.cached = 0;
+  const size_t n = c.cached[0] + c.cached[1];
+  for (auto &kv : c.free_blocks[0]) std::free(kv.second);
+  for (auto &kv : c.free_blocks[1]) cudaFreeHost(kv.second);
+  for (int k = 0; k < 2; ++k) {
+    c.free_blocks[k].clear();
+    c.cached[k] = 0;
+  }
   return n;
 }
 

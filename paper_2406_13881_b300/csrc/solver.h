@@ -146,16 +146,17 @@ int core_enqueue(PlanCore *c, cudaStream_t s, Prof *pf);
 int core_finish(PlanCore *c, cudaStream_t s, int32_t *h_status, bool *rerun);
 // Device view of a core's results (h_status: the status words of its last run).
 void core_view(const PlanCore &c, const int32_t *h_status, ompdart_result *v);
-// Copy the arrays a view points at (device memory if `device`, else host)
-// into a new host result (ompdart_result_free) whose arrays share one host block.
-int result_copy(const ompdart_result &v, bool device, cudaStream_t s, ompdart_result **out);
+// Copy the device arrays a view points at into a new host result
+// (ompdart_result_free) whose arrays share one host block (page-locked if
+// `pin`), on stream s.
+int result_copy(const ompdart_result &v, bool pin, cudaStream_t s, ompdart_result **out);
 // A new host result whose arrays are v's, all inside `block` (one more
 // reference to it); NULL if the host allocation fails.
 ompdart_result *result_in_block(const ompdart_result &v, HostBlock *block);
 
 // ---- hostmem.cpp: reference-counted host blocks for host results
-// (page-locked and cached once released when large)
-HostBlock *host_block_new(size_t bytes);  // one reference; NULL on failure
+// (page-locked or pageable; cached by size class once released when large)
+HostBlock *host_block_new(size_t bytes, bool pin);  // one reference; NULL on failure
 void *host_block_ptr(HostBlock *b);
 void host_block_ref(HostBlock *b);
 void host_block_release(HostBlock *b);  // frees or caches at the last reference
