@@ -115,8 +115,9 @@ typedef struct {
   int32_t path;         /* 0 auto, 1 general sweep solver, 2 chunked scan solver   */
   int32_t chunk_target; /* blocks per chunk for the scan solver; 0 = automatic     */
   int32_t device;       /* CUDA device ordinal                                     */
-  int32_t warps_per_cta; /* warps per CTA of the scan solver's walk kernels, 1-8;
-                            0 = automatic (4, or the batch autotuner's choice)    */
+  int32_t warps_per_cta; /* warps per CTA of the scan solver's walk kernels, 1-4
+                            (larger values count as 4); 0 = automatic (4, or
+                            the batch autotuner's choice)                        */
   int32_t tune;         /* batches: nonzero = let the autotuner pick chunk_target
                            and warps_per_cta per arena (ompdart_batch_create)     */
   int32_t no_graph;     /* batches: nonzero = launch kernels directly instead of

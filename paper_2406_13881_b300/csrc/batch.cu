@@ -211,7 +211,7 @@ double time_core(PlanCore *c, cudaStream_t s, int reps) {
 }
 
 // Pick (chunk_target, wpc) for an arena of `members`: coordinate search
-// over chunk targets (16..512) at 4 warps per CTA, then over warps per CTA at the
+// over chunk targets (16..512) at 4 warps per CTA, then 2 warps per CTA at the
 // best target, each candidate a trial arena over a sample of about 2^18
 // positions (every step-th CFG), timed on the device.
 void tune_arena(Arena *a, const std::vector<int32_t> &members, std::vector<Ingest> &ing, const ompdart_cfg *cfgs,
@@ -249,7 +249,7 @@ void tune_arena(Arena *a, const std::vector<int32_t> &members, std::vector<Inges
       best_chunk = chunk;
     }
   }
-  for (int wpc : {2, 8}) {
+  for (int wpc : {2}) {
     const double t = trial(best_chunk, wpc);
     if (t < best) {
       best = t;

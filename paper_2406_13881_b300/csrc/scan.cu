@@ -45,8 +45,14 @@ constexpr int BACK = -4;       // slot id (forward in-edges): a back edge, close
 #ifndef OMPDART_SH_WORDS
 #define OMPDART_SH_WORDS 256
 #endif
+// The chain kernels are compiled for at most 4 warps per CTA and at least
+// 5 CTAs per SM: registers capped at 102 per thread, so 20 warps fit on an
+// SM (with 4 CTAs, 16 warps, the host-validity walk took 15% longer)
 #ifndef OMPDART_CHAIN_MIN_CTAS
-#define OMPDART_CHAIN_MIN_CTAS 1
+#define OMPDART_CHAIN_MIN_CTAS 5
+#endif
+#ifndef OMPDART_MAX_WPC
+#define OMPDART_MAX_WPC 4  // warps per CTA a chain kernel is compiled for at most
 #endif
 constexpr int SH_WORDS = OMPDART_SH_WORDS;  // shared-memory words per warp for slots
 constexpr int WPC = 4;         // warps per CTA of the chain kernels
@@ -646,12 +652,12 @@ __device__ __forceinline__ void st_word(uint64_t *plane, size_t row, int W, int 
 }
 
 // shared memory per warp (words):
-//   slots [nsh][np][64] | mask table [2][2*np][64] | kill sets 128 | window
+//   slots [nsh][np][64] | mask table [2][2*np][64] | window | kill sets 128 (loop masks only)
 // each part a multiple of 16 words (128 B): slots and masks are read and
 // written as 16-byte ulonglong2 and must stay 16-byte aligned
 constexpr size_t WIN_WORDS = ((sizeof(Win) + 127) / 128) * 16;
-__host__ __device__ inline size_t warp_smem_words(int nsh, int np) {
-  return (size_t)nsh * np * 64 + (size_t)4 * np * 64 + 128 + WIN_WORDS;
+__host__ __device__ inline size_t warp_smem_words(int nsh, int np, bool kill) {
+  return (size_t)nsh * np * 64 + (size_t)4 * np * 64 + WIN_WORDS + (kill ? 128 : 0);
 }
 static_assert(WIN_WORDS % 16 == 0 && WIN_WORDS * 8 >= sizeof(Win), "window layout");
 static_assert(alignof(Win) <= 16, "window alignment");
@@ -660,14 +666,14 @@ struct WarpMem {
   uint64_t *slots, *tbl, *kill;
   Win *win;
 };
-template <int NP>
+template <int NP, bool KILL>
 __device__ __forceinline__ WarpMem carve(uint64_t *smem, int warp_in_cta, int nsh) {
-  uint64_t *b = smem + (size_t)warp_in_cta * warp_smem_words(nsh, NP);
+  uint64_t *b = smem + (size_t)warp_in_cta * warp_smem_words(nsh, NP, KILL);
   WarpMem m;
   m.slots = b;
   m.tbl = b + (size_t)nsh * NP * 64;
-  m.kill = m.tbl + 4 * NP * 64;
-  m.win = reinterpret_cast<Win *>(m.kill + 128);
+  m.win = reinterpret_cast<Win *>(m.tbl + 4 * NP * 64);
+  m.kill = KILL ? m.tbl + 4 * NP * 64 + WIN_WORDS : nullptr;
   return m;
 }
 
@@ -1013,11 +1019,12 @@ __device__ __forceinline__ int next_item(const ScanDev &sd, int qslot) {
 // Persistent forward chain: each warp takes items (longest chunks first)
 // from the launch's work queue until none is left.
 template <int PH>
-__global__ void __launch_bounds__(256, OMPDART_CHAIN_MIN_CTAS) k_fwd_chain(DevPlan p, ScanDev sd, int qslot) {
+__global__ void __launch_bounds__(32 * OMPDART_MAX_WPC, OMPDART_CHAIN_MIN_CTAS)
+    k_fwd_chain(DevPlan p, ScanDev sd, int qslot) {
   extern __shared__ __align__(16) uint64_t smem[];
   const int warp_in_cta = threadIdx.x >> 5;
   const int gw = blockIdx.x * (blockDim.x >> 5) + warp_in_cta;
-  const WarpMem wm = carve<2>(smem, warp_in_cta, sd.sh_slots);
+  const WarpMem wm = carve<2, false>(smem, warp_in_cta, sd.sh_slots);
   uint64_t *spill = sd.spill + (size_t)gw * sd.spill_stride;
   const int n_items = sd.C * sd.G;
   for (int item = next_item(sd, qslot); item < n_items; item = next_item(sd, qslot)) {
@@ -1258,12 +1265,13 @@ __device__ __forceinline__ void lant_walk(const DevPlan &p, const ScanDev &sd, c
 // persistent backward chain (same work queue scheme as the forward one);
 // the loop-mask walks take one loop per item
 template <int MODE>
-__global__ void __launch_bounds__(256, OMPDART_CHAIN_MIN_CTAS) k_bwd_chain(DevPlan p, ScanDev sd, int qslot) {
+__global__ void __launch_bounds__(32 * OMPDART_MAX_WPC, OMPDART_CHAIN_MIN_CTAS)
+    k_bwd_chain(DevPlan p, ScanDev sd, int qslot) {
   constexpr int NP = BwdPlanes<MODE>::NP;
   extern __shared__ __align__(16) uint64_t smem[];
   const int warp_in_cta = threadIdx.x >> 5;
   const int gw = blockIdx.x * (blockDim.x >> 5) + warp_in_cta;
-  const WarpMem wm = carve<NP>(smem, warp_in_cta, sd.sh_slots);
+  const WarpMem wm = carve<NP, MODE == M_LANT>(smem, warp_in_cta, sd.sh_slots);
   uint64_t *spill = sd.spill + (size_t)gw * sd.spill_stride;
   const int n_items = (MODE == M_LANT ? sd.n_loops : sd.C) * sd.G;
   for (int item = next_item(sd, qslot); item < n_items; item = next_item(sd, qslot)) {
@@ -1733,21 +1741,21 @@ static bool scan_set_streams(ScanState *st) {
 
 namespace {
 // warps of one CTA of a chain kernel: 1..8, default 4
-int clamp_wpc(int wpc) { return wpc <= 0 ? WPC : std::min(8, std::max(1, wpc)); }
+int clamp_wpc(int wpc) { return wpc <= 0 ? WPC : std::min(OMPDART_MAX_WPC, std::max(1, wpc)); }
 
 // Shape of a persistent chain launch: as many CTAs as can be resident at
 // once (never more than the items need), slots in shared memory up to
 // SH_WORDS words per plane group.
 template <class K>
-ChainShape chain_shape(K kern, int need, int np, int wpc, int n_items, int n_sm) {
+ChainShape chain_shape(K kern, int need, int np, bool kill, int wpc, int n_items, int n_sm) {
   ChainShape c;
   c.wpc = wpc;
   c.sh_slots = std::min(need, SH_WORDS / (64 * np));
-  c.smem = (size_t)wpc * warp_smem_words(c.sh_slots, np) * 8;
+  c.smem = (size_t)wpc * warp_smem_words(c.sh_slots, np, kill) * 8;
   // the attribute belongs to the kernel, not to this plan: always the
-  // largest size any plan launches with (8 warps, every slot in shared
+  // largest size any plan launches with (most warps, every slot in shared
   // memory), so plans alive at the same time never shrink it for each other
-  set_smem(kern, (size_t)8 * warp_smem_words(SH_WORDS / (64 * np), np) * 8);
+  set_smem(kern, (size_t)OMPDART_MAX_WPC * warp_smem_words(SH_WORDS / (64 * np), np, kill) * 8);
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpc, c.smem) != cudaSuccess || per_sm < 1)
     per_sm = 1;
@@ -2005,11 +2013,12 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     int dev = 0, n_sm = 148;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     const int items = C * G;
-    st->shape[CK_BSUM] = chain_shape(k_bwd_chain<M_SUM>, st->bslots, BwdPlanes<M_SUM>::NP, wpc, items, n_sm);
-    st->shape[CK_BLANT] = chain_shape(k_bwd_chain<M_LANT>, st->bslots, 2, wpc, std::max(1, g.L) * G, n_sm);
-    st->shape[CK_FSUM] = chain_shape(k_fwd_chain<K_HP>, st->fslots, 2, wpc, items, n_sm);
-    chain_shape(k_fwd_chain<K_D>, st->fslots, 2, wpc, items, n_sm);
-    chain_shape(k_fwd_chain<K_H>, st->fslots, 2, wpc, items, n_sm);
+    st->shape[CK_BSUM] =
+        chain_shape(k_bwd_chain<M_SUM>, st->bslots, BwdPlanes<M_SUM>::NP, false, wpc, items, n_sm);
+    st->shape[CK_BLANT] = chain_shape(k_bwd_chain<M_LANT>, st->bslots, 2, true, wpc, std::max(1, g.L) * G, n_sm);
+    st->shape[CK_FSUM] = chain_shape(k_fwd_chain<K_HP>, st->fslots, 2, false, wpc, items, n_sm);
+    chain_shape(k_fwd_chain<K_D>, st->fslots, 2, false, wpc, items, n_sm);
+    chain_shape(k_fwd_chain<K_H>, st->fslots, 2, false, wpc, items, n_sm);
   }
   int max_warps = 1;
   for (const ChainShape &c : st->shape) max_warps = std::max(max_warps, c.grid * c.wpc);

@@ -174,7 +174,7 @@ def test_autotuned_batch():
     b = _native.Batch(cfgs, keep_states=True, tune=True)
     info = b.info()
     for a in info["arenas"]:
-        assert a["chunk_target"] in (16, 32, 64, 128, 256, 512) and a["warps_per_cta"] in (2, 4, 8)
+        assert a["chunk_target"] in (16, 32, 64, 128, 256, 512) and a["warps_per_cta"] in (2, 4)
     b.run()
     assert (b.sync() == 0).all()
     for i, g in enumerate(cfgs):
