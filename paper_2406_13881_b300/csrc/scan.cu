@@ -42,19 +42,31 @@ namespace {
 constexpr int CARRY = -2;      // slot id: the chunk's incoming carry
 constexpr int PREV = -3;       // slot id: the value of the position walked just before
 constexpr int BACK = -4;       // slot id (forward in-edges): a back edge, closed at the loop's end
-#ifndef OMPDART_SH_WORDS
-#define OMPDART_SH_WORDS 256
+// Occupancy of the chain kernels (latency-bound walks: more warps per SM
+// help until registers spill).  They are compiled for at most 4 warps per
+// CTA and at least 6 (forward) / 5 (backward) CTAs per SM, which caps
+// registers at 85 and 102 per thread, and keep 128 / 256 shared-memory
+// words per warp for slots, so 24 / 20 warps fit on an SM.  Measured on the
+// 2^20-block CFG: 16 warps per SM made the host-validity walk 20% slower,
+// 7 forward CTAs (73 registers, spilling) 20% slower too; the liveness walk
+// loses with 6 CTAs (85 registers) or with no slot in shared memory.
+#ifndef OMPDART_FWD_SH_WORDS
+#define OMPDART_FWD_SH_WORDS 128
 #endif
-// The chain kernels are compiled for at most 4 warps per CTA and at least
-// 5 CTAs per SM: registers capped at 102 per thread, so 20 warps fit on an
-// SM (with 4 CTAs, 16 warps, the host-validity walk took 15% longer)
-#ifndef OMPDART_CHAIN_MIN_CTAS
-#define OMPDART_CHAIN_MIN_CTAS 5
+#ifndef OMPDART_BWD_SH_WORDS
+#define OMPDART_BWD_SH_WORDS 256
+#endif
+#ifndef OMPDART_FWD_MIN_CTAS
+#define OMPDART_FWD_MIN_CTAS 6
+#endif
+#ifndef OMPDART_BWD_MIN_CTAS
+#define OMPDART_BWD_MIN_CTAS 5
 #endif
 #ifndef OMPDART_MAX_WPC
 #define OMPDART_MAX_WPC 4  // warps per CTA a chain kernel is compiled for at most
 #endif
-constexpr int SH_WORDS = OMPDART_SH_WORDS;  // shared-memory words per warp for slots
+constexpr int FWD_SH_WORDS = OMPDART_FWD_SH_WORDS;  // shared-memory words per warp for slots
+constexpr int BWD_SH_WORDS = OMPDART_BWD_SH_WORDS;
 constexpr int WPC = 4;         // warps per CTA of the chain kernels
 constexpr int MAX_DEPTH = 31;  // loop nesting depth the chain handles
 // bound on loop re-runs per chunk walk: each loop of a reducible CFG needs
@@ -651,13 +663,18 @@ __device__ __forceinline__ void st_word(uint64_t *plane, size_t row, int W, int 
   if (w < W) plane[row * W + w] = v;
 }
 
+// Rows of one mask table (64 words each): the affine walks keep [set,
+// clear] of the local plane and one `clear' row shared by the coefficient
+// planes; the loop-mask walk keeps [set, clear] per plane (H, D).
+__host__ __device__ constexpr int mask_rows(int np, bool lant) { return lant ? 2 * np : 3; }
+
 // shared memory per warp (words):
-//   slots [nsh][np][64] | mask table [2][2*np][64] | window | kill sets 128 (loop masks only)
+//   slots [nsh][np][64] | mask tables [2][rows][64] | window | kill sets 128 (loop masks only)
 // each part a multiple of 16 words (128 B): slots and masks are read and
 // written as 16-byte ulonglong2 and must stay 16-byte aligned
 constexpr size_t WIN_WORDS = ((sizeof(Win) + 127) / 128) * 16;
-__host__ __device__ inline size_t warp_smem_words(int nsh, int np, bool kill) {
-  return (size_t)nsh * np * 64 + (size_t)4 * np * 64 + WIN_WORDS + (kill ? 128 : 0);
+__host__ __device__ inline size_t warp_smem_words(int nsh, int np, bool lant) {
+  return (size_t)nsh * np * 64 + (size_t)2 * mask_rows(np, lant) * 64 + WIN_WORDS + (lant ? 128 : 0);
 }
 static_assert(WIN_WORDS % 16 == 0 && WIN_WORDS * 8 >= sizeof(Win), "window layout");
 static_assert(alignof(Win) <= 16, "window alignment");
@@ -672,8 +689,8 @@ __device__ __forceinline__ WarpMem carve(uint64_t *smem, int warp_in_cta, int ns
   WarpMem m;
   m.slots = b;
   m.tbl = b + (size_t)nsh * NP * 64;
-  m.win = reinterpret_cast<Win *>(m.tbl + 4 * NP * 64);
-  m.kill = KILL ? m.tbl + 4 * NP * 64 + WIN_WORDS : nullptr;
+  m.win = reinterpret_cast<Win *>(m.tbl + 2 * mask_rows(NP, KILL) * 64);
+  m.kill = KILL ? m.tbl + 2 * mask_rows(NP, KILL) * 64 + WIN_WORDS : nullptr;
   return m;
 }
 
@@ -686,10 +703,11 @@ __device__ __forceinline__ WarpMem carve(uint64_t *smem, int warp_in_cta, int ns
 // masks while the current value is still being computed.
 //   liveness (AntH | AntD share the kill "any write", so their union is one
 //   problem): local: read in either space first -> set, else write -> clear;
-//   coefficient: both -> clear.  LANT: separate H and D planes, and the
+//   coefficients: both -> clear.  LANT: separate H and D planes, and the
 //   block's kills ORed into `kill` ([H|D][64]).
 //   forward planes (stale sets): local: GEN -> clear (valid), KILL -> set
 //   (stale); coefficient: both -> clear.
+// Rows: [set, clear, coefficient clear], LANT [H set, H clear, D set, D clear].
 template <int PH, int MODE>
 __device__ __forceinline__ void prep_masks(const ScanDev &sd, const Win &w, const WinRegs &wr, const PosMeta &m,
                                            const Lane &L, uint64_t *tb, uint64_t *kill) {
@@ -710,39 +728,37 @@ __device__ __forceinline__ void prep_masks(const ScanDev &sd, const Win &w, cons
       } else {
         const bool ue = uh || ud;
         if (ue) atomicOr(t, bit); else if (df) atomicOr(t + 64, bit);
-        if (MODE == M_SUM && (ue || df)) {
-          atomicOr(t + 192, bit);  // coefficient of the carry
-          atomicOr(t + 320, bit);  // coefficient of the outermost open loop's header value
-        }
+        if (MODE == M_SUM && (ue || df)) atomicOr(t + 128, bit);
       }
     } else {
       const uint32_t GEN = PH == K_D ? R_GD : R_GH, KILL = PH == K_D ? R_KD : R_KH;
       if (rc & GEN) atomicOr(t + 64, bit); else if (rc & KILL) atomicOr(t, bit);
-      if (MODE == M_SUM && (rc & (GEN | KILL))) atomicOr(t + 192, bit);
+      if (MODE == M_SUM && (rc & (GEN | KILL))) atomicOr(t + 128, bit);
     }
   }
 }
 
 // apply the lane's words of the prepared masks and clear them
-template <int NP>
+template <int NP, bool LANT>
 __device__ __forceinline__ void take_masks(uint64_t *tb, int lane, uint64_t (&z)[NP][2]) {
+  ulonglong2 *row = reinterpret_cast<ulonglong2 *>(tb) + lane;  // row r at row[32 * r]
 #pragma unroll
   for (int pl = 0; pl < NP; ++pl) {
-    ulonglong2 *st = reinterpret_cast<ulonglong2 *>(tb + (2 * pl) * 64 + 2 * lane);
-    ulonglong2 *cl = reinterpret_cast<ulonglong2 *>(tb + (2 * pl + 1) * 64 + 2 * lane);
-    const ulonglong2 a = *st, b = *cl;
+    const int rs = LANT ? 2 * pl : (pl ? -1 : 0), rc = LANT ? 2 * pl + 1 : (pl ? 2 : 1);
+    const ulonglong2 a = rs >= 0 ? row[32 * rs] : make_ulonglong2(0ull, 0ull), b = row[32 * rc];
     z[pl][0] = (z[pl][0] & ~b.x) | a.x;
     z[pl][1] = (z[pl][1] & ~b.y) | a.y;
-    *st = make_ulonglong2(0ull, 0ull);
-    *cl = make_ulonglong2(0ull, 0ull);
   }
+#pragma unroll
+  for (int r = 0; r < mask_rows(NP, LANT); ++r) row[32 * r] = make_ulonglong2(0ull, 0ull);
 }
 
 // clear the lane's words of a prepared table that will not be used
-template <int NP>
+template <int NP, bool LANT>
 __device__ __forceinline__ void drop_masks(uint64_t *tb, int lane) {
 #pragma unroll
-  for (int q = 0; q < 2 * NP; ++q) *reinterpret_cast<ulonglong2 *>(tb + q * 64 + 2 * lane) = make_ulonglong2(0ull, 0ull);
+  for (int r = 0; r < mask_rows(NP, LANT); ++r)
+    *reinterpret_cast<ulonglong2 *>(tb + r * 64 + 2 * lane) = make_ulonglong2(0ull, 0ull);
 }
 
 // Append the nonzero words of one edge's transfers to the warp's record
@@ -842,10 +858,10 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
   int depth = 0;
   uint64_t z[NP][2], zo[NP][2], pv[NP][2] = {};
   int top_pend = -1;  // end of the innermost open loop (warp-uniform)
-  constexpr int TBW = 2 * NP * 64;  // words of one mask table
+  constexpr int TBW = mask_rows(NP, false) * 64;  // words of one mask table
   int pbuf = 0, prep_pos = -1;      // table holding the built masks of prep_pos
-  drop_masks<NP>(wm.tbl, L.lane);   // shared memory starts undefined: the
-  drop_masks<NP>(wm.tbl + TBW, L.lane);  // masks are built by ORing into zeros
+  drop_masks<NP, false>(wm.tbl, L.lane);   // shared memory starts undefined: the
+  drop_masks<NP, false>(wm.tbl + TBW, L.lane);  // masks are built by ORing into zeros
   __syncwarp();
   uint64_t din[2] = {0, 0}, lv[2] = {0, 0};
   uint64_t pdin[2] = {0, 0}, plv[2] = {0, 0};
@@ -855,7 +871,7 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
     const PosMeta m = w.meta[i - wr.mbase];
     if (prep_pos != i) {  // masks of this position not built yet (start, window edge)
       if (prep_pos >= 0) {
-        drop_masks<NP>(wm.tbl + pbuf * TBW, L.lane);
+        drop_masks<NP, false>(wm.tbl + pbuf * TBW, L.lane);
         __syncwarp();
       }
       prep_masks<PH, MODE>(sd, w, wr, m, L, wm.tbl + pbuf * TBW, wm.kill);
@@ -928,7 +944,7 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
 #pragma unroll
     for (int pl = 0; pl < NP; ++pl) { zo[pl][0] = z[pl][0]; zo[pl][1] = z[pl][1]; }
     __syncwarp();
-    take_masks<NP>(wm.tbl + pbuf * TBW, L.lane, zo);
+    take_masks<NP, false>(wm.tbl + pbuf * TBW, L.lane, zo);
     // build the next position's masks while this value is finished
     if (i + 1 < wr.we) {
       pbuf ^= 1;
@@ -1019,7 +1035,7 @@ __device__ __forceinline__ int next_item(const ScanDev &sd, int qslot) {
 // Persistent forward chain: each warp takes items (longest chunks first)
 // from the launch's work queue until none is left.
 template <int PH>
-__global__ void __launch_bounds__(32 * OMPDART_MAX_WPC, OMPDART_CHAIN_MIN_CTAS)
+__global__ void __launch_bounds__(32 * OMPDART_MAX_WPC, OMPDART_FWD_MIN_CTAS)
     k_fwd_chain(DevPlan p, ScanDev sd, int qslot) {
   extern __shared__ __align__(16) uint64_t smem[];
   const int warp_in_cta = threadIdx.x >> 5;
@@ -1061,10 +1077,11 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
   int lwm = e;  // lowest position walked so far
   int top_ph = -1;  // header of the innermost open loop (warp-uniform)
   uint64_t pv[NP][2] = {};
-  constexpr int TBW = 2 * NP * 64;  // words of one mask table
+  constexpr bool LANT = MODE == M_LANT;
+  constexpr int TBW = mask_rows(NP, LANT) * 64;  // words of one mask table
   int pbuf = 0, prep_pos = -1;      // table holding the built masks of prep_pos
-  drop_masks<NP>(wm.tbl, L.lane);   // shared memory starts undefined: the
-  drop_masks<NP>(wm.tbl + TBW, L.lane);  // masks are built by ORing into zeros
+  drop_masks<NP, LANT>(wm.tbl, L.lane);   // shared memory starts undefined: the
+  drop_masks<NP, LANT>(wm.tbl + TBW, L.lane);  // masks are built by ORing into zeros
   __syncwarp();
   int i = e - 1;
   while (i >= s) {
@@ -1072,7 +1089,7 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
     const PosMeta m = w.meta[i - wr.mbase];
     if (prep_pos != i) {
       if (prep_pos >= 0) {
-        drop_masks<NP>(wm.tbl + pbuf * TBW, L.lane);
+        drop_masks<NP, LANT>(wm.tbl + pbuf * TBW, L.lane);
         __syncwarp();
       }
       prep_masks<K_ANT, MODE>(sd, w, wr, m, L, wm.tbl + pbuf * TBW, wm.kill);
@@ -1132,7 +1149,7 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
       }
     }
     __syncwarp();
-    take_masks<NP>(wm.tbl + pbuf * TBW, L.lane, z);
+    take_masks<NP, LANT>(wm.tbl + pbuf * TBW, L.lane, z);
     if (i - 1 >= wr.ws && i - 1 >= s) {
       pbuf ^= 1;
       prep_masks<K_ANT, MODE>(sd, w, wr, w.meta[i - 1 - wr.mbase], L, wm.tbl + pbuf * TBW, wm.kill);
@@ -1265,7 +1282,7 @@ __device__ __forceinline__ void lant_walk(const DevPlan &p, const ScanDev &sd, c
 // persistent backward chain (same work queue scheme as the forward one);
 // the loop-mask walks take one loop per item
 template <int MODE>
-__global__ void __launch_bounds__(32 * OMPDART_MAX_WPC, OMPDART_CHAIN_MIN_CTAS)
+__global__ void __launch_bounds__(32 * OMPDART_MAX_WPC, OMPDART_BWD_MIN_CTAS)
     k_bwd_chain(DevPlan p, ScanDev sd, int qslot) {
   constexpr int NP = BwdPlanes<MODE>::NP;
   extern __shared__ __align__(16) uint64_t smem[];
@@ -1745,17 +1762,17 @@ int clamp_wpc(int wpc) { return wpc <= 0 ? WPC : std::min(OMPDART_MAX_WPC, std::
 
 // Shape of a persistent chain launch: as many CTAs as can be resident at
 // once (never more than the items need), slots in shared memory up to
-// SH_WORDS words per plane group.
+// sh_words words per warp.
 template <class K>
-ChainShape chain_shape(K kern, int need, int np, bool kill, int wpc, int n_items, int n_sm) {
+ChainShape chain_shape(K kern, int need, int np, bool kill, int sh_words, int wpc, int n_items, int n_sm) {
   ChainShape c;
   c.wpc = wpc;
-  c.sh_slots = std::min(need, SH_WORDS / (64 * np));
+  c.sh_slots = std::min(need, sh_words / (64 * np));
   c.smem = (size_t)wpc * warp_smem_words(c.sh_slots, np, kill) * 8;
   // the attribute belongs to the kernel, not to this plan: always the
   // largest size any plan launches with (most warps, every slot in shared
   // memory), so plans alive at the same time never shrink it for each other
-  set_smem(kern, (size_t)OMPDART_MAX_WPC * warp_smem_words(SH_WORDS / (64 * np), np, kill) * 8);
+  set_smem(kern, (size_t)OMPDART_MAX_WPC * warp_smem_words(sh_words / (64 * np), np, kill) * 8);
   int per_sm = 0;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpc, c.smem) != cudaSuccess || per_sm < 1)
     per_sm = 1;
@@ -2013,21 +2030,22 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     int dev = 0, n_sm = 148;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     const int items = C * G;
-    st->shape[CK_BSUM] =
-        chain_shape(k_bwd_chain<M_SUM>, st->bslots, BwdPlanes<M_SUM>::NP, false, wpc, items, n_sm);
-    st->shape[CK_BLANT] = chain_shape(k_bwd_chain<M_LANT>, st->bslots, 2, true, wpc, std::max(1, g.L) * G, n_sm);
-    st->shape[CK_FSUM] = chain_shape(k_fwd_chain<K_HP>, st->fslots, 2, false, wpc, items, n_sm);
-    chain_shape(k_fwd_chain<K_D>, st->fslots, 2, false, wpc, items, n_sm);
-    chain_shape(k_fwd_chain<K_H>, st->fslots, 2, false, wpc, items, n_sm);
+    const int NPS = BwdPlanes<M_SUM>::NP;
+    st->shape[CK_BSUM] = chain_shape(k_bwd_chain<M_SUM>, st->bslots, NPS, false, BWD_SH_WORDS, wpc, items, n_sm);
+    st->shape[CK_BLANT] =
+        chain_shape(k_bwd_chain<M_LANT>, st->bslots, 2, true, BWD_SH_WORDS, wpc, std::max(1, g.L) * G, n_sm);
+    st->shape[CK_FSUM] = chain_shape(k_fwd_chain<K_HP>, st->fslots, 2, false, FWD_SH_WORDS, wpc, items, n_sm);
+    chain_shape(k_fwd_chain<K_D>, st->fslots, 2, false, FWD_SH_WORDS, wpc, items, n_sm);
+    chain_shape(k_fwd_chain<K_H>, st->fslots, 2, false, FWD_SH_WORDS, wpc, items, n_sm);
   }
   int max_warps = 1;
   for (const ChainShape &c : st->shape) max_warps = std::max(max_warps, c.grid * c.wpc);
   // slots beyond those a kernel keeps in shared memory spill to a per-warp area
   {
-    const int fwd = std::max(0, st->fslots - SH_WORDS / (64 * 2)) * 2 * 64;
-    const int lant = std::max(0, st->bslots - SH_WORDS / (64 * 2)) * 2 * 64;
+    const int fwd = std::max(0, st->fslots - st->shape[CK_FSUM].sh_slots) * 2 * 64;
+    const int lant = std::max(0, st->bslots - st->shape[CK_BLANT].sh_slots) * 2 * 64;
     const int NPS = BwdPlanes<M_SUM>::NP;
-    const int live = std::max(0, st->bslots - SH_WORDS / (64 * NPS)) * NPS * 64;
+    const int live = std::max(0, st->bslots - st->shape[CK_BSUM].sh_slots) * NPS * 64;
     sd.spill_stride = std::max({64, fwd, lant, live});
   }
   st->spill_region = (size_t)std::max(1, sd.spill_stride) * max_warps;
