@@ -166,8 +166,10 @@ struct ScanDev {
   // at the loop's end the header's fixed point (relative to the enclosing
   // level) goes to hdr_*, and the resolve composes up the loop tree
   uint64_t *hdr_g, *hdr_p;      // [L][W] header value, plane at 0 / at top of the enclosing level
+  uint64_t *hdr_ag, *hdr_ap;    // [L][W] the same composed up the loop tree: a pair of the chunk's carry
   const int32_t *pos_loop;      // [M] innermost loop holding each position, or -1
   const int32_t *loop_up;       // [L] enclosing loop, or -1
+  const int32_t *loop_root;     // [L] outermost loop holding it
   const int32_t *src_pos;       // [K] position of each loop-entry edge's source
   const int2 *emit_rng;         // [n_emit] position ranges of the emission items (within one chunk)
   int n_emit;
@@ -1371,12 +1373,27 @@ __global__ void __launch_bounds__(256) k_local_summary_pos(ScanDev sd) {
 // --------------------------------------------------------------------------------------
 enum ResolveKind { RV_LIVE = 0, RV_VALID = 1 };  // liveness as is; stale sets to valid sets
 
+// Each loop's header value composed up the loop tree (maps compose
+// associatively): a pair of the chunk's carry, one thread per (loop, word).
+__global__ void k_loop_abs(DevPlan p, ScanDev sd) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int W = p.W;
+  if (t >= (long long)p.L * W) return;
+  const int l = (int)(t / W), w = (int)(t % W);
+  uint64_t g = sd.hdr_g[t], q = sd.hdr_p[t];
+  for (int a = sd.loop_up[l]; a >= 0; a = sd.loop_up[a])
+    compose_pair(g, q, sd.hdr_g[(size_t)a * W + w], sd.hdr_p[(size_t)a * W + w]);
+  sd.hdr_ag[t] = g;
+  sd.hdr_ap[t] = q;
+}
+
 // out[b] = G[b] | (carry[chunk] & P[b]), converted for RV_VALID to ~x & top
 // (the CFG's valid-variable mask).  A forward (RV_VALID) pair is relative
 // to the header value of the innermost loop holding the position: it is
-// first composed with the header values up the loop tree.  A liveness pair
-// inside a loop first takes in its outermost loop's header value A
-// through PA (G |= A_G & PA, P |= A_P & PA).  A thread takes
+// first composed with that header's value as a pair of the carry
+// (k_loop_abs).  A liveness pair inside a loop first takes in its
+// outermost loop's header value A through PA (G |= A_G & PA,
+// P |= A_P & PA).  A thread takes
 // two consecutive words of a row (16-byte accesses when W is even); the
 // grid strides over (position, word pair).
 template <int KIND>
@@ -1393,22 +1410,21 @@ __global__ void __launch_bounds__(256) k_resolve(DevPlan p, ScanDev sd, const ui
     if ((W & 1) == 0) {
       ulonglong2 g = *reinterpret_cast<const ulonglong2 *>(G + o);
       ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(P + o);
-      if (KIND == RV_LIVE && sd.pos_loop[i] >= 0) {
-        int l = sd.pos_loop[i];
-        while (sd.loop_up[l] >= 0) l = sd.loop_up[l];
+      const int pl = sd.pos_loop[i];
+      if (KIND == RV_LIVE && pl >= 0) {
+        const int l = sd.loop_root[pl];
         const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(sd.pair_a + o);
         const ulonglong2 h0 = *reinterpret_cast<const ulonglong2 *>(sd.hdrl_g + (size_t)l * W + w);
         const ulonglong2 h1 = *reinterpret_cast<const ulonglong2 *>(sd.hdrl_p + (size_t)l * W + w);
         g = make_ulonglong2(g.x | (h0.x & a.x), g.y | (h0.y & a.y));
         q = make_ulonglong2(q.x | (h1.x & a.x), q.y | (h1.y & a.y));
       }
-      if (KIND == RV_VALID)
-        for (int l = sd.pos_loop[i]; l >= 0; l = sd.loop_up[l]) {
-          const ulonglong2 h0 = *reinterpret_cast<const ulonglong2 *>(sd.hdr_g + (size_t)l * W + w);
-          const ulonglong2 h1 = *reinterpret_cast<const ulonglong2 *>(sd.hdr_p + (size_t)l * W + w);
-          compose_pair(g.x, q.x, h0.x, h1.x);
-          compose_pair(g.y, q.y, h0.y, h1.y);
-        }
+      if (KIND == RV_VALID && pl >= 0) {
+        const ulonglong2 h0 = *reinterpret_cast<const ulonglong2 *>(sd.hdr_ag + (size_t)pl * W + w);
+        const ulonglong2 h1 = *reinterpret_cast<const ulonglong2 *>(sd.hdr_ap + (size_t)pl * W + w);
+        compose_pair(g.x, q.x, h0.x, h1.x);
+        compose_pair(g.y, q.y, h0.y, h1.y);
+      }
       const ulonglong2 k = *reinterpret_cast<const ulonglong2 *>(sd.carry + oc);
       ulonglong2 x = make_ulonglong2(g.x | (k.x & q.x), g.y | (k.y & q.y));
       if (KIND == RV_VALID) x = make_ulonglong2(~x.x & tp[0], ~x.y & tp[1]);
@@ -1416,16 +1432,15 @@ __global__ void __launch_bounds__(256) k_resolve(DevPlan p, ScanDev sd, const ui
     } else {
       for (int u = 0; u < 2 && w + u < W; ++u) {
         uint64_t g = G[o + u], q = P[o + u];
-        if (KIND == RV_LIVE && sd.pos_loop[i] >= 0) {
-          int l = sd.pos_loop[i];
-          while (sd.loop_up[l] >= 0) l = sd.loop_up[l];
+        const int pl = sd.pos_loop[i];
+        if (KIND == RV_LIVE && pl >= 0) {
+          const int l = sd.loop_root[pl];
           const uint64_t a = sd.pair_a[o + u];
           g |= sd.hdrl_g[(size_t)l * W + w + u] & a;
           q |= sd.hdrl_p[(size_t)l * W + w + u] & a;
         }
-        if (KIND == RV_VALID)
-          for (int l = sd.pos_loop[i]; l >= 0; l = sd.loop_up[l])
-            compose_pair(g, q, sd.hdr_g[(size_t)l * W + w + u], sd.hdr_p[(size_t)l * W + w + u]);
+        if (KIND == RV_VALID && pl >= 0)
+          compose_pair(g, q, sd.hdr_ag[(size_t)pl * W + w + u], sd.hdr_ap[(size_t)pl * W + w + u]);
         const uint64_t x = g | (sd.carry[oc + u] & q);
         out[o + u] = KIND == RV_LIVE ? x : ~x & tp[u];
       }
@@ -1441,8 +1456,8 @@ __global__ void k_resolve_src(DevPlan p, ScanDev sd, uint64_t *out) {
   const int k = (int)(t / W), w = (int)(t % W);
   const int i = sd.src_pos[k], c = sd.pos_chunk[i];
   uint64_t g = sd.src_g[t], q = sd.src_p[t];
-  for (int l = sd.pos_loop[i]; l >= 0; l = sd.loop_up[l])
-    compose_pair(g, q, sd.hdr_g[(size_t)l * W + w], sd.hdr_p[(size_t)l * W + w]);
+  const int l = sd.pos_loop[i];
+  if (l >= 0) compose_pair(g, q, sd.hdr_ag[(size_t)l * W + w], sd.hdr_ap[(size_t)l * W + w]);
   const uint64_t x = g | (sd.carry[(size_t)c * W + w] & q);
   out[t] = ~x & p.top[(size_t)sd.chunks[c].cfg * W + w];
 }
@@ -2089,8 +2104,16 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     for (int i = 0; i < g.M; ++i) pos_loop[i] = g.inner_loop[g.order[i]];
     chk(sd.pos_loop = st->up(pos_loop));
     chk(sd.loop_up = st->up(g.loop_parent));
+    std::vector<int32_t> loop_root(g.L);
+    for (int l = 0; l < g.L; ++l) {  // parents come first (headers in walk order)
+      const int up = g.loop_parent[l];
+      loop_root[l] = up < 0 ? l : loop_root[up];
+    }
+    chk(sd.loop_root = st->up(loop_root));
     chk(sd.hdr_g = st->alloc<uint64_t>((size_t)std::max(1, g.L) * W));
     chk(sd.hdr_p = st->alloc<uint64_t>((size_t)std::max(1, g.L) * W));
+    chk(sd.hdr_ag = st->alloc<uint64_t>((size_t)std::max(1, g.L) * W));
+    chk(sd.hdr_ap = st->alloc<uint64_t>((size_t)std::max(1, g.L) * W));
     chk(sd.hdrl_g = st->alloc<uint64_t>((size_t)std::max(1, g.L) * W));
     chk(sd.hdrl_p = st->alloc<uint64_t>((size_t)std::max(1, g.L) * W));
     const size_t NW = (size_t)g.N * W, KW = (size_t)std::max(1, g.K) * W;
@@ -2221,6 +2244,10 @@ int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *p
   chain_launch(k_fwd_chain<K_HP>, st->shape[CK_FSUM], p, sq, 3, s); ++n;
   PROF("fwd_scan");
   k_scan_carry<<<W, SCAN_T, 0, s>>>(sq, W, 0, init); ++n;
+  if (p.L) {
+    PROF("loop_abs");
+    k_loop_abs<<<grid_of((long long)p.L * W, 256), 256, 0, s>>>(p, sq); ++n;
+  }
   if (fork) cudaStreamWaitEvent(s, st->ev[1], 0);  // the masks
   if (p.K) {
     PROF("src_resolve");
@@ -2235,6 +2262,10 @@ int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *p
   chain_launch(k_fwd_chain<K_D>, st->shape[CK_FSUM], p, sq, 5, s); ++n;
   PROF("fwd_scan");
   k_scan_carry<<<W, SCAN_T, 0, s>>>(sq, W, 0, init); ++n;
+  if (p.L) {
+    PROF("loop_abs");
+    k_loop_abs<<<grid_of((long long)p.L * W, 256), 256, 0, s>>>(p, sq); ++n;
+  }
   PROF("d_resolve");
   k_resolve<RV_VALID><<<grid_of((nw + 1) / 2, 256), 256, 0, s>>>(p, sq, sq.pair_gd, sq.pair_pd, p.d_in); ++n;
   if (sq.pair_g2) {
@@ -2254,6 +2285,10 @@ int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *p
   chain_launch(k_fwd_chain<K_H>, st->shape[CK_FSUM], p, sq, 7, s); ++n;
   PROF("fwd_scan");
   k_scan_carry<<<W, SCAN_T, 0, s>>>(sq, W, 0, init); ++n;
+  if (p.L) {
+    PROF("loop_abs");
+    k_loop_abs<<<grid_of((long long)p.L * W, 256), 256, 0, s>>>(p, sq); ++n;
+  }
   PROF("h_resolve");
   k_resolve<RV_VALID><<<grid_of((nw + 1) / 2, 256), 256, 0, s>>>(p, sq, sq.pair_g, sq.pair_p, p.h_out); ++n;
   n += run_emission(st, p, s, pf);
