@@ -1480,7 +1480,13 @@ constexpr int EMIT_WARPS = 4;
 #define OMPDART_EMIT_SPAN 8
 #endif
 constexpr int EMIT_SPAN = OMPDART_EMIT_SPAN;  // positions per emission item (its own record stream)
-__global__ void __launch_bounds__(32 * EMIT_WARPS) k_emit(DevPlan p, ScanDev sd, const uint64_t *init) {
+// 10 CTAs of 4 warps per SM (48 registers): the emission waits on loads of
+// state rows; 40 warps per SM ran it 20% faster than 28 (72 registers)
+#ifndef OMPDART_EMIT_MIN_CTAS
+#define OMPDART_EMIT_MIN_CTAS 10
+#endif
+__global__ void __launch_bounds__(32 * EMIT_WARPS, OMPDART_EMIT_MIN_CTAS)
+    k_emit(DevPlan p, ScanDev sd, const uint64_t *init) {
   __shared__ uint64_t hd_all[EMIT_WARPS][128];
   const int gw = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
   if (gw >= sd.n_emit * sd.G) return;
