@@ -1587,17 +1587,37 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_carry(ScanDev sd, int W, int ba
   auto reset_val = [&](int c) -> uint64_t {
     return backward || !init ? 0ull : init[(size_t)sd.chunks[c].cfg * W + w];
   };
+  // the run's chunk maps are read in batches of SCAN_B independent loads
+  // (the composition is sequential, the loads are not)
+  constexpr int SCAN_B = 6;
+  uint64_t gb[SCAN_B], pb[SCAN_B];
+  int32_t fb[SCAN_B];
+  auto load_batch = [&](int k0) {
+#pragma unroll
+    for (int j = 0; j < SCAN_B; ++j) {
+      const int k = k0 + j;
+      if (k < e) {
+        const int c = chunk(k);
+        gb[j] = sd.gsum[(size_t)c * W + w];
+        pb[j] = sd.psum[(size_t)c * W + w];
+        fb[j] = sd.chunks[c].flags;
+      }
+    }
+  };
   // 1. the run's map
   uint64_t g = 0, pp = ~0ull;
-  for (int k = b; k < e; ++k) {
-    const int c = chunk(k);
-    if (sd.chunks[c].flags & rflag) {
-      g = reset_val(c);
-      pp = 0;
+  for (int k0 = b; k0 < e; k0 += SCAN_B) {
+    load_batch(k0);
+#pragma unroll
+    for (int j = 0; j < SCAN_B; ++j) {
+      if (k0 + j >= e) break;
+      if (fb[j] & rflag) {
+        g = reset_val(chunk(k0 + j));
+        pp = 0;
+      }
+      g = gb[j] | (g & pb[j]);
+      pp &= pb[j];
     }
-    const uint64_t gc = sd.gsum[(size_t)c * W + w], pc = sd.psum[(size_t)c * W + w];
-    g = gc | (g & pc);
-    pp &= pc;
   }
   // 2. inclusive scan of the run maps: within the warp, then over warps
   for (int d = 1; d < 32; d <<= 1) {
@@ -1625,11 +1645,16 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_carry(ScanDev sd, int W, int ba
   uint64_t x = __shfl_up_sync(0xffffffffu, g, 1);
   if (lane == 0) x = wid > 0 ? wg_s[wid - 1] : 0ull;
   // 3. every chunk's carry
-  for (int k = b; k < e; ++k) {
-    const int c = chunk(k);
-    if (sd.chunks[c].flags & rflag) x = reset_val(c);
-    sd.carry[(size_t)c * W + w] = x;
-    x = sd.gsum[(size_t)c * W + w] | (x & sd.psum[(size_t)c * W + w]);
+  for (int k0 = b; k0 < e; k0 += SCAN_B) {
+    load_batch(k0);
+#pragma unroll
+    for (int j = 0; j < SCAN_B; ++j) {
+      if (k0 + j >= e) break;
+      const int c = chunk(k0 + j);
+      if (fb[j] & rflag) x = reset_val(c);
+      sd.carry[(size_t)c * W + w] = x;
+      x = gb[j] | (x & pb[j]);
+    }
   }
 }
 
