@@ -192,6 +192,30 @@ struct Interval {
   int a, b, id;
 };
 
+// Host arrays that are written in full by parallel passes: resize leaves
+// them uninitialised, so their pages are first touched by the threads
+// that fill them.
+template <class T>
+struct DefaultInit : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = DefaultInit<U>;
+  };
+  DefaultInit() = default;
+  template <class U>
+  DefaultInit(const DefaultInit<U> &) {}
+  template <class U>
+  void construct(U *p) {
+    ::new (static_cast<void *>(p)) U;
+  }
+  template <class U, class... A>
+  void construct(U *p, A &&...a) {
+    ::new (static_cast<void *>(p)) U(std::forward<A>(a)...);
+  }
+};
+template <class T>
+using HostVec = std::vector<T, DefaultInit<T>>;
+
 // Interval colouring: intervals sharing no position may share a slot
 // (lowest free slot first).  The heaps are the caller's scratch.
 struct Colouring {
@@ -286,8 +310,8 @@ struct ScanState {
     bytes += (long long)b;
     return (T *)p;
   }
-  template <class T>
-  T *up(const std::vector<T> &v) {
+  template <class T, class A>
+  T *up(const std::vector<T, A> &v) {
     T *d = alloc<T>(v.size());
     if (d && !v.empty() && cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
       return nullptr;
@@ -305,7 +329,7 @@ int scan_supported(const Ingest &g) {
 
 namespace {
 
-bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta> &meta, std::vector<LoopMeta> &loops,
+bool build_meta(const Ingest &g, int target, ScanState *st, HostVec<PosMeta> &meta, std::vector<LoopMeta> &loops,
                 std::vector<ChunkMeta> &chunks, std::vector<CarrySrc> &csrc, std::vector<int32_t> &fin_slot,
                 std::vector<int32_t> &out_slot, std::vector<int32_t> &out_pos, std::vector<int32_t> &lat_slot,
                 std::vector<int32_t> &bend_loop, std::vector<int32_t> &srcent, std::vector<int32_t> &exit_slot,
@@ -313,7 +337,7 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
   Ingest &gm = const_cast<Ingest &>(g);
   make_chunks(&gm, target);
   const int M = g.M, C = (int)g.chunk_off.size() - 1, L = g.L;
-  meta.assign(M, PosMeta{});
+  meta.resize(M);  // every record is written by the per-position pass
   loops.assign(L, LoopMeta{});
   chunks.assign(C, ChunkMeta{});
   std::vector<int32_t> head_loop_of_pos(M, -1);
@@ -358,7 +382,7 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
     return l;
   };
   // ---- per chunk: slots by interval colouring (chunks are independent)
-  struct ChunkScratch {
+  struct alignas(128) ChunkScratch {  // one per thread, on cache lines of its own
     std::vector<Interval> iv;
     std::vector<int32_t> loc_loops, so, sb;
     Colouring col;
@@ -465,47 +489,68 @@ bool build_meta(const Ingest &g, int target, ScanState *st, std::vector<PosMeta>
       max_b = std::max(max_b, x.max_b);
     }
   }
-  // ---- per position records
-  for (int i = 0; i < M; ++i) {
-    const int b = g.order[i];
-    PosMeta &m = meta[i];
-    m.blk = b;
-    m.fin_beg = g.fin_off[i];
-    m.nfin = (int16_t)(g.fin_off[i + 1] - g.fin_off[i]);
-    m.out_beg = g.out_off[i];
-    m.nout = (int16_t)(g.out_off[i + 1] - g.out_off[i]);
-    m.acc_beg = 0;  // filled from acc_off by the caller
-    m.fslot = (int16_t)fslot[i];
-    m.bslot = (int16_t)bslot[i];
-    m.head_loop = head_loop_of_pos[i];
-    m.exit_idx = exit_idx[b];
-    m.srcent_beg = (int32_t)srcent.size();
-    srcent.insert(srcent.end(), ebs.begin() + ebs_off[b], ebs.begin() + ebs_off[b + 1]);
-    m.nsrcent = (int16_t)(srcent.size() - m.srcent_beg);
-    m.bend_beg = end_off[i];
-    m.nbend = (int16_t)(end_off[i + 1] - end_off[i]);
-  }
-  for (int c = 0; c < C; ++c) {
-    const int s = chunks[c].s, e = chunks[c].e;
-    for (int i = s; i < e; ++i) {
-      for (int k = g.fin_off[i]; k < g.fin_off[i + 1]; ++k) {
-        const int pp = g.pos[g.fin_src[k]];
-        fin_slot[k] = pp < s ? CARRY : pp >= i ? BACK : pp == i - 1 ? PREV : fslot[pp];
-      }
-      for (int k = g.out_off[i]; k < g.out_off[i + 1]; ++k) {
-        const int pt = g.pos[g.out_dst[k]];
-        out_pos[k] = pt;
-        out_slot[k] = pt >= e ? CARRY : (pt == i + 1 && !bwd_target[i]) ? PREV : bslot[pt];
-      }
+  // ---- per position records (positions independent: loop-entry sources
+  // by block in position order via an offset list)
+  std::vector<int32_t> src_off(M + 1, 0);
+  for (int i = 0; i < M; ++i) src_off[i + 1] = src_off[i] + ebs_off[g.order[i] + 1] - ebs_off[g.order[i]];
+  srcent.resize(src_off[M]);
+  parallel_ranges(M, 1 << 14, 8, [&](int, int lo, int hi) {
+    for (int i = lo; i < hi; ++i) {
+      const int b = g.order[i];
+      PosMeta &m = meta[i];
+      m = PosMeta{};
+      m.blk = b;
+      m.fin_beg = g.fin_off[i];
+      m.nfin = (int16_t)(g.fin_off[i + 1] - g.fin_off[i]);
+      m.out_beg = g.out_off[i];
+      m.nout = (int16_t)(g.out_off[i + 1] - g.out_off[i]);
+      m.acc_beg = 0;  // filled from acc_off by the caller
+      m.fslot = (int16_t)fslot[i];
+      m.bslot = (int16_t)bslot[i];
+      m.head_loop = head_loop_of_pos[i];
+      m.exit_idx = exit_idx[b];
+      m.srcent_beg = src_off[i];
+      std::copy(ebs.begin() + ebs_off[b], ebs.begin() + ebs_off[b + 1], srcent.begin() + src_off[i]);
+      m.nsrcent = (int16_t)(src_off[i + 1] - src_off[i]);
+      m.bend_beg = end_off[i];
+      m.nbend = (int16_t)(end_off[i + 1] - end_off[i]);
     }
-    // carry sources: edges into position e from this chunk
-    chunks[c].carry_beg = (int32_t)csrc.size();
+  });
+  // ---- edge entries per chunk, then the carry sources (edges into the
+  // next chunk's first position from this chunk), counted first
+  std::vector<int32_t> cs_off(C + 1, 0);
+  parallel_ranges(C, 256, 8, [&](int, int lo, int hi) {
+    for (int c = lo; c < hi; ++c) {
+      const int s = chunks[c].s, e = chunks[c].e;
+      for (int i = s; i < e; ++i) {
+        for (int k = g.fin_off[i]; k < g.fin_off[i + 1]; ++k) {
+          const int pp = g.pos[g.fin_src[k]];
+          fin_slot[k] = pp < s ? CARRY : pp >= i ? BACK : pp == i - 1 ? PREV : fslot[pp];
+        }
+        for (int k = g.out_off[i]; k < g.out_off[i + 1]; ++k) {
+          const int pt = g.pos[g.out_dst[k]];
+          out_pos[k] = pt;
+          out_slot[k] = pt >= e ? CARRY : (pt == i + 1 && !bwd_target[i]) ? PREV : bslot[pt];
+        }
+      }
+      int n = 0;
+      if (e < M)
+        for (int k = g.fin_off[e]; k < g.fin_off[e + 1]; ++k) n += g.pos[g.fin_src[k]] < e;
+      cs_off[c + 1] = n;
+    }
+  });
+  for (int c = 0; c < C; ++c) cs_off[c + 1] += cs_off[c];
+  csrc.resize(cs_off[C]);
+  for (int c = 0; c < C; ++c) {
+    const int e = chunks[c].e;
+    chunks[c].carry_beg = cs_off[c];
+    chunks[c].carry_cnt = cs_off[c + 1] - cs_off[c];
+    int q = cs_off[c];
     if (e < M)
       for (int k = g.fin_off[e]; k < g.fin_off[e + 1]; ++k) {
         const int pp = g.pos[g.fin_src[k]];
-        if (pp < e) csrc.push_back(CarrySrc{fslot[pp], g.fin_ent[k], k, 0});
+        if (pp < e) csrc[q++] = CarrySrc{fslot[pp], g.fin_ent[k], k, 0};
       }
-    chunks[c].carry_cnt = (int32_t)csrc.size() - chunks[c].carry_beg;
   }
   for (int l = 0; l < L; ++l) {
     LoopMeta &lm = loops[l];
@@ -1900,7 +1945,7 @@ static void fold_call_block(const uint32_t *acc, int a0, int a1, const CallHost 
 ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *acc, const CallHost &calls,
                        int32_t *cfg_err, DevPlan &p, int chunk_target, int keep_states, std::string *err, int wpc) {
   ScanState *st = new ScanState();
-  std::vector<PosMeta> meta;
+  HostVec<PosMeta> meta;
   std::vector<LoopMeta> loops;
   std::vector<ChunkMeta> chunks;
   std::vector<CarrySrc> csrc;
@@ -1914,7 +1959,7 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     delete st;
     return nullptr;
   }
-  trace_bm.next("scan uploads", g.M);
+  trace_bm.next("scan accesses", g.M);
   // accesses in position order: a block's own accesses with same-variable
   // links inside the block (a short list for the usual handful of accesses,
   // a hash map for long blocks), or, for a block with calls, its folded
@@ -1957,8 +2002,8 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     return nullptr;
   }
   for (int i = 0; i < g.M; ++i) cnt[i + 1] += cnt[i];
-  std::vector<uint32_t> acc_p(cnt[g.M]);
-  std::vector<int2> acc_link(cnt[g.M]);
+  HostVec<uint32_t> acc_p(cnt[g.M]);  // filled in full by the second pass
+  HostVec<int2> acc_link(cnt[g.M]);
   parallel_ranges(g.M, kMinPos, kThreads, [&](int t, int lo, int hi) {
     const Folded &fd = fold[t];
     size_t next_fold = 0;
@@ -2012,6 +2057,7 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
       }
     }
   });
+  trace_bm.next("scan uploads", g.M);
   std::vector<int2> fin_pk(fin_slot.size()), out_pk(out_slot.size());
   // in-edge entries: {source slot, loop-entry edge or -1}
   for (size_t k = 0; k < fin_pk.size(); ++k) fin_pk[k] = make_int2(fin_slot[k], g.fin_ent[k]);
