@@ -709,6 +709,20 @@ __device__ __forceinline__ uint64_t ld_word(const uint64_t *plane, size_t row, i
 __device__ __forceinline__ void st_word(uint64_t *plane, size_t row, int W, int w, uint64_t v) {
   if (w < W) plane[row * W + w] = v;
 }
+// a lane's two words w, w + 1 (w even) of a row: one 16-byte access when
+// both exist and rows are an even number of words (16-byte aligned)
+__device__ __forceinline__ ulonglong2 ld_pair(const uint64_t *plane, size_t row, int W, int w) {
+  if (!(W & 1) && w + 1 < W) return *reinterpret_cast<const ulonglong2 *>(plane + row * W + w);
+  return make_ulonglong2(ld_word(plane, row, W, w), ld_word(plane, row, W, w + 1));
+}
+__device__ __forceinline__ void st_pair(uint64_t *plane, size_t row, int W, int w, uint64_t a, uint64_t b) {
+  if (!(W & 1) && w + 1 < W) {
+    *reinterpret_cast<ulonglong2 *>(plane + row * W + w) = make_ulonglong2(a, b);
+  } else {
+    st_word(plane, row, W, w, a);
+    st_word(plane, row, W, w + 1, b);
+  }
+}
 
 // Rows of one mask table (64 words each): the affine walks keep [set,
 // clear] of the local plane and one `clear' row shared by the coefficient
@@ -857,10 +871,8 @@ __device__ __forceinline__ void close_loop(const ScanDev &sd, const Slots<2> &sl
   }
   const ulonglong2 e0 = *sl.at(hs, 0, L.lane), e1 = *sl.at(hs, 1, L.lane);
   const uint64_t h00 = e0.x | a0, h01 = e0.y | a1, h10 = e1.x | a0, h11 = e1.y | a1;
-  st_word(sd.hdr_g, l, W, L.w0, h00);
-  st_word(sd.hdr_g, l, W, L.w0 + 1, h01);
-  st_word(sd.hdr_p, l, W, L.w0, h10);
-  st_word(sd.hdr_p, l, W, L.w0 + 1, h11);
+  st_pair(sd.hdr_g, l, W, L.w0, h00, h01);
+  st_pair(sd.hdr_p, l, W, L.w0, h10, h11);
   for (int q = 0; q < lm.xs_cnt; ++q) {
     const int x = sd.exit_slot[lm.xs_beg + q];
     ulonglong2 *g = sl.at(x, 0, L.lane), *pp = sl.at(x, 1, L.lane);
@@ -929,14 +941,14 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
       if (ppos == i) {
         lv[0] = plv[0]; lv[1] = plv[1]; din[0] = pdin[0]; din[1] = pdin[1];
       } else {
-        lv[0] = ld_word(p.live, m.blk, W, L.w0); lv[1] = ld_word(p.live, m.blk, W, L.w0 + 1);
-        din[0] = ld_word(p.d_in, m.blk, W, L.w0); din[1] = ld_word(p.d_in, m.blk, W, L.w0 + 1);
+        { const ulonglong2 t = ld_pair(p.live, m.blk, W, L.w0); lv[0] = t.x; lv[1] = t.y; }
+        { const ulonglong2 t = ld_pair(p.d_in, m.blk, W, L.w0); din[0] = t.x; din[1] = t.y; }
       }
       ppos = -1;
       if (i + 1 < wr.we) {
         const int nb = w.meta[i + 1 - wr.mbase].blk;
-        plv[0] = ld_word(p.live, nb, W, L.w0); plv[1] = ld_word(p.live, nb, W, L.w0 + 1);
-        pdin[0] = ld_word(p.d_in, nb, W, L.w0); pdin[1] = ld_word(p.d_in, nb, W, L.w0 + 1);
+        { const ulonglong2 t = ld_pair(p.live, nb, W, L.w0); plv[0] = t.x; plv[1] = t.y; }
+        { const ulonglong2 t = ld_pair(p.d_in, nb, W, L.w0); pdin[0] = t.x; pdin[1] = t.y; }
         ppos = i + 1;
       }
     }
@@ -1013,30 +1025,22 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
     {
       const size_t row = (size_t)m.blk;
       if (PH == K_D) {  // device validity at the block entry (and exit, kept states)
-        st_word(sd.pair_gd, row, W, L.w0, z[0][0]);
-        st_word(sd.pair_gd, row, W, L.w0 + 1, z[0][1]);
-        st_word(sd.pair_pd, row, W, L.w0, z[1][0]);
-        st_word(sd.pair_pd, row, W, L.w0 + 1, z[1][1]);
+        st_pair(sd.pair_gd, row, W, L.w0, z[0][0], z[0][1]);
+        st_pair(sd.pair_pd, row, W, L.w0, z[1][0], z[1][1]);
         if (sd.pair_g2) {
-          st_word(sd.pair_g2, row, W, L.w0, zo[0][0]);
-          st_word(sd.pair_g2, row, W, L.w0 + 1, zo[0][1]);
-          st_word(sd.pair_p2, row, W, L.w0, zo[1][0]);
-          st_word(sd.pair_p2, row, W, L.w0 + 1, zo[1][1]);
+          st_pair(sd.pair_g2, row, W, L.w0, zo[0][0], zo[0][1]);
+          st_pair(sd.pair_p2, row, W, L.w0, zo[1][0], zo[1][1]);
         }
       }
       if (PH == K_H) {  // host validity at the block exit
-        st_word(sd.pair_g, row, W, L.w0, zo[0][0]);
-        st_word(sd.pair_g, row, W, L.w0 + 1, zo[0][1]);
-        st_word(sd.pair_p, row, W, L.w0, zo[1][0]);
-        st_word(sd.pair_p, row, W, L.w0 + 1, zo[1][1]);
+        st_pair(sd.pair_g, row, W, L.w0, zo[0][0], zo[0][1]);
+        st_pair(sd.pair_p, row, W, L.w0, zo[1][0], zo[1][1]);
       }
       if ((PH == K_HP || PH == K_D) && m.nsrcent) {  // at loop-entry sources
         for (int q = 0; q < m.nsrcent; ++q) {
           const int k = sd.srcent[m.srcent_beg + q];
-          st_word(sd.src_g, k, W, L.w0, zo[0][0]);
-          st_word(sd.src_g, k, W, L.w0 + 1, zo[0][1]);
-          st_word(sd.src_p, k, W, L.w0, zo[1][0]);
-          st_word(sd.src_p, k, W, L.w0 + 1, zo[1][1]);
+          st_pair(sd.src_g, k, W, L.w0, zo[0][0], zo[0][1]);
+          st_pair(sd.src_p, k, W, L.w0, zo[1][0], zo[1][1]);
         }
       }
     }
@@ -1064,10 +1068,8 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
     }
   }
   if (cm.carry_cnt) {
-    st_word(sd.gsum, c, W, L.w0, co[0][0]);
-    st_word(sd.gsum, c, W, L.w0 + 1, co[0][1]);
-    st_word(sd.psum, c, W, L.w0, co[1][0]);
-    st_word(sd.psum, c, W, L.w0 + 1, co[1][1]);
+    st_pair(sd.gsum, c, W, L.w0, co[0][0], co[0][1]);
+    st_pair(sd.psum, c, W, L.w0, co[1][0], co[1][1]);
   }
 }
 
@@ -1210,10 +1212,8 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
     // value leaves the loop without the header plane
     const bool sym_close = MODE == M_SUM && is_top_header && depth == base_depth + 1;
     if (MODE == M_SUM && sym_close) {
-      st_word(sd.hdrl_g, m.head_loop, W, L.w0, z[0][0]);
-      st_word(sd.hdrl_g, m.head_loop, W, L.w0 + 1, z[0][1]);
-      st_word(sd.hdrl_p, m.head_loop, W, L.w0, z[1][0]);
-      st_word(sd.hdrl_p, m.head_loop, W, L.w0 + 1, z[1][1]);
+      st_pair(sd.hdrl_g, m.head_loop, W, L.w0, z[0][0], z[0][1]);
+      st_pair(sd.hdrl_p, m.head_loop, W, L.w0, z[1][0], z[1][1]);
       z[NP - 1][0] = z[NP - 1][1] = 0;
     }
     if (m.bslot >= 0) {
@@ -1230,13 +1230,10 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
       if (is_top_header && !sym_close && __any_sync(0xffffffffu, changed)) dirty |= 1u << (depth - 1);
     }
     if (MODE == M_SUM) {  // Live_in as an affine pair of the chunk's carry (and A inside a loop)
-      st_word(sd.pair_g, m.blk, W, L.w0, z[0][0]);
-      st_word(sd.pair_g, m.blk, W, L.w0 + 1, z[0][1]);
-      st_word(sd.pair_p, m.blk, W, L.w0, z[1][0]);
-      st_word(sd.pair_p, m.blk, W, L.w0 + 1, z[1][1]);
+      st_pair(sd.pair_g, m.blk, W, L.w0, z[0][0], z[0][1]);
+      st_pair(sd.pair_p, m.blk, W, L.w0, z[1][0], z[1][1]);
       if (depth > base_depth) {
-        st_word(sd.pair_a, m.blk, W, L.w0, z[NP - 1][0]);
-        st_word(sd.pair_a, m.blk, W, L.w0 + 1, z[NP - 1][1]);
+        st_pair(sd.pair_a, m.blk, W, L.w0, z[NP - 1][0], z[NP - 1][1]);
       }
     }
     __syncwarp();
@@ -1291,10 +1288,8 @@ __device__ __forceinline__ void bwd_walk(const DevPlan &p, const ScanDev &sd, co
   cin[1][0] = L.top0;
   cin[1][1] = L.top1;
   bwd_range<MODE>(p, sd, L, wm, sl, cm.s, cm.e, 0, -1, true, cin, zl, cm.cfg);
-  st_word(sd.gsum, c, W, L.w0, zl[0][0]);
-  st_word(sd.gsum, c, W, L.w0 + 1, zl[0][1]);
-  st_word(sd.psum, c, W, L.w0, zl[1][0]);
-  st_word(sd.psum, c, W, L.w0 + 1, zl[1][1]);
+  st_pair(sd.gsum, c, W, L.w0, zl[0][0], zl[0][1]);
+  st_pair(sd.psum, c, W, L.w0, zl[1][0], zl[1][1]);
 }
 
 // The loop masks of loop l for the 64-word group wg: anticipation
@@ -1320,10 +1315,8 @@ __device__ __forceinline__ void lant_walk(const DevPlan &p, const ScanDev &sd, c
   bwd_range<M_LANT>(p, sd, L, wm, sl, lm.ph, lm.pend, lm.depth, lm.ph, false, cin, zl, lm.cfg);
   const ulonglong2 kh = *reinterpret_cast<const ulonglong2 *>(wm.kill + 2 * L.lane);
   const ulonglong2 kd = *reinterpret_cast<const ulonglong2 *>(wm.kill + 64 + 2 * L.lane);
-  st_word(p.mask_h, l, W, L.w0, zl[0][0] & ~kh.x & L.top0);
-  st_word(p.mask_h, l, W, L.w0 + 1, zl[0][1] & ~kh.y & L.top1);
-  st_word(p.mask_d, l, W, L.w0, zl[1][0] & ~kd.x & L.top0);
-  st_word(p.mask_d, l, W, L.w0 + 1, zl[1][1] & ~kd.y & L.top1);
+  st_pair(p.mask_h, l, W, L.w0, zl[0][0] & ~kh.x & L.top0, zl[0][1] & ~kh.y & L.top1);
+  st_pair(p.mask_d, l, W, L.w0, zl[1][0] & ~kd.x & L.top0, zl[1][1] & ~kd.y & L.top1);
 }
 
 // persistent backward chain (same work queue scheme as the forward one);
@@ -1548,8 +1541,8 @@ __global__ void __launch_bounds__(32 * EMIT_WARPS, OMPDART_EMIT_MIN_CTAS)
   for (int i = rng.x; i < rng.y; ++i) {
     const PosMeta m = sd.meta[i];
     const size_t b = (size_t)m.blk;
-    const uint64_t lv0 = ld_word(p.live, b, W, w0), lv1 = ld_word(p.live, b, W, w0 + 1);
-    const uint64_t di0 = ld_word(p.d_in, b, W, w0), di1 = ld_word(p.d_in, b, W, w0 + 1);
+    const ulonglong2 lv = ld_pair(p.live, b, W, w0), di = ld_pair(p.d_in, b, W, w0);
+    const uint64_t lv0 = lv.x, lv1 = lv.y, di0 = di.x, di1 = di.y;
     const uint64_t c0 = lv0 & ~di0, c1 = lv1 & ~di1;
     uint64_t z0 = 0, z1 = 0;
     if (m.nfin == 0) {  // the CFG's entry
@@ -1560,13 +1553,16 @@ __global__ void __launch_bounds__(32 * EMIT_WARPS, OMPDART_EMIT_MIN_CTAS)
       const int k = m.fin_beg + q;
       const int ent = sd.fin_pk[k].y;  // loop-entry edge or -1
       const size_t src = (size_t)p.fin_src[k];
-      const uint64_t s0 = ~ld_word(p.h_out, src, W, w0) & top0, s1 = ~ld_word(p.h_out, src, W, w0 + 1) & top1;
+      const ulonglong2 ho = ld_pair(p.h_out, src, W, w0);
+      const uint64_t s0 = ~ho.x & top0, s1 = ~ho.y & top1;
       uint64_t m0 = 0, m1 = 0, to0 = 0, to1 = 0;
       if (ent >= 0) {
-        m0 = ld_word(p.ec_h, ent, W, w0);
-        m1 = ld_word(p.ec_h, ent, W, w0 + 1);
-        to0 = ld_word(p.ec_d, ent, W, w0) & ~ld_word(sd.d_src, ent, W, w0);
-        to1 = ld_word(p.ec_d, ent, W, w0 + 1) & ~ld_word(sd.d_src, ent, W, w0 + 1);
+        const ulonglong2 eh = ld_pair(p.ec_h, ent, W, w0), ed = ld_pair(p.ec_d, ent, W, w0),
+                         ds = ld_pair(sd.d_src, ent, W, w0);
+        m0 = eh.x;
+        m1 = eh.y;
+        to0 = ed.x & ~ds.x;
+        to1 = ed.y & ~ds.y;
       }
       const uint64_t e0 = s0 & ~m0, e1 = s1 & ~m1;
       z0 |= e0;
@@ -1577,8 +1573,7 @@ __global__ void __launch_bounds__(32 * EMIT_WARPS, OMPDART_EMIT_MIN_CTAS)
     z0 &= ~c0;
     z1 &= ~c1;
     const uint64_t hi0 = ~z0 & top0, hi1 = ~z1 & top1;
-    st_word(p.h_in, b, W, w0, hi0);
-    st_word(p.h_in, b, W, w0 + 1, hi1);
+    st_pair(p.h_in, b, W, w0, hi0, hi1);
     if (m.nacc && !(m.flags & PM_RECORDS)) {  // flag table at the entry validity
       hd[2 * lane] = hi0;
       hd[2 * lane + 1] = hi1;
