@@ -17,6 +17,7 @@
 #include <atomic>
 #include <cstring>
 #include <map>
+#include <tuple>
 #include <memory>
 #include <mutex>
 #include <new>
@@ -124,12 +125,12 @@ namespace {
 constexpr int kSide = 8;  // forked streams a run spreads its plans over
 
 // Lay the CFGs `members` (ingested in ing) out as one arena and upload it.
-int build_arena(Arena *a, const std::vector<int32_t> &members, std::vector<Ingest> &ing, const ompdart_cfg *cfgs,
-                const ompdart_opts &o, std::string *err) {
+int build_arena(Arena *a, const std::vector<int32_t> &members, const std::vector<const Ingest *> &ing,
+                const ompdart_cfg *cfgs, const ompdart_opts &o, std::string *err) {
   a->members = members;
   std::vector<const Ingest *> parts;
   parts.reserve(members.size());
-  for (int m : members) parts.push_back(&ing[m]);
+  for (int m : members) parts.push_back(ing[m]);
   TraceScope trace_cat("arena concat", (long long)members.size());
   concat_ingests(parts, &a->core.g);
   const int W = a->core.g.W;
@@ -146,7 +147,7 @@ int build_arena(Arena *a, const std::vector<int32_t> &members, std::vector<Inges
   a->x_off.assign(1, 0);
   for (size_t k = 0; k < members.size(); ++k) {
     const ompdart_cfg &c = cfgs[members[k]];
-    const Ingest &g = ing[members[k]];
+    const Ingest &g = *ing[members[k]];
     const int32_t base = (int32_t)acc.size();
     for (int b = 0; b < g.N; ++b) acc_off.push_back(base + c.acc_off[b + 1]);
     acc.insert(acc.end(), c.acc, c.acc + c.acc_off[g.N]);
@@ -214,11 +215,11 @@ double time_core(PlanCore *c, cudaStream_t s, int reps) {
 // over chunk targets (16..512) at 4 warps per CTA, then 2 warps per CTA at the
 // best target, each candidate a trial arena over a sample of about 2^18
 // positions (every step-th CFG), timed on the device.
-void tune_arena(Arena *a, const std::vector<int32_t> &members, std::vector<Ingest> &ing, const ompdart_cfg *cfgs,
-                const ompdart_opts &o, cudaStream_t s) {
+void tune_arena(Arena *a, const std::vector<int32_t> &members, const std::vector<const Ingest *> &ing,
+                const ompdart_cfg *cfgs, const ompdart_opts &o, cudaStream_t s) {
   long long total = 0;
-  for (int m : members) total += ing[m].M;
-  const std::pair<int, int> key(ing[members[0]].W, ilog2(std::max<long long>(1, total)));
+  for (int m : members) total += ing[m]->M;
+  const std::pair<int, int> key(ing[members[0]]->W, ilog2(std::max<long long>(1, total)));
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune_cache.find(key);
@@ -350,15 +351,31 @@ int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts 
   if (ce == cudaSuccess) ce = cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking);
   if (ce == cudaSuccess) ce = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming);
   if (ce != cudaSuccess) return set_error(OMPDART_E_CUDA, std::string("CUDA setup: ") + cudaGetErrorString(ce));
-  // ---- ingestion, one CFG per task
+  // ---- ingestion, one CFG per task.  CFGs given with the same graph and
+  // access arrays (the same function analysed in several contexts: only
+  // the boundary rows differ) are ingested once and share the result.
   TraceScope trace_ingest("batch ingest", n);
+  std::vector<int32_t> canon(n);
+  {
+    std::map<std::tuple<const void *, const void *, const void *, const void *, int, int, int>, int32_t> first;
+    for (int i = 0; i < n; ++i) {
+      const ompdart_cfg &c = cfgs[i];
+      canon[i] = first.emplace(std::make_tuple((const void *)c.succ_off, (const void *)c.succ, (const void *)c.acc_off,
+                                               (const void *)c.acc, c.n_blocks, c.n_vars, c.entry),
+                               i)
+                     .first->second;
+    }
+  }
   std::vector<Ingest> ing(n);
+  std::vector<const Ingest *> ingp(n);
+  for (int i = 0; i < n; ++i) ingp[i] = &ing[canon[i]];
   B->ingest_status.assign(n, OMPDART_OK);
   B->where.assign(n, Where{});
   {
     std::atomic<int> next{0};
     auto work = [&]() {
       for (int i = next++; i < n; i = next++) {
+        if (canon[i] != i) continue;
         std::string e;
         int rc = ingest(&cfgs[i], &ing[i], &e);
         B->ingest_status[i] = rc;
@@ -370,6 +387,7 @@ int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts 
     for (int t = 1; t < T; ++t) pool.emplace_back(work);
     work();
     for (auto &t : pool) t.join();
+    for (int i = 0; i < n; ++i) B->ingest_status[i] = B->ingest_status[canon[i]];
   }
   trace_ingest.next("batch arenas", n);
   // ---- grouping
@@ -377,8 +395,8 @@ int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts 
   std::vector<int32_t> solo_ids;
   for (int i = 0; i < n; ++i) {
     if (B->ingest_status[i]) continue;
-    if (scan_supported(ing[i]))
-      by_w[ing[i].W].push_back(i);
+    if (scan_supported(*ingp[i]))
+      by_w[ingp[i]->W].push_back(i);
     else
       solo_ids.push_back(i);
   }
@@ -393,7 +411,7 @@ int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts 
     if (!built[g]) return set_error(OMPDART_E_NOMEM, "host allocation failed");
     built[g]->chunk_target = o.chunk_target;
     built[g]->wpc = o.warps_per_cta;
-    if (o.tune) tune_arena(built[g].get(), groups[g].second, ing, cfgs, o, B->stream);
+    if (o.tune) tune_arena(built[g].get(), groups[g].second, ingp, cfgs, o, B->stream);
   }
   {
     std::vector<int> rcs(n_ar, OMPDART_OK);
@@ -408,10 +426,15 @@ int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts 
         return;
       }
       for (int g = next++; g < n_ar; g = next++)
-        rcs[g] = build_arena(built[g].get(), groups[g].second, ing, cfgs, o, &errs[g]);
+        rcs[g] = build_arena(built[g].get(), groups[g].second, ingp, cfgs, o, &errs[g]);
     };
+    // small batches (a serving turn) are built on the calling thread: a
+    // thread of its own costs more than such an arena's build
+    long long positions = 0;
+    for (const auto &gr : groups)
+      for (int m : gr.second) positions += ingp[m]->M;
     const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    const int T = std::min(n_ar, (int)std::min(hw, 16u));
+    const int T = positions < (1 << 18) ? 1 : std::min(n_ar, (int)std::min(hw, 16u));
     std::vector<std::thread> pool;
     for (int t = 1; t < T; ++t) pool.emplace_back(work, false);
     work(true);
@@ -426,14 +449,13 @@ int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts 
     if (!a->h_status || !a->h_err) return set_error(OMPDART_E_NOMEM, "host allocation failed");
     const int idx = (int)B->arenas.size();
     for (size_t k = 0; k < a->members.size(); ++k) B->where[a->members[k]] = Where{1, idx, (int)k};
-    for (int m : groups[g].second) ing[m] = Ingest();  // the arena holds the concatenation
     B->arenas.push_back(std::move(a));
   }
   for (int i : solo_ids) {
     std::unique_ptr<Solo> p(new (std::nothrow) Solo());
     if (!p) return set_error(OMPDART_E_NOMEM, "host allocation failed");
     p->member = i;
-    p->core.g = std::move(ing[i]);
+    p->core.g = *ingp[i];  // a copy: CFGs with the same arrays share one ingestion
     std::vector<uint64_t> top, eh, ed, xl;
     boundary_rows(&cfgs[i], p->core.g.W, &top, &eh, &ed, &xl);
     ompdart_opts os = o;

@@ -25,9 +25,12 @@
 #include <atomic>
 #include <cstring>
 #include <functional>
+#include <map>
+#include <mutex>
 #include <queue>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <unordered_map>
 #include <vector>
 
@@ -1858,10 +1861,26 @@ ChainShape chain_shape(K kern, int need, int np, bool kill, int sh_words, int wp
   // the attribute belongs to the kernel, not to this plan: always the
   // largest size any plan launches with (most warps, every slot in shared
   // memory), so plans alive at the same time never shrink it for each other
-  set_smem(kern, (size_t)OMPDART_MAX_WPC * warp_smem_words(sh_words / (64 * np), np, kill) * 8);
+  // both depend only on the device, the kernel and the launch shape: done
+  // once per process and shape (a serving loop builds plans all the time)
+  static std::mutex mu;
+  static std::map<std::tuple<int, const void *, int, size_t>, int> known;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_tuple(dev, (const void *)kern, wpc, c.smem);
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpc, c.smem) != cudaSuccess || per_sm < 1)
-    per_sm = 1;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = known.find(key);
+    if (it != known.end()) per_sm = it->second;
+  }
+  if (!per_sm) {
+    set_smem(kern, (size_t)OMPDART_MAX_WPC * warp_smem_words(sh_words / (64 * np), np, kill) * 8);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * wpc, c.smem) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    std::lock_guard<std::mutex> lk(mu);
+    known[key] = per_sm;
+  }
   const long long need_ctas = ((long long)n_items + wpc - 1) / wpc;
   c.grid = (int)std::max<long long>(1, std::min<long long>(need_ctas, (long long)per_sm * n_sm));
   return c;
