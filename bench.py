@@ -195,6 +195,24 @@ def cpu_info():
 
 # ---------------------------------------------------------------------------
 
+def job_time_ms(ms, world, device):
+    """The timed region of the whole job: the slowest rank's (every rank
+    runs the same steps between barriers), via a MAX all-reduce."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_value(units_per_rank, world, steps, ms):
+    """Whole-job throughput: every rank's units over the job's time."""
+    return units_per_rank * world * steps / (ms / 1e3)
+
+
 def workload_stats(g, plan_ing=None):
     import numpy as np
     W = g.W
@@ -261,14 +279,10 @@ def run_ours(args):
         plan.sync()
     timings = plan.timings()
     plan.profile(False)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
+    ms = job_time_ms(ms, world, "cuda")
     ms_step = ms / args.steps
     units = g.n_blocks * g.W
-    value = units * world * args.steps / (ms / 1e3)
+    value = job_value(units, world, args.steps, ms)
 
     out = None
     if rank == 0:
@@ -348,6 +362,9 @@ def run_batch(args):
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
     t0 = time.perf_counter()
     cfgs = wl.batch(args.batch_seed, n_cfgs=args.n_cfgs)
@@ -364,6 +381,8 @@ def run_batch(args):
         b.run(sh)
         assert (b.sync() == 0).all()
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     clocks = ClockSampler(local)
     clocks.start()
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
@@ -376,7 +395,7 @@ def run_batch(args):
     clk = clocks.stop()
     info = b.info()  # launches per run are known once it has run
     step_ms = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
-    ms = sum(step_ms)
+    ms = job_time_ms(sum(step_ms), world, "cuda")
     # latency of a batch as the caller sees it: run() to sync() returning
     lat_b = []
     for _ in range(max(3, min(args.steps, 10))):
@@ -433,8 +452,11 @@ def run_batch(args):
         u_cpu += g.n_blocks * g.W
         if t_cpu > args.cpu_seconds:
             break
-    value = units * args.steps / (ms / 1e3)
-    cps = len(cfgs) * args.steps / (ms / 1e3)
+    value = job_value(units, world, args.steps, ms)
+    cps = job_value(len(cfgs), world, args.steps, ms)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
     if rank != 0:
         return None
     return {

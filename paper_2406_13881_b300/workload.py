@@ -411,26 +411,33 @@ def random_graph(seed, n_blocks, n_vars, *, p_edge=0.25, max_out=3, acc_max=4, p
     return from_lists(succs, accs, n_vars)
 
 
-def restrict_word(g: CFG, w: int) -> tuple[CFG, np.ndarray]:
-    """The same CFG with only the accesses to variables 64w..64w+63, renumbered
-    to 0..63 (n_vars = how many of them exist).  Returns (cfg, kept) where
-    ``kept`` are the original access indices.  Entry/exit masks are sliced
-    to word w.  Used to check one word column of a wide problem."""
+def restrict_words(g: CFG, w0: int, w1: int) -> tuple[CFG, np.ndarray]:
+    """The same CFG with only the accesses to variables 64*w0 .. 64*w1 - 1,
+    renumbered from 0 (n_vars = how many of them exist).  Returns (cfg,
+    kept) where ``kept`` are the original access indices.  Entry/exit masks
+    are sliced to words w0..w1-1.  A word range is a shard of the problem:
+    variables never interact."""
     var, kind, space = unpack_access(g.acc)
-    keep = np.nonzero((var >> 6) == w)[0]
+    keep = np.nonzero(((var >> 6) >= w0) & ((var >> 6) < w1))[0]
     blk = np.repeat(np.arange(g.n_blocks), np.diff(g.acc_off))
     cnt = np.bincount(blk[keep], minlength=g.n_blocks)
     ao = np.zeros(g.n_blocks + 1, dtype=np.int32)
     ao[1:] = np.cumsum(cnt)
-    nv = min(64, g.n_vars - 64 * w)
-    acc = pack_access(var[keep] - 64 * w, kind[keep], space[keep])
+    nv = min(64 * (w1 - w0), g.n_vars - 64 * w0)
+    acc = pack_access(var[keep] - 64 * w0, kind[keep], space[keep])
 
     def sl(m):
-        return None if m is None else np.ascontiguousarray(m[w:w + 1])
+        return None if m is None else np.ascontiguousarray(m[w0:w1])
 
     h = CFG(g.n_blocks, nv, g.entry, g.succ_off, g.succ, ao, acc, g.region,
             sl(g.entry_host_valid), sl(g.entry_dev_valid), sl(g.exit_host_live))
     return h, keep
+
+
+def restrict_word(g: CFG, w: int) -> tuple[CFG, np.ndarray]:
+    """restrict_words for the single word column w (used to check one word
+    column of a wide problem against the oracle)."""
+    return restrict_words(g, w, w + 1)
 
 
 # --------------------------------------------------------------------------
