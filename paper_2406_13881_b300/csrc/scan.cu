@@ -62,6 +62,9 @@ constexpr int BACK = -4;       // slot id (forward in-edges): a back edge, close
 #ifndef OMPDART_FWD_MIN_CTAS
 #define OMPDART_FWD_MIN_CTAS 6
 #endif
+#ifndef OMPDART_LANT_SH_WORDS  // the loop-mask walk (four planes): no slot in shared memory, 5 CTAs
+#define OMPDART_LANT_SH_WORDS 0
+#endif
 #ifndef OMPDART_BWD_MIN_CTAS
 #define OMPDART_BWD_MIN_CTAS 5
 #endif
@@ -729,8 +732,9 @@ __device__ __forceinline__ void st_pair(uint64_t *plane, size_t row, int W, int 
 
 // Rows of one mask table (64 words each): the affine walks keep [set,
 // clear] of the local plane and one `clear' row shared by the coefficient
-// planes; the loop-mask walk keeps [set, clear] per plane (H, D).
-__host__ __device__ constexpr int mask_rows(int np, bool lant) { return lant ? 2 * np : 3; }
+// planes; the loop-mask walk keeps [set, clear] of H and of D and the
+// `clear' rows of their header-value coefficients.
+__host__ __device__ constexpr int mask_rows(int np, bool lant) { return lant ? 6 : 3; }
 
 // shared memory per warp (words):
 //   slots [nsh][np][64] | mask tables [2][rows][64] | window | kill sets 128 (loop masks only)
@@ -771,7 +775,8 @@ __device__ __forceinline__ WarpMem carve(uint64_t *smem, int warp_in_cta, int ns
 //   block's kills ORed into `kill` ([H|D][64]).
 //   forward planes (stale sets): local: GEN -> clear (valid), KILL -> set
 //   (stale); coefficient: both -> clear.
-// Rows: [set, clear, coefficient clear], LANT [H set, H clear, D set, D clear].
+// Rows: [set, clear, coefficient clear], LANT [H set, H clear, D set, D
+// clear, H coefficient clear, D coefficient clear].
 template <int PH, int MODE>
 __device__ __forceinline__ void prep_masks(const ScanDev &sd, const Win &w, const WinRegs &wr, const PosMeta &m,
                                            const Lane &L, uint64_t *tb, uint64_t *kill) {
@@ -787,6 +792,8 @@ __device__ __forceinline__ void prep_masks(const ScanDev &sd, const Win &w, cons
       if (MODE == M_LANT) {
         if (uh) atomicOr(t, bit); else if (df) atomicOr(t + 64, bit);
         if (ud) atomicOr(t + 128, bit); else if (df) atomicOr(t + 192, bit);
+        if (uh || df) atomicOr(t + 256, bit);  // coefficients of the open loop's header value
+        if (ud || df) atomicOr(t + 320, bit);
         if (rc & R_KH) atomicOr(reinterpret_cast<unsigned long long *>(kill) + lw, bit);
         if (rc & R_KD) atomicOr(reinterpret_cast<unsigned long long *>(kill) + 64 + lw, bit);
       } else {
@@ -808,7 +815,9 @@ __device__ __forceinline__ void take_masks(uint64_t *tb, int lane, uint64_t (&z)
   ulonglong2 *row = reinterpret_cast<ulonglong2 *>(tb) + lane;  // row r at row[32 * r]
 #pragma unroll
   for (int pl = 0; pl < NP; ++pl) {
-    const int rs = LANT ? 2 * pl : (pl ? -1 : 0), rc = LANT ? 2 * pl + 1 : (pl ? 2 : 1);
+    // LANT planes: H, D, then their header-value coefficients
+    const int rs = LANT ? (pl < 2 ? 2 * pl : -1) : (pl ? -1 : 0);
+    const int rc = LANT ? (pl < 2 ? 2 * pl + 1 : 2 + pl) : (pl ? 2 : 1);
     const ulonglong2 a = rs >= 0 ? row[32 * rs] : make_ulonglong2(0ull, 0ull), b = row[32 * rc];
     z[pl][0] = (z[pl][0] & ~b.x) | a.x;
     z[pl][1] = (z[pl][1] & ~b.y) | a.y;
@@ -1105,8 +1114,9 @@ __global__ void __launch_bounds__(32 * OMPDART_MAX_WPC, OMPDART_FWD_MIN_CTAS)
 // backward chain (anticipation; loop-restricted anticipation for the masks)
 // --------------------------------------------------------------------------------------
 template <int MODE>
-struct BwdPlanes {  // SUM: [Live local, carry coefficient, header coefficient]; LANT: [H, D]
-  static constexpr int NP = MODE == M_SUM ? 3 : 2;
+struct BwdPlanes {  // SUM: [Live local, carry coefficient, header coefficient];
+                    // LANT: [H, D, H header coefficient, D header coefficient]
+  static constexpr int NP = MODE == M_SUM ? 3 : 4;
 };
 
 template <int MODE>
@@ -1157,15 +1167,15 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
       depth = bi.x;
       top_ph = bi.y;
       // first visit: the header's value, read by the latches, starts from
-      // nothing (liveness, outermost loop: the latches read A itself, the
-      // header coefficient plane all ones); a re-entry keeps the previous
+      // nothing (outermost open loop: the latches read A itself, the
+      // header coefficient planes all ones); a re-entry keeps the previous
       // visit's value
       if (i < lwm) {
         const int hs = bi.w;
-        const bool sym = MODE == M_SUM && bi.x == base_depth + 1;
+        const bool sym = bi.x == base_depth + 1;  // planes from 2 on: header coefficients
         if (hs >= 0)
           for (int pl = 0; pl < NP; ++pl)
-            *sl.at(hs, pl, L.lane) = sym && pl == 2 ? make_ulonglong2(L.top0, L.top1) : make_ulonglong2(0ull, 0ull);
+            *sl.at(hs, pl, L.lane) = sym && pl >= 2 ? make_ulonglong2(L.top0, L.top1) : make_ulonglong2(0ull, 0ull);
         __syncwarp();
       }
     }
@@ -1210,14 +1220,18 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
       prep_pos = -1;
     }
     const bool is_top_header = depth > base_depth && top_ph == i;
-    // liveness at an outermost loop's header: A = G | (carry & P) | (A & PA)
+    // at the header of an outermost open loop: A = G | (carry & P) | (A & PA)
     // has the least solution A = G | (carry & P) (so no second walk); the
-    // value leaves the loop without the header plane
-    const bool sym_close = MODE == M_SUM && is_top_header && depth == base_depth + 1;
-    if (MODE == M_SUM && sym_close) {
-      st_pair(sd.hdrl_g, m.head_loop, W, L.w0, z[0][0], z[0][1]);
-      st_pair(sd.hdrl_p, m.head_loop, W, L.w0, z[1][0], z[1][1]);
-      z[NP - 1][0] = z[NP - 1][1] = 0;
+    // value leaves the loop without the header planes.  Liveness keeps A
+    // for the resolve; the loop masks need values at their own header only.
+    const bool sym_close = is_top_header && depth == base_depth + 1;
+    if (sym_close) {
+      if (MODE == M_SUM) {
+        st_pair(sd.hdrl_g, m.head_loop, W, L.w0, z[0][0], z[0][1]);
+        st_pair(sd.hdrl_p, m.head_loop, W, L.w0, z[1][0], z[1][1]);
+      }
+#pragma unroll
+      for (int pl = 2; pl < NP; ++pl) z[pl][0] = z[pl][1] = 0;
     }
     if (m.bslot >= 0) {
       bool changed = false;
@@ -1300,7 +1314,7 @@ __device__ __forceinline__ void bwd_walk(const DevPlan &p, const ScanDev &sd, co
 // anywhere in the body, by one walk of the body (Sec. IV-D loop rule).
 __device__ __forceinline__ void lant_walk(const DevPlan &p, const ScanDev &sd, const WarpMem &wm, uint64_t *spill,
                                           int l, int wg) {
-  constexpr int NP = 2;
+  constexpr int NP = BwdPlanes<M_LANT>::NP;
   const int W = p.W;
   const LoopMeta lm = sd.loops[l];
   Lane L;
@@ -2138,8 +2152,8 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     const int items = C * G;
     const int NPS = BwdPlanes<M_SUM>::NP;
     st->shape[CK_BSUM] = chain_shape(k_bwd_chain<M_SUM>, st->bslots, NPS, false, BWD_SH_WORDS, wpc, items, n_sm);
-    st->shape[CK_BLANT] =
-        chain_shape(k_bwd_chain<M_LANT>, st->bslots, 2, true, BWD_SH_WORDS, wpc, std::max(1, g.L) * G, n_sm);
+    st->shape[CK_BLANT] = chain_shape(k_bwd_chain<M_LANT>, st->bslots, BwdPlanes<M_LANT>::NP, true,
+                                      OMPDART_LANT_SH_WORDS, wpc, std::max(1, g.L) * G, n_sm);
     st->shape[CK_FSUM] = chain_shape(k_fwd_chain<K_HP>, st->fslots, 2, false, FWD_SH_WORDS, wpc, items, n_sm);
     chain_shape(k_fwd_chain<K_D>, st->fslots, 2, false, FWD_SH_WORDS, wpc, items, n_sm);
     chain_shape(k_fwd_chain<K_H>, st->fslots, 2, false, FWD_SH_WORDS, wpc, items, n_sm);
@@ -2149,7 +2163,7 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   // slots beyond those a kernel keeps in shared memory spill to a per-warp area
   {
     const int fwd = std::max(0, st->fslots - st->shape[CK_FSUM].sh_slots) * 2 * 64;
-    const int lant = std::max(0, st->bslots - st->shape[CK_BLANT].sh_slots) * 2 * 64;
+    const int lant = std::max(0, st->bslots - st->shape[CK_BLANT].sh_slots) * BwdPlanes<M_LANT>::NP * 64;
     const int NPS = BwdPlanes<M_SUM>::NP;
     const int live = std::max(0, st->bslots - st->shape[CK_BSUM].sh_slots) * NPS * 64;
     sd.spill_stride = std::max({64, fwd, lant, live});
