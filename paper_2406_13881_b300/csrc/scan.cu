@@ -35,6 +35,7 @@
 #include <vector>
 
 #include "ingest.h"
+#include "parallel.h"
 #include "plan.cuh"
 #include "solver.h"
 
@@ -256,19 +257,6 @@ struct Colouring {
   }
 };
 
-// f(t, lo, hi) for t < T over [0, n) split in T contiguous ranges, on up to
-// `max_threads` host threads (the calling thread takes t = 0); returns T
-template <class F>
-int parallel_ranges(int n, int min_per_thread, int max_threads, F f) {
-  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
-  const int T = std::max(1, std::min({hw, max_threads, n / std::max(1, min_per_thread)}));
-  std::vector<std::thread> pool;
-  for (int t = 1; t < T; ++t)
-    pool.emplace_back(f, t, (int)((long long)n * t / T), (int)((long long)n * (t + 1) / T));
-  f(0, 0, (int)((long long)n / T));
-  for (auto &x : pool) x.join();
-  return T;
-}
 
 }  // namespace
 
