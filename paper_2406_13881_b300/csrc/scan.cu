@@ -155,6 +155,8 @@ struct ScanDev {
   int spill_stride;    // words per warp
   uint64_t *gsum, *psum;   // [planes][C][W] chunk maps
   uint64_t *carry;         // [planes][C][W] carry into each chunk
+  uint64_t *seg_g, *seg_p;  // [S][W] maps of the scan's segments (one region per branch of a run)
+  int seg_n;                // segments per word column of the chunk-carry scan
   uint64_t *hp_src, *d_src;  // [K][W] plain host / device validity at loop-entry sources
   // affine pairs the summary walks leave per position: value = G | (carry & P)
   // with the carry into the position's chunk (resolved by k_resolve_*)
@@ -1622,11 +1624,18 @@ __device__ __forceinline__ void compose_after(uint64_t &g, uint64_t &p, uint64_t
   p = p1 & p;
 }
 
+// The walk order of a word column's chunks is cut into S segments, one CTA
+// each (grid W x S): phase 0 leaves each segment's map in seg; phase 1
+// composes the maps of the segments before its own into the carry entering
+// it, then scans its runs again and writes every chunk's carry.
+template <int PHASE>
 __global__ void __launch_bounds__(SCAN_T) k_scan_carry(ScanDev sd, int W, int backward, const uint64_t *init) {
   __shared__ uint64_t wg_s[SCAN_T / 32], wp_s[SCAN_T / 32];
-  const int w = blockIdx.x, t = threadIdx.x, lane = t & 31, wid = t >> 5;
-  const int C = sd.C, per = (C + SCAN_T - 1) / SCAN_T;
-  const int b = t * per, e = min(C, b + per);
+  const int w = blockIdx.x, sg = blockIdx.y, S = gridDim.y, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+  const int C = sd.C;
+  const int s0 = (int)((long long)C * sg / S), s1 = (int)((long long)C * (sg + 1) / S);
+  const int per = (s1 - s0 + SCAN_T - 1) / SCAN_T;
+  const int b = s0 + t * per, e = min(s1, b + per);
   const int32_t rflag = backward ? CH_LAST : CH_FIRST;
   auto chunk = [&](int k) { return backward ? C - 1 - k : k; };  // k-th chunk in walk order
   auto reset_val = [&](int c) -> uint64_t {
@@ -1684,11 +1693,25 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_carry(ScanDev sd, int W, int ba
     wp_s[lane] = q;
   }
   __syncthreads();
+  if (PHASE == 0) {  // the segment's map
+    if (t == 0) {
+      sd.seg_g[(size_t)sg * W + w] = wg_s[SCAN_T / 32 - 1];
+      sd.seg_p[(size_t)sg * W + w] = wp_s[SCAN_T / 32 - 1];
+    }
+    return;
+  }
   if (wid > 0) compose_after(g, pp, wg_s[wid - 1], wp_s[wid - 1]);
-  // carry entering run t: the inclusive map of runs < t applied to nothing
-  // (every walk starts at a CFG's first chunk, which resets)
-  uint64_t x = __shfl_up_sync(0xffffffffu, g, 1);
-  if (lane == 0) x = wid > 0 ? wg_s[wid - 1] : 0ull;
+  // the value entering the segment: the maps of the segments before it
+  // applied to nothing (every walk starts at a CFG's first chunk, which resets)
+  uint64_t cin = 0;
+  for (int q = 0; q < sg; ++q) cin = sd.seg_g[(size_t)q * W + w] | (cin & sd.seg_p[(size_t)q * W + w]);
+  // carry entering run t: the segment's runs before t applied to cin
+  uint64_t xg = __shfl_up_sync(0xffffffffu, g, 1), xp = __shfl_up_sync(0xffffffffu, pp, 1);
+  if (lane == 0) {
+    xg = wid > 0 ? wg_s[wid - 1] : 0ull;
+    xp = wid > 0 ? wp_s[wid - 1] : ~0ull;
+  }
+  uint64_t x = xg | (cin & xp);
   // 3. every chunk's carry
   for (int k0 = b; k0 < e; k0 += SCAN_B) {
     load_batch(k0);
@@ -2165,6 +2188,14 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     cudaMemset(sd.psum, 0, sizeof(uint64_t) * 2 * C * W);
   }
   chk(sd.carry = st->alloc<uint64_t>((size_t)2 * C * W));
+  {
+    // chunk-carry scan: about two CTAs per SM over the word columns' segments
+    int dev = 0, n_sm = 148;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    sd.seg_n = std::max(1, std::min(16, std::min(2 * n_sm / std::max(1, W), (C + 255) / 256)));
+    chk(sd.seg_g = st->alloc<uint64_t>((size_t)2 * sd.seg_n * W));  // one region per branch
+    chk(sd.seg_p = st->alloc<uint64_t>((size_t)2 * sd.seg_n * W));
+  }
   chk(sd.hp_src = st->alloc<uint64_t>((size_t)std::max(1, g.K) * W));
   chk(sd.d_src = st->alloc<uint64_t>((size_t)std::max(1, g.K) * W));
   // emission items: runs of at most EMIT_SPAN positions inside one chunk,
@@ -2280,6 +2311,15 @@ void chain_launch(K kern, const ChainShape &cs, const DevPlan &p, const ScanDev 
   kern<<<cs.grid, 32 * cs.wpc, cs.smem, s>>>(p, sd2, qslot);
 }
 
+// The chunk-carry scan of one problem: segment maps, then the carries (one
+// launch when a column is one segment).  Returns the launches.
+static int scan_carries(const ScanDev &x, int W, int backward, const uint64_t *init, cudaStream_t s) {
+  const dim3 grid(W, x.seg_n);
+  if (x.seg_n > 1) k_scan_carry<0><<<grid, SCAN_T, 0, s>>>(x, W, backward, init);
+  k_scan_carry<1><<<grid, SCAN_T, 0, s>>>(x, W, backward, init);
+  return x.seg_n > 1 ? 2 : 1;
+}
+
 // One run: local summaries; per phase a summary walk that leaves every
 // position's affine pair, the scan of the chunk maps, and a parallel resolve
 // of the pairs with the carries; then the emission from the final states.
@@ -2305,6 +2345,8 @@ int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *p
   sq.gsum = sd.gsum + (size_t)C * W;
   sq.psum = sd.psum + (size_t)C * W;
   sq.carry = sd.carry + (size_t)C * W;
+  sq.seg_g = sd.seg_g + (size_t)sd.seg_n * W;
+  sq.seg_p = sd.seg_p + (size_t)sd.seg_n * W;
   cudaMemsetAsync(p.acc_flag, 0, (size_t)p.A, s);
   cudaMemsetAsync(sd.queue, 0, sizeof(int32_t) * Q_SLOTS, s);
   PROF("local_summary");
@@ -2323,7 +2365,7 @@ int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *p
   PROF("live_summary");
   chain_launch(k_bwd_chain<M_SUM>, st->shape[CK_BSUM], p, sl, 0, s_live); ++n;
   PROF("live_scan");
-  k_scan_carry<<<W, SCAN_T, 0, s_live>>>(sl, W, 1, nullptr); ++n;
+  n += scan_carries(sl, W, 1, nullptr, s_live);
   PROF("live_resolve");
   k_resolve<RV_LIVE><<<grid_of((nw + 1) / 2, 256), 256, 0, s_live>>>(p, sl, sl.pair_g, sl.pair_p, p.live); ++n;
   if (fork) {
@@ -2336,7 +2378,7 @@ int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *p
   PROF("hp_summary");
   chain_launch(k_fwd_chain<K_HP>, st->shape[CK_FSUM], p, sq, 3, s); ++n;
   PROF("fwd_scan");
-  k_scan_carry<<<W, SCAN_T, 0, s>>>(sq, W, 0, init); ++n;
+  n += scan_carries(sq, W, 0, init, s);
   if (p.L) {
     PROF("loop_abs");
     k_loop_abs<<<grid_of((long long)p.L * W, 256), 256, 0, s>>>(p, sq); ++n;
@@ -2354,7 +2396,7 @@ int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *p
   PROF("d_summary");
   chain_launch(k_fwd_chain<K_D>, st->shape[CK_FSUM], p, sq, 5, s); ++n;
   PROF("fwd_scan");
-  k_scan_carry<<<W, SCAN_T, 0, s>>>(sq, W, 0, init); ++n;
+  n += scan_carries(sq, W, 0, init, s);
   if (p.L) {
     PROF("loop_abs");
     k_loop_abs<<<grid_of((long long)p.L * W, 256), 256, 0, s>>>(p, sq); ++n;
@@ -2377,7 +2419,7 @@ int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *p
   PROF("h_summary");
   chain_launch(k_fwd_chain<K_H>, st->shape[CK_FSUM], p, sq, 7, s); ++n;
   PROF("fwd_scan");
-  k_scan_carry<<<W, SCAN_T, 0, s>>>(sq, W, 0, init); ++n;
+  n += scan_carries(sq, W, 0, init, s);
   if (p.L) {
     PROF("loop_abs");
     k_loop_abs<<<grid_of((long long)p.L * W, 256), 256, 0, s>>>(p, sq); ++n;
