@@ -139,6 +139,7 @@ int build_arena(Arena *a, const std::vector<int32_t> &members, const std::vector
   std::vector<uint32_t> acc;
   std::vector<uint64_t> top, eh, ed, xl, table;
   CallHost calls;
+  std::map<std::tuple<const void *, const void *, const void *, int, int>, int> same;
   a->site_off.assign(1, 0);
   acc_off.reserve(a->core.g.N + 1);
   acc.reserve(a->core.g.A);
@@ -155,10 +156,20 @@ int build_arena(Arena *a, const std::vector<int32_t> &members, const std::vector
     for (int b = 0; b < g.N; ++b)
       if (g.pos[b] < 0) unreach_cfg.push_back((int32_t)k);
     exit_local.insert(exit_local.end(), g.exit_blocks.begin(), g.exit_blocks.end());
-    calls.row_base.push_back(calls.rows);
-    if (c.call_planes && c.n_calls > 0) {
-      table.insert(table.end(), c.call_planes, c.call_planes + (size_t)c.n_calls * 7 * W);
-      calls.rows += c.n_calls;
+    // a CFG given with the same arrays and call table as an earlier member
+    // (one function in several contexts) shares its table rows and folds
+    const auto key = std::make_tuple((const void *)c.succ_off, (const void *)c.acc, (const void *)c.call_planes,
+                                     c.n_blocks, c.n_calls);
+    const int first = same.emplace(key, (int)k).first->second;
+    calls.same_as.push_back(first);
+    if (first != (int)k) {
+      calls.row_base.push_back(calls.row_base[first]);
+    } else {
+      calls.row_base.push_back(calls.rows);
+      if (c.call_planes && c.n_calls > 0) {
+        table.insert(table.end(), c.call_planes, c.call_planes + (size_t)c.n_calls * 7 * W);
+        calls.rows += c.n_calls;
+      }
     }
     for (int i = 0; i < c.acc_off[g.N]; ++i)
       if (c.acc[i] >> 31) site_local.push_back(i);

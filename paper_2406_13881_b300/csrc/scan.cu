@@ -2014,14 +2014,29 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   std::vector<Folded> fold(kThreads);
   std::vector<int32_t> cnt(g.M + 1, 0);
   std::atomic<bool> too_big{false};
-  parallel_ranges(g.M, kMinPos, kThreads, [&](int t, int lo, int hi) {
+  // a call block of a CFG given with the same arrays and table as an earlier
+  // one takes that CFG's folded records (the same position in its order)
+  auto twin = [&](int i) -> int {
+    if (calls.same_as.empty()) return -1;
+    const int cfg = (int)(std::upper_bound(g.cfg_pos_off.begin(), g.cfg_pos_off.end(), i) - g.cfg_pos_off.begin()) - 1;
+    const int f = calls.same_as[cfg];
+    return f == cfg ? -1 : i - g.cfg_pos_off[cfg] + g.cfg_pos_off[f];
+  };
+  std::vector<int32_t> twin_pos;  // call positions that copy a twin's records
+  std::mutex twin_mu;
+  const int T = parallel_ranges(g.M, kMinPos, kThreads, [&](int t, int lo, int hi) {
     Folded &fd = fold[t];
+    std::vector<int32_t> mine;
     for (int i = lo; i < hi; ++i) {
       const int b = meta[i].blk, a0 = acc_off[b], a1 = acc_off[b + 1];
       bool has_call = false;
       for (int k = a0; k < a1 && calls.rows; ++k) has_call |= (acc[k] >> 31) != 0;
       int n = a1 - a0;
       if (has_call) {
+        if (twin(i) >= 0) {
+          mine.push_back(i);
+          continue;
+        }
         if (fd.var_idx.empty()) fd.var_idx.assign((size_t)p.W * 64, -1);
         const int cfg =
             (int)(std::upper_bound(g.cfg_pos_off.begin(), g.cfg_pos_off.end(), i) - g.cfg_pos_off.begin()) - 1;
@@ -2034,7 +2049,19 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
       if (n > 32767) too_big = true;
       cnt[i + 1] = n;
     }
+    std::lock_guard<std::mutex> lk(twin_mu);
+    twin_pos.insert(twin_pos.end(), mine.begin(), mine.end());
   });
+  // where each folded position's records are: (thread, first record)
+  std::unordered_map<int32_t, std::pair<int, int32_t>> folded_at;
+  std::vector<uint8_t> is_twin;
+  if (!twin_pos.empty()) {
+    for (int t = 0; t < T; ++t)
+      for (const auto &x : fold[t].at) folded_at.emplace(x.first, std::make_pair(t, x.second));
+    is_twin.assign(g.M, 0);
+    for (int i : twin_pos) is_twin[i] = 1;
+  }
+  for (int i : twin_pos) cnt[i + 1] = cnt[twin(i) + 1];
   if (too_big) {
     if (err) *err = "a block with more than 32767 accesses (or variables touched by its calls)";
     delete st;
@@ -2061,6 +2088,17 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
         std::fill(acc_link.begin() + base, acc_link.begin() + base + m.nacc, make_int2(LINK_RECORD, -1));
         m.flags = PM_RECORDS;
         continue;
+      }
+      if (!is_twin.empty() && is_twin[i]) {
+        const auto it = folded_at.find(twin(i));
+        if (it != folded_at.end()) {  // a call block folded for its twin
+          const std::vector<uint32_t> &recs = fold[it->second.first].recs;
+          std::copy(recs.begin() + it->second.second, recs.begin() + it->second.second + m.nacc,
+                    acc_p.begin() + base);
+          std::fill(acc_link.begin() + base, acc_link.begin() + base + m.nacc, make_int2(LINK_RECORD, -1));
+          m.flags = PM_RECORDS;
+          continue;
+        }
       }
       std::copy(acc + a0, acc + a1, acc_p.begin() + base);
       if (a1 - a0 <= 64) {

@@ -59,6 +59,10 @@ struct CallHost {
   const uint64_t *planes = nullptr;  // [rows][7][W]
   int rows = 0;
   std::vector<int32_t> row_base;     // per CFG of the plan (empty: 0)
+  // per CFG of the plan: the first CFG given with the same arrays and call
+  // table (its blocks fold to the same records), itself if none; empty: all
+  // distinct
+  std::vector<int32_t> same_as;
 };
 
 // ---- calls.cu: the call-site pass (after the host-validity pass)

@@ -79,3 +79,24 @@ def test_calls_need_the_scan_solver():
     b = _native.Batch([g, wl.single_small(2)])
     assert list(b.status) == [_native.E_INVALID, 0]
     b.close()
+
+
+def test_batch_one_function_in_several_contexts():
+    """The same CFG arrays (calls included) given several times with other
+    boundary rows, as the program driver does for a function's calling
+    contexts: ingested and folded once, every context still exact."""
+    import copy
+    rng = np.random.default_rng(77)
+    bases = [structured_with_calls(600 + i, 120 + 50 * i, 100) for i in range(3)]
+    cfgs = []
+    for k in range(12):
+        g = copy.copy(bases[k % 3])
+        W = g.W
+        g.entry_host_valid = rng.integers(0, 2**63, size=W, dtype=np.uint64)
+        g.entry_dev_valid = rng.integers(0, 2**63, size=W, dtype=np.uint64)
+        g.exit_host_live = rng.integers(0, 2**63, size=W, dtype=np.uint64)
+        cfgs.append(g)
+    res, st = _native.analyze_batch(cfgs, keep_states=True)
+    assert (st == 0).all()
+    for g, r in zip(cfgs, res):
+        assert_matches_oracle(g, r, oracle.solve(g))
