@@ -9,15 +9,19 @@
 // goes back), so the influence of one chunk on the next is one bit plane
 // and a chunk's effect on it is one affine map  carry' = G | (carry & P).
 // Each phase therefore runs as
-//   summary  (one warp per chunk and 64-variable word group: G and P),
+//   summary  (one warp per chunk and 64-variable word group: the chunk's
+//            map and every position's affine pair),
 //   scan     (compose the maps over the chunks: every chunk's carry),
-//   apply    (one warp per chunk: final values, outputs, emission).
-// Inside a chunk the warp walks positions in order; a loop body (a
-// contiguous run starting at its header) is walked again only when the
-// value entering its header grew (closed form of a loop: header = entry |
-// what the body contributes along its back edges, so one more pass is
-// exact; Kam-Ullman rapidity).  Values a later position still needs live
-// in slots assigned on the host by interval colouring (16 per plane in
+//   resolve  (every position's pair with its carry: the final plane),
+// and the emission reads the final planes.  Inside a chunk the warp walks
+// positions in order.  A loop body is a contiguous run starting at its
+// header; its header's value has a closed form (entry | what the body
+// contributes along its back edges: Kam-Ullman rapidity), so the forward
+// walks take every body once relative to the header's value and compose
+// at its end, and the backward walks take their outermost open loops once
+// with extra planes for the header's value (deeper loops are walked again
+// when their header's value grew).  Values a later position still needs
+// live in slots assigned on the host by interval colouring (a few in
 // shared memory, the rest spilled to global scratch).
 #include <cuda_runtime.h>
 
