@@ -171,8 +171,9 @@ int build_arena(Arena *a, const std::vector<int32_t> &members, const std::vector
         calls.rows += c.n_calls;
       }
     }
-    for (int i = 0; i < c.acc_off[g.N]; ++i)
-      if (c.acc[i] >> 31) site_local.push_back(i);
+    if (c.call_planes)  // call accesses come with a call table (checked at ingestion)
+      for (int i = 0; i < c.acc_off[g.N]; ++i)
+        if (c.acc[i] >> 31) site_local.push_back(i);
     a->site_off.push_back((int32_t)site_local.size());
     a->n_vars.push_back(c.n_vars);
     a->n_edges.push_back(g.E);

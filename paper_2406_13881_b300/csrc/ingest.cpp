@@ -1,5 +1,6 @@
 // ingest.cpp -- host-side ingestion of one CFG (see ingest.h).
 #include "ingest.h"
+#include "parallel.h"
 
 #include <algorithm>
 #include <cstring>
@@ -401,53 +402,92 @@ int ingest(const ompdart_cfg *c, Ingest *g, std::string *err) {
 
 void concat_ingests(const std::vector<const Ingest *> &parts, Ingest *o) {
   *o = Ingest();
-  o->cfg_pos_off.push_back(0);
-  o->fin_off.push_back(0);
-  o->out_off.push_back(0);
-  o->body_off.push_back(0);
-  for (const Ingest *g : parts) {
-    const int bo = o->N, eo = o->E, ao = o->A, po = o->M, lo = o->L, ko = o->K;
-    o->N += g->N;
-    o->E += g->E;
+  // every part's offsets first, then the parts copied in parallel
+  struct Off {
+    int64_t n, e, m, l, k, fin, out, x, body;
+  };
+  const int P = (int)parts.size();
+  std::vector<Off> off(P + 1, Off{0, 0, 0, 0, 0, 0, 0, 0, 0});
+  for (int q = 0; q < P; ++q) {
+    const Ingest *g = parts[q];
+    off[q + 1] = Off{off[q].n + g->N, off[q].e + g->E, off[q].m + g->M, off[q].l + g->L, off[q].k + g->K,
+                     off[q].fin + (int64_t)g->fin_src.size(), off[q].out + (int64_t)g->out_dst.size(),
+                     off[q].x + (int64_t)g->exit_blocks.size(), off[q].body + (int64_t)g->body_blk.size()};
     o->A += g->A;
-    o->M += g->M;
-    o->L += g->L;
-    o->K += g->K;
     o->V = g->V;
     o->W = g->W;
-    for (int b : g->order) o->order.push_back(b + bo);
-    for (int p : g->pos) o->pos.push_back(p < 0 ? -1 : p + po);
-    for (int i = 0; i < g->M; ++i) {
-      for (int k = g->fin_off[i]; k < g->fin_off[i + 1]; ++k) {
-        o->fin_src.push_back(g->fin_src[k] + bo);
-        o->fin_eid.push_back(g->fin_eid[k]);  // edge ids stay local to their CFG
-        o->fin_ent.push_back(g->fin_ent[k] < 0 ? -1 : g->fin_ent[k] + ko);
-      }
-      o->fin_off.push_back((int32_t)o->fin_src.size());
-      for (int k = g->out_off[i]; k < g->out_off[i + 1]; ++k) o->out_dst.push_back(g->out_dst[k] + bo);
-      o->out_off.push_back((int32_t)o->out_dst.size());
-      o->is_exit.push_back(g->is_exit[i]);
-    }
-    for (int b : g->exit_blocks) o->exit_blocks.push_back(b + bo);
-    for (int l = 0; l < g->L; ++l) {
-      o->loop_head.push_back(g->loop_head[l] + bo);
-      o->loop_parent.push_back(g->loop_parent[l] < 0 ? -1 : g->loop_parent[l] + lo);
-      o->loop_depth.push_back(g->loop_depth[l]);
-      o->loop_end.push_back(g->loop_end[l] + po);
-      for (int q = g->body_off[l]; q < g->body_off[l + 1]; ++q) o->body_blk.push_back(g->body_blk[q] + bo);
-      o->body_off.push_back((int32_t)o->body_blk.size());
-    }
-    for (int x : g->inner_loop) o->inner_loop.push_back(x < 0 ? -1 : x + lo);
-    for (int k = 0; k < g->K; ++k) {
-      o->ent_loop.push_back(g->ent_loop[k] + lo);
-      o->ent_src.push_back(g->ent_src[k] + bo);
-      o->ent_eid.push_back(g->ent_eid[k] + eo);
-    }
     o->reducible = o->reducible && g->reducible;
     o->contiguous = o->contiguous && g->contiguous;
-    o->cfg_pos_off.push_back(o->M);
-    (void)ao;
   }
+  const Off &t = off[P];
+  o->N = (int)t.n;
+  o->E = (int)t.e;
+  o->M = (int)t.m;
+  o->L = (int)t.l;
+  o->K = (int)t.k;
+  o->order.resize(t.m);
+  o->pos.resize(t.n);
+  o->fin_off.resize(t.m + 1);
+  o->fin_src.resize(t.fin);
+  o->fin_eid.resize(t.fin);
+  o->fin_ent.resize(t.fin);
+  o->out_off.resize(t.m + 1);
+  o->out_dst.resize(t.out);
+  o->is_exit.resize(t.m);
+  o->exit_blocks.resize(t.x);
+  o->loop_head.resize(t.l);
+  o->loop_parent.resize(t.l);
+  o->loop_depth.resize(t.l);
+  o->loop_end.resize(t.l);
+  o->body_off.resize(t.l + 1);
+  o->body_blk.resize(t.body);
+  o->inner_loop.resize(t.n);
+  o->ent_loop.resize(t.k);
+  o->ent_src.resize(t.k);
+  o->ent_eid.resize(t.k);
+  o->cfg_pos_off.resize(P + 1);
+  o->fin_off[t.m] = (int32_t)t.fin;
+  o->out_off[t.m] = (int32_t)t.out;
+  o->body_off[t.l] = (int32_t)t.body;
+  o->cfg_pos_off[P] = (int32_t)t.m;
+  parallel_ranges(P, 64, 8, [&](int, int lo_p, int hi_p) {
+    for (int q = lo_p; q < hi_p; ++q) {
+      const Ingest *g = parts[q];
+      const Off &f = off[q];
+      const int bo = (int)f.n, eo = (int)f.e, po = (int)f.m, lo = (int)f.l, ko = (int)f.k;
+      o->cfg_pos_off[q] = po;
+      for (int i = 0; i < g->M; ++i) {
+        o->order[po + i] = g->order[i] + bo;
+        o->fin_off[po + i] = g->fin_off[i] + (int32_t)f.fin;
+        o->out_off[po + i] = g->out_off[i] + (int32_t)f.out;
+        o->is_exit[po + i] = g->is_exit[i];
+      }
+      for (int b = 0; b < g->N; ++b) {
+        o->pos[bo + b] = g->pos[b] < 0 ? -1 : g->pos[b] + po;
+        o->inner_loop[bo + b] = g->inner_loop[b] < 0 ? -1 : g->inner_loop[b] + lo;
+      }
+      for (size_t k = 0; k < g->fin_src.size(); ++k) {
+        o->fin_src[f.fin + k] = g->fin_src[k] + bo;
+        o->fin_eid[f.fin + k] = g->fin_eid[k];  // edge ids stay local to their CFG
+        o->fin_ent[f.fin + k] = g->fin_ent[k] < 0 ? -1 : g->fin_ent[k] + ko;
+      }
+      for (size_t k = 0; k < g->out_dst.size(); ++k) o->out_dst[f.out + k] = g->out_dst[k] + bo;
+      for (size_t k = 0; k < g->exit_blocks.size(); ++k) o->exit_blocks[f.x + k] = g->exit_blocks[k] + bo;
+      for (int l = 0; l < g->L; ++l) {
+        o->loop_head[lo + l] = g->loop_head[l] + bo;
+        o->loop_parent[lo + l] = g->loop_parent[l] < 0 ? -1 : g->loop_parent[l] + lo;
+        o->loop_depth[lo + l] = g->loop_depth[l];
+        o->loop_end[lo + l] = g->loop_end[l] + po;
+        o->body_off[lo + l] = g->body_off[l] + (int32_t)f.body;
+      }
+      for (size_t k = 0; k < g->body_blk.size(); ++k) o->body_blk[f.body + k] = g->body_blk[k] + bo;
+      for (int k = 0; k < g->K; ++k) {
+        o->ent_loop[ko + k] = g->ent_loop[k] + lo;
+        o->ent_src[ko + k] = g->ent_src[k] + bo;
+        o->ent_eid[ko + k] = g->ent_eid[k] + eo;
+      }
+    }
+  });
   o->entry = parts.empty() ? 0 : parts[0]->entry;
   o->chunk_off.assign({0, o->M});
   o->max_chunk = o->M;
