@@ -443,15 +443,25 @@ def run_batch(args):
     # ---- CPU oracle on a bounded sample of the same CFGs
     import oracle
     oracle.build()
+    want = ["h_in", "d_in", "to_edge", "from_edge", "from_exit", "acc_flag"]
     t_cpu, n_cpu, u_cpu = 0.0, 0, 0
+    sample = []
     for g in cfgs[:: max(1, len(cfgs) // 400)]:
         t0 = time.perf_counter()
-        oracle.solve(g, want=["h_in", "d_in", "to_edge", "from_edge", "from_exit", "acc_flag"])
+        oracle.solve(g, want=want)
         t_cpu += time.perf_counter() - t0
         n_cpu += 1
         u_cpu += g.n_blocks * g.W
+        sample.append(g)
         if t_cpu > args.cpu_seconds:
             break
+    # the same sample, one CFG per host thread (the C oracle runs outside the GIL)
+    from concurrent.futures import ThreadPoolExecutor
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        list(ex.map(lambda g: oracle.solve(g, want=want), sample))
+    t_par = time.perf_counter() - t0
     value = job_value(units, world, args.steps, ms)
     cps = job_value(len(cfgs), world, args.steps, ms)
     if world > 1:
@@ -487,6 +497,10 @@ def run_batch(args):
                          "cfgs_per_s": n_cpu / t_cpu,
                          "sample": "%d CFGs (every %d-th), single-threaded C oracle, %.1f s"
                                    % (n_cpu, max(1, len(cfgs) // 400), t_cpu), "cpu": cpu_info()},
+        "cpu_baseline_parallel": {"value": u_cpu / t_par, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                  "cfgs_per_s": n_cpu / t_par,
+                                  "sample": "the same %d CFGs, one per host thread on %d threads, %.1f s"
+                                            % (n_cpu, cores, t_par)},
         "e2e": {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "seconds_per_step": e2e_s, "cfgs_per_s": len(cfgs) / e2e_s,
                 "path": "ompdart_analyze_batch: host ingestion + copies + solve + copy back"},
