@@ -139,7 +139,8 @@ int build_arena(Arena *a, const std::vector<int32_t> &members, const std::vector
   std::vector<uint32_t> acc;
   std::vector<uint64_t> top, eh, ed, xl, table;
   CallHost calls;
-  std::map<std::tuple<const void *, const void *, const void *, int, int>, int> same;
+  std::map<std::tuple<const void *, const void *, const void *, const void *, const void *, int, int, int, int>, int>
+      same;
   a->site_off.assign(1, 0);
   acc_off.reserve(a->core.g.N + 1);
   acc.reserve(a->core.g.A);
@@ -158,8 +159,9 @@ int build_arena(Arena *a, const std::vector<int32_t> &members, const std::vector
     exit_local.insert(exit_local.end(), g.exit_blocks.begin(), g.exit_blocks.end());
     // a CFG given with the same arrays and call table as an earlier member
     // (one function in several contexts) shares its table rows and folds
-    const auto key = std::make_tuple((const void *)c.succ_off, (const void *)c.acc, (const void *)c.call_planes,
-                                     c.n_blocks, c.n_calls);
+    const auto key = std::make_tuple((const void *)c.succ_off, (const void *)c.succ, (const void *)c.acc_off,
+                                     (const void *)c.acc, (const void *)c.call_planes, c.n_blocks, c.n_vars,
+                                     c.entry, c.n_calls);
     const int first = same.emplace(key, (int)k).first->second;
     calls.same_as.push_back(first);
     if (first != (int)k) {
