@@ -723,6 +723,40 @@ __device__ __forceinline__ void st_pair(uint64_t *plane, size_t row, int W, int 
     st_word(plane, row, W, w + 1, b);
   }
 }
+// The same for rows a walk touches once (the dense rows it reads, the pairs
+// it writes; the emission's Live and D_in rows): evict-first cache hints,
+// so that L1 and L2 keep the walks' spilled slots, which are read back a
+// few positions later, rather than the streams.  (The resolves, pure
+// streams themselves, ran 12% slower with these hints, so they have none.)
+#ifndef OMPDART_STREAM_HINTS
+#define OMPDART_STREAM_HINTS 1
+#endif
+__device__ __forceinline__ ulonglong2 ld_stream(const ulonglong2 *a) {
+#if OMPDART_STREAM_HINTS
+  return __ldcs(a);
+#else
+  return *a;
+#endif
+}
+__device__ __forceinline__ void st_stream(ulonglong2 *a, ulonglong2 v) {
+#if OMPDART_STREAM_HINTS
+  __stcs(a, v);
+#else
+  *a = v;
+#endif
+}
+__device__ __forceinline__ ulonglong2 ld_pair_s(const uint64_t *plane, size_t row, int W, int w) {
+  if (!(W & 1) && w + 1 < W) return ld_stream(reinterpret_cast<const ulonglong2 *>(plane + row * W + w));
+  return make_ulonglong2(ld_word(plane, row, W, w), ld_word(plane, row, W, w + 1));
+}
+__device__ __forceinline__ void st_pair_s(uint64_t *plane, size_t row, int W, int w, uint64_t a, uint64_t b) {
+  if (!(W & 1) && w + 1 < W) {
+    st_stream(reinterpret_cast<ulonglong2 *>(plane + row * W + w), make_ulonglong2(a, b));
+  } else {
+    st_word(plane, row, W, w, a);
+    st_word(plane, row, W, w + 1, b);
+  }
+}
 
 // Rows of one mask table (64 words each): the affine walks keep [set,
 // clear] of the local plane and one `clear' row shared by the coefficient
@@ -947,14 +981,14 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
       if (ppos == i) {
         lv[0] = plv[0]; lv[1] = plv[1]; din[0] = pdin[0]; din[1] = pdin[1];
       } else {
-        { const ulonglong2 t = ld_pair(p.live, m.blk, W, L.w0); lv[0] = t.x; lv[1] = t.y; }
-        { const ulonglong2 t = ld_pair(p.d_in, m.blk, W, L.w0); din[0] = t.x; din[1] = t.y; }
+        { const ulonglong2 t = ld_pair_s(p.live, m.blk, W, L.w0); lv[0] = t.x; lv[1] = t.y; }
+        { const ulonglong2 t = ld_pair_s(p.d_in, m.blk, W, L.w0); din[0] = t.x; din[1] = t.y; }
       }
       ppos = -1;
       if (i + 1 < wr.we) {
         const int nb = w.meta[i + 1 - wr.mbase].blk;
-        { const ulonglong2 t = ld_pair(p.live, nb, W, L.w0); plv[0] = t.x; plv[1] = t.y; }
-        { const ulonglong2 t = ld_pair(p.d_in, nb, W, L.w0); pdin[0] = t.x; pdin[1] = t.y; }
+        { const ulonglong2 t = ld_pair_s(p.live, nb, W, L.w0); plv[0] = t.x; plv[1] = t.y; }
+        { const ulonglong2 t = ld_pair_s(p.d_in, nb, W, L.w0); pdin[0] = t.x; pdin[1] = t.y; }
         ppos = i + 1;
       }
     }
@@ -1031,16 +1065,16 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
     {
       const size_t row = (size_t)m.blk;
       if (PH == K_D) {  // device validity at the block entry (and exit, kept states)
-        st_pair(sd.pair_gd, row, W, L.w0, z[0][0], z[0][1]);
-        st_pair(sd.pair_pd, row, W, L.w0, z[1][0], z[1][1]);
+        st_pair_s(sd.pair_gd, row, W, L.w0, z[0][0], z[0][1]);
+        st_pair_s(sd.pair_pd, row, W, L.w0, z[1][0], z[1][1]);
         if (sd.pair_g2) {
-          st_pair(sd.pair_g2, row, W, L.w0, zo[0][0], zo[0][1]);
-          st_pair(sd.pair_p2, row, W, L.w0, zo[1][0], zo[1][1]);
+          st_pair_s(sd.pair_g2, row, W, L.w0, zo[0][0], zo[0][1]);
+          st_pair_s(sd.pair_p2, row, W, L.w0, zo[1][0], zo[1][1]);
         }
       }
       if (PH == K_H) {  // host validity at the block exit
-        st_pair(sd.pair_g, row, W, L.w0, zo[0][0], zo[0][1]);
-        st_pair(sd.pair_p, row, W, L.w0, zo[1][0], zo[1][1]);
+        st_pair_s(sd.pair_g, row, W, L.w0, zo[0][0], zo[0][1]);
+        st_pair_s(sd.pair_p, row, W, L.w0, zo[1][0], zo[1][1]);
       }
       if ((PH == K_HP || PH == K_D) && m.nsrcent) {  // at loop-entry sources
         for (int q = 0; q < m.nsrcent; ++q) {
@@ -1241,10 +1275,10 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
       if (is_top_header && !sym_close && __any_sync(0xffffffffu, changed)) dirty |= 1u << (depth - 1);
     }
     if (MODE == M_SUM) {  // Live_in as an affine pair of the chunk's carry (and A inside a loop)
-      st_pair(sd.pair_g, m.blk, W, L.w0, z[0][0], z[0][1]);
-      st_pair(sd.pair_p, m.blk, W, L.w0, z[1][0], z[1][1]);
+      st_pair_s(sd.pair_g, m.blk, W, L.w0, z[0][0], z[0][1]);
+      st_pair_s(sd.pair_p, m.blk, W, L.w0, z[1][0], z[1][1]);
       if (depth > base_depth) {
-        st_pair(sd.pair_a, m.blk, W, L.w0, z[NP - 1][0], z[NP - 1][1]);
+        st_pair_s(sd.pair_a, m.blk, W, L.w0, z[NP - 1][0], z[NP - 1][1]);
       }
     }
     __syncwarp();
@@ -1552,7 +1586,7 @@ __global__ void __launch_bounds__(32 * EMIT_WARPS, OMPDART_EMIT_MIN_CTAS)
   for (int i = rng.x; i < rng.y; ++i) {
     const PosMeta m = sd.meta[i];
     const size_t b = (size_t)m.blk;
-    const ulonglong2 lv = ld_pair(p.live, b, W, w0), di = ld_pair(p.d_in, b, W, w0);
+    const ulonglong2 lv = ld_pair_s(p.live, b, W, w0), di = ld_pair_s(p.d_in, b, W, w0);
     const uint64_t lv0 = lv.x, lv1 = lv.y, di0 = di.x, di1 = di.y;
     const uint64_t c0 = lv0 & ~di0, c1 = lv1 & ~di1;
     uint64_t z0 = 0, z1 = 0;
