@@ -53,8 +53,10 @@ def workload_name(n_blocks):
 # profiles/): dram__bytes_read.sum + dram__bytes_write.sum on the 2^18-block
 # version of the workload, scaled to the bench's launch by block-words
 MEASURED_TRAFFIC = {
-    "h_summary": {"bytes_2e18": (341007360 + 311611136 + 340936192 + 309394176) / 2.0,
+    "h_summary": {"bytes_2e18": (319374080 + 269608192 + 319529984 + 268443904) / 2.0,
                   "profile": "profiles/h_summary_walk_2e18.md"},
+    "live_summary": {"bytes_2e18": (40509696 + 359516160 + 40363264 + 357572608) / 2.0,
+                     "profile": "profiles/live_summary_walk_2e18.md"},
 }
 
 

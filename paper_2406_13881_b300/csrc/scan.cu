@@ -636,6 +636,7 @@ struct WinRegs {  // warp-uniform copy of the window bounds
 // Load the window containing position i: forward [i, i+WIN) clipped to hi,
 // backward (i-WIN, i] clipped to lo; shrunk so its edges and records fit.
 // A single position too large for the buffers is read from HBM directly.
+// A walk reads each window once: evict-first loads, like the dense rows.
 template <bool FWD>
 __device__ void load_window(Win &w, WinRegs &r, const ScanDev &sd, int i, int lo, int hi, int lane) {
   const unsigned FULL = 0xffffffffu;
@@ -643,7 +644,13 @@ __device__ void load_window(Win &w, WinRegs &r, const ScanDev &sd, int i, int lo
   const int n = FWD ? min(WIN, hi - i) : (i + 1 - mbase);
   int eb = 0, ee = 0, rb = 0, re = 0;
   if (lane < n) {
-    const PosMeta pm = sd.meta[mbase + lane];
+    PosMeta pm;
+    {
+      const ulonglong2 *src = reinterpret_cast<const ulonglong2 *>(sd.meta + mbase + lane);
+      ulonglong2 *dst = reinterpret_cast<ulonglong2 *>(&pm);
+#pragma unroll
+      for (int u = 0; u < 5; ++u) dst[u] = __ldcs(src + u);
+    }
     w.meta[lane] = pm;
     eb = FWD ? pm.fin_beg : pm.out_beg;
     ee = eb + (FWD ? pm.nfin : pm.nout);
@@ -674,8 +681,8 @@ __device__ void load_window(Win &w, WinRegs &r, const ScanDev &sd, int i, int lo
   const int r0 = __shfl_sync(FULL, rb, k0), r1 = __shfl_sync(FULL, re, k1);
   if (!big) {
     const int2 *src = FWD ? sd.fin_pk : sd.out_pk;
-    for (int j = lane; j < e1 - e0; j += 32) w.edge[j] = src[e0 + j];
-    for (int j = lane; j < r1 - r0; j += 32) w.rec[j] = sd.rec_p[r0 + j];
+    for (int j = lane; j < e1 - e0; j += 32) w.edge[j] = __ldcs(src + e0 + j);
+    for (int j = lane; j < r1 - r0; j += 32) w.rec[j] = __ldcs(sd.rec_p + r0 + j);
   }
   __syncwarp();
   r.mbase = mbase; r.ws = ws; r.we = we; r.e0 = e0; r.r0 = r0; r.big = big;
@@ -701,6 +708,23 @@ struct Slots {
     if (slot < nsh) return reinterpret_cast<ulonglong2 *>(sh + ((size_t)(slot * NP + plane) * 64) + 2 * lane);
     return reinterpret_cast<ulonglong2 *>(spill + ((size_t)((slot - nsh) * NP + plane) * 64) + 2 * lane);
   }
+  // Spilled slots are read back a few positions after they are written:
+  // their lines are kept in L1 ahead of the streams (evict-last).
+  __device__ ulonglong2 ld(int slot, int plane, int lane) const {
+    if (slot < nsh) return *at(slot, plane, lane);
+    const size_t g = __cvta_generic_to_global(at(slot, plane, lane));
+    ulonglong2 v;
+    asm volatile("ld.global.L1::evict_last.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(g) : "memory");
+    return v;
+  }
+  __device__ void st(int slot, int plane, int lane, ulonglong2 v) const {
+    if (slot < nsh) {
+      *at(slot, plane, lane) = v;
+      return;
+    }
+    const size_t g = __cvta_generic_to_global(at(slot, plane, lane));
+    asm volatile("st.global.L1::evict_last.v2.u64 [%0], {%1, %2};" ::"l"(g), "l"(v.x), "l"(v.y) : "memory");
+  }
 };
 
 __device__ __forceinline__ uint64_t ld_word(const uint64_t *plane, size_t row, int W, int w) {
@@ -724,7 +748,9 @@ __device__ __forceinline__ void st_pair(uint64_t *plane, size_t row, int W, int 
   }
 }
 // The same for rows a walk touches once (the dense rows it reads, the pairs
-// it writes; the emission's Live and D_in rows): evict-first cache hints,
+// it writes) and for the emission's rows (Live, D_in and H_in of its
+// positions, H_out of their sources, read by a few items at different
+// times, so not worth keeping either): evict-first cache hints,
 // so that L1 and L2 keep the walks' spilled slots, which are read back a
 // few positions later, rather than the streams.  (The resolves, pure
 // streams themselves, ran 12% slower with these hints, so they have none.)
@@ -905,22 +931,21 @@ __device__ __forceinline__ void close_loop(const ScanDev &sd, const Slots<2> &sl
   const LoopMeta lm = sd.loops[l];
   uint64_t a0 = 0, a1 = 0;
   for (int q = 0; q < lm.lat_cnt; ++q) {
-    const ulonglong2 v = *sl.at(sd.lat_slot[lm.lat_beg + q], 0, L.lane);
+    const ulonglong2 v = sl.ld(sd.lat_slot[lm.lat_beg + q], 0, L.lane);
     a0 |= v.x;
     a1 |= v.y;
   }
-  const ulonglong2 e0 = *sl.at(hs, 0, L.lane), e1 = *sl.at(hs, 1, L.lane);
+  const ulonglong2 e0 = sl.ld(hs, 0, L.lane), e1 = sl.ld(hs, 1, L.lane);
   const uint64_t h00 = e0.x | a0, h01 = e0.y | a1, h10 = e1.x | a0, h11 = e1.y | a1;
   st_pair(sd.hdr_g, l, W, L.w0, h00, h01);
   st_pair(sd.hdr_p, l, W, L.w0, h10, h11);
   for (int q = 0; q < lm.xs_cnt; ++q) {
     const int x = sd.exit_slot[lm.xs_beg + q];
-    ulonglong2 *g = sl.at(x, 0, L.lane), *pp = sl.at(x, 1, L.lane);
-    ulonglong2 v0 = *g, v1 = *pp;
+    ulonglong2 v0 = sl.ld(x, 0, L.lane), v1 = sl.ld(x, 1, L.lane);
     compose_pair(v0.x, v1.x, h00, h10);
     compose_pair(v0.y, v1.y, h01, h11);
-    *g = v0;
-    *pp = v1;
+    sl.st(x, 0, L.lane, v0);
+    sl.st(x, 1, L.lane, v1);
   }
   compose_pair(pv[0][0], pv[1][0], h00, h10);
   compose_pair(pv[0][1], pv[1][1], h01, h11);
@@ -1020,7 +1045,7 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
       }
 #pragma unroll
       for (int pl = 0; pl < NP; ++pl) {
-        const ulonglong2 v = *sl.at(slot, pl, L.lane);
+        const ulonglong2 v = sl.ld(slot, pl, L.lane);
         z[pl][0] |= v.x & m0;
         z[pl][1] |= v.y & m1;
       }
@@ -1030,7 +1055,7 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
     if (m.head_loop >= 0) {
       const int hs = m.head_hslot;
 #pragma unroll
-      for (int pl = 0; pl < NP; ++pl) *sl.at(hs, pl, L.lane) = make_ulonglong2(z[pl][0], z[pl][1]);
+      for (int pl = 0; pl < NP; ++pl) sl.st(hs, pl, L.lane, make_ulonglong2(z[pl][0], z[pl][1]));
       z[0][0] = z[0][1] = 0;
       z[1][0] = L.top0;
       z[1][1] = L.top1;
@@ -1054,7 +1079,7 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
     }
     if (m.fslot >= 0) {
 #pragma unroll
-      for (int pl = 0; pl < NP; ++pl) *sl.at(m.fslot, pl, L.lane) = make_ulonglong2(zo[pl][0], zo[pl][1]);
+      for (int pl = 0; pl < NP; ++pl) sl.st(m.fslot, pl, L.lane, make_ulonglong2(zo[pl][0], zo[pl][1]));
     }
 #pragma unroll
     for (int pl = 0; pl < NP; ++pl) {
@@ -1102,7 +1127,7 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
     if (PH != K_HP && cs.ent >= 0) { m0 = ~ld_word(ec, cs.ent, W, L.w0); m1 = ~ld_word(ec, cs.ent, W, L.w0 + 1); }
 #pragma unroll
     for (int pl = 0; pl < NP; ++pl) {
-      const ulonglong2 v = *sl.at(cs.slot, pl, L.lane);
+      const ulonglong2 v = sl.ld(cs.slot, pl, L.lane);
       co[pl][0] |= v.x & m0;
       co[pl][1] |= v.y & m1;
     }
@@ -1203,7 +1228,7 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
         const bool sym = bi.x == base_depth + 1;  // planes from 2 on: header coefficients
         if (hs >= 0)
           for (int pl = 0; pl < NP; ++pl)
-            *sl.at(hs, pl, L.lane) = sym && pl >= 2 ? make_ulonglong2(L.top0, L.top1) : make_ulonglong2(0ull, 0ull);
+            sl.st(hs, pl, L.lane, sym && pl >= 2 ? make_ulonglong2(L.top0, L.top1) : make_ulonglong2(0ull, 0ull));
         __syncwarp();
       }
     }
@@ -1233,7 +1258,7 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
       }
 #pragma unroll
       for (int pl = 0; pl < NP; ++pl) {
-        const ulonglong2 v = *sl.at(slot, pl, L.lane);
+        const ulonglong2 v = sl.ld(slot, pl, L.lane);
         z[pl][0] |= v.x;
         z[pl][1] |= v.y;
       }
@@ -1265,12 +1290,11 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
       bool changed = false;
 #pragma unroll
       for (int pl = 0; pl < NP; ++pl) {
-        ulonglong2 *ptr = sl.at(m.bslot, pl, L.lane);
         if (is_top_header && !sym_close) {
-          const ulonglong2 old = *ptr;
+          const ulonglong2 old = sl.ld(m.bslot, pl, L.lane);
           changed |= (old.x != z[pl][0]) || (old.y != z[pl][1]);
         }
-        *ptr = make_ulonglong2(z[pl][0], z[pl][1]);
+        sl.st(m.bslot, pl, L.lane, make_ulonglong2(z[pl][0], z[pl][1]));
       }
       if (is_top_header && !sym_close && __any_sync(0xffffffffu, changed)) dirty |= 1u << (depth - 1);
     }
@@ -1598,7 +1622,7 @@ __global__ void __launch_bounds__(32 * EMIT_WARPS, OMPDART_EMIT_MIN_CTAS)
       const int k = m.fin_beg + q;
       const int ent = sd.fin_pk[k].y;  // loop-entry edge or -1
       const size_t src = (size_t)p.fin_src[k];
-      const ulonglong2 ho = ld_pair(p.h_out, src, W, w0);
+      const ulonglong2 ho = ld_pair_s(p.h_out, src, W, w0);
       const uint64_t s0 = ~ho.x & top0, s1 = ~ho.y & top1;
       uint64_t m0 = 0, m1 = 0, to0 = 0, to1 = 0;
       if (ent >= 0) {
@@ -1618,7 +1642,7 @@ __global__ void __launch_bounds__(32 * EMIT_WARPS, OMPDART_EMIT_MIN_CTAS)
     z0 &= ~c0;
     z1 &= ~c1;
     const uint64_t hi0 = ~z0 & top0, hi1 = ~z1 & top1;
-    st_pair(p.h_in, b, W, w0, hi0, hi1);
+    st_pair_s(p.h_in, b, W, w0, hi0, hi1);
     if (m.nacc && !(m.flags & PM_RECORDS)) {  // flag table at the entry validity
       hd[2 * lane] = hi0;
       hd[2 * lane + 1] = hi1;
