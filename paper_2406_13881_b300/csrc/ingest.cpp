@@ -16,6 +16,31 @@ bool fail(std::string *err, const char *msg) {
   return false;
 }
 
+// Items per host thread below which a pass of the ingestion stays on the
+// calling thread (batches ingest many small CFGs on a pool already).
+#ifndef OMPDART_INGEST_PAR_MIN
+#define OMPDART_INGEST_PAR_MIN (1 << 16)
+#endif
+constexpr int kParMin = OMPDART_INGEST_PAR_MIN;
+constexpr int kParMax = 16;
+
+// The first i in [0, n) with bad(i), else n (ranges scanned in parallel).
+template <class F>
+int first_bad(int n, F bad) {
+  int first[kParMax];
+  const int T = parallel_ranges(n, kParMin, kParMax, [&](int t, int lo, int hi) {
+    first[t] = n;
+    for (int i = lo; i < hi; ++i)
+      if (bad(i)) {
+        first[t] = i;
+        return;
+      }
+  });
+  for (int t = 0; t < T; ++t)
+    if (first[t] < n) return first[t];
+  return n;
+}
+
 bool check_format(const ompdart_cfg *c, std::string *err) {
   if (!c) return fail(err, "cfg is NULL");
   if (c->n_blocks < 1) return fail(err, "n_blocks must be >= 1");
@@ -23,34 +48,42 @@ bool check_format(const ompdart_cfg *c, std::string *err) {
   if (c->entry < 0 || c->entry >= c->n_blocks) return fail(err, "entry out of range");
   if (!c->succ_off || !c->acc_off) return fail(err, "succ_off / acc_off missing");
   if (c->succ_off[0] != 0 || c->acc_off[0] != 0) return fail(err, "CSR offsets must start at 0");
-  for (int b = 0; b < c->n_blocks; ++b)
-    if (c->succ_off[b + 1] < c->succ_off[b] || c->acc_off[b + 1] < c->acc_off[b])
-      return fail(err, "CSR offsets must be non-decreasing");
+  if (first_bad(c->n_blocks, [&](int b) {
+        return c->succ_off[b + 1] < c->succ_off[b] || c->acc_off[b + 1] < c->acc_off[b];
+      }) < c->n_blocks)
+    return fail(err, "CSR offsets must be non-decreasing");
   const int E = c->succ_off[c->n_blocks], A = c->acc_off[c->n_blocks];
   if ((E && !c->succ) || (A && !c->acc)) return fail(err, "succ / acc missing");
-  for (int e = 0; e < E; ++e) {
+  // the first bad edge and the first bad access decide the message
+  const int e = first_bad(E, [&](int k) { return c->succ[k] < 0 || c->succ[k] >= c->n_blocks || c->succ[k] == c->entry; });
+  if (e < E) {
     if (c->succ[e] < 0 || c->succ[e] >= c->n_blocks) return fail(err, "successor id out of range");
-    if (c->succ[e] == c->entry) return fail(err, "the entry block must have no predecessors");
+    return fail(err, "the entry block must have no predecessors");
   }
-  for (int i = 0; i < A; ++i) {
+  auto acc_msg = [&](int i) -> const char * {
     const uint32_t a = c->acc[i];
     if (a >> 31) {
-      if (!c->call_planes || (int)(a & 0x7FFFFFFFu) >= c->n_calls)
-        return fail(err, "call access without a matching call-table row");
-      continue;
+      if (!c->call_planes || (int)(a & 0x7FFFFFFFu) >= c->n_calls) return "call access without a matching call-table row";
+      return nullptr;
     }
-    if ((a >> 27) & 0xFu) return fail(err, "reserved access bits 27-30 must be zero");
-    if ((int)(a & 0xFFFFFFu) >= c->n_vars) return fail(err, "access variable out of range");
-    if (((a >> 24) & 3u) == 0) return fail(err, "access kind must be 1, 2 or 3");
-  }
+    if ((a >> 27) & 0xFu) return "reserved access bits 27-30 must be zero";
+    if ((int)(a & 0xFFFFFFu) >= c->n_vars) return "access variable out of range";
+    if (((a >> 24) & 3u) == 0) return "access kind must be 1, 2 or 3";
+    return nullptr;
+  };
+  const int a = first_bad(A, [&](int i) { return acc_msg(i) != nullptr; });
+  if (a < A) return fail(err, acc_msg(a));
   return true;
 }
 
 // Lengauer-Tarjan immediate dominators over blocks reachable from `entry`.
-// preorder[] lists reachable blocks in DFS preorder; idom[entry] = entry.
+// preorder[] lists reachable blocks in DFS preorder, dfn[] is each block's
+// index there (-1 if unreachable), and idom[] the DFS number of each DFS
+// number's immediate dominator (idom[0] = 0, the entry).
 void lengauer_tarjan(int N, int entry, const std::vector<int32_t> &so, const int32_t *succ,
                      const std::vector<int32_t> &po, const std::vector<int32_t> &psrc,
-                     std::vector<int32_t> *preorder_out, std::vector<int32_t> *idom_out) {
+                     std::vector<int32_t> *preorder_out, std::vector<int32_t> *dfn_out,
+                     std::vector<int32_t> *idom_out) {
   std::vector<int32_t> dfn(N, kNone), vert, parent(N, kNone);
   vert.reserve(N);
   {  // iterative DFS, preorder numbering
@@ -99,12 +132,30 @@ void lengauer_tarjan(int N, int entry, const std::vector<int32_t> &so, const int
     }
     return label[v];
   };
+  // the reachable predecessors of each DFS number, as DFS numbers (one
+  // gather up front keeps the sequential part on dense arrays)
+  std::vector<int32_t> qoff(n + 1, 0), qdfn;
+  parallel_ranges(n, kParMin, kParMax, [&](int, int lo, int hi) {
+    for (int w = lo; w < hi; ++w) {
+      const int bw = vert[w];
+      int c = 0;
+      for (int k = po[bw]; k < po[bw + 1]; ++k) c += dfn[psrc[k]] != kNone;
+      qoff[w + 1] = c;
+    }
+  });
+  for (int w = 0; w < n; ++w) qoff[w + 1] += qoff[w];
+  qdfn.resize(qoff[n]);
+  parallel_ranges(n, kParMin, kParMax, [&](int, int lo, int hi) {
+    for (int w = lo; w < hi; ++w) {
+      const int bw = vert[w];
+      int x = qoff[w];
+      for (int k = po[bw]; k < po[bw + 1]; ++k)
+        if (dfn[psrc[k]] != kNone) qdfn[x++] = dfn[psrc[k]];
+    }
+  });
   for (int w = n - 1; w >= 1; --w) {
-    const int bw = vert[w];
-    for (int k = po[bw]; k < po[bw + 1]; ++k) {
-      int v = dfn[psrc[k]];
-      if (v == kNone) continue;  // unreachable predecessor
-      int u = eval(v);
+    for (int k = qoff[w]; k < qoff[w + 1]; ++k) {
+      const int u = eval(qdfn[k]);
       if (semi[u] < semi[w]) semi[w] = semi[u];
     }
     // add w to bucket of its semidominator
@@ -119,9 +170,9 @@ void lengauer_tarjan(int N, int entry, const std::vector<int32_t> &so, const int
   }
   for (int w = 1; w < n; ++w)
     if (idom[w] != semi[w]) idom[w] = idom[idom[w]];
-  idom_out->assign(N, kNone);
-  (*idom_out)[entry] = entry;
-  for (int w = 1; w < n; ++w) (*idom_out)[vert[w]] = vert[idom[w]];
+  idom[0] = 0;
+  *idom_out = std::move(idom);
+  *dfn_out = std::move(dfn);
   *preorder_out = std::move(vert);
 }
 
@@ -154,81 +205,85 @@ int ingest(const ompdart_cfg *c, Ingest *g, std::string *err) {
   }
 
   // dominators on the reachable subgraph
-  std::vector<int32_t> pre, idom;
-  lengauer_tarjan(N, c->entry, so, succ, po, psrc, &pre, &idom);
+  std::vector<int32_t> pre, dfn, idom;
+  lengauer_tarjan(N, c->entry, so, succ, po, psrc, &pre, &dfn, &idom);
+  const int n_reach = (int)pre.size();
   std::vector<uint8_t> reach(N, 0);
   for (int b : pre) reach[b] = 1;
 
-  // dominator tree intervals: a dom b  <=>  tin[a] <= tin[b] && tout[b] <= tout[a]
-  std::vector<int32_t> tin(N, kNone), tout(N, kNone);
-  {
-    std::vector<int32_t> coff(N + 1, 0), kids(pre.size());
-    for (int b : pre)
-      if (b != c->entry) coff[idom[b] + 1]++;
-    for (int b = 0; b < N; ++b) coff[b + 1] += coff[b];
-    std::vector<int32_t> f(coff.begin(), coff.end() - 1);
-    for (int b : pre)
-      if (b != c->entry) kids[f[idom[b]]++] = b;
-    int clock = 0;
-    std::vector<std::pair<int32_t, int32_t>> st;
-    st.push_back({c->entry, coff[c->entry]});
-    tin[c->entry] = clock++;
-    while (!st.empty()) {
-      auto &t = st.back();
-      if (t.second < coff[t.first + 1]) {
-        int k = kids[t.second++];
-        tin[k] = clock++;
-        st.push_back({k, coff[k]});
-      } else {
-        tout[t.first] = clock++;
-        st.pop_back();
-      }
-    }
+  // the dominator tree as preorder intervals over DFS numbers:
+  // a dom b  <=>  tin[a] <= tin[b] < tin[a] + sz[a].  An immediate
+  // dominator has a smaller DFS number than the block it dominates, so the
+  // subtree sizes add up in decreasing DFS order and the intervals are
+  // handed out in increasing DFS order (no tree walk).
+  std::vector<int32_t> sz(n_reach, 1), tin(n_reach, 0), nxt(n_reach, 0);
+  for (int w = n_reach - 1; w >= 1; --w) sz[idom[w]] += sz[w];
+  nxt[0] = 1;
+  for (int w = 1; w < n_reach; ++w) {
+    const int u = idom[w];
+    tin[w] = nxt[u];
+    nxt[u] += sz[w];
+    nxt[w] = tin[w] + 1;
   }
-  auto dominates = [&](int a, int b) { return tin[a] <= tin[b] && tout[b] <= tout[a]; };
+  auto dominates = [&](int a, int b) {  // a and b reachable
+    const int da = dfn[a], db = dfn[b];
+    return tin[da] <= tin[db] && tin[db] < tin[da] + sz[da];
+  };
 
   // natural loops; headers in decreasing DFS preorder = inner loops first
-  std::vector<int32_t> dfn(N, kNone);
-  for (int i = 0; i < (int)pre.size(); ++i) dfn[pre[i]] = i;
-  std::vector<int32_t> headers;
-  for (int i = (int)pre.size() - 1; i >= 0; --i) {
-    int h = pre[i];
-    bool is_h = false;
-    for (int k = po[h]; k < po[h + 1] && !is_h; ++k)
-      if (reach[psrc[k]] && dominates(h, psrc[k])) is_h = true;
-    if (is_h) headers.push_back(h);
-  }
-  const int L = (int)headers.size();
-  std::vector<int32_t> lid_of_head(N, kNone);
-  for (int l = 0; l < L; ++l) lid_of_head[headers[l]] = l;
-  std::vector<std::vector<int32_t>> bodies(L);
-  std::vector<int32_t> inner(N, kNone), lparent(L, kNone), mark(N, kNone), stk;
-  for (int l = 0; l < L; ++l) {
-    int h = headers[l];
-    auto &bd = bodies[l];
-    bd.push_back(h);
-    mark[h] = l;
-    stk.clear();
-    for (int k = po[h]; k < po[h + 1]; ++k) {
-      int t = psrc[k];
-      if (reach[t] && dominates(h, t) && mark[t] != l) {
-        mark[t] = l;
-        stk.push_back(t);
-      }
+  std::vector<uint8_t> is_head(n_reach, 0);
+  parallel_ranges(n_reach, kParMin, kParMax, [&](int, int lo, int hi) {
+    for (int i = lo; i < hi; ++i) {
+      const int h = pre[i];
+      for (int k = po[h]; k < po[h + 1]; ++k)
+        if (reach[psrc[k]] && dominates(h, psrc[k])) {
+          is_head[i] = 1;
+          break;
+        }
     }
-    while (!stk.empty()) {
-      int b = stk.back();
-      stk.pop_back();
-      bd.push_back(b);
-      for (int k = po[b]; k < po[b + 1]; ++k) {
-        int p = psrc[k];
-        if (reach[p] && mark[p] != l) {
-          mark[p] = l;
-          stk.push_back(p);
+  });
+  std::vector<int32_t> headers;
+  for (int i = n_reach - 1; i >= 0; --i)
+    if (is_head[i]) headers.push_back(pre[i]);
+  const int L = (int)headers.size();
+  // each natural loop's body: the header and every block reaching a latch
+  // without passing through the header (independent per loop: flooded in
+  // parallel, each thread with its own marks)
+  std::vector<std::vector<int32_t>> bodies(L);
+  parallel_ranges(L, std::max(1, kParMin / 64), kParMax, [&](int, int lo, int hi) {
+    std::vector<int32_t> mark(N, kNone), stk;
+    for (int l = lo; l < hi; ++l) {
+      const int h = headers[l];
+      auto &bd = bodies[l];
+      bd.push_back(h);
+      mark[h] = l;
+      stk.clear();
+      for (int k = po[h]; k < po[h + 1]; ++k) {
+        const int t = psrc[k];
+        if (reach[t] && dominates(h, t) && mark[t] != l) {
+          mark[t] = l;
+          stk.push_back(t);
+        }
+      }
+      while (!stk.empty()) {
+        const int b = stk.back();
+        stk.pop_back();
+        bd.push_back(b);
+        for (int k = po[b]; k < po[b + 1]; ++k) {
+          const int p = psrc[k];
+          if (reach[p] && mark[p] != l) {
+            mark[p] = l;
+            stk.push_back(p);
+          }
         }
       }
     }
-    for (int b : bd) {
+  });
+  // innermost loop of each block and the loop tree, inner loops first
+  std::vector<int32_t> inner(N, kNone), lparent(L, kNone);
+  for (int l = 0; l < L; ++l) {
+    const int h = headers[l];
+    for (int b : bodies[l]) {
       if (inner[b] == kNone) {
         inner[b] = l;
       } else if (b != h || inner[b] != l) {
@@ -266,22 +321,24 @@ int ingest(const ompdart_cfg *c, Ingest *g, std::string *err) {
   {
     std::vector<uint8_t> seen(N, 0);
     std::vector<int32_t> sorted_succ(g->E);
-    std::vector<std::pair<int, int32_t>> key;
-    for (int b = 0; b < N; ++b) {
-      if (!reach[b]) continue;
-      int n = so[b + 1] - so[b];
-      int32_t *dst = sorted_succ.data() + so[b];
-      for (int k = 0; k < n; ++k) dst[k] = succ[so[b] + k];
-      if (n > 1) {  // stable: equal depths keep the successor order
-        key.resize(n);
-        for (int k = 0; k < n; ++k) key[k] = {common_depth(b, dst[k]), dst[k]};
-        std::stable_sort(key.begin(), key.end(),
-                         [](const std::pair<int, int32_t> &x, const std::pair<int, int32_t> &y) {
-                           return x.first < y.first;
-                         });
-        for (int k = 0; k < n; ++k) dst[k] = key[k].second;
+    parallel_ranges(N, kParMin, kParMax, [&](int, int lo, int hi) {
+      std::vector<std::pair<int, int32_t>> key;
+      for (int b = lo; b < hi; ++b) {
+        if (!reach[b]) continue;
+        int n = so[b + 1] - so[b];
+        int32_t *dst = sorted_succ.data() + so[b];
+        for (int k = 0; k < n; ++k) dst[k] = succ[so[b] + k];
+        if (n > 1) {  // stable: equal depths keep the successor order
+          key.resize(n);
+          for (int k = 0; k < n; ++k) key[k] = {common_depth(b, dst[k]), dst[k]};
+          std::stable_sort(key.begin(), key.end(),
+                           [](const std::pair<int, int32_t> &x, const std::pair<int, int32_t> &y) {
+                             return x.first < y.first;
+                           });
+          for (int k = 0; k < n; ++k) dst[k] = key[k].second;
+        }
       }
-    }
+    });
     std::vector<std::pair<int32_t, int32_t>> st;
     st.push_back({c->entry, so[c->entry]});
     seen[c->entry] = 1;
@@ -303,20 +360,19 @@ int ingest(const ompdart_cfg *c, Ingest *g, std::string *err) {
   g->M = M;
   g->order.assign(post.rbegin(), post.rend());
   g->pos.assign(N, kNone);
-  for (int i = 0; i < M; ++i) g->pos[g->order[i]] = i;
+  parallel_ranges(M, kParMin, kParMax, [&](int, int lo, int hi) {
+    for (int i = lo; i < hi; ++i) g->pos[g->order[i]] = i;
+  });
 
   // reducibility: every retreating edge must be a back edge
-  g->reducible = true;
-  for (int i = 0; i < M && g->reducible; ++i) {
-    int u = g->order[i];
-    for (int e = so[u]; e < so[u + 1]; ++e) {
-      int v = succ[e];
-      if (g->pos[v] <= i && !dominates(v, u)) {
-        g->reducible = false;
-        break;
-      }
-    }
-  }
+  g->reducible = first_bad(M, [&](int i) {
+                   const int u = g->order[i];
+                   for (int e = so[u]; e < so[u + 1]; ++e) {
+                     const int v = succ[e];
+                     if (g->pos[v] <= i && !dominates(v, u)) return true;
+                   }
+                   return false;
+                 }) == M;
 
   // loops renumbered by header position
   std::vector<int32_t> perm(L);
@@ -330,68 +386,105 @@ int ingest(const ompdart_cfg *c, Ingest *g, std::string *err) {
   g->loop_depth.resize(L);
   g->loop_end.resize(L);
   g->body_off.assign(L + 1, 0);
-  g->body_blk.clear();
-  g->contiguous = true;
-  for (int k = 0; k < L; ++k) {
-    int l = perm[k];
-    g->loop_head[k] = headers[l];
-    g->loop_parent[k] = lparent[l] == kNone ? kNone : newid[lparent[l]];
-    g->loop_depth[k] = ldepth[l];
-    std::vector<int32_t> &bd = bodies[l];  // not needed in build order any more
-    std::sort(bd.begin(), bd.end(), [&](int a, int b) { return g->pos[a] < g->pos[b]; });
-    int p0 = g->pos[bd.front()], p1 = g->pos[bd.back()];
-    if (bd.front() != headers[l] || p1 - p0 + 1 != (int)bd.size()) g->contiguous = false;
-    g->loop_end[k] = p1 + 1;
-    g->body_blk.insert(g->body_blk.end(), bd.begin(), bd.end());
-    g->body_off[k + 1] = (int32_t)g->body_blk.size();
-  }
+  for (int k = 0; k < L; ++k) g->body_off[k + 1] = g->body_off[k] + (int32_t)bodies[perm[k]].size();
+  g->body_blk.resize(g->body_off[L]);
+  uint8_t split[kParMax] = {};  // a body that is not one run of positions, per thread
+  parallel_ranges(L, std::max(1, kParMin / 16), kParMax, [&](int t, int lo, int hi) {
+    for (int k = lo; k < hi; ++k) {
+      const int l = perm[k];
+      g->loop_head[k] = headers[l];
+      g->loop_parent[k] = lparent[l] == kNone ? kNone : newid[lparent[l]];
+      g->loop_depth[k] = ldepth[l];
+      std::vector<int32_t> &bd = bodies[l];  // not needed in build order any more
+      std::sort(bd.begin(), bd.end(), [&](int a, int b) { return g->pos[a] < g->pos[b]; });
+      const int p0 = g->pos[bd.front()], p1 = g->pos[bd.back()];
+      if (bd.front() != headers[l] || p1 - p0 + 1 != (int)bd.size()) split[t] = 1;
+      g->loop_end[k] = p1 + 1;
+      std::copy(bd.begin(), bd.end(), g->body_blk.begin() + g->body_off[k]);
+    }
+  });
+  g->contiguous = std::none_of(split, split + kParMax, [](uint8_t x) { return x != 0; });
   g->inner_loop.assign(N, kNone);
   for (int b = 0; b < N; ++b)
     if (inner[b] != kNone) g->inner_loop[b] = newid[inner[b]];
 
-  // loop-entry edges: p -> header with p outside the body
-  g->ent_loop.clear();
-  g->ent_src.clear();
-  g->ent_eid.clear();
-  std::vector<int32_t> eid_ent(g->E, kNone);
-  for (int k = 0; k < L; ++k) {
-    int h = g->loop_head[k];
-    for (int q = po[h]; q < po[h + 1]; ++q) {
-      int p = psrc[q];
-      if (!reach[p]) continue;
-      // p outside body(k)  <=>  k is not an ancestor-or-self of inner(p)
-      bool inside = false;
-      for (int x = g->inner_loop[p]; x != kNone; x = g->loop_parent[x])
-        if (x == k) { inside = true; break; }
-      if (inside) continue;
-      eid_ent[peid[q]] = (int32_t)g->ent_loop.size();
-      g->ent_loop.push_back(k);
-      g->ent_src.push_back(p);
-      g->ent_eid.push_back(peid[q]);
+  // loop-entry edges: p -> header with p outside the body, by loop and in
+  // predecessor order (counted, then filled, in parallel over loops)
+  std::vector<int32_t> eid_ent(g->E, kNone), ent_off(L + 1, 0);
+  auto is_entry = [&](int k, int q) {
+    const int p = psrc[q];
+    if (!reach[p]) return false;
+    // p outside body(k)  <=>  k is not an ancestor-or-self of inner(p)
+    for (int x = g->inner_loop[p]; x != kNone; x = g->loop_parent[x])
+      if (x == k) return false;
+    return true;
+  };
+  const int loops_per_thread = std::max(1, kParMin / 16);
+  parallel_ranges(L, loops_per_thread, kParMax, [&](int, int lo, int hi) {
+    for (int k = lo; k < hi; ++k) {
+      const int h = g->loop_head[k];
+      int n = 0;
+      for (int q = po[h]; q < po[h + 1]; ++q) n += is_entry(k, q);
+      ent_off[k + 1] = n;
     }
-  }
-  g->K = (int)g->ent_loop.size();
+  });
+  for (int k = 0; k < L; ++k) ent_off[k + 1] += ent_off[k];
+  g->K = ent_off[L];
+  g->ent_loop.resize(g->K);
+  g->ent_src.resize(g->K);
+  g->ent_eid.resize(g->K);
+  parallel_ranges(L, loops_per_thread, kParMax, [&](int, int lo, int hi) {
+    for (int k = lo; k < hi; ++k) {
+      const int h = g->loop_head[k];
+      int x = ent_off[k];
+      for (int q = po[h]; q < po[h + 1]; ++q) {
+        if (!is_entry(k, q)) continue;
+        eid_ent[peid[q]] = x;
+        g->ent_loop[x] = k;
+        g->ent_src[x] = psrc[q];
+        g->ent_eid[x] = peid[q];
+        ++x;
+      }
+    }
+  });
 
-  // position-ordered edge lists
+  // position-ordered edge lists (counted, then filled, in parallel over positions)
   g->fin_off.assign(M + 1, 0);
   g->out_off.assign(M + 1, 0);
   g->is_exit.assign(M, 0);
-  g->fin_src.clear(); g->fin_eid.clear(); g->fin_ent.clear(); g->out_dst.clear();
-  g->fin_src.reserve(g->E); g->fin_eid.reserve(g->E); g->fin_ent.reserve(g->E); g->out_dst.reserve(g->E);
-  g->exit_blocks.clear();
-  for (int i = 0; i < M; ++i) {
-    int b = g->order[i];
-    for (int q = po[b]; q < po[b + 1]; ++q) {
-      if (!reach[psrc[q]]) continue;
-      g->fin_src.push_back(psrc[q]);
-      g->fin_eid.push_back(peid[q]);
-      g->fin_ent.push_back(eid_ent[peid[q]]);
+  parallel_ranges(M, kParMin, kParMax, [&](int, int lo, int hi) {
+    for (int i = lo; i < hi; ++i) {
+      const int b = g->order[i];
+      int n = 0;
+      for (int q = po[b]; q < po[b + 1]; ++q) n += reach[psrc[q]];
+      g->fin_off[i + 1] = n;
+      g->out_off[i + 1] = so[b + 1] - so[b];
+      g->is_exit[i] = so[b] == so[b + 1];
     }
-    g->fin_off[i + 1] = (int32_t)g->fin_src.size();
-    for (int e = so[b]; e < so[b + 1]; ++e) g->out_dst.push_back(succ[e]);
-    g->out_off[i + 1] = (int32_t)g->out_dst.size();
-    g->is_exit[i] = so[b] == so[b + 1];
+  });
+  for (int i = 0; i < M; ++i) {
+    g->fin_off[i + 1] += g->fin_off[i];
+    g->out_off[i + 1] += g->out_off[i];
   }
+  g->fin_src.resize(g->fin_off[M]);
+  g->fin_eid.resize(g->fin_off[M]);
+  g->fin_ent.resize(g->fin_off[M]);
+  g->out_dst.resize(g->out_off[M]);
+  parallel_ranges(M, kParMin, kParMax, [&](int, int lo, int hi) {
+    for (int i = lo; i < hi; ++i) {
+      const int b = g->order[i];
+      int x = g->fin_off[i];
+      for (int q = po[b]; q < po[b + 1]; ++q) {
+        if (!reach[psrc[q]]) continue;
+        g->fin_src[x] = psrc[q];
+        g->fin_eid[x] = peid[q];
+        g->fin_ent[x] = eid_ent[peid[q]];
+        ++x;
+      }
+      std::copy(succ + so[b], succ + so[b + 1], g->out_dst.begin() + g->out_off[i]);
+    }
+  });
+  g->exit_blocks.clear();
   for (int b = 0; b < N; ++b)
     if (reach[b] && so[b] == so[b + 1]) g->exit_blocks.push_back(b);
   g->chunk_off.assign({0, M});

@@ -11,7 +11,11 @@ namespace ompdart {
 // one per `min_per_thread` items; returns T
 template <class F>
 int parallel_ranges(int n, int min_per_thread, int max_threads, F f) {
-  const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
+  if (max_threads < 2 || n / std::max(1, min_per_thread) < 2) {  // small: no thread, no query
+    f(0, 0, n);
+    return 1;
+  }
+  static const int hw = (int)std::max(1u, std::thread::hardware_concurrency());
   const int T = std::max(1, std::min({hw, max_threads, n / std::max(1, min_per_thread)}));
   std::vector<std::thread> pool;
   for (int t = 1; t < T; ++t)

@@ -2054,146 +2054,180 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   // short chunks give more independent walks (one warp each) and shorter
   // longest walks; 32 positions measured fastest on the 2^20-block CFG
   if (chunk_target <= 0) chunk_target = 32;
-  TraceScope trace_bm("scan build_meta", g.M);
-  if (!build_meta(g, chunk_target, st, meta, loops, chunks, csrc, fin_slot, out_slot, out_pos, lat_slot, bend_loop,
-                  srcent, exit_slot, err)) {
-    delete st;
-    return nullptr;
-  }
-  trace_bm.next("scan accesses", g.M);
-  // accesses in position order: a block's own accesses with same-variable
-  // links inside the block (a short list for the usual handful of accesses,
-  // a hash map for long blocks), or, for a block with calls, its folded
-  // summary records.  Positions are independent once their offsets are
-  // known: a first parallel pass sizes them (folding the call blocks into
-  // per-thread buffers), a second fills them, over the same ranges.
-  constexpr int kThreads = 8, kMinPos = 4096;
-  struct Folded {
-    std::vector<uint32_t> recs;
-    std::vector<std::pair<int32_t, int32_t>> at;  // (position, first record), in position order
-    std::vector<int32_t> var_idx;
+  // The accesses in position order need only the order, so on a large CFG
+  // they are laid out on a second host thread while build_meta runs.
+  struct AccPos {
+    int32_t pacc_beg;
+    int16_t nacc;
+    int16_t flags;
   };
-  std::vector<Folded> fold(kThreads);
-  std::vector<int32_t> cnt(g.M + 1, 0);
-  std::atomic<bool> too_big{false};
-  // a call block of a CFG given with the same arrays and table as an earlier
-  // one takes that CFG's folded records (the same position in its order)
-  auto twin = [&](int i) -> int {
-    if (calls.same_as.empty()) return -1;
-    const int cfg = (int)(std::upper_bound(g.cfg_pos_off.begin(), g.cfg_pos_off.end(), i) - g.cfg_pos_off.begin()) - 1;
-    const int f = calls.same_as[cfg];
-    return f == cfg ? -1 : i - g.cfg_pos_off[cfg] + g.cfg_pos_off[f];
-  };
-  std::vector<int32_t> twin_pos;  // call positions that copy a twin's records
-  std::mutex twin_mu;
-  const int T = parallel_ranges(g.M, kMinPos, kThreads, [&](int t, int lo, int hi) {
-    Folded &fd = fold[t];
-    std::vector<int32_t> mine;
-    for (int i = lo; i < hi; ++i) {
-      const int b = meta[i].blk, a0 = acc_off[b], a1 = acc_off[b + 1];
-      bool has_call = false;
-      for (int k = a0; k < a1 && calls.rows; ++k) has_call |= (acc[k] >> 31) != 0;
-      int n = a1 - a0;
-      if (has_call) {
-        if (twin(i) >= 0) {
-          mine.push_back(i);
-          continue;
+  HostVec<uint32_t> acc_p;
+  HostVec<int2> acc_link;
+  std::vector<AccPos> apos;
+  std::string acc_err;
+  auto access_pass = [&]() {
+    // accesses in position order: a block's own accesses with same-variable
+    // links inside the block (a short list for the usual handful of accesses,
+    // a hash map for long blocks), or, for a block with calls, its folded
+    // summary records.  Positions are independent once their offsets are
+    // known: a first parallel pass sizes them (folding the call blocks into
+    // per-thread buffers), a second fills them, over the same ranges.
+    constexpr int kThreads = 8, kMinPos = 4096;
+    struct Folded {
+      std::vector<uint32_t> recs;
+      std::vector<std::pair<int32_t, int32_t>> at;  // (position, first record), in position order
+      std::vector<int32_t> var_idx;
+    };
+    std::vector<Folded> fold(kThreads);
+    std::vector<int32_t> cnt(g.M + 1, 0);
+    std::atomic<bool> too_big{false};
+    // a call block of a CFG given with the same arrays and table as an earlier
+    // one takes that CFG's folded records (the same position in its order)
+    auto twin = [&](int i) -> int {
+      if (calls.same_as.empty()) return -1;
+      const int cfg = (int)(std::upper_bound(g.cfg_pos_off.begin(), g.cfg_pos_off.end(), i) - g.cfg_pos_off.begin()) - 1;
+      const int f = calls.same_as[cfg];
+      return f == cfg ? -1 : i - g.cfg_pos_off[cfg] + g.cfg_pos_off[f];
+    };
+    std::vector<int32_t> twin_pos;  // call positions that copy a twin's records
+    std::mutex twin_mu;
+    const int T = parallel_ranges(g.M, kMinPos, kThreads, [&](int t, int lo, int hi) {
+      Folded &fd = fold[t];
+      std::vector<int32_t> mine;
+      for (int i = lo; i < hi; ++i) {
+        const int b = g.order[i], a0 = acc_off[b], a1 = acc_off[b + 1];
+        bool has_call = false;
+        for (int k = a0; k < a1 && calls.rows; ++k) has_call |= (acc[k] >> 31) != 0;
+        int n = a1 - a0;
+        if (has_call) {
+          if (twin(i) >= 0) {
+            mine.push_back(i);
+            continue;
+          }
+          if (fd.var_idx.empty()) fd.var_idx.assign((size_t)p.W * 64, -1);
+          const int cfg =
+              (int)(std::upper_bound(g.cfg_pos_off.begin(), g.cfg_pos_off.end(), i) - g.cfg_pos_off.begin()) - 1;
+          const size_t r0 = fd.recs.size();
+          fold_call_block(acc, a0, a1, calls, calls.row_base.empty() ? 0 : calls.row_base[cfg], p.W, fd.var_idx,
+                          &fd.recs);
+          fd.at.push_back({i, (int32_t)r0});
+          n = (int)(fd.recs.size() - r0);
         }
-        if (fd.var_idx.empty()) fd.var_idx.assign((size_t)p.W * 64, -1);
-        const int cfg =
-            (int)(std::upper_bound(g.cfg_pos_off.begin(), g.cfg_pos_off.end(), i) - g.cfg_pos_off.begin()) - 1;
-        const size_t r0 = fd.recs.size();
-        fold_call_block(acc, a0, a1, calls, calls.row_base.empty() ? 0 : calls.row_base[cfg], p.W, fd.var_idx,
-                        &fd.recs);
-        fd.at.push_back({i, (int32_t)r0});
-        n = (int)(fd.recs.size() - r0);
+        if (n > 32767) too_big = true;
+        cnt[i + 1] = n;
       }
-      if (n > 32767) too_big = true;
-      cnt[i + 1] = n;
+      std::lock_guard<std::mutex> lk(twin_mu);
+      twin_pos.insert(twin_pos.end(), mine.begin(), mine.end());
+    });
+    // where each folded position's records are: (thread, first record)
+    std::unordered_map<int32_t, std::pair<int, int32_t>> folded_at;
+    std::vector<uint8_t> is_twin;
+    if (!twin_pos.empty()) {
+      for (int t = 0; t < T; ++t)
+        for (const auto &x : fold[t].at) folded_at.emplace(x.first, std::make_pair(t, x.second));
+      is_twin.assign(g.M, 0);
+      for (int i : twin_pos) is_twin[i] = 1;
     }
-    std::lock_guard<std::mutex> lk(twin_mu);
-    twin_pos.insert(twin_pos.end(), mine.begin(), mine.end());
-  });
-  // where each folded position's records are: (thread, first record)
-  std::unordered_map<int32_t, std::pair<int, int32_t>> folded_at;
-  std::vector<uint8_t> is_twin;
-  if (!twin_pos.empty()) {
-    for (int t = 0; t < T; ++t)
-      for (const auto &x : fold[t].at) folded_at.emplace(x.first, std::make_pair(t, x.second));
-    is_twin.assign(g.M, 0);
-    for (int i : twin_pos) is_twin[i] = 1;
-  }
-  for (int i : twin_pos) cnt[i + 1] = cnt[twin(i) + 1];
-  if (too_big) {
-    if (err) *err = "a block with more than 32767 accesses (or variables touched by its calls)";
-    delete st;
-    return nullptr;
-  }
-  for (int i = 0; i < g.M; ++i) cnt[i + 1] += cnt[i];
-  HostVec<uint32_t> acc_p(cnt[g.M]);  // filled in full by the second pass
-  HostVec<int2> acc_link(cnt[g.M]);
-  parallel_ranges(g.M, kMinPos, kThreads, [&](int t, int lo, int hi) {
-    const Folded &fd = fold[t];
-    size_t next_fold = 0;
-    std::vector<std::pair<int32_t, int32_t>> seen;  // (variable, its latest access) within the block
-    std::unordered_map<int32_t, int32_t> latest;
-    for (int i = lo; i < hi; ++i) {
-      const int b = meta[i].blk, a0 = acc_off[b], a1 = acc_off[b + 1], base = cnt[i];
-      PosMeta &m = meta[i];
-      m.acc_beg = a0;
-      m.pacc_beg = base;
-      m.nacc = (int16_t)(cnt[i + 1] - base);
-      m.flags = 0;
-      if (next_fold < fd.at.size() && fd.at[next_fold].first == i) {
-        const int r0 = fd.at[next_fold++].second;
-        std::copy(fd.recs.begin() + r0, fd.recs.begin() + r0 + m.nacc, acc_p.begin() + base);
-        std::fill(acc_link.begin() + base, acc_link.begin() + base + m.nacc, make_int2(LINK_RECORD, -1));
-        m.flags = PM_RECORDS;
-        continue;
-      }
-      if (!is_twin.empty() && is_twin[i]) {
-        const auto it = folded_at.find(twin(i));
-        if (it != folded_at.end()) {  // a call block folded for its twin
-          const std::vector<uint32_t> &recs = fold[it->second.first].recs;
-          std::copy(recs.begin() + it->second.second, recs.begin() + it->second.second + m.nacc,
-                    acc_p.begin() + base);
+    for (int i : twin_pos) cnt[i + 1] = cnt[twin(i) + 1];
+    if (too_big) {
+      acc_err = "a block with more than 32767 accesses (or variables touched by its calls)";
+      return;
+    }
+    for (int i = 0; i < g.M; ++i) cnt[i + 1] += cnt[i];
+    acc_p.resize(cnt[g.M]);  // filled in full by the second pass
+    acc_link.resize(cnt[g.M]);
+    apos.resize(g.M);
+    parallel_ranges(g.M, kMinPos, kThreads, [&](int t, int lo, int hi) {
+      const Folded &fd = fold[t];
+      size_t next_fold = 0;
+      std::vector<std::pair<int32_t, int32_t>> seen;  // (variable, its latest access) within the block
+      std::unordered_map<int32_t, int32_t> latest;
+      for (int i = lo; i < hi; ++i) {
+        const int b = g.order[i], a0 = acc_off[b], a1 = acc_off[b + 1], base = cnt[i];
+        AccPos &m = apos[i];
+        m.pacc_beg = base;
+        m.nacc = (int16_t)(cnt[i + 1] - base);
+        m.flags = 0;
+        if (next_fold < fd.at.size() && fd.at[next_fold].first == i) {
+          const int r0 = fd.at[next_fold++].second;
+          std::copy(fd.recs.begin() + r0, fd.recs.begin() + r0 + m.nacc, acc_p.begin() + base);
           std::fill(acc_link.begin() + base, acc_link.begin() + base + m.nacc, make_int2(LINK_RECORD, -1));
           m.flags = PM_RECORDS;
           continue;
         }
-      }
-      std::copy(acc + a0, acc + a1, acc_p.begin() + base);
-      if (a1 - a0 <= 64) {
-        seen.clear();
-        for (int k = a0; k < a1; ++k) {
-          const int v = (int)(acc[k] & 0xFFFFFFu), idx = base + (k - a0);
-          int first = idx;
-          for (auto &sv : seen)
-            if (sv.first == v) {
-              first = acc_link[sv.second].x;
-              acc_link[sv.second].y = idx;
-              sv.second = idx;
-              break;
-            }
-          if (first == idx) seen.push_back({v, idx});
-          acc_link[idx] = make_int2(first, -1);
-        }
-      } else {
-        latest.clear();
-        for (int k = a0; k < a1; ++k) {
-          const int v = (int)(acc[k] & 0xFFFFFFu), idx = base + (k - a0);
-          auto it = latest.find(v);
-          int first = idx;
-          if (it != latest.end()) {
-            first = acc_link[it->second].x;
-            acc_link[it->second].y = idx;
-            it->second = idx;
-          } else {
-            latest.emplace(v, idx);
+        if (!is_twin.empty() && is_twin[i]) {
+          const auto it = folded_at.find(twin(i));
+          if (it != folded_at.end()) {  // a call block folded for its twin
+            const std::vector<uint32_t> &recs = fold[it->second.first].recs;
+            std::copy(recs.begin() + it->second.second, recs.begin() + it->second.second + m.nacc,
+                      acc_p.begin() + base);
+            std::fill(acc_link.begin() + base, acc_link.begin() + base + m.nacc, make_int2(LINK_RECORD, -1));
+            m.flags = PM_RECORDS;
+            continue;
           }
-          acc_link[idx] = make_int2(first, -1);
+        }
+        std::copy(acc + a0, acc + a1, acc_p.begin() + base);
+        if (a1 - a0 <= 64) {
+          seen.clear();
+          for (int k = a0; k < a1; ++k) {
+            const int v = (int)(acc[k] & 0xFFFFFFu), idx = base + (k - a0);
+            int first = idx;
+            for (auto &sv : seen)
+              if (sv.first == v) {
+                first = acc_link[sv.second].x;
+                acc_link[sv.second].y = idx;
+                sv.second = idx;
+                break;
+              }
+            if (first == idx) seen.push_back({v, idx});
+            acc_link[idx] = make_int2(first, -1);
+          }
+        } else {
+          latest.clear();
+          for (int k = a0; k < a1; ++k) {
+            const int v = (int)(acc[k] & 0xFFFFFFu), idx = base + (k - a0);
+            auto it = latest.find(v);
+            int first = idx;
+            if (it != latest.end()) {
+              first = acc_link[it->second].x;
+              acc_link[it->second].y = idx;
+              it->second = idx;
+            } else {
+              latest.emplace(v, idx);
+            }
+            acc_link[idx] = make_int2(first, -1);
+          }
         }
       }
+    });
+  };
+  TraceScope trace_bm("scan build_meta + accesses", g.M);
+  bool meta_ok;
+  if (g.M >= (1 << 16)) {
+    std::thread th(access_pass);
+    meta_ok = build_meta(g, chunk_target, st, meta, loops, chunks, csrc, fin_slot, out_slot, out_pos, lat_slot,
+                         bend_loop, srcent, exit_slot, err);
+    th.join();
+  } else {
+    meta_ok = build_meta(g, chunk_target, st, meta, loops, chunks, csrc, fin_slot, out_slot, out_pos, lat_slot,
+                         bend_loop, srcent, exit_slot, err);
+    if (meta_ok) access_pass();
+  }
+  if (meta_ok && !acc_err.empty()) {
+    if (err) *err = acc_err;
+    meta_ok = false;
+  }
+  if (!meta_ok) {
+    delete st;
+    return nullptr;
+  }
+  parallel_ranges(g.M, 1 << 15, 8, [&](int, int lo, int hi) {
+    for (int i = lo; i < hi; ++i) {
+      PosMeta &m = meta[i];
+      m.acc_beg = acc_off[m.blk];
+      m.pacc_beg = apos[i].pacc_beg;
+      m.nacc = apos[i].nacc;
+      m.flags = apos[i].flags;
     }
   });
   trace_bm.next("scan uploads", g.M);
@@ -2255,6 +2289,7 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   chk(sd.work = st->up(work));
   chk(sd.lant_work = st->up(lant_work));
   chk(sd.queue = st->alloc<int32_t>(Q_SLOTS));
+  trace_bm.next("scan shapes", g.M);
   // launch shapes (persistent: the grid is what fits on the GPU at once)
   {
     wpc = clamp_wpc(wpc);
@@ -2298,6 +2333,7 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   }
   chk(sd.hp_src = st->alloc<uint64_t>((size_t)std::max(1, g.K) * W));
   chk(sd.d_src = st->alloc<uint64_t>((size_t)std::max(1, g.K) * W));
+  trace_bm.next("scan emission items", g.M);
   // emission items: runs of at most EMIT_SPAN positions inside one chunk,
   // each with a record stream per word group, in position order, so each
   // chunk's (and each CFG's) records are contiguous
@@ -2334,6 +2370,7 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
       loop_root[l] = up < 0 ? l : loop_root[up];
     }
     chk(sd.loop_root = st->up(loop_root));
+    trace_bm.next("scan state planes", g.M);
     chk(sd.hdr_g = st->alloc<uint64_t>((size_t)std::max(1, g.L) * W));
     chk(sd.hdr_p = st->alloc<uint64_t>((size_t)std::max(1, g.L) * W));
     chk(sd.hdr_ag = st->alloc<uint64_t>((size_t)std::max(1, g.L) * W));
@@ -2354,6 +2391,7 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     chk(sd.src_g = st->alloc<uint64_t>(KW));
     chk(sd.src_p = st->alloc<uint64_t>(KW));
   }
+  trace_bm.next("scan record streams", g.M);
   chk(st->d_rec_cap = st->alloc<int32_t>(st->n_streams));
   chk(st->d_rec_base = st->alloc<int32_t>(st->n_streams));
   chk(sd.rec_cnt = st->alloc<int32_t>(st->n_streams + 1));
