@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "../../include/ompdart.h"
+#include "parallel.h"
 #include "solver.h"
 
 using namespace ompdart;
@@ -101,8 +102,10 @@ int core_build(PlanCore *P, const int32_t *acc_off, const uint32_t *acc, const C
   P->keep_states = o.keep_states;
   const int W = g.W;
   std::vector<int32_t> fin_dst(g.fin_src.size());
-  for (int i = 0; i < g.M; ++i)
-    for (int k = g.fin_off[i]; k < g.fin_off[i + 1]; ++k) fin_dst[k] = g.order[i];
+  parallel_ranges(g.M, 1 << 16, 8, [&](int, int lo, int hi) {
+    for (int i = lo; i < hi; ++i)
+      for (int k = g.fin_off[i]; k < g.fin_off[i + 1]; ++k) fin_dst[k] = g.order[i];
+  });
   P->n_fin = (int)g.fin_src.size();
 
   DevPlan &d = P->dp;
@@ -166,7 +169,8 @@ int core_build(PlanCore *P, const int32_t *acc_off, const uint32_t *acc, const C
   // ---- call sites (Sec. IV-C): every call access; the reachable blocks holding them
   {
     std::vector<int32_t> site_acc, cblk, cblk_site0, cblk_rowbase, cblk_cfg;
-    for (int b = 0; b < g.N; ++b) {
+    // without a call table no access is a call (the format check rejects one)
+    for (int b = 0; b < g.N && calls.planes; ++b) {
       int first = -1;
       for (int i = acc_off[b]; i < acc_off[b + 1]; ++i)
         if (acc[i] >> 31) {

@@ -2233,8 +2233,12 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   trace_bm.next("scan uploads", g.M);
   std::vector<int2> fin_pk(fin_slot.size()), out_pk(out_slot.size());
   // in-edge entries: {source slot, loop-entry edge or -1}
-  for (size_t k = 0; k < fin_pk.size(); ++k) fin_pk[k] = make_int2(fin_slot[k], g.fin_ent[k]);
-  for (size_t k = 0; k < out_pk.size(); ++k) out_pk[k] = make_int2(out_slot[k], out_pos[k]);
+  parallel_ranges((int)fin_pk.size(), 1 << 17, 8, [&](int, int lo, int hi) {
+    for (int k = lo; k < hi; ++k) fin_pk[k] = make_int2(fin_slot[k], g.fin_ent[k]);
+  });
+  parallel_ranges((int)out_pk.size(), 1 << 17, 8, [&](int, int lo, int hi) {
+    for (int k = lo; k < hi; ++k) out_pk[k] = make_int2(out_slot[k], out_pos[k]);
+  });
   const int W = p.W, C = st->C, G = (W + 63) / 64;
   st->G = G;
   ScanDev &sd = st->sd;
@@ -2248,13 +2252,15 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   // position inside d nested loops may be walked up to about 2^d times
   std::vector<int32_t> work(C);
   std::vector<long long> cost(C, 0);
-  for (int c = 0; c < C; ++c) {
-    work[c] = c;
-    for (int i = chunks[c].s; i < chunks[c].e; ++i) {
-      const int l = g.inner_loop[g.order[i]];
-      cost[c] += 1ll << std::min(l >= 0 ? g.loop_depth[l] : 0, 4);
+  parallel_ranges(C, 2048, 8, [&](int, int lo, int hi) {
+    for (int c = lo; c < hi; ++c) {
+      work[c] = c;
+      for (int i = chunks[c].s; i < chunks[c].e; ++i) {
+        const int l = g.inner_loop[g.order[i]];
+        cost[c] += 1ll << std::min(l >= 0 ? g.loop_depth[l] : 0, 4);
+      }
     }
-  }
+  });
   std::stable_sort(work.begin(), work.end(), [&](int a, int b) { return cost[a] > cost[b]; });
   std::vector<int32_t> lant_work(g.L);
   for (int l = 0; l < g.L; ++l) lant_work[l] = l;
@@ -2355,13 +2361,17 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   // affine pairs of the summary walks and where each position's carry comes from
   {
     std::vector<int32_t> pos_chunk(g.M), src_pos(std::max(1, g.K), 0);
-    for (int c = 0; c < C; ++c)
-      for (int i = chunks[c].s; i < chunks[c].e; ++i) pos_chunk[i] = c;
+    parallel_ranges(C, 2048, 8, [&](int, int lo, int hi) {
+      for (int c = lo; c < hi; ++c)
+        for (int i = chunks[c].s; i < chunks[c].e; ++i) pos_chunk[i] = c;
+    });
     for (int k = 0; k < g.K; ++k) src_pos[k] = g.pos[g.ent_src[k]];
     chk(sd.pos_chunk = st->up(pos_chunk));
     chk(sd.src_pos = st->up(src_pos));
     std::vector<int32_t> pos_loop(g.M);
-    for (int i = 0; i < g.M; ++i) pos_loop[i] = g.inner_loop[g.order[i]];
+    parallel_ranges(g.M, 1 << 16, 8, [&](int, int lo, int hi) {
+      for (int i = lo; i < hi; ++i) pos_loop[i] = g.inner_loop[g.order[i]];
+    });
     chk(sd.pos_loop = st->up(pos_loop));
     chk(sd.loop_up = st->up(g.loop_parent));
     std::vector<int32_t> loop_root(g.L);
