@@ -53,9 +53,9 @@ def workload_name(n_blocks):
 # profiles/): dram__bytes_read.sum + dram__bytes_write.sum on the 2^18-block
 # version of the workload, scaled to the bench's launch by block-words
 MEASURED_TRAFFIC = {
-    "h_summary": {"bytes_2e18": (319374080 + 269608192 + 319529984 + 268443904) / 2.0,
+    "h_summary": {"bytes_2e18": (319307008 + 269504768 + 319343360 + 268663296) / 2.0,
                   "profile": "profiles/h_summary_walk_2e18.md"},
-    "live_summary": {"bytes_2e18": (40509696 + 359516160 + 40363264 + 357572608) / 2.0,
+    "live_summary": {"bytes_2e18": (40253184 + 359559168 + 40314112 + 357505792) / 2.0,
                      "profile": "profiles/live_summary_walk_2e18.md"},
 }
 

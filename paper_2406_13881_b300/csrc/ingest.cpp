@@ -598,26 +598,27 @@ void make_chunks(Ingest *g, int target) {
   if (target <= 0) target = M + 1;  // one chunk per CFG
   // fwd[i]: edges with pos(src) < i <= pos(dst), counted by difference
   // arrays; into[i]: edges into order[i] from positions < i; back[i]:
-  // edges with pos(dst) < i <= pos(src).
-  std::vector<int64_t> fwd(M + 1, 0), back(M + 1, 0);
-  std::vector<int32_t> into(M, 0);
-  for (int j = 0; j < M; ++j) {
-    int u = g->order[j];
-    (void)u;
-    for (int k = g->out_off[j]; k < g->out_off[j + 1]; ++k) {
-      int pd = g->pos[g->out_dst[k]];
-      if (pd > j) {
-        fwd[j + 1]++;
-        fwd[pd + 1]--;
-        into[pd]++;
-      } else {
-        back[pd + 1]++;
-        back[j + 1]--;
+  // edges with pos(dst) < i <= pos(src).  Positions in parallel, the
+  // counts by atomic adds (most land next to the position's own).
+  std::vector<int32_t> fwd(M + 1, 0), back(M + 1, 0), into(M, 0);  // counts of edges: below 2^31
+  auto add = [](auto *x, auto v) { __atomic_fetch_add(x, v, __ATOMIC_RELAXED); };
+  parallel_ranges(M, kParMin, kParMax, [&](int, int lo, int hi) {
+    for (int j = lo; j < hi; ++j) {
+      for (int k = g->out_off[j]; k < g->out_off[j + 1]; ++k) {
+        const int pd = g->pos[g->out_dst[k]];
+        if (pd > j) {
+          add(&fwd[j + 1], 1);
+          add(&fwd[pd + 1], -1);
+          add(&into[pd], 1);
+        } else {
+          add(&back[pd + 1], 1);
+          add(&back[j + 1], -1);
+        }
       }
     }
-  }
+  });
   std::vector<uint8_t> ok(M + 1, 0);
-  int64_t f = 0, bk = 0;
+  int32_t f = 0, bk = 0;
   for (int i = 0; i <= M; ++i) {
     f += fwd[i];
     bk += back[i];

@@ -91,19 +91,21 @@ enum ModeKind { M_SUM = 0, M_LANT = 2 };  // summary walk; loop-restricted antic
 struct PosMeta {  // one per position, 80 B
   int32_t blk;
   int32_t fin_beg, out_beg, acc_beg, srcent_beg, bend_beg;  // acc_beg: in caller order
-  int16_t nfin, nout, nacc, nsrcent, nbend, fslot, bslot, pad0;
+  int16_t nfin, nout, nacc, nsrcent, nbend, fslot, bslot;
+  int16_t bend_depth;     // the first (outermost) loop ending here: its depth,
   int32_t head_loop;      // loop whose header is this position, else -1
-  int32_t pad4;
+  int32_t bend_ph;        // header position,
   int32_t exit_idx;       // index in exit_blocks, else -1
   int32_t pacc_beg;       // first access of the block in position order
   int32_t flags;          // PM_RECORDS: the block's summary records are given
-  int32_t pad3;
+  int32_t bend_pend;      // body end and header slot (the backward walks read
+                          // them here instead of from bend_info)
   // a header position: its loop's body end, header slot and depth (kept
   // here so the walks need no loop record at a header)
   int32_t head_pend;
   int16_t head_hslot, head_depth;
   int32_t pad6;
-  int16_t pad7, pad5;
+  int16_t bend_hslot, pad5;
 };
 // a block with call pseudo-accesses: its entries in the position-ordered
 // access stream are already summary records (folded on the host with the
@@ -330,8 +332,8 @@ int scan_supported(const Ingest &g) {
 namespace {
 
 bool build_meta(const Ingest &g, int target, ScanState *st, HostVec<PosMeta> &meta, std::vector<LoopMeta> &loops,
-                std::vector<ChunkMeta> &chunks, std::vector<CarrySrc> &csrc, std::vector<int32_t> &fin_slot,
-                std::vector<int32_t> &out_slot, std::vector<int32_t> &out_pos, std::vector<int32_t> &lat_slot,
+                std::vector<ChunkMeta> &chunks, std::vector<CarrySrc> &csrc, HostVec<int32_t> &fin_slot,
+                HostVec<int32_t> &out_slot, HostVec<int32_t> &out_pos, std::vector<int32_t> &lat_slot,
                 std::vector<int32_t> &bend_loop, std::vector<int32_t> &srcent, std::vector<int32_t> &exit_slot,
                 std::string *err) {
   Ingest &gm = const_cast<Ingest &>(g);
@@ -371,10 +373,11 @@ bool build_meta(const Ingest &g, int target, ScanState *st, HostVec<PosMeta> &me
   // position once, in order.
   std::vector<uint8_t> bwd_target(M, 0);
   for (int l = 0; l < L; ++l) bwd_target[g.loop_end[l] - 1] = 1;
-  fin_slot.assign(g.fin_src.size(), -1);
-  out_slot.assign(g.out_dst.size(), -1);
-  out_pos.assign(g.out_dst.size(), -1);
-  std::vector<int32_t> fslot(M, -1), bslot(M, -1), hslot(L, -1);
+  // every entry of these is written by the per-chunk passes below
+  fin_slot.resize(g.fin_src.size());
+  out_slot.resize(g.out_dst.size());
+  out_pos.resize(g.out_dst.size());
+  HostVec<int32_t> fslot(M), bslot(M), hslot(L);
   // loop containing a block but not another: outermost such
   auto contains = [&](int l, int p) { return p >= g.pos[g.loop_head[l]] && p < g.loop_end[l]; };
   auto outermost = [&](int l) {
@@ -514,6 +517,13 @@ bool build_meta(const Ingest &g, int target, ScanState *st, HostVec<PosMeta> &me
       m.nsrcent = (int16_t)(src_off[i + 1] - src_off[i]);
       m.bend_beg = end_off[i];
       m.nbend = (int16_t)(end_off[i + 1] - end_off[i]);
+      if (m.nbend) {
+        const int l = end_l[end_off[i]], ph = g.pos[g.loop_head[l]];
+        m.bend_depth = (int16_t)g.loop_depth[l];
+        m.bend_ph = ph;
+        m.bend_pend = g.loop_end[l];
+        m.bend_hslot = (int16_t)bslot[ph];
+      }
     }
   });
   // ---- edge entries per chunk, then the carry sources (edges into the
@@ -552,41 +562,69 @@ bool build_meta(const Ingest &g, int target, ScanState *st, HostVec<PosMeta> &me
         if (pp < e) csrc[q++] = CarrySrc{fslot[pp], g.fin_ent[k], k, 0};
       }
   }
-  for (int l = 0; l < L; ++l) {
-    LoopMeta &lm = loops[l];
-    lm.cfg = (int32_t)(std::upper_bound(g.cfg_pos_off.begin(), g.cfg_pos_off.end(), g.pos[g.loop_head[l]]) -
-                       g.cfg_pos_off.begin()) - 1;
-    lm.ph = g.pos[g.loop_head[l]];
-    lm.pend = g.loop_end[l];
-    lm.hslot = (int16_t)hslot[l];
-    lm.depth = (int16_t)g.loop_depth[l];
-    lm.lat_beg = (int32_t)lat_slot.size();
-    const int i = lm.ph;
-    for (int k = g.fin_off[i]; k < g.fin_off[i + 1]; ++k) {
+  // ---- per loop: its record, latch slots and exit sources (loops
+  // independent: counted, then written at their offsets, in parallel)
+  auto loop_lists = [&](int l, std::vector<int32_t> &lat, std::vector<int32_t> &xs) {
+    const int ph = g.pos[g.loop_head[l]], pend = g.loop_end[l];
+    lat.clear();
+    xs.clear();
+    for (int k = g.fin_off[ph]; k < g.fin_off[ph + 1]; ++k) {
       const int pp = g.pos[g.fin_src[k]];
-      if (pp >= i && std::find(lat_slot.begin() + lm.lat_beg, lat_slot.end(), fslot[pp]) == lat_slot.end())
-        lat_slot.push_back(fslot[pp]);
+      if (pp >= ph && std::find(lat.begin(), lat.end(), fslot[pp]) == lat.end()) lat.push_back(fslot[pp]);
     }
-    lm.lat_cnt = (int32_t)lat_slot.size() - lm.lat_beg;
     // exit sources: body positions whose value is read from their slot
     // outside the body: after it (or as the next chunk's carry), or at an
     // enclosing loop's end (a back edge to an enclosing header)
-    const int ce = chunks[std::upper_bound(g.chunk_off.begin(), g.chunk_off.end(), lm.ph) - g.chunk_off.begin() - 1].e;
-    lm.xs_beg = (int32_t)exit_slot.size();
-    for (int q = lm.ph; q < lm.pend; ++q) {
+    const int ce = chunks[std::upper_bound(g.chunk_off.begin(), g.chunk_off.end(), ph) - g.chunk_off.begin() - 1].e;
+    for (int q = ph; q < pend; ++q) {
       if (fslot[q] < 0) continue;
       bool read_after = false;
       for (int k = g.out_off[q]; k < g.out_off[q + 1] && !read_after; ++k) {
         const int pt = g.pos[g.out_dst[k]];
-        read_after = (pt >= lm.pend || pt < lm.ph) && (pt >= ce || pt != q + 1);
+        read_after = (pt >= pend || pt < ph) && (pt >= ce || pt != q + 1);
       }
-      if (read_after) exit_slot.push_back(fslot[q]);
+      if (read_after) xs.push_back(fslot[q]);
     }
-    lm.xs_cnt = (int32_t)exit_slot.size() - lm.xs_beg;
-    PosMeta &hm = meta[lm.ph];
-    hm.head_pend = lm.pend;
-    hm.head_hslot = lm.hslot;
-    hm.head_depth = lm.depth;
+  };
+  {
+    std::vector<int32_t> lat_off(L + 1, 0), xs_off(L + 1, 0);
+    parallel_ranges(L, 1024, 8, [&](int, int lo, int hi) {
+      std::vector<int32_t> lat, xs;
+      for (int l = lo; l < hi; ++l) {
+        loop_lists(l, lat, xs);
+        lat_off[l + 1] = (int32_t)lat.size();
+        xs_off[l + 1] = (int32_t)xs.size();
+      }
+    });
+    for (int l = 0; l < L; ++l) {
+      lat_off[l + 1] += lat_off[l];
+      xs_off[l + 1] += xs_off[l];
+    }
+    lat_slot.resize(lat_off[L]);
+    exit_slot.resize(xs_off[L]);
+    parallel_ranges(L, 1024, 8, [&](int, int lo, int hi) {
+      std::vector<int32_t> lat, xs;
+      for (int l = lo; l < hi; ++l) {
+        loop_lists(l, lat, xs);
+        std::copy(lat.begin(), lat.end(), lat_slot.begin() + lat_off[l]);
+        std::copy(xs.begin(), xs.end(), exit_slot.begin() + xs_off[l]);
+        LoopMeta &lm = loops[l];
+        lm.cfg = (int32_t)(std::upper_bound(g.cfg_pos_off.begin(), g.cfg_pos_off.end(), g.pos[g.loop_head[l]]) -
+                           g.cfg_pos_off.begin()) - 1;
+        lm.ph = g.pos[g.loop_head[l]];
+        lm.pend = g.loop_end[l];
+        lm.hslot = (int16_t)hslot[l];
+        lm.depth = (int16_t)g.loop_depth[l];
+        lm.lat_beg = lat_off[l];
+        lm.lat_cnt = lat_off[l + 1] - lat_off[l];
+        lm.xs_beg = xs_off[l];
+        lm.xs_cnt = xs_off[l + 1] - xs_off[l];
+        PosMeta &hm = meta[lm.ph];
+        hm.head_pend = lm.pend;
+        hm.head_hslot = lm.hslot;
+        hm.head_depth = lm.depth;
+      }
+    });
   }
   st->C = C;
   st->fslots = std::max(max_f, 1);
@@ -1212,7 +1250,8 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
     }
     // enter loops whose range ends here (outer first)
     for (int q = 0; q < m.nbend; ++q) {
-      const int4 bi = sd.bend_info[m.bend_beg + q];  // {depth, header position, body end, header slot}
+      // {depth, header position, body end, header slot}
+      const int4 bi = q ? sd.bend_info[m.bend_beg + q] : make_int4(m.bend_depth, m.bend_ph, m.bend_pend, m.bend_hslot);
       if (bi.x <= depth) continue;
       st_ph[bi.x - 1] = bi.y;
       st_pend[bi.x - 1] = bi.z;
@@ -2050,7 +2089,8 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   std::vector<LoopMeta> loops;
   std::vector<ChunkMeta> chunks;
   std::vector<CarrySrc> csrc;
-  std::vector<int32_t> fin_slot, out_slot, out_pos, lat_slot, bend_loop, srcent, exit_slot;
+  HostVec<int32_t> fin_slot, out_slot, out_pos;
+  std::vector<int32_t> lat_slot, bend_loop, srcent, exit_slot;
   // short chunks give more independent walks (one warp each) and shorter
   // longest walks; 32 positions measured fastest on the 2^20-block CFG
   if (chunk_target <= 0) chunk_target = 32;
