@@ -1710,33 +1710,69 @@ __global__ void __launch_bounds__(32 * EMIT_WARPS, OMPDART_EMIT_MIN_CTAS)
 // --------------------------------------------------------------------------------------
 // scan of the chunk maps: carry[c] for every chunk (one thread per word and plane)
 // --------------------------------------------------------------------------------------
-// One CTA of SCAN_T threads per word column: thread t composes the maps of
-// a contiguous run of chunks (walk order), the CTA scans the runs' maps in
-// parallel, then every thread walks its run again to write each chunk's
-// carry.  Map composition: first (g1, p1), then (g2, p2) gives
-// (g2 | (g1 & p2), p1 & p2).  The first chunk (in walk order) of each CFG
-// of a batch starts from that CFG's own boundary value -- the forward entry
-// value, or nothing for the backward problem -- so in the run maps it acts
-// as a constant map.
+// The walk order of the chunks is cut into S segments.  A CTA of SCAN_T
+// threads takes one segment for a block of WB word columns (WB a power of
+// two up to 64, covering W where it can), so the WB threads of a run read
+// a chunk's row of maps together: thread (run r, word w) composes the maps
+// of its contiguous run of chunks (walk order), the CTA scans the runs'
+// maps per word in shared memory, then every thread walks its run again
+// to write each chunk's carry.  Map composition: first (g1, p1), then
+// (g2, p2) gives (g2 | (g1 & p2), p1 & p2).  The first chunk (in walk
+// order) of each CFG of a batch starts from that CFG's own boundary value
+// -- the forward entry value, or nothing for the backward problem -- so in
+// the run maps it acts as a constant map.
 constexpr int SCAN_T = 1024;
 __device__ __forceinline__ void compose_after(uint64_t &g, uint64_t &p, uint64_t g1, uint64_t p1) {
   // (g1, p1) first, then the current (g, p)
   g = g | (g1 & p);
   p = p1 & p;
 }
+// word columns per scan CTA: the least power of two >= W, at most 64
+inline int scan_wb(int W) {
+  int wb = 1;
+  while (wb < W && wb < 64) wb <<= 1;
+  return wb;
+}
 
-// The walk order of a word column's chunks is cut into S segments, one CTA
-// each (grid W x S): phase 0 leaves each segment's map in seg; phase 1
+// Inclusive scan over the runs of a CTA, word by word: thread t holds run
+// t / WB of word t % WB; afterwards (g, p) is the composition of runs
+// 0..r and the shared arrays hold every run's inclusive value.
+__device__ __forceinline__ void scan_runs(uint64_t *gs, uint64_t *ps, uint64_t &g, uint64_t &p, int t, int r,
+                                          int R, int WB) {
+  gs[t] = g;
+  ps[t] = p;
+  __syncthreads();
+  for (int d = 1; d < R; d <<= 1) {
+    uint64_t g1 = 0, p1 = ~0ull;
+    const bool has = r >= d;
+    if (has) {
+      g1 = gs[t - d * WB];
+      p1 = ps[t - d * WB];
+    }
+    __syncthreads();
+    if (has) {
+      compose_after(g, p, g1, p1);
+      gs[t] = g;
+      ps[t] = p;
+    }
+    __syncthreads();
+  }
+}
+
+// Grid (ceil(W / WB), S): phase 0 leaves each segment's map in seg; phase 1
 // composes the maps of the segments before its own into the carry entering
-// it, then scans its runs again and writes every chunk's carry.
+// it (the CTA's runs share that work), then scans its runs again and
+// writes every chunk's carry.
 template <int PHASE>
-__global__ void __launch_bounds__(SCAN_T) k_scan_carry(ScanDev sd, int W, int backward, const uint64_t *init) {
-  __shared__ uint64_t wg_s[SCAN_T / 32], wp_s[SCAN_T / 32];
-  const int w = blockIdx.x, sg = blockIdx.y, S = gridDim.y, t = threadIdx.x, lane = t & 31, wid = t >> 5;
+__global__ void __launch_bounds__(SCAN_T) k_scan_carry(ScanDev sd, int W, int WB, int backward, const uint64_t *init) {
+  __shared__ uint64_t gs[SCAN_T], ps[SCAN_T];
+  const int t = threadIdx.x, wl = t & (WB - 1), r = t / WB, R = SCAN_T / WB;
+  const int w = blockIdx.x * WB + wl, sg = blockIdx.y, S = gridDim.y;
+  const bool on = w < W;
   const int C = sd.C;
   const int s0 = (int)((long long)C * sg / S), s1 = (int)((long long)C * (sg + 1) / S);
-  const int per = (s1 - s0 + SCAN_T - 1) / SCAN_T;
-  const int b = s0 + t * per, e = min(s1, b + per);
+  const int per = (s1 - s0 + R - 1) / R;
+  const int b = min(s1, s0 + r * per), e = min(s1, b + per);
   const int32_t rflag = backward ? CH_LAST : CH_FIRST;
   auto chunk = [&](int k) { return backward ? C - 1 - k : k; };  // k-th chunk in walk order
   auto reset_val = [&](int c) -> uint64_t {
@@ -1761,70 +1797,72 @@ __global__ void __launch_bounds__(SCAN_T) k_scan_carry(ScanDev sd, int W, int ba
   };
   // 1. the run's map
   uint64_t g = 0, pp = ~0ull;
-  for (int k0 = b; k0 < e; k0 += SCAN_B) {
-    load_batch(k0);
+  if (on)
+    for (int k0 = b; k0 < e; k0 += SCAN_B) {
+      load_batch(k0);
 #pragma unroll
-    for (int j = 0; j < SCAN_B; ++j) {
-      if (k0 + j >= e) break;
-      if (fb[j] & rflag) {
-        g = reset_val(chunk(k0 + j));
-        pp = 0;
+      for (int j = 0; j < SCAN_B; ++j) {
+        if (k0 + j >= e) break;
+        if (fb[j] & rflag) {
+          g = reset_val(chunk(k0 + j));
+          pp = 0;
+        }
+        g = gb[j] | (g & pb[j]);
+        pp &= pb[j];
       }
-      g = gb[j] | (g & pb[j]);
-      pp &= pb[j];
     }
-  }
-  // 2. inclusive scan of the run maps: within the warp, then over warps
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint64_t g1 = __shfl_up_sync(0xffffffffu, g, d), p1 = __shfl_up_sync(0xffffffffu, pp, d);
-    if (lane >= d) compose_after(g, pp, g1, p1);
-  }
-  if (lane == 31) {
-    wg_s[wid] = g;
-    wp_s[wid] = pp;
-  }
-  __syncthreads();
-  if (wid == 0) {
-    uint64_t a = wg_s[lane], q = wp_s[lane];
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint64_t g1 = __shfl_up_sync(0xffffffffu, a, d), p1 = __shfl_up_sync(0xffffffffu, q, d);
-      if (lane >= d) compose_after(a, q, g1, p1);
-    }
-    wg_s[lane] = a;
-    wp_s[lane] = q;
-  }
-  __syncthreads();
+  // 2. inclusive scan of the run maps over the CTA's runs
+  scan_runs(gs, ps, g, pp, t, r, R, WB);
   if (PHASE == 0) {  // the segment's map
-    if (t == 0) {
-      sd.seg_g[(size_t)sg * W + w] = wg_s[SCAN_T / 32 - 1];
-      sd.seg_p[(size_t)sg * W + w] = wp_s[SCAN_T / 32 - 1];
+    if (r == R - 1 && on) {
+      sd.seg_g[(size_t)sg * W + w] = g;
+      sd.seg_p[(size_t)sg * W + w] = pp;
     }
     return;
   }
-  if (wid > 0) compose_after(g, pp, wg_s[wid - 1], wp_s[wid - 1]);
-  // the value entering the segment: the maps of the segments before it
-  // applied to nothing (every walk starts at a CFG's first chunk, which resets)
-  uint64_t cin = 0;
-  for (int q = 0; q < sg; ++q) cin = sd.seg_g[(size_t)q * W + w] | (cin & sd.seg_p[(size_t)q * W + w]);
-  // carry entering run t: the segment's runs before t applied to cin
-  uint64_t xg = __shfl_up_sync(0xffffffffu, g, 1), xp = __shfl_up_sync(0xffffffffu, pp, 1);
-  if (lane == 0) {
-    xg = wid > 0 ? wg_s[wid - 1] : 0ull;
-    xp = wid > 0 ? wp_s[wid - 1] : ~0ull;
+  // the runs before this one
+  uint64_t xg = 0, xp = ~0ull;
+  if (r > 0) {
+    xg = gs[t - WB];
+    xp = ps[t - WB];
   }
-  uint64_t x = xg | (cin & xp);
-  // 3. every chunk's carry
-  for (int k0 = b; k0 < e; k0 += SCAN_B) {
-    load_batch(k0);
+  __syncthreads();
+  // 3. the value entering the segment: the maps of the segments before it
+  // applied to nothing (every walk starts at a CFG's first chunk, which
+  // resets); run r composes segments [q0, q1), then the runs' parts are
+  // composed in order
+  uint64_t cg = 0, cp = ~0ull;
+  if (on)
+    for (int q0 = (int)((long long)sg * r / R), q1 = (int)((long long)sg * (r + 1) / R); q0 < q1; q0 += SCAN_B) {
 #pragma unroll
-    for (int j = 0; j < SCAN_B; ++j) {
-      if (k0 + j >= e) break;
-      const int c = chunk(k0 + j);
-      if (fb[j] & rflag) x = reset_val(c);
-      sd.carry[(size_t)c * W + w] = x;
-      x = gb[j] | (x & pb[j]);
+      for (int j = 0; j < SCAN_B; ++j)
+        if (q0 + j < q1) {
+          gb[j] = sd.seg_g[(size_t)(q0 + j) * W + w];
+          pb[j] = sd.seg_p[(size_t)(q0 + j) * W + w];
+        }
+#pragma unroll
+      for (int j = 0; j < SCAN_B; ++j)
+        if (q0 + j < q1) {
+          cg = gb[j] | (cg & pb[j]);
+          cp &= pb[j];
+        }
     }
-  }
+  scan_runs(gs, ps, cg, cp, t, r, R, WB);
+  const uint64_t cin = gs[(R - 1) * WB + wl];
+  uint64_t x = xg | (cin & xp);
+  // 4. every chunk's carry
+  if (on)
+    for (int k0 = b; k0 < e; k0 += SCAN_B) {
+      load_batch(k0);
+#pragma unroll
+      for (int j = 0; j < SCAN_B; ++j) {
+        if (k0 + j >= e) break;
+        const int c = chunk(k0 + j);
+        if (fb[j] & rflag) x = reset_val(c);
+        sd.carry[(size_t)c * W + w] = x;
+        x = gb[j] | (x & pb[j]);
+      }
+    }
 }
 
 // initial stale sets at the entry block of each CFG (forward problems): ~valid & top
@@ -2373,7 +2411,9 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     // chunk-carry scan: about two CTAs per SM over the word columns' segments
     int dev = 0, n_sm = 148;
     if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-    sd.seg_n = std::max(1, std::min(16, std::min(2 * n_sm / std::max(1, W), (C + 255) / 256)));
+    // about two CTAs per SM over the column blocks' segments, a few chunks per run
+    const int wb = scan_wb(W), gx = (W + wb - 1) / wb, runs = SCAN_T / wb;
+    sd.seg_n = std::max(1, std::min({2 * n_sm / gx, (C + 4 * runs - 1) / (4 * runs), 1024}));
     chk(sd.seg_g = st->alloc<uint64_t>((size_t)2 * sd.seg_n * W));  // one region per branch
     chk(sd.seg_p = st->alloc<uint64_t>((size_t)2 * sd.seg_n * W));
   }
@@ -2502,9 +2542,10 @@ void chain_launch(K kern, const ChainShape &cs, const DevPlan &p, const ScanDev 
 // The chunk-carry scan of one problem: segment maps, then the carries (one
 // launch when a column is one segment).  Returns the launches.
 static int scan_carries(const ScanDev &x, int W, int backward, const uint64_t *init, cudaStream_t s) {
-  const dim3 grid(W, x.seg_n);
-  if (x.seg_n > 1) k_scan_carry<0><<<grid, SCAN_T, 0, s>>>(x, W, backward, init);
-  k_scan_carry<1><<<grid, SCAN_T, 0, s>>>(x, W, backward, init);
+  const int wb = scan_wb(W);
+  const dim3 grid((W + wb - 1) / wb, x.seg_n);
+  if (x.seg_n > 1) k_scan_carry<0><<<grid, SCAN_T, 0, s>>>(x, W, wb, backward, init);
+  k_scan_carry<1><<<grid, SCAN_T, 0, s>>>(x, W, wb, backward, init);
   return x.seg_n > 1 ? 2 : 1;
 }
 
