@@ -98,7 +98,7 @@ def byte_model(st):
         "live_resolve": resolve + in_loop + 4.0 * (M + L) + hdr_top,
         "loop_masks": G * st["body"] * (64.0 + 4.0 * A / max(1, M) + 8.0 * E / max(1, M)) + 2 * L * 8.0 * W,
         "hp_summary": walk + 2 * edge_plane + hdr,      # pairs at loop-entry sources, header pairs
-        "src_resolve": 3 * edge_plane,
+        "src_resolve": 4.5 * edge_plane,                # pairs and loop masks in; edge constants (and D) out
         "d_summary": walk + 3 * edge_plane + 2 * plane + hdr,  # reads `to' constants; writes D_in pairs
         "d_resolve": fwd_resolve,
         "h_summary": walk + edge_plane + 4 * plane + hdr,  # reads Live, D_in; writes H_out pairs

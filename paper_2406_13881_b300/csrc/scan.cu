@@ -163,7 +163,7 @@ struct ScanDev {
   uint64_t *carry;         // [planes][C][W] carry into each chunk
   uint64_t *seg_g, *seg_p;  // [S][W] maps of the scan's segments (one region per branch of a run)
   int seg_n;                // segments per word column of the chunk-carry scan
-  uint64_t *hp_src, *d_src;  // [K][W] plain host / device validity at loop-entry sources
+  uint64_t *d_src;  // [K][W] device validity at loop-entry sources
   // affine pairs the summary walks leave per position: value = G | (carry & P)
   // with the carry into the position's chunk (resolved by k_resolve_*)
   uint64_t *pair_g, *pair_p;    // [N][W] by block: Live_in, later H_out stale
@@ -1594,8 +1594,12 @@ __global__ void __launch_bounds__(256) k_resolve(DevPlan p, ScanDev sd, const ui
   }
 }
 
-// the same for the out values at loop-entry sources ([K][W]), as valid sets
-__global__ void k_resolve_src(DevPlan p, ScanDev sd, uint64_t *out) {
+// The same for the out values at loop-entry sources ([K][W]), as valid
+// sets, and the edge constants they decide (Sec. IV-D hoisting) in the same
+// pass: which = 0, plain host validity: ec_d = mask_d & Hp (the value itself
+// is not kept); which = 1, device validity: d_src (the emission reads it)
+// and ec_h = mask_h & D.
+__global__ void k_resolve_src(DevPlan p, ScanDev sd, int which) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int W = p.W;
   if (t >= (long long)p.K * W) return;
@@ -1604,8 +1608,14 @@ __global__ void k_resolve_src(DevPlan p, ScanDev sd, uint64_t *out) {
   uint64_t g = sd.src_g[t], q = sd.src_p[t];
   const int l = sd.pos_loop[i];
   if (l >= 0) compose_pair(g, q, sd.hdr_ag[(size_t)l * W + w], sd.hdr_ap[(size_t)l * W + w]);
-  const uint64_t x = g | (sd.carry[(size_t)c * W + w] & q);
-  out[t] = ~x & p.top[(size_t)sd.chunks[c].cfg * W + w];
+  const uint64_t x = ~(g | (sd.carry[(size_t)c * W + w] & q)) & p.top[(size_t)sd.chunks[c].cfg * W + w];
+  const size_t le = (size_t)p.ent_loop[k] * W + w;
+  if (which == 0) {
+    p.ec_d[t] = p.mask_d[le] & x;
+  } else {
+    sd.d_src[t] = x;
+    p.ec_h[t] = p.mask_h[le] & x;
+  }
 }
 
 // --------------------------------------------------------------------------------------
@@ -1871,18 +1881,6 @@ __global__ void k_entry_stale(const uint64_t *valid, const uint64_t *top, uint64
   if (t < (long long)W * n_cfg) out[t] = ~valid[t] & top[t];
 }
 
-// loop-entry edge constants (hoisted transfers): device = mask_d & plain
-// host valid at the source; host = mask_h & device valid at the source
-__global__ void k_scan_edge_const(DevPlan p, ScanDev sd, int which) {
-  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (t >= (long long)p.K * p.W) return;
-  const int k = (int)(t / p.W), w = (int)(t % p.W);
-  const int l = p.ent_loop[k];
-  if (which == 0)
-    p.ec_d[t] = p.mask_d[(size_t)l * p.W + w] & sd.hp_src[t];
-  else
-    p.ec_h[t] = p.mask_h[(size_t)l * p.W + w] & sd.d_src[t];
-}
 
 // gather the record streams into the result array: per-CTA sums of the
 // streams' counts, a scan of those sums, per-CTA offsets, then the copy
@@ -2417,7 +2415,6 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     chk(sd.seg_g = st->alloc<uint64_t>((size_t)2 * sd.seg_n * W));  // one region per branch
     chk(sd.seg_p = st->alloc<uint64_t>((size_t)2 * sd.seg_n * W));
   }
-  chk(sd.hp_src = st->alloc<uint64_t>((size_t)std::max(1, g.K) * W));
   chk(sd.d_src = st->alloc<uint64_t>((size_t)std::max(1, g.K) * W));
   trace_bm.next("scan emission items", g.M);
   // emission items: runs of at most EMIT_SPAN positions inside one chunk,
@@ -2615,9 +2612,7 @@ int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *p
   if (fork) cudaStreamWaitEvent(s, st->ev[1], 0);  // the masks
   if (p.K) {
     PROF("src_resolve");
-    k_resolve_src<<<grid_of(kw, 256), 256, 0, s>>>(p, sq, sq.hp_src); ++n;
-    PROF("edge_const");
-    k_scan_edge_const<<<grid_of(kw, 256), 256, 0, s>>>(p, sq, 0); ++n;
+    k_resolve_src<<<grid_of(kw, 256), 256, 0, s>>>(p, sq, 0); ++n;
   }
   // ---- device validity
   PROF("entry_stale");
@@ -2637,9 +2632,7 @@ int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *p
   }
   if (p.K) {
     PROF("src_resolve");
-    k_resolve_src<<<grid_of(kw, 256), 256, 0, s>>>(p, sq, sq.d_src); ++n;
-    PROF("edge_const");
-    k_scan_edge_const<<<grid_of(kw, 256), 256, 0, s>>>(p, sq, 1); ++n;
+    k_resolve_src<<<grid_of(kw, 256), 256, 0, s>>>(p, sq, 1); ++n;
   }
   // ---- host validity (its exit states), then the emission
   if (fork) cudaStreamWaitEvent(s, st->ev[2], 0);  // liveness
