@@ -70,3 +70,33 @@ def test_call_accesses_without_table_rejected():
     with pytest.raises(_native.OmpdartError) as ei:
         _native.analyze(g)
     assert ei.value.code == _native.E_INVALID
+
+
+@pytest.mark.parametrize("first,later,msg", [
+    ("kind_zero", "var_range", "access kind"),
+    ("var_range", "kind_zero", "access variable out of range"),
+    ("succ_range", "entry_pred", "successor id out of range"),
+    ("entry_pred", "succ_range", "entry block must have no predecessors"),
+])
+def test_first_invalid_entry_decides_on_large_inputs(first, later, msg):
+    """Large inputs are checked in parallel ranges; the message is still the
+    one of the lowest-indexed bad entry, as in a sequential scan."""
+    n, per = 300_000, 4
+    succ_off = np.arange(n + 1, dtype=np.int32)
+    succ_off[-1] = n - 1                      # the last block has no successor
+    succ = np.arange(1, n, dtype=np.int32)
+    acc_off = (np.arange(n + 1) * per).astype(np.int32)
+    acc = wl.pack_access(np.arange(n * per) % 8, np.full(n * per, 1), np.zeros(n * per, dtype=np.int64))
+    acc = np.asarray(acc, dtype=np.uint32).copy()
+    bad = {"kind_zero": lambda i: acc.__setitem__(i, np.uint32(3)),
+           "var_range": lambda i: acc.__setitem__(i, wl.pack_access([9], [1], [0])[0]),
+           "succ_range": lambda i: succ.__setitem__(i, n + 5),
+           "entry_pred": lambda i: succ.__setitem__(i, 0)}
+    lo, hi = (10, len(acc) - 5) if first in ("kind_zero", "var_range") else (5, len(succ) - 3)
+    bad[first](lo)
+    bad[later](hi)
+    g = wl.CFG(n_blocks=n, n_vars=8, entry=0, succ_off=succ_off, succ=succ, acc_off=acc_off, acc=acc)
+    with pytest.raises(_native.OmpdartError) as ei:
+        _native.analyze(g)
+    assert ei.value.code == _native.E_INVALID
+    assert msg in str(ei.value)
