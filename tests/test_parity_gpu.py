@@ -202,3 +202,15 @@ def test_large_cfg_sampled_words(large_cfg):
         orc = oracle.solve(sub)
         assert_matches_oracle(sub, res, orc, words=slice(w, w + 1), acc_keep=keep)
     p.close()
+
+
+@pytest.mark.parametrize("nv", [64, 300])
+def test_large_cfg_parallel_host_build(nv):
+    """A CFG large enough that ingestion and plan building run their passes
+    on several host threads (and the accesses beside build_meta), with one
+    or five words per row, so the chunk-carry scan takes column blocks of 1
+    and 8 words: full parity with the oracle."""
+    g = wl.structured(4242 + nv, 300_000, nv, acc_min=0, acc_max=4)
+    res = _native.analyze(g, keep_states=True)
+    assert res["path"] == 2
+    assert_matches_oracle(g, res, oracle.solve(g))
