@@ -57,6 +57,8 @@ MEASURED_TRAFFIC = {
                   "profile": "profiles/h_summary_walk_2e18.md"},
     "live_summary": {"bytes_2e18": (40253184 + 359559168 + 40314112 + 357505792) / 2.0,
                      "profile": "profiles/live_summary_walk_2e18.md"},
+    "emit": {"bytes_2e18": (489899776 + 96055552 + 489456384 + 93677824) / 2.0,
+             "profile": "profiles/emit_2e18.md"},
 }
 
 
