@@ -2279,7 +2279,7 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   };
   TraceScope trace_bm("scan build_meta + accesses", g.M);
   bool meta_ok;
-  if (g.M >= (1 << 16)) {
+  if (g.M >= (1 << 14)) {  // (a thread start costs tens of microseconds)
     std::thread th(access_pass);
     meta_ok = build_meta(g, chunk_target, st, meta, loops, chunks, csrc, fin_slot, out_slot, out_pos, lat_slot,
                          bend_loop, srcent, exit_slot, err);
