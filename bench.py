@@ -17,7 +17,13 @@ the fixed point: n_blocks * n_words / step time.
             L2 so no flush is needed
   e2e    -- the same metric through ompdart_analyze with host buffers
             (ingestion, host->device copies, solve, device->host copies)
-  roofline, cpu_baseline, clocks, gpu_launches -- see the design doc
+  roofline  -- the dominant kernel (by CUDA-event time) against the
+               measured HBM copy bandwidth, plus `step': the whole step's
+               modelled bytes over its time
+  batch, serve -- the batched (10,000 CFGs) and serving (Poisson 1k-100k
+               requests/s) workloads, CFGs/s and p50/p99 beside the plain
+               form (one plan and launch sequence per CFG)
+  cpu_baseline, clocks, gpu_launches
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -49,17 +55,23 @@ def workload_name(n_blocks):
     return WORKLOAD if n_blocks == 1 << 20 else WORKLOAD.replace("2^20", str(n_blocks))
 
 
-# DRAM traffic per launch from ncu captures of the current kernels (see
-# profiles/): dram__bytes_read.sum + dram__bytes_write.sum on the 2^18-block
-# version of the workload, scaled to the bench's launch by block-words
+# DRAM traffic per launch from ncu captures (see profiles/):
+# dram__bytes_read.sum + dram__bytes_write.sum on the 2^18-block version of
+# the workload, scaled to the bench's launch by block-words.  These are
+# estimates from an earlier capture, not counters of this run: each entry
+# names the commit its capture was taken at, and an entry is removed when
+# its kernel changes.
 MEASURED_TRAFFIC = {
     "h_summary": {"bytes_2e18": (319307008 + 269504768 + 319343360 + 268663296) / 2.0,
-                  "profile": "profiles/h_summary_walk_2e18.md"},
+                  "profile": "profiles/h_summary_walk_2e18.md", "captured_at": "a70c254"},
     "live_summary": {"bytes_2e18": (40253184 + 359559168 + 40314112 + 357505792) / 2.0,
-                     "profile": "profiles/live_summary_walk_2e18.md"},
+                     "profile": "profiles/live_summary_walk_2e18.md", "captured_at": "a70c254"},
     "emit": {"bytes_2e18": (489899776 + 96055552 + 489456384 + 93677824) / 2.0,
-             "profile": "profiles/emit_2e18.md"},
+             "profile": "profiles/emit_2e18.md", "captured_at": "f047219"},
 }
+# the survey's per-phase traffic model for a dense-state design: about 140 B
+# per block-word for the whole step (Ant 37, Hp 18, D 19, H 34, emission 32)
+SURVEY_BYTES_PER_BLOCK_WORD = 140.0
 
 
 def peaks():
@@ -217,17 +229,93 @@ def job_value(units_per_rank, world, steps, ms):
     return units_per_rank * world * steps / (ms / 1e3)
 
 
-def workload_stats(g, plan_ing=None):
+def loop_entry_edges(g):
+    """Loop-entry edges of a generated CFG: every loop header's in-edges
+    except its one back edge (the generator's loops have a single latch)."""
     import numpy as np
+    heads = np.array([h for h, _, _, _ in g.meta.get("loops", [])], dtype=np.int64)
+    if not len(heads):
+        return 0
+    indeg = np.bincount(np.asarray(g.succ, dtype=np.int64), minlength=g.n_blocks)
+    return int((indeg[heads] - 1).sum())
+
+
+def workload_stats(g):
     W = g.W
     loops = g.meta.get("loops", [])
     st = {"N": g.n_blocks, "M": g.n_blocks, "E": g.n_edges, "A": g.n_acc, "W": W,
-          "K": g.meta.get("loop_entry_edges", 0), "L": len(loops)}
+          "K": loop_entry_edges(g), "L": len(loops)}
     st["body"] = float(sum(e - f + 1 for _, f, e, _ in loops))
     # blocks inside some loop (the bodies of the outermost loops) and those loops
     st["in_loop"] = float(sum(e - h for h, _, e, d in loops if d == 1))
     st["L_top"] = sum(1 for *_, d in loops if d == 1)
     return st
+
+
+def batch_byte_model(cfgs):
+    """Algorithmic bytes per run of each kernel name of a batch: the CFGs of
+    one word count share an arena (one plan over all of them), whose model
+    is byte_model of the summed statistics; summed over the arenas."""
+    groups = {}
+    for g in cfgs:
+        st = workload_stats(g)
+        acc = groups.setdefault(st["W"], {k: 0.0 for k in st})
+        for k, v in st.items():
+            if k != "W":
+                acc[k] += v
+        acc["W"] = st["W"]
+    total = {}
+    for st in groups.values():
+        for k, v in byte_model(st).items():
+            total[k] = total.get(k, 0.0) + v
+    return total
+
+
+def bytes_per_run(timings, model, n_runs, n_plans=1):
+    """Modelled bytes of one run per kernel name: the per-launch model
+    (summed over the plans of a batch, which share the launch sequence)
+    times the launches of that name per plan and run."""
+    return {k: model[k] * v[0] / float(n_runs * n_plans) for k, v in timings.items() if k in model}
+
+
+def dominant_roofline(timings, per_run, n_runs, peak, src, traffic=None, traffic_source=None):
+    """The kernel with the most CUDA-event time: its modelled bytes over its
+    measured time, against the measured copy bandwidth."""
+    name, (nl, tot_ms) = max(timings.items(), key=lambda kv: kv[1][1])
+    avg_ms = tot_ms / max(1, nl)
+    b = per_run.get(name)
+    per_launch = b * n_runs / max(1, nl) if b is not None else None
+    achieved = per_launch / (avg_ms / 1e3) / 1e9 if per_launch else None
+    total = sum(x[1] for x in timings.values())
+    return {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak if achieved else None, "traffic": traffic, "traffic_source": traffic_source,
+            "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src,
+            "algorithmic_bytes_per_launch": per_launch, "avg_launch_ms": avg_ms,
+            "kernels": {k: {"launches": v[0], "ms": round(v[1], 4), "share": round(v[1] / total, 4)}
+                        for k, v in sorted(timings.items(), key=lambda kv: -kv[1][1])}}
+
+
+def step_roofline(timings, per_run, ms_step, peak, units):
+    """The whole step: the summed byte model of every modelled kernel per
+    step over the step's time, and the survey's ~140 B per block-word model
+    over the same time."""
+    modelled = sum(per_run.values())
+    survey = SURVEY_BYTES_PER_BLOCK_WORD * units
+    gbs = lambda b: b / (ms_step / 1e3) / 1e9  # noqa: E731
+    return {"bytes_per_step": modelled, "ms_per_step": ms_step, "achieved": gbs(modelled), "peak": peak,
+            "unit": "GB/s", "frac": gbs(modelled) / peak,
+            "survey_model_bytes_per_step": survey, "survey_model_frac": gbs(survey) / peak,
+            "unmodelled_kernels": sorted(k for k in timings if k not in per_run),
+            "note": "achieved = modelled bytes per step / ms_per_step of the timed region; 60%% of the measured "
+                    "peak on the survey model is %.2f ms per step" % (survey / (0.6 * peak * 1e9) * 1e3)}
+
+
+def single_config(g, seed, world):
+    """The `config' object of the single-CFG workload (both arms)."""
+    return {"workload": workload_name(g.n_blocks), "n_blocks": g.n_blocks, "n_vars": g.n_vars, "n_words": g.W,
+            "n_edges": g.n_edges, "n_acc": g.n_acc, "seed": seed,
+            "l2": "no flush: every state plane (%d MiB) is larger than the 126 MB L2" % (8 * g.n_blocks * g.W >> 20),
+            "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
 def run_ours(args):
@@ -244,14 +332,6 @@ def run_ours(args):
     torch.cuda.set_device(local)
     build.build()
     g = wl.single_large(args.seed, n_blocks=args.n_blocks)
-    # loop-entry edge count for the byte model comes from the plan's ingestion;
-    # count it here from the generator's loops (every header's non-latch preds)
-    so, su = g.succ_off, g.succ
-    n = g.n_blocks
-    preds = np.zeros(n + 1, dtype=np.int64)
-    np.add.at(preds, su + 1, 1)
-    heads = np.array([h for h, _, _, _ in g.meta["loops"]], dtype=np.int64)
-    g.meta["loop_entry_edges"] = int((preds[heads + 1] - 1).sum()) if len(heads) else 0
 
     plan = _native.Plan(g, device=local, chunk_target=args.chunk_target)
     stream = torch.cuda.Stream(device=local)
@@ -278,7 +358,8 @@ def run_ours(args):
     # per-kernel device time: a few more steps with an event before every
     # launch (the phases then run one after another on one stream)
     plan.profile(True)
-    for _ in range(min(args.steps, 5)):
+    n_prof = min(args.steps, 5)
+    for _ in range(n_prof):
         plan.run(sh)
         plan.sync()
     timings = plan.timings()
@@ -293,23 +374,15 @@ def run_ours(args):
         # ---- roofline of the dominant kernel (CUDA events over the timed region)
         st = workload_stats(g)
         model = byte_model(st)
-        dom = max(timings.items(), key=lambda kv: kv[1][1])
-        name, (nl, tot_ms) = dom
-        avg_ms = tot_ms / max(1, nl)
         peak, src = peaks()
-        bytes_ = model.get(name)
-        achieved = bytes_ / (avg_ms / 1e3) / 1e9 if bytes_ else None
+        name = max(timings.items(), key=lambda kv: kv[1][1])[0]
         meas = MEASURED_TRAFFIC.get(name)
         traffic = meas["bytes_2e18"] * (g.n_blocks * g.W) / float((1 << 18) * 64) if meas else None
-        roof = {"kernel": name, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": traffic,
-                "traffic_source": ("ncu, 2^18-block capture scaled by block-words: " + meas["profile"]) if meas
-                else None,
-                "peak_source": src + " (MEASURED_PEAKS.json hbm_gbs)" if src == "measured" else src,
-                "algorithmic_bytes_per_launch": bytes_, "avg_launch_ms": avg_ms,
-                "kernels": {k: {"launches": v[0], "ms": round(v[1], 4),
-                                "share": round(v[1] / sum(x[1] for x in timings.values()), 4)}
-                            for k, v in sorted(timings.items(), key=lambda kv: -kv[1][1])}}
+        tsrc = ("estimate, not counters of this run: an ncu capture (commit %s) of the 2^18-block case scaled by "
+                "block-words, %s" % (meas["captured_at"], meas["profile"])) if meas else None
+        per_run = bytes_per_run(timings, model, n_prof)
+        roof = dominant_roofline(timings, per_run, n_prof, peak, src, traffic, tsrc)
+        roof["step"] = step_roofline(timings, per_run, ms_step, peak, g.n_blocks * g.W)
         # ---- end to end through the public API with host buffers
         # (one untimed warm-up call, like the batch workload, then the median
         # of e2e_steps calls)
@@ -331,11 +404,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": workload_name(g.n_blocks), "n_blocks": g.n_blocks, "n_vars": g.n_vars, "n_words": g.W,
-                       "n_edges": g.n_edges, "n_acc": g.n_acc, "seed": args.seed,
-                       "solver": "chunked scan" if plan.view().path == 2 else "sweep",
-                       "l2": "no flush: every state plane (512 MiB) is larger than the 126 MB L2",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": single_config(g, args.seed, world),
+            "solver": "chunked scan" if plan.view().path == 2 else "sweep",
             "roofline": roof,
             "cpu_baseline": {"value": cpu_val, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "%d of 64 word columns of the same CFG, single-threaded C oracle, %.1f s"
@@ -348,6 +418,19 @@ def run_ours(args):
             "clocks": clk,
         }
     plan.close()
+    if out is not None and world == 1 and args.sub_workloads:
+        # the metric's CFGs/s and p50/p99 part: the batch (10,000 CFGs) and
+        # the serving streams, each beside its plain one-plan-per-CFG form
+        sub = argparse.Namespace(**vars(args))
+        sub.steps, sub.warmup, sub.e2e_steps = 10, 3, 1
+        sub.plain_cfgs, sub.cpu_seconds = args.sub_plain_cfgs, args.sub_cpu_seconds
+        sub.seconds, sub.max_requests, sub.plain_requests = 1.0, args.sub_max_requests, args.sub_plain_requests
+        bt = measure_batch(sub, local, 1)
+        out["batch"] = {k: bt[k] for k in ("value", "unit", "ms_per_step", "steps", "cfgs_per_s", "batch_latency_ms",
+                                           "plain_per_cfg", "speedup_vs_plain", "roofline", "e2e", "cpu_baseline",
+                                           "cpu_baseline_parallel", "gpu_launches", "config")}
+        sv = measure_serve(sub, local)
+        out["serve"] = {k: sv[k] for k in ("config", "served", "plain_per_cfg", "note")}
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -361,9 +444,8 @@ def percentile(xs, q):
 
 def run_batch(args):
     """Batched analysis of config-3-shaped CFGs vs one plan per CFG."""
-    import numpy as np
     import torch
-    from paper_2406_13881_b300 import _native, build, workload as wl
+    from paper_2406_13881_b300 import build
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     rank = int(os.environ.get("RANK", "0"))
@@ -373,6 +455,20 @@ def run_batch(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build.build()
+    out = measure_batch(args, local, world)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return out if rank == 0 else None
+
+
+def measure_batch(args, local, world):
+    """The 10,000-CFG batch: graph replays (CUDA events), batch latency,
+    per-kernel events for the roofline, the plain form, end to end through
+    ompdart_analyze_batch, and the oracle on a sample."""
+    import torch
+    from paper_2406_13881_b300 import _native, workload as wl
+
     t0 = time.perf_counter()
     cfgs = wl.batch(args.batch_seed, n_cfgs=args.n_cfgs)
     t_gen = time.perf_counter() - t0
@@ -389,6 +485,7 @@ def run_batch(args):
         assert (b.sync() == 0).all()
     torch.cuda.synchronize()
     if world > 1:
+        import torch.distributed as dist
         dist.barrier()
     clocks = ClockSampler(local)
     clocks.start()
@@ -410,7 +507,24 @@ def run_batch(args):
         b.run(sh)
         b.sync()
         lat_b.append(1e3 * (time.perf_counter() - t0))
+    # per-kernel CUDA events (arenas one after another on the stream) for the
+    # roofline of the batch's dominant kernel
+    b.profile(True)
+    n_prof = 3
+    for _ in range(n_prof):
+        b.run(sh)
+        b.sync()
+    timings = b.timings()
+    b.profile(False)
     b.close()
+    peak, src = peaks()
+    n_plans = len(info["arenas"]) + info["solo"]
+    per_run = bytes_per_run(timings, batch_byte_model(cfgs), n_prof, n_plans)
+    roof = dominant_roofline(timings, per_run, n_prof, peak, src, None,
+                             "no DRAM counters of this kernel's batch launch in this run")
+    roof["run_under_profile_ms"] = sum(v[1] for v in timings.values()) / n_prof
+    roof["note"] = ("per-kernel events serialise the arenas (no graph, no overlap); bytes per kernel from "
+                    "byte_model of each arena's summed statistics")
     # ---- the plain form: one plan per CFG, one launch sequence and one wait per CFG
     n_plain = len(cfgs) if args.plain_cfgs <= 0 else min(args.plain_cfgs, len(cfgs))
     plans = [_native.Plan(g, device=local) for g in cfgs[:n_plain]]
@@ -471,11 +585,6 @@ def run_batch(args):
     t_par = time.perf_counter() - t0
     value = job_value(units, world, args.steps, ms)
     cps = job_value(len(cfgs), world, args.steps, ms)
-    if world > 1:
-        dist.barrier()
-        dist.destroy_process_group()
-    if rank != 0:
-        return None
     return {
         "metric": "block·var-word updates/s to fixed point; CFGs/s and p50/p99 vs per-CFG launch",
         "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -511,6 +620,7 @@ def run_batch(args):
         "e2e": {"value": units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "seconds_per_step": e2e_s, "cfgs_per_s": len(cfgs) / e2e_s,
                 "path": "ompdart_analyze_batch: host ingestion + copies + solve + copy back"},
+        "roofline": roof,
         "gpu_launches": info["launches"] * args.steps,
         "clocks": clk,
     }
@@ -529,14 +639,21 @@ def serve_pool(seed, n_small, n_large, large_blocks):
 def run_serve(args):
     """Poisson request streams through the serving loop at several arrival
     rates, beside the plain form (one plan and launch sequence per request)."""
-    import numpy as np
     import torch
-    from paper_2406_13881_b300 import _native, build
+    from paper_2406_13881_b300 import build
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     rank = int(os.environ.get("RANK", "0"))
     torch.cuda.set_device(local)
     build.build()
+    out = measure_serve(args, local)
+    return out if rank == 0 else None
+
+
+def measure_serve(args, local):
+    import numpy as np
+    from paper_2406_13881_b300 import _native
+
     small, large = serve_pool(args.batch_seed, args.pool, 2, args.large_blocks)
     rng = np.random.default_rng(args.batch_seed)
 
@@ -577,8 +694,6 @@ def run_serve(args):
         served.append(one(rate, n, 4096, args.inflight))
         plain.append(one(rate, int(min(n, args.plain_requests)), 1, 1))
     top = served[-1]
-    if rank != 0:
-        return None
     return {
         "metric": "block·var-word updates/s to fixed point; CFGs/s and p50/p99 vs per-CFG launch",
         "value": top["updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": len(args.rates), "warmup": 1,
@@ -694,7 +809,7 @@ def run_reference(args):
         "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot / len(times), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_blocks": g.n_blocks, "n_vars": g.n_vars, "seed": args.seed},
+        "config": single_config(g, args.seed, int(os.environ.get("WORLD_SIZE", "1"))),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": "one of 64 word columns of the CFG per step", "cpu": cpu_info()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -732,6 +847,12 @@ def main():
     ap.add_argument("--plain-cfgs", type=int, default=0,
                     help="batch: CFGs timed in the one-plan-per-CFG form (0 = all)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--sub-workloads", type=int, default=1,
+                    help="single: also run the batch and serving workloads (sub-objects `batch' and `serve')")
+    ap.add_argument("--sub-plain-cfgs", type=int, default=2000)
+    ap.add_argument("--sub-cpu-seconds", type=float, default=4.0)
+    ap.add_argument("--sub-max-requests", type=int, default=20000)
+    ap.add_argument("--sub-plain-requests", type=int, default=1000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

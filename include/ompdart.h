@@ -92,7 +92,14 @@ extern "C" {
 #define OMPDART_MEM_HOST 0
 #define OMPDART_MEM_DEVICE 1
 
-/* One CFG (see INPUT FORMAT).  All pointers are host pointers. */
+/* One CFG (see INPUT FORMAT).  `mem' says where its arrays live:
+   OMPDART_MEM_HOST (0, a zero-initialised struct) for host memory, or
+   OMPDART_MEM_DEVICE for device memory of the current CUDA device (every
+   non-NULL array pointer must then be a device or managed allocation, else
+   OMPDART_E_INVALID).  Ingestion runs on the host, so an entry point given
+   device arrays first copies them to host buffers it owns (a device array
+   shared by several CFGs of one call is copied once); the caller's arrays
+   are only read, and may be reused as soon as the call returns. */
 typedef struct {
   int32_t n_blocks, n_vars, entry;
   const int32_t *succ_off, *succ;
@@ -107,6 +114,7 @@ typedef struct {
      NULL when no access has bit 31 set. */
   const uint64_t *call_planes;
   int32_t n_calls;
+  int32_t mem;                      /* OMPDART_MEM_HOST or OMPDART_MEM_DEVICE        */
 } ompdart_cfg;
 
 typedef struct {
@@ -266,6 +274,16 @@ int ompdart_batch_fetch(ompdart_batch *batch, int32_t i, ompdart_result **out);
 int ompdart_batch_info(const ompdart_batch *batch, int32_t *n_arenas, int32_t *n_solo, int32_t *launches,
                        int32_t max, int32_t *arena_w, int32_t *arena_cfgs, int32_t *arena_chunk,
                        int32_t *arena_wpc);
+
+/* Per-kernel device time of a batch's runs, as ompdart_plan_profile /
+   ompdart_plan_timings do for a plan: while profiling is on, a run
+   launches every plan of the batch directly, one after another on the
+   run's stream (no graph, no overlap between arenas), with a CUDA event
+   before each kernel; ompdart_batch_sync charges the time between
+   consecutive events to the kernel between them, summed per kernel name
+   over all arenas.  Enabling or disabling resets the totals. */
+int ompdart_batch_profile(ompdart_batch *batch, int enable);
+int ompdart_batch_timings(ompdart_batch *batch, ompdart_timing *out, int32_t max, int32_t *n);
 
 void ompdart_batch_destroy(ompdart_batch *batch);
 
@@ -428,12 +446,16 @@ void ompdart_server_destroy(ompdart_server *server);
    ompdart_result.live_in); unreachable blocks are zero.
    Limits: n_blocks <= 65536, n_vars <= 4096, accesses <= 2^20; larger
    inputs return OMPDART_E_BUDGET with a message, call pseudo-accesses
-   OMPDART_E_INVALID.  Scratch: one static device array of 4.2 MiB per
-   device, resident until the process exits; its device address is looked
-   up (cudaGetSymbolAddress) on the first call on each device, which should
-   come before any stream capture.  Calls share that array: calls that
-   overlap on the GPU race and must be serialised by the caller.  The call
-   enqueues on `stream' (cudaStream_t) and waits for it. */
+   OMPDART_E_INVALID.  The liveness sweeps visit the reachable blocks in
+   breadth-first order from the entry, farthest first; a call that runs
+   for more than 20 s of device time stops and returns OMPDART_E_TIMEOUT.
+   Scratch: one static device array of 4.5 MiB per device, resident until
+   the process exits; its device address is looked up
+   (cudaGetSymbolAddress) on the first call on each device, which should
+   come before any stream capture (a failed lookup is retried by the next
+   call).  Calls share that array: calls that overlap on the GPU race and
+   must be serialised by the caller.  The call enqueues on `stream'
+   (cudaStream_t) and waits for that stream to finish before it returns. */
 int ompdart_liveness_noalloc(int32_t n_blocks, int32_t n_vars, int32_t entry, const int32_t *succ_off,
                              const int32_t *succ, const int32_t *acc_off, const uint32_t *acc,
                              const uint64_t *exit_host_live, uint64_t *live_in, void *stream);

@@ -35,7 +35,7 @@ class Cfg(C.Structure):
                 ("succ_off", C.c_void_p), ("succ", C.c_void_p), ("acc_off", C.c_void_p),
                 ("acc", C.c_void_p), ("entry_host_valid", C.c_void_p),
                 ("entry_dev_valid", C.c_void_p), ("exit_host_live", C.c_void_p),
-                ("call_planes", C.c_void_p), ("n_calls", C.c_int32)]
+                ("call_planes", C.c_void_p), ("n_calls", C.c_int32), ("mem", C.c_int32)]
 
 
 class Opts(C.Structure):
@@ -102,6 +102,8 @@ class Timing(C.Structure):
 EXPORTS = {
     "ompdart_plan_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "ompdart_plan_timings": (C.c_int, [C.c_void_p, C.POINTER(Timing), C.c_int32, C.POINTER(C.c_int32)]),
+    "ompdart_batch_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "ompdart_batch_timings": (C.c_int, [C.c_void_p, C.POINTER(Timing), C.c_int32, C.POINTER(C.c_int32)]),
     "ompdart_plan_create": (C.c_int, [C.POINTER(Cfg), C.POINTER(Opts), C.POINTER(C.c_void_p)]),
     "ompdart_plan_run": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ompdart_plan_sync": (C.c_int, [C.c_void_p]),
@@ -163,10 +165,37 @@ def _check(rc):
         raise OmpdartError(rc, load().ompdart_last_error().decode())
 
 
+MEM_HOST, MEM_DEVICE = 0, 1
+
+
+class DeviceCfg:
+    """A CFG whose arrays already sit in device memory (``ompdart_cfg.mem``
+    = OMPDART_MEM_DEVICE): integer device addresses (``None`` for an
+    omitted optional array) and the sizes.  ``owner`` keeps whatever holds
+    that memory alive while the CFG is in use."""
+
+    def __init__(self, n_blocks, n_vars, entry, succ_off, succ, acc_off, acc, entry_host_valid=None,
+                 entry_dev_valid=None, exit_host_live=None, call_planes=None, n_calls=0, owner=None):
+        self.n_blocks, self.n_vars, self.entry = int(n_blocks), int(n_vars), int(entry)
+        self.ptrs = (succ_off, succ, acc_off, acc, entry_host_valid, entry_dev_valid, exit_host_live, call_planes)
+        self.n_calls = int(n_calls)
+        self.owner = owner
+
+    @property
+    def W(self):
+        return (self.n_vars + 63) // 64
+
+
 class _Inputs:
-    """Keeps the contiguous numpy copies alive while the C struct points at them."""
+    """Keeps the contiguous numpy copies alive while the C struct points at
+    them (or, for a DeviceCfg, passes its device addresses through)."""
 
     def __init__(self, cfg):
+        if isinstance(cfg, DeviceCfg):
+            self.n, self.nv, self.W = cfg.n_blocks, cfg.n_vars, cfg.W
+            self.dev = cfg
+            self.c = Cfg(cfg.n_blocks, cfg.n_vars, cfg.entry, *cfg.ptrs, cfg.n_calls, MEM_DEVICE)
+            return
         g = cfg if isinstance(cfg, dict) else cfg.__dict__
         self.n, self.nv = int(g["n_blocks"]), int(g["n_vars"])
         self.W = (self.nv + 63) // 64
@@ -184,7 +213,7 @@ class _Inputs:
         p = lambda a: None if a is None else a.ctypes.data  # noqa: E731
         self.c = Cfg(self.n, self.nv, int(g.get("entry", 0)), p(self.so), p(self.s), p(self.ao),
                      p(self.acc), p(self.ehv), p(self.edv), p(self.xhl), p(self.calls),
-                     0 if self.calls is None else int(self.calls.size // (7 * self.W)))
+                     0 if self.calls is None else int(self.calls.size // (7 * self.W)), MEM_HOST)
 
 
 def _opts(max_sweeps=0, keep_states=False, path=0, chunk_target=0, device=0, warps_per_cta=0, tune=False,
@@ -370,6 +399,19 @@ class Batch:
         res = C.POINTER(Result)()
         _check(self._lib.ompdart_batch_fetch(self._h, int(i), C.byref(res)))
         return _owned_result(self._lib, res)
+
+    def profile(self, enable: bool = True):
+        """Per-kernel CUDA events on every later run (plans one after
+        another on the run's stream, no graph)."""
+        _check(self._lib.ompdart_batch_profile(self._h, int(bool(enable))))
+
+    def timings(self) -> dict:
+        """{kernel name: (launches, total ms)} summed over the arenas since profile(True)."""
+        n = C.c_int32()
+        _check(self._lib.ompdart_batch_timings(self._h, None, 0, C.byref(n)))
+        arr = (Timing * max(1, n.value))()
+        _check(self._lib.ompdart_batch_timings(self._h, arr, n.value, C.byref(n)))
+        return {arr[i].name.decode(): (arr[i].launches, arr[i].ms) for i in range(n.value)}
 
     def info(self) -> dict:
         na, ns, nl = C.c_int32(), C.c_int32(), C.c_int32()

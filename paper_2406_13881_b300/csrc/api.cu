@@ -441,6 +441,12 @@ int ompdart_plan_create(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdar
   *out = nullptr;
   ompdart_opts o{};
   if (opts) o = *opts;
+  StagedCfgs staged;  // device-resident inputs copied for ingestion
+  if (cfg) {
+    std::string serr;
+    const int src = stage_cfgs(cfg, 1, &staged, &cfg, &serr);
+    if (src) return set_err(src, serr);
+  }
   ompdart_plan *P = new (std::nothrow) ompdart_plan();
   if (!P) return set_err(OMPDART_E_NOMEM, "host allocation failed");
   std::string err;

@@ -91,6 +91,7 @@ struct ompdart_batch {
   int launches = 0;
   int runs = 0;
   bool ran = false;
+  Prof prof;  // per-kernel events (ompdart_batch_profile): plans run one after another on the caller's stream
 
   // host status words (pageable: a batch is created and destroyed often by
   // the serving loop, and freeing pinned memory can wait for the device)
@@ -355,6 +356,12 @@ int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts 
   if (!out) return set_error(OMPDART_E_INVALID, "batch output pointer is NULL");
   *out = nullptr;
   if (n < 0 || (n > 0 && !cfgs)) return set_error(OMPDART_E_INVALID, "bad CFG array");
+  StagedCfgs staged;  // device-resident inputs copied for ingestion; a CFG that fails fails alone
+  {
+    std::string serr;
+    const int src = stage_cfgs(cfgs, n, &staged, &cfgs, &serr, true);
+    if (src) return set_error(src, serr);
+  }
   ompdart_batch *B = new (std::nothrow) ompdart_batch();
   if (!B) return set_error(OMPDART_E_NOMEM, "host allocation failed");
   std::unique_ptr<ompdart_batch> hold(B);
@@ -402,6 +409,8 @@ int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts 
     work();
     for (auto &t : pool) t.join();
     for (int i = 0; i < n; ++i) B->ingest_status[i] = B->ingest_status[canon[i]];
+    for (int i = 0; i < (int)staged.rc.size(); ++i)
+      if (staged.rc[i]) B->ingest_status[i] = staged.rc[i];
   }
   trace_ingest.next("batch arenas", n);
   // ---- grouping
@@ -517,6 +526,13 @@ int ompdart_batch_run(ompdart_batch *B, void *stream) {
   cudaError_t ce;
   if (B->arenas.empty() && B->solos.empty()) {  // nothing to run (empty batch, or every CFG rejected)
     B->launches = 0;
+  } else if (B->prof.on) {
+    B->prof.collect_pending = true;
+    int n = 0;
+    for (auto &a : B->arenas) n += core_enqueue(&a->core, s, &B->prof);
+    for (auto &p : B->solos) n += core_enqueue(&p->core, s, &B->prof);
+    B->prof.close(s);
+    B->launches = n;
   } else if (B->opts.no_graph) {
     B->launches = enqueue_all(B, s);
   } else {
@@ -560,6 +576,10 @@ int ompdart_batch_sync(ompdart_batch *B, int32_t *status) {
       ce = cudaMemcpyAsync(p->h_status, p->core.dp.status, ST_COUNT * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
   if (ce != cudaSuccess) return set_error(OMPDART_E_CUDA, std::string("device run: ") + cudaGetErrorString(ce));
+  if (B->prof.on && B->prof.collect_pending) {
+    B->prof.collect();
+    B->prof.collect_pending = false;
+  }
   B->run_status = B->ingest_status;
   for (auto &a : B->arenas) {
     bool rerun = false;
@@ -580,6 +600,27 @@ int ompdart_batch_sync(ompdart_batch *B, int32_t *status) {
     if (rerun) B->graph_ok = false;
   }
   if (status) std::copy(B->run_status.begin(), B->run_status.end(), status);
+  return OMPDART_OK;
+}
+
+int ompdart_batch_profile(ompdart_batch *B, int enable) {
+  if (!B) return set_error(OMPDART_E_INVALID, "batch is NULL");
+  B->prof.on = enable != 0;
+  for (double &x : B->prof.ms) x = 0.0;
+  for (int &x : B->prof.cnt) x = 0;
+  B->prof.used = 0;
+  return OMPDART_OK;
+}
+
+int ompdart_batch_timings(ompdart_batch *B, ompdart_timing *out, int32_t max, int32_t *n) {
+  if (!B || !n) return set_error(OMPDART_E_INVALID, "NULL argument");
+  const int k = (int)B->prof.names.size();
+  *n = k;
+  for (int i = 0; i < k && i < max && out; ++i) {
+    out[i].name = B->prof.names[i].c_str();
+    out[i].launches = B->prof.cnt[i];
+    out[i].ms = B->prof.ms[i];
+  }
   return OMPDART_OK;
 }
 

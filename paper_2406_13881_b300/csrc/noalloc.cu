@@ -7,16 +7,18 @@
 // them ompdart_liveness_noalloc: the caller passes its CFG and the output
 // plane already in device memory, and every scratch byte the kernel needs
 // lives in one file-scope static device array (NOALLOC_SCRATCH_WORDS words,
-// 4.2 MiB, resident on every device that loads the library until the
+// 4.5 MiB, resident on every device that loads the library until the
 // process exits).
 //
 // The host code may not hand the array's name to a kernel (on the host it
-// is only a stand-in for the symbol): on its first call on a device the
-// entry point, with that device current, asks cudaGetSymbolAddress for the
-// device address and keeps it; the first call on each device should
-// therefore come before any stream capture.  Every call shares the array:
-// calls whose kernels overlap on the GPU race and must be ordered by the
-// caller (one stream, or events).
+// is only a stand-in for the symbol): with the device current, the entry
+// point asks cudaGetSymbolAddress for the device address and keeps it once
+// the lookup has succeeded (a failed lookup is tried again by the next
+// call).  That lookup happens on the first call on each device, which
+// should therefore come before any stream capture.  Every call waits for
+// `stream' before it returns.  Every call shares the array: calls whose
+// kernels overlap on the GPU race and must be ordered by the caller (one
+// stream, or events).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -35,36 +37,57 @@ constexpr int NA_MAX_BLOCKS = 65536;
 constexpr int NA_MAX_WORDS = 64;          // 4096 variables
 constexpr int NA_MAX_ACC = 1 << 20;       // accesses
 constexpr int NA_STATUS_WORDS = 32;
-// layout (uint64 words): [status 32][reach flags 65536 B][records 4 MiB]
-constexpr size_t NA_REACH_WORDS = NA_MAX_BLOCKS / 8;
+// layout (uint64 words): [status 32][reach flags, int32 per block]
+// [breadth-first order, int32 per block][summary records, uint32 per access]
+constexpr size_t NA_REACH_WORDS = NA_MAX_BLOCKS / 2;
+constexpr size_t NA_ORDER_WORDS = NA_MAX_BLOCKS / 2;
 constexpr size_t NA_REC_WORDS = NA_MAX_ACC / 2;
-constexpr size_t NOALLOC_SCRATCH_WORDS = NA_STATUS_WORDS + NA_REACH_WORDS + NA_REC_WORDS;
+constexpr size_t NOALLOC_SCRATCH_WORDS = NA_STATUS_WORDS + NA_REACH_WORDS + NA_ORDER_WORDS + NA_REC_WORDS;
+// device time a call may take before it gives up (OMPDART_E_TIMEOUT);
+// valid inputs within the limits above finish in well under a second
+constexpr unsigned long long NA_TIME_LIMIT_NS = 20ull * 1000 * 1000 * 1000;
 
 static __device__ __align__(256) uint64_t g_noalloc_scratch[NOALLOC_SCRATCH_WORDS];
 
-enum { NA_OK = 0, NA_BAD_CSR = 1, NA_TOO_MANY_ACC = 2, NA_NOCONVERGE = 3 };
+enum { NA_OK = 0, NA_BAD_CSR = 1, NA_TOO_MANY_ACC = 2, NA_NOCONVERGE = 3, NA_TIMEOUT = 4 };
+
+__device__ __forceinline__ unsigned long long na_now() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 // One CTA does everything (the sizes are bounded), with block-wide
 // barriers between the steps:
 //   1. validate the CSR offsets and ids, clear the reach flags and output
 //   2. summary records of every block (one warp per block)
-//   3. reachability from the entry (frontier relaxation, <= n rounds)
-//   4. liveness, one thread per 64-variable word, Gauss-Seidel sweeps in
-//      reverse block order until nothing changes (<= n + 2 sweeps):
+//   3. breadth-first search from the entry, level by level: the blocks
+//      reachable from the entry in order of their distance from it
+//   4. liveness, one thread per 64-variable word, Gauss-Seidel sweeps over
+//      the reachable blocks farthest first (a block after the successors it
+//      reaches by tree edges, so a chain settles in one sweep), until
+//      nothing changes (<= n + 2 sweeps):
 //        Live_in[b] = UE[b] | (Live_out[b] & ~Def[b]),
 //        Live_out[b] = OR of the successors' Live_in, or exit_host_live;
 //      UE = a read in either space before any write (Sec. II-B liveness,
 //      Sec. IV-D region-exit liveness); unreachable blocks stay zero.
+// Steps 3 and 4 stop with NA_TIMEOUT once the call has run for
+// NA_TIME_LIMIT_NS of device time.
 __global__ void __launch_bounds__(1024) k_live_noalloc(int n, int nv, int entry, const int32_t *so,
                                                        const int32_t *su, const int32_t *ao, const uint32_t *acc,
                                                        const uint64_t *xl, uint64_t *live, uint64_t *scratch) {
   int32_t *status = reinterpret_cast<int32_t *>(scratch);
-  uint8_t *reach = reinterpret_cast<uint8_t *>(scratch + NA_STATUS_WORDS);
-  uint32_t *rec = reinterpret_cast<uint32_t *>(scratch + NA_STATUS_WORDS + NA_REACH_WORDS);
-  __shared__ int bad, changed;
+  int32_t *reach = reinterpret_cast<int32_t *>(scratch + NA_STATUS_WORDS);
+  int32_t *order = reinterpret_cast<int32_t *>(scratch + NA_STATUS_WORDS + NA_REACH_WORDS);
+  uint32_t *rec = reinterpret_cast<uint32_t *>(scratch + NA_STATUS_WORDS + NA_REACH_WORDS + NA_ORDER_WORDS);
+  __shared__ int bad, tail, stop;
   const int t = threadIdx.x, T = blockDim.x, lane = t & 31, warp = t >> 5, nwarp = T >> 5;
   const int W = (nv + 63) / 64;
-  if (t == 0) bad = NA_OK;
+  const unsigned long long t0 = na_now();
+  if (t == 0) {
+    bad = NA_OK;
+    stop = 0;
+  }
   __syncthreads();
   // ---- 1. validation and clearing
   const int E = so[n], A = ao[n];
@@ -91,24 +114,38 @@ __global__ void __launch_bounds__(1024) k_live_noalloc(int n, int nv, int entry,
   }
   // ---- 2. summary records
   for (int b = warp; b < n; b += nwarp) summarize_block(acc, rec, ao[b], ao[b + 1], lane);
-  // ---- 3. reachability
-  if (t == 0) reach[entry] = 1;
-  __syncthreads();
-  for (int round = 0; round <= n; ++round) {
-    if (t == 0) changed = 0;
-    __syncthreads();
-    for (int b = t; b < n; b += T)
-      if (reach[b])
-        for (int e = so[b]; e < so[b + 1]; ++e)
-          if (!reach[su[e]]) {
-            reach[su[e]] = 1;
-            changed = 1;
-          }
-    __syncthreads();
-    if (!changed) break;
-    __syncthreads();
+  // ---- 3. breadth-first order of the reachable blocks (each block enters
+  // the order once: the thread that flips its flag appends it)
+  if (t == 0) {
+    reach[entry] = 1;
+    order[0] = entry;
+    tail = 1;
   }
-  // ---- 4. liveness, one thread per word
+  __syncthreads();
+  int head = 0;
+  while (true) {
+    const int hi = tail;  // this level: order[head, hi)
+    __syncthreads();      // every thread has read the level's end before any appends
+    if (head == hi) break;
+    for (int i = head + t; i < hi; i += T) {
+      const int b = order[i];
+      for (int e = so[b]; e < so[b + 1]; ++e) {
+        const int s = su[e];
+        if (atomicCAS(&reach[s], 0, 1) == 0) order[atomicAdd(&tail, 1)] = s;
+      }
+    }
+    if (t == 0 && na_now() - t0 > NA_TIME_LIMIT_NS) stop = 1;
+    __syncthreads();
+    if (stop) break;
+    head = hi;
+  }
+  const int nr = tail;  // reachable blocks
+  __syncthreads();
+  if (stop) {
+    if (t == 0) status[0] = NA_TIMEOUT;
+    return;
+  }
+  // ---- 4. liveness, one thread per word, farthest blocks first
   int result = NA_OK;
   if (t < W) {
     const int w = t;
@@ -121,9 +158,13 @@ __global__ void __launch_bounds__(1024) k_live_noalloc(int n, int nv, int entry,
         result = NA_NOCONVERGE;
         break;
       }
+      if (na_now() - t0 > NA_TIME_LIMIT_NS) {
+        result = NA_TIMEOUT;
+        break;
+      }
       again = false;
-      for (int b = n - 1; b >= 0; --b) {
-        if (!reach[b]) continue;
+      for (int k = nr - 1; k >= 0; --k) {
+        const int b = order[k];
         uint64_t z = so[b] == so[b + 1] ? x : 0;
         for (int e = so[b]; e < so[b + 1]; ++e) z |= live[(size_t)su[e] * W + w];
         for (int r = ao[b]; r < ao[b + 1]; ++r) {
@@ -140,13 +181,13 @@ __global__ void __launch_bounds__(1024) k_live_noalloc(int n, int nv, int entry,
       }
     }
   }
-  if (result != NA_OK) atomicExch(&status[0], result);
+  if (result != NA_OK) atomicMax(&status[0], result);
 }
 
+// the scratch array's device address per device, once a lookup succeeded
 struct DeviceSlot {
-  std::once_flag once;
+  std::mutex mu;
   uint64_t *ptr = nullptr;
-  cudaError_t err = cudaSuccess;
 };
 DeviceSlot g_slots[64];
 
@@ -175,27 +216,35 @@ extern "C" int ompdart_liveness_noalloc(int32_t n_blocks, int32_t n_vars, int32_
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
     return na_fail(OMPDART_E_CUDA, "cudaGetDevice failed");
   DeviceSlot &slot = g_slots[dev];
-  std::call_once(slot.once, [&] {
-    void *p = nullptr;
-    slot.err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    slot.ptr = static_cast<uint64_t *>(p);
-  });
-  if (slot.err != cudaSuccess || !slot.ptr) return na_fail(OMPDART_E_CUDA, "cudaGetSymbolAddress of the scratch failed");
+  uint64_t *scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(slot.mu);
+    if (!slot.ptr) {
+      void *p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();  // not sticky: the next call tries again
+        return na_fail(OMPDART_E_CUDA, "cudaGetSymbolAddress of the scratch failed");
+      }
+      slot.ptr = static_cast<uint64_t *>(p);
+    }
+    scratch = slot.ptr;
+  }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   // status words start at zero for every call
-  if (cudaMemsetAsync(slot.ptr, 0, NA_STATUS_WORDS * sizeof(uint64_t), s) != cudaSuccess)
+  if (cudaMemsetAsync(scratch, 0, NA_STATUS_WORDS * sizeof(uint64_t), s) != cudaSuccess)
     return na_fail(OMPDART_E_CUDA, "clearing the status words failed");
   k_live_noalloc<<<1, 1024, 0, s>>>(n_blocks, n_vars, entry, succ_off, succ, acc_off, acc, exit_host_live, live_in,
-                                    slot.ptr);
+                                    scratch);
   if (cudaGetLastError() != cudaSuccess) return na_fail(OMPDART_E_CUDA, "kernel launch failed");
   int32_t st = 0;
-  if (cudaMemcpyAsync(&st, slot.ptr, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+  if (cudaMemcpyAsync(&st, scratch, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
     return na_fail(OMPDART_E_CUDA, "device run failed");
   switch (st) {
     case NA_OK: return OMPDART_OK;
     case NA_BAD_CSR: return na_fail(OMPDART_E_INVALID, "malformed CSR, id out of range or entry with predecessors");
     case NA_TOO_MANY_ACC: return na_fail(OMPDART_E_BUDGET, "more than 2^20 accesses for the no-allocation entry point");
+    case NA_TIMEOUT: return na_fail(OMPDART_E_TIMEOUT, "the no-allocation liveness ran past its device time limit");
     default: return na_fail(OMPDART_E_NOCONVERGE, "liveness sweeps did not converge");
   }
 }

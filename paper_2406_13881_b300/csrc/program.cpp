@@ -89,10 +89,19 @@ void ompdart_program_result_free(ompdart_program_result *r) {
   free(r);
 }
 
-int ompdart_analyze_program(const ompdart_program *P, const ompdart_opts *opts, ompdart_program_result **out) {
+int ompdart_analyze_program(const ompdart_program *Pin, const ompdart_opts *opts, ompdart_program_result **out) {
   set_last_error_text("");
-  if (!P || !out || P->n_funcs < 0 || (P->n_funcs > 0 && (!P->funcs || !P->site_off)))
+  if (!Pin || !out || Pin->n_funcs < 0 || (Pin->n_funcs > 0 && (!Pin->funcs || !Pin->site_off)))
     return set_error(OMPDART_E_INVALID, "bad program");
+  // functions given in device memory: their arrays copied to the host first
+  StagedCfgs staged;
+  ompdart_program prog = *Pin;
+  {
+    std::string serr;
+    const int src = stage_cfgs(Pin->funcs, Pin->n_funcs, &staged, &prog.funcs, &serr);
+    if (src) return set_error(src, serr);
+  }
+  const ompdart_program *P = &prog;
   *out = nullptr;
   ompdart_opts o{};
   if (opts) o = *opts;

@@ -246,6 +246,12 @@ int ompdart_server_create(const ompdart_server_opts *opts, ompdart_server **out)
 
 int ompdart_server_submit(ompdart_server *S, const ompdart_cfg *c, int64_t *ticket) {
   if (!S || !c || !ticket) return set_error(OMPDART_E_INVALID, "NULL argument");
+  StagedCfgs staged;  // a CFG in device memory: its arrays copied to the host first
+  {
+    std::string serr;
+    const int src = stage_cfgs(c, 1, &staged, &c, &serr);
+    if (src) return set_error(src, serr);
+  }
   if (c->n_blocks < 1 || !c->succ_off || !c->acc_off || c->n_vars < 1)
     return set_error(OMPDART_E_INVALID, "malformed CFG header");
   ReqPtr r = std::make_shared<Request>();

@@ -5,7 +5,10 @@
 #include <chrono>
 #include <cstdint>
 #include <cstdio>
+#include <deque>
+#include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/ompdart.h"
@@ -41,6 +44,22 @@ struct TraceScope {
     std::fprintf(stderr, "[ompdart] %-22s %9.3f ms  (%lld)\n", name, ms, n);
   }
 };
+
+// ---- staging.cpp: CFGs given in device memory (ompdart_cfg.mem =
+// OMPDART_MEM_DEVICE) copied to host buffers for ingestion
+struct StagedCfgs {
+  std::vector<ompdart_cfg> cfgs;           // the CFGs with host pointers
+  std::deque<std::vector<uint8_t>> bufs;   // host copies of the device arrays
+  std::map<std::pair<const void *, size_t>, const void *> seen;  // one copy per device array
+  std::vector<int> rc;                     // per CFG (per_cfg mode): its staging error or OK
+  std::vector<std::string> err;
+};
+// *out = in when every CFG is in host memory, else st->cfgs.  A CFG that
+// cannot be staged fails the call (per_cfg false) or, with per_cfg, is
+// replaced by an empty CFG that ingestion rejects and its code is left in
+// st->rc[i] for the caller to report.
+int stage_cfgs(const ompdart_cfg *in, int n, StagedCfgs *st, const ompdart_cfg **out, std::string *err,
+               bool per_cfg = false);
 
 // ---- api.cu: thread-local error text of ompdart_last_error
 void set_last_error_text(const std::string &msg);

@@ -358,13 +358,25 @@ int ompdart_summarize_batch(const ompdart_cfg *callees, int32_t n, const ompdart
   ompdart_opts o{};
   if (opts) o = *opts;
   if (cudaSetDevice(o.device) != cudaSuccess) return set_error(OMPDART_E_CUDA, "cudaSetDevice failed");
-  return summarize_run(callees, n, o, rows, status);
+  StagedCfgs staged;  // callees given in device memory: copied for ingestion, a failure fails alone
+  std::string serr;
+  const int src = stage_cfgs(callees, n, &staged, &callees, &serr, true);
+  if (src) return set_error(src, serr);
+  const int rc = summarize_run(callees, n, o, rows, status);
+  if (status)
+    for (int i = 0; i < (int)staged.rc.size(); ++i)
+      if (staged.rc[i]) status[i] = staged.rc[i];
+  return rc;
 }
 
 int ompdart_summarize_callee(const ompdart_cfg *callee, const int32_t *var_map, int32_t caller_n_vars,
                              uint64_t *caller_row, const ompdart_opts *opts) {
   set_last_error_text("");
   if (!callee || !caller_row || caller_n_vars < 1) return set_error(OMPDART_E_INVALID, "bad arguments");
+  StagedCfgs staged;
+  std::string serr;
+  const int src = stage_cfgs(callee, 1, &staged, &callee, &serr);
+  if (src) return set_error(src, serr);
   std::vector<uint64_t> sum((size_t)7 * ((callee->n_vars + 63) / 64));
   uint64_t *rows[1] = {sum.data()};
   int32_t st = 0;
