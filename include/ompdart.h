@@ -320,8 +320,10 @@ int ompdart_summarize_batch(const ompdart_cfg *callees, int32_t n, const ompdart
    variable it denotes (a global, or the actual argument of a pointer
    parameter) or -1 (a local, dropped); NULL = identity.  caller_row
    receives 7 * ceil(caller_n_vars / 64) words.  Callee variables that
-   denote the same caller variable combine pessimistically: Req, Kill and
-   MustDef by OR, Gen by AND (a kill overrides a gen). */
+   denote the same caller variable combine into the tightest row that is
+   sound for every callee with these per-variable summaries: Req, Kill,
+   MustDef and Gen of any alias carry over, and a kill of one alias
+   overrides a gen of another. */
 int ompdart_summarize_callee(const ompdart_cfg *callee, const int32_t *var_map, int32_t caller_n_vars,
                              uint64_t *caller_row, const ompdart_opts *opts);
 
@@ -345,7 +347,11 @@ int ompdart_summarize_callee(const ompdart_cfg *callee, const int32_t *var_map, 
         numbering (a callee local starts valid on the host only and is dead
         after the exit).  A site passes on at most max_contexts contexts
         (0 = 4): sorted, the excess merged into the last by the meet
-        (validity AND, liveness OR). */
+        (validity AND, liveness OR), which lies below every context it
+        absorbs, so the merged instance's transfers serve each of them;
+        a context whose meet would leave a variable valid nowhere that one
+        of them holds somewhere (a host-only and a device-only copy) is not
+        merged and runs as a context of its own. */
 typedef struct {
   int32_t n_funcs;
   const ompdart_cfg *funcs;    /* [n_funcs]                                     */

@@ -15,7 +15,9 @@
 //      the call (validity the callee starts from, liveness after the call)
 //      mapped into the callee's numbering; a site passes on at most
 //      max_contexts of them (sorted, the excess merged into the last by the
-//      meet: validity AND, liveness OR).
+//      meet: validity AND, liveness OR), except that a context whose meet
+//      would leave a variable valid nowhere that either holds somewhere
+//      stays a context of its own.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -260,15 +262,31 @@ int ompdart_analyze_program(const ompdart_program *Pin, const ompdart_opts *opts
       std::vector<Ctx> &v = kv.second;
       std::sort(v.begin(), v.end());
       v.erase(std::unique(v.begin(), v.end()), v.end());
-      if ((int)v.size() > max_ctx) {  // merge the excess into the last kept one
-        Ctx &m = v[max_ctx - 1];
-        for (size_t e = max_ctx; e < v.size(); ++e)
-          for (size_t w = 0; w < m.eh.size(); ++w) {
-            m.eh[w] &= v[e].eh[w];
-            m.ed[w] &= v[e].ed[w];
-            m.xl[w] |= v[e].xl[w];
+      if ((int)v.size() > max_ctx) {
+        // merge the excess into the last kept one by the meet, except a
+        // context whose meet would leave a variable valid nowhere that one
+        // of the two holds somewhere: it stays a context of its own
+        Ctx m = v[max_ctx - 1];
+        std::vector<Ctx> alone;
+        const size_t Wn = m.eh.size();
+        for (size_t e = max_ctx; e < v.size(); ++e) {
+          const Ctx &c = v[e];
+          Ctx t{Row(Wn), Row(Wn), Row(Wn)};
+          bool hole = false;
+          for (size_t w = 0; w < Wn; ++w) {
+            t.eh[w] = m.eh[w] & c.eh[w];
+            t.ed[w] = m.ed[w] & c.ed[w];
+            t.xl[w] = m.xl[w] | c.xl[w];
+            hole |= ((m.eh[w] | m.ed[w] | c.eh[w] | c.ed[w]) & ~(t.eh[w] | t.ed[w])) != 0;
           }
-        v.resize(max_ctx);
+          if (hole)
+            alone.push_back(c);
+          else
+            m = std::move(t);
+        }
+        v.resize(max_ctx - 1);
+        v.push_back(std::move(m));
+        v.insert(v.end(), alone.begin(), alone.end());
       }
       const int g = P->site_callee[kv.first];
       ctxs[g].insert(ctxs[g].end(), v.begin(), v.end());

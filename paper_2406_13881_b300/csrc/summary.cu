@@ -321,25 +321,19 @@ int summarize_run(const ompdart_cfg *cfgs, int n, const ompdart_opts &o, uint64_
 // Callee variables sharing one caller variable combine pessimistically:
 // Req, Kill and MustDef by OR, Gen by AND.
 void map_summary(const uint64_t *sum, int callee_vars, const int32_t *var_map, int caller_vars, uint64_t *row) {
+  // Aliases (callee variables denoting one caller variable) combine into
+  // the tightest row sound for every callee with these per-variable
+  // summaries: Req, Kill, MustDef and Gen of any alias carry over, and a
+  // kill of one alias overrides a gen of another (Sec. IV-C, applied
+  // pessimistically at the call site).
   const int Wc = (callee_vars + 63) / 64, Wr = (caller_vars + 63) / 64;
-  std::vector<uint8_t> seen((size_t)caller_vars, 0);
   memset(row, 0, sizeof(uint64_t) * 7 * Wr);
   for (int v = 0; v < callee_vars; ++v) {
     const int t = var_map ? var_map[v] : v;
     if (t < 0 || t >= caller_vars) continue;
     const uint64_t mb = 1ull << (v & 63), tb = 1ull << (t & 63);
-    for (int k = 0; k < 7; ++k) {
-      const bool x = (sum[(size_t)k * Wc + (v >> 6)] & mb) != 0;
-      uint64_t &r = row[(size_t)k * Wr + (t >> 6)];
-      const bool gen = k == 2 || k == 4;
-      if (gen) {
-        if (!seen[t] ? x : ((r & tb) && x)) r |= tb;
-        else r &= ~tb;
-      } else if (x) {
-        r |= tb;
-      }
-    }
-    seen[t] = 1;
+    for (int k = 0; k < 7; ++k)
+      if (sum[(size_t)k * Wc + (v >> 6)] & mb) row[(size_t)k * Wr + (t >> 6)] |= tb;
   }
   for (int w = 0; w < Wr; ++w) {  // a kill overrides a gen of an alias
     row[2 * Wr + w] &= ~row[3 * Wr + w];

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-import refprog
+from oracle import program as refprog
 from paper_2406_13881_b300 import _native, workload as wl
 from compare import assert_matches_oracle
 from test_calls_gpu import structured_with_calls
