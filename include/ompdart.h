@@ -61,6 +61,38 @@
  *   with calls take the chunked scan solver (reducible CFG, loop bodies
  *   contiguous in loop order); others return OMPDART_E_INVALID.
  *
+ * DATA REGION AND DIRECTIVES (opts.data_region, cfg.region)
+ *   The constructs of Table II.  The single target data region R of the
+ *   function (Sec. IV-D) is the set of blocks b with S dom b, E pdom b and
+ *   b != E, where S is the nearest common dominator of the kernel blocks
+ *   and of the headers of the natural loops whose body holds a kernel
+ *   block ("begin before any loop capturing the first kernel"), and E the
+ *   nearest common post-dominator (towards one virtual exit fed by every
+ *   block without successors) of the blocks those kernel blocks and loop
+ *   bodies lead to outside themselves ("end after any loop capturing the
+ *   last kernel"; E is the virtual exit when there is none).  On every edge
+ *   leaving R the host copy of each variable live at its target is made
+ *   valid (a `from' there: "if stale data may be read on the host after
+ *   exit from a target data region, the from map-type is included"); this
+ *   is the one change the mode makes to the analysis.  Then:
+ *     map_to      `to's made on every way into R (every edge entering R, or
+ *                 the `to's of the kernel whose entry edges are R's);
+ *     map_from    `from's made on every way out of R (every edge leaving R
+ *                 and every function exit inside R);
+ *     map_alloc   variables a kernel accesses on the device with neither;
+ *                 tofrom = map_to & map_from;
+ *     kernel_to / kernel_from   the `to's (`from's) right before accesses
+ *                 inside kernel k, made right before the kernel instead (no
+ *                 host code runs in a kernel), less what map_to carries;
+ *     acc_point   Sec. IV-F consolidation: a transfer right before a host
+ *                 access moves up to just after the previous access of the
+ *                 same variable in the block (or to the block's first
+ *                 access); all transfers of one direction at one point form
+ *                 one `target update'; a call keeps its own;
+ *   edge records and exit sets stay as they are: on an edge entering or
+ *   leaving R (region_entry_edges / region_exit_edges) and at exits inside
+ *   R, the bits in map_to / map_from are carried by the map clauses.
+ *
  * ERRORS
  *   Every call returns OMPDART_OK (0) or a negative code; the text of the
  *   last error of the calling thread is ompdart_last_error().  Invalid
@@ -115,6 +147,18 @@ typedef struct {
   const uint64_t *call_planes;
   int32_t n_calls;
   int32_t mem;                      /* OMPDART_MEM_HOST or OMPDART_MEM_DEVICE        */
+  /* offload kernels (Sec. IV-B offloaded nodes): region[b] = id (0 ..
+     n_blocks-1) of the kernel block b belongs to, or -1 for host code;
+     NULL = no kernel information (no data region, no directives). */
+  const int32_t *region;
+  /* [W] scalar variables (Sec. IV-D firstprivate paragraph); NULL = none.
+     With region: a scalar that a kernel reads on the device and never
+     writes is passed to that kernel as firstprivate -- its device reads
+     there read the private copy made from the host value at the launch,
+     so they need the host copy valid and leave the device copy as it was
+     (they are analysed as host reads), and the kernel gets a firstprivate
+     clause instead of a `to'. */
+  const uint64_t *scalar_vars;
 } ompdart_cfg;
 
 typedef struct {
@@ -130,6 +174,9 @@ typedef struct {
                            and warps_per_cta per arena (ompdart_batch_create)     */
   int32_t no_graph;     /* batches: nonzero = launch kernels directly instead of
                            replaying a captured CUDA graph                        */
+  int32_t data_region;  /* nonzero (CFGs with region): the single target data
+                           region of Sec. IV-D and the directives (see
+                           DATA REGION AND DIRECTIVES)                            */
 } ompdart_opts;
 
 typedef struct {
@@ -160,6 +207,19 @@ typedef struct {
   uint64_t *call_to, *call_from;          /* [n_call_sites*n_words]            */
   uint64_t *call_entry_h, *call_entry_d;  /* [n_call_sites*n_words]            */
   uint64_t *call_exit_live;               /* [n_call_sites*n_words]            */
+  /* data region and directives (opts.data_region with cfg.region, else
+     NULL / 0; see DATA REGION AND DIRECTIVES) */
+  uint8_t *in_region;          /* [n_blocks] inside the target data region   */
+  uint64_t *map_to, *map_from, *map_alloc;  /* [n_words] map clauses        */
+  int32_t n_kernels;           /* kernel ids 0 .. n_kernels-1                 */
+  uint64_t *kernel_to;         /* [n_kernels*n_words] update to before kernel k */
+  uint64_t *kernel_from;       /* [n_kernels*n_words] update from before kernel k */
+  uint64_t *firstprivate;      /* [n_kernels*n_words] firstprivate on kernel k  */
+  int32_t *acc_point;          /* [n_acc] insertion point of the transfer
+                                  flagged at this access, or -1             */
+  int32_t n_region_entries, n_region_exits;
+  int32_t *region_entry_edges; /* [n_region_entries] edge ids into the region */
+  int32_t *region_exit_edges;  /* [n_region_exits] edge ids out of it        */
   void *host_block;            /* library-internal: the host allocation that
                                   holds a host result's arrays (shared by the
                                   results of one batch arena); NULL in views  */

@@ -269,6 +269,8 @@ typedef struct {
   const uint64_t *edge_src;                /* [N*W] source-valid test of p   */
   const uint64_t *node_gen;                /* [N*W] or NULL                  */
   uint64_t *x_in, *x_out, *x_meet;         /* x_meet may be NULL             */
+  const uint8_t *is_exit_edge;             /* [E] edges leaving the data region, or NULL */
+  const uint64_t *exit_gen;                /* [N*W] added along such an edge p->b: row b */
 } fwd_problem;
 
 static int forward_must(const graph *g, fwd_problem *P) {
@@ -297,6 +299,7 @@ static int forward_must(const graph *g, fwd_problem *P) {
           uint64_t ev = P->x_out[(size_t)p * W + w];
           if (P->is_entry_edge && P->is_entry_edge[e])
             ev |= P->edge_mask[(size_t)b * W + w] & P->edge_src[(size_t)p * W + w];
+          if (P->is_exit_edge && P->is_exit_edge[e]) ev |= P->exit_gen[(size_t)b * W + w];
           m[w] &= ev;
         }
       }
@@ -504,6 +507,197 @@ static int natural_loops(const graph *g, const uint64_t *KH, const uint64_t *KD,
   return ORACLE_OK;
 }
 
+/* ---- the single target data region (Sec. IV-D) ---------------------------
+ * Post-dominators: Cooper, Harvey and Kennedy's iterative algorithm on the
+ * reversed graph, rooted at a virtual exit (node N) whose reversed edges
+ * lead to every reachable block without successors.  Blocks that reach no
+ * exit get no post-dominator (-1). */
+static int post_dominators(const graph *g, int32_t *ipdom, int32_t *prpo) {
+  int N = g->N, X = N;  /* X: the virtual exit */
+  int32_t *order = xcalloc((size_t)N + 1, sizeof(int32_t));
+  int32_t *stk = xcalloc((size_t)N + 1, sizeof(int32_t));
+  int32_t *it = xcalloc((size_t)N + 1, sizeof(int32_t));
+  uint8_t *seen = xcalloc((size_t)N + 1, 1);
+  int32_t *xs = xcalloc((size_t)N + 1, sizeof(int32_t));  /* exit blocks */
+  if (!order || !stk || !it || !seen || !xs) return ORACLE_E_NOMEM;
+  int nx = 0;
+  for (int b = 0; b < N; ++b)
+    if (g->reach[b] && g->so[b] == g->so[b + 1]) xs[nx++] = b;
+  /* depth-first search over reversed edges from X: X's successors are the
+     exit blocks, a block's successors are its reachable predecessors */
+  int sp = 0, npost = 0;
+  stk[sp++] = X; seen[X] = 1; it[X] = 0;
+  while (sp) {
+    int b = stk[sp - 1], nxt = -1;
+    if (b == X) {
+      if (it[X] < nx) nxt = xs[it[X]++];
+    } else {
+      while (it[b] < g->po[b + 1] - g->po[b]) {
+        int p = g->ps[g->po[b] + it[b]++];
+        if (g->reach[p]) { nxt = p; break; }
+      }
+    }
+    if (nxt >= 0) {
+      if (!seen[nxt]) { seen[nxt] = 1; it[nxt] = 0; stk[sp++] = nxt; }
+    } else {
+      order[npost++] = b; --sp;
+    }
+  }
+  for (int b = 0; b <= N; ++b) { prpo[b] = -1; ipdom[b] = -1; }
+  for (int i = 0; i < npost; ++i) prpo[order[i]] = npost - 1 - i;
+  int32_t *rpo = stk;
+  for (int i = 0; i < npost; ++i) rpo[npost - 1 - i] = order[i];
+  ipdom[X] = X;
+  int changed = 1;
+  while (changed) {
+    changed = 0;
+    for (int i = 1; i < npost; ++i) {
+      int b = rpo[i], nd = -1;
+      /* reversed predecessors of b = its successors, or X for an exit block */
+      int ns = g->so[b + 1] - g->so[b];
+      for (int k = 0; k < (ns ? ns : 1); ++k) {
+        int q = ns ? g->s[g->so[b] + k] : X;
+        if (ipdom[q] < 0) continue;
+        if (nd < 0) { nd = q; continue; }
+        int f1 = q, f2 = nd;
+        while (f1 != f2) {
+          while (prpo[f1] > prpo[f2]) f1 = ipdom[f1];
+          while (prpo[f2] > prpo[f1]) f2 = ipdom[f2];
+        }
+        nd = f1;
+      }
+      if (nd >= 0 && ipdom[b] != nd) { ipdom[b] = nd; changed = 1; }
+    }
+  }
+  free(order); free(stk); free(it); free(seen); free(xs);
+  return ORACLE_OK;
+}
+
+/* Interval numbering of a tree given by parent[] over nodes [0, n) with
+   `root' (nodes with parent < 0 other than the root are left out):
+   a is an ancestor-or-self of b iff pre[a] <= pre[b] and post[b] <= post[a]. */
+static int tree_intervals(int n, const int32_t *parent, int root, int32_t *pre, int32_t *post) {
+  int32_t *co = xcalloc((size_t)n + 1, sizeof(int32_t));
+  int32_t *ch = xcalloc((size_t)n, sizeof(int32_t));
+  int32_t *fill = xcalloc((size_t)n, sizeof(int32_t));
+  int32_t *stk = xcalloc((size_t)n, sizeof(int32_t));
+  int32_t *it = xcalloc((size_t)n, sizeof(int32_t));
+  if (!co || !ch || !fill || !stk || !it) return ORACLE_E_NOMEM;
+  for (int b = 0; b < n; ++b) { pre[b] = -1; post[b] = -1; }
+  for (int b = 0; b < n; ++b)
+    if (b != root && parent[b] >= 0) co[parent[b] + 1]++;
+  for (int b = 0; b < n; ++b) co[b + 1] += co[b];
+  for (int b = 0; b < n; ++b)
+    if (b != root && parent[b] >= 0) ch[co[parent[b]] + fill[parent[b]]++] = b;
+  int sp = 0, clock = 0;
+  stk[sp++] = root; it[root] = co[root]; pre[root] = clock++;
+  while (sp) {
+    int b = stk[sp - 1];
+    if (it[b] < co[b + 1]) {
+      int c = ch[it[b]++];
+      pre[c] = clock++; it[c] = co[c]; stk[sp++] = c;
+    } else {
+      post[b] = clock++; --sp;
+    }
+  }
+  free(co); free(ch); free(fill); free(stk); free(it);
+  return ORACLE_OK;
+}
+
+/* nearest common ancestor of a and b in a tree with CHK numbering */
+static int tree_meet(int a, int b, const int32_t *parent, const int32_t *num) {
+  while (a != b) {
+    while (num[a] > num[b]) a = parent[a];
+    while (num[b] > num[a]) b = parent[b];
+  }
+  return a;
+}
+
+/* R (see oracle_cfg.data_region) into in_r[N]; its exit edges into
+   exit_e[E].  Nothing when no reachable block belongs to a kernel. */
+static int data_region(const oracle_cfg *c, const graph *g, uint8_t *in_r, uint8_t *exit_e) {
+  int N = g->N, rc;
+  memset(in_r, 0, (size_t)N);
+  memset(exit_e, 0, (size_t)g->E);
+  int32_t *idom = xcalloc((size_t)N, sizeof(int32_t)), *num = xcalloc((size_t)N, sizeof(int32_t));
+  int32_t *pre = xcalloc((size_t)N, sizeof(int32_t)), *post = xcalloc((size_t)N, sizeof(int32_t));
+  int32_t *ipd = xcalloc((size_t)N + 1, sizeof(int32_t)), *pnum = xcalloc((size_t)N + 1, sizeof(int32_t));
+  int32_t *ppre = xcalloc((size_t)N + 1, sizeof(int32_t)), *ppost = xcalloc((size_t)N + 1, sizeof(int32_t));
+  int32_t *stamp = xcalloc((size_t)N, sizeof(int32_t)), *stk = xcalloc((size_t)N, sizeof(int32_t));
+  int32_t *body = xcalloc((size_t)N, sizeof(int32_t));
+  uint8_t *cap = xcalloc((size_t)N, 1);  /* block in a loop body that holds a kernel block, or a kernel block */
+  uint8_t *hcap = xcalloc((size_t)N, 1); /* header of such a loop */
+  if (!idom || !num || !pre || !post || !ipd || !pnum || !ppre || !ppost || !stamp || !stk || !body || !cap ||
+      !hcap)
+    return ORACLE_E_NOMEM;
+  int nk = 0;
+  for (int b = 0; b < N; ++b)
+    if (g->reach[b] && c->region[b] >= 0) { cap[b] = 1; ++nk; }
+  if (!nk) goto out;
+  if ((rc = dominators(g, idom, num))) return rc;
+  if ((rc = dom_intervals(g, idom, pre, post))) return rc;
+  if ((rc = post_dominators(g, ipd, pnum))) return rc;
+  if ((rc = tree_intervals(N + 1, ipd, N, ppre, ppost))) return rc;
+  /* natural loops whose body holds a kernel block: their headers and bodies */
+  for (int b = 0; b < N; ++b) stamp[b] = -1;
+  for (int h = 0; h < N; ++h) {
+    if (!g->reach[h]) continue;
+    int sp = 0, nb = 0, is_h = 0;
+    for (int k = g->po[h]; k < g->po[h + 1]; ++k) {
+      int t = g->ps[k];
+      if (!g->reach[t] || !(pre[h] <= pre[t] && post[t] <= post[h])) continue;
+      is_h = 1;
+      if (t != h && stamp[t] != h) { stamp[t] = h; stk[sp++] = t; }
+    }
+    if (!is_h) continue;
+    stamp[h] = h;
+    body[nb++] = h;
+    while (sp) {
+      int b = stk[--sp];
+      body[nb++] = b;
+      for (int k = g->po[b]; k < g->po[b + 1]; ++k) {
+        int p = g->ps[k];
+        if (g->reach[p] && stamp[p] != h) { stamp[p] = h; stk[sp++] = p; }
+      }
+    }
+    int holds = 0;
+    for (int i = 0; i < nb; ++i) holds |= c->region[body[i]] >= 0;
+    if (!holds) continue;
+    hcap[h] = 1;
+    for (int i = 0; i < nb; ++i) cap[body[i]] = 2 | (cap[body[i]] & 1);
+  }
+  /* S: nearest common dominator of the kernel blocks and the capturing
+     headers (the region begins at S); E: nearest common post-dominator of
+     the blocks that the kernel blocks and the capturing bodies lead to
+     outside themselves (the region ends where E begins; the virtual exit
+     if there is none, or one of them reaches no exit) */
+  int S = -1, E = -1;
+  for (int b = 0; b < N; ++b) {
+    if ((cap[b] & 1) || hcap[b]) S = S < 0 ? b : tree_meet(S, b, idom, num);
+    if (!cap[b]) continue;
+    for (int e = g->so[b]; e < g->so[b + 1]; ++e) {
+      int t = g->s[e];
+      if (cap[t]) continue;
+      if (ipd[t] < 0) E = N;
+      else if (E != N) E = E < 0 ? t : tree_meet(E, t, ipd, pnum);
+    }
+  }
+  if (E < 0) E = N;
+  for (int b = 0; b < N; ++b) {
+    if (!g->reach[b] || b == E) continue;
+    int sdom = pre[S] <= pre[b] && post[b] <= post[S];
+    int epdom = E == N || (ppre[b] >= 0 && ppre[E] <= ppre[b] && ppost[b] <= ppost[E]);
+    in_r[b] = (uint8_t)(sdom && epdom);
+  }
+  for (int b = 0; b < N; ++b)
+    for (int e = g->so[b]; e < g->so[b + 1]; ++e)
+      exit_e[e] = (uint8_t)(g->reach[b] && in_r[b] && !in_r[g->s[e]]);
+out:
+  free(idom); free(num); free(pre); free(post); free(ipd); free(pnum); free(ppre); free(ppost);
+  free(stamp); free(stk); free(body); free(cap); free(hcap);
+  return ORACLE_OK;
+}
+
 /* ---- step 7: access flags --------------------------------------------------
  * Replay each reachable block from (H_in, D_in): an S-read that finds S
  * stale gets a transfer right before it (`to' for a device read, `from'
@@ -612,11 +806,17 @@ int oracle_solve(const oracle_cfg *c, oracle_out *out) {
   uint64_t *MH = pl[14], *MD = pl[15];
   uint64_t *DI = pl[16], *DO = pl[17], *HM = pl[18], *HI = pl[19], *HO = pl[20], *FX = pl[21];
   uint8_t *hdr = xcalloc((size_t)N, 1), *ent = xcalloc((size_t)E, 1);
+  uint8_t *inr = xcalloc((size_t)N, 1), *rxe = xcalloc((size_t)E, 1);
   uint64_t *TE = xcalloc((size_t)E * W, sizeof(uint64_t)), *FE = xcalloc((size_t)E * W, sizeof(uint64_t));
   uint8_t *fl = xcalloc((size_t)g.A, 1);
   uint64_t *init_h = xcalloc((size_t)W, sizeof(uint64_t)), *init_d = xcalloc((size_t)W, sizeof(uint64_t));
   uint64_t *xlive = xcalloc((size_t)W, sizeof(uint64_t));
-  if (!hdr || !ent || !TE || !FE || !fl || !init_h || !init_d || !xlive) { rc = ORACLE_E_NOMEM; goto done; }
+  if (!hdr || !ent || !inr || !rxe || !TE || !FE || !fl || !init_h || !init_d || !xlive) {
+    rc = ORACLE_E_NOMEM;
+    goto done;
+  }
+  const int region_mode = c->data_region && c->region;
+  if (region_mode && (rc = data_region(c, &g, inr, rxe))) goto done;
   for (int w = 0; w < W; ++w) {
     init_h[w] = (c->entry_host_valid ? c->entry_host_valid[w] : ~(uint64_t)0) & g.top[w];
     init_d[w] = (c->entry_dev_valid ? c->entry_dev_valid[w] : 0) & g.top[w];
@@ -647,7 +847,11 @@ int oracle_solve(const oracle_cfg *c, oracle_out *out) {
   {
     uint64_t *C = pl[22];
     for (size_t i = 0; i < NW; ++i) C[i] = LV[i] & ~DI[i];
-    fwd_problem P = {GH, KH, init_h, ent, MH, DO, C, HI, HO, HM};
+    fwd_problem P = {GH, KH, init_h, ent, MH, DO, C, HI, HO, HM, NULL, NULL};
+    if (region_mode) {  /* leaving the data region: live data made valid on the host */
+      P.is_exit_edge = rxe;
+      P.exit_gen = LV;
+    }
     if ((rc = forward_must(&g, &P))) goto done;
   }
   /* 7. emission */
@@ -663,6 +867,10 @@ int oracle_solve(const oracle_cfg *c, oracle_out *out) {
           TE[oe] = MD[ob] & ~DO[op] & HPO[op];
           FE[oe] = MH[ob] & ~HO[op] & DO[op];
           hedge |= MH[ob] & DO[op];
+        }
+        if (rxe[e]) {  /* the data region's exit: `from' for live data stale on the host */
+          FE[oe] |= LV[ob] & ~HO[op];
+          hedge |= LV[ob];
         }
         FE[oe] |= (LV[ob] & ~DI[ob] & ~HM[ob]) & ~hedge;
       }
@@ -701,11 +909,14 @@ int oracle_solve(const oracle_cfg *c, oracle_out *out) {
   CP(out->to_edge, TE, (size_t)E * W); CP(out->from_edge, FE, (size_t)E * W);
   CP(out->from_exit, FX, NW);
   CP(out->acc_flag, fl, (size_t)g.A);
+  CP(out->in_region, inr, (size_t)N);
+  CP(out->region_exit, rxe, (size_t)E);
 #undef CP
   rc = ORACLE_OK;
 done:
   for (int i = 0; i < 26; ++i) free(pl[i]);
-  free(hdr); free(ent); free(TE); free(FE); free(fl); free(init_h); free(init_d); free(xlive);
+  free(hdr); free(ent); free(inr); free(rxe); free(TE); free(FE); free(fl); free(init_h); free(init_d);
+  free(xlive);
   free_graph(&g);
   return rc;
 }

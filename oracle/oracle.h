@@ -60,6 +60,22 @@ typedef struct {
      has bit 31 set. */
   const uint64_t *call_planes;
   int32_t n_calls;
+  /* kernels (Sec. IV-B offloaded nodes): region[b] = id of the offload
+     kernel block b belongs to, or -1 for host code; NULL = no kernels. */
+  const int32_t *region;
+  /* nonzero: the single target data region of Sec. IV-D.  The region R is
+     the set of blocks b with S dom b, E pdom b and b != E, where S is the
+     nearest common dominator of the kernel blocks and the headers of every
+     natural loop whose body holds a kernel block ("begin before any loop
+     capturing the first kernel"), and E the nearest common post-dominator
+     of the blocks those kernel blocks and loop bodies lead to outside
+     themselves ("end after any loop capturing the last kernel";
+     post-dominance towards one virtual exit fed by every block without
+     successors; E is that virtual exit when there is no such block).  On every edge leaving R the
+     host copy of each variable live at its target is made valid ("if
+     stale data may be read on the host after exit from a target data
+     region, the from map-type is included"). */
+  int32_t data_region;
 } oracle_cfg;
 
 /* Every pointer is caller-allocated; any may be NULL (then not written).
@@ -82,6 +98,9 @@ typedef struct {
   uint64_t *call_to, *call_from;                 /* [S*W] transfers right before the call */
   uint64_t *call_entry_h, *call_entry_d;         /* [S*W] validity the callee starts from */
   uint64_t *call_exit_live;                      /* [S*W] Live (AntH | AntD) right after it */
+  /* data region (cfg->data_region with kernels; zero otherwise) */
+  uint8_t *in_region;                            /* [N] block in R                   */
+  uint8_t *region_exit;                          /* [E] edge from R to a block not in R */
 } oracle_out;
 
 int oracle_solve(const oracle_cfg *cfg, oracle_out *out);

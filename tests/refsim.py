@@ -270,6 +270,13 @@ class PathSim:
       'to_edge'  {edge: bitset}, 'from_edge' {edge: bitset},
       'flag'     {access index: 1 (to) | 2 (from)},
       'from_exit' {block: bitset}
+    and optionally
+      'pre'      {access index: [('to'|'from', var), ...]} made right
+                 before that access (before its own flag),
+      'start'    [('to'|'from', var), ...] made before the first block,
+      'edge_post' {edge: [('to'|'from', var), ...]} made on the edge after
+                 its 'to_edge' / 'from_edge' transfers (right before the
+                 block it enters)
     """
 
     def __init__(self, cfg, transfers, entry_h, entry_d, exit_live, hoist_edges=()):
@@ -319,6 +326,8 @@ class PathSim:
             evlog.append((pos[0], v, t, s))
             pos[0] += 1
 
+        for kind, v in self.t.get("start", ()):
+            xfer(kind, v, False)
         for i, b in enumerate(blocks):
             if i > 0:
                 e = edges[i - 1]
@@ -328,8 +337,12 @@ class PathSim:
                         xfer("to", v, hoist)
                     if (self.t["from_edge"].get(e, 0) >> v) & 1:
                         xfer("from", v, hoist)
+                for kind, v in self.t.get("edge_post", {}).get(e, ()):
+                    xfer(kind, v, False)
             base = int(self.cfg.acc_off[b])
             for j, (v, k, s) in enumerate(self.accs[b]):
+                for kind, u in self.t.get("pre", {}).get(base + j, ()):
+                    xfer(kind, u, False)
                 f = self.t["flag"].get(base + j, 0)
                 if f == 1:
                     xfer("to", v, False)
