@@ -419,6 +419,36 @@ def run_ours(args):
         }
     plan.close()
     if out is not None and world == 1 and args.sub_workloads:
+        # the same step with the data region and the directives (Table II,
+        # Sec. IV-D/IV-F): the classification's cost beside the analysis
+        rp = _native.Plan(g, device=local, chunk_target=args.chunk_target, data_region=True)
+        for _ in range(3):
+            rp.run(sh)
+            rp.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n_dr = max(3, min(args.steps, 10))
+        e0.record(stream)
+        for _ in range(n_dr):
+            rp.run(sh)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rp.sync()
+        rp.profile(True)
+        for _ in range(3):
+            rp.run(sh)
+            rp.sync()
+        tdr = rp.timings()
+        rv = rp.fetch()
+        rp.close()
+        out["directives"] = {
+            "ms_per_step": e0.elapsed_time(e1) / n_dr, "steps": n_dr,
+            "classify_ms_per_step": tdr.get("classify", (0, 0.0))[1] / 3,
+            "region_blocks": int(rv["in_region"].sum()), "kernels": int(rv["kernel_to"].shape[0]),
+            "map_to_vars": int(sum(bin(int(x)).count("1") for x in rv["map_to"])),
+            "map_from_vars": int(sum(bin(int(x)).count("1") for x in rv["map_from"])),
+            "map_alloc_vars": int(sum(bin(int(x)).count("1") for x in rv["map_alloc"])),
+            "mode": "opts.data_region: the single target data region's exit rule, then the classification pass"}
+        del rv
         # the metric's CFGs/s and p50/p99 part: the batch (10,000 CFGs) and
         # the serving streams, each beside its plain one-plan-per-CFG form
         sub = argparse.Namespace(**vars(args))

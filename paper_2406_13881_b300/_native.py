@@ -35,13 +35,14 @@ class Cfg(C.Structure):
                 ("succ_off", C.c_void_p), ("succ", C.c_void_p), ("acc_off", C.c_void_p),
                 ("acc", C.c_void_p), ("entry_host_valid", C.c_void_p),
                 ("entry_dev_valid", C.c_void_p), ("exit_host_live", C.c_void_p),
-                ("call_planes", C.c_void_p), ("n_calls", C.c_int32), ("mem", C.c_int32)]
+                ("call_planes", C.c_void_p), ("n_calls", C.c_int32), ("mem", C.c_int32),
+                ("region", C.c_void_p), ("scalar_vars", C.c_void_p)]
 
 
 class Opts(C.Structure):
     _fields_ = [("max_sweeps", C.c_int32), ("keep_states", C.c_int32), ("path", C.c_int32),
                 ("chunk_target", C.c_int32), ("device", C.c_int32), ("warps_per_cta", C.c_int32),
-                ("tune", C.c_int32), ("no_graph", C.c_int32)]
+                ("tune", C.c_int32), ("no_graph", C.c_int32), ("data_region", C.c_int32)]
 
 
 class EdgeXfer(C.Structure):
@@ -63,7 +64,13 @@ class Result(C.Structure):
                 ("sweeps", C.c_int32), ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64),
                 ("live_in", C.c_void_p), ("n_call_sites", C.c_int32), ("call_site_acc", C.c_void_p),
                 ("call_to", C.c_void_p), ("call_from", C.c_void_p), ("call_entry_h", C.c_void_p),
-                ("call_entry_d", C.c_void_p), ("call_exit_live", C.c_void_p), ("host_block", C.c_void_p)]
+                ("call_entry_d", C.c_void_p), ("call_exit_live", C.c_void_p),
+                ("in_region", C.c_void_p), ("map_to", C.c_void_p), ("map_from", C.c_void_p),
+                ("map_alloc", C.c_void_p), ("n_kernels", C.c_int32), ("kernel_to", C.c_void_p),
+                ("kernel_from", C.c_void_p), ("firstprivate", C.c_void_p), ("acc_point", C.c_void_p),
+                ("n_region_entries", C.c_int32), ("n_region_exits", C.c_int32),
+                ("region_entry_edges", C.c_void_p), ("region_exit_edges", C.c_void_p),
+                ("host_block", C.c_void_p)]
 
 
 class ServerOpts(C.Structure):
@@ -175,10 +182,12 @@ class DeviceCfg:
     that memory alive while the CFG is in use."""
 
     def __init__(self, n_blocks, n_vars, entry, succ_off, succ, acc_off, acc, entry_host_valid=None,
-                 entry_dev_valid=None, exit_host_live=None, call_planes=None, n_calls=0, owner=None):
+                 entry_dev_valid=None, exit_host_live=None, call_planes=None, n_calls=0, owner=None,
+                 region=None, scalar_vars=None):
         self.n_blocks, self.n_vars, self.entry = int(n_blocks), int(n_vars), int(entry)
         self.ptrs = (succ_off, succ, acc_off, acc, entry_host_valid, entry_dev_valid, exit_host_live, call_planes)
         self.n_calls = int(n_calls)
+        self.region, self.scalar_vars = region, scalar_vars
         self.owner = owner
 
     @property
@@ -194,7 +203,8 @@ class _Inputs:
         if isinstance(cfg, DeviceCfg):
             self.n, self.nv, self.W = cfg.n_blocks, cfg.n_vars, cfg.W
             self.dev = cfg
-            self.c = Cfg(cfg.n_blocks, cfg.n_vars, cfg.entry, *cfg.ptrs, cfg.n_calls, MEM_DEVICE)
+            self.c = Cfg(cfg.n_blocks, cfg.n_vars, cfg.entry, *cfg.ptrs, cfg.n_calls, MEM_DEVICE, cfg.region,
+                         cfg.scalar_vars)
             return
         g = cfg if isinstance(cfg, dict) else cfg.__dict__
         self.n, self.nv = int(g["n_blocks"]), int(g["n_vars"])
@@ -210,16 +220,20 @@ class _Inputs:
 
         self.ehv, self.edv, self.xhl = opt("entry_host_valid"), opt("entry_dev_valid"), opt("exit_host_live")
         self.calls = opt("call_planes")
+        self.scal = opt("scalar_vars")
+        reg = g.get("region")
+        self.reg = None if reg is None else np.ascontiguousarray(reg, dtype=np.int32)
         p = lambda a: None if a is None else a.ctypes.data  # noqa: E731
         self.c = Cfg(self.n, self.nv, int(g.get("entry", 0)), p(self.so), p(self.s), p(self.ao),
                      p(self.acc), p(self.ehv), p(self.edv), p(self.xhl), p(self.calls),
-                     0 if self.calls is None else int(self.calls.size // (7 * self.W)), MEM_HOST)
+                     0 if self.calls is None else int(self.calls.size // (7 * self.W)), MEM_HOST,
+                     p(self.reg), p(self.scal))
 
 
 def _opts(max_sweeps=0, keep_states=False, path=0, chunk_target=0, device=0, warps_per_cta=0, tune=False,
-          no_graph=False):
+          no_graph=False, data_region=False):
     return Opts(int(max_sweeps), int(bool(keep_states)), int(path), int(chunk_target), int(device),
-                int(warps_per_cta), int(bool(tune)), int(bool(no_graph)))
+                int(warps_per_cta), int(bool(tune)), int(bool(no_graph)), int(bool(data_region)))
 
 
 class _Owned:
@@ -278,6 +292,16 @@ def _result_to_numpy(r: Result, owner: "_Owned | None" = None) -> dict:
     out["call_site_acc"] = arr(r.call_site_acc, S, np.int32)
     for k in ("call_to", "call_from", "call_entry_h", "call_entry_d", "call_exit_live"):
         out[k] = arr(getattr(r, k), S * W, np.uint64, (S, W))
+    if r.in_region:  # data region and directives
+        K = r.n_kernels
+        out["in_region"] = arr(r.in_region, n, np.uint8)
+        for k in ("map_to", "map_from", "map_alloc"):
+            out[k] = arr(getattr(r, k), W, np.uint64)
+        for k in ("kernel_to", "kernel_from", "firstprivate"):
+            out[k] = arr(getattr(r, k), K * W, np.uint64, (K, W))
+        out["acc_point"] = arr(r.acc_point, r.n_acc, np.int32)
+        out["region_entry_edges"] = arr(r.region_entry_edges, r.n_region_entries, np.int32)
+        out["region_exit_edges"] = arr(r.region_exit_edges, r.n_region_exits, np.int32)
     return out
 
 

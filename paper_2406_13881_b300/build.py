@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libompdart.so")
 SOURCES = ["api.cu", "batch.cu", "sweep.cu", "scan.cu", "calls.cu", "summary.cu", "noalloc.cu", "ingest.cpp",
-           "server.cpp", "program.cpp", "hostmem.cpp", "staging.cpp"]
+           "server.cpp", "program.cpp", "hostmem.cpp", "staging.cpp", "classify.cu"]
 HEADERS = ["common.cuh", "plan.cuh", "ingest.h", "parallel.h", "solver.h", os.path.join("..", "..", "include", "ompdart.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

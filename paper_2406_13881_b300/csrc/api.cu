@@ -93,10 +93,107 @@ void boundary_rows(const ompdart_cfg *cfg, int W, std::vector<uint64_t> *top, st
   }
 }
 
+// Device arrays of the data-region mode (Ingest::region_mode): the
+// classification inputs, the boundary rows the emission fills and every
+// output of the directives (see classify.cu).
+int region_build(PlanCore *P, const int32_t *acc_off, int n_cfg, const std::vector<uint64_t> &fp, std::string *err) {
+  const Ingest &g = P->g;
+  DevPlan &d = P->dp;
+  const int W = g.W, N = g.N, A = g.A, nk = g.kern_off.back();
+  P->region = true;
+  std::vector<int32_t> blk_cfg(N), kern(N, -1), acc_blk(A), acc_base(n_cfg);
+  std::vector<uint8_t> has_r(n_cfg, 0);
+  for (int c = 0; c < n_cfg; ++c) {
+    acc_base[c] = acc_off[g.cfg_blk_off[c]];
+    for (int b = g.cfg_blk_off[c]; b < g.cfg_blk_off[c + 1]; ++b) {
+      blk_cfg[b] = c;
+      if (g.kernel[b] >= 0) kern[b] = g.kern_off[c] + g.kernel[b];
+      has_r[c] |= g.in_region[b];
+    }
+  }
+  parallel_ranges(N, 1 << 16, 8, [&](int, int lo, int hi) {
+    for (int b = lo; b < hi; ++b)
+      for (int i = acc_off[b]; i < acc_off[b + 1]; ++i) acc_blk[i] = b;
+  });
+  // boundary rows: entry edges, then exit edges; the in-edge (fin index) of each
+  const int n_rin = (int)g.rin_eid.size(), n_rout = (int)g.rout_eid.size();
+  std::vector<int32_t> fin_bnd(std::max(1, P->n_fin), -1);
+  for (int c = 0; c < n_cfg; ++c) {
+    std::vector<std::pair<int32_t, int32_t>> rows;  // (local edge id, row)
+    for (int r = g.rin_off[c]; r < g.rin_off[c + 1]; ++r) rows.push_back({g.rin_eid[r], r});
+    for (int r = g.rout_off[c]; r < g.rout_off[c + 1]; ++r) rows.push_back({g.rout_eid[r], n_rin + r});
+    if (rows.empty()) continue;
+    for (int i = g.cfg_pos_off[c]; i < g.cfg_pos_off[c + 1]; ++i)
+      for (int k = g.fin_off[i]; k < g.fin_off[i + 1]; ++k)
+        for (const auto &x : rows)
+          if (x.first == g.fin_eid[k]) fin_bnd[k] = x.second;
+  }
+  std::vector<int32_t> xin, xin_off(n_cfg + 1, 0), start_k(n_cfg, -1);
+  for (size_t x = 0; x < g.exit_blocks.size(); ++x) {
+    const int b = g.exit_blocks[x];
+    if (g.in_region[b]) {
+      xin.push_back((int32_t)x);
+      xin_off[blk_cfg[b] + 1]++;
+    }
+  }
+  for (int c = 0; c < n_cfg; ++c) {
+    xin_off[c + 1] += xin_off[c];
+    if (g.start_kernel[c] >= 0) start_k[c] = g.kern_off[c] + g.start_kernel[c];
+  }
+  std::vector<uint64_t> fp_rows = fp;
+  fp_rows.resize((size_t)nk * W, 0);
+  bool ok = true;
+  auto chk = [&](const void *q) { ok = ok && q != nullptr; };
+  ClsDev &c = P->cls;
+  c.A = A; c.W = W; c.n_cfg = n_cfg; c.n_k = nk; c.n_rin = n_rin;
+  c.acc = d.acc; c.acc_off = d.acc_off; c.pos = d.pos; c.acc_flag = d.acc_flag; c.from_exit = d.from_exit;
+  chk(c.acc_blk = P->upload(acc_blk));
+  chk(c.kern = P->upload(kern));
+  chk(c.blk_cfg = P->upload(blk_cfg));
+  chk(c.acc_base = P->upload(acc_base));
+  chk(c.kw_h = P->dalloc<uint64_t>((size_t)nk * W));
+  chk(c.kw_d = P->dalloc<uint64_t>((size_t)nk * W));
+  chk(c.kernel_to = P->dalloc<uint64_t>((size_t)nk * W));
+  chk(c.kernel_from = P->dalloc<uint64_t>((size_t)nk * W));
+  chk(c.dev_touched = P->dalloc<uint64_t>((size_t)n_cfg * W));
+  chk(c.acc_point = P->dalloc<int32_t>(A));
+  chk(c.rin_off = P->upload(g.rin_off));
+  chk(c.rout_off = P->upload(g.rout_off));
+  chk(c.xin_off = P->upload(xin_off));
+  chk(c.xin = P->upload(xin));
+  chk(c.has_r = P->upload(has_r));
+  chk(c.entry_in_r = P->upload(g.entry_in_region));
+  chk(c.start_k = P->upload(start_k));
+  uint64_t *bt = P->dalloc<uint64_t>((size_t)(n_rin + n_rout) * W), *bf = P->dalloc<uint64_t>((size_t)(n_rin + n_rout) * W);
+  chk(bt);
+  chk(bf);
+  c.bnd_to = d.bnd_to = bt;
+  c.bnd_from = d.bnd_from = bf;
+  chk(c.map_to = P->dalloc<uint64_t>((size_t)n_cfg * W));
+  chk(c.map_from = P->dalloc<uint64_t>((size_t)n_cfg * W));
+  chk(c.map_alloc = P->dalloc<uint64_t>((size_t)n_cfg * W));
+  chk(d.fin_bnd = P->upload(fin_bnd));
+  chk(d.ent_rx = P->upload(g.ent_rx));
+  chk(d.ent_dst = P->upload(g.ent_dst));
+  chk(P->d_in_region = P->upload(g.in_region));
+  chk(P->d_rin = P->upload(g.rin_eid));
+  chk(P->d_rout = P->upload(g.rout_eid));
+  chk(P->d_fp = P->upload(fp_rows));
+  if (!ok) {
+    *err = "device allocation failed";
+    return OMPDART_E_NOMEM;
+  }
+  P->h_kern_off = g.kern_off;
+  P->h_rin_off = g.rin_off;
+  P->h_rout_off = g.rout_off;
+  P->h_acc_base = acc_base;
+  return OMPDART_OK;
+}
+
 int core_build(PlanCore *P, const int32_t *acc_off, const uint32_t *acc, const CallHost &calls,
                const std::vector<uint64_t> &top, const std::vector<uint64_t> &eh, const std::vector<uint64_t> &ed,
                const std::vector<uint64_t> &xl, int n_cfg, const std::vector<int32_t> &unreach_cfg,
-               const ompdart_opts &o, std::string *err) {
+               const ompdart_opts &o, std::string *err, const std::vector<uint64_t> &fp) {
   TraceScope trace("core_build", P->g.M);
   const Ingest &g = P->g;
   P->keep_states = o.keep_states;
@@ -165,6 +262,11 @@ int core_build(PlanCore *P, const int32_t *acc_off, const uint32_t *acc, const C
   if (!ok) {
     *err = "device allocation failed";
     return OMPDART_E_NOMEM;
+  }
+  // ---- the data region and the directives
+  if (g.region_mode) {
+    const int rc = region_build(P, acc_off, n_cfg, fp, err);
+    if (rc) return rc;
   }
   // ---- call sites (Sec. IV-C): every call access; the reachable blocks holding them
   {
@@ -267,6 +369,7 @@ int core_enqueue(PlanCore *P, cudaStream_t s, Prof *pf) {
   else
     n += enqueue_scan_solver(P->scan, P->dp, s, pf) + enqueue_call_sites(P->dp, s, pf);
   n += enqueue_fill_unreachable(P->dp, s, P->keep_states, pf);
+  if (P->region) n += enqueue_classify(P->cls, s, pf);
   return n;
 }
 
@@ -331,6 +434,21 @@ void core_view(const PlanCore &P, const int32_t *h_status, ompdart_result *v) {
   v->call_entry_h = P.dp.call_entry_h;
   v->call_entry_d = P.dp.call_entry_d;
   v->call_exit_live = P.dp.call_exit_live;
+  if (P.region) {  // CFG 0 of the plan (a batch arena's views offset these per CFG)
+    v->in_region = P.d_in_region;
+    v->map_to = P.cls.map_to;
+    v->map_from = P.cls.map_from;
+    v->map_alloc = P.cls.map_alloc;
+    v->n_kernels = P.h_kern_off.size() > 1 ? P.h_kern_off[1] - P.h_kern_off[0] : 0;
+    v->kernel_to = P.cls.kernel_to;
+    v->kernel_from = P.cls.kernel_from;
+    v->firstprivate = P.d_fp;
+    v->acc_point = P.cls.acc_point;
+    v->n_region_entries = P.h_rin_off.size() > 1 ? P.h_rin_off[1] : 0;
+    v->n_region_exits = P.h_rout_off.size() > 1 ? P.h_rout_off[1] : 0;
+    v->region_entry_edges = P.d_rin;
+    v->region_exit_edges = P.d_rout;
+  }
 }
 
 int result_copy(const ompdart_result &v, bool pin, cudaStream_t s, ompdart_result **out) {
@@ -361,6 +479,16 @@ int result_copy(const ompdart_result &v, bool pin, cudaStream_t s, ompdart_resul
       {(void **)&r.call_entry_h, v.call_entry_h, 8 * SW},
       {(void **)&r.call_entry_d, v.call_entry_d, 8 * SW},
       {(void **)&r.call_exit_live, v.call_exit_live, 8 * SW},
+      {(void **)&r.in_region, v.in_region, v.in_region ? (size_t)v.n_blocks : 0},
+      {(void **)&r.map_to, v.map_to, v.map_to ? 8 * (size_t)v.n_words : 0},
+      {(void **)&r.map_from, v.map_from, v.map_from ? 8 * (size_t)v.n_words : 0},
+      {(void **)&r.map_alloc, v.map_alloc, v.map_alloc ? 8 * (size_t)v.n_words : 0},
+      {(void **)&r.kernel_to, v.kernel_to, v.kernel_to ? 8 * (size_t)v.n_kernels * v.n_words : 0},
+      {(void **)&r.kernel_from, v.kernel_from, v.kernel_from ? 8 * (size_t)v.n_kernels * v.n_words : 0},
+      {(void **)&r.firstprivate, v.firstprivate, v.firstprivate ? 8 * (size_t)v.n_kernels * v.n_words : 0},
+      {(void **)&r.acc_point, v.acc_point, v.acc_point ? 4 * (size_t)v.n_acc : 0},
+      {(void **)&r.region_entry_edges, v.region_entry_edges, v.region_entry_edges ? 4 * (size_t)v.n_region_entries : 0},
+      {(void **)&r.region_exit_edges, v.region_exit_edges, v.region_exit_edges ? 4 * (size_t)v.n_region_exits : 0},
   };
   size_t total = 0;
   for (const Part &p : parts) total += (p.bytes + 63) & ~size_t(63);
@@ -372,7 +500,12 @@ int result_copy(const ompdart_result &v, bool pin, cudaStream_t s, ompdart_resul
   for (const Part &p : parts) {
     // optional arrays stay NULL when absent; the others point into the
     // block even when empty
-    const bool optional = p.dst == (void **)&r.h_out || p.dst == (void **)&r.d_out || p.dst == (void **)&r.live_in;
+    const bool optional = p.dst == (void **)&r.h_out || p.dst == (void **)&r.d_out || p.dst == (void **)&r.live_in ||
+                          p.dst == (void **)&r.in_region || p.dst == (void **)&r.map_to ||
+                          p.dst == (void **)&r.map_from || p.dst == (void **)&r.map_alloc ||
+                          p.dst == (void **)&r.kernel_to || p.dst == (void **)&r.kernel_from ||
+                          p.dst == (void **)&r.firstprivate || p.dst == (void **)&r.acc_point ||
+                          p.dst == (void **)&r.region_entry_edges || p.dst == (void **)&r.region_exit_edges;
     if (optional && !p.src) {
       *p.dst = nullptr;
       continue;
@@ -451,9 +584,17 @@ int ompdart_plan_create(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdar
   if (!P) return set_err(OMPDART_E_NOMEM, "host allocation failed");
   std::string err;
   TraceScope trace("ingest", cfg ? cfg->n_blocks : 0);
-  int rc = ingest(cfg, &P->core.g, &err);
+  int rc = ingest(cfg, &P->core.g, &err, o.data_region != 0);
   trace.next("plan rows");
   if (rc) {
+    delete P;
+    return set_err(rc, err);
+  }
+  // firstprivate scalars (Sec. IV-D): their kernel reads analysed as host reads
+  ompdart_cfg fpc = *cfg;
+  std::vector<uint64_t> fp;
+  int n_kernels = 0;
+  if (o.data_region && (rc = firstprivate_view(*cfg, &staged, &fpc, &fp, &n_kernels, &err))) {
     delete P;
     return set_err(rc, err);
   }
@@ -476,7 +617,7 @@ int ompdart_plan_create(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdar
   CallHost calls;
   calls.planes = cfg->call_planes;
   calls.rows = cfg->call_planes ? cfg->n_calls : 0;
-  rc = core_build(&P->core, cfg->acc_off, cfg->acc, calls, top, eh, ed, xl, 1, {}, o, &err);
+  rc = core_build(&P->core, cfg->acc_off, fpc.acc, calls, top, eh, ed, xl, 1, {}, o, &err, fp);
   if (rc) {
     delete P;
     return set_err(rc, err);

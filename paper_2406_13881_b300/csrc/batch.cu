@@ -127,7 +127,8 @@ constexpr int kSide = 8;  // forked streams a run spreads its plans over
 
 // Lay the CFGs `members` (ingested in ing) out as one arena and upload it.
 int build_arena(Arena *a, const std::vector<int32_t> &members, const std::vector<const Ingest *> &ing,
-                const ompdart_cfg *cfgs, const ompdart_opts &o, std::string *err) {
+                const ompdart_cfg *cfgs, const ompdart_opts &o, std::string *err,
+                const std::vector<std::vector<uint64_t>> &fps) {
   a->members = members;
   std::vector<const Ingest *> parts;
   parts.reserve(members.size());
@@ -190,8 +191,11 @@ int build_arena(Arena *a, const std::vector<int32_t> &members, const std::vector
   oa.chunk_target = a->chunk_target;
   oa.warps_per_cta = a->wpc;
   calls.planes = table.empty() ? nullptr : table.data();
+  std::vector<uint64_t> fp;  // firstprivate rows of the members' kernels, in kernel order
+  if (!fps.empty())
+    for (int m : members) fp.insert(fp.end(), fps[m].begin(), fps[m].end());
   int rc = core_build(&a->core, acc_off.data(), acc.data(), calls, top, eh, ed, xl, (int)members.size(),
-                      unreach_cfg, oa, err);
+                      unreach_cfg, oa, err, fp);
   if (rc) return rc;
   const std::vector<int32_t> &co = a->core.g.chunk_off, &cp = a->core.g.cfg_pos_off;
   a->chunk_beg.resize(members.size() + 1);
@@ -231,7 +235,8 @@ double time_core(PlanCore *c, cudaStream_t s, int reps) {
 // best target, each candidate a trial arena over a sample of about 2^18
 // positions (every step-th CFG), timed on the device.
 void tune_arena(Arena *a, const std::vector<int32_t> &members, const std::vector<const Ingest *> &ing,
-                const ompdart_cfg *cfgs, const ompdart_opts &o, cudaStream_t s) {
+                const ompdart_cfg *cfgs, const ompdart_opts &o, cudaStream_t s,
+                const std::vector<std::vector<uint64_t>> &fps) {
   long long total = 0;
   for (int m : members) total += ing[m]->M;
   const std::pair<int, int> key(ing[members[0]]->W, ilog2(std::max<long long>(1, total)));
@@ -253,7 +258,7 @@ void tune_arena(Arena *a, const std::vector<int32_t> &members, const std::vector
     t.chunk_target = chunk;
     t.wpc = wpc;
     std::string err;
-    if (build_arena(&t, sample, ing, cfgs, o, &err)) return 1e30;
+    if (build_arena(&t, sample, ing, cfgs, o, &err, fps)) return 1e30;
     return time_core(&t.core, s, 3);
   };
   int best_chunk = 128, best_wpc = 4;
@@ -344,6 +349,23 @@ void arena_view(const Arena &a, int k, ompdart_result *v) {
   }
   v->h2d_bytes = a.core.h2d + scan_h2d_bytes(a.core.scan);
   v->d2h_bytes = 0;
+  const PlanCore &c = a.core;
+  if (c.region) {  // this member's slice of the arena's data-region outputs
+    const size_t kb = (size_t)c.h_kern_off[k] * W;
+    v->in_region = c.d_in_region + a.blk_off[k];
+    v->map_to = c.cls.map_to + (size_t)k * W;
+    v->map_from = c.cls.map_from + (size_t)k * W;
+    v->map_alloc = c.cls.map_alloc + (size_t)k * W;
+    v->n_kernels = c.h_kern_off[k + 1] - c.h_kern_off[k];
+    v->kernel_to = c.cls.kernel_to + kb;
+    v->kernel_from = c.cls.kernel_from + kb;
+    v->firstprivate = c.d_fp + kb;
+    v->acc_point = c.cls.acc_point + a.acc_base[k];
+    v->n_region_entries = c.h_rin_off[k + 1] - c.h_rin_off[k];
+    v->n_region_exits = c.h_rout_off[k + 1] - c.h_rout_off[k];
+    v->region_entry_edges = c.d_rin + c.h_rin_off[k];
+    v->region_exit_edges = c.d_rout + c.h_rout_off[k];
+  }
 }
 
 }  // namespace
@@ -378,11 +400,15 @@ int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts 
   TraceScope trace_ingest("batch ingest", n);
   std::vector<int32_t> canon(n);
   {
-    std::map<std::tuple<const void *, const void *, const void *, const void *, int, int, int>, int32_t> first;
+    std::map<std::tuple<const void *, const void *, const void *, const void *, const void *, const void *, int, int,
+                        int>,
+             int32_t>
+        first;
     for (int i = 0; i < n; ++i) {
       const ompdart_cfg &c = cfgs[i];
       canon[i] = first.emplace(std::make_tuple((const void *)c.succ_off, (const void *)c.succ, (const void *)c.acc_off,
-                                               (const void *)c.acc, c.n_blocks, c.n_vars, c.entry),
+                                               (const void *)c.acc, (const void *)c.region,
+                                               (const void *)c.scalar_vars, c.n_blocks, c.n_vars, c.entry),
                                i)
                      .first->second;
     }
@@ -398,7 +424,7 @@ int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts 
       for (int i = next++; i < n; i = next++) {
         if (canon[i] != i) continue;
         std::string e;
-        int rc = ingest(&cfgs[i], &ing[i], &e);
+        int rc = ingest(&cfgs[i], &ing[i], &e, o.data_region != 0);
         B->ingest_status[i] = rc;
       }
     };
@@ -411,6 +437,31 @@ int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts 
     for (int i = 0; i < n; ++i) B->ingest_status[i] = B->ingest_status[canon[i]];
     for (int i = 0; i < (int)staged.rc.size(); ++i)
       if (staged.rc[i]) B->ingest_status[i] = staged.rc[i];
+  }
+  // ---- firstprivate scalars (data-region mode): each ingested CFG's kernel
+  // reads of read-only scalars analysed as host reads (a copy of the
+  // access array; CFGs sharing arrays share the copy)
+  std::vector<ompdart_cfg> fcfgs;
+  std::vector<std::vector<uint64_t>> fps;
+  StagedCfgs fp_bufs;
+  if (o.data_region) {
+    fcfgs.assign(cfgs, cfgs + n);
+    fps.resize(n);
+    for (int i = 0; i < n; ++i) {
+      if (B->ingest_status[i]) continue;
+      if (canon[i] != i) {
+        fcfgs[i].acc = fcfgs[canon[i]].acc;
+        fps[i] = fps[canon[i]];
+        continue;
+      }
+      int nk = 0;
+      std::string e;
+      const int rc = firstprivate_view(cfgs[i], &fp_bufs, &fcfgs[i], &fps[i], &nk, &e);
+      if (rc) B->ingest_status[i] = rc;
+    }
+    for (int i = 0; i < n; ++i)
+      if (canon[i] != i && B->ingest_status[canon[i]]) B->ingest_status[i] = B->ingest_status[canon[i]];
+    cfgs = fcfgs.data();
   }
   trace_ingest.next("batch arenas", n);
   // ---- grouping
@@ -434,7 +485,7 @@ int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts 
     if (!built[g]) return set_error(OMPDART_E_NOMEM, "host allocation failed");
     built[g]->chunk_target = o.chunk_target;
     built[g]->wpc = o.warps_per_cta;
-    if (o.tune) tune_arena(built[g].get(), groups[g].second, ingp, cfgs, o, B->stream);
+    if (o.tune) tune_arena(built[g].get(), groups[g].second, ingp, cfgs, o, B->stream, fps);
   }
   {
     std::vector<int> rcs(n_ar, OMPDART_OK);
@@ -449,7 +500,7 @@ int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts 
         return;
       }
       for (int g = next++; g < n_ar; g = next++)
-        rcs[g] = build_arena(built[g].get(), groups[g].second, ingp, cfgs, o, &errs[g]);
+        rcs[g] = build_arena(built[g].get(), groups[g].second, ingp, cfgs, o, &errs[g], fps);
     };
     // small batches (a serving turn) are built on the calling thread: a
     // thread of its own costs more than such an arena's build
@@ -486,7 +537,8 @@ int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts 
     CallHost calls;
     calls.planes = cfgs[i].call_planes;
     calls.rows = cfgs[i].call_planes ? cfgs[i].n_calls : 0;
-    int rc = core_build(&p->core, cfgs[i].acc_off, cfgs[i].acc, calls, top, eh, ed, xl, 1, {}, os, &err);
+    int rc = core_build(&p->core, cfgs[i].acc_off, cfgs[i].acc, calls, top, eh, ed, xl, 1, {}, os, &err,
+                        fps.empty() ? std::vector<uint64_t>() : fps[i]);
     if (rc == OMPDART_E_INVALID) {  // this CFG alone (calls without the scan solver)
       B->ingest_status[i] = rc;
       B->where[i] = Where{};

@@ -176,10 +176,166 @@ void lengauer_tarjan(int N, int entry, const std::vector<int32_t> &so, const int
   *preorder_out = std::move(vert);
 }
 
+// The single target data region (see ingest.h) of one ingested CFG:
+// in_region, kernel ids, the region's entry and exit edges, the kernel whose
+// entry opens it, and the exit edges added to the edge constants (eid_ent
+// updated for the new ones).
+template <class Dom>
+void find_data_region(const ompdart_cfg *c, Ingest *g, const std::vector<int32_t> &so, const int32_t *succ,
+                      const std::vector<int32_t> &po, const std::vector<int32_t> &psrc,
+                      const std::vector<int32_t> &peid, const std::vector<uint8_t> &reach,
+                      const std::vector<int32_t> &pre, const std::vector<int32_t> &dfn,
+                      const std::vector<int32_t> &idom, Dom dominates, std::vector<int32_t> *eid_ent) {
+  const int N = g->N;
+  g->region_mode = true;
+  g->kernel.assign(c->region, c->region + N);
+  int nk = 0;
+  for (int b = 0; b < N; ++b) nk = std::max(nk, c->region[b] + 1);
+  g->kern_off = {0, nk};
+  g->in_region.assign(N, 0);
+  g->start_kernel = {kNone};
+  g->entry_in_region = {0};
+  g->rin_off = {0, 0};
+  g->rout_off = {0, 0};
+  // kernel blocks (cap 1) and bodies of loops holding one (cap 2), their headers
+  std::vector<uint8_t> cap(N, 0), hcap(N, 0);
+  bool any = false;
+  for (int b = 0; b < N; ++b)
+    if (reach[b] && c->region[b] >= 0) cap[b] = 1, any = true;
+  if (!any) return;
+  for (int l = 0; l < g->L; ++l) {
+    bool holds = false;
+    for (int x = g->body_off[l]; x < g->body_off[l + 1] && !holds; ++x) holds = c->region[g->body_blk[x]] >= 0;
+    if (!holds) continue;
+    hcap[g->loop_head[l]] = 1;
+    for (int x = g->body_off[l]; x < g->body_off[l + 1]; ++x) cap[g->body_blk[x]] |= 2;
+  }
+  // S: meet of the kernel blocks and capturing headers in the dominator
+  // tree (DFS numbers: an immediate dominator has a smaller one)
+  auto meet = [](int a, int b, const std::vector<int32_t> &par) {
+    while (a != b) {
+      if (a > b) a = par[a];
+      else b = par[b];
+    }
+    return a;
+  };
+  int S = kNone;
+  for (int b = 0; b < N; ++b)
+    if ((cap[b] & 1) || hcap[b]) S = S == kNone ? dfn[b] : meet(S, dfn[b], idom);
+  S = pre[S];
+  // post-dominators: Lengauer-Tarjan on the reversed graph rooted at a
+  // virtual exit X = N whose successors are the exit blocks; a block's
+  // successors there are its reachable predecessors
+  const int X = N;
+  std::vector<int32_t> so2(N + 2, 0), su2, po2(N + 2, 0), ps2;
+  for (int b = 0; b < N; ++b) {
+    int n = 0;
+    for (int k = po[b]; k < po[b + 1]; ++k) n += reach[psrc[k]];
+    so2[b + 1] = n;
+  }
+  for (int b = 0; b < N; ++b) so2[X + 1] += reach[b] && so[b] == so[b + 1];
+  for (int b = 0; b <= N; ++b) so2[b + 1] += so2[b];
+  su2.resize(so2[N + 1]);
+  for (int b = 0, x = 0; b < N; ++b)
+    for (int k = po[b]; k < po[b + 1]; ++k)
+      if (reach[psrc[k]]) su2[x++] = psrc[k];
+  for (int b = 0, x = so2[X]; b < N; ++b)
+    if (reach[b] && so[b] == so[b + 1]) su2[x++] = b;
+  // predecessors in the reversed graph: the forward successors, and X for an exit
+  for (int b = 0; b < N; ++b) po2[b + 1] = reach[b] ? (so[b + 1] - so[b]) + (so[b] == so[b + 1]) : 0;
+  for (int b = 0; b <= N; ++b) po2[b + 1] += po2[b];
+  ps2.resize(po2[N + 1]);
+  for (int b = 0; b < N; ++b) {
+    if (!reach[b]) continue;
+    int x = po2[b];
+    for (int e = so[b]; e < so[b + 1]; ++e) ps2[x++] = succ[e];
+    if (so[b] == so[b + 1]) ps2[x++] = X;
+  }
+  std::vector<int32_t> pre2, dfn2, ipd;
+  lengauer_tarjan(N + 1, X, so2, su2.data(), po2, ps2, &pre2, &dfn2, &ipd);
+  const int n2 = (int)pre2.size();
+  std::vector<int32_t> sz2(n2, 1), tin2(n2, 0), nxt2(n2, 0);
+  for (int w = n2 - 1; w >= 1; --w) sz2[ipd[w]] += sz2[w];
+  nxt2[0] = 1;
+  for (int w = 1; w < n2; ++w) {
+    tin2[w] = nxt2[ipd[w]];
+    nxt2[ipd[w]] += sz2[w];
+    nxt2[w] = tin2[w] + 1;
+  }
+  // E: meet, in the post-dominator tree, of the blocks the captured blocks lead to outside themselves
+  int E = kNone;
+  bool to_x = false;
+  for (int b = 0; b < N; ++b) {
+    if (!cap[b]) continue;
+    for (int e = so[b]; e < so[b + 1]; ++e) {
+      const int t = succ[e];
+      if (cap[t]) continue;
+      if (dfn2[t] == kNone) to_x = true;
+      else E = E == kNone ? dfn2[t] : meet(E, dfn2[t], ipd);
+    }
+  }
+  if (to_x || E == kNone) E = 0;  // the virtual exit (DFS number 0)
+  const int Eb = pre2[E];         // X when the region runs to the virtual exit
+  for (int b = 0; b < N; ++b) {
+    if (!reach[b] || b == Eb || !dominates(S, b)) continue;
+    const int d = dfn2[b];
+    if (E != 0 && (d == kNone || !(tin2[E] <= tin2[d] && tin2[d] < tin2[E] + sz2[E]))) continue;
+    g->in_region[b] = 1;
+  }
+  // boundary edges; the exit edges join the edge constants
+  for (int b = 0; b < N; ++b) {
+    if (!reach[b]) continue;
+    for (int e = so[b]; e < so[b + 1]; ++e) {
+      const int t = succ[e];
+      if (!g->in_region[b] && g->in_region[t]) g->rin_eid.push_back(e);
+      if (g->in_region[b] && !g->in_region[t]) g->rout_eid.push_back(e);
+    }
+  }
+  g->rin_off = {0, (int32_t)g->rin_eid.size()};
+  g->rout_off = {0, (int32_t)g->rout_eid.size()};
+  g->entry_in_region = {g->in_region[c->entry]};
+  for (int e : g->rout_eid) {
+    int &k = (*eid_ent)[e];
+    if (k == kNone) {
+      k = g->K++;
+      g->ent_loop.push_back(kNone);
+      g->ent_src.push_back((int32_t)(std::upper_bound(so.begin(), so.end(), e) - so.begin()) - 1);
+      g->ent_eid.push_back(e);
+      g->ent_rx.push_back(1);
+    } else {
+      g->ent_rx[k] = 1;
+    }
+  }
+  // the kernel whose entry edges are exactly the region's entry edges (and
+  // that holds the CFG's entry iff the region starts there) opens the region
+  std::vector<int32_t> rin = g->rin_eid;
+  std::sort(rin.begin(), rin.end());
+  for (int k = 0; k < nk; ++k) {
+    std::vector<int32_t> ke;
+    for (int t = 0; t < N; ++t) {
+      if (!reach[t] || c->region[t] != k) continue;
+      for (int q = po[t]; q < po[t + 1]; ++q)
+        if (reach[psrc[q]] && c->region[psrc[q]] != k) ke.push_back(peid[q]);
+    }
+    std::sort(ke.begin(), ke.end());
+    const bool holds_entry = c->region[c->entry] == k;
+    if (ke == rin && (bool)g->entry_in_region[0] == holds_entry && (holds_entry || !rin.empty())) {
+      g->start_kernel[0] = k;
+      break;
+    }
+  }
+}
+
 }  // namespace
 
-int ingest(const ompdart_cfg *c, Ingest *g, std::string *err) {
+int ingest(const ompdart_cfg *c, Ingest *g, std::string *err, bool data_region) {
   if (!check_format(c, err)) return OMPDART_E_INVALID;
+  if (data_region && c->region &&
+      first_bad(c->n_blocks, [&](int b) { return c->region[b] < -1 || c->region[b] >= c->n_blocks; }) <
+          c->n_blocks) {
+    if (err) *err = "kernel ids (region) must be -1 or in [0, n_blocks)";
+    return OMPDART_E_INVALID;
+  }
   const int N = c->n_blocks;
   g->N = N;
   g->E = c->succ_off[N];
@@ -448,6 +604,12 @@ int ingest(const ompdart_cfg *c, Ingest *g, std::string *err) {
     }
   });
 
+  g->ent_rx.assign(g->K, 0);
+  if (data_region && c->region) find_data_region(c, g, so, succ, po, psrc, peid, reach, pre, dfn, idom, dominates,
+                                                 &eid_ent);
+  g->ent_dst.resize(g->K);
+  for (int k = 0; k < g->K; ++k) g->ent_dst[k] = succ[g->ent_eid[k]];
+
   // position-ordered edge lists (counted, then filled, in parallel over positions)
   g->fin_off.assign(M + 1, 0);
   g->out_off.assign(M + 1, 0);
@@ -490,6 +652,7 @@ int ingest(const ompdart_cfg *c, Ingest *g, std::string *err) {
   g->chunk_off.assign({0, M});
   g->max_chunk = M;
   g->cfg_pos_off.assign({0, M});
+  g->cfg_blk_off.assign({0, N});
   return OMPDART_OK;
 }
 
@@ -538,7 +701,32 @@ void concat_ingests(const std::vector<const Ingest *> &parts, Ingest *o) {
   o->ent_loop.resize(t.k);
   o->ent_src.resize(t.k);
   o->ent_eid.resize(t.k);
+  o->ent_dst.resize(t.k);
+  o->ent_rx.resize(t.k);
   o->cfg_pos_off.resize(P + 1);
+  o->cfg_blk_off.resize(P + 1);
+  for (int q = 0; q <= P; ++q) o->cfg_blk_off[q] = (int32_t)off[q].n;
+  // region mode: per-CFG regions laid end to end (a part without kernels
+  // or without the mode contributes an empty region)
+  for (int q = 0; q < P; ++q) o->region_mode = o->region_mode || parts[q]->region_mode;
+  std::vector<int32_t> kern_base(P + 1, 0), rin_base(P + 1, 0), rout_base(P + 1, 0);
+  if (o->region_mode) {
+    for (int q = 0; q < P; ++q) {
+      const Ingest *g = parts[q];
+      kern_base[q + 1] = kern_base[q] + (g->region_mode ? g->kern_off.back() : 0);
+      rin_base[q + 1] = rin_base[q] + (int32_t)g->rin_eid.size();
+      rout_base[q + 1] = rout_base[q] + (int32_t)g->rout_eid.size();
+    }
+    o->in_region.assign(t.n, 0);
+    o->kernel.assign(t.n, -1);
+    o->kern_off = kern_base;
+    o->rin_eid.resize(rin_base[P]);
+    o->rout_eid.resize(rout_base[P]);
+    o->rin_off = rin_base;
+    o->rout_off = rout_base;
+    o->start_kernel.assign(P, -1);
+    o->entry_in_region.assign(P, 0);
+  }
   o->fin_off[t.m] = (int32_t)t.fin;
   o->out_off[t.m] = (int32_t)t.out;
   o->body_off[t.l] = (int32_t)t.body;
@@ -575,9 +763,19 @@ void concat_ingests(const std::vector<const Ingest *> &parts, Ingest *o) {
       }
       for (size_t k = 0; k < g->body_blk.size(); ++k) o->body_blk[f.body + k] = g->body_blk[k] + bo;
       for (int k = 0; k < g->K; ++k) {
-        o->ent_loop[ko + k] = g->ent_loop[k] + lo;
+        o->ent_loop[ko + k] = g->ent_loop[k] < 0 ? -1 : g->ent_loop[k] + lo;
         o->ent_src[ko + k] = g->ent_src[k] + bo;
         o->ent_eid[ko + k] = g->ent_eid[k] + eo;
+        o->ent_dst[ko + k] = g->ent_dst[k] + bo;
+        o->ent_rx[ko + k] = g->ent_rx[k];
+      }
+      if (o->region_mode && g->region_mode) {
+        std::copy(g->in_region.begin(), g->in_region.end(), o->in_region.begin() + bo);
+        std::copy(g->kernel.begin(), g->kernel.end(), o->kernel.begin() + bo);
+        std::copy(g->rin_eid.begin(), g->rin_eid.end(), o->rin_eid.begin() + rin_base[q]);
+        std::copy(g->rout_eid.begin(), g->rout_eid.end(), o->rout_eid.begin() + rout_base[q]);
+        o->start_kernel[q] = g->start_kernel[0];
+        o->entry_in_region[q] = g->entry_in_region[0];
       }
     }
   });

@@ -43,9 +43,23 @@ struct Ingest {
   std::vector<int32_t> body_blk;    // blocks of each body, ascending position
   std::vector<int32_t> inner_loop;  // [N] innermost loop of each block or -1
   std::vector<int32_t> loop_end;    // [L] one past the last body position (contiguous order)
-  // loop-entry edges p->h (h header, p outside body(h)), reachable p only
+  // edges with constants: loop-entry edges p->h (h header, p outside
+  // body(h)), reachable p only, then (region mode) the edges leaving the
+  // data region that are not loop-entry edges (ent_loop -1)
   int K = 0;
   std::vector<int32_t> ent_loop, ent_src, ent_eid;
+  std::vector<int32_t> ent_dst;     // [K] target block
+  std::vector<uint8_t> ent_rx;      // [K] the edge leaves the data region
+  // ---- the single target data region of each CFG (Sec. IV-D; region
+  // mode only, see ingest()): per-CFG lists are concatenated for a batch
+  bool region_mode = false;
+  std::vector<uint8_t> in_region;   // [N] block in its CFG's region
+  std::vector<int32_t> kernel;      // [N] kernel id (local to its CFG) or -1
+  std::vector<int32_t> kern_off;    // [n_cfg+1] kernels of CFG c: kern_off[c] + local id
+  std::vector<int32_t> rin_eid, rout_eid;  // edges entering / leaving a region (edge ids local to the CFG)
+  std::vector<int32_t> rin_off, rout_off;  // [n_cfg+1]
+  std::vector<int32_t> start_kernel;       // [n_cfg] local kernel id whose entry opens the region, or -1
+  std::vector<uint8_t> entry_in_region;    // [n_cfg] the region starts at the CFG's entry
   bool reducible = true;            // every retreating edge is a back edge
   bool contiguous = true;           // every loop body is a run of positions
   // chunks of the order for the scan solver: chunk c = positions
@@ -53,8 +67,10 @@ struct Ingest {
   std::vector<int32_t> chunk_off;
   int max_chunk = 0;
   // a batch of independent CFGs laid end to end: CFG k owns positions
-  // [cfg_pos_off[k], cfg_pos_off[k+1]) (one CFG: {0, M})
+  // [cfg_pos_off[k], cfg_pos_off[k+1]) (one CFG: {0, M}) and blocks
+  // [cfg_blk_off[k], cfg_blk_off[k+1]) (one CFG: {0, N})
   std::vector<int32_t> cfg_pos_off;
+  std::vector<int32_t> cfg_blk_off;
 };
 
 // Lay independent ingested CFGs end to end: block, position, loop and
@@ -64,7 +80,15 @@ struct Ingest {
 void concat_ingests(const std::vector<const Ingest *> &parts, Ingest *out);
 
 // Returns OMPDART_OK or OMPDART_E_INVALID (message in *err).
-int ingest(const ompdart_cfg *cfg, Ingest *g, std::string *err);
+// data_region (with cfg->region): also the single target data region of
+// Sec. IV-D.  Its blocks are those b with S dom b, E pdom b and b != E:
+// S is the nearest common dominator of the kernel blocks and of the
+// headers of the natural loops whose body holds a kernel block, E the
+// nearest common post-dominator (towards one virtual exit fed by every
+// block without successors) of the blocks those kernel blocks and loop
+// bodies lead to outside themselves, or the virtual exit if there is none.
+// The edges leaving the region join the edge constants (ent_rx).
+int ingest(const ompdart_cfg *cfg, Ingest *g, std::string *err, bool data_region = false);
 
 // Build chunks of about `target` positions at single-entry cut points.
 void make_chunks(Ingest *g, int target);

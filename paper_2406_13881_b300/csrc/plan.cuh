@@ -58,8 +58,14 @@ struct DevPlan {
   const int32_t *loop_head;  // [L]
   const int32_t *body_off;   // [L+1]
   const int32_t *body_blk;   // blocks of each body, ascending position
-  const int32_t *ent_loop;   // [K]
+  const int32_t *ent_loop;   // [K] loop of a loop-entry edge, -1 for a region-exit-only edge
   const int32_t *ent_src;    // [K]
+  const uint8_t *ent_rx;     // [K] the edge leaves the data region, or null (no region)
+  const int32_t *ent_dst;    // [K] target block
+  // data region: boundary row of each in-edge (fin index) or -1, and the
+  // transfers the emission leaves on those edges ([rows][W]); null without
+  const int32_t *fin_bnd;
+  uint64_t *bnd_to, *bnd_from;
   // boundary conditions and valid-variable masks, [n_cfg][W] each
   const uint64_t *entry_h, *entry_d, *exit_live, *top;
   // state planes [N*W]

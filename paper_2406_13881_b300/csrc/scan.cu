@@ -1594,11 +1594,13 @@ __global__ void __launch_bounds__(256) k_resolve(DevPlan p, ScanDev sd, const ui
   }
 }
 
-// The same for the out values at loop-entry sources ([K][W]), as valid
-// sets, and the edge constants they decide (Sec. IV-D hoisting) in the same
-// pass: which = 0, plain host validity: ec_d = mask_d & Hp (the value itself
-// is not kept); which = 1, device validity: d_src (the emission reads it)
-// and ec_h = mask_h & D.
+// The same for the out values at the sources of the edges with constants
+// ([K][W]), as valid sets, and the constants they decide (Sec. IV-D) in the
+// same pass: which = 0, plain host validity: ec_d = mask_d & Hp on a
+// loop-entry edge (the value itself is not kept); which = 1, device
+// validity: d_src (the emission reads it) and ec_h = mask_h & D on a
+// loop-entry edge, plus, on an edge leaving the data region, what is live
+// at its target (made valid on the host there).
 __global__ void k_resolve_src(DevPlan p, ScanDev sd, int which) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const int W = p.W;
@@ -1609,12 +1611,14 @@ __global__ void k_resolve_src(DevPlan p, ScanDev sd, int which) {
   const int l = sd.pos_loop[i];
   if (l >= 0) compose_pair(g, q, sd.hdr_ag[(size_t)l * W + w], sd.hdr_ap[(size_t)l * W + w]);
   const uint64_t x = ~(g | (sd.carry[(size_t)c * W + w] & q)) & p.top[(size_t)sd.chunks[c].cfg * W + w];
-  const size_t le = (size_t)p.ent_loop[k] * W + w;
+  const int le = p.ent_loop[k];
   if (which == 0) {
-    p.ec_d[t] = p.mask_d[le] & x;
+    p.ec_d[t] = le >= 0 ? p.mask_d[(size_t)le * W + w] & x : 0ull;
   } else {
     sd.d_src[t] = x;
-    p.ec_h[t] = p.mask_h[le] & x;
+    uint64_t h = le >= 0 ? p.mask_h[(size_t)le * W + w] & x : 0ull;
+    if (p.ent_rx && p.ent_rx[k]) h |= p.live[(size_t)p.ent_dst[k] * W + w];
+    p.ec_h[t] = h;
   }
 }
 
@@ -1685,8 +1689,15 @@ __global__ void __launch_bounds__(32 * EMIT_WARPS, OMPDART_EMIT_MIN_CTAS)
       const uint64_t e0 = s0 & ~m0, e1 = s1 & ~m1;
       z0 |= e0;
       z1 |= e1;
-      push_edge_records(sd, stream, rec_count, p.fin_eid[k], w0, to0, (m0 & s0) | (c0 & e0), to1,
-                        (m1 & s1) | (c1 & e1), lane);
+      const uint64_t fr0 = (m0 & s0) | (c0 & e0), fr1 = (m1 & s1) | (c1 & e1);
+      if (p.fin_bnd) {  // an edge on the data region's boundary: its row for the map clauses
+        const int bi = p.fin_bnd[k];
+        if (bi >= 0) {
+          st_pair(p.bnd_to, bi, W, w0, to0, to1);
+          st_pair(p.bnd_from, bi, W, w0, fr0, fr1);
+        }
+      }
+      push_edge_records(sd, stream, rec_count, p.fin_eid[k], w0, to0, fr0, to1, fr1, lane);
     }
     z0 &= ~c0;
     z1 &= ~c1;
@@ -2630,12 +2641,12 @@ int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *p
   if (sq.pair_g2) {
     k_resolve<RV_VALID><<<grid_of((nw + 1) / 2, 256), 256, 0, s>>>(p, sq, sq.pair_g2, sq.pair_p2, p.d_out); ++n;
   }
+  // ---- host validity (its exit states), then the emission
+  if (fork) cudaStreamWaitEvent(s, st->ev[2], 0);  // liveness (also in the constants of region exits)
   if (p.K) {
     PROF("src_resolve");
     k_resolve_src<<<grid_of(kw, 256), 256, 0, s>>>(p, sq, 1); ++n;
   }
-  // ---- host validity (its exit states), then the emission
-  if (fork) cudaStreamWaitEvent(s, st->ev[2], 0);  // liveness
   PROF("entry_stale");
   k_entry_stale<<<grid_of((long long)W * p.n_cfg, 128), 128, 0, s>>>(p.entry_h, p.top, init, W, p.n_cfg); ++n;
   PROF("h_summary");

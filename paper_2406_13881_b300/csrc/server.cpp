@@ -42,7 +42,8 @@ struct Request {
   int64_t id = 0;
   std::vector<int32_t> so, su, ao;
   std::vector<uint32_t> acc;
-  std::vector<uint64_t> eh, ed, xl, calls;
+  std::vector<uint64_t> eh, ed, xl, calls, scalars;
+  std::vector<int32_t> region;
   ompdart_cfg cfg{};
   long long est = 0;
   Clock::time_point t_submit, t_done;
@@ -266,6 +267,8 @@ int ompdart_server_submit(ompdart_server *S, const ompdart_cfg *c, int64_t *tick
   if (c->entry_dev_valid) r->ed.assign(c->entry_dev_valid, c->entry_dev_valid + W);
   if (c->exit_host_live) r->xl.assign(c->exit_host_live, c->exit_host_live + W);
   if (c->call_planes && c->n_calls > 0) r->calls.assign(c->call_planes, c->call_planes + (size_t)c->n_calls * 7 * W);
+  if (c->region) r->region.assign(c->region, c->region + N);
+  if (c->scalar_vars) r->scalars.assign(c->scalar_vars, c->scalar_vars + W);
   r->cfg = *c;
   r->cfg.succ_off = r->so.data();
   r->cfg.succ = r->su.data();
@@ -275,6 +278,8 @@ int ompdart_server_submit(ompdart_server *S, const ompdart_cfg *c, int64_t *tick
   r->cfg.entry_dev_valid = c->entry_dev_valid ? r->ed.data() : nullptr;
   r->cfg.exit_host_live = c->exit_host_live ? r->xl.data() : nullptr;
   r->cfg.call_planes = r->calls.empty() ? nullptr : r->calls.data();
+  r->cfg.region = c->region ? r->region.data() : nullptr;
+  r->cfg.scalar_vars = c->scalar_vars ? r->scalars.data() : nullptr;
   r->est = estimate_device_bytes(r->cfg, S->o.opts.keep_states);
   std::lock_guard<std::mutex> lk(S->mu);
   if (S->stop) return set_error(OMPDART_E_INVALID, "server is shutting down");

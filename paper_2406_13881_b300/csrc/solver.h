@@ -106,6 +106,42 @@ bool scan_chunk_record_offsets(const ScanState *st, cudaStream_t s, std::vector<
 long long scan_device_bytes(const ScanState *st);
 void scan_destroy(ScanState *st);
 
+// ---- classify.cu: directive classification of the data-region mode
+// (device arrays of one plan; per-CFG arrays indexed by the CFG of a batch)
+struct ClsDev {
+  long long A;
+  int W, n_cfg, n_k, n_rin;
+  const uint32_t *acc;       // [A] the accesses the analysis read
+  const int32_t *acc_off;    // [N+1]
+  const int32_t *acc_blk;    // [A] block of each access
+  const int32_t *pos;        // [N] position or -1 (unreachable)
+  const int32_t *kern;       // [N] plan-wide kernel index or -1
+  const int32_t *blk_cfg;    // [N] CFG of each block
+  const int32_t *acc_base;   // [n_cfg] first access of each CFG
+  const uint8_t *acc_flag;   // [A]
+  uint64_t *kw_h, *kw_d;     // [n_k][W] written by kernel k on the host / device (scratch)
+  uint64_t *kernel_to, *kernel_from;  // [n_k][W]
+  uint64_t *dev_touched;     // [n_cfg][W] (scratch)
+  int32_t *acc_point;        // [A] insertion point (index local to the CFG) or -1
+  const int32_t *rin_off, *rout_off;  // [n_cfg+1] boundary rows: entry rows, then n_rin + exit rows
+  const int32_t *xin_off, *xin;       // [n_cfg+1], exit indices of the exits inside the region
+  const uint8_t *has_r, *entry_in_r;  // [n_cfg]
+  const int32_t *start_k;    // [n_cfg] kernel whose entry opens the region, or -1
+  const uint64_t *bnd_to, *bnd_from, *from_exit;
+  uint64_t *map_to, *map_from, *map_alloc;  // [n_cfg][W]
+};
+int enqueue_classify(const ClsDev &c, cudaStream_t s, Prof *pf);
+
+// ---- staging.cpp: firstprivate (Sec. IV-D, scalar paragraph).  With
+// cfg.region and cfg.scalar_vars: the device reads of a scalar that a kernel
+// reads and never writes are relabelled as host reads in a copy of the
+// access array kept in *st (*out points at it); fp receives the
+// [n_kernels * W] firstprivate rows, *n_kernels = max kernel id + 1 (0
+// without region).  Returns OMPDART_E_INVALID for a kernel id outside
+// [-1, n_blocks).  The CFG must have passed ingestion's format checks.
+int firstprivate_view(const ompdart_cfg &in, StagedCfgs *st, ompdart_cfg *out, std::vector<uint64_t> *fp,
+                      int *n_kernels, std::string *err);
+
 // ---- api.cu: one device plan over one CFG or a batch of CFGs of equal
 // word count (shared by the single-CFG plan and the batch)
 struct PlanCore {
@@ -119,6 +155,14 @@ struct PlanCore {
   ScanState *scan = nullptr;
   int32_t *cfg_err = nullptr;  // device [n_cfg] (scan path)
   std::vector<int32_t> site_acc;   // host copy: access index of each call site
+  // data region and directives (region mode): device arrays and the host
+  // per-CFG offsets views need
+  bool region = false;
+  ClsDev cls{};
+  uint8_t *d_in_region = nullptr;
+  int32_t *d_rin = nullptr, *d_rout = nullptr;
+  uint64_t *d_fp = nullptr;
+  std::vector<int32_t> h_kern_off, h_rin_off, h_rout_off, h_acc_base;
 
   long long dev_bytes = 0;  // device bytes this core holds (with its scan state)
 
@@ -157,10 +201,12 @@ void boundary_rows(const ompdart_cfg *cfg, int W, std::vector<uint64_t> *top, st
 // solver (path 0 auto, 1 sweep, 2 scan; a batch must take the scan) and
 // allocate every plane.  unreach_cfg: CFG of each unreachable block in
 // ascending block order (empty for one CFG).  Returns an OMPDART_* code.
+// fp: the firstprivate rows of every kernel ([n_kernels][W], kernels
+// numbered plan-wide by Ingest::kern_off; empty = none).
 int core_build(PlanCore *c, const int32_t *acc_off, const uint32_t *acc, const CallHost &calls,
                const std::vector<uint64_t> &top, const std::vector<uint64_t> &eh, const std::vector<uint64_t> &ed,
                const std::vector<uint64_t> &xl, int n_cfg, const std::vector<int32_t> &unreach_cfg,
-               const ompdart_opts &o, std::string *err);
+               const ompdart_opts &o, std::string *err, const std::vector<uint64_t> &fp = {});
 // Enqueue one full run on s; returns the number of kernels launched.
 int core_enqueue(PlanCore *c, cudaStream_t s, Prof *pf);
 // After the stream finished a run (h_status: its ST_COUNT status words):

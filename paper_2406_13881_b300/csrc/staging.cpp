@@ -6,8 +6,10 @@
 // contexts) is copied once, so those CFGs keep sharing one ingestion.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <string>
+#include <unordered_map>
 
 #include "solver.h"
 
@@ -87,6 +89,10 @@ int stage_one(const ompdart_cfg &in, StagedCfgs *st, ompdart_cfg *out, std::stri
   if (in.call_planes && in.n_calls > 0)
     out->call_planes = static_cast<const uint64_t *>(
         copy_in(st, in.call_planes, (size_t)in.n_calls * 7 * W * 8, "call_planes", &rc, err));
+  if (rc) return rc;
+  out->region = static_cast<const int32_t *>(copy_in(st, in.region, N * 4, "region", &rc, err));
+  if (rc) return rc;
+  out->scalar_vars = static_cast<const uint64_t *>(copy_in(st, in.scalar_vars, W * 8, "scalar_vars", &rc, err));
   return rc;
 }
 
@@ -117,6 +123,66 @@ int stage_cfgs(const ompdart_cfg *in, int n, StagedCfgs *st, const ompdart_cfg *
     }
   }
   *out = st->cfgs.data();
+  return OMPDART_OK;
+}
+
+int firstprivate_view(const ompdart_cfg &in, StagedCfgs *st, ompdart_cfg *out, std::vector<uint64_t> *fp,
+                      int *n_kernels, std::string *err) {
+  *out = in;
+  fp->clear();
+  *n_kernels = 0;
+  if (!in.region) return OMPDART_OK;
+  const int N = in.n_blocks, W = (in.n_vars + 63) / 64;
+  int nk = 0;
+  for (int b = 0; b < N; ++b) {
+    if (in.region[b] < -1 || in.region[b] >= N) {
+      if (err) *err = "kernel ids (region) must be -1 or in [0, n_blocks)";
+      return OMPDART_E_INVALID;
+    }
+    nk = std::max(nk, in.region[b] + 1);
+  }
+  *n_kernels = nk;
+  fp->assign((size_t)nk * W, 0);
+  if (!in.scalar_vars || !nk) return OMPDART_OK;
+  auto scalar = [&](int v) { return (in.scalar_vars[v >> 6] >> (v & 63)) & 1ull; };
+  // per (kernel, scalar): bit 1 read on the device, bit 2 written (either space)
+  std::unordered_map<long long, uint8_t> use;
+  for (int b = 0; b < N; ++b) {
+    const int k = in.region[b];
+    if (k < 0) continue;
+    for (int i = in.acc_off[b]; i < in.acc_off[b + 1]; ++i) {
+      const uint32_t a = in.acc[i];
+      const int v = (int)(a & 0xFFFFFFu);
+      if ((a >> 31) || !scalar(v)) continue;
+      uint8_t &u = use[(long long)k * in.n_vars + v];
+      const int kind = (int)((a >> 24) & 3u);
+      if (kind & 2) u |= 2;
+      if ((kind & 1) && ((a >> 26) & 1u)) u |= 1;
+    }
+  }
+  bool any = false;
+  for (const auto &kv : use)
+    if (kv.second == 1) {
+      const int k = (int)(kv.first / in.n_vars), v = (int)(kv.first % in.n_vars);
+      (*fp)[(size_t)k * W + (v >> 6)] |= 1ull << (v & 63);
+      any = true;
+    }
+  if (!any) return OMPDART_OK;
+  const size_t A = (size_t)in.acc_off[N];
+  st->bufs.emplace_back(std::max<size_t>(A, 1) * 4);
+  uint32_t *acc = reinterpret_cast<uint32_t *>(st->bufs.back().data());
+  std::memcpy(acc, in.acc, A * 4);
+  for (int b = 0; b < N; ++b) {
+    const int k = in.region[b];
+    if (k < 0) continue;
+    for (int i = in.acc_off[b]; i < in.acc_off[b + 1]; ++i) {
+      const uint32_t a = acc[i];
+      const int v = (int)(a & 0xFFFFFFu);
+      if ((a >> 31) || !((a >> 26) & 1u) || !scalar(v)) continue;
+      if (((*fp)[(size_t)k * W + (v >> 6)] >> (v & 63)) & 1ull) acc[i] = a & ~(1u << 26);  // a host read
+    }
+  }
+  out->acc = acc;
   return OMPDART_OK;
 }
 

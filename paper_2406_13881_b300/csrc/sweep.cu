@@ -208,18 +208,23 @@ __global__ void k_sweep_masks(DevPlan p) {
   p.mask_d[(size_t)l * W + w] = p.lant[((size_t)b0 * W + w) * 2 + 1] & ~kod;
 }
 
-// loop-entry edge constants: device side = mask_d of the loop & host valid
-// (plain) at the source; host side = mask_h & device valid at the source
+// edge constants: on a loop-entry edge, device side = mask_d of the loop &
+// host valid (plain) at the source, host side = mask_h & device valid at
+// the source; on an edge leaving the data region the host side also holds
+// what is live at its target (made valid on the host there)
 template <int PH>
 __global__ void k_edge_const(DevPlan p) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)p.K * p.W) return;
   const int k = (int)(t / p.W), w = (int)(t % p.W), W = p.W;
   const int l = p.ent_loop[k], src = p.ent_src[k];
-  if (PH == PH_D)
-    p.ec_d[t] = p.mask_d[(size_t)l * W + w] & p.hp_out[(size_t)src * W + w];
-  else
-    p.ec_h[t] = p.mask_h[(size_t)l * W + w] & p.d_out[(size_t)src * W + w];
+  if (PH == PH_D) {
+    p.ec_d[t] = l >= 0 ? p.mask_d[(size_t)l * W + w] & p.hp_out[(size_t)src * W + w] : 0ull;
+  } else {
+    uint64_t x = l >= 0 ? p.mask_h[(size_t)l * W + w] & p.d_out[(size_t)src * W + w] : 0ull;
+    if (p.ent_rx && p.ent_rx[k]) x |= p.live[(size_t)p.ent_dst[k] * W + w];
+    p.ec_h[t] = x;
+  }
 }
 
 // ---- emission (Table II) ------------------------------------------------------------
@@ -267,6 +272,10 @@ __global__ void k_emit_edges(DevPlan p, int n_fin) {
     hedge |= p.ec_h[(size_t)ent * W + w];
   }
   fr |= p.live[(size_t)dst * W + w] & ~p.d_in[(size_t)dst * W + w] & ~hedge;
+  if (p.fin_bnd && p.fin_bnd[k] >= 0) {  // an edge on the data region's boundary
+    p.bnd_to[(size_t)p.fin_bnd[k] * W + w] = to;
+    p.bnd_from[(size_t)p.fin_bnd[k] * W + w] = fr;
+  }
   if (to | fr) {
     const int slot = atomicAdd(&p.status[ST_NREC], 1);
     if (slot < p.xfer_cap) p.xfer[slot] = EdgeXfer{p.fin_eid[k], w, to, fr};
