@@ -460,7 +460,7 @@ def run_ours(args):
                                            "plain_per_cfg", "speedup_vs_plain", "roofline", "e2e", "cpu_baseline",
                                            "cpu_baseline_parallel", "gpu_launches", "config")}
         sv = measure_serve(sub, local)
-        out["serve"] = {k: sv[k] for k in ("config", "served", "plain_per_cfg", "note")}
+        out["serve"] = {k: sv[k] for k in ("config", "served", "plain_per_cfg", "resident", "note")}
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -723,6 +723,39 @@ def measure_serve(args, local):
         n = int(min(args.max_requests, max(200, rate * args.seconds)))
         served.append(one(rate, n, 4096, args.inflight))
         plain.append(one(rate, int(min(n, args.plain_requests)), 1, 1))
+    # resident mode: CFGs stay on the device between requests (a plan per
+    # distinct CFG, cached by content); one server for every rate, its cache
+    # filled with the request pool first (untimed)
+    rsrv = _native.Server(hbm_budget_bytes=args.budget_gb << 30, resident=True, workers=args.workers, device=local)
+    warm = [rsrv.submit(g) for g in small + large]
+    rsrv.drain()
+    for t in warm:
+        rsrv.wait(t, want_result=False)
+    resident = []
+    for rate in args.rates:
+        n = int(min(args.max_requests, max(200, rate * args.seconds)))
+        cfgs = draw(n)
+        arrival = np.cumsum(rng.exponential(1e6 / rate, size=n))
+        s0 = rsrv.stats()
+        t0 = time.perf_counter()
+        tickets = rsrv.replay(cfgs, arrival)
+        t_sub = time.perf_counter() - t0
+        rsrv.drain()
+        wall = time.perf_counter() - t0
+        lats, fails = [], 0
+        for t in tickets:
+            st, lat, _ = rsrv.wait(t, want_result=False)
+            lats.append(lat)
+            fails += st != 0
+        s1 = rsrv.stats()
+        units = sum(g.n_blocks * g.W for g in cfgs)
+        resident.append({"rate_req_s": rate, "requests": n, "offered_req_s": n / (arrival[-1] / 1e6),
+                         "submitted_req_s": n / t_sub, "cfgs_per_s": n / wall, "updates_per_s": units / wall,
+                         "p50_ms": percentile(lats, 50), "p99_ms": percentile(lats, 99), "max_ms": max(lats),
+                         "failed": int(fails), "cache_hits": s1["cache_hits"] - s0["cache_hits"],
+                         "cache_misses": s1["cache_misses"] - s0["cache_misses"],
+                         "cached_plans": s1["cached_plans"], "device_bytes": s1["bytes_in_use"], "wall_s": wall})
+    rsrv.close()
     top = served[-1]
     return {
         "metric": "block·var-word updates/s to fixed point; CFGs/s and p50/p99 vs per-CFG launch",
@@ -737,7 +770,10 @@ def measure_serve(args, local):
                    "parallelism": "single GPU"},
         "served": served,
         "plain_per_cfg": plain,
-        "note": "value = updates/s completed at the highest rate; latency = submission to result on the host",
+        "resident": resident,
+        "note": "value = updates/s completed at the highest rate (batched serving); latency = submission to result "
+                "on the host; `resident': CFGs kept on the device between requests (plan cache warmed with the "
+                "request pool first)",
     }
 
 
@@ -871,6 +907,7 @@ def main():
     ap.add_argument("--large-blocks", type=int, default=1 << 16)
     ap.add_argument("--budget-gb", type=int, default=40)
     ap.add_argument("--inflight", type=int, default=2)
+    ap.add_argument("--workers", type=int, default=8, help="serve: worker threads of the resident mode")
     ap.add_argument("--n-cfgs", type=int, default=10000, help="CFGs of the batch workload")
     ap.add_argument("--batch-seed", type=int, default=3)
     ap.add_argument("--tune", type=int, default=1, help="batch: autotune the arenas' launch shapes")

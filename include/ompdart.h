@@ -454,7 +454,20 @@ void ompdart_program_result_free(ompdart_program_result *res);
    memory is released and the next pending requests are admitted.
    A serving batch runs once, so its kernels are launched directly (no
    graph capture).  max_batch = 1 is the plain form: one plan and one
-   launch sequence per request. */
+   launch sequence per request.
+
+   RESIDENT MODE (resident != 0): CFGs stay on the device between requests.
+   `workers' threads, each with its own stream, take requests in arrival
+   order.  A request's CFG is looked up by its content (graph, accesses,
+   call table, kernels and scalars; not the entry and exit rows, which can
+   differ per request) in a cache of device-resident plans: a hit uploads
+   the request's entry and exit rows into the cached plan and runs it; a
+   miss ingests the CFG into a new plan first (ompdart_plan_create) and
+   keeps it.  Runs of one cached plan are serialised; different plans run
+   concurrently.  The plans' device bytes stay within hbm_budget_bytes:
+   the least recently used idle plans are dropped to make room, and a
+   request that still does not fit runs on a plan of its own that is
+   freed afterwards.  max_batch and max_inflight are not used. */
 typedef struct ompdart_server ompdart_server;
 typedef struct {
   int64_t hbm_budget_bytes; /* device bytes admitted work may hold; 0 = 40 GiB     */
@@ -463,6 +476,8 @@ typedef struct {
   int32_t device;           /* CUDA device ordinal                                  */
   int32_t keep_results;     /* nonzero: copy each result to the host for the waiter */
   ompdart_opts opts;        /* analysis options of every batch                      */
+  int32_t resident;         /* nonzero: resident mode (see below)                   */
+  int32_t workers;          /* resident mode: worker threads; 0 = 8                 */
 } ompdart_server_opts;
 
 typedef struct {
@@ -470,6 +485,9 @@ typedef struct {
   double mean_batch;               /* CFGs per batch                              */
   double p50_ms, p99_ms, max_ms;   /* latency: submission to result on the host   */
   int64_t peak_bytes, bytes_in_use; /* device bytes held by admitted batches       */
+  int64_t cache_hits, cache_misses; /* resident mode: requests served by a cached
+                                       plan / that had to build one              */
+  int64_t cached_plans;            /* resident mode: plans held now                */
 } ompdart_server_stats;
 
 int ompdart_server_create(const ompdart_server_opts *opts, ompdart_server **server);

@@ -75,14 +75,16 @@ class Result(C.Structure):
 
 class ServerOpts(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_int64), ("max_batch", C.c_int32), ("max_inflight", C.c_int32),
-                ("device", C.c_int32), ("keep_results", C.c_int32), ("opts", Opts)]
+                ("device", C.c_int32), ("keep_results", C.c_int32), ("opts", Opts), ("resident", C.c_int32),
+                ("workers", C.c_int32)]
 
 
 class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64),
                 ("batches", C.c_int64), ("mean_batch", C.c_double), ("p50_ms", C.c_double),
                 ("p99_ms", C.c_double), ("max_ms", C.c_double), ("peak_bytes", C.c_int64),
-                ("bytes_in_use", C.c_int64)]
+                ("bytes_in_use", C.c_int64), ("cache_hits", C.c_int64), ("cache_misses", C.c_int64),
+                ("cached_plans", C.c_int64)]
 
 
 class Program(C.Structure):
@@ -480,10 +482,11 @@ class Server:
     returns its ticket, ``wait`` returns (status, latency ms, result dict or
     None), ``replay`` submits many CFGs at given arrival times."""
 
-    def __init__(self, hbm_budget_bytes=0, max_batch=0, max_inflight=0, device=0, keep_results=True, **opts):
+    def __init__(self, hbm_budget_bytes=0, max_batch=0, max_inflight=0, device=0, keep_results=True, resident=False,
+                 workers=0, **opts):
         self._lib = load()
         so = ServerOpts(int(hbm_budget_bytes), int(max_batch), int(max_inflight), int(device),
-                        int(bool(keep_results)), _opts(device=device, **opts))
+                        int(bool(keep_results)), _opts(device=device, **opts), int(bool(resident)), int(workers))
         self._h = C.c_void_p()
         self._keep = []
         _check(self._lib.ompdart_server_create(C.byref(so), C.byref(self._h)))

@@ -564,6 +564,26 @@ struct ompdart_plan {
   }
 };
 
+namespace ompdart {
+
+int plan_set_boundary(ompdart_plan *P, const ompdart_cfg *cfg, cudaStream_t s) {
+  std::vector<uint64_t> top, eh, ed, xl;
+  boundary_rows(cfg, P->core.g.W, &top, &eh, &ed, &xl);
+  const DevPlan &d = P->core.dp;
+  const size_t bytes = sizeof(uint64_t) * eh.size();
+  cudaError_t ce = cudaMemcpyAsync(const_cast<uint64_t *>(d.entry_h), eh.data(), bytes, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(const_cast<uint64_t *>(d.entry_d), ed.data(), bytes, cudaMemcpyHostToDevice, s);
+  if (ce == cudaSuccess)
+    ce = cudaMemcpyAsync(const_cast<uint64_t *>(d.exit_live), xl.data(), bytes, cudaMemcpyHostToDevice, s);
+  // (copies from pageable memory have read their source when they return)
+  return ce == cudaSuccess ? OMPDART_OK : cuda_err(ce, "uploading entry and exit rows");
+}
+
+long long plan_device_bytes(const ompdart_plan *P) { return P ? P->core.dev_bytes : 0; }
+
+}  // namespace ompdart
+
 extern "C" {
 
 const char *ompdart_last_error(void) { return g_err.c_str(); }

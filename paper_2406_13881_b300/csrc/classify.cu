@@ -31,20 +31,52 @@ namespace {
 __device__ __forceinline__ void or_bit(uint64_t *row, int v) {
   atomicOr(reinterpret_cast<unsigned long long *>(row) + (v >> 6), 1ull << (v & 63));
 }
+// OR bit v into word w of `row' for every lane with key >= 0, one atomic per
+// distinct (key, word) in the warp: many accesses of one CFG or kernel hit
+// the same few words, so lanes with the same target combine their bits
+// first.  Every lane of the warp must call it (inactive ones with key -1).
+__device__ __forceinline__ void or_bit_warp(uint64_t *base, long long key, int v) {
+  const long long target = key < 0 ? -1 : key + (v >> 6);
+  const unsigned grp = __match_any_sync(0xffffffffu, target);
+  if (target < 0) return;
+  unsigned long long bits = 0;
+  for (unsigned m = grp; m; m &= m - 1) bits |= __shfl_sync(grp, 1ull << (v & 63), __ffs(m) - 1);
+  if ((threadIdx.x & 31) == __ffs(grp) - 1) atomicOr(reinterpret_cast<unsigned long long *>(base) + target, bits);
+}
 __device__ __forceinline__ bool has_bit(const uint64_t *row, int v) { return (row[v >> 6] >> (v & 63)) & 1ull; }
 
 __global__ void k_cls_writes(ClsDev c) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (i >= c.A) return;
-  const uint32_t a = c.acc[i];
-  if (a >> 31) return;
-  const int k = c.kern[c.acc_blk[i]];
-  if (k < 0 || !(acc_kind(a) & 2)) return;
-  or_bit((acc_space(a) ? c.kw_d : c.kw_h) + (size_t)k * c.W, acc_var(a));
+  long long kh = -1, kd = -1;
+  int v = 0;
+  if (i < c.A) {
+    const uint32_t a = c.acc[i];
+    const int k = (a >> 31) ? -1 : c.kern[c.acc_blk[i]];
+    if (k >= 0 && (acc_kind(a) & 2)) {
+      v = acc_var(a);
+      (acc_space(a) ? kd : kh) = (long long)k * c.W;
+    }
+  }
+  or_bit_warp(c.kw_h, kh, v);
+  or_bit_warp(c.kw_d, kd, v);
 }
 
 __global__ void k_cls_access(ClsDev c) {
   const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  // variables the kernels touch on the device (reachable blocks)
+  {
+    long long key = -1;
+    int v = 0;
+    if (i < c.A) {
+      const int b = c.acc_blk[i];
+      const uint32_t a = c.acc[i];
+      if (c.pos[b] >= 0 && !(a >> 31) && c.kern[b] >= 0 && acc_space(a)) {
+        key = (long long)c.blk_cfg[b] * c.W;
+        v = acc_var(a);
+      }
+    }
+    or_bit_warp(c.dev_touched, key, v);
+  }
   if (i >= c.A) return;
   const int b = c.acc_blk[i];
   if (c.pos[b] < 0) {  // unreachable: no transfer
@@ -55,7 +87,6 @@ __global__ void k_cls_access(ClsDev c) {
   const int cfg = c.blk_cfg[b], k = c.kern[b], W = c.W;
   const bool call = (a >> 31) != 0;
   const int v = acc_var(a);
-  if (!call && k >= 0 && acc_space(a)) or_bit(c.dev_touched + (size_t)cfg * W, v);
   const int f = c.acc_flag[i];
   if (!f) {
     c.acc_point[i] = -1;

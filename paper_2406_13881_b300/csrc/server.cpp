@@ -14,6 +14,13 @@
 //      uploaded on the host while earlier batches run, then launched on its
 //      own stream, so batches overlap on the device.
 // Submitting copies the request, so callers may reuse their buffers.
+//
+// Resident mode (opts.resident): `workers' threads, each with its own
+// stream, take requests in arrival order and serve each from a cache of
+// device-resident plans keyed by the CFG's content (its entry and exit rows
+// excluded): a hit uploads the request's rows into the cached plan and
+// runs it; a miss builds the plan and keeps it, dropping the least recently
+// used idle plans when the device budget would overflow.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,6 +34,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/ompdart.h"
@@ -81,6 +89,27 @@ struct ompdart_server {
   long long bytes_in_use = 0, peak_bytes = 0;
   int64_t submitted = 0, completed = 0, failed = 0, batches = 0, batched_cfgs = 0;
   std::vector<double> lat_ms;
+  // ---- resident mode
+  struct Cached {
+    ompdart_plan *plan = nullptr;
+    std::mutex run;         // runs of one plan are serialised
+    long long bytes = 0;
+    uint64_t last_use = 0;  // LRU clock (guarded by cache_mu)
+    ~Cached() { ompdart_plan_destroy(plan); }
+  };
+  struct KeyHash {
+    size_t operator()(const std::pair<uint64_t, uint64_t> &k) const { return (size_t)(k.first ^ (k.second * 31)); }
+  };
+  std::vector<std::thread> workers;
+  // one stream per worker, owned by the server: a cached plan synchronises
+  // the stream it last ran on when it is destroyed, so the streams outlive
+  // the cache
+  std::vector<cudaStream_t> worker_streams;
+  std::mutex cache_mu;
+  std::unordered_map<std::pair<uint64_t, uint64_t>, std::shared_ptr<Cached>, KeyHash> cache;
+  long long cache_bytes = 0;
+  uint64_t lru_clock = 0;
+  int64_t cache_hits = 0, cache_misses = 0;
 };
 
 namespace {
@@ -165,6 +194,150 @@ void launch(ompdart_server *S, std::vector<ReqPtr> &take, long long reserved) {
   S->inflight.push_back(std::move(f));
 }
 
+// ---- resident mode ---------------------------------------------------------------
+// 128-bit content key of a CFG: its graph, accesses, call table, kernels and
+// scalars (two independent word-wise mixes)
+struct Mix {
+  uint64_t a = 0x9e3779b97f4a7c15ull, b = 0xc2b2ae3d27d4eb4full;
+  void add(uint64_t x) {
+    a = (a ^ x) * 0x100000001b3ull;
+    a ^= a >> 29;
+    b = (b + x) * 0xff51afd7ed558ccdull;
+    b ^= b >> 33;
+  }
+  template <class T>
+  void add(const T *p, size_t n) {
+    add((uint64_t)n);
+    if (!p) return add(0x5bd1e995ull);
+    const unsigned char *c = reinterpret_cast<const unsigned char *>(p);
+    const size_t bytes = n * sizeof(T);
+    size_t i = 0;
+    for (; i + 8 <= bytes; i += 8) {
+      uint64_t x;
+      memcpy(&x, c + i, 8);
+      add(x);
+    }
+    uint64_t t = 0;
+    memcpy(&t, c + i, bytes - i);
+    add(t);
+  }
+};
+std::pair<uint64_t, uint64_t> content_key(const ompdart_cfg &c) {
+  Mix m;
+  const size_t N = (size_t)c.n_blocks, W = (size_t)(c.n_vars + 63) / 64;
+  m.add((uint64_t)c.n_blocks);
+  m.add((uint64_t)c.n_vars);
+  m.add((uint64_t)c.entry);
+  m.add(c.succ_off, N + 1);
+  m.add(c.succ, (size_t)c.succ_off[N]);
+  m.add(c.acc_off, N + 1);
+  m.add(c.acc, (size_t)c.acc_off[N]);
+  m.add(c.call_planes, c.call_planes ? (size_t)c.n_calls * 7 * W : 0);
+  m.add(c.region, c.region ? N : 0);
+  m.add(c.scalar_vars, c.scalar_vars ? W : 0);
+  return {m.a, m.b};
+}
+
+void finish_one(ompdart_server *S, const ReqPtr &r, int rc, ompdart_result *res, const std::string &err) {
+  const Clock::time_point now = Clock::now();
+  std::lock_guard<std::mutex> lk(S->mu);
+  --S->n_inflight;
+  finish_request(S, r, rc, res, now, err);
+  S->cv_done.notify_all();
+}
+
+// Make room for `need' more device bytes of cached plans by dropping idle
+// plans, least recently used first.  cache_mu held.
+void evict_for(ompdart_server *S, long long need) {
+  while (S->cache_bytes + need > S->o.hbm_budget_bytes) {
+    auto victim = S->cache.end();
+    for (auto it = S->cache.begin(); it != S->cache.end(); ++it) {
+      if (it->second.use_count() > 1) continue;  // a worker holds it
+      if (victim == S->cache.end() || it->second->last_use < victim->second->last_use) victim = it;
+    }
+    if (victim == S->cache.end()) return;
+    S->cache_bytes -= victim->second->bytes;
+    S->cache.erase(victim);
+  }
+}
+
+void serve_resident(ompdart_server *S, const ReqPtr &r, cudaStream_t s) {
+  const auto key = content_key(r->cfg);
+  std::shared_ptr<ompdart_server::Cached> c;
+  {
+    std::lock_guard<std::mutex> lk(S->cache_mu);
+    auto it = S->cache.find(key);
+    if (it != S->cache.end()) {
+      c = it->second;
+      c->last_use = ++S->lru_clock;
+      ++S->cache_hits;
+    } else {
+      ++S->cache_misses;
+    }
+  }
+  bool keep = true;
+  if (!c) {  // ingest and build it (outside the locks)
+    c = std::make_shared<ompdart_server::Cached>();
+    const int rc = ompdart_plan_create(&r->cfg, &S->o.opts, &c->plan);
+    if (rc) {
+      c->plan = nullptr;
+      finish_one(S, r, rc, nullptr, ompdart_last_error());
+      return;
+    }
+    c->bytes = plan_device_bytes(c->plan);
+    std::lock_guard<std::mutex> lk(S->cache_mu);
+    auto it = S->cache.find(key);
+    if (it != S->cache.end()) {  // another worker built it meanwhile
+      c = it->second;
+    } else {
+      evict_for(S, c->bytes);
+      if (S->cache_bytes + c->bytes <= S->o.hbm_budget_bytes) {
+        S->cache.emplace(key, c);
+        S->cache_bytes += c->bytes;
+      } else {
+        keep = false;  // no room: a plan of its own, freed after the run
+      }
+    }
+    c->last_use = ++S->lru_clock;
+  }
+  int rc;
+  ompdart_result *res = nullptr;
+  {
+    std::lock_guard<std::mutex> run(c->run);
+    rc = plan_set_boundary(c->plan, &r->cfg, s);
+    if (!rc) rc = ompdart_plan_run(c->plan, s);
+    if (!rc) rc = ompdart_plan_sync(c->plan);
+    if (!rc && S->o.keep_results) rc = ompdart_plan_fetch(c->plan, &res);
+  }
+  const std::string err = rc ? ompdart_last_error() : "";
+  (void)keep;  // an uncached plan dies with the last reference
+  c.reset();
+  finish_one(S, r, rc, res, err);
+}
+
+void resident_worker(ompdart_server *S, cudaStream_t s) {
+  cudaSetDevice(S->o.device);
+  for (;;) {
+    ReqPtr r;
+    {
+      std::unique_lock<std::mutex> lk(S->mu);
+      S->cv_work.wait(lk, [&] { return S->stop || !S->pending.empty(); });
+      if (S->pending.empty()) break;  // stopping with nothing left
+      r = S->pending.front();
+      S->pending.pop_front();
+      ++S->n_inflight;
+      if (r->est > S->o.hbm_budget_bytes) {
+        --S->n_inflight;
+        finish_request(S, r, OMPDART_E_BUDGET, nullptr, Clock::now(),
+                       "the request needs more device memory than the whole budget");
+        S->cv_done.notify_all();
+        continue;
+      }
+    }
+    serve_resident(S, r, s);
+  }
+}
+
 void worker_main(ompdart_server *S) {
   cudaSetDevice(S->o.device);
   for (;;) {
@@ -240,7 +413,21 @@ int ompdart_server_create(const ompdart_server_opts *opts, ompdart_server **out)
     delete S;
     return set_error(OMPDART_E_CUDA, "cudaSetDevice failed");
   }
-  S->worker = std::thread(worker_main, S);
+  if (S->o.resident) {
+    const int nw = S->o.workers > 0 ? S->o.workers : 8;
+    for (int k = 0; k < nw; ++k) {
+      cudaStream_t x = nullptr;
+      if (cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) {
+        for (cudaStream_t y : S->worker_streams) cudaStreamDestroy(y);
+        delete S;
+        return set_error(OMPDART_E_CUDA, "stream creation failed");
+      }
+      S->worker_streams.push_back(x);
+    }
+    for (int k = 0; k < nw; ++k) S->workers.emplace_back(resident_worker, S, S->worker_streams[k]);
+  } else {
+    S->worker = std::thread(worker_main, S);
+  }
   *out = S;
   return OMPDART_OK;
 }
@@ -358,6 +545,16 @@ int ompdart_server_get_stats(ompdart_server *S, ompdart_server_stats *out) {
   out->mean_batch = S->batches ? (double)S->batched_cfgs / S->batches : 0.0;
   out->peak_bytes = S->peak_bytes;
   out->bytes_in_use = S->bytes_in_use;
+  {
+    std::lock_guard<std::mutex> ck(S->cache_mu);
+    out->cache_hits = S->cache_hits;
+    out->cache_misses = S->cache_misses;
+    out->cached_plans = (int64_t)S->cache.size();
+    if (S->o.resident) {
+      out->bytes_in_use = S->cache_bytes;
+      out->peak_bytes = std::max<int64_t>(out->peak_bytes, S->cache_bytes);
+    }
+  }
   std::vector<double> l = S->lat_ms;
   if (!l.empty()) {
     std::sort(l.begin(), l.end());
@@ -377,6 +574,9 @@ void ompdart_server_destroy(ompdart_server *S) {
   }
   S->cv_work.notify_all();
   if (S->worker.joinable()) S->worker.join();  // finishes what was submitted
+  for (auto &t : S->workers) t.join();
+  S->cache.clear();  // the cached plans (each synchronises its last stream)
+  for (cudaStream_t x : S->worker_streams) cudaStreamDestroy(x);
   for (auto &kv : S->live)
     if (kv.second->res) ompdart_result_free(kv.second->res);
   delete S;

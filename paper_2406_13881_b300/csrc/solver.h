@@ -223,6 +223,13 @@ int result_copy(const ompdart_result &v, bool pin, cudaStream_t s, ompdart_resul
 // reference to it); NULL if the host allocation fails.
 ompdart_result *result_in_block(const ompdart_result &v, HostBlock *block);
 
+// ---- api.cu: hooks of the serving loop's resident mode on a plan
+// Upload the entry / exit rows of `cfg' (a CFG with the plan's graph) into
+// the plan's device rows on `stream'.
+int plan_set_boundary(ompdart_plan *plan, const ompdart_cfg *cfg, cudaStream_t stream);
+// Device bytes a plan holds.
+long long plan_device_bytes(const ompdart_plan *plan);
+
 // ---- hostmem.cpp: reference-counted host blocks for host results
 // (page-locked or pageable; cached by size class once released when large)
 HostBlock *host_block_new(size_t bytes, bool pin);  // one reference; NULL on failure
