@@ -43,7 +43,7 @@ class _Cfg(C.Structure):
                 ("acc", C.c_void_p), ("entry_host_valid", C.c_void_p),
                 ("entry_dev_valid", C.c_void_p), ("exit_host_live", C.c_void_p),
                 ("call_planes", C.c_void_p), ("n_calls", C.c_int32), ("region", C.c_void_p),
-                ("data_region", C.c_int32)]
+                ("data_region", C.c_int32), ("eager_to", C.c_int32)]
 
 
 _OUT_FIELDS = [
@@ -58,7 +58,7 @@ _OUT_FIELDS = [
     ("from_exit", "NW", np.uint64), ("acc_flag", "A", np.uint8),
     ("call_to", "SW", np.uint64), ("call_from", "SW", np.uint64), ("call_entry_h", "SW", np.uint64),
     ("call_entry_d", "SW", np.uint64), ("call_exit_live", "SW", np.uint64),
-    ("in_region", "N", np.uint8), ("region_exit", "E", np.uint8),
+    ("in_region", "N", np.uint8), ("region_exit", "E", np.uint8), ("ant_dm_in", "NW", np.uint64),
 ]
 
 
@@ -121,14 +121,16 @@ def summarize(cfg) -> np.ndarray:
     return out
 
 
-def solve(cfg, want=None, data_region=False) -> dict:
+def solve(cfg, want=None, data_region=False, eager_to=False) -> dict:
     """Run the oracle on ``cfg`` (an object with the CSR fields of
     ``paper_2406_13881_b300.workload.CFG`` or a dict with the same keys).
 
     ``want``: iterable of output names to produce (default: all).  Returns a
     dict of numpy arrays; plane outputs are shaped [rows, W].
     ``data_region``: the single target data region of Sec. IV-D around the
-    kernels given by ``cfg.region`` (see oracle_cfg.data_region)."""
+    kernels given by ``cfg.region`` (see oracle_cfg.data_region).
+    ``eager_to``: eager `to' placement after the producing host write
+    (Sec. IV-E; see oracle_cfg.eager_to)."""
     lib = _load()
     g = cfg if isinstance(cfg, dict) else cfg.__dict__
     n, nv = int(g["n_blocks"]), int(g["n_vars"])
@@ -150,7 +152,7 @@ def solve(cfg, want=None, data_region=False) -> dict:
     c = _Cfg(n, nv, int(g.get("entry", 0)), _ptr(so), _ptr(s), _ptr(ao), _ptr(acc),
              _ptr(ehv), _ptr(edv), _ptr(xhl), _ptr(calls),
              0 if calls is None else int(calls.size // (7 * W)), _ptr(reg),
-             int(bool(data_region) and reg is not None))
+             int(bool(data_region) and reg is not None), int(bool(eager_to)))
     S = int(np.count_nonzero(acc >> np.uint32(31)))
     sizes = {"N": (n,), "E": (E,), "A": (A,), "NW": (n, W), "EW": (E, W), "SW": (S, W)}
     res, ptrs = {}, {}

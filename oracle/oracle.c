@@ -13,7 +13,8 @@
  *   4. loop masks: needed by a node of the loop and never made stale in
  *      the body (Sec. IV-D loop rule; Algorithm 1's outward walk)
  *   5. device validity D, forward must, with the masks as hoisted `to' on
- *      loop-entry edges
+ *      loop-entry edges (eager placement: the must-anticipation of device
+ *      reads first, and its `to' on every edge)
  *   6. host validity H, forward must, hoisted `from' on loop-entry edges and
  *      a live join where neither space is valid resolved toward the host
  *   7. emission of the Table II transfers from the final states.
@@ -257,6 +258,44 @@ static int anticipation(const graph *g, const uint64_t *UES, const uint64_t *DF,
   return ORACLE_OK;
 }
 
+/* ---- eager `to': must-anticipation of a device read (Sec. IV-E) ----------
+ * AntDm_in[b] = UED[b] | (AntDm_out[b] & ~Def[b]); AntDm_out[b] = AND over
+ * successors s of AntDm_in[s]; a block without successors: nothing (a path
+ * that leaves the function first does not read the copy).  Greatest fixed
+ * point over reachable blocks: v is in AntDm at a point when every path
+ * from there reads v on the device before any write of v. */
+static int must_anticipation(const graph *g, const uint64_t *UES, const uint64_t *DF, uint64_t *am_in) {
+  int W = g->W;
+  wlist wl;
+  if (wl_init(&wl, g->N)) return ORACLE_E_NOMEM;
+  uint64_t *out = xcalloc((size_t)W, sizeof(uint64_t));
+  if (!out) { wl_free(&wl); return ORACLE_E_NOMEM; }
+  for (int b = 0; b < g->N; ++b)
+    for (int w = 0; w < W; ++w) am_in[(size_t)b * W + w] = g->reach[b] ? g->top[w] : 0;
+  for (int b = g->N - 1; b >= 0; --b) if (g->reach[b]) wl_push(&wl, b);
+  while (wl.count) {
+    int b = wl_pop(&wl);
+    if (g->so[b] == g->so[b + 1]) {
+      memset(out, 0, (size_t)W * sizeof(uint64_t));
+    } else {
+      for (int w = 0; w < W; ++w) out[w] = g->top[w];
+      for (int e = g->so[b]; e < g->so[b + 1]; ++e)
+        for (int w = 0; w < W; ++w) out[w] &= am_in[(size_t)g->s[e] * W + w];
+    }
+    int changed = 0;
+    for (int w = 0; w < W; ++w) {
+      size_t o = (size_t)b * W + w;
+      uint64_t nv = UES[o] | (out[w] & ~DF[o]);
+      if (nv != am_in[o]) { am_in[o] = nv; changed = 1; }
+    }
+    if (changed)
+      for (int k = g->po[b]; k < g->po[b + 1]; ++k)
+        if (g->reach[g->ps[k]]) wl_push(&wl, g->ps[k]);
+  }
+  free(out); wl_free(&wl);
+  return ORACLE_OK;
+}
+
 /* ---- steps 3, 5, 6: forward must problems (greatest fixed point) --------
  * x_in[entry] = init; x_in[b] = AND over reachable predecessors p of
  *   (x_out[p] | edge_gen(p->b)); then x_in[b] |= node_gen[b] (H only);
@@ -271,6 +310,8 @@ typedef struct {
   uint64_t *x_in, *x_out, *x_meet;         /* x_meet may be NULL             */
   const uint8_t *is_exit_edge;             /* [E] edges leaving the data region, or NULL */
   const uint64_t *exit_gen;                /* [N*W] added along such an edge p->b: row b */
+  const uint64_t *any_mask, *any_src;      /* [N*W] or NULL: added along every edge
+                                              p->b: any_mask row b & any_src row p */
 } fwd_problem;
 
 static int forward_must(const graph *g, fwd_problem *P) {
@@ -300,6 +341,7 @@ static int forward_must(const graph *g, fwd_problem *P) {
           if (P->is_entry_edge && P->is_entry_edge[e])
             ev |= P->edge_mask[(size_t)b * W + w] & P->edge_src[(size_t)p * W + w];
           if (P->is_exit_edge && P->is_exit_edge[e]) ev |= P->exit_gen[(size_t)b * W + w];
+          if (P->any_mask) ev |= P->any_mask[(size_t)b * W + w] & P->any_src[(size_t)p * W + w];
           m[w] &= ev;
         }
       }
@@ -433,8 +475,8 @@ static int natural_loops(const graph *g, const uint64_t *KH, const uint64_t *KD,
   if ((rc = dominators(g, idom, rpo_num))) return rc;
   if ((rc = dom_intervals(g, idom, pre, post))) return rc;
   for (int b = 0; b < N; ++b) stamp[b] = -1;
-  memset(is_header, 0, (size_t)N);
-  memset(is_entry_edge, 0, (size_t)g->E);
+  for (int b = 0; b < N; ++b) is_header[b] = 0;
+  for (int e = 0; e < g->E; ++e) is_entry_edge[e] = 0;
   for (int h = 0; h < N; ++h) {
     if (!g->reach[h]) continue;
     int sp = 0, nb = 0;
@@ -803,7 +845,7 @@ int oracle_solve(const oracle_cfg *c, oracle_out *out) {
   }
   uint64_t *GH = pl[0], *KH = pl[1], *GD = pl[2], *KD = pl[3], *UH = pl[4], *UD = pl[5], *DF = pl[6];
   uint64_t *AH = pl[7], *AD = pl[8], *LV = pl[9], *HPI = pl[10], *HPO = pl[11];
-  uint64_t *MH = pl[14], *MD = pl[15];
+  uint64_t *AM = pl[12], *MH = pl[14], *MD = pl[15];
   uint64_t *DI = pl[16], *DO = pl[17], *HM = pl[18], *HI = pl[19], *HO = pl[20], *FX = pl[21];
   uint8_t *hdr = xcalloc((size_t)N, 1), *ent = xcalloc((size_t)E, 1);
   uint8_t *inr = xcalloc((size_t)N, 1), *rxe = xcalloc((size_t)E, 1);
@@ -837,9 +879,17 @@ int oracle_solve(const oracle_cfg *c, oracle_out *out) {
   /* 4. loops and masks */
   if ((rc = natural_loops(&g, KH, KD, UH, UD, DF, hdr, ent, MH, MD))) goto done;
   /* 5. device validity: hoisted `to' on loop-entry edges where the host
-        copy is valid (plain host validity as the source test) */
+        copy is valid (plain host validity as the source test); eager
+        placement: on every edge, what every path on reads on the device
+        first, where the host copy is the latest */
+  const int eager = c->eager_to != 0;
+  if (eager && (rc = must_anticipation(&g, UD, DF, AM))) goto done;
   {
     fwd_problem P = {GD, KD, init_d, ent, MD, HPO, NULL, DI, DO, NULL};
+    if (eager) {
+      P.any_mask = AM;
+      P.any_src = HPO;
+    }
     if ((rc = forward_must(&g, &P))) goto done;
   }
   /* 6. host validity: hoisted `from' on loop-entry edges where the device
@@ -863,8 +913,9 @@ int oracle_solve(const oracle_cfg *c, oracle_out *out) {
       for (int w = 0; w < W; ++w) {
         size_t ob = (size_t)b * W + w, op = (size_t)p * W + w, oe = (size_t)e * W + w;
         uint64_t hedge = HO[op];
+        if (eager) TE[oe] = AM[ob] & ~DO[op] & HPO[op];
         if (ent[e]) {
-          TE[oe] = MD[ob] & ~DO[op] & HPO[op];
+          TE[oe] |= MD[ob] & ~DO[op] & HPO[op];
           FE[oe] = MH[ob] & ~HO[op] & DO[op];
           hedge |= MH[ob] & DO[op];
         }
@@ -911,6 +962,7 @@ int oracle_solve(const oracle_cfg *c, oracle_out *out) {
   CP(out->acc_flag, fl, (size_t)g.A);
   CP(out->in_region, inr, (size_t)N);
   CP(out->region_exit, rxe, (size_t)E);
+  CP(out->ant_dm_in, AM, NW);
 #undef CP
   rc = ORACLE_OK;
 done:

@@ -76,6 +76,19 @@ typedef struct {
      stale data may be read on the host after exit from a target data
      region, the from map-type is included"). */
   int32_t data_region;
+  /* nonzero: eager `to' placement (Sec. IV-E: a `target update to' follows
+     the host write that produced the data, Algorithm 1 moving it past the
+     loops that sweep the array).  Read here as the earliest point after
+     the producing write from which EVERY path reads the variable on the
+     device before any write of it: AntDm (device-read must-anticipation,
+     ant_dm_in) holds there.  On every edge p->b the device copy is made
+     valid for AntDm_in[b] & Hp_out[p] (the host copy is the only latest
+     one), so a write inside a host loop gets its `to' on the loop's exit
+     edges, and a branch that leads to no device read gets none.  The
+     lazy rule (a `to' right before a device read that finds the device
+     copy stale) covers what is left, e.g. data valid on the host at the
+     function's entry. */
+  int32_t eager_to;
 } oracle_cfg;
 
 /* Every pointer is caller-allocated; any may be NULL (then not written).
@@ -101,6 +114,8 @@ typedef struct {
   /* data region (cfg->data_region with kernels; zero otherwise) */
   uint8_t *in_region;                            /* [N] block in R                   */
   uint8_t *region_exit;                          /* [E] edge from R to a block not in R */
+  /* eager `to' (cfg->eager_to; zero otherwise) */
+  uint64_t *ant_dm_in;                           /* [N*W] AntDm at block entry */
 } oracle_out;
 
 int oracle_solve(const oracle_cfg *cfg, oracle_out *out);
