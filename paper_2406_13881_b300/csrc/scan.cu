@@ -175,6 +175,13 @@ struct ScanDev {
   // to hdrl_* and the resolve folds it in
   uint64_t *pair_a;             // [N][W] PA of positions inside a loop
   uint64_t *hdrl_g, *hdrl_p;    // [L][W] liveness at an outermost loop's header (pair of the carry)
+  // a loop one level down is closed the same way with a fourth plane, the
+  // coefficient of its own header value A2: at its header A2 (a triple of
+  // the carry and A) goes to hdrl2_*; deeper loops are walked again until
+  // their header values stop changing
+  uint64_t *pair_a2;                     // [N][W] PA2 of positions inside a second-level loop
+  uint64_t *hdrl2_g, *hdrl2_p, *hdrl2_a;  // [L][W] A2 = G | (carry & P) | (A & PA) at its header
+  const int32_t *loop_d2;       // [L] second-level loop holding loop l (itself at that level), or -1
   uint64_t *src_g, *src_p;      // [K][W] out value at each loop-entry edge's source
   const int32_t *pos_chunk;     // [M] chunk of each position
   // forward walks take each loop body once, relative to the header's value;
@@ -1205,9 +1212,9 @@ __global__ void __launch_bounds__(32 * OMPDART_MAX_WPC, OMPDART_FWD_MIN_CTAS)
 // backward chain (anticipation; loop-restricted anticipation for the masks)
 // --------------------------------------------------------------------------------------
 template <int MODE>
-struct BwdPlanes {  // SUM: [Live local, carry coefficient, header coefficient];
+struct BwdPlanes {  // SUM: [Live local, carry coefficient, A coefficient, A2 coefficient];
                     // LANT: [H, D, H header coefficient, D header coefficient]
-  static constexpr int NP = MODE == M_SUM ? 3 : 4;
+  static constexpr int NP = 4;
 };
 
 template <int MODE>
@@ -1260,14 +1267,16 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
       top_ph = bi.y;
       // first visit: the header's value, read by the latches, starts from
       // nothing (outermost open loop: the latches read A itself, the
-      // header coefficient planes all ones); a re-entry keeps the previous
-      // visit's value
+      // header coefficient planes all ones; liveness, one level down: A2
+      // itself, plane 3 all ones); a re-entry keeps the previous visit's
+      // value
       if (i < lwm) {
-        const int hs = bi.w;
-        const bool sym = bi.x == base_depth + 1;  // planes from 2 on: header coefficients
+        const int hs = bi.w, rel = bi.x - base_depth;
         if (hs >= 0)
-          for (int pl = 0; pl < NP; ++pl)
-            sl.st(hs, pl, L.lane, sym && pl >= 2 ? make_ulonglong2(L.top0, L.top1) : make_ulonglong2(0ull, 0ull));
+          for (int pl = 0; pl < NP; ++pl) {
+            const bool one = LANT ? rel == 1 && pl >= 2 : (rel == 1 && pl == 2) || (rel == 2 && pl == 3);
+            sl.st(hs, pl, L.lane, one ? make_ulonglong2(L.top0, L.top1) : make_ulonglong2(0ull, 0ull));
+          }
         __syncwarp();
       }
     }
@@ -1317,6 +1326,9 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
     // value leaves the loop without the header planes.  Liveness keeps A
     // for the resolve; the loop masks need values at their own header only.
     const bool sym_close = is_top_header && depth == base_depth + 1;
+    // liveness, one level down: A2 = X | (A2 & PA2) likewise has the least
+    // solution X, a triple of the carry and A kept for the resolve
+    const bool sym2_close = MODE == M_SUM && is_top_header && depth == base_depth + 2;
     if (sym_close) {
       if (MODE == M_SUM) {
         st_pair(sd.hdrl_g, m.head_loop, W, L.w0, z[0][0], z[0][1]);
@@ -1325,24 +1337,30 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
 #pragma unroll
       for (int pl = 2; pl < NP; ++pl) z[pl][0] = z[pl][1] = 0;
     }
+    if (sym2_close) {
+      st_pair(sd.hdrl2_g, m.head_loop, W, L.w0, z[0][0], z[0][1]);
+      st_pair(sd.hdrl2_p, m.head_loop, W, L.w0, z[1][0], z[1][1]);
+      st_pair(sd.hdrl2_a, m.head_loop, W, L.w0, z[2][0], z[2][1]);
+      z[3][0] = z[3][1] = 0;
+    }
+    const bool rewalk = is_top_header && !sym_close && !sym2_close;
     if (m.bslot >= 0) {
       bool changed = false;
 #pragma unroll
       for (int pl = 0; pl < NP; ++pl) {
-        if (is_top_header && !sym_close) {
+        if (rewalk) {
           const ulonglong2 old = sl.ld(m.bslot, pl, L.lane);
           changed |= (old.x != z[pl][0]) || (old.y != z[pl][1]);
         }
         sl.st(m.bslot, pl, L.lane, make_ulonglong2(z[pl][0], z[pl][1]));
       }
-      if (is_top_header && !sym_close && __any_sync(0xffffffffu, changed)) dirty |= 1u << (depth - 1);
+      if (rewalk && __any_sync(0xffffffffu, changed)) dirty |= 1u << (depth - 1);
     }
-    if (MODE == M_SUM) {  // Live_in as an affine pair of the chunk's carry (and A inside a loop)
+    if (MODE == M_SUM) {  // Live_in as an affine pair of the chunk's carry (and A, A2 inside loops)
       st_pair_s(sd.pair_g, m.blk, W, L.w0, z[0][0], z[0][1]);
       st_pair_s(sd.pair_p, m.blk, W, L.w0, z[1][0], z[1][1]);
-      if (depth > base_depth) {
-        st_pair_s(sd.pair_a, m.blk, W, L.w0, z[NP - 1][0], z[NP - 1][1]);
-      }
+      if (depth > base_depth) st_pair_s(sd.pair_a, m.blk, W, L.w0, z[2][0], z[2][1]);
+      if (depth > base_depth + 1) st_pair_s(sd.pair_a2, m.blk, W, L.w0, z[3][0], z[3][1]);
     }
     __syncwarp();
 #pragma unroll
@@ -1558,8 +1576,18 @@ __global__ void __launch_bounds__(256) k_resolve(DevPlan p, ScanDev sd, const ui
       ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(P + o);
       const int pl = sd.pos_loop[i];
       if (KIND == RV_LIVE && pl >= 0) {
-        const int l = sd.loop_root[pl];
-        const ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(sd.pair_a + o);
+        const int l = sd.loop_root[pl], l2 = sd.loop_d2[pl];
+        ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(sd.pair_a + o);
+        if (l2 >= 0) {  // first A2 (a triple of the carry and A) through PA2
+          const size_t ol = (size_t)l2 * W + w;
+          const ulonglong2 a2 = *reinterpret_cast<const ulonglong2 *>(sd.pair_a2 + o);
+          const ulonglong2 x0 = *reinterpret_cast<const ulonglong2 *>(sd.hdrl2_g + ol);
+          const ulonglong2 x1 = *reinterpret_cast<const ulonglong2 *>(sd.hdrl2_p + ol);
+          const ulonglong2 x2 = *reinterpret_cast<const ulonglong2 *>(sd.hdrl2_a + ol);
+          g = make_ulonglong2(g.x | (x0.x & a2.x), g.y | (x0.y & a2.y));
+          q = make_ulonglong2(q.x | (x1.x & a2.x), q.y | (x1.y & a2.y));
+          a = make_ulonglong2(a.x | (x2.x & a2.x), a.y | (x2.y & a2.y));
+        }
         const ulonglong2 h0 = *reinterpret_cast<const ulonglong2 *>(sd.hdrl_g + (size_t)l * W + w);
         const ulonglong2 h1 = *reinterpret_cast<const ulonglong2 *>(sd.hdrl_p + (size_t)l * W + w);
         g = make_ulonglong2(g.x | (h0.x & a.x), g.y | (h0.y & a.y));
@@ -1580,8 +1608,15 @@ __global__ void __launch_bounds__(256) k_resolve(DevPlan p, ScanDev sd, const ui
         uint64_t g = G[o + u], q = P[o + u];
         const int pl = sd.pos_loop[i];
         if (KIND == RV_LIVE && pl >= 0) {
-          const int l = sd.loop_root[pl];
-          const uint64_t a = sd.pair_a[o + u];
+          const int l = sd.loop_root[pl], l2 = sd.loop_d2[pl];
+          uint64_t a = sd.pair_a[o + u];
+          if (l2 >= 0) {
+            const size_t ol = (size_t)l2 * W + w + u;
+            const uint64_t a2 = sd.pair_a2[o + u];
+            g |= sd.hdrl2_g[ol] & a2;
+            q |= sd.hdrl2_p[ol] & a2;
+            a |= sd.hdrl2_a[ol] & a2;
+          }
           g |= sd.hdrl_g[(size_t)l * W + w + u] & a;
           q |= sd.hdrl_p[(size_t)l * W + w + u] & a;
         }
@@ -2468,6 +2503,12 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
       loop_root[l] = up < 0 ? l : loop_root[up];
     }
     chk(sd.loop_root = st->up(loop_root));
+    std::vector<int32_t> loop_d2(g.L);
+    for (int l = 0; l < g.L; ++l) {
+      const int up = g.loop_parent[l];
+      loop_d2[l] = up < 0 ? -1 : g.loop_parent[up] < 0 ? l : loop_d2[up];
+    }
+    chk(sd.loop_d2 = st->up(loop_d2));
     trace_bm.next("scan state planes", g.M);
     chk(sd.hdr_g = st->alloc<uint64_t>((size_t)std::max(1, g.L) * W));
     chk(sd.hdr_p = st->alloc<uint64_t>((size_t)std::max(1, g.L) * W));
@@ -2475,8 +2516,12 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     chk(sd.hdr_ap = st->alloc<uint64_t>((size_t)std::max(1, g.L) * W));
     chk(sd.hdrl_g = st->alloc<uint64_t>((size_t)std::max(1, g.L) * W));
     chk(sd.hdrl_p = st->alloc<uint64_t>((size_t)std::max(1, g.L) * W));
+    chk(sd.hdrl2_g = st->alloc<uint64_t>((size_t)std::max(1, g.L) * W));
+    chk(sd.hdrl2_p = st->alloc<uint64_t>((size_t)std::max(1, g.L) * W));
+    chk(sd.hdrl2_a = st->alloc<uint64_t>((size_t)std::max(1, g.L) * W));
     const size_t NW = (size_t)g.N * W, KW = (size_t)std::max(1, g.K) * W;
     chk(sd.pair_a = st->alloc<uint64_t>(NW));
+    chk(sd.pair_a2 = st->alloc<uint64_t>(NW));
     chk(sd.pair_g = st->alloc<uint64_t>(NW));
     chk(sd.pair_p = st->alloc<uint64_t>(NW));
     chk(sd.pair_gd = st->alloc<uint64_t>(NW));
