@@ -334,6 +334,8 @@ def run_ours(args):
     g = wl.single_large(args.seed, n_blocks=args.n_blocks)
 
     plan = _native.Plan(g, device=local, chunk_target=args.chunk_target)
+    if not args.no_graph:
+        plan.graph(True)  # the first warm-up run captures the step; the others replay it
     stream = torch.cuda.Stream(device=local)
     sh = stream.cuda_stream
     for _ in range(args.warmup):
@@ -406,6 +408,7 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "u64", "data": "synthetic",
             "config": single_config(g, args.seed, world),
             "solver": "chunked scan" if plan.view().path == 2 else "sweep",
+            "launch": "kernel by kernel" if args.no_graph else "one CUDA graph per step (ompdart_plan_graph)",
             "roofline": roof,
             "cpu_baseline": {"value": cpu_val, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "%d of 64 word columns of the same CFG, single-threaded C oracle, %.1f s"
@@ -891,6 +894,8 @@ def main():
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-words", type=int, default=8)
+    ap.add_argument("--no-graph", action="store_true",
+                    help="single workload: launch every kernel of a step instead of replaying one CUDA graph")
     ap.add_argument("--chunk-target", type=int, default=0,
                     help="positions per chunk of the scan solver (0 = the library's choice)")
     ap.add_argument("--n-blocks", type=int, default=1 << 20,

@@ -177,7 +177,26 @@ typedef struct {
   int32_t data_region;  /* nonzero (CFGs with region): the single target data
                            region of Sec. IV-D and the directives (see
                            DATA REGION AND DIRECTIVES)                            */
+  int32_t eager_to;     /* nonzero: eager `to' placement (see EAGER `TO')        */
 } ompdart_opts;
+
+/* EAGER `TO' (opts.eager_to; Sec. IV-E, Algorithm 1: a `target update to'
+   follows the host write that produced the data, moved past the loops that
+   sweep the array).  By default a `to' is lazy: right before the device
+   read that finds the device copy stale, or hoisted onto a loop's entry
+   edges.  The eager placement first computes AntDm, the variables that
+   every path from a point reads on the device before any write of them
+   (a path that leaves the function first does not count), and then makes
+   the device copy valid on every edge p->b for AntDm_in[b] & Hp_out[p]
+   (Hp: the host copy is the latest one with no transfer).  The `to' thus
+   sits on the first edge after the producing write from which every path
+   reads the data on the device: a write inside a host loop gets it on the
+   loop's exit edges, a branch that reads nothing on the device gets none,
+   and no path makes more `to's than the lazy placement.  These transfers
+   are edge records (ompdart_edge_xfer.to_bits); a device read that still
+   finds its copy stale keeps its access flag.  Runs on the sweep solver
+   (path 1; path = 2 with eager_to is OMPDART_E_INVALID, and so is a CFG
+   with call pseudo-accesses); batches put every CFG on a plan of its own. */
 
 typedef struct {
   int32_t edge, word;
@@ -248,6 +267,17 @@ int ompdart_plan_view(ompdart_plan *plan, ompdart_result *view);
 /* Copy the results of the plan's last run to host memory; *out is
    library-owned (ompdart_result_free), mem = OMPDART_MEM_HOST. */
 int ompdart_plan_fetch(ompdart_plan *plan, ompdart_result **out);
+
+/* Graph replay of a plan's runs (enable != 0): the next ompdart_plan_run
+   captures the whole enqueue (every kernel, memset and the fork onto the
+   plan's side streams) into a CUDA graph on its stream and launches it;
+   later runs launch the same graph, on any stream, in one call.  A run
+   whose ompdart_plan_sync had to grow a buffer (an overflowed transfer
+   record stream) drops the graph and the next run captures it again.
+   Profiling (ompdart_plan_profile) takes precedence: profiled runs are
+   enqueued kernel by kernel.  enable = 0 waits for the last run and frees
+   the graph. */
+int ompdart_plan_graph(ompdart_plan *plan, int enable);
 
 /* Number of kernel launches one ompdart_plan_run enqueues. */
 int ompdart_plan_launches(const ompdart_plan *plan);
@@ -463,7 +493,8 @@ void ompdart_program_result_free(ompdart_program_result *res);
    differ per request) in a cache of device-resident plans: a hit uploads
    the request's entry and exit rows into the cached plan and runs it; a
    miss ingests the CFG into a new plan first (ompdart_plan_create) and
-   keeps it.  Runs of one cached plan are serialised; different plans run
+   keeps it.  A cached plan replays its run as one CUDA graph
+   (ompdart_plan_graph).  Runs of one cached plan are serialised; different plans run
    concurrently.  The plans' device bytes stay within hbm_budget_bytes:
    the least recently used idle plans are dropped to make room, and a
    request that still does not fit runs on a plan of its own that is

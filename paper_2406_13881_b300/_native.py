@@ -42,7 +42,8 @@ class Cfg(C.Structure):
 class Opts(C.Structure):
     _fields_ = [("max_sweeps", C.c_int32), ("keep_states", C.c_int32), ("path", C.c_int32),
                 ("chunk_target", C.c_int32), ("device", C.c_int32), ("warps_per_cta", C.c_int32),
-                ("tune", C.c_int32), ("no_graph", C.c_int32), ("data_region", C.c_int32)]
+                ("tune", C.c_int32), ("no_graph", C.c_int32), ("data_region", C.c_int32),
+                ("eager_to", C.c_int32)]
 
 
 class EdgeXfer(C.Structure):
@@ -110,6 +111,7 @@ class Timing(C.Structure):
 
 EXPORTS = {
     "ompdart_plan_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "ompdart_plan_graph": (C.c_int, [C.c_void_p, C.c_int]),
     "ompdart_plan_timings": (C.c_int, [C.c_void_p, C.POINTER(Timing), C.c_int32, C.POINTER(C.c_int32)]),
     "ompdart_batch_profile": (C.c_int, [C.c_void_p, C.c_int]),
     "ompdart_batch_timings": (C.c_int, [C.c_void_p, C.POINTER(Timing), C.c_int32, C.POINTER(C.c_int32)]),
@@ -233,9 +235,10 @@ class _Inputs:
 
 
 def _opts(max_sweeps=0, keep_states=False, path=0, chunk_target=0, device=0, warps_per_cta=0, tune=False,
-          no_graph=False, data_region=False):
+          no_graph=False, data_region=False, eager_to=False):
     return Opts(int(max_sweeps), int(bool(keep_states)), int(path), int(chunk_target), int(device),
-                int(warps_per_cta), int(bool(tune)), int(bool(no_graph)), int(bool(data_region)))
+                int(warps_per_cta), int(bool(tune)), int(bool(no_graph)), int(bool(data_region)),
+                int(bool(eager_to)))
 
 
 class _Owned:
@@ -341,6 +344,10 @@ class Plan:
 
     def sync(self):
         _check(self._lib.ompdart_plan_sync(self._h))
+
+    def graph(self, enable: bool = True):
+        """Replay later runs as one captured CUDA graph."""
+        _check(self._lib.ompdart_plan_graph(self._h, int(bool(enable))))
 
     def view(self) -> Result:
         r = Result()

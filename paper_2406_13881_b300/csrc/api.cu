@@ -290,9 +290,9 @@ int core_build(PlanCore *P, const int32_t *acc_off, const uint32_t *acc, const C
     d.n_sites = (int)site_acc.size();
     d.n_cblk = (int)cblk.size();
     if (d.n_sites) {
-      if (!scan_supported(g) || o.path == 1) {
+      if (!scan_supported(g) || o.path == 1 || o.eager_to) {
         *err = "CFGs with call pseudo-accesses need the chunked scan solver (a reducible CFG whose loop bodies "
-               "are contiguous in loop order)";
+               "are contiguous in loop order, lazy `to' placement)";
         return OMPDART_E_INVALID;
       }
       const size_t SW = (size_t)d.n_sites * W;
@@ -315,6 +315,13 @@ int core_build(PlanCore *P, const int32_t *acc_off, const uint32_t *acc, const C
     P->site_acc = std::move(site_acc);
   }
   int want = o.path;
+  if (o.eager_to) {  // eager `to' placement runs on the sweep solver
+    if (want == 2) {
+      *err = "eager `to' placement runs on the sweep solver (path 1)";
+      return OMPDART_E_INVALID;
+    }
+    want = 1;
+  }
   if (want == 0) want = scan_supported(g) ? 2 : 1;
   if (want == 2 && !scan_supported(g)) {
     *err = "the chunked scan solver needs a reducible CFG whose loop bodies are contiguous in loop order";
@@ -330,6 +337,7 @@ int core_build(PlanCore *P, const int32_t *acc_off, const uint32_t *acc, const C
     chk(d.hp_out = P->dalloc<uint64_t>(NW));
     chk(d.ant_h = P->dalloc<uint64_t>(NW));
     chk(d.ant_d = P->dalloc<uint64_t>(NW));
+    if (o.eager_to) chk(d.ant_dm = P->dalloc<uint64_t>(NW));
     chk(d.lant = P->dalloc<uint64_t>(g.body_blk.size() * (size_t)W * 2));
   } else {
     chk(P->cfg_err = P->dalloc<int32_t>(n_cfg));
@@ -555,10 +563,20 @@ struct ompdart_plan {
   int launches = 0;
   int32_t *h_status = nullptr;  // pinned
   Prof prof;
+  // graph replay: the first run after enabling is captured into a CUDA
+  // graph and later runs launch it whole; a run that changes the plan's
+  // buffers (record streams grown after an overflow) drops it
+  bool graph_on = false;
+  cudaGraphExec_t gexec = nullptr;
+  void drop_graph() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+  }
   ~ompdart_plan() {
     // the plan's memory goes back to the pool: its last run must be done
     if (last_stream) cudaStreamSynchronize(last_stream);
     if (stream) cudaStreamSynchronize(stream);
+    drop_graph();
     if (stream) cudaStreamDestroy(stream);
     if (h_status) cudaFreeHost(h_status);
   }
@@ -653,11 +671,39 @@ int ompdart_plan_run(ompdart_plan *P, void *stream) {
   P->last_stream = s;
   (void)cudaGetLastError();  // clear a stale "not ready" of an earlier query
   Prof *pf = P->prof.on ? &P->prof : nullptr;
+  if (P->graph_on && !pf) {
+    if (!P->gexec) {
+      cudaGraph_t g = nullptr;
+      cudaError_t ce = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+      if (ce != cudaSuccess) return cuda_err(ce, "graph capture");
+      P->launches = core_enqueue(&P->core, s, nullptr);
+      ce = cudaStreamEndCapture(s, &g);
+      if (ce == cudaSuccess) ce = cudaGraphInstantiate(&P->gexec, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (ce != cudaSuccess) {
+        P->gexec = nullptr;
+        return cuda_err(ce, "graph capture");
+      }
+    }
+    const cudaError_t ce = cudaGraphLaunch(P->gexec, s);
+    if (ce != cudaSuccess) return cuda_err(ce, "graph launch");
+    return OMPDART_OK;
+  }
   if (pf) pf->collect_pending = true;
   P->launches = core_enqueue(&P->core, s, pf);
   if (pf) pf->close(s);
   cudaError_t ce = cudaGetLastError();
   if (ce != cudaSuccess) return cuda_err(ce, "kernel launch");
+  return OMPDART_OK;
+}
+
+int ompdart_plan_graph(ompdart_plan *P, int enable) {
+  if (!P) return set_err(OMPDART_E_INVALID, "plan is NULL");
+  P->graph_on = enable != 0;
+  if (!P->graph_on) {
+    if (P->last_stream) cudaStreamSynchronize(P->last_stream);
+    P->drop_graph();
+  }
   return OMPDART_OK;
 }
 
@@ -676,6 +722,7 @@ int ompdart_plan_sync(ompdart_plan *P) {
     return set_err(OMPDART_E_NOCONVERGE, "a device fixed-point loop reached max_sweeps");
   bool rerun = false;
   int rc = core_finish(&P->core, s, P->h_status, &rerun);
+  if (rerun) P->drop_graph();  // its launches hold the old buffers
   if (rc) return rc;
   if (P->h_status[ST_ERROR] == ERR_NOCONVERGE)
     return set_err(OMPDART_E_NOCONVERGE, "a device fixed-point loop reached max_sweeps");

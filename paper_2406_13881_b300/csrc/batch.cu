@@ -469,7 +469,7 @@ int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts 
   std::vector<int32_t> solo_ids;
   for (int i = 0; i < n; ++i) {
     if (B->ingest_status[i]) continue;
-    if (scan_supported(*ingp[i]))
+    if (scan_supported(*ingp[i]) && !o.eager_to)  // eager placement: the sweep solver
       by_w[ingp[i]->W].push_back(i);
     else
       solo_ids.push_back(i);

@@ -70,6 +70,9 @@ HostBlock *host_block_new(size_t bytes, bool pin) {
   HostBlock *b = new (std::nothrow) HostBlock();
   if (!b) return nullptr;
   b->bytes = bytes ? bytes : 1;
+  // a small block is not worth page-locking: cudaHostAlloc costs far more
+  // than the staged copy it saves, and it serialises concurrent callers
+  if (b->bytes < kCacheMin) pin = false;
   if (b->bytes >= kCacheMin) {
     Cache &c = cache();
     b->bytes = size_class(b->bytes);

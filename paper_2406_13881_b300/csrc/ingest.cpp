@@ -1,6 +1,7 @@
 // ingest.cpp -- host-side ingestion of one CFG (see ingest.h).
 #include "ingest.h"
 #include "parallel.h"
+#include "solver.h"
 
 #include <algorithm>
 #include <cstring>
@@ -345,6 +346,7 @@ int ingest(const ompdart_cfg *c, Ingest *g, std::string *err, bool data_region) 
   g->entry = c->entry;
   std::vector<int32_t> so(c->succ_off, c->succ_off + N + 1);
   const int32_t *succ = c->succ;
+  TraceScope trace("ingest: predecessors", N);
 
   // predecessor CSR with edge ids
   std::vector<int32_t> po(N + 1, 0), psrc(g->E), peid(g->E);
@@ -361,6 +363,7 @@ int ingest(const ompdart_cfg *c, Ingest *g, std::string *err, bool data_region) 
   }
 
   // dominators on the reachable subgraph
+  trace.next("ingest: dominators", N);
   std::vector<int32_t> pre, dfn, idom;
   lengauer_tarjan(N, c->entry, so, succ, po, psrc, &pre, &dfn, &idom);
   const int n_reach = (int)pre.size();
@@ -387,6 +390,7 @@ int ingest(const ompdart_cfg *c, Ingest *g, std::string *err, bool data_region) 
   };
 
   // natural loops; headers in decreasing DFS preorder = inner loops first
+  trace.next("ingest: natural loops", n_reach);
   std::vector<uint8_t> is_head(n_reach, 0);
   parallel_ranges(n_reach, kParMin, kParMax, [&](int, int lo, int hi) {
     for (int i = lo; i < hi; ++i) {
@@ -472,6 +476,7 @@ int ingest(const ompdart_cfg *c, Ingest *g, std::string *err, bool data_region) 
   // loop-ordered DFS: at every block visit successors that leave the most
   // loops first, so that their subtrees finish first and every loop body
   // ends up as one run of positions right after its header.
+  trace.next("ingest: loop-ordered DFS", n_reach);
   std::vector<int32_t> post;
   post.reserve(pre.size());
   {
@@ -531,6 +536,7 @@ int ingest(const ompdart_cfg *c, Ingest *g, std::string *err, bool data_region) 
                  }) == M;
 
   // loops renumbered by header position
+  trace.next("ingest: loop tables", L);
   std::vector<int32_t> perm(L);
   for (int l = 0; l < L; ++l) perm[l] = l;
   std::sort(perm.begin(), perm.end(), [&](int a, int b) { return g->pos[headers[a]] < g->pos[headers[b]]; });
@@ -611,6 +617,7 @@ int ingest(const ompdart_cfg *c, Ingest *g, std::string *err, bool data_region) 
   for (int k = 0; k < g->K; ++k) g->ent_dst[k] = succ[g->ent_eid[k]];
 
   // position-ordered edge lists (counted, then filled, in parallel over positions)
+  trace.next("ingest: edge lists", M);
   g->fin_off.assign(M + 1, 0);
   g->out_off.assign(M + 1, 0);
   g->is_exit.assign(M, 0);

@@ -72,6 +72,8 @@ struct DevPlan {
   uint64_t *h_in, *d_in, *h_out, *d_out;
   uint64_t *hp_out, *live;
   uint64_t *ant_h, *ant_d;
+  // eager `to' placement (sweep solver): AntDm at block entry, or null
+  uint64_t *ant_dm;
   // loop planes [L*W], loop-entry edge constants [K*W]
   uint64_t *mask_h, *mask_d;
   uint64_t *ec_h, *ec_d;

@@ -89,9 +89,45 @@ __global__ void k_sweep_ant(DevPlan p) {
   }
 }
 
+// ---- eager `to': must-anticipation of device reads (Sec. IV-E) --------------------
+// AntDm_in[b] = UED[b] | (AntDm_out[b] & ~Def[b]); AntDm_out[b] = AND of the
+// successors' AntDm_in, nothing for a block without successors.  Greatest
+// fixed point from all ones: v is in it where every path reads v on the
+// device before any write of v.
+__global__ void k_sweep_antm(DevPlan p) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= p.W) return;
+  const int W = p.W;
+  const uint64_t top = p.top[w];
+  for (int i = 0; i < p.M; ++i) p.ant_dm[(size_t)p.order[i] * W + w] = top;
+  int sweeps = 0;
+  bool changed = true;
+  while (changed) {
+    if (sweeps >= p.max_sweeps) { atomicExch(&p.status[ST_ERROR], ERR_NOCONVERGE); break; }
+    changed = false;
+    ++sweeps;
+    for (int i = p.M - 1; i >= 0; --i) {
+      const int b = p.order[i];
+      uint64_t x = p.out_off[i] == p.out_off[i + 1] ? 0ull : top;
+      for (int k = p.out_off[i]; k < p.out_off[i + 1]; ++k) x &= p.ant_dm[(size_t)p.out_dst[k] * W + w];
+      for (int r = p.acc_off[b]; r < p.acc_off[b + 1]; ++r) {
+        const uint32_t rc = p.rec[r];
+        if (rc == REC_NONE || (acc_var(rc) >> 6) != w) continue;
+        const uint64_t bit = 1ull << (acc_var(rc) & 63);
+        if (rc & R_UD) x |= bit; else if (rc & R_DF) x &= ~bit;
+      }
+      const size_t o = (size_t)b * W + w;
+      if (x != p.ant_dm[o]) { p.ant_dm[o] = x; changed = true; }
+    }
+  }
+  atomicMax(&p.status[ST_SWEEPS], sweeps);
+}
+
 // ---- forward must problems (Sec. IV-D) -------------------------------------------
 // PH_HP: plain host validity (host access -> valid, device write -> stale)
-// PH_D : device validity; loop-entry edges add the hoisted `to' set
+// PH_D : device validity; loop-entry edges add the hoisted `to' set; with
+//        eager placement every edge p->b adds AntDm_in[b] & Hp_out[p] (what
+//        every path on reads on the device first, from the latest host copy)
 // PH_H : host validity; loop-entry edges add the hoisted `from' set, and a
 //        live variable valid in neither space after the join is resolved
 //        toward the host (a `from' on the disagreeing in-edges).
@@ -124,6 +160,7 @@ __global__ void k_sweep_fwd(DevPlan p) {
         for (int k = p.fin_off[i]; k < p.fin_off[i + 1]; ++k) {
           uint64_t v = out[(size_t)p.fin_src[k] * W + w];
           if (PH != PH_HP && p.fin_ent[k] >= 0) v |= ec[(size_t)p.fin_ent[k] * W + w];
+          if (PH == PH_D && p.ant_dm) v |= p.ant_dm[(size_t)b * W + w] & p.hp_out[(size_t)p.fin_src[k] * W + w];
           x &= v;
         }
       }
@@ -257,17 +294,20 @@ __global__ void k_emit_flags(DevPlan p) {
   }
 }
 
-// Edge transfers: hoisted `to'/`from' on loop-entry edges; `from' on any
-// in-edge where a live variable valid in neither space after the join is
-// not host-valid on that edge.
+// Edge transfers: hoisted `to'/`from' on loop-entry edges; eager `to' on
+// any edge (AntDm at the target, the host copy the latest at the source,
+// the device copy stale); `from' on any in-edge where a live variable valid
+// in neither space after the join is not host-valid on that edge.
 __global__ void k_emit_edges(DevPlan p, int n_fin) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (t >= (long long)n_fin * p.W) return;
   const int k = (int)(t / p.W), w = (int)(t % p.W), W = p.W;
   const int src = p.fin_src[k], dst = p.fin_dst[k], ent = p.fin_ent[k];
   uint64_t hedge = p.h_out[(size_t)src * W + w], to = 0, fr = 0;
+  if (p.ant_dm)
+    to = p.ant_dm[(size_t)dst * W + w] & p.hp_out[(size_t)src * W + w] & ~p.d_out[(size_t)src * W + w];
   if (ent >= 0) {
-    to = p.ec_d[(size_t)ent * W + w] & ~p.d_out[(size_t)src * W + w];
+    to |= p.ec_d[(size_t)ent * W + w] & ~p.d_out[(size_t)src * W + w];
     fr = p.ec_h[(size_t)ent * W + w] & ~p.h_out[(size_t)src * W + w];
     hedge |= p.ec_h[(size_t)ent * W + w];
   }
@@ -333,6 +373,7 @@ int enqueue_sweep_solver(const DevPlan &p, cudaStream_t s, int n_fin, Prof *pf) 
   cudaMemsetAsync(p.acc_flag, 0, (size_t)p.A, s);
   PROF("sweep_ant");
   k_sweep_ant<<<grid_for(p.W, T), T, 0, s>>>(p); ++n;
+  if (p.ant_dm) { PROF("sweep_antm"); k_sweep_antm<<<grid_for(p.W, T), T, 0, s>>>(p); ++n; }
   PROF("sweep_hp");
   k_sweep_fwd<PH_HP><<<grid_for(p.W, T), T, 0, s>>>(p); ++n;
   if (p.L) { PROF("sweep_masks"); k_sweep_masks<<<grid_for((long long)p.L * p.W, T), T, 0, s>>>(p); ++n; }

@@ -100,6 +100,28 @@ def test_plan_reuse_is_deterministic():
     p.close()
 
 
+@pytest.mark.parametrize("path", [1, 2])
+def test_graph_replay_equals_oracle(path):
+    """Runs replayed as one captured CUDA graph (the first run captures,
+    the next ones launch it) give the oracle's answer every time, with and
+    without the data region, and stay right after graph replay is switched
+    off again."""
+    for seed, region in ((3, False), (4, True)):
+        g = wl.single_small(seed)
+        orc = oracle.solve(g, data_region=region)
+        p = _native.Plan(g, path=path, keep_states=True, data_region=region)
+        p.graph(True)
+        for _ in range(3):
+            p.run()
+            p.sync()
+            assert_matches_oracle(g, p.fetch(), orc)
+        p.graph(False)
+        p.run()
+        p.sync()
+        assert_matches_oracle(g, p.fetch(), orc)
+        p.close()
+
+
 # --------------------------------------------------------------------------
 # chunked scan solver
 # --------------------------------------------------------------------------
