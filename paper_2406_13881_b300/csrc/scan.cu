@@ -1680,6 +1680,22 @@ constexpr int EMIT_SPAN = OMPDART_EMIT_SPAN;  // positions per emission item (it
 #ifndef OMPDART_EMIT_MIN_CTAS
 #define OMPDART_EMIT_MIN_CTAS 10
 #endif
+// H_out (valid) of position i, block b, resolved from the host-validity
+// walk's pairs: composed with the innermost loop's header, then the carry
+// `car' of the position's chunk (G | (carry & P), as a stale set)
+__device__ __forceinline__ ulonglong2 h_out_at(const ScanDev &sd, size_t b, int i, int W, int w0, uint64_t car0,
+                                               uint64_t car1, uint64_t top0, uint64_t top1) {
+  const ulonglong2 g = ld_pair_s(sd.pair_g, b, W, w0), q = ld_pair_s(sd.pair_p, b, W, w0);
+  uint64_t g0 = g.x, g1 = g.y, q0 = q.x, q1 = q.y;
+  const int lp = sd.pos_loop[i];
+  if (lp >= 0) {
+    const ulonglong2 h0 = ld_pair(sd.hdr_ag, lp, W, w0), h1 = ld_pair(sd.hdr_ap, lp, W, w0);
+    compose_pair(g0, q0, h0.x, h1.x);
+    compose_pair(g1, q1, h0.y, h1.y);
+  }
+  return make_ulonglong2(~(g0 | (car0 & q0)) & top0, ~(g1 | (car1 & q1)) & top1);
+}
+
 __global__ void __launch_bounds__(32 * EMIT_WARPS, OMPDART_EMIT_MIN_CTAS)
     k_emit(DevPlan p, ScanDev sd, const uint64_t *init) {
   __shared__ uint64_t hd_all[EMIT_WARPS][128];
@@ -1688,16 +1704,26 @@ __global__ void __launch_bounds__(32 * EMIT_WARPS, OMPDART_EMIT_MIN_CTAS)
   const int item = gw / sd.G, wg = gw % sd.G, lane = threadIdx.x & 31, W = p.W;
   uint64_t *hd = hd_all[threadIdx.x >> 5];
   const int2 rng = sd.emit_rng[item];
-  const ChunkMeta cm = sd.chunks[sd.pos_chunk[rng.x]];
+  const int ci = sd.pos_chunk[rng.x];
+  const ChunkMeta cm = sd.chunks[ci];
   const int w0 = wg * 64 + 2 * lane;
   const uint64_t *tp = p.top + (size_t)cm.cfg * W;
   const uint64_t top0 = w0 < W ? tp[w0] : 0, top1 = w0 + 1 < W ? tp[w0 + 1] : 0;
   const uint64_t *xl = p.exit_live + (size_t)cm.cfg * W;
   const int stream = item * sd.G + wg;
+  // H_out is resolved here, not in a pass of its own: each position's own
+  // value (kept for the next position, whose in-edge from it is the usual
+  // one), and a source elsewhere from its pairs and its chunk's carry
+  ulonglong2 prev_ho = make_ulonglong2(0ull, 0ull);
   int rec_count = 0;
   for (int i = rng.x; i < rng.y; ++i) {
     const PosMeta m = sd.meta[i];
     const size_t b = (size_t)m.blk;
+    ulonglong2 own_ho;
+    {
+      const ulonglong2 hcar = ld_pair(sd.carry, ci, W, w0);  // the same row all item long: cached
+      own_ho = h_out_at(sd, b, i, W, w0, hcar.x, hcar.y, top0, top1);
+    }
     const ulonglong2 lv = ld_pair_s(p.live, b, W, w0), di = ld_pair_s(p.d_in, b, W, w0);
     const uint64_t lv0 = lv.x, lv1 = lv.y, di0 = di.x, di1 = di.y;
     const uint64_t c0 = lv0 & ~di0, c1 = lv1 & ~di1;
@@ -1708,9 +1734,17 @@ __global__ void __launch_bounds__(32 * EMIT_WARPS, OMPDART_EMIT_MIN_CTAS)
     }
     for (int q = 0; q < m.nfin; ++q) {
       const int k = m.fin_beg + q;
-      const int ent = sd.fin_pk[k].y;  // loop-entry edge or -1
+      const int2 fk = sd.fin_pk[k];
+      const int ent = fk.y;  // loop-entry edge or -1
       const size_t src = (size_t)p.fin_src[k];
-      const ulonglong2 ho = ld_pair_s(p.h_out, src, W, w0);
+      ulonglong2 ho;
+      if (fk.x == PREV && i > rng.x) {
+        ho = prev_ho;
+      } else {
+        const int sp = p.pos[src], sc = sd.pos_chunk[sp];
+        const ulonglong2 car = ld_pair(sd.carry, sc, W, w0);
+        ho = h_out_at(sd, src, sp, W, w0, car.x, car.y, top0, top1);
+      }
       const uint64_t s0 = ~ho.x & top0, s1 = ~ho.y & top1;
       uint64_t m0 = 0, m1 = 0, to0 = 0, to1 = 0;
       if (ent >= 0) {
@@ -1755,10 +1789,11 @@ __global__ void __launch_bounds__(32 * EMIT_WARPS, OMPDART_EMIT_MIN_CTAS)
       __syncwarp();
     }
     if (m.exit_idx >= 0) {  // region exit: live after it and stale on the host
-      if (w0 < W) st_word(p.from_exit, m.exit_idx, W, w0, xl[w0] & ~ld_word(p.h_out, b, W, w0) & top0);
-      if (w0 + 1 < W)
-        st_word(p.from_exit, m.exit_idx, W, w0 + 1, xl[w0 + 1] & ~ld_word(p.h_out, b, W, w0 + 1) & top1);
+      if (w0 < W) st_word(p.from_exit, m.exit_idx, W, w0, xl[w0] & ~own_ho.x & top0);
+      if (w0 + 1 < W) st_word(p.from_exit, m.exit_idx, W, w0 + 1, xl[w0 + 1] & ~own_ho.y & top1);
     }
+    if (sd.keep_states) st_pair_s(p.h_out, b, W, w0, own_ho.x, own_ho.y);
+    prev_ho = own_ho;
   }
   if (lane == 0) sd.rec_cnt[stream] = rec_count;
 }
@@ -2572,8 +2607,10 @@ static int run_emission(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *p
   ScanDev &sd = st->sd;
   int32_t *offs = st->offs;
   const long long nw = (long long)sd.n_emit * sd.G;
+  ScanDev se = sd;  // the forward problems' chunk carries (host validity's, the last scanned)
+  se.carry = sd.carry + (size_t)sd.C * p.W;
   PROF("emit");
-  k_emit<<<grid_of(nw * 32, 32 * EMIT_WARPS), 32 * EMIT_WARPS, 0, s>>>(p, sd, st->init);
+  k_emit<<<grid_of(nw * 32, 32 * EMIT_WARPS), 32 * EMIT_WARPS, 0, s>>>(p, se, st->init);
   PROF("streams_prefix");
   const int n_parts = (sd.n_streams + PF_TILE - 1) / PF_TILE;
   k_streams_sums<<<std::max(1, n_parts), PF_T, 0, s>>>(sd, st->part, p.status);
@@ -2702,8 +2739,7 @@ int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *p
     PROF("loop_abs");
     k_loop_abs<<<grid_of((long long)p.L * W, 256), 256, 0, s>>>(p, sq); ++n;
   }
-  PROF("h_resolve");
-  k_resolve<RV_VALID><<<grid_of((nw + 1) / 2, 256), 256, 0, s>>>(p, sq, sq.pair_g, sq.pair_p, p.h_out); ++n;
+  // (H_out is resolved by the emission)
   n += run_emission(st, p, s, pf);
   return n;
 }
