@@ -62,12 +62,12 @@ def workload_name(n_blocks):
 # names the commit its capture was taken at, and an entry is removed when
 # its kernel changes.
 MEASURED_TRAFFIC = {
-    "h_summary": {"bytes_2e18": (319307008 + 269504768 + 319343360 + 268663296) / 2.0,
-                  "profile": "profiles/h_summary_walk_2e18.md", "captured_at": "a70c254"},
-    "live_summary": {"bytes_2e18": (40253184 + 359559168 + 40314112 + 357505792) / 2.0,
-                     "profile": "profiles/live_summary_walk_2e18.md", "captured_at": "a70c254"},
-    "emit": {"bytes_2e18": (489899776 + 96055552 + 489456384 + 93677824) / 2.0,
-             "profile": "profiles/emit_2e18.md", "captured_at": "f047219"},
+    "h_summary": {"bytes_2e18": (319428096 + 268645376),
+                  "profile": "profiles/h_summary_walk_2e18.md", "captured_at": "a52a605"},
+    "live_summary": {"bytes_2e18": (38950144 + 365891328 + 38896384 + 364616960) / 2.0,
+                     "profile": "profiles/live_summary_walk_2e18.md", "captured_at": "a52a605"},
+    "emit": {"bytes_2e18": (743276288 + 110661632 + 743400448 + 110947584 + 743296256 + 110883584) / 3.0,
+             "profile": "profiles/emit_2e18.md", "captured_at": "a52a605"},
 }
 # the survey's per-phase traffic model for a dense-state design: about 140 B
 # per block-word for the whole step (Ant 37, Hp 18, D 19, H 34, emission 32)
@@ -93,7 +93,11 @@ def byte_model(st):
     structure read once per walk, each dense plane read or written once).
     A chain walk reads per position its 64 B position record, 8 B per edge
     entry and 4 B per access record (`walk`); a dense plane is W words of
-    8 B per block; loop-entry edge constants are W words per edge."""
+    8 B per block; loop-entry edge constants are W words per edge.  The
+    emission resolves H_out itself: each position's own pair (two planes),
+    kept for the next position, and the pair of every other in-edge's
+    source, counted as the in-edges beyond one per position plus one per
+    8-position emission item (the positions whose previous one is elsewhere)."""
     N, M, E, A, W, K, L = (st[k] for k in ("N", "M", "E", "A", "W", "K", "L"))
     G = (W + 63) // 64
     plane = 8.0 * W * N
@@ -101,6 +105,8 @@ def byte_model(st):
     in_loop = 8.0 * W * st["in_loop"]                  # a plane's rows of the blocks inside loops
     hdr = 2 * 8.0 * W * L                               # one header pair per loop
     hdr_top = 2 * 8.0 * W * st["L_top"]
+    in_loop2 = 8.0 * W * st.get("in_loop2", 0.0)
+    hdr_2 = 3 * 8.0 * W * st.get("L_2", 0)              # a header triple per second-level loop
     walk = G * (M * 64.0 + E * 8.0 + A * 4.0)
     # two pair planes in, one plane out; forward pairs also take the loop
     # tree (a loop id per position and loop, each header pair once)
@@ -108,16 +114,18 @@ def byte_model(st):
     fwd_resolve = resolve + 4.0 * (M + L) + hdr
     return {
         "local_summary": A * 20.0,                      # access, link in; record, emission word out
-        "live_summary": walk + 2 * plane + in_loop + hdr_top,  # Live pairs, the header plane inside loops
-        "live_resolve": resolve + in_loop + 4.0 * (M + L) + hdr_top,
+        # Live pairs, the header planes inside loops (two levels)
+        "live_summary": walk + 2 * plane + in_loop + in_loop2 + hdr_top + hdr_2,
+        "live_resolve": resolve + in_loop + in_loop2 + 8.0 * (M + L) + hdr_top + hdr_2,
         "loop_masks": G * st["body"] * (64.0 + 4.0 * A / max(1, M) + 8.0 * E / max(1, M)) + 2 * L * 8.0 * W,
         "hp_summary": walk + 2 * edge_plane + hdr,      # pairs at loop-entry sources, header pairs
         "src_resolve": 4.5 * edge_plane,                # pairs and loop masks in; edge constants (and D) out
         "d_summary": walk + 3 * edge_plane + 2 * plane + hdr,  # reads `to' constants; writes D_in pairs
         "d_resolve": fwd_resolve,
         "h_summary": walk + edge_plane + 4 * plane + hdr,  # reads Live, D_in; writes H_out pairs
-        "h_resolve": fwd_resolve,
-        "emit": 4 * plane + E * 8.0 * W + M * 64.0 + E * 16.0 + A * 9.0 + 3 * edge_plane,
+        # reads Live, D_in and the H pairs; writes H_in; other sources' H pairs
+        "emit": 5 * plane + (max(0, E - M) + M / 8.0) * 16.0 * W + M * 64.0 + E * 16.0 + A * 9.0
+                + 3 * edge_plane,
     }
 
 
@@ -249,6 +257,9 @@ def workload_stats(g):
     # blocks inside some loop (the bodies of the outermost loops) and those loops
     st["in_loop"] = float(sum(e - h for h, _, e, d in loops if d == 1))
     st["L_top"] = sum(1 for *_, d in loops if d == 1)
+    # the same one level down (liveness closes those loops with a fourth plane)
+    st["in_loop2"] = float(sum(e - h for h, _, e, d in loops if d == 2))
+    st["L_2"] = sum(1 for *_, d in loops if d == 2)
     return st
 
 
@@ -912,7 +923,7 @@ def main():
     ap.add_argument("--large-blocks", type=int, default=1 << 16)
     ap.add_argument("--budget-gb", type=int, default=40)
     ap.add_argument("--inflight", type=int, default=2)
-    ap.add_argument("--workers", type=int, default=8, help="serve: worker threads of the resident mode")
+    ap.add_argument("--workers", type=int, default=4, help="serve: worker threads of the resident mode")
     ap.add_argument("--n-cfgs", type=int, default=10000, help="CFGs of the batch workload")
     ap.add_argument("--batch-seed", type=int, default=3)
     ap.add_argument("--tune", type=int, default=1, help="batch: autotune the arenas' launch shapes")
