@@ -487,15 +487,17 @@ void ompdart_program_result_free(ompdart_program_result *res);
    launch sequence per request.
 
    RESIDENT MODE (resident != 0): CFGs stay on the device between requests.
-   `workers' threads, each with its own stream, take requests in arrival
-   order.  A request's CFG is looked up by its content (graph, accesses,
+   `workers' threads take requests in arrival order, up to 16 at a time
+   each.  A request's CFG is looked up by its content (graph, accesses,
    call table, kernels and scalars; not the entry and exit rows, which can
    differ per request) in a cache of device-resident plans: a hit uploads
    the request's entry and exit rows into the cached plan and runs it; a
    miss ingests the CFG into a new plan first (ompdart_plan_create) and
    keeps it.  A cached plan replays its run as one CUDA graph
-   (ompdart_plan_graph).  Runs of one cached plan are serialised; different plans run
-   concurrently.  The plans' device bytes stay within hbm_budget_bytes:
+   (ompdart_plan_graph).  Each request of a group runs on a stream of its
+   own, so the group runs on the device together; the worker then waits
+   for each in turn and copies its results back.  Runs of one cached plan
+   are serialised; different plans run concurrently.  The plans' device bytes stay within hbm_budget_bytes:
    the least recently used idle plans are dropped to make room, and a
    request that still does not fit runs on a plan of its own that is
    freed afterwards.  max_batch and max_inflight are not used. */
@@ -508,7 +510,7 @@ typedef struct {
   int32_t keep_results;     /* nonzero: copy each result to the host for the waiter */
   ompdart_opts opts;        /* analysis options of every batch                      */
   int32_t resident;         /* nonzero: resident mode (see below)                   */
-  int32_t workers;          /* resident mode: worker threads; 0 = 8                 */
+  int32_t workers;          /* resident mode: worker threads; 0 = 4                 */
 } ompdart_server_opts;
 
 typedef struct {

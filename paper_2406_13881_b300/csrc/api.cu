@@ -459,7 +459,7 @@ void core_view(const PlanCore &P, const int32_t *h_status, ompdart_result *v) {
   }
 }
 
-int result_copy(const ompdart_result &v, bool pin, cudaStream_t s, ompdart_result **out) {
+int result_copy(const ompdart_result &v, bool pin, cudaStream_t s, ompdart_result **out, HostStage *stage) {
   *out = nullptr;
   const size_t NW = (size_t)v.n_blocks * v.n_words, SW = (size_t)v.n_call_sites * v.n_words;
   // one host block: every array at a 64-byte aligned offset
@@ -500,9 +500,14 @@ int result_copy(const ompdart_result &v, bool pin, cudaStream_t s, ompdart_resul
   };
   size_t total = 0;
   for (const Part &p : parts) total += (p.bytes + 63) & ~size_t(63);
-  HostBlock *blk = host_block_new(total + 64, pin);
+  // a small result goes through the caller's page-locked staging buffer:
+  // every copy asynchronous, one wait, then one host copy into the block
+  // (copies into pageable memory each wait on their own)
+  char *stage_base = stage ? (char *)stage->get(total + 64) : nullptr;
+  HostBlock *blk = host_block_new(total + 64, stage_base ? false : pin);
   if (!blk) return set_err(OMPDART_E_NOMEM, "host allocation failed");
   char *base = (char *)host_block_ptr(blk);
+  char *land = stage_base ? stage_base : base;
   size_t off = 0;
   cudaError_t ce = cudaSuccess;
   for (const Part &p : parts) {
@@ -520,10 +525,11 @@ int result_copy(const ompdart_result &v, bool pin, cudaStream_t s, ompdart_resul
     }
     *p.dst = base + off;
     if (p.bytes && p.src && ce == cudaSuccess)
-      ce = cudaMemcpyAsync(base + off, p.src, p.bytes, cudaMemcpyDeviceToHost, s);
+      ce = cudaMemcpyAsync(land + off, p.src, p.bytes, cudaMemcpyDeviceToHost, s);
     off += (p.bytes + 63) & ~size_t(63);
   }
   if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+  if (ce == cudaSuccess && stage_base) memcpy(base, stage_base, off);
   if (ce != cudaSuccess) {
     host_block_release(blk);
     return cuda_err(ce, "copy of results");
@@ -568,6 +574,7 @@ struct ompdart_plan {
   // buffers (record streams grown after an overflow) drops it
   bool graph_on = false;
   cudaGraphExec_t gexec = nullptr;
+  HostStage stage;  // small results and boundary rows pass through it
   void drop_graph() {
     if (gexec) cudaGraphExecDestroy(gexec);
     gexec = nullptr;
@@ -589,12 +596,19 @@ int plan_set_boundary(ompdart_plan *P, const ompdart_cfg *cfg, cudaStream_t s) {
   boundary_rows(cfg, P->core.g.W, &top, &eh, &ed, &xl);
   const DevPlan &d = P->core.dp;
   const size_t bytes = sizeof(uint64_t) * eh.size();
-  cudaError_t ce = cudaMemcpyAsync(const_cast<uint64_t *>(d.entry_h), eh.data(), bytes, cudaMemcpyHostToDevice, s);
-  if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync(const_cast<uint64_t *>(d.entry_d), ed.data(), bytes, cudaMemcpyHostToDevice, s);
-  if (ce == cudaSuccess)
-    ce = cudaMemcpyAsync(const_cast<uint64_t *>(d.exit_live), xl.data(), bytes, cudaMemcpyHostToDevice, s);
-  // (copies from pageable memory have read their source when they return)
+  // through the plan's page-locked staging buffer: the copies do not wait.
+  // The buffer is free again here: the plan's previous run (and the copy
+  // of its results) completed before this run may start.
+  uint64_t *h = (uint64_t *)P->stage.get(3 * bytes);
+  const uint64_t *src[3] = {eh.data(), ed.data(), xl.data()};
+  if (h)
+    for (int k = 0; k < 3; ++k) memcpy(h + k * eh.size(), src[k], bytes);
+  uint64_t *dst[3] = {const_cast<uint64_t *>(d.entry_h), const_cast<uint64_t *>(d.entry_d),
+                      const_cast<uint64_t *>(d.exit_live)};
+  cudaError_t ce = cudaSuccess;
+  for (int k = 0; k < 3 && ce == cudaSuccess; ++k)
+    ce = cudaMemcpyAsync(dst[k], h ? h + k * eh.size() : src[k], bytes, cudaMemcpyHostToDevice, s);
+  // (a copy from pageable memory has read its source when it returns)
   return ce == cudaSuccess ? OMPDART_OK : cuda_err(ce, "uploading entry and exit rows");
 }
 
@@ -771,7 +785,8 @@ int ompdart_plan_fetch(ompdart_plan *P, ompdart_result **out) {
   *out = nullptr;
   ompdart_result v;
   core_view(P->core, P->h_status, &v);
-  return result_copy(v, true, P->last_stream ? P->last_stream : P->stream, out);  // one large block: page-locked
+  // one large block: page-locked; a small one through the plan's staging buffer
+  return result_copy(v, true, P->last_stream ? P->last_stream : P->stream, out, &P->stage);
 }
 
 int ompdart_analyze(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdart_result **out) {

@@ -15,12 +15,13 @@
 //      own stream, so batches overlap on the device.
 // Submitting copies the request, so callers may reuse their buffers.
 //
-// Resident mode (opts.resident): `workers' threads, each with its own
-// stream, take requests in arrival order and serve each from a cache of
+// Resident mode (opts.resident): `workers' threads take requests in
+// arrival order, up to 16 at a time each, and serve each from a cache of
 // device-resident plans keyed by the CFG's content (its entry and exit rows
 // excluded): a hit uploads the request's rows into the cached plan and
-// runs it; a miss builds the plan and keeps it, dropping the least recently
-// used idle plans when the device budget would overflow.
+// replays its graph on a stream of its own, so a group runs on the device
+// together; a miss builds the plan and keeps it, dropping the least
+// recently used idle plans when the device budget would overflow.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -45,6 +46,7 @@ using namespace ompdart;
 namespace {
 
 using Clock = std::chrono::steady_clock;
+constexpr int kResidentStreams = 16;  // resident mode: streams (requests in flight) per worker
 
 struct Request {
   int64_t id = 0;
@@ -101,9 +103,9 @@ struct ompdart_server {
     size_t operator()(const std::pair<uint64_t, uint64_t> &k) const { return (size_t)(k.first ^ (k.second * 31)); }
   };
   std::vector<std::thread> workers;
-  // one stream per worker, owned by the server: a cached plan synchronises
-  // the stream it last ran on when it is destroyed, so the streams outlive
-  // the cache
+  // the workers' streams (kResidentStreams each), owned by the server: a
+  // cached plan synchronises the stream it last ran on when it is
+  // destroyed, so the streams outlive the cache
   std::vector<cudaStream_t> worker_streams;
   std::mutex cache_mu;
   std::unordered_map<std::pair<uint64_t, uint64_t>, std::shared_ptr<Cached>, KeyHash> cache;
@@ -261,7 +263,10 @@ void evict_for(ompdart_server *S, long long need) {
   }
 }
 
-void serve_resident(ompdart_server *S, const ReqPtr &r, cudaStream_t s) {
+// The cached plan of a request's CFG, ingested and cached on a miss; NULL
+// (the request finished with the error) when it cannot be built.
+std::shared_ptr<ompdart_server::Cached> resident_plan(ompdart_server *S, const ReqPtr &r) {
+  TraceScope trace("resident: lookup", r->cfg.n_blocks);
   const auto key = content_key(r->cfg);
   std::shared_ptr<ompdart_server::Cached> c;
   {
@@ -275,67 +280,108 @@ void serve_resident(ompdart_server *S, const ReqPtr &r, cudaStream_t s) {
       ++S->cache_misses;
     }
   }
-  bool keep = true;
-  if (!c) {  // ingest and build it (outside the locks)
-    c = std::make_shared<ompdart_server::Cached>();
-    const int rc = ompdart_plan_create(&r->cfg, &S->o.opts, &c->plan);
-    if (rc) {
-      c->plan = nullptr;
-      finish_one(S, r, rc, nullptr, ompdart_last_error());
-      return;
-    }
-    ompdart_plan_graph(c->plan, 1);  // every later hit replays one graph
-    c->bytes = plan_device_bytes(c->plan);
-    std::lock_guard<std::mutex> lk(S->cache_mu);
-    auto it = S->cache.find(key);
-    if (it != S->cache.end()) {  // another worker built it meanwhile
-      c = it->second;
-    } else {
-      evict_for(S, c->bytes);
-      if (S->cache_bytes + c->bytes <= S->o.hbm_budget_bytes) {
-        S->cache.emplace(key, c);
-        S->cache_bytes += c->bytes;
-      } else {
-        keep = false;  // no room: a plan of its own, freed after the run
-      }
-    }
-    c->last_use = ++S->lru_clock;
+  if (c) return c;
+  // ingest and build it (outside the locks)
+  c = std::make_shared<ompdart_server::Cached>();
+  const int rc = ompdart_plan_create(&r->cfg, &S->o.opts, &c->plan);
+  if (rc) {
+    c->plan = nullptr;
+    finish_one(S, r, rc, nullptr, ompdart_last_error());
+    return nullptr;
   }
-  int rc;
-  ompdart_result *res = nullptr;
-  {
-    std::lock_guard<std::mutex> run(c->run);
-    rc = plan_set_boundary(c->plan, &r->cfg, s);
-    if (!rc) rc = ompdart_plan_run(c->plan, s);
-    if (!rc) rc = ompdart_plan_sync(c->plan);
-    if (!rc && S->o.keep_results) rc = ompdart_plan_fetch(c->plan, &res);
+  ompdart_plan_graph(c->plan, 1);  // every later hit replays one graph
+  c->bytes = plan_device_bytes(c->plan);
+  std::lock_guard<std::mutex> lk(S->cache_mu);
+  auto it = S->cache.find(key);
+  if (it != S->cache.end()) return it->second;  // another worker built it meanwhile
+  evict_for(S, c->bytes);
+  if (S->cache_bytes + c->bytes <= S->o.hbm_budget_bytes) {  // else a plan of its own, freed after the run
+    S->cache.emplace(key, c);
+    S->cache_bytes += c->bytes;
   }
-  const std::string err = rc ? ompdart_last_error() : "";
-  (void)keep;  // an uncached plan dies with the last reference
-  c.reset();
-  finish_one(S, r, rc, res, err);
+  c->last_use = ++S->lru_clock;
+  return c;
 }
 
-void resident_worker(ompdart_server *S, cudaStream_t s) {
+// A resident worker takes up to one request per stream it owns at a time.
+// Each runs on a stream of its own -- upload of its rows, then its cached
+// plan's graph -- so the group runs on the device together; then the
+// worker waits for each and copies its results back.  Requests for one
+// plan run in successive rounds (runs of one plan are serialised), and a
+// plan another worker is running is taken in a later round (try_lock: a
+// worker never waits for a plan while holding another).
+void resident_worker(ompdart_server *S, const cudaStream_t *streams, int n_streams) {
   cudaSetDevice(S->o.device);
-  for (;;) {
+  struct Job {
     ReqPtr r;
+    std::shared_ptr<ompdart_server::Cached> c;
+    int rc = OMPDART_OK;
+  };
+  for (;;) {
+    std::vector<ReqPtr> take;
     {
       std::unique_lock<std::mutex> lk(S->mu);
       S->cv_work.wait(lk, [&] { return S->stop || !S->pending.empty(); });
       if (S->pending.empty()) break;  // stopping with nothing left
-      r = S->pending.front();
-      S->pending.pop_front();
-      ++S->n_inflight;
-      if (r->est > S->o.hbm_budget_bytes) {
-        --S->n_inflight;
-        finish_request(S, r, OMPDART_E_BUDGET, nullptr, Clock::now(),
-                       "the request needs more device memory than the whole budget");
-        S->cv_done.notify_all();
-        continue;
+      while (!S->pending.empty() && (int)take.size() < n_streams) {
+        const ReqPtr r = S->pending.front();
+        S->pending.pop_front();
+        ++S->n_inflight;
+        if (r->est > S->o.hbm_budget_bytes) {
+          --S->n_inflight;
+          finish_request(S, r, OMPDART_E_BUDGET, nullptr, Clock::now(),
+                         "the request needs more device memory than the whole budget");
+          S->cv_done.notify_all();
+          continue;
+        }
+        take.push_back(r);
       }
     }
-    serve_resident(S, r, s);
+    std::vector<Job> jobs;
+    jobs.reserve(take.size());
+    for (const ReqPtr &r : take) {
+      auto c = resident_plan(S, r);
+      if (c) jobs.push_back(Job{r, std::move(c)});
+    }
+    std::vector<Job *> rest;
+    for (Job &j : jobs) rest.push_back(&j);
+    while (!rest.empty()) {
+      std::vector<Job *> round, later;
+      for (Job *j : rest) {
+        bool dup = false;
+        for (Job *x : round) dup = dup || x->c == j->c;
+        if (!dup && j->c->run.try_lock())
+          round.push_back(j);
+        else
+          later.push_back(j);
+      }
+      if (round.empty()) {  // every plan is busy elsewhere: wait for the first, holding none
+        later.front()->c->run.lock();
+        round.push_back(later.front());
+        later.erase(later.begin());
+      }
+      {
+        TraceScope trace("resident: launch", (long long)round.size());
+        for (size_t k = 0; k < round.size(); ++k) {
+          Job *j = round[k];
+          const cudaStream_t st = streams[k % n_streams];
+          j->rc = plan_set_boundary(j->c->plan, &j->r->cfg, st);
+          if (!j->rc) j->rc = ompdart_plan_run(j->c->plan, st);
+        }
+      }
+      for (Job *j : round) {
+        TraceScope trace("resident: wait+fetch", j->r->cfg.n_blocks);
+        ompdart_result *res = nullptr;
+        int rc = j->rc;
+        if (!rc) rc = ompdart_plan_sync(j->c->plan);
+        if (!rc && S->o.keep_results) rc = ompdart_plan_fetch(j->c->plan, &res);
+        const std::string err = rc ? ompdart_last_error() : "";
+        j->c->run.unlock();
+        j->c.reset();  // an uncached plan dies with its last reference
+        finish_one(S, j->r, rc, res, err);
+      }
+      rest.swap(later);
+    }
   }
 }
 
@@ -415,8 +461,8 @@ int ompdart_server_create(const ompdart_server_opts *opts, ompdart_server **out)
     return set_error(OMPDART_E_CUDA, "cudaSetDevice failed");
   }
   if (S->o.resident) {
-    const int nw = S->o.workers > 0 ? S->o.workers : 8;
-    for (int k = 0; k < nw; ++k) {
+    const int nw = S->o.workers > 0 ? S->o.workers : 4;
+    for (int k = 0; k < nw * kResidentStreams; ++k) {
       cudaStream_t x = nullptr;
       if (cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) {
         for (cudaStream_t y : S->worker_streams) cudaStreamDestroy(y);
@@ -425,7 +471,9 @@ int ompdart_server_create(const ompdart_server_opts *opts, ompdart_server **out)
       }
       S->worker_streams.push_back(x);
     }
-    for (int k = 0; k < nw; ++k) S->workers.emplace_back(resident_worker, S, S->worker_streams[k]);
+    for (int k = 0; k < nw; ++k)
+      S->workers.emplace_back(resident_worker, S, S->worker_streams.data() + (size_t)k * kResidentStreams,
+                              kResidentStreams);
   } else {
     S->worker = std::thread(worker_main, S);
   }

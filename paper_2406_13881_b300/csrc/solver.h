@@ -218,7 +218,36 @@ void core_view(const PlanCore &c, const int32_t *h_status, ompdart_result *v);
 // Copy the device arrays a view points at into a new host result
 // (ompdart_result_free) whose arrays share one host block (page-locked if
 // `pin`), on stream s.
-int result_copy(const ompdart_result &v, bool pin, cudaStream_t s, ompdart_result **out);
+// A page-locked staging buffer owned by one user (a plan): small copies to
+// and from the device land here asynchronously.  get(bytes) returns a
+// buffer of at least `bytes' (grown on demand), or NULL for a request above
+// kMax or when page-locking fails (the caller then copies directly).
+struct HostStage {
+  static constexpr size_t kMax = size_t(4) << 20;
+  void *p = nullptr;
+  size_t cap = 0;
+  void *get(size_t bytes) {
+    if (bytes > kMax) return nullptr;
+    if (bytes > cap) {
+      if (p) cudaFreeHost(p);
+      p = nullptr;
+      cap = 0;
+      size_t want = 4096;
+      while (want < bytes) want <<= 1;
+      if (cudaHostAlloc(&p, want, cudaHostAllocPortable) != cudaSuccess) {
+        (void)cudaGetLastError();
+        p = nullptr;
+        return nullptr;
+      }
+      cap = want;
+    }
+    return p;
+  }
+  ~HostStage() {
+    if (p) cudaFreeHost(p);
+  }
+};
+int result_copy(const ompdart_result &v, bool pin, cudaStream_t s, ompdart_result **out, HostStage *stage = nullptr);
 // A new host result whose arrays are v's, all inside `block` (one more
 // reference to it); NULL if the host allocation fails.
 ompdart_result *result_in_block(const ompdart_result &v, HostBlock *block);
