@@ -69,9 +69,10 @@ MEASURED_TRAFFIC = {
     "emit": {"bytes_2e18": (743276288 + 110661632 + 743400448 + 110947584 + 743296256 + 110883584) / 3.0,
              "profile": "profiles/emit_2e18.md", "captured_at": "a52a605"},
 }
-# the survey's per-phase traffic model for a dense-state design: about 140 B
+# a per-phase traffic model for a dense-state design (each phase reading and
+# writing whole state planes, no pairs or chunk carries): about 140 B
 # per block-word for the whole step (Ant 37, Hp 18, D 19, H 34, emission 32)
-SURVEY_BYTES_PER_BLOCK_WORD = 140.0
+DENSE_BYTES_PER_BLOCK_WORD = 140.0
 
 
 def peaks():
@@ -308,17 +309,17 @@ def dominant_roofline(timings, per_run, n_runs, peak, src, traffic=None, traffic
 
 def step_roofline(timings, per_run, ms_step, peak, units):
     """The whole step: the summed byte model of every modelled kernel per
-    step over the step's time, and the survey's ~140 B per block-word model
+    step over the step's time, and the dense-state ~140 B per block-word model
     over the same time."""
     modelled = sum(per_run.values())
-    survey = SURVEY_BYTES_PER_BLOCK_WORD * units
+    dense = DENSE_BYTES_PER_BLOCK_WORD * units
     gbs = lambda b: b / (ms_step / 1e3) / 1e9  # noqa: E731
     return {"bytes_per_step": modelled, "ms_per_step": ms_step, "achieved": gbs(modelled), "peak": peak,
             "unit": "GB/s", "frac": gbs(modelled) / peak,
-            "survey_model_bytes_per_step": survey, "survey_model_frac": gbs(survey) / peak,
+            "dense_model_bytes_per_step": dense, "dense_model_frac": gbs(dense) / peak,
             "unmodelled_kernels": sorted(k for k in timings if k not in per_run),
             "note": "achieved = modelled bytes per step / ms_per_step of the timed region; 60%% of the measured "
-                    "peak on the survey model is %.2f ms per step" % (survey / (0.6 * peak * 1e9) * 1e3)}
+                    "peak on the dense-state model is %.2f ms per step" % (dense / (0.6 * peak * 1e9) * 1e3)}
 
 
 def single_config(g, seed, world):

@@ -338,6 +338,13 @@ int scan_supported(const Ingest &g) {
 
 namespace {
 
+// host threads of the plan builder's parallel passes (each pass takes no
+// more than the machine has, and one per a few thousand items)
+#ifndef OMPDART_HOST_THREADS
+#define OMPDART_HOST_THREADS 16
+#endif
+constexpr int kHostThreads = OMPDART_HOST_THREADS;
+
 bool build_meta(const Ingest &g, int target, ScanState *st, HostVec<PosMeta> &meta, std::vector<LoopMeta> &loops,
                 std::vector<ChunkMeta> &chunks, std::vector<CarrySrc> &csrc, HostVec<int32_t> &fin_slot,
                 HostVec<int32_t> &out_slot, HostVec<int32_t> &out_pos, std::vector<int32_t> &lat_slot,
@@ -486,8 +493,8 @@ bool build_meta(const Ingest &g, int target, ScanState *st, HostVec<PosMeta> &me
   };
   int max_f = 0, max_b = 0;
   {
-    std::vector<ChunkScratch> xs(8);
-    parallel_ranges(C, 256, 8, [&](int t, int lo, int hi) {
+    std::vector<ChunkScratch> xs(kHostThreads);  // one per thread of the pass below
+    parallel_ranges(C, 256, kHostThreads, [&](int t, int lo, int hi) {
       for (int c = lo; c < hi && !xs[t].bad; ++c) colour_chunk(c, xs[t]);
     });
     for (const ChunkScratch &x : xs) {
@@ -504,7 +511,7 @@ bool build_meta(const Ingest &g, int target, ScanState *st, HostVec<PosMeta> &me
   std::vector<int32_t> src_off(M + 1, 0);
   for (int i = 0; i < M; ++i) src_off[i + 1] = src_off[i] + ebs_off[g.order[i] + 1] - ebs_off[g.order[i]];
   srcent.resize(src_off[M]);
-  parallel_ranges(M, 1 << 14, 8, [&](int, int lo, int hi) {
+  parallel_ranges(M, 1 << 14, kHostThreads, [&](int, int lo, int hi) {
     for (int i = lo; i < hi; ++i) {
       const int b = g.order[i];
       PosMeta &m = meta[i];
@@ -536,7 +543,7 @@ bool build_meta(const Ingest &g, int target, ScanState *st, HostVec<PosMeta> &me
   // ---- edge entries per chunk, then the carry sources (edges into the
   // next chunk's first position from this chunk), counted first
   std::vector<int32_t> cs_off(C + 1, 0);
-  parallel_ranges(C, 256, 8, [&](int, int lo, int hi) {
+  parallel_ranges(C, 256, kHostThreads, [&](int, int lo, int hi) {
     for (int c = lo; c < hi; ++c) {
       const int s = chunks[c].s, e = chunks[c].e;
       for (int i = s; i < e; ++i) {
@@ -595,7 +602,7 @@ bool build_meta(const Ingest &g, int target, ScanState *st, HostVec<PosMeta> &me
   };
   {
     std::vector<int32_t> lat_off(L + 1, 0), xs_off(L + 1, 0);
-    parallel_ranges(L, 1024, 8, [&](int, int lo, int hi) {
+    parallel_ranges(L, 1024, kHostThreads, [&](int, int lo, int hi) {
       std::vector<int32_t> lat, xs;
       for (int l = lo; l < hi; ++l) {
         loop_lists(l, lat, xs);
@@ -609,7 +616,7 @@ bool build_meta(const Ingest &g, int target, ScanState *st, HostVec<PosMeta> &me
     }
     lat_slot.resize(lat_off[L]);
     exit_slot.resize(xs_off[L]);
-    parallel_ranges(L, 1024, 8, [&](int, int lo, int hi) {
+    parallel_ranges(L, 1024, kHostThreads, [&](int, int lo, int hi) {
       std::vector<int32_t> lat, xs;
       for (int l = lo; l < hi; ++l) {
         loop_lists(l, lat, xs);
@@ -2229,7 +2236,7 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     // summary records.  Positions are independent once their offsets are
     // known: a first parallel pass sizes them (folding the call blocks into
     // per-thread buffers), a second fills them, over the same ranges.
-    constexpr int kThreads = 8, kMinPos = 4096;
+    constexpr int kThreads = kHostThreads, kMinPos = 4096;
     struct Folded {
       std::vector<uint32_t> recs;
       std::vector<std::pair<int32_t, int32_t>> at;  // (position, first record), in position order
@@ -2378,7 +2385,7 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     delete st;
     return nullptr;
   }
-  parallel_ranges(g.M, 1 << 15, 8, [&](int, int lo, int hi) {
+  parallel_ranges(g.M, 1 << 15, kHostThreads, [&](int, int lo, int hi) {
     for (int i = lo; i < hi; ++i) {
       PosMeta &m = meta[i];
       m.acc_beg = acc_off[m.blk];
@@ -2387,13 +2394,13 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
       m.flags = apos[i].flags;
     }
   });
-  trace_bm.next("scan uploads", g.M);
+  trace_bm.next("scan uploads: edge entries", g.M);
   std::vector<int2> fin_pk(fin_slot.size()), out_pk(out_slot.size());
   // in-edge entries: {source slot, loop-entry edge or -1}
-  parallel_ranges((int)fin_pk.size(), 1 << 17, 8, [&](int, int lo, int hi) {
+  parallel_ranges((int)fin_pk.size(), 1 << 17, kHostThreads, [&](int, int lo, int hi) {
     for (int k = lo; k < hi; ++k) fin_pk[k] = make_int2(fin_slot[k], g.fin_ent[k]);
   });
-  parallel_ranges((int)out_pk.size(), 1 << 17, 8, [&](int, int lo, int hi) {
+  parallel_ranges((int)out_pk.size(), 1 << 17, kHostThreads, [&](int, int lo, int hi) {
     for (int k = lo; k < hi; ++k) out_pk[k] = make_int2(out_slot[k], out_pos[k]);
   });
   const int W = p.W, C = st->C, G = (W + 63) / 64;
@@ -2409,7 +2416,7 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   // position inside d nested loops may be walked up to about 2^d times
   std::vector<int32_t> work(C);
   std::vector<long long> cost(C, 0);
-  parallel_ranges(C, 2048, 8, [&](int, int lo, int hi) {
+  parallel_ranges(C, 2048, kHostThreads, [&](int, int lo, int hi) {
     for (int c = lo; c < hi; ++c) {
       work[c] = c;
       for (int i = chunks[c].s; i < chunks[c].e; ++i) {
@@ -2418,6 +2425,7 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
       }
     }
   });
+  trace_bm.next("scan work order", C);
   std::stable_sort(work.begin(), work.end(), [&](int a, int b) { return cost[a] > cost[b]; });
   std::vector<int32_t> lant_work(g.L);
   for (int l = 0; l < g.L; ++l) lant_work[l] = l;
@@ -2427,6 +2435,7 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   sd.n_loops = g.L;
   bool ok = true;
   auto chk = [&](const void *x) { ok = ok && x; };
+  trace_bm.next("scan uploads: copies", g.M);
   chk(sd.meta = st->up(meta));
   chk(sd.loops = st->up(loops));
   chk(sd.chunks = st->up(chunks));
@@ -2519,7 +2528,7 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   // affine pairs of the summary walks and where each position's carry comes from
   {
     std::vector<int32_t> pos_chunk(g.M), src_pos(std::max(1, g.K), 0);
-    parallel_ranges(C, 2048, 8, [&](int, int lo, int hi) {
+    parallel_ranges(C, 2048, kHostThreads, [&](int, int lo, int hi) {
       for (int c = lo; c < hi; ++c)
         for (int i = chunks[c].s; i < chunks[c].e; ++i) pos_chunk[i] = c;
     });
@@ -2527,7 +2536,7 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     chk(sd.pos_chunk = st->up(pos_chunk));
     chk(sd.src_pos = st->up(src_pos));
     std::vector<int32_t> pos_loop(g.M);
-    parallel_ranges(g.M, 1 << 16, 8, [&](int, int lo, int hi) {
+    parallel_ranges(g.M, 1 << 16, kHostThreads, [&](int, int lo, int hi) {
       for (int i = lo; i < hi; ++i) pos_loop[i] = g.inner_loop[g.order[i]];
     });
     chk(sd.pos_loop = st->up(pos_loop));
