@@ -741,7 +741,8 @@ def measure_serve(args, local):
     # resident mode: CFGs stay on the device between requests (a plan per
     # distinct CFG, cached by content); one server for every rate, its cache
     # filled with the request pool first (untimed)
-    rsrv = _native.Server(hbm_budget_bytes=args.budget_gb << 30, resident=True, workers=args.workers, device=local)
+    rsrv = _native.Server(hbm_budget_bytes=args.budget_gb << 30, resident=True, workers=args.workers,
+                          max_batch=args.group, device=local)
     warm = [rsrv.submit(g) for g in small + large]
     rsrv.drain()
     for t in warm:
@@ -924,6 +925,7 @@ def main():
     ap.add_argument("--large-blocks", type=int, default=1 << 16)
     ap.add_argument("--budget-gb", type=int, default=40)
     ap.add_argument("--inflight", type=int, default=2)
+    ap.add_argument("--group", type=int, default=0, help="serve: requests a resident worker launches at once (0 = 16)")
     ap.add_argument("--workers", type=int, default=4, help="serve: worker threads of the resident mode")
     ap.add_argument("--n-cfgs", type=int, default=10000, help="CFGs of the batch workload")
     ap.add_argument("--batch-seed", type=int, default=3)

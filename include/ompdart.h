@@ -487,8 +487,8 @@ void ompdart_program_result_free(ompdart_program_result *res);
    launch sequence per request.
 
    RESIDENT MODE (resident != 0): CFGs stay on the device between requests.
-   `workers' threads take requests in arrival order, up to 16 at a time
-   each.  A request's CFG is looked up by its content (graph, accesses,
+   `workers' threads take requests in arrival order, up to max_batch (16
+   by default) at a time each.  A request's CFG is looked up by its content (graph, accesses,
    call table, kernels and scalars; not the entry and exit rows, which can
    differ per request) in a cache of device-resident plans: a hit uploads
    the request's entry and exit rows into the cached plan and runs it; a
@@ -500,11 +500,12 @@ void ompdart_program_result_free(ompdart_program_result *res);
    are serialised; different plans run concurrently.  The plans' device bytes stay within hbm_budget_bytes:
    the least recently used idle plans are dropped to make room, and a
    request that still does not fit runs on a plan of its own that is
-   freed afterwards.  max_batch and max_inflight are not used. */
+   freed afterwards.  max_batch is the group a worker launches at once
+   (0 = 16, at most 256); max_inflight is not used. */
 typedef struct ompdart_server ompdart_server;
 typedef struct {
   int64_t hbm_budget_bytes; /* device bytes admitted work may hold; 0 = 40 GiB     */
-  int32_t max_batch;        /* CFGs per batch; 0 = 4096                             */
+  int32_t max_batch;        /* CFGs per batch; 0 = 4096 (resident: group, 0 = 16)  */
   int32_t max_inflight;     /* batches on the GPU at once; 0 = 2                    */
   int32_t device;           /* CUDA device ordinal                                  */
   int32_t keep_results;     /* nonzero: copy each result to the host for the waiter */

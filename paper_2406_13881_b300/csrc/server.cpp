@@ -46,7 +46,7 @@ using namespace ompdart;
 namespace {
 
 using Clock = std::chrono::steady_clock;
-constexpr int kResidentStreams = 16;  // resident mode: streams (requests in flight) per worker
+constexpr int kResidentGroup = 16;  // resident mode: streams (requests in flight) per worker by default
 
 struct Request {
   int64_t id = 0;
@@ -103,7 +103,7 @@ struct ompdart_server {
     size_t operator()(const std::pair<uint64_t, uint64_t> &k) const { return (size_t)(k.first ^ (k.second * 31)); }
   };
   std::vector<std::thread> workers;
-  // the workers' streams (kResidentStreams each), owned by the server: a
+  // the workers' streams (a group's worth each), owned by the server: a
   // cached plan synchronises the stream it last ran on when it is
   // destroyed, so the streams outlive the cache
   std::vector<cudaStream_t> worker_streams;
@@ -450,6 +450,8 @@ int ompdart_server_create(const ompdart_server_opts *opts, ompdart_server **out)
   if (!S) return set_error(OMPDART_E_NOMEM, "host allocation failed");
   if (opts) S->o = *opts;
   if (S->o.hbm_budget_bytes <= 0) S->o.hbm_budget_bytes = 40ll << 30;
+  // resident mode: max_batch is the group a worker launches at once
+  const int group = S->o.max_batch > 0 ? std::min(S->o.max_batch, 256) : kResidentGroup;
   if (S->o.max_batch <= 0) S->o.max_batch = 4096;
   if (S->o.max_inflight <= 0) S->o.max_inflight = 2;
   S->o.opts.device = S->o.device;
@@ -462,7 +464,7 @@ int ompdart_server_create(const ompdart_server_opts *opts, ompdart_server **out)
   }
   if (S->o.resident) {
     const int nw = S->o.workers > 0 ? S->o.workers : 4;
-    for (int k = 0; k < nw * kResidentStreams; ++k) {
+    for (int k = 0; k < nw * group; ++k) {
       cudaStream_t x = nullptr;
       if (cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking) != cudaSuccess) {
         for (cudaStream_t y : S->worker_streams) cudaStreamDestroy(y);
@@ -472,8 +474,7 @@ int ompdart_server_create(const ompdart_server_opts *opts, ompdart_server **out)
       S->worker_streams.push_back(x);
     }
     for (int k = 0; k < nw; ++k)
-      S->workers.emplace_back(resident_worker, S, S->worker_streams.data() + (size_t)k * kResidentStreams,
-                              kResidentStreams);
+      S->workers.emplace_back(resident_worker, S, S->worker_streams.data() + (size_t)k * group, group);
   } else {
     S->worker = std::thread(worker_main, S);
   }

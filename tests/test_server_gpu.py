@@ -100,10 +100,13 @@ def _copy_cfg(g, **rows):
     return h
 
 
-def test_resident_mode_reuses_plans_with_per_request_rows():
+@pytest.mark.parametrize("workers,group", [(4, 0), (1, 2), (3, 64)])
+def test_resident_mode_reuses_plans_with_per_request_rows(workers, group):
     """Resident mode: the same CFGs sent again in fresh buffers hit the plan
     cache, requests for one CFG with different entry / exit rows get their
-    own results, and every result equals the oracle."""
+    own results, and every result equals the oracle -- with groups that
+    hold several requests for one plan (successive rounds) and workers
+    that find a plan busy in another worker."""
     rng = np.random.default_rng(12)
     base = mixed_cfgs(23, n=12)
     reqs = []
@@ -116,7 +119,7 @@ def test_resident_mode_reuses_plans_with_per_request_rows():
                 "entry_dev_valid": rng.integers(0, 2**63, size=W, dtype=np.uint64) & top,
                 "exit_host_live": rng.integers(0, 2**63, size=W, dtype=np.uint64) & top}
             reqs.append(_copy_cfg(g, **rows))
-    srv = _native.Server(resident=True, workers=4, keep_states=True)
+    srv = _native.Server(resident=True, workers=workers, max_batch=group, keep_states=True)
     tickets = [srv.submit(g) for g in reqs]
     srv.drain()
     for g, t in zip(reqs, tickets):
