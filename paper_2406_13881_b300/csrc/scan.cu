@@ -339,9 +339,12 @@ int scan_supported(const Ingest &g) {
 namespace {
 
 // host threads of the plan builder's parallel passes (each pass takes no
-// more than the machine has, and one per a few thousand items)
+// more than the machine has, and one per a few thousand items).  Batches
+// build their arenas on parallel threads already: 16 here made the
+// 2,000-function program 35% slower end to end and the single large CFG
+// no faster beyond the host's noise
 #ifndef OMPDART_HOST_THREADS
-#define OMPDART_HOST_THREADS 16
+#define OMPDART_HOST_THREADS 8
 #endif
 constexpr int kHostThreads = OMPDART_HOST_THREADS;
 
