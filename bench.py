@@ -69,6 +69,10 @@ MEASURED_TRAFFIC = {
     "emit": {"bytes_2e18": (743276288 + 110661632 + 743400448 + 110947584 + 743296256 + 110883584) / 3.0,
              "profile": "profiles/emit_2e18.md", "captured_at": "a52a605"},
 }
+# DRAM bytes of the batch workload's emission (10,000 CFGs, four arenas),
+# per launch averaged over one run's launches: an ncu capture
+BATCH_TRAFFIC = {"emit": {"bytes_per_launch": 6772.0e6 / 4, "profile": "profiles/batch_emit_config3.md",
+                          "captured_at": "2de5cc9"}}
 # a per-phase traffic model for a dense-state design (each phase reading and
 # writing whole state planes, no pairs or chunk carries): about 140 B
 # per block-word for the whole step (Ant 37, Hp 18, D 19, H 34, emission 32)
@@ -563,10 +567,16 @@ def measure_batch(args, local, world):
     b.profile(False)
     b.close()
     peak, src = peaks()
-    n_plans = len(info["arenas"]) + info["solo"]
+    # the byte model covers the chunked scan solver's kernels, which every
+    # arena launches once per run (a solo CFG runs the sweep solver's)
+    n_plans = max(1, len(info["arenas"]))
     per_run = bytes_per_run(timings, batch_byte_model(cfgs), n_prof, n_plans)
-    roof = dominant_roofline(timings, per_run, n_prof, peak, src, None,
-                             "no DRAM counters of this kernel's batch launch in this run")
+    dom = max(timings.items(), key=lambda kv: kv[1][1])[0] if timings else None
+    bt = BATCH_TRAFFIC.get(dom) if (args.n_cfgs == 10000 and args.batch_seed == 3) else None
+    roof = dominant_roofline(timings, per_run, n_prof, peak, src, bt["bytes_per_launch"] if bt else None,
+                             ("estimate, not counters of this run: an ncu capture (commit %s) of the same batch, "
+                              "%s" % (bt["captured_at"], bt["profile"])) if bt else
+                             "no DRAM counters of this kernel's batch launch")
     roof["run_under_profile_ms"] = sum(v[1] for v in timings.values()) / n_prof
     roof["note"] = ("per-kernel events serialise the arenas (no graph, no overlap); bytes per kernel from "
                     "byte_model of each arena's summed statistics")
