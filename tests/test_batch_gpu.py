@@ -169,6 +169,24 @@ def test_record_buffers_grow_plan_and_batch():
     b.close()
 
 
+def test_plan_graph_replay_after_record_growth():
+    """A plan replaying its run as a graph: the first run (the capture)
+    overflows the record streams, so the sync grows them and drops the
+    graph; the next run captures it again with the new buffers.  Every run
+    equals the oracle."""
+    g = fanout_cfg()
+    orc = oracle.solve(g)
+    p = _native.Plan(g, path=2, chunk_target=1000, keep_states=True)
+    p.graph(True)
+    for _ in range(3):
+        p.run()
+        p.sync()
+        res = p.fetch()
+        assert_matches_oracle(g, res, orc)
+        assert len(res["edge_xfers"]) == 128
+    p.close()
+
+
 def test_autotuned_batch():
     cfgs = mixed_cfgs(14, n=40)
     b = _native.Batch(cfgs, keep_states=True, tune=True)
