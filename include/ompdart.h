@@ -194,9 +194,13 @@ typedef struct {
    loop's exit edges, a branch that reads nothing on the device gets none,
    and no path makes more `to's than the lazy placement.  These transfers
    are edge records (ompdart_edge_xfer.to_bits); a device read that still
-   finds its copy stale keeps its access flag.  Runs on the sweep solver
-   (path 1; path = 2 with eager_to is OMPDART_E_INVALID, and so is a CFG
-   with call pseudo-accesses); batches put every CFG on a plan of its own. */
+   finds its copy stale keeps its access flag.  On the chunked scan solver
+   (the default for reducible CFGs) every edge gets an edge constant:
+   AntDm comes from a second backward walk (its complement is a may-problem
+   shaped like liveness), and a back edge's constant is taken where the
+   loop closes; path = 1 runs the sweep solver instead (any CFG, far
+   slower).  A CFG with call pseudo-accesses is OMPDART_E_INVALID; batches
+   put every CFG on a sweep-solver plan of its own. */
 
 typedef struct {
   int32_t edge, word;

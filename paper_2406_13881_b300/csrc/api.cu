@@ -315,14 +315,11 @@ int core_build(PlanCore *P, const int32_t *acc_off, const uint32_t *acc, const C
     P->site_acc = std::move(site_acc);
   }
   int want = o.path;
-  if (o.eager_to) {  // eager `to' placement runs on the sweep solver
-    if (want == 2) {
-      *err = "eager `to' placement runs on the sweep solver (path 1)";
-      return OMPDART_E_INVALID;
-    }
-    want = 1;
-  }
   if (want == 0) want = scan_supported(g) ? 2 : 1;
+  if (want == 2 && o.eager_to && g.K < (int)g.fin_src.size()) {
+    *err = "eager `to' placement on the scan solver needs the CFG ingested with every edge's constant entry";
+    return OMPDART_E_INVALID;
+  }
   if (want == 2 && !scan_supported(g)) {
     *err = "the chunked scan solver needs a reducible CFG whose loop bodies are contiguous in loop order";
     return OMPDART_E_INVALID;
@@ -341,6 +338,10 @@ int core_build(PlanCore *P, const int32_t *acc_off, const uint32_t *acc, const C
     chk(d.lant = P->dalloc<uint64_t>(g.body_blk.size() * (size_t)W * 2));
   } else {
     chk(P->cfg_err = P->dalloc<int32_t>(n_cfg));
+    if (o.eager_to) {  // AntDm and the edge constants' targets (eager `to' placement)
+      chk(d.ant_dm = P->dalloc<uint64_t>(NW));
+      if (!d.ent_dst) chk(d.ent_dst = P->upload(g.ent_dst));
+    }
     if (!ok) {
       *err = "device allocation failed";
       return OMPDART_E_NOMEM;
@@ -636,7 +637,9 @@ int ompdart_plan_create(const ompdart_cfg *cfg, const ompdart_opts *opts, ompdar
   if (!P) return set_err(OMPDART_E_NOMEM, "host allocation failed");
   std::string err;
   TraceScope trace("ingest", cfg ? cfg->n_blocks : 0);
-  int rc = ingest(cfg, &P->core.g, &err, o.data_region != 0);
+  // eager placement puts constants on any edge: every edge gets an entry
+  // unless the sweep solver is asked for (it needs none)
+  int rc = ingest(cfg, &P->core.g, &err, o.data_region != 0, o.eager_to != 0 && o.path != 1);
   trace.next("plan rows");
   if (rc) {
     delete P;

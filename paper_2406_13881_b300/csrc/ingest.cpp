@@ -329,7 +329,7 @@ void find_data_region(const ompdart_cfg *c, Ingest *g, const std::vector<int32_t
 
 }  // namespace
 
-int ingest(const ompdart_cfg *c, Ingest *g, std::string *err, bool data_region) {
+int ingest(const ompdart_cfg *c, Ingest *g, std::string *err, bool data_region, bool all_edges) {
   if (!check_format(c, err)) return OMPDART_E_INVALID;
   if (data_region && c->region &&
       first_bad(c->n_blocks, [&](int b) { return c->region[b] < -1 || c->region[b] >= c->n_blocks; }) <
@@ -610,6 +610,21 @@ int ingest(const ompdart_cfg *c, Ingest *g, std::string *err, bool data_region) 
     }
   });
 
+  if (all_edges) {
+    // eager `to' placement: a constant may sit on any edge, so every
+    // reachable edge gets an entry (after the loop-entry ones, in position
+    // order of the edge's target)
+    for (int i = 0; i < M; ++i) {
+      const int b = g->order[i];
+      for (int q = po[b]; q < po[b + 1]; ++q) {
+        if (!reach[psrc[q]] || eid_ent[peid[q]] != kNone) continue;
+        eid_ent[peid[q]] = g->K++;
+        g->ent_loop.push_back(kNone);
+        g->ent_src.push_back(psrc[q]);
+        g->ent_eid.push_back(peid[q]);
+      }
+    }
+  }
   g->ent_rx.assign(g->K, 0);
   if (data_region && c->region) find_data_region(c, g, so, succ, po, psrc, peid, reach, pre, dfn, idom, dominates,
                                                  &eid_ent);

@@ -88,7 +88,9 @@ void concat_ingests(const std::vector<const Ingest *> &parts, Ingest *out);
 // block without successors) of the blocks those kernel blocks and loop
 // bodies lead to outside themselves, or the virtual exit if there is none.
 // The edges leaving the region join the edge constants (ent_rx).
-int ingest(const ompdart_cfg *cfg, Ingest *g, std::string *err, bool data_region = false);
+// all_edges: every reachable edge gets an edge-constant entry (eager `to'
+// placement puts constants on any edge); the loop-entry ones come first.
+int ingest(const ompdart_cfg *cfg, Ingest *g, std::string *err, bool data_region = false, bool all_edges = false);
 
 // Build chunks of about `target` positions at single-entry cut points.
 void make_chunks(Ingest *g, int target);

@@ -86,7 +86,10 @@ constexpr int MAX_DEPTH = 31;  // loop nesting depth the chain handles
 __host__ __device__ inline int rerun_cap(int len) { return 8 * len + 64; }
 
 enum PhaseKind { K_ANT = 0, K_HP = 1, K_D = 2, K_H = 3 };
-enum ModeKind { M_SUM = 0, M_LANT = 2 };  // summary walk; loop-restricted anticipation
+// summary walk (liveness); its complement problem for eager `to'
+// placement (not anticipated by a device read: ~AntDm); loop-restricted
+// anticipation (the loop masks)
+enum ModeKind { M_SUM = 0, M_NA = 1, M_LANT = 2 };
 
 struct PosMeta {  // one per position, 80 B
   int32_t blk;
@@ -154,6 +157,7 @@ struct ScanDev {
   long long n_acc_p;      // entries of the position-ordered access stream
   int sh_slots;           // slots per plane held in shared memory
   const int32_t *lat_slot;
+  const int32_t *lat_ent;   // edge-constant entry of each latch's back edge, or -1
   const int32_t *exit_slot;  // per loop (xs_beg, xs_cnt): forward slots of its exit sources
   const int4 *bend_info;  // per loop ending at a position: {depth, header position, body end, header's backward slot}
   const int32_t *srcent;
@@ -280,7 +284,7 @@ struct ChainShape {
   int grid = 1, wpc = 4, sh_slots = 0;
   size_t smem = 0;
 };
-enum ChainKind { CK_BSUM, CK_BLANT, CK_FSUM, CK_COUNT };
+enum ChainKind { CK_BSUM, CK_BLANT, CK_FSUM, CK_BNA, CK_COUNT };
 
 struct ScanState {
   int C = 0, G = 0, fslots = 0, bslots = 0, n_streams = 0;
@@ -303,6 +307,11 @@ struct ScanState {
   cudaStream_t side[2] = {nullptr, nullptr};
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   size_t spill_region = 0;  // words per branch
+  // eager `to' placement: the not-anticipated walk (~AntDm) keeps its own
+  // pairs, header values and chunk maps (it runs beside liveness)
+  bool eager = false;
+  uint64_t *na_pg = nullptr, *na_pp = nullptr, *na_pa = nullptr, *na_pa2 = nullptr;
+  uint64_t *na_hg = nullptr, *na_hp = nullptr, *na_h2g = nullptr, *na_h2p = nullptr, *na_h2a = nullptr;
   ~ScanState() {
     for (cudaStream_t x : side)
       if (x) cudaStreamDestroy(x);
@@ -351,8 +360,8 @@ constexpr int kHostThreads = OMPDART_HOST_THREADS;
 bool build_meta(const Ingest &g, int target, ScanState *st, HostVec<PosMeta> &meta, std::vector<LoopMeta> &loops,
                 std::vector<ChunkMeta> &chunks, std::vector<CarrySrc> &csrc, HostVec<int32_t> &fin_slot,
                 HostVec<int32_t> &out_slot, HostVec<int32_t> &out_pos, std::vector<int32_t> &lat_slot,
-                std::vector<int32_t> &bend_loop, std::vector<int32_t> &srcent, std::vector<int32_t> &exit_slot,
-                std::string *err) {
+                std::vector<int32_t> &lat_ent, std::vector<int32_t> &bend_loop, std::vector<int32_t> &srcent,
+                std::vector<int32_t> &exit_slot, std::string *err) {
   Ingest &gm = const_cast<Ingest &>(g);
   make_chunks(&gm, target);
   const int M = g.M, C = (int)g.chunk_off.size() - 1, L = g.L;
@@ -581,13 +590,17 @@ bool build_meta(const Ingest &g, int target, ScanState *st, HostVec<PosMeta> &me
   }
   // ---- per loop: its record, latch slots and exit sources (loops
   // independent: counted, then written at their offsets, in parallel)
-  auto loop_lists = [&](int l, std::vector<int32_t> &lat, std::vector<int32_t> &xs) {
+  auto loop_lists = [&](int l, std::vector<int32_t> &lat, std::vector<int32_t> &lent, std::vector<int32_t> &xs) {
     const int ph = g.pos[g.loop_head[l]], pend = g.loop_end[l];
     lat.clear();
+    lent.clear();
     xs.clear();
     for (int k = g.fin_off[ph]; k < g.fin_off[ph + 1]; ++k) {
       const int pp = g.pos[g.fin_src[k]];
-      if (pp >= ph && std::find(lat.begin(), lat.end(), fslot[pp]) == lat.end()) lat.push_back(fslot[pp]);
+      if (pp >= ph && std::find(lat.begin(), lat.end(), fslot[pp]) == lat.end()) {
+        lat.push_back(fslot[pp]);
+        lent.push_back(g.fin_ent[k]);  // the back edge's constant entry (eager placement), else -1
+      }
     }
     // exit sources: body positions whose value is read from their slot
     // outside the body: after it (or as the next chunk's carry), or at an
@@ -606,9 +619,9 @@ bool build_meta(const Ingest &g, int target, ScanState *st, HostVec<PosMeta> &me
   {
     std::vector<int32_t> lat_off(L + 1, 0), xs_off(L + 1, 0);
     parallel_ranges(L, 1024, kHostThreads, [&](int, int lo, int hi) {
-      std::vector<int32_t> lat, xs;
+      std::vector<int32_t> lat, lent, xs;
       for (int l = lo; l < hi; ++l) {
-        loop_lists(l, lat, xs);
+        loop_lists(l, lat, lent, xs);
         lat_off[l + 1] = (int32_t)lat.size();
         xs_off[l + 1] = (int32_t)xs.size();
       }
@@ -618,12 +631,14 @@ bool build_meta(const Ingest &g, int target, ScanState *st, HostVec<PosMeta> &me
       xs_off[l + 1] += xs_off[l];
     }
     lat_slot.resize(lat_off[L]);
+    lat_ent.resize(lat_off[L]);
     exit_slot.resize(xs_off[L]);
     parallel_ranges(L, 1024, kHostThreads, [&](int, int lo, int hi) {
-      std::vector<int32_t> lat, xs;
+      std::vector<int32_t> lat, lent, xs;
       for (int l = lo; l < hi; ++l) {
-        loop_lists(l, lat, xs);
+        loop_lists(l, lat, lent, xs);
         std::copy(lat.begin(), lat.end(), lat_slot.begin() + lat_off[l]);
+        std::copy(lent.begin(), lent.end(), lat_ent.begin() + lat_off[l]);
         std::copy(xs.begin(), xs.end(), exit_slot.begin() + xs_off[l]);
         LoopMeta &lm = loops[l];
         lm.cfg = (int32_t)(std::upper_bound(g.cfg_pos_off.begin(), g.cfg_pos_off.end(), g.pos[g.loop_head[l]]) -
@@ -906,9 +921,14 @@ __device__ __forceinline__ void prep_masks(const ScanDev &sd, const Win &w, cons
         if (rc & R_KH) atomicOr(reinterpret_cast<unsigned long long *>(kill) + lw, bit);
         if (rc & R_KD) atomicOr(reinterpret_cast<unsigned long long *>(kill) + 64 + lw, bit);
       } else {
-        const bool ue = uh || ud;
-        if (ue) atomicOr(t, bit); else if (df) atomicOr(t + 64, bit);
-        if (MODE == M_SUM && (ue || df)) atomicOr(t + 128, bit);
+        if (MODE == M_NA) {  // not anticipated: a write before any device read sets, a device read clears
+          if (!ud && df) atomicOr(t, bit); else if (ud) atomicOr(t + 64, bit);
+          if (ud || df) atomicOr(t + 128, bit);
+        } else {
+          const bool ue = uh || ud;
+          if (ue) atomicOr(t, bit); else if (df) atomicOr(t + 64, bit);
+          if (MODE == M_SUM && (ue || df)) atomicOr(t + 128, bit);
+        }
       }
     } else {
       const uint32_t GEN = PH == K_D ? R_GD : R_GH, KILL = PH == K_D ? R_KD : R_KH;
@@ -981,14 +1001,22 @@ __device__ __forceinline__ void compose_pair(T &v0, T &v1, uint64_t h0, uint64_t
 // is stored for the resolve, and the values still to be read after the
 // body (exit sources, the previous position) are re-expressed in the
 // enclosing level.
+// With eager `to' placement a back edge can carry an edge constant: the
+// latch's value enters the header less it (ec, or null).
 __device__ __forceinline__ void close_loop(const ScanDev &sd, const Slots<2> &sl, const Lane &L, int W, int l,
-                                           int hs, uint64_t (&pv)[2][2]) {
+                                           int hs, uint64_t (&pv)[2][2], const uint64_t *ec) {
   const LoopMeta lm = sd.loops[l];
   uint64_t a0 = 0, a1 = 0;
   for (int q = 0; q < lm.lat_cnt; ++q) {
     const ulonglong2 v = sl.ld(sd.lat_slot[lm.lat_beg + q], 0, L.lane);
-    a0 |= v.x;
-    a1 |= v.y;
+    const int ent = ec ? sd.lat_ent[lm.lat_beg + q] : -1;
+    if (ent >= 0) {
+      a0 |= v.x & ~ld_word(ec, ent, W, L.w0);
+      a1 |= v.y & ~ld_word(ec, ent, W, L.w0 + 1);
+    } else {
+      a0 |= v.x;
+      a1 |= v.y;
+    }
   }
   const ulonglong2 e0 = sl.ld(hs, 0, L.lane), e1 = sl.ld(hs, 1, L.lane);
   const uint64_t h00 = e0.x | a0, h01 = e0.y | a1, h10 = e1.x | a0, h11 = e1.y | a1;
@@ -1168,7 +1196,7 @@ __device__ __forceinline__ void fwd_walk(const DevPlan &p, const ScanDev &sd, co
     // ---- close the loops ending here
     while (depth > 0 && top_pend - 1 == i) {
       --depth;
-      close_loop(sd, sl, L, W, st_l[depth], st_hs[depth], pv);
+      close_loop(sd, sl, L, W, st_l[depth], st_hs[depth], pv, PH == K_D && p.ant_dm ? p.ec_d : nullptr);
       top_pend = depth > 0 ? st_pend[depth - 1] : -1;
     }
   }
@@ -1293,8 +1321,8 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
 #pragma unroll
     for (int pl = 0; pl < NP; ++pl) z[pl][0] = z[pl][1] = 0;
     if (MODE != M_LANT && m.exit_idx >= 0) {  // region exit: the host may read what is live
-      z[0][0] = xl0;
-      z[0][1] = xl1;
+      z[0][0] = MODE == M_NA ? L.top0 : xl0;    // (not anticipated: nothing is read after it)
+      z[0][1] = MODE == M_NA ? L.top1 : xl1;
     }
     for (int q = 0; q < m.nout; ++q) {
       const int2 oe = win_edge(w, wr, sd.out_pk, m.out_beg + q);
@@ -1338,9 +1366,9 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
     const bool sym_close = is_top_header && depth == base_depth + 1;
     // liveness, one level down: A2 = X | (A2 & PA2) likewise has the least
     // solution X, a triple of the carry and A kept for the resolve
-    const bool sym2_close = MODE == M_SUM && is_top_header && depth == base_depth + 2;
+    const bool sym2_close = MODE != M_LANT && is_top_header && depth == base_depth + 2;
     if (sym_close) {
-      if (MODE == M_SUM) {
+      if (MODE != M_LANT) {
         st_pair(sd.hdrl_g, m.head_loop, W, L.w0, z[0][0], z[0][1]);
         st_pair(sd.hdrl_p, m.head_loop, W, L.w0, z[1][0], z[1][1]);
       }
@@ -1366,7 +1394,7 @@ __device__ void bwd_range(const DevPlan &p, const ScanDev &sd, const Lane &L, co
       }
       if (rewalk && __any_sync(0xffffffffu, changed)) dirty |= 1u << (depth - 1);
     }
-    if (MODE == M_SUM) {  // Live_in as an affine pair of the chunk's carry (and A, A2 inside loops)
+    if (MODE != M_LANT) {  // the value at entry as an affine pair of the chunk's carry (and A, A2 inside loops)
       st_pair_s(sd.pair_g, m.blk, W, L.w0, z[0][0], z[0][1]);
       st_pair_s(sd.pair_p, m.blk, W, L.w0, z[1][0], z[1][1]);
       if (depth > base_depth) st_pair_s(sd.pair_a, m.blk, W, L.w0, z[2][0], z[2][1]);
@@ -1545,7 +1573,9 @@ __global__ void __launch_bounds__(256) k_local_summary_pos(ScanDev sd) {
 // --------------------------------------------------------------------------------------
 // resolve: every position's value from its pair and its chunk's carry
 // --------------------------------------------------------------------------------------
-enum ResolveKind { RV_LIVE = 0, RV_VALID = 1 };  // liveness as is; stale sets to valid sets
+// liveness as is; stale sets to valid sets; a liveness-shaped complement
+// (not anticipated) to the anticipated set
+enum ResolveKind { RV_LIVE = 0, RV_VALID = 1, RV_NA = 2 };
 
 // Each loop's header value composed up the loop tree (maps compose
 // associatively): a pair of the chunk's carry, one thread per (loop, word).
@@ -1585,7 +1615,7 @@ __global__ void __launch_bounds__(256) k_resolve(DevPlan p, ScanDev sd, const ui
       ulonglong2 g = *reinterpret_cast<const ulonglong2 *>(G + o);
       ulonglong2 q = *reinterpret_cast<const ulonglong2 *>(P + o);
       const int pl = sd.pos_loop[i];
-      if (KIND == RV_LIVE && pl >= 0) {
+      if (KIND != RV_VALID && pl >= 0) {
         const int l = sd.loop_root[pl], l2 = sd.loop_d2[pl];
         ulonglong2 a = *reinterpret_cast<const ulonglong2 *>(sd.pair_a + o);
         if (l2 >= 0) {  // first A2 (a triple of the carry and A) through PA2
@@ -1611,13 +1641,13 @@ __global__ void __launch_bounds__(256) k_resolve(DevPlan p, ScanDev sd, const ui
       }
       const ulonglong2 k = *reinterpret_cast<const ulonglong2 *>(sd.carry + oc);
       ulonglong2 x = make_ulonglong2(g.x | (k.x & q.x), g.y | (k.y & q.y));
-      if (KIND == RV_VALID) x = make_ulonglong2(~x.x & tp[0], ~x.y & tp[1]);
+      if (KIND != RV_LIVE) x = make_ulonglong2(~x.x & tp[0], ~x.y & tp[1]);
       *reinterpret_cast<ulonglong2 *>(out + o) = x;
     } else {
       for (int u = 0; u < 2 && w + u < W; ++u) {
         uint64_t g = G[o + u], q = P[o + u];
         const int pl = sd.pos_loop[i];
-        if (KIND == RV_LIVE && pl >= 0) {
+        if (KIND != RV_VALID && pl >= 0) {
           const int l = sd.loop_root[pl], l2 = sd.loop_d2[pl];
           uint64_t a = sd.pair_a[o + u];
           if (l2 >= 0) {
@@ -1658,7 +1688,9 @@ __global__ void k_resolve_src(DevPlan p, ScanDev sd, int which) {
   const uint64_t x = ~(g | (sd.carry[(size_t)c * W + w] & q)) & p.top[(size_t)sd.chunks[c].cfg * W + w];
   const int le = p.ent_loop[k];
   if (which == 0) {
-    p.ec_d[t] = le >= 0 ? p.mask_d[(size_t)le * W + w] & x : 0ull;
+    uint64_t need = le >= 0 ? p.mask_d[(size_t)le * W + w] : 0ull;
+    if (p.ant_dm) need |= p.ant_dm[(size_t)p.ent_dst[k] * W + w];  // eager: read on the device on every path on
+    p.ec_d[t] = need & x;
   } else {
     sd.d_src[t] = x;
     uint64_t h = le >= 0 ? p.mask_h[(size_t)le * W + w] & x : 0ull;
@@ -2217,7 +2249,7 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   std::vector<ChunkMeta> chunks;
   std::vector<CarrySrc> csrc;
   HostVec<int32_t> fin_slot, out_slot, out_pos;
-  std::vector<int32_t> lat_slot, bend_loop, srcent, exit_slot;
+  std::vector<int32_t> lat_slot, lat_ent, bend_loop, srcent, exit_slot;
   // short chunks give more independent walks (one warp each) and shorter
   // longest walks; 32 positions measured fastest on the 2^20-block CFG
   if (chunk_target <= 0) chunk_target = 32;
@@ -2373,11 +2405,11 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   if (g.M >= (1 << 14)) {  // (a thread start costs tens of microseconds)
     std::thread th(access_pass);
     meta_ok = build_meta(g, chunk_target, st, meta, loops, chunks, csrc, fin_slot, out_slot, out_pos, lat_slot,
-                         bend_loop, srcent, exit_slot, err);
+                         lat_ent, bend_loop, srcent, exit_slot, err);
     th.join();
   } else {
     meta_ok = build_meta(g, chunk_target, st, meta, loops, chunks, csrc, fin_slot, out_slot, out_pos, lat_slot,
-                         bend_loop, srcent, exit_slot, err);
+                         lat_ent, bend_loop, srcent, exit_slot, err);
     if (meta_ok) access_pass();
   }
   if (meta_ok && !acc_err.empty()) {
@@ -2451,6 +2483,7 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   chk(sd.acc_link = st->up(acc_link));
   sd.n_acc_p = (long long)acc_p.size();
   chk(sd.lat_slot = st->up(lat_slot));
+  chk(sd.lat_ent = st->up(lat_ent));
   chk(sd.exit_slot = st->up(exit_slot));
   {
     std::vector<int4> bend_info(bend_loop.size());
@@ -2476,6 +2509,9 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     st->shape[CK_BLANT] = chain_shape(k_bwd_chain<M_LANT>, st->bslots, BwdPlanes<M_LANT>::NP, true,
                                       OMPDART_LANT_SH_WORDS, wpc, std::max(1, g.L) * G, n_sm);
     st->shape[CK_FSUM] = chain_shape(k_fwd_chain<K_HP>, st->fslots, 2, false, FWD_SH_WORDS, wpc, items, n_sm);
+    st->shape[CK_BNA] = p.ant_dm ? chain_shape(k_bwd_chain<M_NA>, st->bslots, BwdPlanes<M_NA>::NP, false, BWD_SH_WORDS,
+                                               wpc, items, n_sm)
+                                 : ChainShape{};
     chain_shape(k_fwd_chain<K_D>, st->fslots, 2, false, FWD_SH_WORDS, wpc, items, n_sm);
     chain_shape(k_fwd_chain<K_H>, st->fslots, 2, false, FWD_SH_WORDS, wpc, items, n_sm);
   }
@@ -2491,13 +2527,15 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
   }
   st->spill_region = (size_t)std::max(1, sd.spill_stride) * max_warps;
   chk(sd.spill = st->alloc<uint64_t>(st->spill_region * 3));  // one region per branch of a run
-  chk(sd.gsum = st->alloc<uint64_t>((size_t)2 * C * W));
-  chk(sd.psum = st->alloc<uint64_t>((size_t)2 * C * W));
+  st->eager = p.ant_dm != nullptr;
+  const size_t n_maps = st->eager ? 3 : 2;  // chunk maps: liveness, forward problems (, not anticipated)
+  chk(sd.gsum = st->alloc<uint64_t>(n_maps * C * W));
+  chk(sd.psum = st->alloc<uint64_t>(n_maps * C * W));
   if (ok) {  // chunks that end a CFG never write their map: keep it defined
-    cudaMemset(sd.gsum, 0, sizeof(uint64_t) * 2 * C * W);
-    cudaMemset(sd.psum, 0, sizeof(uint64_t) * 2 * C * W);
+    cudaMemset(sd.gsum, 0, sizeof(uint64_t) * n_maps * C * W);
+    cudaMemset(sd.psum, 0, sizeof(uint64_t) * n_maps * C * W);
   }
-  chk(sd.carry = st->alloc<uint64_t>((size_t)2 * C * W));
+  chk(sd.carry = st->alloc<uint64_t>(n_maps * C * W));
   {
     // chunk-carry scan: about two CTAs per SM over the word columns' segments
     int dev = 0, n_sm = 148;
@@ -2505,8 +2543,8 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     // about two CTAs per SM over the column blocks' segments, a few chunks per run
     const int wb = scan_wb(W), gx = (W + wb - 1) / wb, runs = SCAN_T / wb;
     sd.seg_n = std::max(1, std::min({2 * n_sm / gx, (C + 4 * runs - 1) / (4 * runs), 1024}));
-    chk(sd.seg_g = st->alloc<uint64_t>((size_t)2 * sd.seg_n * W));  // one region per branch
-    chk(sd.seg_p = st->alloc<uint64_t>((size_t)2 * sd.seg_n * W));
+    chk(sd.seg_g = st->alloc<uint64_t>(n_maps * sd.seg_n * W));  // one region per branch
+    chk(sd.seg_p = st->alloc<uint64_t>(n_maps * sd.seg_n * W));
   }
   chk(sd.d_src = st->alloc<uint64_t>((size_t)std::max(1, g.K) * W));
   trace_bm.next("scan emission items", g.M);
@@ -2569,6 +2607,18 @@ ScanState *scan_create(const Ingest &g, const int32_t *acc_off, const uint32_t *
     const size_t NW = (size_t)g.N * W, KW = (size_t)std::max(1, g.K) * W;
     chk(sd.pair_a = st->alloc<uint64_t>(NW));
     chk(sd.pair_a2 = st->alloc<uint64_t>(NW));
+    if (st->eager) {
+      const size_t LW = (size_t)std::max(1, g.L) * W;
+      chk(st->na_pg = st->alloc<uint64_t>(NW));
+      chk(st->na_pp = st->alloc<uint64_t>(NW));
+      chk(st->na_pa = st->alloc<uint64_t>(NW));
+      chk(st->na_pa2 = st->alloc<uint64_t>(NW));
+      chk(st->na_hg = st->alloc<uint64_t>(LW));
+      chk(st->na_hp = st->alloc<uint64_t>(LW));
+      chk(st->na_h2g = st->alloc<uint64_t>(LW));
+      chk(st->na_h2p = st->alloc<uint64_t>(LW));
+      chk(st->na_h2a = st->alloc<uint64_t>(LW));
+    }
     chk(sd.pair_g = st->alloc<uint64_t>(NW));
     chk(sd.pair_p = st->alloc<uint64_t>(NW));
     chk(sd.pair_gd = st->alloc<uint64_t>(NW));
@@ -2691,6 +2741,33 @@ int enqueue_scan_solver(ScanState *st, const DevPlan &p, cudaStream_t s, Prof *p
   if (p.L) {
     PROF("loop_masks");
     chain_launch(k_bwd_chain<M_LANT>, st->shape[CK_BLANT], p, sm, 2, s_lant); ++n;
+  }
+  // ---- eager `to' placement: AntDm, as the complement of "not anticipated"
+  // (a backward may problem shaped like liveness), after the masks on
+  // their stream and in their spill region; the edge constants wait for both
+  if (st->eager) {
+    ScanDev sn = sd;
+    sn.spill = sd.spill;
+    sn.pair_g = st->na_pg;
+    sn.pair_p = st->na_pp;
+    sn.pair_a = st->na_pa;
+    sn.pair_a2 = st->na_pa2;
+    sn.hdrl_g = st->na_hg;
+    sn.hdrl_p = st->na_hp;
+    sn.hdrl2_g = st->na_h2g;
+    sn.hdrl2_p = st->na_h2p;
+    sn.hdrl2_a = st->na_h2a;
+    sn.gsum = sd.gsum + (size_t)2 * C * W;
+    sn.psum = sd.psum + (size_t)2 * C * W;
+    sn.carry = sd.carry + (size_t)2 * C * W;
+    sn.seg_g = sd.seg_g + (size_t)2 * sd.seg_n * W;
+    sn.seg_p = sd.seg_p + (size_t)2 * sd.seg_n * W;
+    PROF("antdm_summary");
+    chain_launch(k_bwd_chain<M_NA>, st->shape[CK_BNA], p, sn, 9, s_lant); ++n;
+    PROF("antdm_scan");
+    n += scan_carries(sn, W, 1, nullptr, s_lant);
+    PROF("antdm_resolve");
+    k_resolve<RV_NA><<<grid_of((nw + 1) / 2, 256), 256, 0, s_lant>>>(p, sn, sn.pair_g, sn.pair_p, p.ant_dm); ++n;
   }
   // ---- liveness (backward)
   PROF("live_summary");

@@ -1,10 +1,12 @@
 """Eager `to' placement on the GPU (opts.eager_to; Sec. IV-E, Algorithm 1):
 every output through the C ABI equals ``oracle.solve(..., eager_to=True)``
 bit for bit -- states, access flags, edge transfers (the eager `to's among
-them) and exit transfers -- on the hand-built programs of the oracle's
-pins, the paper's listings, random reducible and irreducible CFGs, wide
-variable sets, batches, and together with the data region and its
-directives."""
+them) and exit transfers -- on both solvers (the chunked scan solver for
+reducible CFGs, with edge constants on every edge and the back edges'
+constants taken at the loop closure; the sweep solver for any CFG), on
+the hand-built programs of the oracle's pins, the paper's listings, random
+reducible and irreducible CFGs, wide variable sets, small chunks, batches,
+and together with the data region and its directives."""
 import numpy as np
 import pytest
 
@@ -23,10 +25,13 @@ R, W = 1, 2
 
 
 def check(g, **opts):
+    """Both solvers (the scan solver where the CFG allows it) against the oracle."""
     orc = oracle.solve(g, eager_to=True)
-    res = _native.analyze(g, eager_to=True, keep_states=True, **opts)
-    assert res["path"] == 1
-    assert_matches_oracle(g, res, orc)
+    res = None
+    for path in (1, 0):
+        res = _native.analyze(g, eager_to=True, keep_states=True, path=path, **opts)
+        assert res["path"] == 1 or path == 0
+        assert_matches_oracle(g, res, orc)
     return res, orc
 
 
@@ -104,10 +109,31 @@ def test_batch():
     b.close()
 
 
-def test_scan_path_and_calls_refused():
+@pytest.mark.parametrize("target", [1, 3, 8])
+def test_scan_path_small_chunks(target):
+    """Edge constants across chunk boundaries (carry edges) and on back
+    edges at every loop closure: structured CFGs cut into tiny chunks."""
+    for seed in range(6):
+        g = wl.structured(19000 + seed, 400, 130)
+        orc = oracle.solve(g, eager_to=True)
+        res = _native.analyze(g, eager_to=True, keep_states=True, path=2, chunk_target=target)
+        assert res["path"] == 2
+        assert_matches_oracle(g, res, orc)
+
+
+def test_scan_path_is_chosen_for_reducible_cfgs():
     g = wl.single_small(1)
+    res = _native.analyze(g, eager_to=True)
+    assert res["path"] == 2
+    assert_matches_oracle(g, res, oracle.solve(g, eager_to=True))
+
+
+def test_calls_refused_library_stays_usable():
+    """CFGs with call pseudo-accesses take no eager placement (E_INVALID);
+    the library answers the next request."""
+    from test_calls_gpu import structured_with_calls
+    g = structured_with_calls(3, 200, 40)
     with pytest.raises(_native.OmpdartError) as ei:
-        _native.analyze(g, eager_to=True, path=2)
+        _native.analyze(g, eager_to=True)
     assert ei.value.code == _native.E_INVALID
-    # and the library stays usable
-    check(g)
+    check(wl.single_small(2))
