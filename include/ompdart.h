@@ -199,8 +199,7 @@ typedef struct {
    AntDm comes from a second backward walk (its complement is a may-problem
    shaped like liveness), and a back edge's constant is taken where the
    loop closes; path = 1 runs the sweep solver instead (any CFG, far
-   slower).  A CFG with call pseudo-accesses is OMPDART_E_INVALID; batches
-   put every CFG on a sweep-solver plan of its own. */
+   slower).  A CFG with call pseudo-accesses is OMPDART_E_INVALID. */
 
 typedef struct {
   int32_t edge, word;

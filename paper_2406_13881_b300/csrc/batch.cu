@@ -424,7 +424,7 @@ int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts 
       for (int i = next++; i < n; i = next++) {
         if (canon[i] != i) continue;
         std::string e;
-        int rc = ingest(&cfgs[i], &ing[i], &e, o.data_region != 0);
+        int rc = ingest(&cfgs[i], &ing[i], &e, o.data_region != 0, o.eager_to != 0);
         B->ingest_status[i] = rc;
       }
     };
@@ -469,7 +469,9 @@ int ompdart_batch_create(const ompdart_cfg *cfgs, int32_t n, const ompdart_opts 
   std::vector<int32_t> solo_ids;
   for (int i = 0; i < n; ++i) {
     if (B->ingest_status[i]) continue;
-    if (scan_supported(*ingp[i]) && !o.eager_to)  // eager placement: the sweep solver
+    // (eager placement takes no calls: such a CFG fails alone on a plan of its own)
+    const bool calls_eager = o.eager_to && cfgs[i].call_planes && cfgs[i].n_calls > 0;
+    if (scan_supported(*ingp[i]) && !calls_eager)
       by_w[ingp[i]->W].push_back(i);
     else
       solo_ids.push_back(i);

@@ -137,3 +137,16 @@ def test_calls_refused_library_stays_usable():
         _native.analyze(g, eager_to=True)
     assert ei.value.code == _native.E_INVALID
     check(wl.single_small(2))
+
+
+def test_batch_with_a_calls_cfg_fails_it_alone():
+    from test_calls_gpu import structured_with_calls
+    good = [wl.single_small(3), wl.structured(19100, 500, 200)]
+    cfgs = [good[0], structured_with_calls(5, 200, 40), good[1]]
+    b = _native.Batch(cfgs, eager_to=True, keep_states=True)
+    b.run()
+    st = b.sync()
+    assert st[1] == _native.E_INVALID and st[0] == 0 and st[2] == 0
+    for i in (0, 2):
+        assert_matches_oracle(cfgs[i], b.fetch(i), oracle.solve(cfgs[i], eager_to=True))
+    b.close()
