@@ -62,12 +62,12 @@ def workload_name(n_blocks):
 # names the commit its capture was taken at, and an entry is removed when
 # its kernel changes.
 MEASURED_TRAFFIC = {
-    "h_summary": {"bytes_2e18": (319428096 + 268645376),
-                  "profile": "profiles/h_summary_walk_2e18.md", "captured_at": "a52a605"},
-    "live_summary": {"bytes_2e18": (38950144 + 365891328 + 38896384 + 364616960) / 2.0,
-                     "profile": "profiles/live_summary_walk_2e18.md", "captured_at": "a52a605"},
-    "emit": {"bytes_2e18": (743276288 + 110661632 + 743400448 + 110947584 + 743296256 + 110883584) / 3.0,
-             "profile": "profiles/emit_2e18.md", "captured_at": "a52a605"},
+    "h_summary": {"bytes_2e18": 319.27e6 + 268.16e6,
+                  "profile": "profiles/h_summary_walk_2e18.md", "captured_at": "a70e1ed"},
+    "live_summary": {"bytes_2e18": (39.0e6 + 365.88e6 + 38.95e6 + 364.84e6) / 2.0,
+                     "profile": "profiles/live_summary_walk_2e18.md", "captured_at": "a70e1ed"},
+    "emit": {"bytes_2e18": (854.18e6 + 853.99e6 + 854.08e6) / 3.0,
+             "profile": "profiles/emit_2e18.md", "captured_at": "a70e1ed"},
 }
 # DRAM bytes of the batch workload's emission (10,000 CFGs, four arenas),
 # per launch averaged over one run's launches: an ncu capture
