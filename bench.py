@@ -468,6 +468,27 @@ def run_ours(args):
             "map_alloc_vars": int(sum(bin(int(x)).count("1") for x in rv["map_alloc"])),
             "mode": "opts.data_region: the single target data region's exit rule, then the classification pass"}
         del rv
+        # the same step with eager `to' placement (Sec. IV-E, Algorithm 1):
+        # the second backward walk and an edge constant on every edge
+        ep = _native.Plan(g, device=local, chunk_target=args.chunk_target, eager_to=True)
+        for _ in range(3):
+            ep.run(sh)
+            ep.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n_dr):
+            ep.run(sh)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ep.sync()
+        ev_ms = e0.elapsed_time(e1) / n_dr
+        ev = ep.view()
+        out["eager_to"] = {
+            "ms_per_step": ev_ms, "steps": n_dr, "value": g.n_blocks * g.W / (ev_ms / 1e3), "unit": UNIT,
+            "solver": "chunked scan" if ev.path == 2 else "sweep", "edge_transfer_records": int(ev.n_edge_xfers),
+            "mode": "opts.eager_to: device-read must-anticipation, then a `to' on the first edge after the "
+                    "producing host write from which every path reads on the device"}
+        ep.close()
         # the metric's CFGs/s and p50/p99 part: the batch (10,000 CFGs) and
         # the serving streams, each beside its plain one-plan-per-CFG form
         sub = argparse.Namespace(**vars(args))
