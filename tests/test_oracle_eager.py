@@ -248,3 +248,28 @@ def test_planted_to_from_a_stale_host_copy_is_caught():
 
     with pytest.raises(rs.Violation):
         sim_both(g, 1, plant)
+
+
+# --------------------------------------------------------------------------
+# with the single target data region and its directives
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", range(30))
+def test_paths_region_mode_and_directives(seed):
+    """Eager placement in the data-region mode: the raw transfers and the
+    classified program (map clauses, kernel-entry transfers, consolidated
+    updates) both leave no stale read and copy no stale value on any walk,
+    and eager device validity contains the lazy one."""
+    from oracle import classify as C
+    from test_oracle_classify import classified_transfers, kernel_cfg
+    g = kernel_cfg(20000 + seed, int(8 + seed % 16), int(1 + seed % 4))
+    top = (1 << g.n_vars) - 1
+    res = oracle.solve(g, data_region=True, eager_to=True)
+    lazy = oracle.solve(g, data_region=True)
+    assert not (lazy["d_in"] & ~res["d_in"]).any()
+    walks = rs.maximal_walks(g, g.entry, 2)
+    raw = rs.PathSim(g, rs.transfers_from_oracle(g, res), top, 0, top)
+    classified = rs.PathSim(g, classified_transfers(g, res, C.classify(g, res)), top, 0, top)
+    for blocks, edges in walks:
+        raw.run(blocks, edges)
+        classified.run(blocks, edges)
